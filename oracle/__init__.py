@@ -1,0 +1,216 @@
+"""FP64 CPU oracle of the free-surface LBM with moving spheres -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package.  It loads ``fslbm_oracle.c`` compiled with gcc (``build()``) through
+ctypes; the state lives in NumPy arrays owned here, so any state (including one copied
+out of the CUDA library) can be stepped by the oracle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fslbm_oracle.c")
+_LIBPATH = os.path.join(_HERE, "_build", "liboracle_fslbm.so")
+_lib = None
+
+# the oracle's cell-type codes and record layouts (fslbm_oracle.c)
+LIQ, IFACE, GAS, OBS = 1, 2, 4, 8
+S_X, S_U, S_W, S_R, S_RHO, S_F, S_T, S_FLUB, S_LEN = 0, 3, 6, 9, 10, 11, 14, 17, 24
+B_C, B_R, B_V0, B_V, B_RHOG, B_LEN = 0, 3, 4, 5, 6, 8
+SC_POOL, SC_NIF, SC_SBB, SC_SCOV, SC_SUNC, SC_STEPS, SC_STATUS, SC_LEN = 0, 1, 2, 3, 4, 5, 6, 16
+
+
+def build(force: bool = False) -> str:
+    """compile the oracle with gcc (plain C11, no FMA contraction so x86 and Arm agree)"""
+    os.makedirs(os.path.dirname(_LIBPATH), exist_ok=True)
+    if force or not os.path.exists(_LIBPATH) or os.path.getmtime(_LIBPATH) < os.path.getmtime(_SRC):
+        tmp = _LIBPATH + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIBPATH)
+    return _LIBPATH
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("bc", ctypes.c_int32 * 3), ("n_substeps", ctypes.c_int32), ("sphere_mode", ctypes.c_int32),
+                ("nbub", ctypes.c_int32), ("nsph", ctypes.c_int32),
+                ("tau", ctypes.c_double), ("g", ctypes.c_double * 3), ("sigma", ctypes.c_double),
+                ("rho_g0", ctypes.c_double), ("eps", ctypes.c_double), ("near_tol", ctypes.c_double)]
+
+
+_P = ctypes.POINTER
+class _State(ctypes.Structure):
+    _fields_ = [("f", _P(ctypes.c_double)), ("ft", _P(ctypes.c_double)),
+                ("flag", _P(ctypes.c_uint8)), ("mark", _P(ctypes.c_uint8)),
+                ("m", _P(ctypes.c_double)), ("phi", _P(ctypes.c_double)), ("phit", _P(ctypes.c_double)),
+                ("kappa", _P(ctypes.c_double)), ("owner", _P(ctypes.c_int32)), ("nown", _P(ctypes.c_int32)),
+                ("near", _P(ctypes.c_int32)), ("bub", _P(ctypes.c_double)), ("sph", _P(ctypes.c_double)),
+                ("scal", _P(ctypes.c_double))]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        pp, ps = ctypes.POINTER(_Params), ctypes.POINTER(_State)
+        _lib.orc_init.argtypes = [pp, ps]
+        _lib.orc_step.argtypes = [pp, ps, ctypes.c_int]
+        _lib.orc_fields.argtypes = [pp, ps, _P(ctypes.c_double), _P(ctypes.c_double)]
+        _lib.orc_total_mass.argtypes = [pp, ps]
+        _lib.orc_total_mass.restype = ctypes.c_double
+        _lib.orc_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, _P(ctypes.c_double)]
+        _lib.orc_equilibrium.restype = ctypes.c_double
+        _lib.orc_lambda_minus.argtypes = [ctypes.c_double]
+        _lib.orc_lambda_minus.restype = ctypes.c_double
+        _lib.orc_lubrication.argtypes = [pp, ps, _P(ctypes.c_double)]
+        _lib.orc_curvature.argtypes = [pp, ps]
+        _lib.orc_bubble_model.argtypes = [pp, ps]
+        _lib.orc_velocity.argtypes = [ctypes.c_int, ctypes.c_int]
+    return _lib
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+def velocities() -> np.ndarray:
+    """the oracle's D3Q19 velocity table, [19][3]"""
+    L = lib()
+    return np.array([[L.orc_velocity(q, k) for k in range(3)] for q in range(19)], dtype=np.int64)
+
+
+def equilibrium(q: int, rho: float, u) -> float:
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_equilibrium(q, rho, _ptr(u, ctypes.c_double))
+
+
+def lambda_minus(tau: float) -> float:
+    return lib().orc_lambda_minus(tau)
+
+
+class Sim:
+    """FP64 oracle simulation.  Arrays are NumPy, shaped [z][y][x] (PDFs [19][z][y][x])."""
+
+    def __init__(self, wl=None, *, nx=None, ny=None, nz=None, tau=0.6, g=(0, 0, 0), bc=(0, 0, 0), sigma=0.0,
+                 rho_g0=1.0, eps=0.0, near_tol=1e-4, n_substeps=10, sphere_mode=1, bubbles=(), spheres=(),
+                 init=True):
+        if wl is not None:
+            nx, ny, nz, tau, g, bc = wl.nx, wl.ny, wl.nz, wl.tau, wl.g, wl.bc
+            sigma, rho_g0, eps, n_substeps, sphere_mode = wl.sigma, wl.rho_g0, wl.eps, wl.n_substeps, wl.sphere_mode
+            bubbles = [(b.c[0], b.c[1], b.c[2], b.r) for b in wl.bubbles]
+            spheres = [(s.x[0], s.x[1], s.x[2], s.r, s.rho, *s.u, *s.w) for s in wl.spheres]
+        self.shape = (nz, ny, nx)
+        self.N = nx * ny * nz
+        p = _Params()
+        p.nx, p.ny, p.nz = nx, ny, nz
+        for k in range(3):
+            p.bc[k] = int(bc[k])
+            p.g[k] = float(g[k])
+        p.n_substeps, p.sphere_mode = int(n_substeps), int(sphere_mode)
+        p.nbub, p.nsph = len(bubbles), len(spheres)
+        p.tau, p.sigma, p.rho_g0, p.eps, p.near_tol = tau, sigma, rho_g0, eps, near_tol
+        self.p = p
+        N = self.N
+        self.f = np.zeros((19,) + self.shape)
+        self.ft = np.zeros((19,) + self.shape)
+        self.flag = np.zeros(self.shape, np.uint8)
+        self.mark = np.zeros(self.shape, np.uint8)
+        self.m = np.zeros(self.shape)
+        self.phi = np.zeros(self.shape)
+        self.phit = np.zeros(self.shape)
+        self.kappa = np.zeros(self.shape)
+        self.owner = np.full(self.shape, -1, np.int32)
+        self.nown = np.zeros(self.shape, np.int32)
+        self.near = np.zeros(self.shape, np.int32)
+        self.bub = np.zeros((max(1, len(bubbles)), B_LEN))
+        for b, (cx, cy, cz, r) in enumerate(bubbles):
+            self.bub[b, B_C:B_C + 3] = (cx, cy, cz)
+            self.bub[b, B_R] = r
+        self.sph = np.zeros((max(1, len(spheres)), S_LEN))
+        for a, sp in enumerate(spheres):
+            x, y, z, r, rho = sp[:5]
+            u = sp[5:8] if len(sp) >= 8 else (0, 0, 0)
+            w = sp[8:11] if len(sp) >= 11 else (0, 0, 0)
+            self.sph[a, S_X:S_X + 3] = (x, y, z)
+            self.sph[a, S_U:S_U + 3] = u
+            self.sph[a, S_W:S_W + 3] = w
+            self.sph[a, S_R] = r
+            self.sph[a, S_RHO] = rho
+        self.scal = np.zeros(SC_LEN)
+        self._bind()
+        if init:
+            lib().orc_init(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    def _bind(self):
+        s = _State()
+        d, u8, i32 = ctypes.c_double, ctypes.c_uint8, ctypes.c_int32
+        s.f, s.ft = _ptr(self.f, d), _ptr(self.ft, d)
+        s.flag, s.mark = _ptr(self.flag, u8), _ptr(self.mark, u8)
+        s.m, s.phi, s.phit, s.kappa = _ptr(self.m, d), _ptr(self.phi, d), _ptr(self.phit, d), _ptr(self.kappa, d)
+        s.owner, s.nown, s.near = _ptr(self.owner, i32), _ptr(self.nown, i32), _ptr(self.near, i32)
+        s.bub, s.sph, s.scal = _ptr(self.bub, d), _ptr(self.sph, d), _ptr(self.scal, d)
+        self.s = s
+
+    def step(self, n: int = 1) -> int:
+        return lib().orc_step(ctypes.byref(self.p), ctypes.byref(self.s), int(n))
+
+    def fields(self):
+        """(rho [z][y][x], u [3][z][y][x]) of the active cells, 0 elsewhere"""
+        rho = np.zeros(self.shape)
+        u = np.zeros((3,) + self.shape)
+        lib().orc_fields(ctypes.byref(self.p), ctypes.byref(self.s), _ptr(rho, ctypes.c_double), _ptr(u, ctypes.c_double))
+        return rho, u
+
+    def total_mass(self) -> float:
+        return lib().orc_total_mass(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    def mass_budget(self):
+        """(M, S_bb, S_cover, S_uncover, pool)"""
+        return (self.total_mass(), self.scal[SC_SBB], self.scal[SC_SCOV], self.scal[SC_SUNC], self.scal[SC_POOL])
+
+    def lubrication(self) -> np.ndarray:
+        Fl = np.zeros((max(1, int(self.p.nsph)), 3))
+        lib().orc_lubrication(ctypes.byref(self.p), ctypes.byref(self.s), _ptr(Fl, ctypes.c_double))
+        return Fl[: self.p.nsph]
+
+    def curvature(self):
+        lib().orc_curvature(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    def bubble_model(self):
+        lib().orc_bubble_model(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    @property
+    def forces(self):
+        return self.sph[: self.p.nsph, S_F:S_F + 3].copy(), self.sph[: self.p.nsph, S_T:S_T + 3].copy()
+
+    @property
+    def positions(self):
+        return self.sph[: self.p.nsph, S_X:S_X + 3].copy()
+
+    @property
+    def rho_gas(self):
+        return self.bub[: self.p.nbub, B_RHOG].copy()
+
+    @property
+    def volumes(self):
+        return self.bub[: self.p.nbub, B_V].copy()
+
+    def momentum(self, with_positions=False):
+        """total first moment sum_x sum_q c_q f*_q over active cells; optionally also the
+        angular moment sum_x x cross (sum_q c_q f*_q)"""
+        c = velocities().astype(np.float64)
+        act = (self.flag & (LIQ | IFACE)) != 0
+        j = np.einsum("qk,qzyx->kzyx", c, self.f) * act
+        P = j.reshape(3, -1).sum(axis=1)
+        if not with_positions:
+            return P
+        z, y, x = np.meshgrid(*[np.arange(n, dtype=np.float64) for n in self.shape], indexing="ij")
+        X = np.stack([x, y, z])
+        L = np.cross(X.reshape(3, -1).T, j.reshape(3, -1).T).sum(axis=0)
+        return P, L

@@ -1,0 +1,884 @@
+/*
+ * fslbm_oracle.c -- plain FP64 CPU oracle of one time step of the liquid-gas-solid
+ * free-surface lattice Boltzmann method (Bogner, Harting, Ruede, "Direct simulation of
+ * liquid-gas-solid flow with a free surface lattice Boltzmann method", Sec. 2).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously-correct statement of the
+ * method against which the CUDA library is checked.  Only the tests, the smoke check and
+ * the CPU-baseline leg of the benchmark may load it.  It shares no code, header, constant
+ * table or helper with the CUDA library; the only thing both sides share is the seeded
+ * workload generator, which holds none of the method's arithmetic.
+ *
+ * Everything is FP64, single threaded, plain loops, in the order of the step below.
+ * Lattice units: dx = dt = 1, c_s^2 = 1/3, cell (x,y,z) centred at integer coordinates,
+ * linear index i = x + nx*(y + ny*z), PDF q of cell i at f[q*N + i].
+ *
+ * One step t -> t+1 (state between steps: post-collision f*(t)):
+ *   1. sweep over active cells (liquid, interface): pull streaming (Eq. LBE1) with
+ *      halfway bounce-back at walls, moving-wall bounce-back at sphere links (Eq. bbrule)
+ *      with momentum exchange (Eqs. netforce, torque, momentum_transfer), free-surface
+ *      reconstruction from gas neighbours (Eq. fsk), mass exchange of interface cells
+ *      (Eqs. massExchange, massExchangeb), moments, TRT collision (Eq. LBE2) with the
+ *      "magic" parameter 3/16 (Eq. latticeViscosity and the relation below it) and a
+ *      Guo body force (the paper uses gravity without naming a forcing scheme);
+ *   2. cell conversions with layer closure, new-interface initialisation from the
+ *      equilibrium and excess-mass redistribution (Sec. 2.2, Fig. cellConversions);
+ *   3. bubble model: per-bubble volume and gas density (Sec. 2.2, last paragraph);
+ *   4. curvature from fill levels, Parker-Youngs normals (Sec. 2.2, only if sigma > 0);
+ *   5. sphere update: momentum exchange of links between two spheres, lubrication
+ *      correction (Eq. lubrication) and n_substeps Newton-Euler sub-steps (Sec. 2.3);
+ *   6. cells covered / uncovered by the moved spheres, refill of uncovered cells.
+ *
+ * Parity: pinned by the tests (Poiseuille profile, rest-state invariance, exact per-step
+ * mass, momentum and angular-momentum balances, Stokes drag in a periodic array, the
+ * Laplace pressure jump, the layer invariant and brute-force comparison with a NumPy
+ * transcription on tiny grids).  The conversion details of step 2 (new-interface
+ * initialisation, excess weights) and the refill rule of step 6 have no published
+ * numeric check: parity unpinned for those beyond conservation and invariants.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NQ 19
+#define ORC_PI 3.14159265358979323846
+
+/* D3Q19 velocity set: 0 rest, 1..6 faces, 7..18 edges; q and q^ (opposite) are (odd, odd+1). */
+static const int CX[NQ] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+static const int CY[NQ] = {0, 0, 0, 1, -1, 0, 0, 1, -1, -1, 1, 0, 0, 0, 0, 1, -1, 1, -1};
+static const int CZ[NQ] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, -1, -1, 1, 1, -1, -1, 1};
+
+static double wq(int q) { return q == 0 ? 1.0 / 3.0 : (q <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+static int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+
+/* cell types (the oracle's own codes) */
+enum { C_LIQ = 1, C_IF = 2, C_GAS = 4, C_OBS = 8 };
+/* transient marks during conversions / covering */
+enum { M_FILLED = 1, M_EMPTIED = 2, M_NEWIF = 4, M_FROMLIQ = 8, M_UNCOV = 16, M_RECV = 32 };
+
+/* sphere record layout, doubles */
+enum { S_X = 0, S_U = 3, S_W = 6, S_R = 9, S_RHO = 10, S_F = 11, S_T = 14, S_FLUB = 17, S_LEN = 24 };
+/* bubble record layout, doubles */
+enum { B_C = 0, B_R = 3, B_V0 = 4, B_V = 5, B_RHOG = 6, B_LEN = 8 };
+/* scalar slots */
+enum { SC_POOL = 0, SC_NIF = 1, SC_SBB = 2, SC_SCOV = 3, SC_SUNC = 4, SC_STEPS = 5, SC_STATUS = 6, SC_LEN = 16 };
+/* status bits */
+enum { ST_UNSTABLE = 1, ST_BUBBLE_GONE = 2, ST_MERGE = 4 };
+
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t bc[3];          /* 0: no-slip wall (halfway bounce-back), 1: periodic */
+    int32_t n_substeps;     /* sphere sub-steps per LBM step (Sec. 2.3: up to 10) */
+    int32_t sphere_mode;    /* 0: fixed, 1: free Newton-Euler, 2: prescribed constant velocity */
+    int32_t nbub, nsph;
+    double tau;             /* tau = -1/lambda_plus */
+    double g[3];            /* body force per unit mass (gravity) */
+    double sigma;           /* surface tension */
+    double rho_g0;          /* initial gas density of every bubble */
+    double eps;             /* conversion band: fill >= 1+eps -> liquid, fill <= -eps -> gas */
+    double near_tol;        /* band logged as "near a conversion threshold" */
+} orc_params;
+
+typedef struct {
+    double *f, *ft;         /* [19][N] post-collision PDFs; ft is scratch */
+    uint8_t *flag;          /* [N] cell type */
+    uint8_t *mark;          /* [N] scratch */
+    double *m, *phi, *phit; /* [N] interface mass, fill level, scratch */
+    double *kappa;          /* [N] curvature of interface cells */
+    int32_t *owner;         /* [N] bubble id (gas / interface) or sphere id (obstacle), -1 none */
+    int32_t *nown;          /* [N] scratch */
+    int32_t *near;          /* [N] steps at which this interface cell was near a threshold */
+    double *bub;            /* [nbub][B_LEN] */
+    double *sph;            /* [nsph][S_LEN] */
+    double *scal;           /* [SC_LEN] */
+} orc_state;
+
+/* ------------------------------------------------------------------------- helpers */
+
+static long ncell(const orc_params *p) { return (long)p->nx * p->ny * p->nz; }
+
+/* neighbour of (x,y,z) displaced by (dx,dy,dz); periodic axes wrap, wall axes give -1 */
+static long nbr(const orc_params *p, int x, int y, int z, int dx, int dy, int dz)
+{
+    int a = x + dx, b = y + dy, c = z + dz;
+    if (a < 0 || a >= p->nx) { if (!p->bc[0]) return -1; a = (a + p->nx) % p->nx; }
+    if (b < 0 || b >= p->ny) { if (!p->bc[1]) return -1; b = (b + p->ny) % p->ny; }
+    if (c < 0 || c >= p->nz) { if (!p->bc[2]) return -1; c = (c + p->nz) % p->nz; }
+    return (long)a + (long)p->nx * ((long)b + (long)p->ny * c);
+}
+
+/* d = a - b with the minimum-image convention on periodic axes */
+static void mindiff(const orc_params *p, const double a[3], const double b[3], double d[3])
+{
+    const int L[3] = {p->nx, p->ny, p->nz};
+    for (int k = 0; k < 3; k++) {
+        d[k] = a[k] - b[k];
+        if (p->bc[k]) {
+            while (d[k] > 0.5 * L[k]) d[k] -= L[k];
+            while (d[k] < -0.5 * L[k]) d[k] += L[k];
+        }
+    }
+}
+
+static void cross(const double a[3], const double b[3], double c[3])
+{
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+/* Eq. equilibrium: e_q(rho,u) = rho w_q (1 + c.u/cs2 + u u:(c c - cs2 I)/(2 cs2^2)) */
+static double equi(int q, double rho, const double u[3])
+{
+    double cu = CX[q] * u[0] + CY[q] * u[1] + CZ[q] * u[2];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return rho * wq(q) * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+}
+
+/* even part of the equilibrium, e+_q = (e_q + e_q^)/2 */
+static double equi_even(int q, double rho, const double u[3])
+{
+    double cu = CX[q] * u[0] + CY[q] * u[1] + CZ[q] * u[2];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return rho * wq(q) * (1.0 + 4.5 * cu * cu - 1.5 * uu);
+}
+
+/* density and velocity of a post-collision state: rho = sum f*, u = (sum c f* - rho g/2)/rho.
+ * With the Guo force the collision adds rho*g to the first moment, so this u is the
+ * velocity the collision used. */
+static void post_moments(const orc_params *p, const double *f, long N, long i, double *rho, double u[3])
+{
+    double r = 0, j[3] = {0, 0, 0};
+    for (int q = 0; q < NQ; q++) {
+        double v = f[(long)q * N + i];
+        r += v;
+        j[0] += CX[q] * v; j[1] += CY[q] * v; j[2] += CZ[q] * v;
+    }
+    *rho = r;
+    for (int k = 0; k < 3; k++) u[k] = (j[k] - 0.5 * r * p->g[k]) / r;
+}
+
+static void cell_xyz(const orc_params *p, long i, int *x, int *y, int *z)
+{
+    *x = (int)(i % p->nx);
+    *y = (int)((i / p->nx) % p->ny);
+    *z = (int)(i / ((long)p->nx * p->ny));
+}
+
+/* fill level as seen by the normal / curvature stencils: interface -> phi, liquid -> 1,
+ * gas -> 0, sphere cells and cells beyond a wall -> 1 (perfect wetting, Sec. 2.2). */
+static double fill_seen(const orc_params *p, const orc_state *s, int x, int y, int z, int dx, int dy, int dz)
+{
+    long j = nbr(p, x, y, z, dx, dy, dz);
+    if (j < 0) return 1.0;
+    uint8_t t = s->flag[j];
+    if (t & C_IF) return s->phi[j];
+    if (t & C_GAS) return 0.0;
+    return 1.0;
+}
+
+/* Parker-Youngs gradient of the fill level: central difference smoothed by the
+ * [1,2,1] x [1,2,1] / 16 weights over the 3x3x3 block.  Points into the liquid. */
+static void py_gradient(const orc_params *p, const orc_state *s, int x, int y, int z, double n[3])
+{
+    static const double w1[3] = {1.0, 2.0, 1.0};
+    n[0] = n[1] = n[2] = 0.0;
+    for (int a = -1; a <= 1; a++)
+        for (int b = -1; b <= 1; b++) {
+            double w = w1[a + 1] * w1[b + 1];
+            n[0] += w * (fill_seen(p, s, x, y, z, 1, a, b) - fill_seen(p, s, x, y, z, -1, a, b));
+            n[1] += w * (fill_seen(p, s, x, y, z, a, 1, b) - fill_seen(p, s, x, y, z, a, -1, b));
+            n[2] += w * (fill_seen(p, s, x, y, z, a, b, 1) - fill_seen(p, s, x, y, z, a, b, -1));
+        }
+    for (int k = 0; k < 3; k++) n[k] /= 32.0;
+}
+
+static void unit_normal(const orc_params *p, const orc_state *s, int x, int y, int z, double nh[3])
+{
+    double n[3];
+    py_gradient(p, s, x, y, z, n);
+    double l = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    for (int k = 0; k < 3; k++) nh[k] = l > 0 ? n[k] / l : 0.0;
+}
+
+/* ------------------------------------------------------------------ step 4: curvature */
+
+/* kappa = -(1/2) div(n^) (the mean curvature, so that a gas sphere of radius R has
+ * kappa = -1/R and p_w = p_g - 2 sigma / R on its liquid side).  Central differences of
+ * the unit normal; beyond a wall the cell's own normal is used (one-sided difference). */
+static void curvature(const orc_params *p, orc_state *s)
+{
+    const long N = ncell(p);
+    for (long i = 0; i < N; i++) {
+        s->kappa[i] = 0.0;
+        if (!(s->flag[i] & C_IF)) continue;
+        int x, y, z;
+        cell_xyz(p, i, &x, &y, &z);
+        double n0[3];
+        unit_normal(p, s, x, y, z, n0);
+        double div = 0.0;
+        for (int k = 0; k < 3; k++) {
+            int d[3] = {0, 0, 0};
+            double np[3], nm[3];
+            d[k] = 1;
+            if (nbr(p, x, y, z, d[0], d[1], d[2]) >= 0) {
+                int a = x + d[0], b = y + d[1], c = z + d[2];
+                a = (a + p->nx) % p->nx; b = (b + p->ny) % p->ny; c = (c + p->nz) % p->nz;
+                unit_normal(p, s, a, b, c, np);
+            } else {
+                memcpy(np, n0, sizeof np);
+            }
+            d[k] = -1;
+            if (nbr(p, x, y, z, d[0], d[1], d[2]) >= 0) {
+                int a = x + d[0], b = y + d[1], c = z + d[2];
+                a = (a + p->nx) % p->nx; b = (b + p->ny) % p->ny; c = (c + p->nz) % p->nz;
+                unit_normal(p, s, a, b, c, nm);
+            } else {
+                memcpy(nm, n0, sizeof nm);
+            }
+            div += 0.5 * (np[k] - nm[k]);
+        }
+        s->kappa[i] = -0.5 * div;
+    }
+}
+
+/* ---------------------------------------------------------------- step 3: bubble model */
+
+/* V_b = #gas cells of bubble b + sum over its interface cells of (1 - phi);
+ * isothermal ideal gas of conserved mass: rho_g,b = rho_g0 V_b(0) / V_b(t). */
+static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
+{
+    const long N = ncell(p);
+    long nif = 0;
+    for (int b = 0; b < p->nbub; b++) s->bub[b * B_LEN + B_V] = 0.0;
+    for (long i = 0; i < N; i++) {
+        uint8_t t = s->flag[i];
+        int b = s->owner[i];
+        if (t & C_IF) {
+            nif++;
+            if (b >= 0 && b < p->nbub) s->bub[b * B_LEN + B_V] += 1.0 - s->phi[i];
+        } else if (t & C_GAS) {
+            if (b >= 0 && b < p->nbub) s->bub[b * B_LEN + B_V] += 1.0;
+        }
+    }
+    s->scal[SC_NIF] = (double)nif;
+    for (int b = 0; b < p->nbub; b++) {
+        double *B = s->bub + b * B_LEN;
+        if (set_reference) {
+            B[B_V0] = B[B_V];
+            B[B_RHOG] = p->rho_g0;
+        } else if (B[B_V] > 0.0) {
+            B[B_RHOG] = p->rho_g0 * B[B_V0] / B[B_V];
+        } else {
+            s->scal[SC_STATUS] = (double)((int)s->scal[SC_STATUS] | ST_BUBBLE_GONE);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------ step 1: the sweep */
+
+static void sweep(const orc_params *p, orc_state *s, double share)
+{
+    const long N = ncell(p);
+    const double lp = -1.0 / p->tau;                                  /* lambda_+ */
+    const double lm = 1.0 / ((3.0 / 16.0) / (1.0 / lp + 0.5) - 0.5);  /* lambda_- from Lambda = 3/16 */
+    const double *g = p->g;
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                const long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
+                const uint8_t t = s->flag[i];
+                if (!(t & (C_LIQ | C_IF))) continue;
+                double fo[NQ], fin[NQ];
+                for (int q = 0; q < NQ; q++) fo[q] = s->f[(long)q * N + i];
+                double rho0, u0[3];
+                post_moments(p, s->f, N, i, &rho0, u0);
+                const double xc[3] = {(double)x, (double)y, (double)z};
+
+                for (int q = 0; q < NQ; q++) {
+                    const long src = nbr(p, x, y, z, -CX[q], -CY[q], -CZ[q]);
+                    if (src < 0) {                       /* wall: halfway bounce-back */
+                        fin[q] = fo[opp(q)];
+                        continue;
+                    }
+                    const uint8_t ts = s->flag[src];
+                    if (ts & (C_LIQ | C_IF)) {           /* Eq. LBE1 */
+                        fin[q] = s->f[(long)q * N + src];
+                    } else if (ts & C_OBS) {             /* Eq. bbrule at the link midpoint */
+                        double *S = s->sph + (long)s->owner[src] * S_LEN;
+                        const double cq[3] = {CX[q], CY[q], CZ[q]};
+                        double xw[3] = {xc[0] - 0.5 * cq[0], xc[1] - 0.5 * cq[1], xc[2] - 0.5 * cq[2]};
+                        double d[3], wxd[3], uw[3];
+                        mindiff(p, xw, S + S_X, d);
+                        cross(S + S_W, d, wxd);
+                        for (int k = 0; k < 3; k++) uw[k] = S[S_U + k] + wxd[k];
+                        const double cu = cq[0] * uw[0] + cq[1] * uw[1] + cq[2] * uw[2];
+                        /* f_q(x,t+1) = f*_q^(x,t) - 2 e-_q^(rho_w,u_w), e-_q^ = -3 w rho c_q.u */
+                        fin[q] = fo[opp(q)] + 6.0 * wq(q) * rho0 * cu;
+                        /* Eq. momentum_transfer along the link x -> particle (direction q^):
+                         * dj = c_q^ f*_q^(x,t) - c_q f_q(x,t+1) */
+                        double a = fo[opp(q)] + fin[q], dj[3], r[3], rxj[3];
+                        for (int k = 0; k < 3; k++) dj[k] = -cq[k] * a;
+                        mindiff(p, xc, S + S_X, r);
+                        cross(r, dj, rxj);
+                        for (int k = 0; k < 3; k++) {
+                            S[S_F + k] += dj[k];
+                            S[S_T + k] += rxj[k];
+                        }
+                        if (t & C_LIQ) s->scal[SC_SBB] += 6.0 * wq(q) * rho0 * cu;
+                    } else {                             /* gas: Eq. fsk */
+                        const int b = s->owner[src];
+                        const double rg = (b >= 0 && b < p->nbub) ? s->bub[(long)b * B_LEN + B_RHOG] : p->rho_g0;
+                        const double rw = rg + 6.0 * p->sigma * s->kappa[i];
+                        fin[q] = -fo[opp(q)] + 2.0 * equi_even(q, rw, u0);
+                    }
+                }
+
+                double mnew = 0.0;
+                if (t & C_IF) {                          /* Eqs. massExchange, massExchangeb */
+                    double dm = 0.0;
+                    for (int q = 1; q < NQ; q++) {
+                        const long nb = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+                        if (nb < 0) continue;
+                        const uint8_t tn = s->flag[nb];
+                        const double ex = s->f[(long)opp(q) * N + nb] - fo[q];
+                        if (tn & C_LIQ) dm += ex;
+                        else if (tn & C_IF) dm += 0.5 * (s->phi[i] + s->phi[nb]) * ex;
+                    }
+                    mnew = (s->m[i] + share) + dm;
+                }
+
+                /* moments with the Guo half-force shift, then TRT collision (Eq. LBE2) */
+                double rho = 0, j[3] = {0, 0, 0};
+                for (int q = 0; q < NQ; q++) {
+                    rho += fin[q];
+                    j[0] += CX[q] * fin[q]; j[1] += CY[q] * fin[q]; j[2] += CZ[q] * fin[q];
+                }
+                double u[3];
+                for (int k = 0; k < 3; k++) u[k] = (j[k] + 0.5 * rho * g[k]) / rho;
+                const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+                for (int q = 0; q < NQ; q++) {
+                    const int qb = opp(q);
+                    const double cu = CX[q] * u[0] + CY[q] * u[1] + CZ[q] * u[2];
+                    const double cg = CX[q] * g[0] + CY[q] * g[1] + CZ[q] * g[2];
+                    const double ep = wq(q) * rho * (1.0 + 4.5 * cu * cu - 1.5 * uu);
+                    const double em = wq(q) * rho * 3.0 * cu;
+                    const double fp = 0.5 * (fin[q] + fin[qb]);
+                    const double fm = 0.5 * (fin[q] - fin[qb]);
+                    const double Gp = wq(q) * rho * (9.0 * cu * cg - 3.0 * ug);
+                    const double Gm = wq(q) * rho * 3.0 * cg;
+                    s->ft[(long)q * N + i] = fin[q] + lp * (fp - ep) + lm * (fm - em)
+                                           + (1.0 + 0.5 * lp) * Gp + (1.0 + 0.5 * lm) * Gm;
+                }
+                if (!(rho > 0.0) || rho != rho)
+                    s->scal[SC_STATUS] = (double)((int)s->scal[SC_STATUS] | ST_UNSTABLE);
+                if (t & C_IF) {
+                    s->m[i] = mnew;
+                    s->phit[i] = mnew / rho;
+                }
+            }
+    for (long i = 0; i < N; i++)
+        if (s->flag[i] & C_IF) s->phi[i] = s->phit[i];
+}
+
+/* ---------------------------------------------------------------- step 2: conversions */
+
+static void conversions(const orc_params *p, orc_state *s)
+{
+    const long N = ncell(p);
+    double *F = s->ft;  /* f*(t+1) */
+    memset(s->mark, 0, (size_t)N);
+
+    /* (i) interface cells past a threshold; log cells near one */
+    for (long i = 0; i < N; i++) {
+        if (!(s->flag[i] & C_IF)) continue;
+        const double ph = s->phi[i];
+        if (fabs(ph - 1.0) <= p->near_tol || fabs(ph) <= p->near_tol) s->near[i]++;
+        if (ph >= 1.0 + p->eps) s->mark[i] = M_FILLED;
+        else if (ph <= -p->eps) s->mark[i] = M_EMPTIED;
+    }
+    /* (ii) filled cells: gas neighbours become interface, emptied neighbours stay interface */
+    for (long i = 0; i < N; i++) {
+        if (!(s->mark[i] & M_FILLED)) continue;
+        int x, y, z;
+        cell_xyz(p, i, &x, &y, &z);
+        for (int q = 1; q < NQ; q++) {
+            long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+            if (j < 0) continue;
+            if (s->flag[j] & C_GAS) s->mark[j] |= M_NEWIF;
+            if (s->mark[j] & M_EMPTIED) s->mark[j] &= (uint8_t)~M_EMPTIED;
+        }
+    }
+    /* (iii) emptied cells: liquid neighbours become interface with m = rho */
+    for (long i = 0; i < N; i++) {
+        if (!(s->mark[i] & M_EMPTIED)) continue;
+        int x, y, z;
+        cell_xyz(p, i, &x, &y, &z);
+        for (int q = 1; q < NQ; q++) {
+            long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+            if (j < 0 || !(s->flag[j] & C_LIQ)) continue;
+            if (!(s->mark[j] & M_FROMLIQ)) {
+                double r, u[3];
+                post_moments(p, F, N, j, &r, u);
+                s->mark[j] |= M_FROMLIQ;
+                s->m[j] = r;
+                s->owner[j] = s->owner[i];
+            } else if (s->owner[i] >= 0 && (s->owner[j] < 0 || s->owner[i] < s->owner[j])) {
+                s->owner[j] = s->owner[i];
+            }
+        }
+    }
+    /* (iv) new interface cells from gas: equilibrium of the mean density and velocity of
+     * neighbours that carry PDFs (liquid, interface not emptied, filled) */
+    for (long i = 0; i < N; i++) {
+        if (!(s->mark[i] & M_NEWIF)) continue;
+        int x, y, z;
+        cell_xyz(p, i, &x, &y, &z);
+        double rs = 0, us[3] = {0, 0, 0};
+        int n = 0;
+        for (int q = 1; q < NQ; q++) {
+            long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+            if (j < 0 || !(s->flag[j] & (C_LIQ | C_IF)) || (s->mark[j] & M_EMPTIED)) continue;
+            double r, u[3];
+            post_moments(p, F, N, j, &r, u);
+            rs += r;
+            for (int k = 0; k < 3; k++) us[k] += u[k];
+            n++;
+        }
+        double rb = n ? rs / n : 1.0, ub[3];
+        for (int k = 0; k < 3; k++) ub[k] = n ? us[k] / n : 0.0;
+        for (int q = 0; q < NQ; q++) F[(long)q * N + i] = equi(q, rb, ub);
+        s->m[i] = 0.0;
+    }
+    /* (v) excess mass of converting cells to the neighbours that will be interface cells,
+     * weighted by the interface normal pointing into the gas (n_g = -grad phi):
+     * filled -> max(0, n_g.c_q), emptied -> max(0, -n_g.c_q); uniform if all weights vanish;
+     * into the global pool if there is no such neighbour.  The normal sees the fill levels
+     * and cell types of the sweep result, before any conversion. */
+    for (long i = 0; i < N; i++) {
+        const uint8_t mk = s->mark[i];
+        if (!(mk & (M_FILLED | M_EMPTIED))) continue;
+        int x, y, z;
+        cell_xyz(p, i, &x, &y, &z);
+        double ng[3];
+        py_gradient(p, s, x, y, z, ng);
+        for (int k = 0; k < 3; k++) ng[k] = -ng[k];
+        double r, u[3];
+        post_moments(p, F, N, i, &r, u);
+        double mex;
+        if (mk & M_FILLED) { mex = s->m[i] - r; s->m[i] = r; }
+        else { mex = s->m[i]; s->m[i] = 0.0; }
+        long rec[NQ];
+        double wr[NQ], W = 0.0;
+        int nr = 0;
+        for (int q = 1; q < NQ; q++) {
+            long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+            if (j < 0) continue;
+            const uint8_t mj = s->mark[j];
+            const int is_rec = ((s->flag[j] & C_IF) && !(mj & (M_FILLED | M_EMPTIED))) ||
+                               (mj & (M_NEWIF | M_FROMLIQ));
+            if (!is_rec) continue;
+            double nc = ng[0] * CX[q] + ng[1] * CY[q] + ng[2] * CZ[q];
+            double w = (mk & M_FILLED) ? (nc > 0 ? nc : 0.0) : (nc < 0 ? -nc : 0.0);
+            rec[nr] = j;
+            wr[nr] = w;
+            W += w;
+            nr++;
+        }
+        if (nr == 0) {
+            s->scal[SC_POOL] += mex;
+            continue;
+        }
+        for (int k = 0; k < nr; k++) {
+            s->m[rec[k]] += W > 0.0 ? mex * (wr[k] / W) : mex / nr;
+            s->mark[rec[k]] |= M_RECV;
+        }
+    }
+    /* (vi) finalise types; fill level of every interface cell whose mass changed here */
+    for (long i = 0; i < N; i++) {
+        const uint8_t mk = s->mark[i];
+        if (!mk) continue;
+        if (mk & M_FILLED) { s->flag[i] = C_LIQ; s->owner[i] = -1; }
+        else if (mk & M_EMPTIED) { s->flag[i] = C_GAS; }
+        else if (mk & (M_NEWIF | M_FROMLIQ)) { s->flag[i] = C_IF; }
+    }
+    for (long i = 0; i < N; i++) {
+        const uint8_t mk = s->mark[i];
+        if (!(mk & (M_NEWIF | M_FROMLIQ | M_RECV)) || !(s->flag[i] & C_IF)) continue;
+        double r, u[3];
+        post_moments(p, F, N, i, &r, u);
+        s->phi[i] = s->m[i] / r;
+    }
+}
+
+/* --------------------------------------------------------------- step 5: the spheres */
+
+static double sphere_mass(const double *S) { return S[S_RHO] * 4.0 / 3.0 * ORC_PI * S[S_R] * S[S_R] * S[S_R]; }
+
+static int covers(const orc_params *p, const double *S, int x, int y, int z)
+{
+    const double xc[3] = {(double)x, (double)y, (double)z};
+    double d[3];
+    mindiff(p, xc, S + S_X, d);
+    return d[0] * d[0] + d[1] * d[1] + d[2] * d[2] <= S[S_R] * S[S_R];
+}
+
+/* Links between obstacle nodes of two different spheres: the node inside sphere P' is
+ * given the equilibrium e_q(1, u_P'(x)) of its own sphere's surface velocity (Sec. 2.3,
+ * end of the momentum-exchange paragraph), reflected by Eq. bbrule with rho_w = 1. */
+static void contact_links(const orc_params *p, orc_state *s)
+{
+    const long N = ncell(p);
+    for (long i = 0; i < N; i++) {
+        if (!(s->flag[i] & C_OBS)) continue;
+        int x, y, z;
+        cell_xyz(p, i, &x, &y, &z);
+        const double xc[3] = {(double)x, (double)y, (double)z};
+        const double *Sp = s->sph + (long)s->owner[i] * S_LEN;
+        for (int q = 1; q < NQ; q++) {
+            long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+            if (j < 0 || !(s->flag[j] & C_OBS) || s->owner[j] == s->owner[i]) continue;
+            double *S = s->sph + (long)s->owner[j] * S_LEN;
+            const double cq[3] = {CX[q], CY[q], CZ[q]};
+            double d[3], wxd[3], us[3], uw[3];
+            mindiff(p, xc, Sp + S_X, d);
+            cross(Sp + S_W, d, wxd);
+            for (int k = 0; k < 3; k++) us[k] = Sp[S_U + k] + wxd[k];
+            const double fstar = equi(q, 1.0, us);
+            double xw[3] = {xc[0] + 0.5 * cq[0], xc[1] + 0.5 * cq[1], xc[2] + 0.5 * cq[2]};
+            mindiff(p, xw, S + S_X, d);
+            cross(S + S_W, d, wxd);
+            for (int k = 0; k < 3; k++) uw[k] = S[S_U + k] + wxd[k];
+            const double cu = cq[0] * uw[0] + cq[1] * uw[1] + cq[2] * uw[2];
+            const double fback = fstar - 6.0 * wq(q) * 1.0 * cu;
+            double dj[3], r[3], rxj[3];
+            for (int k = 0; k < 3; k++) dj[k] = cq[k] * (fstar + fback);
+            mindiff(p, xc, S + S_X, r);
+            cross(r, dj, rxj);
+            for (int k = 0; k < 3; k++) {
+                S[S_F + k] += dj[k];
+                S[S_T + k] += rxj[k];
+            }
+        }
+    }
+}
+
+/* Eq. lubrication for every pair with gap < Delta_c = 2/3, gap floored at 0.2 Delta_c,
+ * mu = rho nu with rho = 1; +F on the first sphere, -F on the second. */
+static void lubrication(const orc_params *p, orc_state *s, double *Fl)
+{
+    const double dc = 2.0 / 3.0, mu = (p->tau - 0.5) / 3.0;
+    for (long a = 0; a < 3L * p->nsph; a++) Fl[a] = 0.0;
+    for (int a = 0; a < p->nsph; a++)
+        for (int b = a + 1; b < p->nsph; b++) {
+            const double *A = s->sph + (long)a * S_LEN, *B = s->sph + (long)b * S_LEN;
+            double d[3];
+            mindiff(p, B + S_X, A + S_X, d);  /* x_12 = x_2 - x_1 */
+            const double dist = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double h = dist - A[S_R] - B[S_R];
+            if (!(h < dc) || dist <= 0.0) continue;
+            if (h < 0.2 * dc) h = 0.2 * dc;
+            const double rr = A[S_R] * B[S_R], rs = A[S_R] + B[S_R];
+            double n[3] = {d[0] / dist, d[1] / dist, d[2] / dist};
+            const double vn = n[0] * (A[S_U] - B[S_U]) + n[1] * (A[S_U + 1] - B[S_U + 1]) + n[2] * (A[S_U + 2] - B[S_U + 2]);
+            const double mag = -6.0 * ORC_PI * mu * rr * rr / (rs * rs) * (1.0 / h - 1.0 / dc) * vn;
+            for (int k = 0; k < 3; k++) {
+                Fl[3 * a + k] += mag * n[k];
+                Fl[3 * b + k] -= mag * n[k];
+            }
+        }
+}
+
+static void wrap_position(const orc_params *p, double *X)
+{
+    const int L[3] = {p->nx, p->ny, p->nz};
+    for (int k = 0; k < 3; k++)
+        if (p->bc[k]) {
+            while (X[k] >= L[k] - 0.5) X[k] -= L[k];
+            while (X[k] < -0.5) X[k] += L[k];
+        }
+}
+
+/* Newton-Euler in n_substeps semi-implicit Euler sub-steps: the hydrodynamic force and
+ * torque of the sweep are held, lubrication and gravity are re-evaluated each sub-step. */
+static void move_spheres(const orc_params *p, orc_state *s)
+{
+    if (p->nsph == 0) return;
+    if (p->sphere_mode == 2) {
+        for (int a = 0; a < p->nsph; a++) {
+            double *S = s->sph + (long)a * S_LEN;
+            for (int k = 0; k < 3; k++) S[S_X + k] += S[S_U + k];
+            wrap_position(p, S + S_X);
+        }
+        return;
+    }
+    if (p->sphere_mode != 1) return;
+    double *Fl = (double *)calloc((size_t)3 * p->nsph, sizeof(double));
+    const double dt = 1.0 / p->n_substeps;
+    for (int sub = 0; sub < p->n_substeps; sub++) {
+        lubrication(p, s, Fl);
+        for (int a = 0; a < p->nsph; a++) {
+            double *S = s->sph + (long)a * S_LEN;
+            const double mp = sphere_mass(S), I = 0.4 * mp * S[S_R] * S[S_R];
+            for (int k = 0; k < 3; k++) {
+                S[S_FLUB + k] = Fl[3 * a + k];
+                S[S_U + k] += dt * (S[S_F + k] + Fl[3 * a + k] + mp * p->g[k]) / mp;
+                S[S_W + k] += dt * S[S_T + k] / I;
+            }
+            for (int k = 0; k < 3; k++) S[S_X + k] += dt * S[S_U + k];
+            wrap_position(p, S + S_X);
+        }
+    }
+    free(Fl);
+}
+
+/* ---------------------------------------------------- step 6: cover / uncover, refill */
+
+static void box_range(const orc_params *p, const double *S, int k, int *lo, int *hi)
+{
+    const int L[3] = {p->nx, p->ny, p->nz};
+    *lo = (int)floor(S[S_X + k] - S[S_R]) - 1;
+    *hi = (int)ceil(S[S_X + k] + S[S_R]) + 1;
+    if (!p->bc[k]) {
+        if (*lo < 0) *lo = 0;
+        if (*hi > L[k] - 1) *hi = L[k] - 1;
+    }
+}
+
+static void cover_uncover(const orc_params *p, orc_state *s)
+{
+    const long N = ncell(p);
+    for (long i = 0; i < N; i++) s->nown[i] = -1;
+    for (int a = 0; a < p->nsph; a++) {
+        const double *S = s->sph + (long)a * S_LEN;
+        int lo[3], hi[3];
+        for (int k = 0; k < 3; k++) box_range(p, S, k, lo + k, hi + k);
+        for (int zz = lo[2]; zz <= hi[2]; zz++)
+            for (int yy = lo[1]; yy <= hi[1]; yy++)
+                for (int xx = lo[0]; xx <= hi[0]; xx++) {
+                    int x = (xx % p->nx + p->nx) % p->nx, y = (yy % p->ny + p->ny) % p->ny, z = (zz % p->nz + p->nz) % p->nz;
+                    long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
+                    if (s->nown[i] < 0 && covers(p, S, x, y, z)) s->nown[i] = a;
+                }
+    }
+    memset(s->mark, 0, (size_t)N);
+    for (long i = 0; i < N; i++) {
+        if (s->flag[i] & C_OBS) {
+            if (s->nown[i] < 0) s->mark[i] = M_UNCOV;
+            else s->owner[i] = s->nown[i];
+        } else if (s->nown[i] >= 0) {
+            if (s->flag[i] & C_LIQ) {
+                double r, u[3];
+                post_moments(p, s->f, N, i, &r, u);
+                s->scal[SC_SCOV] += r;
+            } else if (s->flag[i] & C_IF) {
+                s->scal[SC_SCOV] += s->m[i];
+            }
+            s->flag[i] = C_OBS;
+            s->owner[i] = s->nown[i];
+        }
+    }
+    /* refill: neighbours that are neither obstacle nor uncovered in this step decide the
+     * type; PDFs are the equilibrium of their mean density and the sphere's surface velocity */
+    for (long i = 0; i < N; i++) {
+        if (!(s->mark[i] & M_UNCOV)) continue;
+        int x, y, z;
+        cell_xyz(p, i, &x, &y, &z);
+        int ngas = 0, nfl = 0, gas_owner = -1;
+        double rs = 0, ps = 0;
+        for (int q = 1; q < NQ; q++) {
+            long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+            if (j < 0 || (s->flag[j] & C_OBS) || (s->mark[j] & M_UNCOV)) continue;
+            if (s->flag[j] & C_GAS) {
+                if (gas_owner < 0) gas_owner = s->owner[j];
+                ngas++;
+            } else {
+                double r, u[3];
+                post_moments(p, s->f, N, j, &r, u);
+                rs += r;
+                ps += (s->flag[j] & C_IF) ? s->phi[j] : 1.0;
+                nfl++;
+            }
+        }
+        const double *S = s->sph + (long)s->owner[i] * S_LEN;
+        const double xc[3] = {(double)x, (double)y, (double)z};
+        double d[3], wxd[3], uf[3];
+        mindiff(p, xc, S + S_X, d);
+        cross(S + S_W, d, wxd);
+        for (int k = 0; k < 3; k++) uf[k] = S[S_U + k] + wxd[k];
+        if (nfl == 0 && ngas > 0) {
+            s->flag[i] = C_GAS;
+            s->owner[i] = gas_owner;
+            s->m[i] = 0.0;
+            s->phi[i] = 0.0;
+            continue;
+        }
+        const double rb = nfl ? rs / nfl : 1.0;
+        if (ngas > 0) {
+            const double pb = ps / nfl;
+            s->flag[i] = C_IF;
+            s->owner[i] = gas_owner;
+            s->phi[i] = pb;
+            s->m[i] = pb * rb;
+            s->scal[SC_SUNC] += s->m[i];
+        } else {
+            s->flag[i] = C_LIQ;
+            s->owner[i] = -1;
+            s->phi[i] = 1.0;
+            s->m[i] = rb;
+            s->scal[SC_SUNC] += rb;
+        }
+        for (int q = 0; q < NQ; q++) s->f[(long)q * N + i] = equi(q, rb, uf);
+    }
+}
+
+/* ------------------------------------------------------------------------ public API */
+
+/* Initial state (spherical bubbles in quiescent liquid, then spheres):
+ * phi = prod_b clamp(|x - c_b| - (r_b - 1/2), 0, 1); gas if 0, liquid if 1, else interface;
+ * liquid cells with a gas neighbour become interface cells (phi = 1) to close the layer;
+ * f* = e(1, 0), m = phi; cells with |x - x_P|^2 <= R^2 become obstacle cells of the lowest
+ * such sphere id; then the bubble model sets V_b(0) and rho_g = rho_g0. */
+int orc_init(const orc_params *p, orc_state *s)
+{
+    const long N = ncell(p);
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                const long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
+                double ph = 1.0;
+                int own = -1;
+                for (int b = 0; b < p->nbub; b++) {
+                    const double *B = s->bub + b * B_LEN;
+                    const double xc[3] = {(double)x, (double)y, (double)z};
+                    double d[3];
+                    mindiff(p, xc, B + B_C, d);
+                    double v = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]) - (B[B_R] - 0.5);
+                    if (v < 0) v = 0;
+                    if (v > 1) v = 1;
+                    if (v < 1.0 && own < 0) own = b;
+                    ph *= v;
+                }
+                s->phi[i] = ph;
+                s->owner[i] = own;
+                s->flag[i] = ph <= 0.0 ? C_GAS : (ph >= 1.0 ? C_LIQ : C_IF);
+            }
+    memset(s->mark, 0, (size_t)N);
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                const long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
+                if (!(s->flag[i] & C_LIQ)) continue;
+                for (int q = 1; q < NQ; q++) {
+                    long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+                    if (j >= 0 && (s->flag[j] & C_GAS)) {
+                        s->mark[i] = 1;
+                        s->owner[i] = s->owner[j];
+                        break;
+                    }
+                }
+            }
+    const double u0[3] = {0, 0, 0};
+    for (long i = 0; i < N; i++) {
+        if (s->mark[i]) { s->flag[i] = C_IF; s->phi[i] = 1.0; }
+        if (s->flag[i] & C_LIQ) s->owner[i] = -1;
+        s->m[i] = s->phi[i];
+        s->kappa[i] = 0.0;
+        s->near[i] = 0;
+        for (int q = 0; q < NQ; q++) s->f[(long)q * N + i] = equi(q, 1.0, u0);
+    }
+    for (int a = 0; a < p->nsph; a++) {
+        const double *S = s->sph + (long)a * S_LEN;
+        int lo[3], hi[3];
+        for (int k = 0; k < 3; k++) box_range(p, S, k, lo + k, hi + k);
+        for (int zz = lo[2]; zz <= hi[2]; zz++)
+            for (int yy = lo[1]; yy <= hi[1]; yy++)
+                for (int xx = lo[0]; xx <= hi[0]; xx++) {
+                    int x = (xx % p->nx + p->nx) % p->nx, y = (yy % p->ny + p->ny) % p->ny, z = (zz % p->nz + p->nz) % p->nz;
+                    long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
+                    if (!(s->flag[i] & C_OBS) && covers(p, S, x, y, z)) {
+                        s->flag[i] = C_OBS;
+                        s->owner[i] = a;
+                        s->m[i] = 0.0;
+                        s->phi[i] = 1.0;
+                    }
+                }
+    }
+    for (int k = 0; k < SC_LEN; k++) s->scal[k] = 0.0;
+    bubble_model(p, s, 1);
+    if (p->sigma > 0.0) curvature(p, s);
+    return 0;
+}
+
+int orc_step(const orc_params *p, orc_state *s, int nsteps)
+{
+    const long N = ncell(p);
+    for (int it = 0; it < nsteps; it++) {
+        /* excess mass that found no receiving neighbour last step, spread evenly */
+        double share = 0.0;
+        if (s->scal[SC_POOL] != 0.0) {
+            long nif = 0;
+            for (long i = 0; i < N; i++) nif += (s->flag[i] & C_IF) ? 1 : 0;
+            if (nif > 0) {
+                share = s->scal[SC_POOL] / (double)nif;
+                s->scal[SC_POOL] = 0.0;
+            }
+        }
+        for (int a = 0; a < p->nsph; a++)
+            for (int k = 0; k < 6; k++) s->sph[(long)a * S_LEN + S_F + k] = 0.0;
+        sweep(p, s, share);                                        /* 1 */
+        conversions(p, s);                                         /* 2 */
+        memcpy(s->f, s->ft, sizeof(double) * (size_t)NQ * (size_t)N);
+        bubble_model(p, s, 0);                                     /* 3 */
+        if (p->sigma > 0.0) curvature(p, s);                       /* 4 */
+        contact_links(p, s);                                       /* 5 */
+        move_spheres(p, s);
+        if (p->sphere_mode != 0 && p->nsph > 0) cover_uncover(p, s); /* 6 */
+        s->scal[SC_STEPS] += 1.0;
+    }
+    return (int)s->scal[SC_STATUS];
+}
+
+/* rho and velocity (Guo-shifted, the one the collision used) of every active cell; 0 elsewhere */
+void orc_fields(const orc_params *p, const orc_state *s, double *rho, double *u)
+{
+    const long N = ncell(p);
+    for (long i = 0; i < N; i++) {
+        double r = 0, v[3] = {0, 0, 0};
+        if (s->flag[i] & (C_LIQ | C_IF)) post_moments(p, s->f, N, i, &r, v);
+        rho[i] = r;
+        for (int k = 0; k < 3; k++) u[(long)k * N + i] = v[k];
+    }
+}
+
+/* mass of the liquid: sum over liquid cells of rho plus sum over interface cells of m,
+ * plus the undistributed excess pool */
+double orc_total_mass(const orc_params *p, const orc_state *s)
+{
+    const long N = ncell(p);
+    double M = 0.0;
+    for (long i = 0; i < N; i++) {
+        if (s->flag[i] & C_LIQ) {
+            double r, u[3];
+            post_moments(p, s->f, N, i, &r, u);
+            M += r;
+        } else if (s->flag[i] & C_IF) {
+            M += s->m[i];
+        }
+    }
+    return M + s->scal[SC_POOL];
+}
+
+/* the pieces of the method exposed for unit pins */
+double orc_equilibrium(int q, double rho, const double *u) { return equi(q, rho, u); }
+double orc_lambda_minus(double tau)
+{
+    const double lp = -1.0 / tau;
+    return 1.0 / ((3.0 / 16.0) / (1.0 / lp + 0.5) - 0.5);
+}
+void orc_lubrication(const orc_params *p, orc_state *s, double *Fl) { lubrication(p, s, Fl); }
+void orc_curvature(const orc_params *p, orc_state *s) { curvature(p, s); }
+void orc_bubble_model(const orc_params *p, orc_state *s) { bubble_model(p, s, 0); }
+int orc_velocity(int q, int k) { return k == 0 ? CX[q] : (k == 1 ? CY[q] : CZ[q]); }

@@ -1,0 +1,221 @@
+"""Seeded synthetic workloads: domain, bubbles and spheres of the bubble-particle columns.
+
+This module only *places* things.  It holds none of the method's arithmetic, so both the
+CUDA path and the CPU oracle may take their inputs from it.
+
+Random numbers come from splitmix64 (Steele, Lea, Flood 2014) mapped to uniform doubles
+by the top 53 bits.  Placement is rejection sampling, bubbles first, then spheres, with
+every sampled centre rounded to integer cell coordinates (cells sit at integer
+coordinates 0..n-1).  The shapes follow the paper's bubble-in-particle-bed runs
+(Sec. 4: a spherical bubble rising through a random bed of resolved spheres of about five
+cells per diameter) scaled to what one GPU holds.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Tuple
+
+_MASK = (1 << 64) - 1
+
+
+class SplitMix64:
+    """splitmix64 generator; ``uniform()`` returns a double in [0, 1)."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform(self) -> float:
+        return (self.next_u64() >> 11) * (1.0 / 9007199254740992.0)
+
+    def uniform_in(self, lo: float, hi: float) -> float:
+        return lo + (hi - lo) * self.uniform()
+
+
+WALL, PERIODIC = 0, 1
+STORAGE = {"f32": 0, "f16dev": 1, "bf16dev": 2}
+SPHERES_FIXED, SPHERES_FREE, SPHERES_PRESCRIBED = 0, 1, 2
+
+
+@dataclasses.dataclass
+class Sphere:
+    x: Tuple[float, float, float]
+    r: float
+    rho: float
+    u: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    w: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+
+
+@dataclasses.dataclass
+class Bubble:
+    c: Tuple[float, float, float]
+    r: float
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    tau: float = 0.6
+    g: Tuple[float, float, float] = (0.0, 0.0, 0.0)
+    bc: Tuple[int, int, int] = (WALL, WALL, WALL)
+    sigma: float = 0.0
+    rho_g0: float = 1.0
+    eps: float = 0.0
+    n_substeps: int = 10
+    sphere_mode: int = SPHERES_FREE
+    storage: str = "f32"
+    steps: int = 1
+    bubbles: List[Bubble] = dataclasses.field(default_factory=list)
+    spheres: List[Sphere] = dataclasses.field(default_factory=list)
+
+    @property
+    def cells(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def describe(self) -> dict:
+        return {
+            "workload": self.name,
+            "grid": [self.nx, self.ny, self.nz],
+            "tau": self.tau,
+            "g": list(self.g),
+            "bubbles": len(self.bubbles),
+            "spheres": len(self.spheres),
+            "storage": self.storage,
+        }
+
+
+class _Hash:
+    """uniform-grid hash of sphere centres for the rejection test"""
+
+    def __init__(self, h: float):
+        self.h = h
+        self.cells = {}
+
+    def key(self, p):
+        return tuple(int(math.floor(v / self.h)) for v in p)
+
+    def near(self, p):
+        k = self.key(p)
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    yield from self.cells.get((k[0] + dx, k[1] + dy, k[2] + dz), ())
+
+    def add(self, p):
+        self.cells.setdefault(self.key(p), []).append(p)
+
+
+def _dist2(a, b):
+    return (a[0] - b[0]) ** 2 + (a[1] - b[1]) ** 2 + (a[2] - b[2]) ** 2
+
+
+def place_bubbles(rng: SplitMix64, n, r, dims, zrange, gap):
+    """n bubbles of radius r, centres uniform in x,y in [r+2, n-3-r] and z in zrange,
+    centre distance >= 2r + gap"""
+    out = []
+    for _ in range(200000):
+        if len(out) == n:
+            break
+        c = (round(rng.uniform_in(r + 2, dims[0] - 3 - r)),
+             round(rng.uniform_in(r + 2, dims[1] - 3 - r)),
+             round(rng.uniform_in(zrange[0], zrange[1])))
+        if all(_dist2(c, b.c) >= (2 * r + gap) ** 2 for b in out):
+            out.append(Bubble(c=tuple(float(v) for v in c), r=float(r)))
+    if len(out) != n:
+        raise RuntimeError("bubble placement failed")
+    return out
+
+
+def place_spheres(rng: SplitMix64, n, R, rho, dims, bubbles, max_tries=None):
+    """n spheres of radius R, centres uniform in [R+1, n-2-R] per axis; rejection keeps
+    centre distances >= 2R+1 between spheres and >= r_b+R+2 to every bubble centre"""
+    h = 2 * R + 1
+    grid = _Hash(h)
+    out = []
+    tries = 0
+    max_tries = max_tries or 200 * n + 1000
+    while len(out) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("sphere placement failed after %d tries (%d placed)" % (tries, len(out)))
+        c = (round(rng.uniform_in(R + 1, dims[0] - 2 - R)),
+             round(rng.uniform_in(R + 1, dims[1] - 2 - R)),
+             round(rng.uniform_in(R + 1, dims[2] - 2 - R)))
+        if any(_dist2(c, b.c) < (b.r + R + 2) ** 2 for b in bubbles):
+            continue
+        if any(_dist2(c, o) < h * h for o in grid.near(c)):
+            continue
+        grid.add(c)
+        out.append(Sphere(x=tuple(float(v) for v in c), r=float(R), rho=float(rho)))
+    return out
+
+
+def column_c0() -> Workload:
+    """32^3, walls, tau 0.6, gravity 1e-5 along -z, one gas bubble r=6 at (16,16,10) and one
+    sphere r=3 of density 2.0 at (16,16,22), 200 steps"""
+    return Workload(name="column32_bubble_sphere", nx=32, ny=32, nz=32, tau=0.6, g=(0.0, 0.0, -1e-5),
+                    steps=200, bubbles=[Bubble((16.0, 16.0, 10.0), 6.0)],
+                    spheres=[Sphere((16.0, 16.0, 22.0), 3.0, 2.0)])
+
+
+def column_c1() -> Workload:
+    """128^3 FP32, walls, gravity 1e-6, one bubble r=16 at (64,64,32), 64 spheres r=4 of
+    density 1.5, seed 1, 2000 steps"""
+    dims = (128, 128, 128)
+    rng = SplitMix64(1)
+    bubbles = [Bubble((64.0, 64.0, 32.0), 16.0)]
+    spheres = place_spheres(rng, 64, 4, 1.5, dims, bubbles)
+    return Workload(name="column128_1bubble_64spheres", nx=128, ny=128, nz=128, tau=0.6, g=(0.0, 0.0, -1e-6),
+                    steps=2000, bubbles=bubbles, spheres=spheres)
+
+
+def periodic_array_c2() -> Workload:
+    """96^3 periodic, liquid only, 27 static spheres r=4 on a jittered 32-lattice (seed 2),
+    body force 1e-5 along +x, 500-step window"""
+    rng = SplitMix64(2)
+    spheres = []
+    for k in range(3):
+        for j in range(3):
+            for i in range(3):
+                c = tuple(float(round(16 + 32 * a + rng.uniform_in(-2.0, 2.0))) for a in (i, j, k))
+                spheres.append(Sphere(c, 4.0, 1.5))
+    return Workload(name="periodic96_27spheres", nx=96, ny=96, nz=96, tau=0.6, g=(1e-5, 0.0, 0.0),
+                    bc=(PERIODIC, PERIODIC, PERIODIC), sphere_mode=SPHERES_FIXED, steps=500,
+                    spheres=spheres)
+
+
+def column_c3(storage="f32") -> Workload:
+    """256x256x512, walls, gravity 1e-6, 8 bubbles r=16 in z in [40,256] (gap >= 8),
+    20000 spheres r=4 of density 1.5, seed 3, 5000 steps"""
+    dims = (256, 256, 512)
+    rng = SplitMix64(3)
+    bubbles = place_bubbles(rng, 8, 16, dims, (40, 256), 8)
+    spheres = place_spheres(rng, 20000, 4, 1.5, dims, bubbles)
+    return Workload(name="column256x256x512_8bubbles_20000spheres", nx=256, ny=256, nz=512, tau=0.6,
+                    g=(0.0, 0.0, -1e-6), steps=5000, bubbles=bubbles, spheres=spheres, storage=storage)
+
+
+def column_c4(storage="f16dev") -> Workload:
+    """512x512x1024, FP16-deviation storage, gravity 1e-6, 32 bubbles r=24 in z in [56,512],
+    100000 spheres r=4 of density 1.5, seed 4, 2000 steps"""
+    dims = (512, 512, 1024)
+    rng = SplitMix64(4)
+    bubbles = place_bubbles(rng, 32, 24, dims, (56, 512), 8)
+    spheres = place_spheres(rng, 100000, 4, 1.5, dims, bubbles)
+    return Workload(name="column512x512x1024_32bubbles_100000spheres", nx=512, ny=512, nz=1024, tau=0.6,
+                    g=(0.0, 0.0, -1e-6), steps=2000, bubbles=bubbles, spheres=spheres, storage=storage)
+
+
+def liquid_box(n=32, bc=(WALL, WALL, WALL), g=(0.0, 0.0, 0.0), tau=0.6, name=None) -> Workload:
+    """an all-liquid box, the simplest case of the sweep"""
+    return Workload(name=name or "liquid%d" % n, nx=n, ny=n, nz=n, tau=tau, g=g, bc=bc)
