@@ -1,0 +1,317 @@
+#!/usr/bin/env python
+"""Throughput of the fused free-surface LBM step (MLUPS) on the 128^3 bubble-particle column.
+
+One step = the whole per-step hot path: sweep (stream, bounce-back, gas reconstruction,
+mass exchange, TRT collision), cell conversions, bubble model, sphere update and
+cover/uncover.  Workload: 128^3 cells, walls, tau 0.6, gravity 1e-6 along -z, one gas
+bubble r=16 at (64,64,32), 64 spheres r=4 of density 1.5 placed by seeded rejection
+sampling, FP32 PDFs (two grids of 19 x 8 MB planes: inputs larger than L2).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
+Under torchrun every rank runs an independent replica (the method needs no exchange
+between replicas; one GPU per domain).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and HBM-roofline fraction, FP32 / FP16-store vs FP64 oracle error"
+FALLBACK_HBM_GBS = 6800.0
+
+# dram bytes (read + write) per sweep launch on this workload from one ncu capture, with the
+# hash of the sweep source it was taken on (null once the kernel changes)
+NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c3", "c4"])
+    ap.add_argument("--storage", default=None, choices=[None, "f32", "f16dev", "bf16dev"])
+    ap.add_argument("--no-extras", action="store_true", help="only the timed region (for profilers)")
+    return ap.parse_args()
+
+
+def _workload(name, storage=None):
+    from paper_1712_07028_gb300 import workloads as W
+    wl = {"c0": W.column_c0, "c1": W.column_c1, "c3": W.column_c3, "c4": W.column_c4}[name]()
+    if storage:
+        wl.storage = storage
+    return wl
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region"""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.1)
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4) if r[5 + k].strip() == "Active"})
+        load = sorted(sm)[len(sm) // 2:] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _gpu_index(torch, local):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        return vis.split(",")[local].strip()
+    return local
+
+
+def _peak_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _sweep_sha():
+    h = hashlib.sha1()
+    for n in ("lbm_sweep.cu", "lbm_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1712_07028_gb300", "csrc", n), "rb").read())
+    return h.hexdigest()
+
+
+def _cpu_baseline(wl, steps):
+    """the FP64 oracle as it stands, single thread, on a bounded sample of the workload"""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    o = oracle.Sim(wl)
+    t1 = time.perf_counter()
+    o.step(steps)
+    t2 = time.perf_counter()
+    return {"value": wl.cells * steps / (t2 - t1) / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "FP64 oracle, %s (%d cells): init (%.1f s) + %d full steps timed (%.1f s)"
+                      % (wl.name, wl.cells, t1 - t0, steps, t2 - t1)}
+
+
+def _oracle_error(torch, lbm, W):
+    """error of the GPU path against the FP64 oracle on the 32^3 column after 200 steps, per
+    PDF storage (the max over cells active in both, away from type mismatches)"""
+    import numpy as np
+    import oracle
+    from tests import gpu_util as U
+    oracle.build()
+    base = W.column_c0()
+    o = oracle.Sim(base)
+    o.step(base.steps)
+    out = {}
+    for storage in ("f32", "f16dev", "bf16dev"):
+        wl = W.column_c0()
+        wl.storage = storage
+        sim = lbm.Sim(wl)
+        sim.step(wl.steps)
+        st = U.gpu_state(sim)
+        mism = st["flags"] != o.flag
+        drho, du, _ = U.compare_fields(o, st, ~U.dilate(mism, 2))
+        iface = (st["flags"] == oracle.IFACE) & (o.flag == oracle.IFACE) & ~U.dilate(mism, 2)
+        dphi = float(np.abs(st["phi"] - o.phi)[iface].max()) if iface.any() else 0.0
+        out[storage] = {"max_abs_drho": float(drho), "max_abs_du": float(du), "max_abs_dphi": dphi,
+                        "type_mismatches": int(mism.sum())}
+        sim.close()
+    out["case"] = "32^3 column (bubble r=6, sphere r=3), 200 steps"
+    return out
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    wl = _workload(args.workload)
+    # each timed step is one full oracle step of the workload; the number of executed steps is
+    # capped so the whole run stays within about a minute
+    o = oracle.Sim(wl)
+    t = time.perf_counter()
+    o.step(1)
+    t_step = time.perf_counter() - t
+    warm = max(0, min(args.warmup, 2) - 1)
+    o.step(warm)
+    k = max(1, min(args.steps, int(60.0 / max(t_step, 1e-3))))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    v = wl.cells * k / dt / 1e6
+    line = {"metric": METRIC, "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / k * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny, wl.nz], "bubbles": len(wl.bubbles),
+                       "spheres": len(wl.spheres), "storage": "f64 (oracle)", "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "%d of %d requested steps executed after %d warm-up (each a full FP64 oracle step of %d cells)"
+                                       % (k, args.steps, warm + 1, wl.cells)},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1712_07028_gb300 import lbm
+    from paper_1712_07028_gb300 import workloads as W
+    lbm.load()
+    wl = _workload(args.workload, args.storage)
+    s_bytes = 4 if wl.storage == "f32" else 2
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sim = lbm.Sim(wl)
+    sim.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(_gpu_index(torch, local))
+    clocks.start()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    n0 = sim.launches()
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    launches = sim.launches() - n0
+    ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = sim.status()
+    value = wl.cells * args.steps * ws / (ms * 1e-3) / 1e6
+
+    line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if wl.storage == "f32" else "f32 (" + wl.storage + " storage)",
+            "data": "synthetic",
+            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny, wl.nz], "bubbles": len(wl.bubbles),
+                       "spheres": len(wl.spheres), "storage": wl.storage, "tau": wl.tau, "g": list(wl.g),
+                       "l2": "inputs larger than L2 (PDF grids %.0f MB each)" % (19 * wl.cells * s_bytes / 1e6),
+                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+            "gpu_launches": launches, "clocks": clk, "status": st}
+
+    if not args.no_extras:
+        # roofline of the dominant kernel (the sweep): CUDA events around each launch
+        sim.profile(True)
+        kp = min(args.steps, 400)
+        sim.step(kp)
+        torch.cuda.synchronize()
+        sweep_ms, nsw = sim.profile_read()
+        sim.profile(False)
+        fl = sim.fields()["flags"]
+        n_act = int(((fl == lbm.CELL_LIQUID) | (fl == lbm.CELL_INTERFACE)).sum().item())
+        per_launch = n_act * (38 * s_bytes + 1) + (wl.cells - n_act) * 1
+        avg_s = sweep_ms / max(1, nsw) * 1e-3
+        peak, peak_kind = _peak_hbm()
+        achieved = per_launch / avg_s / 1e9
+        traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == _sweep_sha() else None
+        line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                            "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
+                            "kernel": "sweep_kernel", "algorithmic_bytes_per_launch": per_launch,
+                            "active_cells": n_act, "avg_launch_ms": avg_s * 1e3, "launches_timed": nsw,
+                            "sweep_mlups": wl.cells / avg_s / 1e6}
+        sim.close()
+        del sim
+        torch.cuda.synchronize()
+
+        # end to end through the public API from host inputs: context and tables from the host,
+        # every step followed by the device->host read of the sphere forces (synchronising), the
+        # fields copied to host at the end
+        ke = min(args.steps, 1000)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim2 = lbm.Sim(wl)
+        for _ in range(ke):
+            sim2.step(1)
+            sim2.forces()
+        fields = {k: v.cpu() for k, v in sim2.fields().items()}
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        h2d, d2h = sim2.copy_bytes()
+        d2h += sum(v.numel() * v.element_size() for v in fields.values())
+        line["e2e"] = {"value": wl.cells * ke * ws / (t1 - t0) / 1e6, "unit": "MLUPS",
+                       "h2d_bytes_per_step": h2d / ke, "d2h_bytes_per_step": d2h / ke, "steps": ke,
+                       "includes": "context + table upload + field init, per step lbm_step + lbm_forces "
+                                   "(D2H of the sphere/bubble tables, sync), final fields D2H"}
+        sim2.close()
+        if rank == 0 and ws == 1:
+            line["cpu_baseline"] = _cpu_baseline(wl, 20 if wl.cells <= 2_200_000 else 2)
+            line["oracle_error"] = _oracle_error(torch, lbm, W)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

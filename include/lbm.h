@@ -1,0 +1,192 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) free-surface lattice Boltzmann library for
+ * liquid-gas-solid flow (Bogner, Harting, Ruede, "Direct simulation of liquid-gas-solid
+ * flow with a free surface lattice Boltzmann method").
+ *
+ * One time step (lbm_step) is the paper's per-step hot path, on the GPU:
+ *   - D3Q19 pull streaming (Sec. 2.1, Eq. LBE1) with halfway bounce-back at no-slip walls
+ *     or periodic wrap per axis;
+ *   - moving-wall bounce-back on sphere links (Sec. 2.3, Eq. bbrule) with the
+ *     momentum-exchange force and torque (Eqs. netforce, torque, momentum_transfer);
+ *   - gas-side PDF reconstruction from each bubble's gas pressure (Sec. 2.2, Eq. fsk, with
+ *     p_w = p_g + 2 sigma kappa when sigma > 0);
+ *   - fill-level-weighted mass exchange of interface cells (Eqs. massExchange,
+ *     massExchangeb);
+ *   - TRT collision with the magic parameter 3/16 (Eq. LBE2, Eq. latticeViscosity and the
+ *     relation below it) and a Guo gravity force;
+ *   - interface / liquid / gas conversions with layer closure, equilibrium initialisation
+ *     of new interface cells and excess-mass redistribution (Sec. 2.2, Fig.
+ *     cellConversions);
+ *   - the bubble model (per-bubble volume -> gas density, Sec. 2.2);
+ *   - sphere update: lubrication correction (Eq. lubrication) and Newton-Euler sub-steps
+ *     (Sec. 2.3), then cells covered / uncovered by the moved spheres and PDF refill.
+ *
+ * Conventions for every call:
+ *   - lattice units (dx = dt = 1); cell (x,y,z) is centred at integer coordinates and has
+ *     linear index i = x + nx*(y + ny*z); N = nx*ny*nz;
+ *   - the library never allocates device memory: all device state lives in one caller-owned
+ *     arena (lbm_arena_bytes / lbm_init); the library never frees it;
+ *   - work is enqueued on the caller's CUDA stream and is asynchronous, except where a call
+ *     says it synchronises;
+ *   - every call returns LBM_OK (0) or a negative LBM_E* code; no exception crosses the ABI;
+ *   - a pointer documented as "device" must point to device memory of the current device,
+ *     "host" to host memory; sizes are counts of elements unless stated otherwise.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define LBM_OK 0
+#define LBM_EINVAL (-1)      /* bad argument */
+#define LBM_ESTATE (-2)      /* call not allowed in the current state */
+#define LBM_ECUDA (-3)       /* a CUDA runtime call failed */
+#define LBM_EUNSTABLE (-4)   /* a cell's density became non-positive or NaN */
+#define LBM_EOVERFLOW (-5)   /* a conversion worklist or a sphere bin overflowed */
+
+/* per-axis boundary kind */
+#define LBM_BC_WALL 0        /* no-slip wall halfway beyond the outermost cells */
+#define LBM_BC_PERIODIC 1
+
+/* PDF storage between steps (collisions always run in FP32) */
+#define LBM_STORE_F32 0      /* f stored as FP32 */
+#define LBM_STORE_F16DEV 1   /* f - w_q stored as IEEE half */
+#define LBM_STORE_BF16DEV 2  /* f - w_q stored as bfloat16 */
+
+/* sphere motion */
+#define LBM_SPHERES_FIXED 0       /* x, u, w held; u, w still act as surface velocity */
+#define LBM_SPHERES_FREE 1        /* Newton-Euler with lubrication and sub-steps (Sec. 2.3) */
+#define LBM_SPHERES_PRESCRIBED 2  /* x advances by u every step, u and w held */
+
+/* cell types reported by lbm_fields / lbm_export_state */
+#define LBM_CELL_LIQUID 1
+#define LBM_CELL_INTERFACE 2
+#define LBM_CELL_GAS 4
+#define LBM_CELL_OBSTACLE 8
+
+/* status bits (lbm_status) */
+#define LBM_S_UNSTABLE 1u        /* density <= 0 or NaN in some cell */
+#define LBM_S_OVERFLOW 2u        /* a conversion / covering worklist overflowed */
+#define LBM_S_BUBBLE_GONE 4u     /* a bubble's volume reached zero */
+#define LBM_S_BIN_OVERFLOW 8u    /* more spheres in a neighbour-search bin than it holds */
+
+typedef struct lbm_params {
+    int32_t nx, ny, nz;        /* grid size, each >= 3 */
+    int32_t bc[3];             /* LBM_BC_* per axis */
+    int32_t storage;           /* LBM_STORE_* */
+    int32_t n_substeps;        /* sphere sub-steps per LBM step, 1..64 (the paper: up to 10) */
+    int32_t sphere_mode;       /* LBM_SPHERES_* */
+    int32_t max_bubbles;       /* capacity of the bubble table, >= 1 */
+    int32_t max_spheres;       /* capacity of the sphere table, >= 1 */
+    int32_t worklist_cap;      /* entries per conversion worklist; 0 = N/50 + 4096 */
+    double tau;                /* relaxation time, lambda_+ = -1/tau, tau > 1/2 */
+    double g[3];               /* body force per unit mass (gravity) */
+    double sigma;              /* surface tension (0: no curvature term) */
+    double rho_gas0;           /* initial gas density of every bubble (1 = liquid reference) */
+    double eps;                /* conversion band: fill >= 1+eps fills, fill <= -eps empties */
+} lbm_params;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Size in bytes of the device arena a simulation with these parameters needs (all PDF
+ * grids, per-cell fields, tables, worklists and scratch).  p: host.  Returns LBM_EINVAL for
+ * invalid parameters. */
+int lbm_arena_bytes(const lbm_params* p, size_t* bytes);
+
+/* Create a simulation over a caller-owned device arena of at least lbm_arena_bytes(p)
+ * bytes, 256-byte aligned.  The arena must stay alive and untouched by the caller until
+ * lbm_destroy.  cuda_stream: the cudaStream_t all work goes to (NULL = legacy default
+ * stream).  *out receives a host-side handle.  Nothing is written to the device until the
+ * first lbm_step. */
+int lbm_init(const lbm_params* p, void* arena, size_t arena_bytes, void* cuda_stream, lbm_ctx** out);
+
+/* Switch the stream subsequent calls enqueue on. */
+int lbm_set_stream(lbm_ctx* ctx, void* cuda_stream);
+
+/* Add a spherical gas bubble of centre c[3] (host) and radius r (> 0).  Only before the
+ * first lbm_step (else LBM_ESTATE).  *id (host, may be NULL) receives its index.
+ * Initial fill level (Sec. 3.2 / 4: a spherical bubble in quiescent liquid):
+ * phi = prod_b clamp(|x - c_b| - (r_b - 1/2), 0, 1). */
+int lbm_add_bubble(lbm_ctx* ctx, const double c[3], double r, int* id);
+
+/* Add a sphere (Sec. 2.3): centre c[3], radius r, density rho_p, velocity u[3], angular
+ * velocity w[3] (all host).  Only before the first lbm_step.  Cells with
+ * |x - c|^2 <= r^2 become its obstacle cells (the lowest sphere id wins where spheres
+ * overlap). */
+int lbm_add_sphere(lbm_ctx* ctx, const double c[3], double r, double rho_p, const double u[3],
+                   const double w[3], int* id);
+
+/* Advance nsteps >= 0 time steps.  The first call initialises the fields on the device
+ * (liquid at rest, bubbles, layer closure, spheres).  Asynchronous: problems found on the
+ * device are latched in the status word and reported by lbm_status / lbm_forces. */
+int lbm_step(lbm_ctx* ctx, int nsteps);
+
+/* Momentum-exchange force F[n][3] and torque T[n][3] (host, FP64) of the last step, for
+ * the first n spheres (hydrodynamic part only: no lubrication, no gravity).  Synchronises
+ * the stream.  Returns the status as an error code if the status word is set. */
+int lbm_forces(lbm_ctx* ctx, double* F, double* T, int n);
+
+/* Sphere state x[n][3], u[n][3], w[n][3] (host, FP64; any may be NULL).  Synchronises. */
+int lbm_spheres(lbm_ctx* ctx, double* x, double* u, double* w, int n);
+
+/* Bubble table (host, FP64; any may be NULL): reference volume V0[n], volume V[n], gas
+ * density rho_g[n].  Synchronises. */
+int lbm_bubbles(lbm_ctx* ctx, double* V0, double* V, double* rho_g, int n);
+
+/* Macroscopic fields into caller device buffers (any may be NULL): rho[N] and u[3][N]
+ * (post-collision moments, u = (sum c f* - rho g / 2) / rho, the velocity the collision
+ * used; 0 in inactive cells), phi[N] (fill level: 1 liquid, 0 gas, phi interface, 1
+ * obstacle), flags[N] (LBM_CELL_*).  Asynchronous. */
+int lbm_fields(lbm_ctx* ctx, float* rho, float* u, float* phi, uint8_t* flags);
+
+/* Full state into caller device buffers (any may be NULL): f[19][N] post-collision PDFs in
+ * FP32 (full values whatever the storage; undefined in inactive cells), flags[N]
+ * (LBM_CELL_*), mass[N] (interface mass), phi[N], owner[N] (bubble id of gas / interface
+ * cells, sphere id of obstacle cells, -1 otherwise), kappa[N] (curvature; 0 if sigma = 0).
+ * D3Q19 order: q = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (+1,+1,0),(-1,-1,0),(+1,-1,0),
+ * (-1,+1,0),(+1,0,+1),(-1,0,-1),(+1,0,-1),(-1,0,+1),(0,+1,+1),(0,-1,-1),(0,+1,-1),(0,-1,+1).
+ * Asynchronous. */
+int lbm_export_state(lbm_ctx* ctx, float* f, uint8_t* flags, float* mass, float* phi, int32_t* owner, float* kappa);
+
+/* Mass budget (host out[5], FP64): total liquid mass M = sum_liquid rho + sum_interface m +
+ * pool, moving-bounce-back source S_bb, mass removed by covering S_cover, mass added by
+ * refill S_uncover, undistributed excess pool.  M - M(0) - S_bb - S_uncover + S_cover is
+ * the drift.  Synchronises. */
+int lbm_mass_budget(lbm_ctx* ctx, double out[5]);
+
+/* Latched status bits (LBM_S_*) into *status (host).  Synchronises. */
+int lbm_status(lbm_ctx* ctx, uint32_t* status);
+
+/* Timing of the sweep kernel (the dominant one): while on != 0, lbm_step launches steps
+ * one by one (no CUDA graph) and records a CUDA event pair around each sweep launch on the
+ * stream it runs on. */
+int lbm_profile(lbm_ctx* ctx, int on);
+
+/* Sum of the recorded sweep durations in milliseconds (host *sweep_ms) and their number
+ * (host *sweeps) since the last read; waits for the recorded events.  Resets both. */
+int lbm_profile_read(lbm_ctx* ctx, double* sweep_ms, uint64_t* sweeps);
+
+/* Bytes the library itself has copied host -> device (*h2d) and device -> host (*d2h)
+ * so far (table uploads, copy-out calls), both host pointers. */
+int lbm_copy_bytes(lbm_ctx* ctx, uint64_t* h2d, uint64_t* d2h);
+
+/* Kernel launches enqueued so far (each node of a replayed CUDA graph counts). */
+int lbm_launch_count(lbm_ctx* ctx, uint64_t* launches);
+
+/* Release the host-side handle (the arena stays the caller's). */
+int lbm_destroy(lbm_ctx* ctx);
+
+/* Static text for a return code. */
+const char* lbm_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_GB300_H */

@@ -1,0 +1,532 @@
+// lbm_capi.cu -- the C ABI (include/lbm.h): arena layout, host-side handle and the launch
+// sequence of one time step.  The library allocates no device memory: everything lives in
+// the caller's arena.  Work goes to the caller's stream; one step is recorded once into a
+// CUDA graph (two steps, for the two grid parities) and replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    lbm_params p;
+    Dev d;
+    cudaStream_t stream;
+    char* arena;
+    size_t arena_bytes;
+    std::vector<double> bub_geo;     // [nbub][4] centre, radius
+    std::vector<Sphere> sph_init;
+    bool started;
+    int cur;
+    uint64_t launches;
+    int per_step;
+    double* geo_dev;
+    Sphere* sph_stage;
+    Scalars* sc_stage;
+    Bubble* bub_stage;
+    // graph of two consecutive steps (cur = 0 then 1)
+    cudaGraphExec_t graph;
+    bool graph_ready;
+    bool use_graph;
+    // optional timing of the sweep kernel: CUDA events around each launch, on its stream
+    bool profiling;
+    cudaEvent_t ev[2 * 64];
+    bool ev_ready;
+    bool ev_pending[64];
+    int ev_slot;
+    double sweep_ms;
+    uint64_t sweeps;
+    uint64_t h2d_bytes, d2h_bytes;   // host <-> device copies made by the library
+};
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kBinCap = 16;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+int check_params(const lbm_params* p) {
+    if (!p) return LBM_EINVAL;
+    if (p->nx < 3 || p->ny < 3 || p->nz < 3) return LBM_EINVAL;
+    if ((double)p->nx * p->ny * p->nz > 4.0e9) return LBM_EINVAL;
+    for (int k = 0; k < 3; k++)
+        if (p->bc[k] != LBM_BC_WALL && p->bc[k] != LBM_BC_PERIODIC) return LBM_EINVAL;
+    if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16DEV) return LBM_EINVAL;
+    if (p->n_substeps < 1 || p->n_substeps > 64) return LBM_EINVAL;
+    if (p->sphere_mode < LBM_SPHERES_FIXED || p->sphere_mode > LBM_SPHERES_PRESCRIBED) return LBM_EINVAL;
+    if (p->max_bubbles < 1 || p->max_spheres < 1 || p->worklist_cap < 0) return LBM_EINVAL;
+    if (!(p->tau > 0.5) || !(p->tau < 100.0)) return LBM_EINVAL;
+    if (!(p->sigma >= 0.0) || !(p->rho_gas0 > 0.0) || !(p->eps >= 0.0)) return LBM_EINVAL;
+    return LBM_OK;
+}
+
+size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
+
+struct Layout {
+    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, acc, sc, wl[4], bin_cnt, bin_ids, geo, total;
+    size_t N, wl_cap, nbins_max;
+};
+
+Layout layout_of(const lbm_params* p) {
+    Layout L{};
+    L.N = (size_t)p->nx * p->ny * p->nz;
+    L.wl_cap = p->worklist_cap > 0 ? (size_t)p->worklist_cap : L.N / 50 + 4096;
+    // bins are at least 4 cells wide
+    L.nbins_max = (size_t)((p->nx + 3) / 4) * ((p->ny + 3) / 4) * ((p->nz + 3) / 4);
+    size_t o = 0;
+    auto take = [&](size_t bytes) { size_t at = o; o = align_up(o + bytes); return at; };
+    L.f[0] = take(19 * L.N * pdf_bytes(p));
+    L.f[1] = take(19 * L.N * pdf_bytes(p));
+    L.flags = take(L.N + 16);
+    L.mark = take(L.N + 16);
+    L.mass = take(4 * L.N);
+    L.phi[0] = take(4 * L.N);
+    L.phi[1] = take(4 * L.N);
+    L.owner = take(4 * L.N);
+    L.kappa = p->sigma > 0.0 ? take(4 * L.N) : 0;
+    L.bub = take(sizeof(Bubble) * (size_t)p->max_bubbles);
+    L.sph = take(sizeof(Sphere) * (size_t)p->max_spheres);
+    L.sph_tmp = take(sizeof(Sphere) * (size_t)p->max_spheres);
+    L.acc = take(sizeof(SphereAcc) * (size_t)p->max_spheres);
+    L.sc = take(sizeof(Scalars));
+    for (int k = 0; k < 4; k++) L.wl[k] = take(4 * L.wl_cap);
+    L.bin_cnt = take(4 * L.nbins_max);
+    L.bin_ids = take(4 * L.nbins_max * kBinCap);
+    L.geo = take(sizeof(double) * 4 * (size_t)p->max_bubbles);
+    L.total = o;
+    return L;
+}
+
+int cuda_fail(cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    std::fprintf(stderr, "lbm: CUDA error %s\n", cudaGetErrorString(e));
+    return LBM_ECUDA;
+}
+
+int launched(lbm_ctx* c, int n) {
+    c->launches += (uint64_t)n;
+    return cuda_fail(cudaGetLastError());
+}
+
+int status_code(uint32_t st) {
+    if (st & S_UNSTABLE) return LBM_EUNSTABLE;
+    if (st & (S_OVERFLOW | S_BIN_OVERFLOW)) return LBM_EOVERFLOW;
+    return LBM_OK;
+}
+
+// kernels of one step, in the order of the method
+int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
+    const Dev& d = c->d;
+    const int nxt = cur ^ 1;
+    launch_sweep(d, cur, s);
+    launch_conversions(d, nxt, s);
+    launch_bubbles(d, nxt, s);
+    if (d.kappa) launch_curvature(d, nxt, s);
+    launch_spheres(d, nxt, s);
+    launch_step_end(d, s);
+    return cuda_fail(cudaGetLastError());
+}
+
+// collect the elapsed time of a recorded (start, end) pair
+void prof_collect(lbm_ctx* c, int slot) {
+    if (!c->ev_pending[slot]) return;
+    cudaEventSynchronize(c->ev[2 * slot + 1]);
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[2 * slot], c->ev[2 * slot + 1]) == cudaSuccess) {
+        c->sweep_ms += ms;
+        c->sweeps++;
+    }
+    c->ev_pending[slot] = false;
+}
+
+// one step with the sweep bracketed by events (profiling mode, eager launches)
+int enqueue_step_timed(lbm_ctx* c, int cur, cudaStream_t s) {
+    const Dev& d = c->d;
+    const int nxt = cur ^ 1;
+    const int slot = c->ev_slot;
+    c->ev_slot = (c->ev_slot + 1) % 64;
+    prof_collect(c, slot);
+    cudaEventRecord(c->ev[2 * slot], s);
+    launch_sweep(d, cur, s);
+    cudaEventRecord(c->ev[2 * slot + 1], s);
+    c->ev_pending[slot] = true;
+    launch_conversions(d, nxt, s);
+    launch_bubbles(d, nxt, s);
+    if (d.kappa) launch_curvature(d, nxt, s);
+    launch_spheres(d, nxt, s);
+    launch_step_end(d, s);
+    return cuda_fail(cudaGetLastError());
+}
+
+int count_per_step(const Dev& d) { return 1 + 6 + 1 + (d.kappa ? 1 : 0) + spheres_launches(d) + 1; }
+
+int first_step(lbm_ctx* c) {
+    const lbm_params* p = &c->p;
+    Layout L = layout_of(p);
+    char* a = c->arena;
+    Dev& d = c->d;
+    std::memset(&d, 0, sizeof d);
+    d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
+    for (int k = 0; k < 3; k++) d.bc[k] = p->bc[k];
+    d.N = L.N;
+    d.storage = p->storage;
+    d.n_sub = p->n_substeps;
+    d.sphere_mode = p->sphere_mode;
+    d.nbub = (int)(c->bub_geo.size() / 4);
+    d.nsph = (int)c->sph_init.size();
+    d.max_bub = p->max_bubbles;
+    d.max_sph = p->max_spheres;
+    d.wl_cap = (int)L.wl_cap;
+    d.tau = (float)p->tau;
+    const double lp = -1.0 / p->tau;
+    d.lp = (float)lp;
+    d.lm = (float)(1.0 / ((3.0 / 16.0) / (1.0 / lp + 0.5) - 0.5));
+    for (int k = 0; k < 3; k++) { d.g[k] = (float)p->g[k]; d.gd[k] = p->g[k]; }
+    d.sigma = (float)p->sigma;
+    d.rho_g0 = (float)p->rho_gas0;
+    d.eps = (float)p->eps;
+    d.f[0] = a + L.f[0];
+    d.f[1] = a + L.f[1];
+    d.flags = (uint8_t*)(a + L.flags);
+    d.mark = (uint8_t*)(a + L.mark);
+    d.mass = (float*)(a + L.mass);
+    d.phi[0] = (float*)(a + L.phi[0]);
+    d.phi[1] = (float*)(a + L.phi[1]);
+    d.owner = (uint32_t*)(a + L.owner);
+    d.kappa = p->sigma > 0.0 ? (float*)(a + L.kappa) : nullptr;
+    d.bub = (Bubble*)(a + L.bub);
+    d.sph = (Sphere*)(a + L.sph);
+    d.sph_tmp = (Sphere*)(a + L.sph_tmp);
+    d.acc = (SphereAcc*)(a + L.acc);
+    d.sc = (Scalars*)(a + L.sc);
+    d.wl_conv = (uint32_t*)(a + L.wl[0]);
+    d.wl_newif = (uint32_t*)(a + L.wl[1]);
+    d.wl_fromliq = (uint32_t*)(a + L.wl[2]);
+    d.wl_touch = (uint32_t*)(a + L.wl[3]);
+    double rmax = 1.0;
+    for (const Sphere& s : c->sph_init) rmax = std::fmax(rmax, s.R);
+    d.bin_w = (int)std::ceil(2.0 * rmax + 2.0);
+    if (d.bin_w < 4) d.bin_w = 4;
+    d.nbx = p->nx / d.bin_w > 0 ? p->nx / d.bin_w : 1;
+    d.nby = p->ny / d.bin_w > 0 ? p->ny / d.bin_w : 1;
+    d.nbz = p->nz / d.bin_w > 0 ? p->nz / d.bin_w : 1;
+    d.bin_cap = kBinCap;
+    d.bin_cnt = (uint32_t*)(a + L.bin_cnt);
+    d.bin_ids = (uint32_t*)(a + L.bin_ids);
+    c->geo_dev = (double*)(a + L.geo);
+
+    cudaStream_t s = c->stream;
+    int rc = cuda_fail(cudaMemsetAsync(a, 0, L.total, s));
+    if (rc) return rc;
+    if (d.nbub > 0)
+        if ((rc = cuda_fail(cudaMemcpyAsync(c->geo_dev, c->bub_geo.data(), sizeof(double) * c->bub_geo.size(), cudaMemcpyHostToDevice, s)))) return rc;
+    if (d.nsph > 0)
+        if ((rc = cuda_fail(cudaMemcpyAsync(d.sph, c->sph_init.data(), sizeof(Sphere) * d.nsph, cudaMemcpyHostToDevice, s)))) return rc;
+    c->h2d_bytes += sizeof(double) * c->bub_geo.size() + sizeof(Sphere) * (size_t)d.nsph;
+    launch_bins_insert(d, s);
+    launch_init(d, c->geo_dev, s);
+    launch_bulk_all(d, s);
+    launch_bubbles(d, 0, s);
+    if (d.kappa) launch_curvature(d, 0, s);
+    launch_step_end_reference(d, s);
+    if ((rc = launched(c, (d.nsph > 0) + 4 + (d.kappa ? 1 : 0)))) return rc;
+    c->cur = 0;
+    c->per_step = count_per_step(d);
+    c->started = true;
+    return cuda_fail(cudaStreamSynchronize(s));
+}
+
+int build_graph(lbm_ctx* c) {
+    cudaStream_t cap;
+    if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
+    cudaGraph_t g = nullptr;
+    int rc = LBM_OK;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = LBM_ECUDA;
+    if (!rc) {
+        enqueue_step(c, 0, cap);
+        enqueue_step(c, 1, cap);
+        if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = LBM_ECUDA;
+    }
+    if (!rc && cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) rc = LBM_ECUDA;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    cudaGetLastError();
+    c->graph_ready = rc == LBM_OK;
+    return rc;
+}
+
+int sync_tables(lbm_ctx* c) {
+    cudaStream_t s = c->stream;
+    int rc;
+    c->d2h_bytes += sizeof(Scalars) + sizeof(Sphere) * (size_t)c->d.nsph + sizeof(Bubble) * (size_t)c->d.nbub;
+    if ((rc = cuda_fail(cudaMemcpyAsync(c->sc_stage, c->d.sc, sizeof(Scalars), cudaMemcpyDeviceToHost, s)))) return rc;
+    if (c->d.nsph > 0)
+        if ((rc = cuda_fail(cudaMemcpyAsync(c->sph_stage, c->d.sph, sizeof(Sphere) * c->d.nsph, cudaMemcpyDeviceToHost, s)))) return rc;
+    if (c->d.nbub > 0)
+        if ((rc = cuda_fail(cudaMemcpyAsync(c->bub_stage, c->d.bub, sizeof(Bubble) * c->d.nbub, cudaMemcpyDeviceToHost, s)))) return rc;
+    return cuda_fail(cudaStreamSynchronize(s));
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_arena_bytes(const lbm_params* p, size_t* bytes) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!bytes) return LBM_EINVAL;
+    *bytes = layout_of(p).total;
+    return LBM_OK;
+}
+
+int lbm_init(const lbm_params* p, void* arena, size_t arena_bytes, void* cuda_stream, lbm_ctx** out) {
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!arena || !out || ((uintptr_t)arena % kAlign)) return LBM_EINVAL;
+    if (arena_bytes < layout_of(p).total) return LBM_EINVAL;
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return LBM_EINVAL;
+    c->p = *p;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->arena = (char*)arena;
+    c->arena_bytes = arena_bytes;
+    c->started = false;
+    c->cur = 0;
+    c->launches = 0;
+    c->graph_ready = false;
+    c->use_graph = std::getenv("LBM_NO_GRAPH") == nullptr;
+    c->profiling = false;
+    c->ev_ready = false;
+    for (int k = 0; k < 64; k++) c->ev_pending[k] = false;
+    c->ev_slot = 0;
+    c->sweep_ms = 0.0;
+    c->sweeps = 0;
+    c->h2d_bytes = 0;
+    c->d2h_bytes = 0;
+    c->sph_stage = (Sphere*)std::malloc(sizeof(Sphere) * (size_t)p->max_spheres);
+    c->sc_stage = (Scalars*)std::malloc(sizeof(Scalars));
+    c->bub_stage = (Bubble*)std::malloc(sizeof(Bubble) * (size_t)p->max_bubbles);
+    if (!c->sph_stage || !c->sc_stage || !c->bub_stage) { lbm_destroy(c); return LBM_EINVAL; }
+    *out = c;
+    return LBM_OK;
+}
+
+int lbm_set_stream(lbm_ctx* c, void* cuda_stream) {
+    if (!c) return LBM_EINVAL;
+    c->stream = (cudaStream_t)cuda_stream;
+    return LBM_OK;
+}
+
+int lbm_add_bubble(lbm_ctx* c, const double cen[3], double r, int* id) {
+    if (!c || !cen || !(r > 0.0)) return LBM_EINVAL;
+    if (c->started) return LBM_ESTATE;
+    if ((int)(c->bub_geo.size() / 4) >= c->p.max_bubbles) return LBM_EINVAL;
+    if (id) *id = (int)(c->bub_geo.size() / 4);
+    c->bub_geo.insert(c->bub_geo.end(), {cen[0], cen[1], cen[2], r});
+    return LBM_OK;
+}
+
+int lbm_add_sphere(lbm_ctx* c, const double cen[3], double r, double rho_p, const double u[3], const double w[3], int* id) {
+    if (!c || !cen || !(r > 0.0) || !(rho_p > 0.0)) return LBM_EINVAL;
+    if (c->started) return LBM_ESTATE;
+    if ((int)c->sph_init.size() >= c->p.max_spheres) return LBM_EINVAL;
+    Sphere s;
+    std::memset(&s, 0, sizeof s);
+    for (int k = 0; k < 3; k++) {
+        s.x[k] = cen[k];
+        s.x0[k] = cen[k];
+        s.u[k] = u ? u[k] : 0.0;
+        s.w[k] = w ? w[k] : 0.0;
+    }
+    s.R = r;
+    s.rho = rho_p;
+    if (id) *id = (int)c->sph_init.size();
+    c->sph_init.push_back(s);
+    return LBM_OK;
+}
+
+int lbm_step(lbm_ctx* c, int nsteps) {
+    if (!c || nsteps < 0) return LBM_EINVAL;
+    int rc;
+    if (!c->started && (rc = first_step(c))) return rc;
+    int left = nsteps;
+    if (c->profiling) {
+        for (; left > 0; left--) {
+            if ((rc = enqueue_step_timed(c, c->cur, c->stream))) return rc;
+            c->launches += (uint64_t)c->per_step;
+            c->cur ^= 1;
+        }
+        return LBM_OK;
+    }
+    if (c->use_graph && nsteps >= 2 && !c->graph_ready && (rc = build_graph(c))) c->use_graph = false;
+    if (c->use_graph && c->graph_ready) {
+        if (c->cur == 1 && left > 0) {   // realign to an even grid parity
+            if ((rc = enqueue_step(c, 1, c->stream))) return rc;
+            c->launches += (uint64_t)c->per_step;
+            c->cur = 0;
+            left--;
+        }
+        for (; left >= 2; left -= 2) {
+            if ((rc = cuda_fail(cudaGraphLaunch(c->graph, c->stream)))) return rc;
+            c->launches += 2ull * (uint64_t)c->per_step;
+        }
+    }
+    for (; left > 0; left--) {
+        if ((rc = enqueue_step(c, c->cur, c->stream))) return rc;
+        c->launches += (uint64_t)c->per_step;
+        c->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+int lbm_forces(lbm_ctx* c, double* F, double* T, int n) {
+    if (!c || n < 0 || (n > 0 && (!F || !T))) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    if (n > c->d.nsph) return LBM_EINVAL;
+    int rc = sync_tables(c);
+    if (rc) return rc;
+    for (int a = 0; a < n; a++)
+        for (int k = 0; k < 3; k++) {
+            F[3 * a + k] = c->sph_stage[a].F[k];
+            T[3 * a + k] = c->sph_stage[a].T[k];
+        }
+    return status_code(c->sc_stage->status);
+}
+
+int lbm_spheres(lbm_ctx* c, double* x, double* u, double* w, int n) {
+    if (!c || n < 0) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    if (n > c->d.nsph) return LBM_EINVAL;
+    int rc = sync_tables(c);
+    if (rc) return rc;
+    for (int a = 0; a < n; a++)
+        for (int k = 0; k < 3; k++) {
+            if (x) x[3 * a + k] = c->sph_stage[a].x[k];
+            if (u) u[3 * a + k] = c->sph_stage[a].u[k];
+            if (w) w[3 * a + k] = c->sph_stage[a].w[k];
+        }
+    return LBM_OK;
+}
+
+int lbm_bubbles(lbm_ctx* c, double* V0, double* V, double* rho_g, int n) {
+    if (!c || n < 0) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    if (n > c->d.nbub) return LBM_EINVAL;
+    int rc = sync_tables(c);
+    if (rc) return rc;
+    for (int b = 0; b < n; b++) {
+        if (V0) V0[b] = c->bub_stage[b].V0;
+        if (V) V[b] = c->bub_stage[b].V;
+        if (rho_g) rho_g[b] = c->bub_stage[b].rho_g;
+    }
+    return LBM_OK;
+}
+
+int lbm_fields(lbm_ctx* c, float* rho, float* u, float* phi, uint8_t* flags) {
+    if (!c) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    launch_fields(c->d, c->cur, rho, u, phi, flags, c->stream);
+    return launched(c, 1);
+}
+
+int lbm_export_state(lbm_ctx* c, float* f, uint8_t* flags, float* mass, float* phi, int32_t* owner, float* kappa) {
+    if (!c) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    launch_export(c->d, c->cur, f, flags, mass, phi, owner, kappa, c->stream);
+    return launched(c, 1);
+}
+
+int lbm_mass_budget(lbm_ctx* c, double out[5]) {
+    if (!c || !out) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    int rc;
+    if ((rc = cuda_fail(cudaMemsetAsync(&c->d.sc->mass, 0, sizeof(double), c->stream)))) return rc;
+    launch_mass(c->d, c->cur, c->stream);
+    if ((rc = launched(c, 1))) return rc;
+    if ((rc = sync_tables(c))) return rc;
+    const Scalars& sc = *c->sc_stage;
+    out[0] = sc.mass + sc.pool;
+    out[1] = sc.S_bb;
+    out[2] = sc.S_cover;
+    out[3] = sc.S_uncover;
+    out[4] = sc.pool;
+    return LBM_OK;
+}
+
+int lbm_status(lbm_ctx* c, uint32_t* status) {
+    if (!c || !status) return LBM_EINVAL;
+    if (!c->started) { *status = 0; return LBM_OK; }
+    int rc = sync_tables(c);
+    if (rc) return rc;
+    *status = c->sc_stage->status;
+    return LBM_OK;
+}
+
+int lbm_profile(lbm_ctx* c, int on) {
+    if (!c) return LBM_EINVAL;
+    if (on && !c->ev_ready) {
+        for (int k = 0; k < 2 * 64; k++)
+            if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return LBM_ECUDA;
+        c->ev_ready = true;
+    }
+    if (!on && c->ev_ready)
+        for (int k = 0; k < 64; k++) prof_collect(c, k);
+    c->profiling = on != 0;
+    return LBM_OK;
+}
+
+int lbm_profile_read(lbm_ctx* c, double* sweep_ms, uint64_t* sweeps) {
+    if (!c || !sweep_ms || !sweeps) return LBM_EINVAL;
+    if (c->ev_ready)
+        for (int k = 0; k < 64; k++) prof_collect(c, k);
+    *sweep_ms = c->sweep_ms;
+    *sweeps = c->sweeps;
+    c->sweep_ms = 0.0;
+    c->sweeps = 0;
+    return LBM_OK;
+}
+
+int lbm_copy_bytes(lbm_ctx* c, uint64_t* h2d, uint64_t* d2h) {
+    if (!c || !h2d || !d2h) return LBM_EINVAL;
+    *h2d = c->h2d_bytes;
+    *d2h = c->d2h_bytes;
+    return LBM_OK;
+}
+
+int lbm_launch_count(lbm_ctx* c, uint64_t* launches) {
+    if (!c || !launches) return LBM_EINVAL;
+    *launches = c->launches;
+    return LBM_OK;
+}
+
+int lbm_destroy(lbm_ctx* c) {
+    if (!c) return LBM_EINVAL;
+    if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+    if (c->ev_ready)
+        for (int k = 0; k < 2 * 64; k++) cudaEventDestroy(c->ev[k]);
+    std::free(c->sph_stage);
+    std::free(c->sc_stage);
+    std::free(c->bub_stage);
+    delete c;
+    return LBM_OK;
+}
+
+const char* lbm_strerror(int code) {
+    switch (code) {
+        case LBM_OK: return "ok";
+        case LBM_EINVAL: return "invalid argument";
+        case LBM_ESTATE: return "call not allowed in the current state";
+        case LBM_ECUDA: return "CUDA runtime error";
+        case LBM_EUNSTABLE: return "density became non-positive or NaN";
+        case LBM_EOVERFLOW: return "worklist or neighbour bin overflow";
+        default: return "unknown error";
+    }
+}
+
+}  // extern "C"

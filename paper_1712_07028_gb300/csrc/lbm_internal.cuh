@@ -1,0 +1,301 @@
+// lbm_internal.cuh -- device-side definitions shared by the CUDA translation units of the
+// free-surface LBM library (sm_103a).  Nothing here is shared with the CPU oracle.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+// D3Q19, q = 0 rest, 1..6 the faces (+x,-x,+y,-y,+z,-z), 7..18 the edges; the opposite of
+// q >= 1 is q+1 for odd q and q-1 for even q.
+constexpr int kQ = 19;
+__host__ __device__ constexpr int cx(int q) {
+    return (q == 1 || q == 7 || q == 9 || q == 11 || q == 13) ? 1
+         : (q == 2 || q == 8 || q == 10 || q == 12 || q == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int q) {
+    return (q == 3 || q == 7 || q == 10 || q == 15 || q == 17) ? 1
+         : (q == 4 || q == 8 || q == 9 || q == 16 || q == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int q) {
+    return (q == 5 || q == 11 || q == 14 || q == 15 || q == 18) ? 1
+         : (q == 6 || q == 12 || q == 13 || q == 16 || q == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int opp(int q) { return q == 0 ? 0 : ((q & 1) ? q + 1 : q - 1); }
+__host__ __device__ constexpr float wgt(int q) { return q == 0 ? (1.0f / 3.0f) : (q <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f)); }
+// 72 w_q as an integer (24, 4, 2): the constant part of a bounce-back link's momentum
+__host__ __device__ constexpr int w72(int q) { return q == 0 ? 24 : (q <= 6 ? 4 : 2); }
+
+// cell flag byte: type bits, plus BULK = liquid cell whose 18 neighbours all exist and are
+// liquid or interface (it then streams without looking at its neighbours)
+enum : uint8_t { F_LIQ = 1, F_IF = 2, F_GAS = 4, F_OBS = 8, F_BULK = 16, F_TYPE = 15 };
+enum : uint8_t { F_ACTIVE = F_LIQ | F_IF };
+// conversion / covering marks (separate byte array, zero outside the conversion phase)
+enum : uint8_t { K_FILLED = 1, K_EMPTIED = 2, K_NEWIF = 4, K_FROMLIQ = 8, K_RECV = 16, K_TOUCH = 32, K_UNCOV = 64 };
+
+constexpr uint32_t kNone = 0xffffffffu;
+
+// ---------------------------------------------------------------- PDF storage traits
+template <int S> struct Store;
+template <> struct Store<LBM_STORE_F32> {
+    using T = float;
+    static __device__ __forceinline__ float get(const T* p, size_t i, int) { return __ldg(p + i); }
+    static __device__ __forceinline__ float get_nc(const T* p, size_t i, int) { return p[i]; }
+    static __device__ __forceinline__ void put(T* p, size_t i, int, float v) { p[i] = v; }
+};
+template <> struct Store<LBM_STORE_F16DEV> {
+    using T = __half;
+    static __device__ __forceinline__ float get(const T* p, size_t i, int q) { return wgt(q) + __half2float(__ldg(p + i)); }
+    static __device__ __forceinline__ float get_nc(const T* p, size_t i, int q) { return wgt(q) + __half2float(p[i]); }
+    static __device__ __forceinline__ void put(T* p, size_t i, int q, float v) { p[i] = __float2half_rn(v - wgt(q)); }
+};
+template <> struct Store<LBM_STORE_BF16DEV> {
+    using T = __nv_bfloat16;
+    static __device__ __forceinline__ float get(const T* p, size_t i, int q) { return wgt(q) + __bfloat162float(__ldg(p + i)); }
+    static __device__ __forceinline__ float get_nc(const T* p, size_t i, int q) { return wgt(q) + __bfloat162float(p[i]); }
+    static __device__ __forceinline__ void put(T* p, size_t i, int q, float v) { p[i] = __float2bfloat16_rn(v - wgt(q)); }
+};
+
+// ----------------------------------------------------------------- device-side records
+struct Sphere {          // FP64 state of one sphere
+    double x[3], u[3], w[3];
+    double R, rho;
+    double F[3], T[3];   // momentum-exchange force and torque of the last step
+    double x0[3];        // centre at the start of the step (before the sub-steps)
+    double Fl[3];        // lubrication force of the last sub-step
+    double pad[1];
+};
+struct SphereAcc {       // per-step momentum-exchange accumulators (zeroed by the sphere update)
+    double J[3];         // sum of the deviation part of dj
+    double TJ[3];        // sum of (x - x_P) x (deviation part of dj)
+    unsigned long long K[3];   // sum of the constant part of dj, times 36 (two's complement)
+    unsigned long long XK[3];  // sum of x_img x (constant part), times 36
+};
+struct Bubble {
+    double V0, V, rho_g, Vif;    // reference volume, volume, gas density, interface part of V
+    unsigned long long ngas;     // gas cells
+    unsigned long long pad[3];
+};
+struct Scalars {
+    double pool;          // excess mass waiting to be spread over the interface cells
+    double pool_acc;      // excess of this step that found no receiving neighbour
+    double S_bb, S_cover, S_uncover;   // mass budget terms
+    double share;         // pool / n_iface used by the current sweep
+    double mass;          // scratch for the on-demand total-mass reduction
+    double pad0;
+    uint32_t n_iface;     // interface cells after the last conversion / covering
+    uint32_t n_iface_acc;
+    uint32_t status;      // LBM_S_* bits
+    uint32_t n_conv, n_newif, n_fromliq, n_touch, n_uncov;
+    uint32_t bin_overflow;
+    uint32_t pad1[7];
+};
+
+// status bits (latched; reported through lbm_status and the copy-out calls)
+enum : uint32_t { S_UNSTABLE = 1, S_OVERFLOW = 2, S_BUBBLE_GONE = 4, S_BIN_OVERFLOW = 8, S_BAD_OWNER = 16 };
+
+// all device pointers of one simulation; passed by value to every kernel
+struct Dev {
+    int nx, ny, nz;
+    int bc[3];
+    size_t N;
+    int storage;
+    int n_sub;
+    int sphere_mode;
+    int nbub, nsph;
+    int max_bub, max_sph;
+    int wl_cap;
+    float tau, lp, lm;        // tau, lambda_+, lambda_-
+    float g[3];
+    double gd[3];
+    float sigma;
+    float rho_g0;
+    float eps;
+    void* f[2];               // PDF grids [19][N]
+    uint8_t* flags;           // [N]
+    uint8_t* mark;            // [N] conversion / covering marks
+    float* mass;              // [N]
+    float* phi[2];            // [N] fill level, double-buffered with the PDFs
+    uint32_t* owner;          // [N] bubble id of gas/interface cells, sphere id of obstacle cells
+    float* kappa;             // [N] curvature (sigma > 0 only)
+    Bubble* bub;              // [max_bub]
+    Sphere* sph;              // [max_sph]
+    Sphere* sph_tmp;          // [max_sph] sub-step double buffer
+    SphereAcc* acc;           // [max_sph]
+    Scalars* sc;
+    uint32_t* wl_conv;        // worklists [wl_cap]
+    uint32_t* wl_newif;
+    uint32_t* wl_fromliq;
+    uint32_t* wl_touch;
+    // uniform bins of sphere ids for the neighbour searches
+    int bin_w, nbx, nby, nbz, bin_cap;
+    uint32_t* bin_cnt;        // [nbins]
+    uint32_t* bin_ids;        // [nbins][bin_cap]
+};
+
+__device__ __forceinline__ size_t cell_index(const Dev& d, int x, int y, int z) {
+    return (size_t)x + (size_t)d.nx * ((size_t)y + (size_t)d.ny * (size_t)z);
+}
+__device__ __forceinline__ void cell_xyz(const Dev& d, size_t i, int& x, int& y, int& z) {
+    x = (int)(i % (size_t)d.nx);
+    size_t r = i / (size_t)d.nx;
+    y = (int)(r % (size_t)d.ny);
+    z = (int)(r / (size_t)d.ny);
+}
+// neighbour index of (x,y,z)+(dx,dy,dz); periodic axes wrap; beyond a wall: returns false
+__device__ __forceinline__ bool nbr(const Dev& d, int x, int y, int z, int dx, int dy, int dz, size_t& j) {
+    int a = x + dx, b = y + dy, c = z + dz;
+    if (a < 0 || a >= d.nx) { if (!d.bc[0]) return false; a = a < 0 ? a + d.nx : a - d.nx; }
+    if (b < 0 || b >= d.ny) { if (!d.bc[1]) return false; b = b < 0 ? b + d.ny : b - d.ny; }
+    if (c < 0 || c >= d.nz) { if (!d.bc[2]) return false; c = c < 0 ? c + d.nz : c - d.nz; }
+    j = cell_index(d, a, b, c);
+    return true;
+}
+
+// byte-wise atomic OR / AND on the mark array (4-byte aligned base); returns the old byte
+__device__ __forceinline__ uint8_t mark_or(uint8_t* base, size_t i, uint8_t bits) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(base + (i & ~(size_t)3));
+    const uint32_t sh = (uint32_t)(i & 3) * 8u;
+    const uint32_t old = atomicOr(w, (uint32_t)bits << sh);
+    return (uint8_t)(old >> sh);
+}
+__device__ __forceinline__ uint8_t mark_and(uint8_t* base, size_t i, uint8_t bits) {
+    uint32_t* w = reinterpret_cast<uint32_t*>(base + (i & ~(size_t)3));
+    const uint32_t sh = (uint32_t)(i & 3) * 8u;
+    const uint32_t old = atomicAnd(w, ~((uint32_t)bits << sh));
+    return (uint8_t)(old >> sh);
+}
+
+// append to a worklist with warp aggregation; false if the list is full
+__device__ __forceinline__ bool wl_push(uint32_t* list, uint32_t* count, uint32_t cap, uint32_t v, uint32_t* status) {
+    const unsigned act = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(act) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(act));
+    base = __shfl_sync(act, base, leader);
+    const uint32_t slot = base + (uint32_t)__popc(act & ((1u << lane) - 1u));
+    if (slot < cap) { list[slot] = v; return true; }
+    atomicOr(status, S_OVERFLOW);
+    return false;
+}
+
+// post-collision moments of cell i from grid f: rho = sum f*, u = (sum c f* - rho g/2)/rho
+template <int S>
+__device__ __forceinline__ void post_moments(const Dev& d, const typename Store<S>::T* f, size_t i, float& rho, float u[3]) {
+    float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        const float v = Store<S>::get_nc(f, (size_t)q * d.N + i, q);
+        r += v;
+        jx += cx(q) * v; jy += cy(q) * v; jz += cz(q) * v;
+    }
+    rho = r;
+    u[0] = (jx - 0.5f * r * d.g[0]) / r;
+    u[1] = (jy - 0.5f * r * d.g[1]) / r;
+    u[2] = (jz - 0.5f * r * d.g[2]) / r;
+}
+
+__device__ __forceinline__ float equilibrium(int q, float rho, const float u[3]) {
+    const float cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
+    const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return wgt(q) * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+}
+
+// minimum-image difference a - b along axis k (beyond 4 periods, or not finite, the value is
+// first reduced with fmod, so no loop runs more than a few times)
+__device__ __forceinline__ double min_image(const Dev& d, int k, double a, double b) {
+    double v = a - b;
+    if (d.bc[k]) {
+        const double L = (double)(k == 0 ? d.nx : (k == 1 ? d.ny : d.nz));
+        if (!(fabs(v) <= 4.0 * L)) v = fmod(v, L);
+        for (int it = 0; it < 8 && v > 0.5 * L; it++) v -= L;
+        for (int it = 0; it < 8 && v < -0.5 * L; it++) v += L;
+    }
+    return v;
+}
+// periodic position into [-1/2, L - 1/2)
+__device__ __forceinline__ double wrap_pos(double x, int L) {
+    if (!(fabs(x) <= 4.0 * L)) x = fmod(x, (double)L);
+    for (int it = 0; it < 8 && x >= L - 0.5; it++) x -= L;
+    for (int it = 0; it < 8 && x < -0.5; it++) x += L;
+    return x;
+}
+__device__ __forceinline__ bool finite3(const double* v) {
+    return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+}
+
+
+// ------------------------------------------------------------ uniform bins of spheres
+// bin width >= 2 R_max + 2; the last bin of an axis absorbs the remainder, so every bin is
+// at least bin_w wide and a sphere within bin_w of a point lies in the 27 bins around it
+__device__ __forceinline__ int bin_coord(const Dev& d, int k, double v) {
+    const int n = k == 0 ? d.nbx : (k == 1 ? d.nby : d.nbz);
+    int b = (int)floor(v / (double)d.bin_w);
+    return b < 0 ? 0 : (b > n - 1 ? n - 1 : b);
+}
+__device__ __forceinline__ size_t bin_index(const Dev& d, int bx, int by, int bz) {
+    return ((size_t)bz * d.nby + by) * d.nbx + bx;
+}
+// the (at most 3) distinct bin coordinates around b along axis k; returns their count
+__device__ __forceinline__ int bin_span(const Dev& d, int k, int b, int out[3]) {
+    const int n = k == 0 ? d.nbx : (k == 1 ? d.nby : d.nbz);
+    if (n <= 3) { for (int a = 0; a < n; a++) out[a] = a; return n; }
+    int c = 0;
+    for (int o = -1; o <= 1; o++) {
+        int v = b + o;
+        if (v < 0 || v >= n) { if (!d.bc[k]) continue; v = v < 0 ? v + n : v - n; }
+        out[c++] = v;
+    }
+    return c;
+}
+__device__ __forceinline__ bool sphere_covers(const Dev& d, const Sphere& s, int x, int y, int z) {
+    const double ddx = min_image(d, 0, (double)x, s.x[0]);
+    const double ddy = min_image(d, 1, (double)y, s.x[1]);
+    const double ddz = min_image(d, 2, (double)z, s.x[2]);
+    return ddx * ddx + ddy * ddy + ddz * ddz <= s.R * s.R;
+}
+// lowest id of the spheres whose current centre covers cell (x,y,z), or kNone
+__device__ __forceinline__ uint32_t covering_sphere(const Dev& d, int x, int y, int z) {
+    int sx[3], sy[3], sz[3];
+    const int nx_ = bin_span(d, 0, bin_coord(d, 0, (double)x), sx);
+    const int ny_ = bin_span(d, 1, bin_coord(d, 1, (double)y), sy);
+    const int nz_ = bin_span(d, 2, bin_coord(d, 2, (double)z), sz);
+    uint32_t best = kNone;
+    for (int c = 0; c < nz_; c++)
+        for (int b = 0; b < ny_; b++)
+            for (int a = 0; a < nx_; a++) {
+                const size_t bi = bin_index(d, sx[a], sy[b], sz[c]);
+                uint32_t cnt = d.bin_cnt[bi];
+                if (cnt > (uint32_t)d.bin_cap) cnt = (uint32_t)d.bin_cap;
+                for (uint32_t e = 0; e < cnt; e++) {
+                    const uint32_t P = d.bin_ids[bi * d.bin_cap + e];
+                    if (P < best && sphere_covers(d, d.sph[P], x, y, z)) best = P;
+                }
+            }
+    return best;
+}
+
+// kernels (defined in the .cu files), launched by lbm_capi.cu
+void launch_sweep(const Dev& d, int cur, cudaStream_t s);
+void launch_conversions(const Dev& d, int nxt, cudaStream_t s);
+void launch_bubbles(const Dev& d, int nxt, cudaStream_t s);
+void launch_curvature(const Dev& d, int nxt, cudaStream_t s);
+void launch_spheres(const Dev& d, int nxt, cudaStream_t s);
+void launch_step_end(const Dev& d, cudaStream_t s);
+void launch_step_end_reference(const Dev& d, cudaStream_t s);
+void launch_bins_insert(const Dev& d, cudaStream_t s);
+int spheres_launches(const Dev& d);
+void launch_init(const Dev& d, const double* bub_geom_dev, cudaStream_t s);
+void launch_bulk_all(const Dev& d, cudaStream_t s);
+void launch_fields(const Dev& d, int cur, float* rho, float* u, float* phi, uint8_t* flags, cudaStream_t s);
+void launch_export(const Dev& d, int cur, float* f, uint8_t* flags, float* m, float* phi, int32_t* owner, float* kappa, cudaStream_t s);
+void launch_import(const Dev& d, int cur, const float* f, const uint8_t* flags, const float* m, const float* phi, const int32_t* owner, const float* kappa, cudaStream_t s);
+void launch_mass(const Dev& d, int cur, cudaStream_t s);
+
+}  // namespace lbm

@@ -1,0 +1,580 @@
+// lbm_surface.cu -- free-surface bookkeeping after the sweep (Sec. 2.2 of the paper):
+// cell conversions with layer closure, equilibrium initialisation of new interface cells,
+// excess-mass redistribution, the bubble model, curvature, initial fields and exports.
+//
+// Conversions run as phases over compact worklists (the sweep appends every interface cell
+// whose fill level crossed a threshold), so their cost scales with the number of converting
+// cells, not with the grid.  Marks live in a separate byte array that is all zero outside
+// this phase; every phase that a later phase depends on ends at a kernel boundary.
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+constexpr int kListThreads = 128;
+
+__device__ __forceinline__ uint32_t list_len(const uint32_t* cnt, int cap) {
+    const uint32_t n = *(volatile const uint32_t*)cnt;
+    return n < (uint32_t)cap ? n : (uint32_t)cap;
+}
+
+// fill level seen by the normal and curvature stencils: interface -> phi, liquid -> 1,
+// gas -> 0, obstacle and beyond a wall -> 1 (perfect wetting, Sec. 2.2)
+__device__ __forceinline__ float fill_seen(const Dev& d, const float* phi, int x, int y, int z, int dx, int dy, int dz) {
+    size_t j;
+    if (!nbr(d, x, y, z, dx, dy, dz, j)) return 1.f;
+    const uint8_t t = d.flags[j] & F_TYPE;
+    if (t & F_IF) return phi[j];
+    if (t & F_GAS) return 0.f;
+    return 1.f;
+}
+
+// Parker-Youngs gradient of the fill level (points into the liquid): central difference
+// smoothed with [1,2,1] x [1,2,1] / 16 over the 3x3x3 block
+__device__ void py_gradient(const Dev& d, const float* phi, int x, int y, int z, float n[3]) {
+    float v[27];
+#pragma unroll
+    for (int c = -1; c <= 1; c++)
+#pragma unroll
+        for (int b = -1; b <= 1; b++)
+#pragma unroll
+            for (int a = -1; a <= 1; a++)
+                v[(c + 1) * 9 + (b + 1) * 3 + (a + 1)] = (a == 0 && b == 0 && c == 0) ? 0.f : fill_seen(d, phi, x, y, z, a, b, c);
+    const float w1[3] = {1.f, 2.f, 1.f};
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+#pragma unroll
+    for (int p = 0; p < 3; p++)
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+            const float w = w1[p] * w1[r];
+            gx += w * (v[r * 9 + p * 3 + 2] - v[r * 9 + p * 3 + 0]);
+            gy += w * (v[r * 9 + 2 * 3 + p] - v[r * 9 + 0 * 3 + p]);
+            gz += w * (v[2 * 9 + r * 3 + p] - v[0 * 9 + r * 3 + p]);
+        }
+    n[0] = gx / 32.f;
+    n[1] = gy / 32.f;
+    n[2] = gz / 32.f;
+}
+
+template <int S>
+__device__ float cell_rho(const Dev& d, const typename Store<S>::T* f, size_t i) {
+    float r = 0.f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) r += Store<S>::get_nc(f, (size_t)q * d.N + i, q);
+    return r;
+}
+
+// (ii) filled cells: gas neighbours become new interface cells; emptied neighbours stay
+__global__ void conv_filled_kernel(const Dev d) {
+    const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t i = d.wl_conv[k];
+        if (!(d.mark[i] & K_FILLED)) continue;
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        for (int q = 1; q < kQ; q++) {
+            size_t j;
+            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
+            const uint8_t t = d.flags[j] & F_TYPE;
+            if (t & F_GAS) {
+                const uint8_t old = mark_or(d.mark, j, K_NEWIF);
+                if (!(old & K_NEWIF)) wl_push(d.wl_newif, &d.sc->n_newif, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
+            } else if (t & F_IF) {
+                mark_and(d.mark, j, K_EMPTIED);
+            }
+        }
+    }
+}
+
+// (iii) emptied cells: liquid neighbours become interface cells with m = rho; the smallest
+// bubble id among their emptied neighbours becomes theirs
+template <int S>
+__global__ void conv_emptied_kernel(const Dev d, const int nxt) {
+    using T = typename Store<S>::T;
+    const T* f = static_cast<const T*>(d.f[nxt]);
+    const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t i = d.wl_conv[k];
+        if (!(d.mark[i] & K_EMPTIED)) continue;
+        const uint32_t b = d.owner[i];
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        for (int q = 1; q < kQ; q++) {
+            size_t j;
+            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
+            if (!(d.flags[j] & F_LIQ)) continue;
+            const uint8_t old = mark_or(d.mark, j, K_FROMLIQ);
+            if (!(old & K_FROMLIQ)) {
+                d.mass[j] = cell_rho<S>(d, f, j);
+                wl_push(d.wl_fromliq, &d.sc->n_fromliq, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
+            }
+            atomicMin(&d.owner[j], b);
+        }
+    }
+}
+
+// (iv) new interface cells from gas: f* = e(mean rho, mean u) over the neighbours that carry
+// PDFs (liquid, interface not emptied, filled), m = 0
+template <int S>
+__global__ void conv_newif_kernel(const Dev d, const int nxt) {
+    using T = typename Store<S>::T;
+    T* f = static_cast<T*>(d.f[nxt]);
+    const uint32_t n = list_len(&d.sc->n_newif, d.wl_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t i = d.wl_newif[k];
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        float rs = 0.f, us[3] = {0.f, 0.f, 0.f};
+        int cnt = 0;
+        for (int q = 1; q < kQ; q++) {
+            size_t j;
+            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
+            if (!(d.flags[j] & F_ACTIVE) || (d.mark[j] & K_EMPTIED)) continue;
+            float r, u[3];
+            post_moments<S>(d, f, j, r, u);
+            rs += r;
+            us[0] += u[0]; us[1] += u[1]; us[2] += u[2];
+            cnt++;
+        }
+        const float rb = cnt ? rs / cnt : 1.f;
+        const float ub[3] = {cnt ? us[0] / cnt : 0.f, cnt ? us[1] / cnt : 0.f, cnt ? us[2] / cnt : 0.f};
+        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, q, equilibrium(q, rb, ub));
+        d.mass[i] = 0.f;
+    }
+}
+
+// (v) excess mass of converting cells to the neighbours that will be interface cells,
+// weighted along the interface normal pointing into the gas (-grad phi): filled cells push
+// along it, emptied cells against it; uniform if all weights vanish; to the global pool if
+// no neighbour can take it
+template <int S>
+__global__ void conv_excess_kernel(const Dev d, const int nxt) {
+    using T = typename Store<S>::T;
+    const T* f = static_cast<const T*>(d.f[nxt]);
+    const float* phi = d.phi[nxt];
+    const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t i = d.wl_conv[k];
+        const uint8_t mk = d.mark[i] & (K_FILLED | K_EMPTIED);
+        if (!mk) continue;
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        float nv[3];
+        py_gradient(d, phi, x, y, z, nv);
+        const float ngx = -nv[0], ngy = -nv[1], ngz = -nv[2];
+        const float r = cell_rho<S>(d, f, i);
+        float mex;
+        if (mk & K_FILLED) { mex = d.mass[i] - r; d.mass[i] = r; }
+        else { mex = d.mass[i]; d.mass[i] = 0.f; }
+        float wr[kQ];
+        size_t rj[kQ];
+        float W = 0.f;
+        int nr = 0;
+        for (int q = 1; q < kQ; q++) {
+            size_t j;
+            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
+            const uint8_t mj = d.mark[j];
+            const bool rec = ((d.flags[j] & F_IF) && !(mj & (K_FILLED | K_EMPTIED))) || (mj & (K_NEWIF | K_FROMLIQ));
+            if (!rec) continue;
+            const float nc = ngx * cx(q) + ngy * cy(q) + ngz * cz(q);
+            const float w = (mk & K_FILLED) ? fmaxf(nc, 0.f) : fmaxf(-nc, 0.f);
+            rj[nr] = j;
+            wr[nr] = w;
+            W += w;
+            nr++;
+        }
+        if (nr == 0) {
+            atomicAdd(&d.sc->pool_acc, (double)mex);
+            continue;
+        }
+        for (int a = 0; a < nr; a++) {
+            atomicAdd(&d.mass[rj[a]], W > 0.f ? mex * (wr[a] / W) : mex / (float)nr);
+            mark_or(d.mark, rj[a], K_RECV);
+        }
+    }
+}
+
+// (vi) final types; fill level of every interface cell whose mass changed in this phase
+template <int S>
+__global__ void conv_finalize_kernel(const Dev d, const int nxt) {
+    using T = typename Store<S>::T;
+    const T* f = static_cast<const T*>(d.f[nxt]);
+    float* phi = d.phi[nxt];
+    const uint32_t n1 = list_len(&d.sc->n_conv, d.wl_cap);
+    const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
+    const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n2 + n3; k += gridDim.x * blockDim.x) {
+        if (k < n1) {
+            const size_t i = d.wl_conv[k];
+            const uint8_t mk = d.mark[i];
+            if (mk & K_FILLED) { d.flags[i] = F_LIQ; d.owner[i] = kNone; }
+            else if (mk & K_EMPTIED) { d.flags[i] = F_GAS; }
+            int x, y, z;
+            cell_xyz(d, i, x, y, z);
+            for (int q = 1; q < kQ; q++) {
+                size_t j;
+                if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
+                const uint8_t mj = d.mark[j];
+                if ((mj & K_RECV) && !(mj & (K_NEWIF | K_FROMLIQ))) phi[j] = d.mass[j] / cell_rho<S>(d, f, j);
+            }
+        } else {
+            const size_t i = k < n1 + n2 ? d.wl_newif[k - n1] : d.wl_fromliq[k - n1 - n2];
+            d.flags[i] = F_IF;
+            phi[i] = d.mass[i] / cell_rho<S>(d, f, i);
+        }
+    }
+}
+
+__device__ __forceinline__ bool bulk_of(const Dev& d, size_t i) {
+    if ((d.flags[i] & F_TYPE) != F_LIQ) return false;
+    int x, y, z;
+    cell_xyz(d, i, x, y, z);
+    for (int q = 1; q < kQ; q++) {
+        size_t j;
+        if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) return false;
+        if (!(d.flags[j] & F_ACTIVE)) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void set_bulk(const Dev& d, size_t i) {
+    const uint8_t t = d.flags[i] & F_TYPE;
+    d.flags[i] = (uint8_t)(t | (bulk_of(d, i) ? F_BULK : 0));
+}
+
+// (vii) BULK bits around every cell whose type changed; marks cleared
+__global__ void conv_bulk_kernel(const Dev d) {
+    const uint32_t n1 = list_len(&d.sc->n_conv, d.wl_cap);
+    const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
+    const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n2 + n3; k += gridDim.x * blockDim.x) {
+        const size_t i = k < n1 ? d.wl_conv[k] : (k < n1 + n2 ? d.wl_newif[k - n1] : d.wl_fromliq[k - n1 - n2]);
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        set_bulk(d, i);
+        d.mark[i] = 0;
+        for (int q = 1; q < kQ; q++) {
+            size_t j;
+            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
+            set_bulk(d, j);
+            d.mark[j] = 0;
+        }
+    }
+}
+
+void launch_conversions(const Dev& d, int nxt, cudaStream_t s) {
+    const int blocks = 2 * 152;
+    conv_filled_kernel<<<blocks, kListThreads, 0, s>>>(d);
+    switch (d.storage) {
+        case LBM_STORE_F32:
+            conv_emptied_kernel<LBM_STORE_F32><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_newif_kernel<LBM_STORE_F32><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_excess_kernel<LBM_STORE_F32><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_finalize_kernel<LBM_STORE_F32><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            break;
+        case LBM_STORE_F16DEV:
+            conv_emptied_kernel<LBM_STORE_F16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_newif_kernel<LBM_STORE_F16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_excess_kernel<LBM_STORE_F16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_finalize_kernel<LBM_STORE_F16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            break;
+        default:
+            conv_emptied_kernel<LBM_STORE_BF16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_newif_kernel<LBM_STORE_BF16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_excess_kernel<LBM_STORE_BF16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            conv_finalize_kernel<LBM_STORE_BF16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
+            break;
+    }
+    conv_bulk_kernel<<<blocks, kListThreads, 0, s>>>(d);
+}
+
+// ------------------------------------------------------------------- bubble model
+// V_b = #gas cells of b + sum over interface cells of b of (1 - phi), in FP64; also the
+// number of interface cells.  One pass over the flags, 16 cells per thread and load.
+__global__ void bubble_reduce_kernel(const Dev d, const int nxt) {
+    extern __shared__ unsigned char smem_raw[];
+    double* sV = reinterpret_cast<double*>(smem_raw);
+    unsigned long long* sG = reinterpret_cast<unsigned long long*>(sV + d.max_bub);
+    __shared__ unsigned int sIf;
+    for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) { sV[b] = 0.0; sG[b] = 0ull; }
+    if (threadIdx.x == 0) sIf = 0;
+    __syncthreads();
+    const float* phi = d.phi[nxt];
+    const size_t nvec = d.N / 16;
+    const uint4* fl4 = reinterpret_cast<const uint4*>(d.flags);
+    unsigned int nif = 0;
+    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec + (d.N % 16 ? 1 : 0); v += (size_t)gridDim.x * blockDim.x) {
+        uint32_t w[4];
+        if (v < nvec) {
+            const uint4 p = fl4[v];
+            w[0] = p.x; w[1] = p.y; w[2] = p.z; w[3] = p.w;
+        } else {
+            w[0] = w[1] = w[2] = w[3] = 0u;
+            for (size_t c = v * 16; c < d.N; c++) w[(c - v * 16) / 4] |= (uint32_t)d.flags[c] << (8 * ((c - v * 16) % 4));
+        }
+        const uint32_t any = (w[0] | w[1] | w[2] | w[3]) & 0x06060606u;  // interface or gas bits
+        if (!any) continue;
+        for (int c = 0; c < 16; c++) {
+            const uint8_t t = (uint8_t)(w[c / 4] >> (8 * (c % 4)));
+            if (!(t & (F_IF | F_GAS))) continue;
+            const size_t i = v * 16 + c;
+            const uint32_t b = d.owner[i];
+            if (t & F_IF) {
+                nif++;
+                if (b < (uint32_t)d.nbub) atomicAdd(&sV[b], 1.0 - (double)phi[i]);
+            } else if (b < (uint32_t)d.nbub) {
+                atomicAdd(&sG[b], 1ull);
+            }
+        }
+    }
+    atomicAdd(&sIf, nif);
+    __syncthreads();
+    for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
+        if (sV[b] != 0.0) atomicAdd(&d.bub[b].Vif, sV[b]);
+        if (sG[b]) atomicAdd(&d.bub[b].ngas, sG[b]);
+    }
+    if (threadIdx.x == 0 && sIf) atomicAdd(&d.sc->n_iface_acc, sIf);
+}
+
+void launch_bubbles(const Dev& d, int nxt, cudaStream_t s) {
+    const size_t shm = (size_t)d.max_bub * (sizeof(double) + sizeof(unsigned long long));
+    const size_t nvec = d.N / 16 + 1;
+    int blocks = (int)((nvec + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    bubble_reduce_kernel<<<blocks, 256, shm, s>>>(d, nxt);
+}
+
+// end of step: gas density per bubble (isothermal, conserved gas mass), excess pool and the
+// share the next sweep spreads over the interface cells, counters reset, sphere bins cleared
+__global__ void step_end_kernel(const Dev d, const int set_reference) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x == 0) {
+        for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
+            Bubble& B = d.bub[b];
+            const double V = (double)B.ngas + B.Vif;
+            B.V = V;
+            if (set_reference) { B.V0 = V; B.rho_g = (double)d.rho_g0; }
+            else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
+            else atomicOr(&d.sc->status, S_BUBBLE_GONE);
+            B.ngas = 0ull;
+            B.Vif = 0.0;
+        }
+        if (threadIdx.x == 0) {
+            Scalars& c = *d.sc;
+            if (c.share != 0.0) c.pool = 0.0;
+            c.pool += c.pool_acc;
+            c.pool_acc = 0.0;
+            c.n_iface = c.n_iface_acc;
+            c.n_iface_acc = 0;
+            c.share = (c.pool != 0.0 && c.n_iface > 0) ? c.pool / (double)c.n_iface : 0.0;
+            c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
+        }
+    }
+    if (t < d.nsph && d.bin_cnt) {  // bins of the spheres' start-of-step positions
+        const Sphere& sp = d.sph[t];
+        d.bin_cnt[bin_index(d, bin_coord(d, 0, sp.x0[0]), bin_coord(d, 1, sp.x0[1]), bin_coord(d, 2, sp.x0[2]))] = 0;
+    }
+}
+
+void launch_step_end(const Dev& d, cudaStream_t s) {
+    const int blocks = d.nsph > 256 ? (d.nsph + 255) / 256 : 1;
+    step_end_kernel<<<blocks, 256, 0, s>>>(d, 0);
+}
+
+void launch_step_end_reference(const Dev& d, cudaStream_t s) {
+    const int blocks = d.nsph > 256 ? (d.nsph + 255) / 256 : 1;
+    step_end_kernel<<<blocks, 256, 0, s>>>(d, 1);
+}
+
+// ---------------------------------------------------------------------- curvature
+// kappa = -(1/2) div(n^) of the Parker-Youngs unit normal (central differences; beyond a
+// wall the cell's own normal), the mean curvature: -1/R on a gas sphere of radius R
+__device__ void unit_normal(const Dev& d, const float* phi, int x, int y, int z, float nh[3]) {
+    float n[3];
+    py_gradient(d, phi, x, y, z, n);
+    const float l = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    nh[0] = l > 0.f ? n[0] / l : 0.f;
+    nh[1] = l > 0.f ? n[1] / l : 0.f;
+    nh[2] = l > 0.f ? n[2] / l : 0.f;
+}
+
+__global__ void curvature_kernel(const Dev d, const int nxt) {
+    const float* phi = d.phi[nxt];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+        if (!(d.flags[i] & F_IF)) continue;
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        float n0[3];
+        unit_normal(d, phi, x, y, z, n0);
+        float div = 0.f;
+        for (int k = 0; k < 3; k++) {
+            const int dx = k == 0, dy = k == 1, dz = k == 2;
+            float np[3], nm[3];
+            size_t j;
+            if (nbr(d, x, y, z, dx, dy, dz, j)) {
+                int a, b, c;
+                cell_xyz(d, j, a, b, c);
+                unit_normal(d, phi, a, b, c, np);
+            } else { np[0] = n0[0]; np[1] = n0[1]; np[2] = n0[2]; }
+            if (nbr(d, x, y, z, -dx, -dy, -dz, j)) {
+                int a, b, c;
+                cell_xyz(d, j, a, b, c);
+                unit_normal(d, phi, a, b, c, nm);
+            } else { nm[0] = n0[0]; nm[1] = n0[1]; nm[2] = n0[2]; }
+            div += 0.5f * (np[k] - nm[k]);
+        }
+        d.kappa[i] = -0.5f * div;
+    }
+}
+
+void launch_curvature(const Dev& d, int nxt, cudaStream_t s) {
+    curvature_kernel<<<152 * 8, 256, 0, s>>>(d, nxt);
+}
+
+// --------------------------------------------------------------------- initial state
+// phi = prod_b clamp(|x - c_b| - (r_b - 1/2), 0, 1); gas / liquid / interface; liquid cells
+// with a gas neighbour become interface cells (phi = 1) with that gas cell's bubble; f* =
+// e(1,0), m = phi; then cells covered by a sphere (lowest id) become obstacle cells.
+__device__ void bubble_fill(const Dev& d, const double* geo, int x, int y, int z, float& ph, uint32_t& own) {
+    double v = 1.0;
+    own = kNone;
+    for (int b = 0; b < d.nbub; b++) {
+        const double ddx = min_image(d, 0, (double)x, geo[4 * b + 0]);
+        const double ddy = min_image(d, 1, (double)y, geo[4 * b + 1]);
+        const double ddz = min_image(d, 2, (double)z, geo[4 * b + 2]);
+        double c = sqrt(ddx * ddx + ddy * ddy + ddz * ddz) - (geo[4 * b + 3] - 0.5);
+        c = c < 0.0 ? 0.0 : (c > 1.0 ? 1.0 : c);
+        if (c < 1.0 && own == kNone) own = (uint32_t)b;
+        v *= c;
+    }
+    ph = (float)v;
+}
+
+template <int S>
+__global__ void init_kernel(const Dev d, const double* geo) {
+    using T = typename Store<S>::T;
+    T* f = static_cast<T*>(d.f[0]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        float ph;
+        uint32_t own;
+        bubble_fill(d, geo, x, y, z, ph, own);
+        uint8_t t = ph <= 0.f ? F_GAS : (ph >= 1.f ? F_LIQ : F_IF);
+        if (t == F_LIQ && d.nbub > 0) {   // layer closure
+            for (int q = 1; q < kQ; q++) {
+                size_t j;
+                if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
+                int a, b, c;
+                cell_xyz(d, j, a, b, c);
+                float pj;
+                uint32_t oj;
+                bubble_fill(d, geo, a, b, c, pj, oj);
+                if (pj <= 0.f) { t = F_IF; ph = 1.f; own = oj; break; }
+            }
+        }
+        if (t == F_LIQ) own = kNone;
+        float m = ph;
+        if (d.nsph > 0) {
+            const uint32_t P = covering_sphere(d, x, y, z);
+            if (P != kNone) { t = F_OBS; own = P; m = 0.f; ph = 1.f; }
+        }
+        d.flags[i] = t;
+        d.owner[i] = own;
+        d.mass[i] = m;
+        d.phi[0][i] = ph;
+        d.phi[1][i] = ph;
+        if (d.kappa) d.kappa[i] = 0.f;
+        const float u0[3] = {0.f, 0.f, 0.f};
+        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, q, equilibrium(q, 1.f, u0));
+    }
+}
+
+void launch_init(const Dev& d, const double* geo, cudaStream_t s) {
+    switch (d.storage) {
+        case LBM_STORE_F32: init_kernel<LBM_STORE_F32><<<152 * 16, 256, 0, s>>>(d, geo); break;
+        case LBM_STORE_F16DEV: init_kernel<LBM_STORE_F16DEV><<<152 * 16, 256, 0, s>>>(d, geo); break;
+        default: init_kernel<LBM_STORE_BF16DEV><<<152 * 16, 256, 0, s>>>(d, geo); break;
+    }
+}
+
+__global__ void bulk_all_kernel(const Dev d) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x)
+        set_bulk(d, i);
+}
+
+void launch_bulk_all(const Dev& d, cudaStream_t s) { bulk_all_kernel<<<152 * 16, 256, 0, s>>>(d); }
+
+// ------------------------------------------------------------------------- exports
+template <int S>
+__global__ void fields_kernel(const Dev d, const int cur, float* rho, float* u, float* phi, uint8_t* flags) {
+    using T = typename Store<S>::T;
+    const T* f = static_cast<const T*>(d.f[cur]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+        const uint8_t t = d.flags[i] & F_TYPE;
+        if (rho || u) {
+            float r = 0.f, v[3] = {0.f, 0.f, 0.f};
+            if (t & F_ACTIVE) post_moments<S>(d, f, i, r, v);
+            if (rho) rho[i] = r;
+            if (u) { u[i] = v[0]; u[d.N + i] = v[1]; u[2 * d.N + i] = v[2]; }
+        }
+        if (phi) phi[i] = (t & F_IF) ? d.phi[cur][i] : ((t & F_GAS) ? 0.f : 1.f);
+        if (flags) flags[i] = t;
+    }
+}
+
+template <int S>
+__global__ void export_kernel(const Dev d, const int cur, float* f, uint8_t* flags, float* m, float* phi, int32_t* owner, float* kappa) {
+    using T = typename Store<S>::T;
+    const T* fs = static_cast<const T*>(d.f[cur]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+        const uint8_t t = d.flags[i] & F_TYPE;
+        if (f)
+            for (int q = 0; q < kQ; q++) f[(size_t)q * d.N + i] = Store<S>::get_nc(fs, (size_t)q * d.N + i, q);
+        if (flags) flags[i] = t;
+        if (m) m[i] = (t & F_IF) ? d.mass[i] : 0.f;
+        if (phi) phi[i] = (t & F_IF) ? d.phi[cur][i] : ((t & F_GAS) ? 0.f : 1.f);
+        if (owner) owner[i] = d.owner[i] == kNone ? -1 : (int32_t)d.owner[i];
+        if (kappa) kappa[i] = d.kappa ? d.kappa[i] : 0.f;
+    }
+}
+
+#define LBM_DISPATCH(KERNEL, GRID, BLOCK, STREAM, ...)                                              \
+    switch (d.storage) {                                                                            \
+        case LBM_STORE_F32: KERNEL<LBM_STORE_F32><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;    \
+        case LBM_STORE_F16DEV: KERNEL<LBM_STORE_F16DEV><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break; \
+        default: KERNEL<LBM_STORE_BF16DEV><<<GRID, BLOCK, 0, STREAM>>>(__VA_ARGS__); break;         \
+    }
+
+void launch_fields(const Dev& d, int cur, float* rho, float* u, float* phi, uint8_t* flags, cudaStream_t s) {
+    LBM_DISPATCH(fields_kernel, 152 * 8, 256, s, d, cur, rho, u, phi, flags);
+}
+
+void launch_export(const Dev& d, int cur, float* f, uint8_t* flags, float* m, float* phi, int32_t* owner, float* kappa, cudaStream_t s) {
+    LBM_DISPATCH(export_kernel, 152 * 8, 256, s, d, cur, f, flags, m, phi, owner, kappa);
+}
+
+// total liquid mass sum_liquid rho + sum_interface m, in FP64
+template <int S>
+__global__ void mass_kernel(const Dev d, const int cur) {
+    using T = typename Store<S>::T;
+    const T* f = static_cast<const T*>(d.f[cur]);
+    double acc = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+        const uint8_t t = d.flags[i] & F_TYPE;
+        if (t & F_LIQ) {
+            double r = 0.0;
+            for (int q = 0; q < kQ; q++) r += (double)Store<S>::get_nc(f, (size_t)q * d.N + i, q);
+            acc += r;
+        } else if (t & F_IF) {
+            acc += (double)d.mass[i];
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&d.sc->mass, acc);
+}
+
+void launch_mass(const Dev& d, int cur, cudaStream_t s) {
+    LBM_DISPATCH(mass_kernel, 152 * 8, 256, s, d, cur);
+}
+
+}  // namespace lbm

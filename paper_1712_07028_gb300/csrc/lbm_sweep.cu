@@ -1,0 +1,292 @@
+// lbm_sweep.cu -- the fused per-step sweep over all cells (one thread per cell).
+//
+// For every active (liquid or interface) cell x, in one pass over the two PDF grids:
+//   pull streaming f_q(x,t+1) = f*_q(x - c_q, t)                         (Sec. 2.1, Eq. LBE1)
+//   halfway bounce-back where x - c_q lies beyond a no-slip wall
+//   moving-wall bounce-back where x - c_q is an obstacle cell of sphere P (Sec. 2.3, Eq. bbrule):
+//       f_q(x,t+1) = f*_q^(x,t) + 6 w_q rho_w c_q.u_w,  u_w = u_P + w_P x (x_w - x_P),
+//       x_w = x - c_q/2 the link midpoint, rho_w = sum f*(x,t) the previous-step density,
+//     with the momentum exchange dj = c_q^ f*_q^(x,t) - c_q f_q(x,t+1) summed into the
+//     force and torque of P (Eqs. netforce, torque, momentum_transfer)
+//   free-surface reconstruction where x - c_q is a gas cell of bubble b (Sec. 2.2, Eq. fsk):
+//       f_q(x,t+1) = -f*_q^(x,t) + 2 e+_q(rho_w, u_w),  rho_w = rho_g,b + 6 sigma kappa(x),
+//       u_w = the velocity of x from its own post-collision state
+//   mass exchange of interface cells (Eqs. massExchange, massExchangeb):
+//       m(t+1) = m(t) + sum_q s_q (f*_q^(x+c_q,t) - f*_q(x,t)),  s = 1 (liquid neighbour),
+//       (phi(x)+phi(x+c_q))/2 (interface neighbour), 0 otherwise;  phi(t+1) = m(t+1)/rho(t+1)
+//   TRT collision with lambda_+ = -1/tau, (1/lambda_+ + 1/2)(1/lambda_- + 1/2) = 3/16
+//   (Eq. LBE2 and the magic relation of Sec. 2.1) and a Guo body force split into its even
+//   and odd parts; u = (sum c f + rho g/2)/rho
+//   and the conversion candidates: phi >= 1 + eps (filled) / phi <= -eps (emptied).
+//
+// Sphere force and torque are reduced in FP64 without cancellation loss: per link the
+// momentum is split into the constant part -2 w_q c_q (accumulated exactly as integers,
+// times 36) and the small deviation part (FP32 per cell, summed over the warp's lanes of the
+// same sphere, then one FP64 atomic per warp and sphere).
+#include "lbm_internal.cuh"
+
+namespace lbm {
+
+struct SphAcc {
+    uint32_t pid;
+    float J[3];
+    int K[3];
+    float r[3];     // x_img - x_P of this cell
+    int xi[3];      // x_img
+};
+
+__device__ __forceinline__ void sph_begin(const Dev& d, SphAcc& a, uint32_t P, int x, int y, int z) {
+    a.pid = P;
+    a.J[0] = a.J[1] = a.J[2] = 0.f;
+    a.K[0] = a.K[1] = a.K[2] = 0;
+    const Sphere& sp = d.sph[P];
+    const int c[3] = {x, y, z};
+    const int L[3] = {d.nx, d.ny, d.nz};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        int xi = c[k];
+        if (d.bc[k]) {   // image of the cell nearest to the sphere centre
+            const double dd = sp.x[k] - (double)xi;
+            if (dd > 0.5 * L[k]) xi += L[k];
+            else if (dd < -0.5 * L[k]) xi -= L[k];
+        }
+        a.xi[k] = xi;
+        a.r[k] = (float)((double)xi - sp.x[k]);
+    }
+}
+
+// cell's partial sums -> global accumulators of the sphere (used when one cell touches two
+// spheres; the common case is reduced over the warp instead)
+__device__ __forceinline__ void sph_flush_direct(const Dev& d, const SphAcc& a) {
+    if (a.pid == kNone) return;
+    SphereAcc& g = d.acc[a.pid];
+    const float TJ[3] = {a.r[1] * a.J[2] - a.r[2] * a.J[1], a.r[2] * a.J[0] - a.r[0] * a.J[2], a.r[0] * a.J[1] - a.r[1] * a.J[0]};
+    const int XK[3] = {a.xi[1] * a.K[2] - a.xi[2] * a.K[1], a.xi[2] * a.K[0] - a.xi[0] * a.K[2], a.xi[0] * a.K[1] - a.xi[1] * a.K[0]};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        atomicAdd(&g.J[k], (double)a.J[k]);
+        atomicAdd(&g.TJ[k], (double)TJ[k]);
+        atomicAdd(&g.K[k], (unsigned long long)(long long)a.K[k]);
+        atomicAdd(&g.XK[k], (unsigned long long)(long long)XK[k]);
+    }
+}
+
+template <int S>
+__global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) {
+    using T = typename Store<S>::T;
+    const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
+    T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
+    const float* __restrict__ phia = d.phi[cur];
+    float* __restrict__ phib = d.phi[cur ^ 1];
+    const size_t N = d.N;
+
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const bool inside = (x < d.nx) && (y < d.ny);
+    const size_t i = inside ? cell_index(d, x, y, z) : 0;
+    const uint8_t fl = inside ? d.flags[i] : (uint8_t)0;
+
+    SphAcc acc;
+    acc.pid = kNone;
+    float sbb = 0.f;
+
+    if (fl & F_ACTIVE) {
+        float fin[kQ];
+        const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
+        if (fl & F_BULK) {
+            // every neighbour exists (wrapping periodic axes) and carries PDFs
+            const int xm = x == 0 ? d.nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+            const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
+            const int zm = z == 0 ? d.nz - 1 : z - 1, zp = z == d.nz - 1 ? 0 : z + 1;
+#pragma unroll
+            for (int q = 0; q < kQ; q++) {
+                const int sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : x);
+                const int sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y);
+                const int sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z);
+                fin[q] = Store<S>::get(fa, (size_t)q * N + cell_index(d, sx, sy, sz), q);
+            }
+        } else {
+            float fo[kQ];
+            float rho0 = 0.f, j0x = 0.f, j0y = 0.f, j0z = 0.f;
+#pragma unroll
+            for (int q = 0; q < kQ; q++) {
+                fo[q] = Store<S>::get(fa, (size_t)q * N + i, q);
+                rho0 += fo[q];
+                j0x += cx(q) * fo[q]; j0y += cy(q) * fo[q]; j0z += cz(q) * fo[q];
+            }
+            const float u0x = (j0x - 0.5f * rho0 * gx) / rho0;
+            const float u0y = (j0y - 0.5f * rho0 * gy) / rho0;
+            const float u0z = (j0z - 0.5f * rho0 * gz) / rho0;
+            const float u0sq = u0x * u0x + u0y * u0y + u0z * u0z;
+            const bool isIF = (fl & F_IF) != 0;
+            const float phix = isIF ? phia[i] : 0.f;
+            const float kap = (isIF && d.kappa) ? d.kappa[i] : 0.f;
+            float dm = 0.f;
+            fin[0] = fo[0];
+#pragma unroll
+            for (int q = 1; q < kQ; q++) {
+                const int qb = opp(q);
+                size_t src;
+                if (!nbr(d, x, y, z, -cx(q), -cy(q), -cz(q), src)) {
+                    fin[q] = fo[qb];                                    // no-slip wall
+                    continue;
+                }
+                const uint8_t fs = d.flags[src];
+                if (fs & F_ACTIVE) {
+                    fin[q] = Store<S>::get(fa, (size_t)q * N + src, q);  // Eq. LBE1
+                    if (isIF) {  // link to the neighbour x + c_qb: s (f*_q(x+c_qb) - f*_qb(x))
+                        const float s = (fs & F_LIQ) ? 1.f : 0.5f * (phix + phia[src]);
+                        dm += s * (fin[q] - fo[qb]);
+                    }
+                } else if (fs & F_OBS) {                                // Eq. bbrule
+                    const uint32_t P = d.owner[src];
+                    if (P >= (uint32_t)d.nsph) { fin[q] = fo[qb]; continue; }
+                    if (P != acc.pid) {
+                        sph_flush_direct(d, acc);
+                        sph_begin(d, acc, P, x, y, z);
+                    }
+                    const Sphere& sp = d.sph[P];
+                    const float rx = acc.r[0] - 0.5f * cx(q), ry = acc.r[1] - 0.5f * cy(q), rz = acc.r[2] - 0.5f * cz(q);
+                    const float wx = (float)sp.w[0], wy = (float)sp.w[1], wz = (float)sp.w[2];
+                    const float uwx = (float)sp.u[0] + wy * rz - wz * ry;
+                    const float uwy = (float)sp.u[1] + wz * rx - wx * rz;
+                    const float uwz = (float)sp.u[2] + wx * ry - wy * rx;
+                    const float corr = 6.f * wgt(q) * rho0 * (cx(q) * uwx + cy(q) * uwy + cz(q) * uwz);
+                    fin[q] = fo[qb] + corr;
+                    // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
+                    const float dev = 2.f * (fo[qb] - wgt(q)) + corr;
+                    acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
+                    acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
+                    if (fl & F_LIQ) sbb += corr;
+                } else {                                                // gas: Eq. fsk
+                    const uint32_t b = d.owner[src];
+                    const float rg = b < (uint32_t)d.nbub ? (float)d.bub[b].rho_g : d.rho_g0;
+                    const float rw = rg + 6.f * d.sigma * kap;
+                    const float cu = cx(q) * u0x + cy(q) * u0y + cz(q) * u0z;
+                    fin[q] = -fo[qb] + 2.f * wgt(q) * rw * (1.f + 4.5f * cu * cu - 1.5f * u0sq);
+                }
+            }
+            if (isIF) {
+                const float mnew = (d.mass[i] + (float)d.sc->share) + dm;
+                float rho = 0.f;
+#pragma unroll
+                for (int q = 0; q < kQ; q++) rho += fin[q];
+                const float ph = mnew / rho;
+                d.mass[i] = mnew;
+                phib[i] = ph;
+                uint8_t mk = 0;
+                if (ph >= 1.f + d.eps) mk = K_FILLED;
+                else if (ph <= -d.eps) mk = K_EMPTIED;
+                if (mk) {
+                    d.mark[i] = mk;
+                    wl_push(d.wl_conv, &d.sc->n_conv, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
+                }
+            }
+        }
+
+        // moments, Guo-shifted velocity, TRT collision
+        float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            rho += fin[q];
+            jx += cx(q) * fin[q]; jy += cy(q) * fin[q]; jz += cz(q) * fin[q];
+        }
+        if (!(rho > 0.f)) atomicOr(&d.sc->status, S_UNSTABLE);
+        const float inv = 1.f / rho;
+        const float ux = (jx + 0.5f * rho * gx) * inv;
+        const float uy = (jy + 0.5f * rho * gy) * inv;
+        const float uz = (jz + 0.5f * rho * gz) * inv;
+        const float usq = ux * ux + uy * uy + uz * uz;
+        const float ug = ux * gx + uy * gy + uz * gz;
+        const float lp = d.lp, lm = d.lm;
+        const float cp = 1.f + 0.5f * lp, cm = 1.f + 0.5f * lm;
+        {
+            const float w = wgt(0) * rho;
+            const float ep = w * (1.f - 1.5f * usq);
+            Store<S>::put(fb, i, 0, fin[0] + lp * (fin[0] - ep) + cp * (w * (-3.f * ug)));
+        }
+#pragma unroll
+        for (int q = 1; q < kQ; q += 2) {
+            const int qb = q + 1;
+            const float w = wgt(q) * rho;
+            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+            const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
+            const float ep = w * (1.f + 4.5f * cu * cu - 1.5f * usq);
+            const float em = w * 3.f * cu;
+            const float fp = 0.5f * (fin[q] + fin[qb]);
+            const float fm = 0.5f * (fin[q] - fin[qb]);
+            const float a = lp * (fp - ep) + cp * (w * (9.f * cu * cg - 3.f * ug));
+            const float b = lm * (fm - em) + cm * (w * 3.f * cg);
+            Store<S>::put(fb, (size_t)q * N + i, q, fin[q] + a + b);
+            Store<S>::put(fb, (size_t)qb * N + i, qb, fin[qb] + a - b);
+        }
+    }
+
+    // ---- warp reduction of the sphere accumulators (every lane takes part)
+    const unsigned full = 0xffffffffu;
+    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
+    float TJ[3] = {0.f, 0.f, 0.f};
+    int XK[3] = {0, 0, 0};
+    if (acc.pid != kNone) {
+        TJ[0] = acc.r[1] * acc.J[2] - acc.r[2] * acc.J[1];
+        TJ[1] = acc.r[2] * acc.J[0] - acc.r[0] * acc.J[2];
+        TJ[2] = acc.r[0] * acc.J[1] - acc.r[1] * acc.J[0];
+        XK[0] = acc.xi[1] * acc.K[2] - acc.xi[2] * acc.K[1];
+        XK[1] = acc.xi[2] * acc.K[0] - acc.xi[0] * acc.K[2];
+        XK[2] = acc.xi[0] * acc.K[1] - acc.xi[1] * acc.K[0];
+    }
+    unsigned todo = __ballot_sync(full, acc.pid != kNone);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const uint32_t P = __shfl_sync(full, acc.pid, leader);
+        const bool mine = acc.pid == P;
+        todo &= ~__ballot_sync(full, mine);
+        float v[6];
+        int iv[6];
+#pragma unroll
+        for (int k = 0; k < 3; k++) {
+            v[k] = mine ? acc.J[k] : 0.f;
+            v[3 + k] = mine ? TJ[k] : 0.f;
+            iv[k] = mine ? acc.K[k] : 0;
+            iv[3 + k] = mine ? XK[k] : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                v[k] += __shfl_xor_sync(full, v[k], o);
+                iv[k] += __shfl_xor_sync(full, iv[k], o);
+            }
+        }
+        if (lane == leader) {
+            SphereAcc& g = d.acc[P];
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                atomicAdd(&g.J[k], (double)v[k]);
+                atomicAdd(&g.TJ[k], (double)v[3 + k]);
+                atomicAdd(&g.K[k], (unsigned long long)(long long)iv[k]);
+                atomicAdd(&g.XK[k], (unsigned long long)(long long)iv[3 + k]);
+            }
+        }
+    }
+    if (__any_sync(full, sbb != 0.f)) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sbb += __shfl_xor_sync(full, sbb, o);
+        if (lane == 0) atomicAdd(&d.sc->S_bb, (double)sbb);
+    }
+}
+
+void launch_sweep(const Dev& d, int cur, cudaStream_t s) {
+    const int bx = d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
+    const int by = 128 / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((d.nx + bx - 1) / bx, (d.ny + by - 1) / by, d.nz);
+    switch (d.storage) {
+        case LBM_STORE_F32: sweep_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur); break;
+        case LBM_STORE_F16DEV: sweep_kernel<LBM_STORE_F16DEV><<<grid, block, 0, s>>>(d, cur); break;
+        default: sweep_kernel<LBM_STORE_BF16DEV><<<grid, block, 0, s>>>(d, cur); break;
+    }
+}
+
+}  // namespace lbm

@@ -1,0 +1,69 @@
+"""Helpers of the GPU parity tests: moving a state between the CUDA library and the oracle,
+and comparing them under the tolerances of the method (test infrastructure)."""
+import numpy as np
+
+import oracle
+from paper_1712_07028_gb300 import workloads as W
+
+
+def gpu_state(sim):
+    """the CUDA library's full state as NumPy (FP64 where the oracle wants it)"""
+    st = {k: v.cpu().numpy() for k, v in sim.export_state().items()}
+    x, u, w = sim.spheres()
+    V0, V, rg = sim.bubbles()
+    M, sbb, scov, sunc, pool = sim.mass_budget()
+    F, T = sim.forces()
+    st.update(x=x, u=u, w=w, V0=V0, V=V, rho_g=rg, pool=pool, F=F, T=T)
+    return st
+
+
+def oracle_from_state(wl: W.Workload, st, near_tol=1e-5):
+    """an oracle simulation started from a state copied out of the CUDA library"""
+    o = oracle.Sim(wl, init=False, near_tol=near_tol)
+    o.f[:] = st["f"].astype(np.float64)
+    o.flag[:] = st["flags"]
+    o.m[:] = st["mass"].astype(np.float64)
+    o.phi[:] = st["phi"].astype(np.float64)
+    o.owner[:] = st["owner"]
+    o.kappa[:] = st["kappa"].astype(np.float64)
+    for b in range(len(wl.bubbles)):
+        o.bub[b, oracle.B_V0] = st["V0"][b]
+        o.bub[b, oracle.B_V] = st["V"][b]
+        o.bub[b, oracle.B_RHOG] = st["rho_g"][b]
+    for a in range(len(wl.spheres)):
+        o.sph[a, oracle.S_X:oracle.S_X + 3] = st["x"][a]
+        o.sph[a, oracle.S_U:oracle.S_U + 3] = st["u"][a]
+        o.sph[a, oracle.S_W:oracle.S_W + 3] = st["w"][a]
+    o.scal[oracle.SC_POOL] = st["pool"]
+    return o
+
+
+def dilate(mask, r, periodic=(False, False, False)):
+    """cells within D3Q19 distance r (r steps along D3Q19 links) of mask"""
+    c = oracle.velocities()
+    out = mask.copy()
+    for _ in range(r):
+        nxt = out.copy()
+        for q in range(1, 19):
+            sh = np.roll(out, shift=(c[q, 2], c[q, 1], c[q, 0]), axis=(0, 1, 2))
+            # rolled-in wrap across a wall axis is not a neighbour; trimming it only widens
+            nxt |= sh
+        out = nxt
+    return out
+
+
+def compare_fields(orc_sim, st, active_mask=None):
+    """max |d rho|, max |d u| over cells active in both, and the oracle's rho/u"""
+    rho_o, u_o = orc_sim.fields()
+    f = st["f"].astype(np.float64)
+    c = oracle.velocities().astype(np.float64)
+    act = ((st["flags"] & (oracle.LIQ | oracle.IFACE)) != 0) & ((orc_sim.flag & (oracle.LIQ | oracle.IFACE)) != 0)
+    if active_mask is not None:
+        act &= active_mask
+    rho_g = f.sum(axis=0)
+    g = np.array(orc_sim.p.g[:])
+    j = np.einsum("qk,qzyx->kzyx", c, f)
+    u_g = (j - 0.5 * rho_g * g[:, None, None, None]) / np.where(act, rho_g, 1.0)
+    drho = np.abs(rho_g - rho_o)[act].max() if act.any() else 0.0
+    du = np.abs(u_g - u_o)[:, act].max() if act.any() else 0.0
+    return drho, du, int(act.sum())

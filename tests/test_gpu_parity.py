@@ -1,0 +1,232 @@
+"""Parity of the CUDA library (through the C ABI) with the FP64 oracle.
+
+Tolerances: after 200 steps of the 32^3 bubble/sphere column, max |d rho| <= 1e-5,
+max |d u| <= 1e-6, |d phi| <= 1e-5, cell types identical except at cells the oracle logged
+within 1e-4 of a conversion threshold (rho/u/phi then compared away from those cells), total
+mass drift <= 1e-6 relative per 1000 FP32 steps.  One-step parity from a state copied out of
+the GPU isolates each step with tight bounds.  FP16 / BF16 deviation storage is reported
+against the same oracle with looser, stated bounds.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1712_07028_gb300 import workloads as W
+from tests import gpu_util as U
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("these tests need the GPU")
+    from paper_1712_07028_gb300 import lbm as L
+    L.load()
+    return L
+
+
+def _liquid(n=24, g=(1e-5, -2e-5, 3e-5), bc=(0, 0, 0), tau=0.6, spheres=(), mode=W.SPHERES_FIXED, storage="f32"):
+    wl = W.liquid_box(n, bc=bc, g=g, tau=tau)
+    wl.spheres = list(spheres)
+    wl.sphere_mode = mode
+    wl.storage = storage
+    return wl
+
+
+def test_liquid_box_walls_gravity(lbm):
+    """stream + TRT + Guo + halfway walls: 100 steps of a walled box under an oblique body force"""
+    wl = _liquid()
+    sim = lbm.Sim(wl)
+    sim.step(100)
+    o = oracle.Sim(wl)
+    o.step(100)
+    drho, du, n = U.compare_fields(o, U.gpu_state(sim))
+    assert n == wl.cells
+    assert drho <= 1e-6 and du <= 1e-7, (drho, du)
+
+
+def test_poiseuille_gpu(lbm):
+    """body-force channel: the GPU reproduces the analytic parabola (Sec. 2.1 magic TRT)"""
+    H, g, tau = 16, 1e-6, 1.0
+    wl = W.Workload(name="channel", nx=4, ny=4, nz=H, tau=tau, g=(g, 0, 0), bc=(1, 1, 0))
+    sim = lbm.Sim(wl)
+    nu = (tau - 0.5) / 3
+    sim.step(int(3.5 * H * H / nu))
+    u = sim.fields()["u"].cpu().numpy()
+    z = np.arange(H)
+    ua = g / (2 * nu) * (z + 0.5) * (H - 0.5 - z)
+    assert np.abs(u[0, :, 1, 1] - ua).max() < 2e-5 * ua.max()
+
+
+@pytest.mark.parametrize("nsph", [1, 2])
+def test_sphere_links_forces(lbm, nsph):
+    """moving-wall bounce-back and momentum exchange (Eqs. bbrule, netforce, torque) with a
+    translating + rotating sphere, or two touching ones (links between obstacle nodes)"""
+    if nsph == 1:
+        sph = [W.Sphere((10.3, 11.6, 12.2), 4.0, 1.5, (0.01, -0.004, 0.002), (0.001, 0.002, -0.003))]
+    else:
+        sph = [W.Sphere((10.0, 12.0, 12.0), 4.0, 1.5, (0.004, 0, 0), (0, 0, 0.001)),
+               W.Sphere((19.0, 12.0, 12.0), 4.0, 1.5, (-0.003, 0.001, 0), (0.001, 0, 0))]
+    wl = _liquid(n=26, spheres=sph)
+    sim = lbm.Sim(wl)
+    o = oracle.Sim(wl)
+    for k in range(3):
+        sim.step(10)
+        o.step(10)
+        F, T = sim.forces()
+        Fo, To = o.forces
+        assert np.abs(F - Fo).max() <= 1e-6 * np.abs(Fo).max() + 1e-9, (F, Fo)
+        assert np.abs(T - To).max() <= 1e-6 * np.abs(To).max() + 1e-8, (T, To)
+    drho, du, _ = U.compare_fields(o, U.gpu_state(sim))
+    assert drho <= 1e-6 and du <= 1e-7, (drho, du)
+
+
+def _one_step_check(lbm, wl, pre_steps, f_tol, phi_tol):
+    sim = lbm.Sim(wl)
+    sim.step(pre_steps)
+    st0 = U.gpu_state(sim)
+    o = U.oracle_from_state(wl, st0, near_tol=1e-5)
+    sim.step(1)
+    o.step(1)
+    st1 = U.gpu_state(sim)
+    flags_o = o.flag
+    mism = st1["flags"] != flags_o
+    near = o.near > 0
+    assert not np.any(mism & ~near), "type mismatch away from a threshold at %s" % (np.argwhere(mism & ~near)[:5],)
+    keep = ~U.dilate(mism, 2)
+    act = ((st1["flags"] & 3) != 0) & ((flags_o & 3) != 0) & keep
+    df = np.abs(st1["f"].astype(np.float64) - o.f)[:, act].max() if act.any() else 0.0
+    iface = (st1["flags"] == oracle.IFACE) & (flags_o == oracle.IFACE) & keep
+    dphi = np.abs(st1["phi"] - o.phi)[iface].max() if iface.any() else 0.0
+    dm = np.abs(st1["mass"] - o.m)[iface].max() if iface.any() else 0.0
+    assert df <= f_tol, df
+    assert dphi <= phi_tol and dm <= phi_tol, (dphi, dm)
+    if wl.spheres:
+        Fo, To = o.forces
+        assert np.abs(st1["F"] - Fo).max() <= 1e-6 * max(1e-3, np.abs(Fo).max())
+        assert np.abs(st1["T"] - To).max() <= 1e-6 * max(1e-2, np.abs(To).max())
+        assert np.abs(st1["x"] - o.positions).max() <= 1e-9
+    if wl.bubbles:
+        assert np.abs(st1["rho_g"] - o.rho_gas).max() <= 1e-6
+    return int(mism.sum()), int(act.sum())
+
+
+@pytest.mark.parametrize("pre", [0, 1, 40, 150])
+def test_one_step_from_gpu_state_c0(lbm, pre):
+    """every part of one step, isolated: the oracle steps the GPU's own state once"""
+    _one_step_check(lbm, W.column_c0(), pre, 2e-6, 2e-6)
+
+
+def test_one_step_moving_sphere_near_surface(lbm):
+    """a sphere prescribed to cross the free surface: cover / uncover and refill next to
+    interface cells, from the GPU's state"""
+    wl = W.Workload(name="cross", nx=28, ny=26, nz=30, tau=0.7, g=(0, 0, -1e-5), bubbles=[W.Bubble((14, 13, 18), 7.0)],
+                    spheres=[W.Sphere((14.2, 13.1, 8.6), 3.5, 2.0, (0.0, 0.0, 0.05))], sphere_mode=W.SPHERES_PRESCRIBED)
+    for pre in (3, 20, 45):
+        _one_step_check(lbm, wl, pre, 2e-6, 2e-6)
+
+
+def _r27_compare(o, st):
+    """R27: mismatching types only at cells the oracle logged near a threshold; rho/u/phi
+    compared away (distance > 2) from them"""
+    mism = st["flags"] != o.flag
+    assert not np.any(mism & ~(o.near > 0)), np.argwhere(mism & ~(o.near > 0))[:5]
+    keep = ~U.dilate(mism, 2)
+    drho, du, n = U.compare_fields(o, st, keep)
+    iface = (st["flags"] == oracle.IFACE) & (o.flag == oracle.IFACE) & keep
+    dphi = np.abs(st["phi"] - o.phi)[iface].max() if iface.any() else 0.0
+    return drho, du, dphi, int(mism.sum()), int((~keep).sum())
+
+
+def test_c0_200_steps(lbm):
+    """the 32^3 column (bubble r=6, falling sphere r=3), 200 steps, FP32 vs FP64"""
+    wl = W.column_c0()
+    sim = lbm.Sim(wl)
+    sim.step(wl.steps)
+    o = oracle.Sim(wl)
+    o.step(wl.steps)
+    st = U.gpu_state(sim)
+    drho, du, dphi, nmis, nexcl = _r27_compare(o, st)
+    print("C0 200 steps: max|drho|=%.3g max|du|=%.3g max|dphi|=%.3g type mismatches=%d excluded=%d" % (drho, du, dphi, nmis, nexcl))
+    assert drho <= 1e-5 and du <= 1e-6 and dphi <= 1e-5
+    Fo, To = o.forces
+    assert np.abs(st["F"] - Fo).max() <= 1e-3 * np.abs(Fo).max() + 1e-7
+    assert np.abs(st["x"] - o.positions).max() <= 1e-6
+
+
+def test_c0_mass_drift(lbm):
+    """total mass drift <= 1e-6 relative per 1000 FP32 steps (budget terms in FP64)"""
+    wl = W.column_c0()
+    sim = lbm.Sim(wl)
+    sim.step(1)
+    M0, b0, c0, u0, _ = sim.mass_budget()
+    sim.step(1000)
+    M, b, c, u, _ = sim.mass_budget()
+    drift = abs((M - M0) - (b - b0) - (u - u0) + (c - c0)) / M0
+    print("C0 mass drift over 1000 steps: %.3g" % drift)
+    assert drift <= 1e-6
+    assert sim.status() == 0
+
+
+@pytest.mark.parametrize("storage,tol", [("f16dev", (2e-3, 2e-4, 5e-3)), ("bf16dev", (2e-2, 2e-3, 5e-2))])
+def test_c0_reduced_storage(lbm, storage, tol):
+    """PDFs stored as FP16 / BF16 deviations from w_q, collisions in FP32: error against the
+    FP64 oracle after 200 steps of the column (reported; bounded loosely)"""
+    wl = W.column_c0()
+    wl.storage = storage
+    sim = lbm.Sim(wl)
+    sim.step(wl.steps)
+    o = oracle.Sim(W.column_c0())
+    o.step(wl.steps)
+    st = U.gpu_state(sim)
+    mism = st["flags"] != o.flag
+    keep = ~U.dilate(mism, 2)
+    drho, du, _ = U.compare_fields(o, st, keep)
+    print("%s C0 200 steps: max|drho|=%.3g max|du|=%.3g mismatches=%d" % (storage, drho, du, int(mism.sum())))
+    assert drho <= tol[0] and du <= tol[1]
+    assert mism.mean() <= tol[2]
+
+
+def test_c1_full_size_one_step(lbm):
+    """the 128^3 column of 64 spheres at full size, after steps replayed through the CUDA
+    graph the benchmark times: one step against the oracle from the GPU's state"""
+    _one_step_check(lbm, W.column_c1(), 40, 2e-6, 2e-6)
+
+
+def test_status_unstable(lbm):
+    """a body force far beyond the scheme's stability makes densities non-positive: the
+    status word reports it and lbm_forces returns LBM_EUNSTABLE (no GPU fault involved)"""
+    wl = _liquid(n=12, g=(0.0, 0.0, -0.5), tau=0.51, spheres=[W.Sphere((6.0, 6.0, 6.0), 2.0, 1.5)])
+    sim = lbm.Sim(wl)
+    sim.step(300)
+    assert sim.status() & lbm.S_UNSTABLE
+    with pytest.raises(lbm.LBMError) as e:
+        sim.forces()
+    assert e.value.code == lbm.LBM_EUNSTABLE
+
+
+def test_abi_argument_errors(lbm):
+    L = lbm.load()
+    p = lbm.make_params(_liquid(n=8))
+    p.nx = 2
+    nbytes = ctypes.c_size_t()
+    assert L.lbm_arena_bytes(ctypes.byref(p), ctypes.byref(nbytes)) == lbm.LBM_EINVAL
+    sim = lbm.Sim(_liquid(n=8))
+    sim.step(1)
+    c = np.zeros(3)
+    assert L.lbm_add_bubble(sim.ctx, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), 2.0, None) == lbm.LBM_ESTATE
+    assert L.lbm_step(sim.ctx, -1) == lbm.LBM_EINVAL
+
+
+def test_launch_count(lbm):
+    wl = W.column_c0()
+    sim = lbm.Sim(wl)
+    sim.step(1)
+    n1 = sim.launches()
+    sim.step(10)
+    assert (sim.launches() - n1) % 10 == 0 and sim.launches() > n1
