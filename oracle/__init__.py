@@ -20,7 +20,7 @@ _lib = None
 
 # the oracle's cell-type codes and record layouts (fslbm_oracle.c)
 LIQ, IFACE, GAS, OBS = 1, 2, 4, 8
-S_X, S_U, S_W, S_R, S_RHO, S_F, S_T, S_FLUB, S_LEN = 0, 3, 6, 9, 10, 11, 14, 17, 24
+S_X, S_U, S_W, S_R, S_RHO, S_F, S_T, S_FLUB, S_FP, S_TP, S_HASP, S_LEN = 0, 3, 6, 9, 10, 11, 14, 17, 20, 23, 26, 32
 B_C, B_R, B_V0, B_V, B_RHOG, B_LEN = 0, 3, 4, 5, 6, 8
 SC_POOL, SC_NIF, SC_SBB, SC_SCOV, SC_SUNC, SC_STEPS, SC_STATUS, SC_LEN = 0, 1, 2, 3, 4, 5, 6, 16
 

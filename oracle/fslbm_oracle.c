@@ -58,7 +58,8 @@ enum { C_LIQ = 1, C_IF = 2, C_GAS = 4, C_OBS = 8 };
 enum { M_FILLED = 1, M_EMPTIED = 2, M_NEWIF = 4, M_FROMLIQ = 8, M_UNCOV = 16, M_RECV = 32 };
 
 /* sphere record layout, doubles */
-enum { S_X = 0, S_U = 3, S_W = 6, S_R = 9, S_RHO = 10, S_F = 11, S_T = 14, S_FLUB = 17, S_LEN = 24 };
+enum { S_X = 0, S_U = 3, S_W = 6, S_R = 9, S_RHO = 10, S_F = 11, S_T = 14, S_FLUB = 17, S_FP = 20, S_TP = 23,
+       S_HASP = 26, S_LEN = 32 };
 /* bubble record layout, doubles */
 enum { B_C = 0, B_R = 3, B_V0 = 4, B_V = 5, B_RHOG = 6, B_LEN = 8 };
 /* scalar slots */
@@ -602,7 +603,11 @@ static void wrap_position(const orc_params *p, double *X)
 }
 
 /* Newton-Euler in n_substeps semi-implicit Euler sub-steps: the hydrodynamic force and
- * torque of the sweep are held, lubrication and gravity are re-evaluated each sub-step. */
+ * torque are held over the LBM step, lubrication and gravity are re-evaluated each sub-step.
+ * The hydrodynamic force and torque used are the mean of the momentum exchange of this step
+ * and of the previous one (Ladd 1994): the explicit coupling of Sec. 2.3 otherwise lets a
+ * two-step oscillation of light spheres (density 1.5 - 2) grow from round-off; on the first
+ * step of a sphere the current values are used alone. */
 static void move_spheres(const orc_params *p, orc_state *s)
 {
     if (p->nsph == 0) return;
@@ -622,10 +627,13 @@ static void move_spheres(const orc_params *p, orc_state *s)
         for (int a = 0; a < p->nsph; a++) {
             double *S = s->sph + (long)a * S_LEN;
             const double mp = sphere_mass(S), I = 0.4 * mp * S[S_R] * S[S_R];
+            const int hasp = S[S_HASP] != 0.0;
             for (int k = 0; k < 3; k++) {
+                const double Fh = hasp ? 0.5 * (S[S_F + k] + S[S_FP + k]) : S[S_F + k];
+                const double Th = hasp ? 0.5 * (S[S_T + k] + S[S_TP + k]) : S[S_T + k];
                 S[S_FLUB + k] = Fl[3 * a + k];
-                S[S_U + k] += dt * (S[S_F + k] + Fl[3 * a + k] + mp * p->g[k]) / mp;
-                S[S_W + k] += dt * S[S_T + k] / I;
+                S[S_U + k] += dt * (Fh + Fl[3 * a + k] + mp * p->g[k]) / mp;
+                S[S_W + k] += dt * Th / I;
             }
             for (int k = 0; k < 3; k++) S[S_X + k] += dt * S[S_U + k];
             wrap_position(p, S + S_X);
@@ -826,8 +834,11 @@ int orc_step(const orc_params *p, orc_state *s, int nsteps)
                 s->scal[SC_POOL] = 0.0;
             }
         }
-        for (int a = 0; a < p->nsph; a++)
-            for (int k = 0; k < 6; k++) s->sph[(long)a * S_LEN + S_F + k] = 0.0;
+        for (int a = 0; a < p->nsph; a++)   /* this step's momentum exchange starts from zero */
+            for (int k = 0; k < 6; k++) {
+                s->sph[(long)a * S_LEN + S_FP + k] = s->sph[(long)a * S_LEN + S_F + k];
+                s->sph[(long)a * S_LEN + S_F + k] = 0.0;
+            }
         sweep(p, s, share);                                        /* 1 */
         conversions(p, s);                                         /* 2 */
         memcpy(s->f, s->ft, sizeof(double) * (size_t)NQ * (size_t)N);
@@ -835,6 +846,7 @@ int orc_step(const orc_params *p, orc_state *s, int nsteps)
         if (p->sigma > 0.0) curvature(p, s);                       /* 4 */
         contact_links(p, s);                                       /* 5 */
         move_spheres(p, s);
+        for (int a = 0; a < p->nsph; a++) s->sph[(long)a * S_LEN + S_HASP] = 1.0;
         if (p->sphere_mode != 0 && p->nsph > 0) cover_uncover(p, s); /* 6 */
         s->scal[SC_STEPS] += 1.0;
     }
