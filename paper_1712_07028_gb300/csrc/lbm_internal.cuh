@@ -41,24 +41,27 @@ enum : uint8_t { K_FILLED = 1, K_EMPTIED = 2, K_NEWIF = 4, K_FROMLIQ = 8, K_RECV
 constexpr uint32_t kNone = 0xffffffffu;
 
 // ---------------------------------------------------------------- PDF storage traits
+// Every storage keeps the deviation f_q - w_q from the rest equilibrium (FP32, FP16 or BF16);
+// the kernels compute in deviation form too, so densities and velocities of a nearly
+// uniform liquid are not rounded against the O(1) weights.
 template <int S> struct Store;
 template <> struct Store<LBM_STORE_F32> {
     using T = float;
-    static __device__ __forceinline__ float get(const T* p, size_t i, int) { return __ldg(p + i); }
-    static __device__ __forceinline__ float get_nc(const T* p, size_t i, int) { return p[i]; }
-    static __device__ __forceinline__ void put(T* p, size_t i, int, float v) { p[i] = v; }
+    static __device__ __forceinline__ float get(const T* p, size_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ float get_nc(const T* p, size_t i) { return p[i]; }
+    static __device__ __forceinline__ void put(T* p, size_t i, float v) { p[i] = v; }
 };
 template <> struct Store<LBM_STORE_F16DEV> {
     using T = __half;
-    static __device__ __forceinline__ float get(const T* p, size_t i, int q) { return wgt(q) + __half2float(__ldg(p + i)); }
-    static __device__ __forceinline__ float get_nc(const T* p, size_t i, int q) { return wgt(q) + __half2float(p[i]); }
-    static __device__ __forceinline__ void put(T* p, size_t i, int q, float v) { p[i] = __float2half_rn(v - wgt(q)); }
+    static __device__ __forceinline__ float get(const T* p, size_t i) { return __half2float(__ldg(p + i)); }
+    static __device__ __forceinline__ float get_nc(const T* p, size_t i) { return __half2float(p[i]); }
+    static __device__ __forceinline__ void put(T* p, size_t i, float v) { p[i] = __float2half_rn(v); }
 };
 template <> struct Store<LBM_STORE_BF16DEV> {
     using T = __nv_bfloat16;
-    static __device__ __forceinline__ float get(const T* p, size_t i, int q) { return wgt(q) + __bfloat162float(__ldg(p + i)); }
-    static __device__ __forceinline__ float get_nc(const T* p, size_t i, int q) { return wgt(q) + __bfloat162float(p[i]); }
-    static __device__ __forceinline__ void put(T* p, size_t i, int q, float v) { p[i] = __float2bfloat16_rn(v - wgt(q)); }
+    static __device__ __forceinline__ float get(const T* p, size_t i) { return __bfloat162float(__ldg(p + i)); }
+    static __device__ __forceinline__ float get_nc(const T* p, size_t i) { return __bfloat162float(p[i]); }
+    static __device__ __forceinline__ void put(T* p, size_t i, float v) { p[i] = __float2bfloat16_rn(v); }
 };
 
 // ----------------------------------------------------------------- device-side records
@@ -68,6 +71,9 @@ struct Sphere {          // FP64 state of one sphere
     double F[3], T[3];   // momentum-exchange force and torque of the last step
     double x0[3];        // centre at the start of the step (before the sub-steps)
     double Fl[3];        // lubrication force of the last sub-step
+    double hasp;         // 1 once F, T of a previous step exist
+    double Fp[3], Tp[3]; // momentum-exchange force and torque of the step before
+    double stepped;      // 1 after the first sphere update
     double pad[1];
 };
 struct SphereAcc {       // per-step momentum-exchange accumulators (zeroed by the sphere update)
@@ -185,26 +191,29 @@ __device__ __forceinline__ bool wl_push(uint32_t* list, uint32_t* count, uint32_
     return false;
 }
 
-// post-collision moments of cell i from grid f: rho = sum f*, u = (sum c f* - rho g/2)/rho
+// post-collision moments of cell i from grid f (deviations): rho = 1 + sum d*,
+// u = (sum c d* - rho g/2)/rho
 template <int S>
 __device__ __forceinline__ void post_moments(const Dev& d, const typename Store<S>::T* f, size_t i, float& rho, float u[3]) {
-    float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int q = 0; q < kQ; q++) {
-        const float v = Store<S>::get_nc(f, (size_t)q * d.N + i, q);
-        r += v;
+        const float v = Store<S>::get_nc(f, (size_t)q * d.N + i);
+        dr += v;
         jx += cx(q) * v; jy += cy(q) * v; jz += cz(q) * v;
     }
+    const float r = 1.f + dr;
     rho = r;
     u[0] = (jx - 0.5f * r * d.g[0]) / r;
     u[1] = (jy - 0.5f * r * d.g[1]) / r;
     u[2] = (jz - 0.5f * r * d.g[2]) / r;
 }
 
-__device__ __forceinline__ float equilibrium(int q, float rho, const float u[3]) {
+// deviation of the equilibrium (Eq. equilibrium) from the weight: e_q(rho,u) - w_q
+__device__ __forceinline__ float equilibrium_dev(int q, float rho, const float u[3]) {
     const float cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    return wgt(q) * rho * (1.f + 3.f * cu + 4.5f * cu * cu - 1.5f * uu);
+    return wgt(q) * ((rho - 1.f) + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
 }
 
 // minimum-image difference a - b along axis k (beyond 4 periods, or not finite, the value is

@@ -36,7 +36,11 @@ __global__ void sph_prepare_kernel(const Dev d) {
     for (int k = 0; k < 3; k++) {
         K[k] = (double)(long long)a.K[k];
         XK[k] = (double)(long long)a.XK[k];
+        s.Fp[k] = s.F[k];   // the step before, kept for the two-step average
+        s.Tp[k] = s.T[k];
     }
+    s.hasp = s.stepped;
+    s.stepped = 1.0;
     const double xK[3] = {s.x[1] * K[2] - s.x[2] * K[1], s.x[2] * K[0] - s.x[0] * K[2], s.x[0] * K[1] - s.x[1] * K[0]};
     for (int k = 0; k < 3; k++) {
         s.F[k] = a.J[k] + K[k] / 36.0;
@@ -171,10 +175,15 @@ __global__ void sph_substep_kernel(const Dev d, const Sphere* src, Sphere* dst, 
     Sphere o = s;
     const double m = s.rho * 4.0 / 3.0 * kPi * s.R * s.R * s.R, I = 0.4 * m * s.R * s.R;
     const int L[3] = {d.nx, d.ny, d.nz};
+    // the hydrodynamic force and torque are the mean of this step's and the previous step's
+    // momentum exchange (Ladd 1994), which keeps light spheres from a two-step oscillation
+    const bool hasp = s.hasp != 0.0;
     for (int k = 0; k < 3; k++) {
+        const double Fh = hasp ? 0.5 * (s.F[k] + s.Fp[k]) : s.F[k];
+        const double Th = hasp ? 0.5 * (s.T[k] + s.Tp[k]) : s.T[k];
         o.Fl[k] = Fl[k];
-        o.u[k] = s.u[k] + dt * (s.F[k] + Fl[k] + m * d.gd[k]) / m;
-        o.w[k] = s.w[k] + dt * s.T[k] / I;
+        o.u[k] = s.u[k] + dt * (Fh + Fl[k] + m * d.gd[k]) / m;
+        o.w[k] = s.w[k] + dt * Th / I;
     }
     for (int k = 0; k < 3; k++) {
         o.x[k] = s.x[k] + dt * o.u[k];
@@ -270,9 +279,9 @@ __global__ void cover_apply_kernel(const Dev d, const int nxt) {
             else d.owner[i] = own;
         } else if (own != kNone) {
             if (t & F_LIQ) {
-                float r = 0.f;
-                for (int q = 0; q < kQ; q++) r += Store<S>::get_nc(f, (size_t)q * d.N + i, q);
-                atomicAdd(&d.sc->S_cover, (double)r);
+                float dr = 0.f;
+                for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + i);
+                atomicAdd(&d.sc->S_cover, (double)(1.f + dr));
             } else if (t & F_IF) {
                 atomicAdd(&d.sc->S_cover, (double)d.mass[i]);
                 atomicSub(&d.sc->n_iface_acc, 1u);
@@ -348,7 +357,7 @@ __global__ void cover_refill_kernel(const Dev d, const int nxt) {
             d.mass[i] = rb;
             atomicAdd(&d.sc->S_uncover, (double)rb);
         }
-        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, q, equilibrium(q, rb, uf));
+        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, equilibrium_dev(q, rb, uf));
     }
 }
 

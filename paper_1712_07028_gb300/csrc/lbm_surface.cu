@@ -57,10 +57,10 @@ __device__ void py_gradient(const Dev& d, const float* phi, int x, int y, int z,
 
 template <int S>
 __device__ float cell_rho(const Dev& d, const typename Store<S>::T* f, size_t i) {
-    float r = 0.f;
+    float dr = 0.f;
 #pragma unroll
-    for (int q = 0; q < kQ; q++) r += Store<S>::get_nc(f, (size_t)q * d.N + i, q);
-    return r;
+    for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + i);
+    return 1.f + dr;
 }
 
 // (ii) filled cells: gas neighbours become new interface cells; emptied neighbours stay
@@ -137,7 +137,7 @@ __global__ void conv_newif_kernel(const Dev d, const int nxt) {
         }
         const float rb = cnt ? rs / cnt : 1.f;
         const float ub[3] = {cnt ? us[0] / cnt : 0.f, cnt ? us[1] / cnt : 0.f, cnt ? us[2] / cnt : 0.f};
-        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, q, equilibrium(q, rb, ub));
+        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, equilibrium_dev(q, rb, ub));
         d.mass[i] = 0.f;
     }
 }
@@ -484,8 +484,7 @@ __global__ void init_kernel(const Dev d, const double* geo) {
         d.phi[0][i] = ph;
         d.phi[1][i] = ph;
         if (d.kappa) d.kappa[i] = 0.f;
-        const float u0[3] = {0.f, 0.f, 0.f};
-        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, q, equilibrium(q, 1.f, u0));
+        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, 0.f);   // e(1, 0) - w = 0
     }
 }
 
@@ -529,7 +528,7 @@ __global__ void export_kernel(const Dev d, const int cur, float* f, uint8_t* fla
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
         const uint8_t t = d.flags[i] & F_TYPE;
         if (f)
-            for (int q = 0; q < kQ; q++) f[(size_t)q * d.N + i] = Store<S>::get_nc(fs, (size_t)q * d.N + i, q);
+            for (int q = 0; q < kQ; q++) f[(size_t)q * d.N + i] = wgt(q) + Store<S>::get_nc(fs, (size_t)q * d.N + i);
         if (flags) flags[i] = t;
         if (m) m[i] = (t & F_IF) ? d.mass[i] : 0.f;
         if (phi) phi[i] = (t & F_IF) ? d.phi[cur][i] : ((t & F_GAS) ? 0.f : 1.f);
@@ -562,9 +561,9 @@ __global__ void mass_kernel(const Dev d, const int cur) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
         const uint8_t t = d.flags[i] & F_TYPE;
         if (t & F_LIQ) {
-            double r = 0.0;
-            for (int q = 0; q < kQ; q++) r += (double)Store<S>::get_nc(f, (size_t)q * d.N + i, q);
-            acc += r;
+            double dr = 0.0;
+            for (int q = 0; q < kQ; q++) dr += (double)Store<S>::get_nc(f, (size_t)q * d.N + i);
+            acc += 1.0 + dr;
         } else if (t & F_IF) {
             acc += (double)d.mass[i];
         }

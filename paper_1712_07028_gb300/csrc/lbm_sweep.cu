@@ -104,17 +104,18 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) 
                 const int sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : x);
                 const int sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y);
                 const int sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z);
-                fin[q] = Store<S>::get(fa, (size_t)q * N + cell_index(d, sx, sy, sz), q);
+                fin[q] = Store<S>::get(fa, (size_t)q * N + cell_index(d, sx, sy, sz));
             }
         } else {
             float fo[kQ];
-            float rho0 = 0.f, j0x = 0.f, j0y = 0.f, j0z = 0.f;
+            float drho0 = 0.f, j0x = 0.f, j0y = 0.f, j0z = 0.f;
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
-                fo[q] = Store<S>::get(fa, (size_t)q * N + i, q);
-                rho0 += fo[q];
+                fo[q] = Store<S>::get(fa, (size_t)q * N + i);
+                drho0 += fo[q];
                 j0x += cx(q) * fo[q]; j0y += cy(q) * fo[q]; j0z += cz(q) * fo[q];
             }
+            const float rho0 = 1.f + drho0;
             const float u0x = (j0x - 0.5f * rho0 * gx) / rho0;
             const float u0y = (j0y - 0.5f * rho0 * gy) / rho0;
             const float u0z = (j0z - 0.5f * rho0 * gz) / rho0;
@@ -134,7 +135,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) 
                 }
                 const uint8_t fs = d.flags[src];
                 if (fs & F_ACTIVE) {
-                    fin[q] = Store<S>::get(fa, (size_t)q * N + src, q);  // Eq. LBE1
+                    fin[q] = Store<S>::get(fa, (size_t)q * N + src);  // Eq. LBE1
                     if (isIF) {  // link to the neighbour x + c_qb: s (f*_q(x+c_qb) - f*_qb(x))
                         const float s = (fs & F_LIQ) ? 1.f : 0.5f * (phix + phia[src]);
                         dm += s * (fin[q] - fo[qb]);
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) 
                     const float corr = 6.f * wgt(q) * rho0 * (cx(q) * uwx + cy(q) * uwy + cz(q) * uwz);
                     fin[q] = fo[qb] + corr;
                     // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
-                    const float dev = 2.f * (fo[qb] - wgt(q)) + corr;
+                    const float dev = 2.f * fo[qb] + corr;
                     acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
                     acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
                     if (fl & F_LIQ) sbb += corr;
@@ -164,15 +165,16 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) 
                     const float rg = b < (uint32_t)d.nbub ? (float)d.bub[b].rho_g : d.rho_g0;
                     const float rw = rg + 6.f * d.sigma * kap;
                     const float cu = cx(q) * u0x + cy(q) * u0y + cz(q) * u0z;
-                    fin[q] = -fo[qb] + 2.f * wgt(q) * rw * (1.f + 4.5f * cu * cu - 1.5f * u0sq);
+                    // -f*_qb + 2 e+_q, in deviations: 2 (e+_q - w_q) - (f*_qb - w_q)
+                    fin[q] = 2.f * wgt(q) * ((rw - 1.f) + rw * (4.5f * cu * cu - 1.5f * u0sq)) - fo[qb];
                 }
             }
             if (isIF) {
                 const float mnew = (d.mass[i] + (float)d.sc->share) + dm;
-                float rho = 0.f;
+                float drho = 0.f;
 #pragma unroll
-                for (int q = 0; q < kQ; q++) rho += fin[q];
-                const float ph = mnew / rho;
+                for (int q = 0; q < kQ; q++) drho += fin[q];
+                const float ph = mnew / (1.f + drho);
                 d.mass[i] = mnew;
                 phib[i] = ph;
                 uint8_t mk = 0;
@@ -185,13 +187,14 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) 
             }
         }
 
-        // moments, Guo-shifted velocity, TRT collision
-        float rho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+        // moments, Guo-shifted velocity, TRT collision, all on deviations f - w
+        float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
         for (int q = 0; q < kQ; q++) {
-            rho += fin[q];
+            drho += fin[q];
             jx += cx(q) * fin[q]; jy += cy(q) * fin[q]; jz += cz(q) * fin[q];
         }
+        const float rho = 1.f + drho;
         if (!(rho > 0.f)) atomicOr(&d.sc->status, S_UNSTABLE);
         const float inv = 1.f / rho;
         const float ux = (jx + 0.5f * rho * gx) * inv;
@@ -202,24 +205,25 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) 
         const float lp = d.lp, lm = d.lm;
         const float cp = 1.f + 0.5f * lp, cm = 1.f + 0.5f * lm;
         {
-            const float w = wgt(0) * rho;
-            const float ep = w * (1.f - 1.5f * usq);
-            Store<S>::put(fb, i, 0, fin[0] + lp * (fin[0] - ep) + cp * (w * (-3.f * ug)));
+            // q = 0: f+ = f, e+ - w = w (rho - 1 - 1.5 rho u.u), G+ = -3 w rho u.g
+            const float w = wgt(0);
+            const float ep = w * (drho - 1.5f * rho * usq);
+            Store<S>::put(fb, i, fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug)));
         }
 #pragma unroll
         for (int q = 1; q < kQ; q += 2) {
             const int qb = q + 1;
-            const float w = wgt(q) * rho;
+            const float w = wgt(q);
             const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
             const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
-            const float ep = w * (1.f + 4.5f * cu * cu - 1.5f * usq);
-            const float em = w * 3.f * cu;
+            const float ep = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));   // e+_q - w_q
+            const float em = w * rho * 3.f * cu;                                  // e-_q
             const float fp = 0.5f * (fin[q] + fin[qb]);
             const float fm = 0.5f * (fin[q] - fin[qb]);
-            const float a = lp * (fp - ep) + cp * (w * (9.f * cu * cg - 3.f * ug));
-            const float b = lm * (fm - em) + cm * (w * 3.f * cg);
-            Store<S>::put(fb, (size_t)q * N + i, q, fin[q] + a + b);
-            Store<S>::put(fb, (size_t)qb * N + i, qb, fin[qb] + a - b);
+            const float a = lp * (fp - ep) + cp * (w * rho * (9.f * cu * cg - 3.f * ug));
+            const float b = lm * (fm - em) + cm * (w * rho * 3.f * cg);
+            Store<S>::put(fb, (size_t)q * N + i, fin[q] + a + b);
+            Store<S>::put(fb, (size_t)qb * N + i, fin[qb] + a - b);
         }
     }
 

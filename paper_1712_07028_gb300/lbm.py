@@ -135,6 +135,7 @@ class Sim:
                                                       _dp(_v3(s.w)), None))
         self.nsph = len(wl.spheres)
         self.nbub = len(wl.bubbles)
+        self.steps_done = 0
 
     def _stream(self) -> int:
         return self._torch.cuda.current_stream(self.device).cuda_stream
@@ -145,6 +146,7 @@ class Sim:
     def step(self, n: int = 1):
         self._bind_stream()
         _check("lbm_step", load().lbm_step(self.ctx, int(n)))
+        self.steps_done += int(n)
 
     def forces(self):
         """(F [n][3], T [n][3]) FP64 momentum-exchange force and torque of the last step"""

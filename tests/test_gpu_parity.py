@@ -2,7 +2,8 @@
 
 Tolerances: after 200 steps of the 32^3 bubble/sphere column, max |d rho| <= 1e-5,
 max |d u| <= 1e-6, |d phi| <= 1e-5, cell types identical except at cells the oracle logged
-within 1e-4 of a conversion threshold (rho/u/phi then compared away from those cells), total
+within 1e-4 of a conversion threshold and their D3Q19 neighbours (the cells such a conversion
+converts with it; rho/u/phi then compared away from every mismatch), total
 mass drift <= 1e-6 relative per 1000 FP32 steps.  One-step parity from a state copied out of
 the GPU isolates each step with tight bounds.  FP16 / BF16 deviation storage is reported
 against the same oracle with looser, stated bounds.
@@ -96,7 +97,7 @@ def _one_step_check(lbm, wl, pre_steps, f_tol, phi_tol):
     st1 = U.gpu_state(sim)
     flags_o = o.flag
     mism = st1["flags"] != flags_o
-    near = o.near > 0
+    near = U.dilate(o.near > 0, 1)
     assert not np.any(mism & ~near), "type mismatch away from a threshold at %s" % (np.argwhere(mism & ~near)[:5],)
     keep = ~U.dilate(mism, 2)
     act = ((st1["flags"] & 3) != 0) & ((flags_o & 3) != 0) & keep
@@ -132,10 +133,12 @@ def test_one_step_moving_sphere_near_surface(lbm):
 
 
 def _r27_compare(o, st):
-    """R27: mismatching types only at cells the oracle logged near a threshold; rho/u/phi
-    compared away (distance > 2) from them"""
+    """mismatching types only at cells the oracle logged near a threshold or at their D3Q19
+    neighbours (which a conversion there converts too); rho/u/phi compared away (distance > 2)
+    from every mismatch"""
     mism = st["flags"] != o.flag
-    assert not np.any(mism & ~(o.near > 0)), np.argwhere(mism & ~(o.near > 0))[:5]
+    near = U.dilate(o.near > 0, 1)
+    assert not np.any(mism & ~near), np.argwhere(mism & ~near)[:5]
     keep = ~U.dilate(mism, 2)
     drho, du, n = U.compare_fields(o, st, keep)
     iface = (st["flags"] == oracle.IFACE) & (o.flag == oracle.IFACE) & keep
