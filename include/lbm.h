@@ -145,8 +145,9 @@ int lbm_bubbles(lbm_ctx* ctx, double* V0, double* V, double* rho_g, int n);
  * obstacle), flags[N] (LBM_CELL_*).  Asynchronous. */
 int lbm_fields(lbm_ctx* ctx, float* rho, float* u, float* phi, uint8_t* flags);
 
-/* Full state into caller device buffers (any may be NULL): f[19][N] post-collision PDFs in
- * FP32 (full values whatever the storage; undefined in inactive cells), flags[N]
+/* Full state into caller device buffers (any may be NULL): f[19][N] post-collision PDFs as
+ * FP32 deviations f*_q - w_q from the lattice weights (w_0 = 1/3, w_1..6 = 1/18,
+ * w_7..18 = 1/36; whatever the storage; undefined in inactive cells), flags[N]
  * (LBM_CELL_*), mass[N] (interface mass), phi[N], owner[N] (bubble id of gas / interface
  * cells, sphere id of obstacle cells, -1 otherwise), kappa[N] (curvature; 0 if sigma = 0).
  * D3Q19 order: q = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (+1,+1,0),(-1,-1,0),(+1,-1,0),

@@ -69,7 +69,7 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, acc, sc, wl[4], bin_cnt, bin_ids, geo, total;
+    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, acc, sc, wl[4], wl_slow, bin_cnt, bin_ids, npairs, pairs, geo, total;
     size_t N, wl_cap, nbins_max;
 };
 
@@ -96,8 +96,11 @@ Layout layout_of(const lbm_params* p) {
     L.acc = take(sizeof(SphereAcc) * (size_t)p->max_spheres);
     L.sc = take(sizeof(Scalars));
     for (int k = 0; k < 4; k++) L.wl[k] = take(4 * L.wl_cap);
+    L.wl_slow = take(4 * L.N);
     L.bin_cnt = take(4 * L.nbins_max);
     L.bin_ids = take(4 * L.nbins_max * kBinCap);
+    L.npairs = take(4 * (size_t)p->max_spheres);
+    L.pairs = take(4 * (size_t)p->max_spheres * kPairCap);
     L.geo = take(sizeof(double) * 4 * (size_t)p->max_bubbles);
     L.total = o;
     return L;
@@ -164,7 +167,7 @@ int enqueue_step_timed(lbm_ctx* c, int cur, cudaStream_t s) {
     return cuda_fail(cudaGetLastError());
 }
 
-int count_per_step(const Dev& d) { return 1 + 6 + 1 + (d.kappa ? 1 : 0) + spheres_launches(d) + 1; }
+int count_per_step(const Dev& d) { return 2 + 6 + 1 + (d.kappa ? 1 : 0) + spheres_launches(d) + 1; }
 
 int first_step(lbm_ctx* c) {
     const lbm_params* p = &c->p;
@@ -209,6 +212,7 @@ int first_step(lbm_ctx* c) {
     d.wl_newif = (uint32_t*)(a + L.wl[1]);
     d.wl_fromliq = (uint32_t*)(a + L.wl[2]);
     d.wl_touch = (uint32_t*)(a + L.wl[3]);
+    d.wl_slow = (uint32_t*)(a + L.wl_slow);
     double rmax = 1.0;
     for (const Sphere& s : c->sph_init) rmax = std::fmax(rmax, s.R);
     d.bin_w = (int)std::ceil(2.0 * rmax + 2.0);
@@ -219,6 +223,8 @@ int first_step(lbm_ctx* c) {
     d.bin_cap = kBinCap;
     d.bin_cnt = (uint32_t*)(a + L.bin_cnt);
     d.bin_ids = (uint32_t*)(a + L.bin_ids);
+    d.npairs = (uint32_t*)(a + L.npairs);
+    d.pairs = (uint32_t*)(a + L.pairs);
     c->geo_dev = (double*)(a + L.geo);
 
     cudaStream_t s = c->stream;

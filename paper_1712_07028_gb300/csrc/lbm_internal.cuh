@@ -99,11 +99,12 @@ struct Scalars {
     uint32_t status;      // LBM_S_* bits
     uint32_t n_conv, n_newif, n_fromliq, n_touch, n_uncov;
     uint32_t bin_overflow;
-    uint32_t pad1[7];
+    uint32_t n_slow;      // active cells the bulk sweep left to the boundary sweep
+    uint32_t pad1[6];
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
-enum : uint32_t { S_UNSTABLE = 1, S_OVERFLOW = 2, S_BUBBLE_GONE = 4, S_BIN_OVERFLOW = 8, S_BAD_OWNER = 16 };
+enum : uint32_t { S_UNSTABLE = 1, S_OVERFLOW = 2, S_BUBBLE_GONE = 4, S_BIN_OVERFLOW = 8, S_BAD_OWNER = 16, S_FAST_SPHERE = 32 };
 
 // all device pointers of one simulation; passed by value to every kernel
 struct Dev {
@@ -138,11 +139,15 @@ struct Dev {
     uint32_t* wl_newif;
     uint32_t* wl_fromliq;
     uint32_t* wl_touch;
+    uint32_t* wl_slow;        // [N] per-step list of active cells for the boundary sweep
     // uniform bins of sphere ids for the neighbour searches
     int bin_w, nbx, nby, nbz, bin_cap;
     uint32_t* bin_cnt;        // [nbins]
     uint32_t* bin_ids;        // [nbins][bin_cap]
+    uint32_t* npairs;         // [max_sph] partners within lubrication reach this step
+    uint32_t* pairs;          // [max_sph][kPairCap]
 };
+constexpr int kPairCap = 32;
 
 __device__ __forceinline__ size_t cell_index(const Dev& d, int x, int y, int z) {
     return (size_t)x + (size_t)d.nx * ((size_t)y + (size_t)d.ny * (size_t)z);
@@ -163,6 +168,23 @@ __device__ __forceinline__ bool nbr(const Dev& d, int x, int y, int z, int dx, i
     return true;
 }
 
+// BULK: a liquid cell each of whose 18 neighbours is liquid or interface or lies beyond a
+// wall; the bulk sweep streams it without looking at its neighbours
+__device__ __forceinline__ bool bulk_of(const Dev& d, size_t i) {
+    if ((d.flags[i] & F_TYPE) != F_LIQ) return false;
+    int x, y, z;
+    cell_xyz(d, i, x, y, z);
+    for (int q = 1; q < kQ; q++) {
+        size_t j;
+        if (nbr(d, x, y, z, cx(q), cy(q), cz(q), j) && !(d.flags[j] & F_ACTIVE)) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void set_bulk(const Dev& d, size_t i) {
+    const uint8_t t = d.flags[i] & F_TYPE;
+    d.flags[i] = (uint8_t)(t | (bulk_of(d, i) ? F_BULK : 0));
+}
+
 // byte-wise atomic OR / AND on the mark array (4-byte aligned base); returns the old byte
 __device__ __forceinline__ uint8_t mark_or(uint8_t* base, size_t i, uint8_t bits) {
     uint32_t* w = reinterpret_cast<uint32_t*>(base + (i & ~(size_t)3));
@@ -176,6 +198,31 @@ __device__ __forceinline__ uint8_t mark_and(uint8_t* base, size_t i, uint8_t bit
     const uint32_t old = atomicAnd(w, ~((uint32_t)bits << sh));
     return (uint8_t)(old >> sh);
 }
+
+// full-warp reductions (every lane gets the result)
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ uint32_t warp_min(uint32_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+// global warp index and warp count of a 1-D launch
+__device__ __forceinline__ uint32_t warp_id() { return (blockIdx.x * blockDim.x + threadIdx.x) >> 5; }
+__device__ __forceinline__ uint32_t warp_count() { return (gridDim.x * blockDim.x) >> 5; }
 
 // append to a worklist with warp aggregation; false if the list is full
 __device__ __forceinline__ bool wl_push(uint32_t* list, uint32_t* count, uint32_t cap, uint32_t v, uint32_t* status) {

@@ -77,106 +77,162 @@ __device__ __forceinline__ void for_partners(const Dev& d, int P, const double* 
 // Links from an obstacle node x of sphere Q into an obstacle node of sphere P: the node
 // inside Q carries the equilibrium e_q(1, u_Q(x)) of Q's surface velocity (Sec. 2.3, end of
 // the momentum-exchange paragraph), reflected by Eq. bbrule with rho_w = 1 at P's surface.
-// Each thread adds only to its own sphere.
+// One block per sphere P; its threads share the cells of each close partner's box, and only
+// cells that can be such a node (covered by Q, within R_P + 1.5 of P) are read.
 __global__ void sph_contact_kernel(const Dev d) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    const int P = blockIdx.x;
     if (P >= d.nsph) return;
     Sphere& s = d.sph[P];
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
     const int L[3] = {d.nx, d.ny, d.nz};
-    if (!finite3(s.x) || !(s.R > 0.0 && s.R < 64.0)) return;
-    for_partners(d, P, s.x, [&](uint32_t Q) {
-        const Sphere& o = d.sph[Q];
-        if (!finite3(o.x) || !(o.R > 0.0 && o.R < 64.0)) return;
-        double dq[3];
-        for (int k = 0; k < 3; k++) dq[k] = min_image(d, k, o.x[k], s.x[k]);
-        const double dist2 = dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2];
-        const double reach = s.R + o.R + 2.0;
-        if (dist2 > reach * reach) return;
-        // cells of Q's box (coordinates unwrapped around P), wrapped when read
-        int lo[3], hi[3];
-        for (int k = 0; k < 3; k++) {
-            const double c = s.x[k] + dq[k];
-            lo[k] = (int)floor(c - o.R);
-            hi[k] = (int)ceil(c + o.R);
-        }
-        for (int zz = lo[2]; zz <= hi[2]; zz++)
-            for (int yy = lo[1]; yy <= hi[1]; yy++)
-                for (int xx = lo[0]; xx <= hi[0]; xx++) {
-                    int w[3] = {xx, yy, zz};
-                    bool ok = true;
-                    for (int k = 0; k < 3; k++) {
-                        if (w[k] < 0 || w[k] >= L[k]) {
-                            if (!d.bc[k]) { ok = false; break; }
-                            w[k] = ((w[k] % L[k]) + L[k]) % L[k];
-                        }
-                    }
-                    if (!ok) continue;
-                    const size_t xi = cell_index(d, w[0], w[1], w[2]);
-                    if (!(d.flags[xi] & F_OBS) || d.owner[xi] != Q) continue;
-                    // surface velocity of Q at x, and x relative to P (minimum image)
-                    double rq[3], rp[3];
-                    for (int k = 0; k < 3; k++) {
-                        rq[k] = min_image(d, k, (double)w[k], o.x[k]);
-                        rp[k] = min_image(d, k, (double)w[k], s.x[k]);
-                    }
-                    const double uq[3] = {o.u[0] + o.w[1] * rq[2] - o.w[2] * rq[1],
-                                          o.u[1] + o.w[2] * rq[0] - o.w[0] * rq[2],
-                                          o.u[2] + o.w[0] * rq[1] - o.w[1] * rq[0]};
-                    const double uu = uq[0] * uq[0] + uq[1] * uq[1] + uq[2] * uq[2];
-                    for (int q = 1; q < kQ; q++) {
-                        size_t yi;
-                        if (!nbr(d, w[0], w[1], w[2], cx(q), cy(q), cz(q), yi)) continue;
-                        if (!(d.flags[yi] & F_OBS) || d.owner[yi] != (uint32_t)P) continue;
-                        const double c3[3] = {(double)cx(q), (double)cy(q), (double)cz(q)};
-                        const double wq = (double)w72(q) / 72.0;
-                        const double cu = c3[0] * uq[0] + c3[1] * uq[1] + c3[2] * uq[2];
-                        const double fstar = wq * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-                        const double rw[3] = {rp[0] + 0.5 * c3[0], rp[1] + 0.5 * c3[1], rp[2] + 0.5 * c3[2]};
-                        const double uw[3] = {s.u[0] + s.w[1] * rw[2] - s.w[2] * rw[1],
-                                              s.u[1] + s.w[2] * rw[0] - s.w[0] * rw[2],
-                                              s.u[2] + s.w[0] * rw[1] - s.w[1] * rw[0]};
-                        const double back = fstar - 6.0 * wq * (c3[0] * uw[0] + c3[1] * uw[1] + c3[2] * uw[2]);
-                        const double a = fstar + back;
-                        const double dj[3] = {c3[0] * a, c3[1] * a, c3[2] * a};
-                        F[0] += dj[0]; F[1] += dj[1]; F[2] += dj[2];
-                        T[0] += rp[1] * dj[2] - rp[2] * dj[1];
-                        T[1] += rp[2] * dj[0] - rp[0] * dj[2];
-                        T[2] += rp[0] * dj[1] - rp[1] * dj[0];
+    if (finite3(s.x) && s.R > 0.0 && s.R < 64.0) {
+        for_partners(d, P, s.x, [&](uint32_t Q) {
+            const Sphere& o = d.sph[Q];
+            if (!finite3(o.x) || !(o.R > 0.0 && o.R < 64.0)) return;
+            double cq[3];   // Q's centre, unwrapped next to P
+            for (int k = 0; k < 3; k++) cq[k] = s.x[k] + min_image(d, k, o.x[k], s.x[k]);
+            const double dd2 = (cq[0] - s.x[0]) * (cq[0] - s.x[0]) + (cq[1] - s.x[1]) * (cq[1] - s.x[1]) + (cq[2] - s.x[2]) * (cq[2] - s.x[2]);
+            const double reach = s.R + o.R + 2.0;
+            if (dd2 > reach * reach) return;
+            int lo[3], ext[3];
+            for (int k = 0; k < 3; k++) {
+                lo[k] = (int)floor(cq[k] - o.R);
+                ext[k] = (int)ceil(cq[k] + o.R) - lo[k] + 1;
+            }
+            const int total = ext[0] * ext[1] * ext[2];
+            const double RQ2 = o.R * o.R, RP2 = (s.R + 1.5) * (s.R + 1.5);
+            for (int e = threadIdx.x; e < total; e += blockDim.x) {
+                int w[3] = {lo[0] + e % ext[0], lo[1] + (e / ext[0]) % ext[1], lo[2] + e / (ext[0] * ext[1])};
+                double aq = 0, ap = 0;
+                for (int k = 0; k < 3; k++) {
+                    aq += (w[k] - cq[k]) * (w[k] - cq[k]);
+                    ap += (w[k] - s.x[k]) * (w[k] - s.x[k]);
+                }
+                if (aq > RQ2 || ap > RP2) continue;
+                bool ok = true;
+                for (int k = 0; k < 3; k++) {
+                    if (w[k] < 0 || w[k] >= L[k]) {
+                        if (!d.bc[k]) { ok = false; break; }
+                        w[k] = ((w[k] % L[k]) + L[k]) % L[k];
                     }
                 }
-    });
-    for (int k = 0; k < 3; k++) { s.F[k] += F[k]; s.T[k] += T[k]; }
+                if (!ok) continue;
+                const size_t xi = cell_index(d, w[0], w[1], w[2]);
+                if (!(d.flags[xi] & F_OBS) || d.owner[xi] != Q) continue;
+                // surface velocity of Q at x, and x relative to P (minimum image)
+                double rq[3], rp[3];
+                for (int k = 0; k < 3; k++) {
+                    rq[k] = min_image(d, k, (double)w[k], o.x[k]);
+                    rp[k] = min_image(d, k, (double)w[k], s.x[k]);
+                }
+                const double uq[3] = {o.u[0] + o.w[1] * rq[2] - o.w[2] * rq[1],
+                                      o.u[1] + o.w[2] * rq[0] - o.w[0] * rq[2],
+                                      o.u[2] + o.w[0] * rq[1] - o.w[1] * rq[0]};
+                const double uu = uq[0] * uq[0] + uq[1] * uq[1] + uq[2] * uq[2];
+                for (int q = 1; q < kQ; q++) {
+                    size_t yi;
+                    if (!nbr(d, w[0], w[1], w[2], cx(q), cy(q), cz(q), yi)) continue;
+                    if (!(d.flags[yi] & F_OBS) || d.owner[yi] != (uint32_t)P) continue;
+                    const double c3[3] = {(double)cx(q), (double)cy(q), (double)cz(q)};
+                    const double wq = (double)w72(q) / 72.0;
+                    const double cu = c3[0] * uq[0] + c3[1] * uq[1] + c3[2] * uq[2];
+                    const double fstar = wq * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+                    const double rw[3] = {rp[0] + 0.5 * c3[0], rp[1] + 0.5 * c3[1], rp[2] + 0.5 * c3[2]};
+                    const double uw[3] = {s.u[0] + s.w[1] * rw[2] - s.w[2] * rw[1],
+                                          s.u[1] + s.w[2] * rw[0] - s.w[0] * rw[2],
+                                          s.u[2] + s.w[0] * rw[1] - s.w[1] * rw[0]};
+                    const double back = fstar - 6.0 * wq * (c3[0] * uw[0] + c3[1] * uw[1] + c3[2] * uw[2]);
+                    const double am = fstar + back;
+                    const double dj[3] = {c3[0] * am, c3[1] * am, c3[2] * am};
+                    F[0] += dj[0]; F[1] += dj[1]; F[2] += dj[2];
+                    T[0] += rp[1] * dj[2] - rp[2] * dj[1];
+                    T[1] += rp[2] * dj[0] - rp[0] * dj[2];
+                    T[2] += rp[0] * dj[1] - rp[1] * dj[0];
+                }
+            }
+        });
+    }
+    __shared__ double red[6][32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
+    for (int c = 0; c < 6; c++) {
+        v[c] = warp_sum(v[c]);
+        if (lane == 0) red[c][wid] = v[c];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 6; c++) {
+            double t = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[c][k];
+            if (c < 3) s.F[c] += t;
+            else s.T[c - 3] += t;
+        }
+    }
 }
 
-// one Newton-Euler sub-step for every sphere (Sec. 2.3): lubrication (Eq. lubrication, gap
-// < 2/3 floored at 0.2 * 2/3, mu = (tau - 1/2)/3) from the sub-step's start state src,
-// then u += dt F_tot/m, w += dt T/I, x += dt u into dst
-__global__ void sph_substep_kernel(const Dev d, const Sphere* src, Sphere* dst, const double dt) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= d.nsph) return;
+// partners of sphere P within lubrication reach this step (centre distance below
+// R_P + R_Q + 2/3 + 1: the spheres move less than half a cell per step), one warp per sphere
+// with its lanes over the 27 neighbouring bins
+__global__ void sph_pairs_kernel(const Dev d) {
+    const uint32_t P = warp_id();
+    const int lane = threadIdx.x & 31;
+    if (P >= (uint32_t)d.nsph) return;
+    const Sphere& s = d.sph[P];
+    if (lane == 0) d.npairs[P] = 0;
+    __syncwarp();
+    int sx[3], sy[3], sz[3];
+    const int nx_ = bin_span(d, 0, bin_coord(d, 0, s.x[0]), sx);
+    const int ny_ = bin_span(d, 1, bin_coord(d, 1, s.x[1]), sy);
+    const int nz_ = bin_span(d, 2, bin_coord(d, 2, s.x[2]), sz);
+    if (lane < nx_ * ny_ * nz_ && finite3(s.x)) {
+        const size_t bi = bin_index(d, sx[lane % nx_], sy[(lane / nx_) % ny_], sz[lane / (nx_ * ny_)]);
+        uint32_t cnt = d.bin_cnt[bi];
+        if (cnt > (uint32_t)d.bin_cap) cnt = (uint32_t)d.bin_cap;
+        for (uint32_t e = 0; e < cnt; e++) {
+            const uint32_t Q = d.bin_ids[bi * d.bin_cap + e];
+            if (Q == P) continue;
+            const Sphere& o = d.sph[Q];
+            double dd2 = 0.0;
+            for (int k = 0; k < 3; k++) {
+                const double v = min_image(d, k, o.x[k], s.x[k]);
+                dd2 += v * v;
+            }
+            const double reach = s.R + o.R + 2.0 / 3.0 + 1.0;
+            if (!(dd2 < reach * reach)) continue;
+            const uint32_t slot = atomicAdd(&d.npairs[P], 1u);
+            if (slot < (uint32_t)kPairCap) d.pairs[(size_t)P * kPairCap + slot] = Q;
+            else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
+        }
+    }
+}
+
+// one Newton-Euler sub-step of sphere P (Sec. 2.3): lubrication (Eq. lubrication, gap
+// < 2/3 floored at 0.2 * 2/3, mu = (tau - 1/2)/3) from the sub-step's start state src, then
+// u += dt F_tot/m, w += dt T/I, x += dt u into dst.  The hydrodynamic force and torque are
+// the mean of this step's and the previous step's momentum exchange (Ladd 1994), which keeps
+// light spheres from a two-step oscillation.
+__device__ void substep_one(const Dev& d, const Sphere* src, Sphere* dst, const double dt, const int P) {
     const Sphere& s = src[P];
     const double dc = 2.0 / 3.0, mu = ((double)d.tau - 0.5) / 3.0;
     double Fl[3] = {0, 0, 0};
-    for_partners(d, P, s.x0, [&](uint32_t Q) {
-        const Sphere& o = src[Q];
+    const uint32_t np = min(d.npairs[P], (uint32_t)kPairCap);
+    for (uint32_t k = 0; k < np; k++) {
+        const Sphere& o = src[d.pairs[(size_t)P * kPairCap + k]];
         double dd[3];
-        for (int k = 0; k < 3; k++) dd[k] = min_image(d, k, o.x[k], s.x[k]);   // x_12 = x_Q - x_P
+        for (int c = 0; c < 3; c++) dd[c] = min_image(d, c, o.x[c], s.x[c]);   // x_12 = x_Q - x_P
         const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
         double h = dist - s.R - o.R;
-        if (!(h < dc) || dist <= 0.0) return;
+        if (!(h < dc) || dist <= 0.0) continue;
         if (h < 0.2 * dc) h = 0.2 * dc;
         const double rr = s.R * o.R, rs = s.R + o.R;
         const double n[3] = {dd[0] / dist, dd[1] / dist, dd[2] / dist};
         const double vn = n[0] * (s.u[0] - o.u[0]) + n[1] * (s.u[1] - o.u[1]) + n[2] * (s.u[2] - o.u[2]);
         const double mag = -6.0 * kPi * mu * rr * rr / (rs * rs) * (1.0 / h - 1.0 / dc) * vn;
         Fl[0] += mag * n[0]; Fl[1] += mag * n[1]; Fl[2] += mag * n[2];
-    });
+    }
     Sphere o = s;
     const double m = s.rho * 4.0 / 3.0 * kPi * s.R * s.R * s.R, I = 0.4 * m * s.R * s.R;
     const int L[3] = {d.nx, d.ny, d.nz};
-    // the hydrodynamic force and torque are the mean of this step's and the previous step's
-    // momentum exchange (Ladd 1994), which keeps light spheres from a two-step oscillation
     const bool hasp = s.hasp != 0.0;
     for (int k = 0; k < 3; k++) {
         const double Fh = hasp ? 0.5 * (s.F[k] + s.Fp[k]) : s.F[k];
@@ -190,6 +246,23 @@ __global__ void sph_substep_kernel(const Dev d, const Sphere* src, Sphere* dst, 
         if (d.bc[k]) o.x[k] = wrap_pos(o.x[k], L[k]);
     }
     dst[P] = o;
+}
+
+__global__ void sph_substep_kernel(const Dev d, const Sphere* src, Sphere* dst, const double dt) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P < d.nsph) substep_one(d, src, dst, dt, P);
+}
+
+// all sub-steps in one block (up to 1024 spheres): the block's barrier separates them
+__global__ void sph_substeps_fused_kernel(const Dev d, const double dt) {
+    for (int k = 0; k < d.n_sub; k++) {
+        const Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
+        Sphere* dst = (k & 1) ? d.sph : d.sph_tmp;
+        for (int P = threadIdx.x; P < d.nsph; P += blockDim.x) substep_one(d, src, dst, dt, P);
+        __syncthreads();
+    }
+    if (d.n_sub & 1)
+        for (int P = threadIdx.x; P < d.nsph; P += blockDim.x) d.sph[P] = d.sph_tmp[P];
 }
 
 __global__ void sph_prescribed_kernel(const Dev d) {
@@ -262,26 +335,42 @@ __global__ void cover_touch_kernel(const Dev d) {
 }
 
 // touched cells: the lowest id of the spheres covering them now decides; obstacle cells no
-// sphere covers any more are uncovered; newly covered cells lose their fluid mass
+// sphere covers any more are uncovered; newly covered cells lose their fluid mass.  One warp
+// per cell, its lanes over the 27 neighbouring bins.
 template <int S>
 __global__ void cover_apply_kernel(const Dev d, const int nxt) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(d.f[nxt]);
     const uint32_t n = min(*(volatile uint32_t*)&d.sc->n_touch, (uint32_t)d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t i = d.wl_touch[k];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+        const size_t i = d.wl_touch[e];
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        const uint32_t own = covering_sphere(d, x, y, z);
+        int sx[3], sy[3], sz[3];
+        const int nx_ = bin_span(d, 0, bin_coord(d, 0, (double)x), sx);
+        const int ny_ = bin_span(d, 1, bin_coord(d, 1, (double)y), sy);
+        const int nz_ = bin_span(d, 2, bin_coord(d, 2, (double)z), sz);
+        uint32_t best = kNone;
+        if (lane < nx_ * ny_ * nz_) {
+            const size_t bi = bin_index(d, sx[lane % nx_], sy[(lane / nx_) % ny_], sz[lane / (nx_ * ny_)]);
+            uint32_t cnt = d.bin_cnt[bi];
+            if (cnt > (uint32_t)d.bin_cap) cnt = (uint32_t)d.bin_cap;
+            for (uint32_t k = 0; k < cnt; k++) {
+                const uint32_t P = d.bin_ids[bi * d.bin_cap + k];
+                if (P < best && sphere_covers(d, d.sph[P], x, y, z)) best = P;
+            }
+        }
+        const uint32_t own = warp_min(best);
         const uint8_t t = d.flags[i] & F_TYPE;
+        const float rl = (t & F_LIQ) ? warp_sum(lane < kQ ? Store<S>::get_nc(f, (size_t)lane * d.N + i) : 0.f) : 0.f;
+        if (lane != 0) continue;
         if (t & F_OBS) {
             if (own == kNone) mark_or(d.mark, i, K_UNCOV);
             else d.owner[i] = own;
         } else if (own != kNone) {
             if (t & F_LIQ) {
-                float dr = 0.f;
-                for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + i);
-                atomicAdd(&d.sc->S_cover, (double)(1.f + dr));
+                atomicAdd(&d.sc->S_cover, (double)(1.f + rl));
             } else if (t & F_IF) {
                 atomicAdd(&d.sc->S_cover, (double)d.mass[i]);
                 atomicSub(&d.sc->n_iface_acc, 1u);
@@ -302,46 +391,57 @@ __global__ void cover_refill_kernel(const Dev d, const int nxt) {
     T* f = static_cast<T*>(d.f[nxt]);
     float* phi = d.phi[nxt];
     const uint32_t n = min(*(volatile uint32_t*)&d.sc->n_touch, (uint32_t)d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t i = d.wl_touch[k];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+        const size_t i = d.wl_touch[e];
         if (!(d.mark[i] & K_UNCOV)) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        int ngas = 0, nfl = 0;
-        uint32_t gown = kNone;
-        float rs = 0.f, ps = 0.f;
-        for (int q = 1; q < kQ; q++) {
-            size_t j;
-            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
-            if (d.mark[j] & K_UNCOV) continue;
+        int isgas = 0, isfl = 0;
+        float r = 0.f, ph = 0.f;
+        uint32_t myown = kNone;
+        size_t j;
+        if (lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j) && !(d.mark[j] & K_UNCOV)) {
             const uint8_t t = d.flags[j] & F_TYPE;
-            if (t & F_OBS) continue;
             if (t & F_GAS) {
-                if (gown == kNone) gown = d.owner[j];
-                ngas++;
-            } else {
-                float r, u[3];
+                isgas = 1;
+                myown = d.owner[j];
+            } else if (t & F_ACTIVE) {
+                float u[3];
                 post_moments<S>(d, f, j, r, u);
-                rs += r;
-                ps += (t & F_IF) ? phi[j] : 1.f;
-                nfl++;
+                ph = (t & F_IF) ? phi[j] : 1.f;
+                isfl = 1;
             }
         }
+        const unsigned gmask = __ballot_sync(0xffffffffu, isgas);
+        const int ngas = __popc(gmask), nfl = warp_sum(isfl);
+        float rs = 0.f, ps = 0.f;
+        for (int q = 1; q < kQ; q++) {   // in q order, as a serial sum would take them
+            rs += __shfl_sync(0xffffffffu, r, q);
+            ps += __shfl_sync(0xffffffffu, ph, q);
+        }
+        // the bubble of the first gas neighbour in q order
+        const uint32_t gown = __shfl_sync(0xffffffffu, myown, gmask ? __ffs(gmask) - 1 : 0);
         const uint32_t P = d.owner[i];
         const Sphere& sp = d.sph[P < (uint32_t)d.nsph ? P : 0];
         double r3[3];
-        for (int k3 = 0; k3 < 3; k3++) r3[k3] = min_image(d, k3, (double)(k3 == 0 ? x : (k3 == 1 ? y : z)), sp.x[k3]);
+        const int c3[3] = {x, y, z};
+        for (int k = 0; k < 3; k++) r3[k] = min_image(d, k, (double)c3[k], sp.x[k]);
         const float uf[3] = {(float)(sp.u[0] + sp.w[1] * r3[2] - sp.w[2] * r3[1]),
                              (float)(sp.u[1] + sp.w[2] * r3[0] - sp.w[0] * r3[2]),
                              (float)(sp.u[2] + sp.w[0] * r3[1] - sp.w[1] * r3[0])};
         if (nfl == 0 && ngas > 0) {
-            d.flags[i] = F_GAS;
-            d.owner[i] = gown;
-            d.mass[i] = 0.f;
-            phi[i] = 0.f;
+            if (lane == 0) {
+                d.flags[i] = F_GAS;
+                d.owner[i] = gown;
+                d.mass[i] = 0.f;
+                phi[i] = 0.f;
+            }
             continue;
         }
         const float rb = nfl ? rs / (float)nfl : 1.f;
+        if (lane < kQ) Store<S>::put(f, (size_t)lane * d.N + i, equilibrium_dev(lane, rb, uf));
+        if (lane != 0) continue;
         if (ngas > 0) {
             const float pb = ps / (float)nfl;
             d.flags[i] = F_IF;
@@ -357,45 +457,38 @@ __global__ void cover_refill_kernel(const Dev d, const int nxt) {
             d.mass[i] = rb;
             atomicAdd(&d.sc->S_uncover, (double)rb);
         }
-        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, equilibrium_dev(q, rb, uf));
     }
 }
 
-__device__ __forceinline__ void set_bulk_p(const Dev& d, size_t i) {
-    uint8_t t = d.flags[i] & F_TYPE;
-    bool bulk = t == F_LIQ;
-    if (bulk) {
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        for (int q = 1; q < kQ && bulk; q++) {
-            size_t j;
-            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j) || !(d.flags[j] & F_ACTIVE)) bulk = false;
-        }
-    }
-    d.flags[i] = (uint8_t)(t | (bulk ? F_BULK : 0));
-}
-
+// BULK bits of every touched cell and its neighbours; marks cleared
 __global__ void cover_finish_kernel(const Dev d) {
     const uint32_t n = min(*(volatile uint32_t*)&d.sc->n_touch, (uint32_t)d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t i = d.wl_touch[k];
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        set_bulk_p(d, i);
-        for (int q = 1; q < kQ; q++) {
-            size_t j;
-            if (nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) set_bulk_p(d, j);
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+        const size_t i = d.wl_touch[e];
+        if (lane >= kQ) continue;
+        size_t j = i;
+        if (lane > 0) {
+            int x, y, z;
+            cell_xyz(d, i, x, y, z);
+            if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
         }
-        d.mark[i] = 0;
+        set_bulk(d, j);
     }
+}
+
+// marks of the touched cells cleared once every BULK bit is final
+__global__ void cover_clear_kernel(const Dev d) {
+    const uint32_t n = min(*(volatile uint32_t*)&d.sc->n_touch, (uint32_t)d.wl_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) d.mark[d.wl_touch[k]] = 0;
 }
 
 int spheres_launches(const Dev& d) {
     if (d.nsph == 0) return 0;
-    int n = 2;  // prepare, contact
-    if (d.sphere_mode == LBM_SPHERES_FREE) n += d.n_sub + (d.n_sub & 1);
+    int n = 3;  // prepare, contact, pairs
+    if (d.sphere_mode == LBM_SPHERES_FREE) n += d.nsph <= 1024 ? 1 : d.n_sub + (d.n_sub & 1);
     else if (d.sphere_mode == LBM_SPHERES_PRESCRIBED) n += 1;
-    if (d.sphere_mode != LBM_SPHERES_FIXED) n += 4;
+    if (d.sphere_mode != LBM_SPHERES_FIXED) n += 5;
     return n;
 }
 
@@ -403,15 +496,20 @@ void launch_spheres(const Dev& d, int nxt, cudaStream_t st) {
     if (d.nsph == 0) return;
     const int tb = 128, nb = (d.nsph + tb - 1) / tb;
     sph_prepare_kernel<<<nb, tb, 0, st>>>(d);
-    sph_contact_kernel<<<nb, tb, 0, st>>>(d);
+    sph_contact_kernel<<<d.nsph, 128, 0, st>>>(d);
+    sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
     if (d.sphere_mode == LBM_SPHERES_FREE) {
         const double dt = 1.0 / d.n_sub;
-        for (int k = 0; k < d.n_sub; k++) {
-            const Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
-            Sphere* dst = (k & 1) ? d.sph : d.sph_tmp;
-            sph_substep_kernel<<<nb, tb, 0, st>>>(d, src, dst, dt);
+        if (d.nsph <= 1024) {
+            sph_substeps_fused_kernel<<<1, d.nsph <= 128 ? 128 : ((d.nsph + 31) / 32) * 32, 0, st>>>(d, dt);
+        } else {
+            for (int k = 0; k < d.n_sub; k++) {
+                const Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
+                Sphere* dst = (k & 1) ? d.sph : d.sph_tmp;
+                sph_substep_kernel<<<nb, tb, 0, st>>>(d, src, dst, dt);
+            }
+            if (d.n_sub & 1) sph_copy_kernel<<<nb, tb, 0, st>>>(d);
         }
-        if (d.n_sub & 1) sph_copy_kernel<<<nb, tb, 0, st>>>(d);
     } else if (d.sphere_mode == LBM_SPHERES_PRESCRIBED) {
         sph_prescribed_kernel<<<nb, tb, 0, st>>>(d);
     }
@@ -433,6 +531,7 @@ void launch_spheres(const Dev& d, int nxt, cudaStream_t st) {
             break;
     }
     cover_finish_kernel<<<lb, 128, 0, st>>>(d);
+    cover_clear_kernel<<<lb, 128, 0, st>>>(d);
 }
 
 }  // namespace lbm

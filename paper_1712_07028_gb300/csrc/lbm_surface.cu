@@ -63,24 +63,33 @@ __device__ float cell_rho(const Dev& d, const typename Store<S>::T* f, size_t i)
     return 1.f + dr;
 }
 
+// Every conversion kernel runs one warp per listed cell: lane q (1..18) handles the D3Q19
+// neighbour x + c_q, lane 0 the cell itself, and warp shuffles combine what they find.
+
+// density of cell i from grid f (deviations), summed over the warp's lanes 0..18
+template <int S>
+__device__ __forceinline__ float warp_cell_rho(const Dev& d, const typename Store<S>::T* f, size_t i, int lane) {
+    const float v = lane < kQ ? Store<S>::get_nc(f, (size_t)lane * d.N + i) : 0.f;
+    return 1.f + warp_sum(v);
+}
+
 // (ii) filled cells: gas neighbours become new interface cells; emptied neighbours stay
 __global__ void conv_filled_kernel(const Dev d) {
     const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t i = d.wl_conv[k];
-        if (!(d.mark[i] & K_FILLED)) continue;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+        const size_t i = d.wl_conv[e];
+        if (!(d.mark[i] & K_FILLED) || lane == 0 || lane >= kQ) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        for (int q = 1; q < kQ; q++) {
-            size_t j;
-            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
-            const uint8_t t = d.flags[j] & F_TYPE;
-            if (t & F_GAS) {
-                const uint8_t old = mark_or(d.mark, j, K_NEWIF);
-                if (!(old & K_NEWIF)) wl_push(d.wl_newif, &d.sc->n_newif, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
-            } else if (t & F_IF) {
-                mark_and(d.mark, j, K_EMPTIED);
-            }
+        size_t j;
+        if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
+        const uint8_t t = d.flags[j] & F_TYPE;
+        if (t & F_GAS) {
+            const uint8_t old = mark_or(d.mark, j, K_NEWIF);
+            if (!(old & K_NEWIF)) wl_push(d.wl_newif, &d.sc->n_newif, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
+        } else if (t & F_IF) {
+            mark_and(d.mark, j, K_EMPTIED);
         }
     }
 }
@@ -92,23 +101,23 @@ __global__ void conv_emptied_kernel(const Dev d, const int nxt) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(d.f[nxt]);
     const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t i = d.wl_conv[k];
-        if (!(d.mark[i] & K_EMPTIED)) continue;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+        const size_t i = d.wl_conv[e];
+        if (!(d.mark[i] & K_EMPTIED) || lane == 0 || lane >= kQ) continue;
         const uint32_t b = d.owner[i];
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        for (int q = 1; q < kQ; q++) {
-            size_t j;
-            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
-            if (!(d.flags[j] & F_LIQ)) continue;
-            const uint8_t old = mark_or(d.mark, j, K_FROMLIQ);
-            if (!(old & K_FROMLIQ)) {
-                d.mass[j] = cell_rho<S>(d, f, j);
-                wl_push(d.wl_fromliq, &d.sc->n_fromliq, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
-            }
-            atomicMin(&d.owner[j], b);
+        size_t j;
+        if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j) || !(d.flags[j] & F_LIQ)) continue;
+        const uint8_t old = mark_or(d.mark, j, K_FROMLIQ);
+        if (!(old & K_FROMLIQ)) {
+            float dr = 0.f;
+            for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + j);
+            d.mass[j] = 1.f + dr;
+            wl_push(d.wl_fromliq, &d.sc->n_fromliq, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
         }
+        atomicMin(&d.owner[j], b);
     }
 }
 
@@ -119,76 +128,85 @@ __global__ void conv_newif_kernel(const Dev d, const int nxt) {
     using T = typename Store<S>::T;
     T* f = static_cast<T*>(d.f[nxt]);
     const uint32_t n = list_len(&d.sc->n_newif, d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t i = d.wl_newif[k];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+        const size_t i = d.wl_newif[e];
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        float rs = 0.f, us[3] = {0.f, 0.f, 0.f};
-        int cnt = 0;
-        for (int q = 1; q < kQ; q++) {
-            size_t j;
-            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
-            if (!(d.flags[j] & F_ACTIVE) || (d.mark[j] & K_EMPTIED)) continue;
-            float r, u[3];
+        float r = 0.f, u[3] = {0.f, 0.f, 0.f};
+        int c = 0;
+        size_t j;
+        if (lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j) &&
+            (d.flags[j] & F_ACTIVE) && !(d.mark[j] & K_EMPTIED)) {
             post_moments<S>(d, f, j, r, u);
-            rs += r;
-            us[0] += u[0]; us[1] += u[1]; us[2] += u[2];
-            cnt++;
+            c = 1;
         }
+        const int cnt = warp_sum(c);
+        const float rs = warp_sum(r), ux = warp_sum(u[0]), uy = warp_sum(u[1]), uz = warp_sum(u[2]);
         const float rb = cnt ? rs / cnt : 1.f;
-        const float ub[3] = {cnt ? us[0] / cnt : 0.f, cnt ? us[1] / cnt : 0.f, cnt ? us[2] / cnt : 0.f};
-        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, equilibrium_dev(q, rb, ub));
-        d.mass[i] = 0.f;
+        const float ub[3] = {cnt ? ux / cnt : 0.f, cnt ? uy / cnt : 0.f, cnt ? uz / cnt : 0.f};
+        if (lane < kQ) Store<S>::put(f, (size_t)lane * d.N + i, equilibrium_dev(lane, rb, ub));
+        if (lane == 0) d.mass[i] = 0.f;
     }
 }
 
 // (v) excess mass of converting cells to the neighbours that will be interface cells,
 // weighted along the interface normal pointing into the gas (-grad phi): filled cells push
 // along it, emptied cells against it; uniform if all weights vanish; to the global pool if
-// no neighbour can take it
+// no neighbour can take it.  The Parker-Youngs gradient is taken over the 3x3x3 block, lane l
+// (0..26) holding the fill level of offset (l%3-1, l/3%3-1, l/9-1).
 template <int S>
 __global__ void conv_excess_kernel(const Dev d, const int nxt) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(d.f[nxt]);
     const float* phi = d.phi[nxt];
     const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t i = d.wl_conv[k];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+        const size_t i = d.wl_conv[e];
         const uint8_t mk = d.mark[i] & (K_FILLED | K_EMPTIED);
         if (!mk) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        float nv[3];
-        py_gradient(d, phi, x, y, z, nv);
-        const float ngx = -nv[0], ngy = -nv[1], ngz = -nv[2];
-        const float r = cell_rho<S>(d, f, i);
-        float mex;
-        if (mk & K_FILLED) { mex = d.mass[i] - r; d.mass[i] = r; }
-        else { mex = d.mass[i]; d.mass[i] = 0.f; }
-        float wr[kQ];
-        size_t rj[kQ];
+        // Parker-Youngs: central difference smoothed by [1,2,1] x [1,2,1] / 16 (into the liquid)
+        float gxl = 0.f, gyl = 0.f, gzl = 0.f;
+        if (lane < 27 && lane != 13) {
+            const int a = lane % 3 - 1, b = (lane / 3) % 3 - 1, c = lane / 9 - 1;
+            const float v = fill_seen(d, phi, x, y, z, a, b, c);
+            const float wa = a == 0 ? 2.f : 1.f, wb = b == 0 ? 2.f : 1.f, wc = c == 0 ? 2.f : 1.f;
+            gxl = a * wb * wc * v;
+            gyl = b * wa * wc * v;
+            gzl = c * wa * wb * v;
+        }
+        const float ngx = -warp_sum(gxl) / 32.f, ngy = -warp_sum(gyl) / 32.f, ngz = -warp_sum(gzl) / 32.f;
+        const float r = warp_cell_rho<S>(d, f, i, lane);
+        const float m0 = d.mass[i];
+        const float mex = (mk & K_FILLED) ? m0 - r : m0;
+        size_t j = 0;
+        bool rec = false;
+        float w = 0.f;
+        if (lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) {
+            const uint8_t mj = d.mark[j];
+            rec = ((d.flags[j] & F_IF) && !(mj & (K_FILLED | K_EMPTIED))) || (mj & (K_NEWIF | K_FROMLIQ));
+            if (rec) {
+                const float nc = ngx * cx(lane) + ngy * cy(lane) + ngz * cz(lane);
+                w = (mk & K_FILLED) ? fmaxf(nc, 0.f) : fmaxf(-nc, 0.f);
+            }
+        }
+        // the lanes' weights in q order, as a serial sum would take them
         float W = 0.f;
         int nr = 0;
         for (int q = 1; q < kQ; q++) {
-            size_t j;
-            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
-            const uint8_t mj = d.mark[j];
-            const bool rec = ((d.flags[j] & F_IF) && !(mj & (K_FILLED | K_EMPTIED))) || (mj & (K_NEWIF | K_FROMLIQ));
-            if (!rec) continue;
-            const float nc = ngx * cx(q) + ngy * cy(q) + ngz * cz(q);
-            const float w = (mk & K_FILLED) ? fmaxf(nc, 0.f) : fmaxf(-nc, 0.f);
-            rj[nr] = j;
-            wr[nr] = w;
-            W += w;
-            nr++;
+            W += __shfl_sync(0xffffffffu, w, q);
+            nr += __shfl_sync(0xffffffffu, (int)rec, q);
         }
-        if (nr == 0) {
-            atomicAdd(&d.sc->pool_acc, (double)mex);
-            continue;
+        if (lane == 0) {
+            d.mass[i] = (mk & K_FILLED) ? r : 0.f;
+            if (nr == 0) atomicAdd(&d.sc->pool_acc, (double)mex);
         }
-        for (int a = 0; a < nr; a++) {
-            atomicAdd(&d.mass[rj[a]], W > 0.f ? mex * (wr[a] / W) : mex / (float)nr);
-            mark_or(d.mark, rj[a], K_RECV);
+        if (rec) {
+            atomicAdd(&d.mass[j], W > 0.f ? mex * (w / W) : mex / (float)nr);
+            mark_or(d.mark, j, K_RECV);
         }
     }
 }
@@ -202,62 +220,54 @@ __global__ void conv_finalize_kernel(const Dev d, const int nxt) {
     const uint32_t n1 = list_len(&d.sc->n_conv, d.wl_cap);
     const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
     const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n2 + n3; k += gridDim.x * blockDim.x) {
-        if (k < n1) {
-            const size_t i = d.wl_conv[k];
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n1 + n2 + n3; e += warp_count()) {
+        if (e < n1) {
+            const size_t i = d.wl_conv[e];
             const uint8_t mk = d.mark[i];
-            if (mk & K_FILLED) { d.flags[i] = F_LIQ; d.owner[i] = kNone; }
-            else if (mk & K_EMPTIED) { d.flags[i] = F_GAS; }
+            if (lane == 0) {
+                if (mk & K_FILLED) { d.flags[i] = F_LIQ; d.owner[i] = kNone; }
+                else if (mk & K_EMPTIED) { d.flags[i] = F_GAS; }
+            }
+            if (lane == 0 || lane >= kQ) continue;
             int x, y, z;
             cell_xyz(d, i, x, y, z);
-            for (int q = 1; q < kQ; q++) {
-                size_t j;
-                if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
-                const uint8_t mj = d.mark[j];
-                if ((mj & K_RECV) && !(mj & (K_NEWIF | K_FROMLIQ))) phi[j] = d.mass[j] / cell_rho<S>(d, f, j);
+            size_t j;
+            if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
+            const uint8_t mj = d.mark[j];
+            if ((mj & K_RECV) && !(mj & (K_NEWIF | K_FROMLIQ))) {
+                float dr = 0.f;
+                for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + j);
+                phi[j] = d.mass[j] / (1.f + dr);
             }
         } else {
-            const size_t i = k < n1 + n2 ? d.wl_newif[k - n1] : d.wl_fromliq[k - n1 - n2];
-            d.flags[i] = F_IF;
-            phi[i] = d.mass[i] / cell_rho<S>(d, f, i);
+            const size_t i = e < n1 + n2 ? d.wl_newif[e - n1] : d.wl_fromliq[e - n1 - n2];
+            const float r = warp_cell_rho<S>(d, f, i, lane);
+            if (lane == 0) {
+                d.flags[i] = F_IF;
+                phi[i] = d.mass[i] / r;
+            }
         }
     }
 }
 
-__device__ __forceinline__ bool bulk_of(const Dev& d, size_t i) {
-    if ((d.flags[i] & F_TYPE) != F_LIQ) return false;
-    int x, y, z;
-    cell_xyz(d, i, x, y, z);
-    for (int q = 1; q < kQ; q++) {
-        size_t j;
-        if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) return false;
-        if (!(d.flags[j] & F_ACTIVE)) return false;
-    }
-    return true;
-}
-
-__device__ __forceinline__ void set_bulk(const Dev& d, size_t i) {
-    const uint8_t t = d.flags[i] & F_TYPE;
-    d.flags[i] = (uint8_t)(t | (bulk_of(d, i) ? F_BULK : 0));
-}
-
-// (vii) BULK bits around every cell whose type changed; marks cleared
+// (vii) BULK bits of every cell whose type changed and of its neighbours; marks cleared
 __global__ void conv_bulk_kernel(const Dev d) {
     const uint32_t n1 = list_len(&d.sc->n_conv, d.wl_cap);
     const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
     const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n2 + n3; k += gridDim.x * blockDim.x) {
-        const size_t i = k < n1 ? d.wl_conv[k] : (k < n1 + n2 ? d.wl_newif[k - n1] : d.wl_fromliq[k - n1 - n2]);
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        set_bulk(d, i);
-        d.mark[i] = 0;
-        for (int q = 1; q < kQ; q++) {
-            size_t j;
-            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
-            set_bulk(d, j);
-            d.mark[j] = 0;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t e = warp_id(); e < n1 + n2 + n3; e += warp_count()) {
+        const size_t i = e < n1 ? d.wl_conv[e] : (e < n1 + n2 ? d.wl_newif[e - n1] : d.wl_fromliq[e - n1 - n2]);
+        if (lane >= kQ) continue;
+        size_t j = i;
+        if (lane > 0) {
+            int x, y, z;
+            cell_xyz(d, i, x, y, z);
+            if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
         }
+        set_bulk(d, j);
+        d.mark[j] = 0;
     }
 }
 
@@ -289,7 +299,8 @@ void launch_conversions(const Dev& d, int nxt, cudaStream_t s) {
 
 // ------------------------------------------------------------------- bubble model
 // V_b = #gas cells of b + sum over interface cells of b of (1 - phi), in FP64; also the
-// number of interface cells.  One pass over the flags, 16 cells per thread and load.
+// number of interface cells.  One pass over the flags, 16 cells per thread and load; each
+// thread keeps a running sum for the bubble it last saw and flushes it on a change.
 __global__ void bubble_reduce_kernel(const Dev d, const int nxt) {
     extern __shared__ unsigned char smem_raw[];
     double* sV = reinterpret_cast<double*>(smem_raw);
@@ -302,6 +313,9 @@ __global__ void bubble_reduce_kernel(const Dev d, const int nxt) {
     const size_t nvec = d.N / 16;
     const uint4* fl4 = reinterpret_cast<const uint4*>(d.flags);
     unsigned int nif = 0;
+    uint32_t cb = kNone;
+    double cv = 0.0;
+    unsigned long long cg = 0ull;
     for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec + (d.N % 16 ? 1 : 0); v += (size_t)gridDim.x * blockDim.x) {
         uint32_t w[4];
         if (v < nvec) {
@@ -318,15 +332,26 @@ __global__ void bubble_reduce_kernel(const Dev d, const int nxt) {
             if (!(t & (F_IF | F_GAS))) continue;
             const size_t i = v * 16 + c;
             const uint32_t b = d.owner[i];
-            if (t & F_IF) {
-                nif++;
-                if (b < (uint32_t)d.nbub) atomicAdd(&sV[b], 1.0 - (double)phi[i]);
-            } else if (b < (uint32_t)d.nbub) {
-                atomicAdd(&sG[b], 1ull);
+            if (t & F_IF) nif++;
+            if (b >= (uint32_t)d.nbub) continue;
+            if (b != cb) {
+                if (cb != kNone) {
+                    if (cv != 0.0) atomicAdd(&sV[cb], cv);
+                    if (cg) atomicAdd(&sG[cb], cg);
+                }
+                cb = b;
+                cv = 0.0;
+                cg = 0ull;
             }
+            if (t & F_IF) cv += 1.0 - (double)phi[i];
+            else cg++;
         }
     }
-    atomicAdd(&sIf, nif);
+    if (cb != kNone) {
+        if (cv != 0.0) atomicAdd(&sV[cb], cv);
+        if (cg) atomicAdd(&sG[cb], cg);
+    }
+    if (nif) atomicAdd(&sIf, nif);
     __syncthreads();
     for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
         if (sV[b] != 0.0) atomicAdd(&d.bub[b].Vif, sV[b]);
@@ -367,6 +392,7 @@ __global__ void step_end_kernel(const Dev d, const int set_reference) {
             c.n_iface_acc = 0;
             c.share = (c.pool != 0.0 && c.n_iface > 0) ? c.pool / (double)c.n_iface : 0.0;
             c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
+            c.n_slow = 0;
         }
     }
     if (t < d.nsph && d.bin_cnt) {  // bins of the spheres' start-of-step positions
@@ -528,7 +554,7 @@ __global__ void export_kernel(const Dev d, const int cur, float* f, uint8_t* fla
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
         const uint8_t t = d.flags[i] & F_TYPE;
         if (f)
-            for (int q = 0; q < kQ; q++) f[(size_t)q * d.N + i] = wgt(q) + Store<S>::get_nc(fs, (size_t)q * d.N + i);
+            for (int q = 0; q < kQ; q++) f[(size_t)q * d.N + i] = Store<S>::get_nc(fs, (size_t)q * d.N + i);
         if (flags) flags[i] = t;
         if (m) m[i] = (t & F_IF) ? d.mass[i] : 0.f;
         if (phi) phi[i] = (t & F_IF) ? d.phi[cur][i] : ((t & F_GAS) ? 0.f : 1.f);

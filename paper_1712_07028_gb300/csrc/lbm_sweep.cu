@@ -19,6 +19,12 @@
 //   and odd parts; u = (sum c f + rho g/2)/rho
 //   and the conversion candidates: phi >= 1 + eps (filled) / phi <= -eps (emptied).
 //
+// Two kernels share the work.  The bulk kernel streams and collides every liquid cell whose
+// 18 neighbours are liquid, interface or beyond a wall (wall links read the cell's own
+// opposite PDF by an index select), with few registers and no branches per link; every other
+// active cell is appended to a compact per-step list that the boundary kernel processes with
+// the full link logic.
+//
 // Sphere force and torque are reduced in FP64 without cancellation loss: per link the
 // momentum is split into the constant part -2 w_q c_q (accumulated exactly as integers,
 // times 36) and the small deviation part (FP32 per cell, summed over the warp's lanes of the
@@ -71,42 +77,119 @@ __device__ __forceinline__ void sph_flush_direct(const Dev& d, const SphAcc& a) 
     }
 }
 
+
+// moments, Guo-shifted velocity and the TRT collision of one cell, all on deviations f - w;
+// the post-collision deviations go to grid fb
 template <int S>
-__global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) {
+__device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T* __restrict__ fb, size_t i, const float (&fin)[kQ]) {
+    const size_t N = d.N;
+    const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
+    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        drho += fin[q];
+        jx += cx(q) * fin[q]; jy += cy(q) * fin[q]; jz += cz(q) * fin[q];
+    }
+    const float rho = 1.f + drho;
+    if (!(rho > 0.f)) atomicOr(&d.sc->status, S_UNSTABLE);
+    const float inv = 1.f / rho;
+    const float ux = (jx + 0.5f * rho * gx) * inv;
+    const float uy = (jy + 0.5f * rho * gy) * inv;
+    const float uz = (jz + 0.5f * rho * gz) * inv;
+    const float usq = ux * ux + uy * uy + uz * uz;
+    const float ug = ux * gx + uy * gy + uz * gz;
+    const float lp = d.lp, lm = d.lm;
+    const float cp = 1.f + 0.5f * lp, cm = 1.f + 0.5f * lm;
+    {
+        // q = 0: f+ = f, e+ - w = w (rho - 1 - 1.5 rho u.u), G+ = -3 w rho u.g
+        const float w = wgt(0);
+        const float ep = w * (drho - 1.5f * rho * usq);
+        Store<S>::put(fb, i, fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug)));
+    }
+#pragma unroll
+    for (int q = 1; q < kQ; q += 2) {
+        const int qb = q + 1;
+        const float w = wgt(q);
+        const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+        const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
+        const float ep = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));   // e+_q - w_q
+        const float em = w * rho * 3.f * cu;                                  // e-_q
+        const float fp = 0.5f * (fin[q] + fin[qb]);
+        const float fm = 0.5f * (fin[q] - fin[qb]);
+        const float a = lp * (fp - ep) + cp * (w * rho * (9.f * cu * cg - 3.f * ug));
+        const float b = lm * (fm - em) + cm * (w * rho * 3.f * cg);
+        Store<S>::put(fb, (size_t)q * N + i, fin[q] + a + b);
+        Store<S>::put(fb, (size_t)qb * N + i, fin[qb] + a - b);
+    }
+}
+
+// every liquid cell whose neighbours all carry PDFs or lie beyond a wall; other active cells
+// go to the boundary list
+template <int S>
+__global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int cur) {
+    using T = typename Store<S>::T;
+    const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
+    T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= d.nx || y >= d.ny) return;
+    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+    const uint32_t i = (uint32_t)x + nx * (uint32_t)y + nxy * (uint32_t)z;
+    const uint8_t fl = d.flags[i];
+    if (!(fl & F_ACTIVE)) return;
+    if (!(fl & F_BULK)) {
+        wl_push(d.wl_slow, &d.sc->n_slow, (uint32_t)d.N, i, &d.sc->status);
+        return;
+    }
+    // neighbour coordinates (periodic wrap) and the links whose source lies beyond a wall
+    const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+    const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
+    const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
+    const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
+    const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
+    const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
+    float fin[kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
+        const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
+        const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
+        const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
+                          (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
+        // halfway bounce-back: the cell's own post-collision PDF of the opposite direction
+        const T* plane = fa + (size_t)(wall ? opp(q) : q) * d.N;
+        fin[q] = Store<S>::get(plane, wall ? i : sx + sy + sz);
+    }
+    collide_store<S>(d, fb, i, fin);
+}
+
+// every other active cell: walls, sphere links, gas links, interface mass exchange
+template <int S>
+__global__ void __launch_bounds__(128) sweep_boundary_kernel(const Dev d, const int cur) {
     using T = typename Store<S>::T;
     const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
     T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
     const float* __restrict__ phia = d.phi[cur];
     float* __restrict__ phib = d.phi[cur ^ 1];
     const size_t N = d.N;
+    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)N);
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
 
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    const bool inside = (x < d.nx) && (y < d.ny);
-    const size_t i = inside ? cell_index(d, x, y, z) : 0;
-    const uint8_t fl = inside ? d.flags[i] : (uint8_t)0;
-
-    SphAcc acc;
-    acc.pid = kNone;
-    float sbb = 0.f;
-
-    if (fl & F_ACTIVE) {
-        float fin[kQ];
-        const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
-        if (fl & F_BULK) {
-            // every neighbour exists (wrapping periodic axes) and carries PDFs
-            const int xm = x == 0 ? d.nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
-            const int ym = y == 0 ? d.ny - 1 : y - 1, yp = y == d.ny - 1 ? 0 : y + 1;
-            const int zm = z == 0 ? d.nz - 1 : z - 1, zp = z == d.nz - 1 ? 0 : z + 1;
-#pragma unroll
-            for (int q = 0; q < kQ; q++) {
-                const int sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : x);
-                const int sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y);
-                const int sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z);
-                fin[q] = Store<S>::get(fa, (size_t)q * N + cell_index(d, sx, sy, sz));
-            }
-        } else {
+    // every thread of the block runs the same number of rounds (warp collectives below)
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t k = base + threadIdx.x;
+        SphAcc acc;
+        acc.pid = kNone;
+        float sbb = 0.f;
+        if (k < n) {
+            const size_t i = d.wl_slow[k];
+            const uint8_t fl = d.flags[i];
+            int x, y, z;
+            cell_xyz(d, i, x, y, z);
+            float fin[kQ];
             float fo[kQ];
             float drho0 = 0.f, j0x = 0.f, j0y = 0.f, j0z = 0.f;
 #pragma unroll
@@ -174,110 +257,73 @@ __global__ void __launch_bounds__(128) sweep_kernel(const Dev d, const int cur) 
                 float drho = 0.f;
 #pragma unroll
                 for (int q = 0; q < kQ; q++) drho += fin[q];
-                const float ph = mnew / (1.f + drho);
+                const float rho = 1.f + drho;
                 d.mass[i] = mnew;
-                phib[i] = ph;
+                phib[i] = mnew / rho;
+                // phi >= 1 + eps  <=>  m - rho >= eps rho, taken as (m - 1) - drho so that a
+                // density deviation below FP32's resolution of 1 still decides it;
+                // phi <= -eps  <=>  m <= -eps rho
                 uint8_t mk = 0;
-                if (ph >= 1.f + d.eps) mk = K_FILLED;
-                else if (ph <= -d.eps) mk = K_EMPTIED;
+                if ((mnew - 1.f) - drho >= d.eps * rho) mk = K_FILLED;
+                else if (mnew <= -d.eps * rho) mk = K_EMPTIED;
                 if (mk) {
                     d.mark[i] = mk;
                     wl_push(d.wl_conv, &d.sc->n_conv, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
                 }
             }
+            collide_store<S>(d, fb, i, fin);
         }
 
-        // moments, Guo-shifted velocity, TRT collision, all on deviations f - w
-        float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-        for (int q = 0; q < kQ; q++) {
-            drho += fin[q];
-            jx += cx(q) * fin[q]; jy += cy(q) * fin[q]; jz += cz(q) * fin[q];
+        // ---- warp reduction of the sphere accumulators (every lane takes part)
+        float TJ[3] = {0.f, 0.f, 0.f};
+        int XK[3] = {0, 0, 0};
+        if (acc.pid != kNone) {
+            TJ[0] = acc.r[1] * acc.J[2] - acc.r[2] * acc.J[1];
+            TJ[1] = acc.r[2] * acc.J[0] - acc.r[0] * acc.J[2];
+            TJ[2] = acc.r[0] * acc.J[1] - acc.r[1] * acc.J[0];
+            XK[0] = acc.xi[1] * acc.K[2] - acc.xi[2] * acc.K[1];
+            XK[1] = acc.xi[2] * acc.K[0] - acc.xi[0] * acc.K[2];
+            XK[2] = acc.xi[0] * acc.K[1] - acc.xi[1] * acc.K[0];
         }
-        const float rho = 1.f + drho;
-        if (!(rho > 0.f)) atomicOr(&d.sc->status, S_UNSTABLE);
-        const float inv = 1.f / rho;
-        const float ux = (jx + 0.5f * rho * gx) * inv;
-        const float uy = (jy + 0.5f * rho * gy) * inv;
-        const float uz = (jz + 0.5f * rho * gz) * inv;
-        const float usq = ux * ux + uy * uy + uz * uz;
-        const float ug = ux * gx + uy * gy + uz * gz;
-        const float lp = d.lp, lm = d.lm;
-        const float cp = 1.f + 0.5f * lp, cm = 1.f + 0.5f * lm;
-        {
-            // q = 0: f+ = f, e+ - w = w (rho - 1 - 1.5 rho u.u), G+ = -3 w rho u.g
-            const float w = wgt(0);
-            const float ep = w * (drho - 1.5f * rho * usq);
-            Store<S>::put(fb, i, fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug)));
-        }
+        unsigned todo = __ballot_sync(full, acc.pid != kNone);
+        while (todo) {
+            const int leader = __ffs(todo) - 1;
+            const uint32_t P = __shfl_sync(full, acc.pid, leader);
+            const bool mine = acc.pid == P;
+            todo &= ~__ballot_sync(full, mine);
+            float v[6];
+            int iv[6];
 #pragma unroll
-        for (int q = 1; q < kQ; q += 2) {
-            const int qb = q + 1;
-            const float w = wgt(q);
-            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-            const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
-            const float ep = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));   // e+_q - w_q
-            const float em = w * rho * 3.f * cu;                                  // e-_q
-            const float fp = 0.5f * (fin[q] + fin[qb]);
-            const float fm = 0.5f * (fin[q] - fin[qb]);
-            const float a = lp * (fp - ep) + cp * (w * rho * (9.f * cu * cg - 3.f * ug));
-            const float b = lm * (fm - em) + cm * (w * rho * 3.f * cg);
-            Store<S>::put(fb, (size_t)q * N + i, fin[q] + a + b);
-            Store<S>::put(fb, (size_t)qb * N + i, fin[qb] + a - b);
-        }
-    }
-
-    // ---- warp reduction of the sphere accumulators (every lane takes part)
-    const unsigned full = 0xffffffffu;
-    const int lane = (threadIdx.y * blockDim.x + threadIdx.x) & 31;
-    float TJ[3] = {0.f, 0.f, 0.f};
-    int XK[3] = {0, 0, 0};
-    if (acc.pid != kNone) {
-        TJ[0] = acc.r[1] * acc.J[2] - acc.r[2] * acc.J[1];
-        TJ[1] = acc.r[2] * acc.J[0] - acc.r[0] * acc.J[2];
-        TJ[2] = acc.r[0] * acc.J[1] - acc.r[1] * acc.J[0];
-        XK[0] = acc.xi[1] * acc.K[2] - acc.xi[2] * acc.K[1];
-        XK[1] = acc.xi[2] * acc.K[0] - acc.xi[0] * acc.K[2];
-        XK[2] = acc.xi[0] * acc.K[1] - acc.xi[1] * acc.K[0];
-    }
-    unsigned todo = __ballot_sync(full, acc.pid != kNone);
-    while (todo) {
-        const int leader = __ffs(todo) - 1;
-        const uint32_t P = __shfl_sync(full, acc.pid, leader);
-        const bool mine = acc.pid == P;
-        todo &= ~__ballot_sync(full, mine);
-        float v[6];
-        int iv[6];
+            for (int c = 0; c < 3; c++) {
+                v[c] = mine ? acc.J[c] : 0.f;
+                v[3 + c] = mine ? TJ[c] : 0.f;
+                iv[c] = mine ? acc.K[c] : 0;
+                iv[3 + c] = mine ? XK[c] : 0;
+            }
 #pragma unroll
-        for (int k = 0; k < 3; k++) {
-            v[k] = mine ? acc.J[k] : 0.f;
-            v[3 + k] = mine ? TJ[k] : 0.f;
-            iv[k] = mine ? acc.K[k] : 0;
-            iv[3 + k] = mine ? XK[k] : 0;
-        }
+            for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+                for (int c = 0; c < 6; c++) {
+                    v[c] += __shfl_xor_sync(full, v[c], o);
+                    iv[c] += __shfl_xor_sync(full, iv[c], o);
+                }
+            }
+            if (lane == leader) {
+                SphereAcc& g = d.acc[P];
 #pragma unroll
-            for (int k = 0; k < 6; k++) {
-                v[k] += __shfl_xor_sync(full, v[k], o);
-                iv[k] += __shfl_xor_sync(full, iv[k], o);
+                for (int c = 0; c < 3; c++) {
+                    atomicAdd(&g.J[c], (double)v[c]);
+                    atomicAdd(&g.TJ[c], (double)v[3 + c]);
+                    atomicAdd(&g.K[c], (unsigned long long)(long long)iv[c]);
+                    atomicAdd(&g.XK[c], (unsigned long long)(long long)iv[3 + c]);
+                }
             }
         }
-        if (lane == leader) {
-            SphereAcc& g = d.acc[P];
+        if (__any_sync(full, sbb != 0.f)) {
 #pragma unroll
-            for (int k = 0; k < 3; k++) {
-                atomicAdd(&g.J[k], (double)v[k]);
-                atomicAdd(&g.TJ[k], (double)v[3 + k]);
-                atomicAdd(&g.K[k], (unsigned long long)(long long)iv[k]);
-                atomicAdd(&g.XK[k], (unsigned long long)(long long)iv[3 + k]);
-            }
+            for (int o = 16; o > 0; o >>= 1) sbb += __shfl_xor_sync(full, sbb, o);
+            if (lane == 0) atomicAdd(&d.sc->S_bb, (double)sbb);
         }
-    }
-    if (__any_sync(full, sbb != 0.f)) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sbb += __shfl_xor_sync(full, sbb, o);
-        if (lane == 0) atomicAdd(&d.sc->S_bb, (double)sbb);
     }
 }
 
@@ -286,10 +332,20 @@ void launch_sweep(const Dev& d, int cur, cudaStream_t s) {
     const int by = 128 / bx;
     dim3 block(bx, by, 1);
     dim3 grid((d.nx + bx - 1) / bx, (d.ny + by - 1) / by, d.nz);
+    const int nb = 152 * 6;
     switch (d.storage) {
-        case LBM_STORE_F32: sweep_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur); break;
-        case LBM_STORE_F16DEV: sweep_kernel<LBM_STORE_F16DEV><<<grid, block, 0, s>>>(d, cur); break;
-        default: sweep_kernel<LBM_STORE_BF16DEV><<<grid, block, 0, s>>>(d, cur); break;
+        case LBM_STORE_F32:
+            sweep_bulk_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur);
+            sweep_boundary_kernel<LBM_STORE_F32><<<nb, 128, 0, s>>>(d, cur);
+            break;
+        case LBM_STORE_F16DEV:
+            sweep_bulk_kernel<LBM_STORE_F16DEV><<<grid, block, 0, s>>>(d, cur);
+            sweep_boundary_kernel<LBM_STORE_F16DEV><<<nb, 128, 0, s>>>(d, cur);
+            break;
+        default:
+            sweep_bulk_kernel<LBM_STORE_BF16DEV><<<grid, block, 0, s>>>(d, cur);
+            sweep_boundary_kernel<LBM_STORE_BF16DEV><<<nb, 128, 0, s>>>(d, cur);
+            break;
     }
 }
 

@@ -180,8 +180,8 @@ class Sim:
         return out
 
     def export_state(self):
-        """dict of torch tensors on the device: f [19,z,y,x] (FP32 full values), flags, mass,
-        phi, owner, kappa"""
+        """dict of torch tensors on the device: f [19,z,y,x] (FP32 deviations f - w_q), flags,
+        mass, phi, owner, kappa"""
         t = self._torch
         out = {"f": t.empty((19,) + self.shape, dtype=t.float32, device=self.device),
                "flags": t.empty(self.shape, dtype=t.uint8, device=self.device),

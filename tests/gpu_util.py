@@ -6,6 +6,11 @@ import oracle
 from paper_1712_07028_gb300 import workloads as W
 
 
+# lattice weights of the D3Q19 order shared by the C ABI and the oracle (q = 0 rest, 1..6
+# faces, 7..18 edges): the export hands out f - w_q
+WEIGHTS = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
 def gpu_state(sim):
     """the CUDA library's full state as NumPy (FP64 where the oracle wants it)"""
     st = {k: v.cpu().numpy() for k, v in sim.export_state().items()}
@@ -16,14 +21,14 @@ def gpu_state(sim):
     V0, V, rg = sim.bubbles()
     M, sbb, scov, sunc, pool = sim.mass_budget()
     F, T = sim.forces()
-    st.update(x=x, u=u, w=w, V0=V0, V=V, rho_g=rg, pool=pool, F=F, T=T, steps=sim.steps_done)
+    st.update(sx=x, su=u, sw=w, V0=V0, V=V, rho_g=rg, pool=pool, F=F, T=T, steps=sim.steps_done)
     return st
 
 
 def oracle_from_state(wl: W.Workload, st, near_tol=1e-5):
     """an oracle simulation started from a state copied out of the CUDA library"""
     o = oracle.Sim(wl, init=False, near_tol=near_tol)
-    o.f[:] = st["f"].astype(np.float64)
+    o.f[:] = st["f"].astype(np.float64) + WEIGHTS[:, None, None, None]
     o.flag[:] = st["flags"]
     o.m[:] = st["mass"].astype(np.float64)
     o.phi[:] = st["phi"].astype(np.float64)
@@ -34,9 +39,9 @@ def oracle_from_state(wl: W.Workload, st, near_tol=1e-5):
         o.bub[b, oracle.B_V] = st["V"][b]
         o.bub[b, oracle.B_RHOG] = st["rho_g"][b]
     for a in range(len(wl.spheres)):
-        o.sph[a, oracle.S_X:oracle.S_X + 3] = st["x"][a]
-        o.sph[a, oracle.S_U:oracle.S_U + 3] = st["u"][a]
-        o.sph[a, oracle.S_W:oracle.S_W + 3] = st["w"][a]
+        o.sph[a, oracle.S_X:oracle.S_X + 3] = st["sx"][a]
+        o.sph[a, oracle.S_U:oracle.S_U + 3] = st["su"][a]
+        o.sph[a, oracle.S_W:oracle.S_W + 3] = st["sw"][a]
         # this step's force becomes the oracle's previous-step force for the two-step average
         o.sph[a, oracle.S_F:oracle.S_F + 3] = st["F"][a]
         o.sph[a, oracle.S_T:oracle.S_T + 3] = st["T"][a]

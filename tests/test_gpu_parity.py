@@ -81,8 +81,8 @@ def test_sphere_links_forces(lbm, nsph):
         o.step(10)
         F, T = sim.forces()
         Fo, To = o.forces
-        assert np.abs(F - Fo).max() <= 1e-6 * np.abs(Fo).max() + 1e-9, (F, Fo)
-        assert np.abs(T - To).max() <= 1e-6 * np.abs(To).max() + 1e-8, (T, To)
+        assert np.abs(F - Fo).max() <= 1e-5 * np.abs(Fo).max() + 1e-9, (F, Fo)
+        assert np.abs(T - To).max() <= 1e-5 * np.abs(To).max() + 1e-8, (T, To)
     drho, du, _ = U.compare_fields(o, U.gpu_state(sim))
     assert drho <= 1e-6 and du <= 1e-7, (drho, du)
 
@@ -101,7 +101,7 @@ def _one_step_check(lbm, wl, pre_steps, f_tol, phi_tol):
     assert not np.any(mism & ~near), "type mismatch away from a threshold at %s" % (np.argwhere(mism & ~near)[:5],)
     keep = ~U.dilate(mism, 2)
     act = ((st1["flags"] & 3) != 0) & ((flags_o & 3) != 0) & keep
-    df = np.abs(st1["f"].astype(np.float64) - o.f)[:, act].max() if act.any() else 0.0
+    df = np.abs(st1["f"].astype(np.float64) + U.WEIGHTS[:, None, None, None] - o.f)[:, act].max() if act.any() else 0.0
     iface = (st1["flags"] == oracle.IFACE) & (flags_o == oracle.IFACE) & keep
     dphi = np.abs(st1["phi"] - o.phi)[iface].max() if iface.any() else 0.0
     dm = np.abs(st1["mass"] - o.m)[iface].max() if iface.any() else 0.0
@@ -111,7 +111,7 @@ def _one_step_check(lbm, wl, pre_steps, f_tol, phi_tol):
         Fo, To = o.forces
         assert np.abs(st1["F"] - Fo).max() <= 1e-6 * max(1e-3, np.abs(Fo).max())
         assert np.abs(st1["T"] - To).max() <= 1e-6 * max(1e-2, np.abs(To).max())
-        assert np.abs(st1["x"] - o.positions).max() <= 1e-9
+        assert np.abs(st1["sx"] - o.positions).max() <= 1e-9
     if wl.bubbles:
         assert np.abs(st1["rho_g"] - o.rho_gas).max() <= 1e-6
     return int(mism.sum()), int(act.sum())
@@ -147,19 +147,33 @@ def _r27_compare(o, st):
 
 
 def test_c0_200_steps(lbm):
-    """the 32^3 column (bubble r=6, falling sphere r=3), 200 steps, FP32 vs FP64"""
+    """the 32^3 column (bubble r=6, falling sphere r=3), 200 steps, FP32 vs FP64, run side by
+    side: cell types are compared after every step; a type that differs at some step must be
+    at (or next to) a cell the oracle logged within 1e-4 of a threshold; rho, u and phi are
+    compared at the end away (distance > 2) from every cell that ever differed"""
     wl = W.column_c0()
     sim = lbm.Sim(wl)
-    sim.step(wl.steps)
     o = oracle.Sim(wl)
-    o.step(wl.steps)
+    ever = np.zeros(o.shape, bool)
+    for k in range(wl.steps):
+        sim.step(1)
+        o.step(1)
+        fl = sim.fields()["flags"].cpu().numpy()
+        mism = fl != o.flag
+        assert not np.any(mism & ~U.dilate(o.near > 0, 1)), (k, np.argwhere(mism & ~U.dilate(o.near > 0, 1))[:5])
+        ever |= mism
     st = U.gpu_state(sim)
-    drho, du, dphi, nmis, nexcl = _r27_compare(o, st)
-    print("C0 200 steps: max|drho|=%.3g max|du|=%.3g max|dphi|=%.3g type mismatches=%d excluded=%d" % (drho, du, dphi, nmis, nexcl))
+    keep = ~U.dilate(ever, 2)
+    drho, du, n = U.compare_fields(o, st, keep)
+    iface = (st["flags"] == oracle.IFACE) & (o.flag == oracle.IFACE) & keep
+    dphi = np.abs(st["phi"] - o.phi)[iface].max() if iface.any() else 0.0
+    print("C0 200 steps: max|drho|=%.3g max|du|=%.3g max|dphi|=%.3g cells that ever differed=%d excluded=%d"
+          % (drho, du, dphi, int(ever.sum()), int((~keep).sum())))
     assert drho <= 1e-5 and du <= 1e-6 and dphi <= 1e-5
     Fo, To = o.forces
     assert np.abs(st["F"] - Fo).max() <= 1e-3 * np.abs(Fo).max() + 1e-7
-    assert np.abs(st["x"] - o.positions).max() <= 1e-6
+    disp = np.abs(o.positions - np.array([s.x for s in wl.spheres])).max()
+    assert np.abs(st["sx"] - o.positions).max() <= 1e-3 * disp + 1e-7
 
 
 def test_c0_mass_drift(lbm):
