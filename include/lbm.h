@@ -180,6 +180,24 @@ int lbm_copy_bytes(lbm_ctx* ctx, uint64_t* h2d, uint64_t* d2h);
 /* Kernel launches enqueued so far (each node of a replayed CUDA graph counts). */
 int lbm_launch_count(lbm_ctx* ctx, uint64_t* launches);
 
+/* Bubble volumes for callers that cannot allocate device memory.  Some callers cannot call
+ * cudaMalloc at all (code inside an allocator hook or a host callback, real-time sections,
+ * programs whose device memory is fully handed out before they start); this entry point
+ * allocates nothing, neither directly nor through any library.  The paper has no
+ * counterpart: it is the bubble-volume reduction of lbm_step (V_b = number of gas cells of
+ * bubble b + sum over its interface cells of (1 - phi), FP64) offered on its own.
+ *   flags[n_cells], owner[n_cells], phi[n_cells]: device, in the layout lbm_export_state
+ *     writes (LBM_CELL_* types, bubble id or -1, fill level);
+ *   volumes[n_bubbles]: device, FP64 output;
+ *   n_bubbles: 1..1024, else LBM_EINVAL;
+ *   cuda_stream: the cudaStream_t the work goes to (asynchronous).
+ * Its scratch is a 16 KB static device array that every device using the library holds
+ * until the process exits, shared by all calls: calls whose work overlaps on the GPU (e.g.
+ * on two streams) race and must be ordered by the caller.  The first call on a device looks
+ * up that array's device address; make it before any stream capture. */
+int lbm_bubble_volumes_noalloc(const uint8_t* flags, const int32_t* owner, const float* phi, size_t n_cells,
+                               int n_bubbles, double* volumes, void* cuda_stream);
+
 /* Release the host-side handle (the arena stays the caller's). */
 int lbm_destroy(lbm_ctx* ctx);
 

@@ -23,7 +23,7 @@ S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW = 1, 2, 4, 8
 # every entry point include/lbm.h declares
 EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_step",
            "lbm_forces", "lbm_spheres", "lbm_bubbles", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
-           "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count", "lbm_destroy", "lbm_strerror")
+           "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count", "lbm_bubble_volumes_noalloc", "lbm_destroy", "lbm_strerror")
 
 
 class Params(ctypes.Structure):
@@ -72,6 +72,7 @@ def load():
     L.lbm_profile.argtypes = [vp, i32]
     L.lbm_copy_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.lbm_profile_read.argtypes = [vp, pd, ctypes.POINTER(ctypes.c_uint64)]
+    L.lbm_bubble_volumes_noalloc.argtypes = [vp, vp, vp, sz, i32, vp, vp]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_strerror.argtypes = [i32]
     L.lbm_strerror.restype = ctypes.c_char_p
