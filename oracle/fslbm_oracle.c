@@ -23,11 +23,12 @@
  *      Guo body force (the paper uses gravity without naming a forcing scheme);
  *   2. cell conversions with layer closure, new-interface initialisation from the
  *      equilibrium and excess-mass redistribution (Sec. 2.2, Fig. cellConversions);
- *   3. bubble model: per-bubble volume and gas density (Sec. 2.2, last paragraph);
- *   4. curvature from fill levels, Parker-Youngs normals (Sec. 2.2, only if sigma > 0);
- *   5. sphere update: momentum exchange of links between two spheres, lubrication
+ *   3. sphere update: momentum exchange of links between two spheres, lubrication
  *      correction (Eq. lubrication) and n_substeps Newton-Euler sub-steps (Sec. 2.3);
- *   6. cells covered / uncovered by the moved spheres, refill of uncovered cells.
+ *   4. cells covered / uncovered by the moved spheres, refill of uncovered cells;
+ *   5. bubble model: per-bubble volume and gas density (Sec. 2.2, last paragraph), on the
+ *      cells as the step leaves them, for the next step's reconstruction;
+ *   6. curvature from fill levels, Parker-Youngs normals (Sec. 2.2, only if sigma > 0).
  *
  * Parity: pinned by the tests (Poiseuille profile, rest-state invariance, exact per-step
  * mass, momentum and angular-momentum balances, Stokes drag in a periodic array, the
@@ -842,12 +843,12 @@ int orc_step(const orc_params *p, orc_state *s, int nsteps)
         sweep(p, s, share);                                        /* 1 */
         conversions(p, s);                                         /* 2 */
         memcpy(s->f, s->ft, sizeof(double) * (size_t)NQ * (size_t)N);
-        bubble_model(p, s, 0);                                     /* 3 */
-        if (p->sigma > 0.0) curvature(p, s);                       /* 4 */
-        contact_links(p, s);                                       /* 5 */
+        contact_links(p, s);                                       /* 3 */
         move_spheres(p, s);
         for (int a = 0; a < p->nsph; a++) s->sph[(long)a * S_LEN + S_HASP] = 1.0;
-        if (p->sphere_mode != 0 && p->nsph > 0) cover_uncover(p, s); /* 6 */
+        if (p->sphere_mode != 0 && p->nsph > 0) cover_uncover(p, s); /* 4 */
+        bubble_model(p, s, 0);                                     /* 5 */
+        if (p->sigma > 0.0) curvature(p, s);                       /* 6 */
         s->scal[SC_STEPS] += 1.0;
     }
     return (int)s->scal[SC_STATUS];
