@@ -75,6 +75,8 @@ extern "C" {
 #define LBM_S_OVERFLOW 2u        /* a conversion / covering worklist overflowed */
 #define LBM_S_BUBBLE_GONE 4u     /* a bubble's volume reached zero */
 #define LBM_S_BIN_OVERFLOW 8u    /* more spheres in a neighbour-search bin than it holds */
+#define LBM_S_FAST_SPHERE 32u    /* a sphere moved more than a quarter cell in one step (the
+                                    per-step partner searches assume less) */
 
 typedef struct lbm_params {
     int32_t nx, ny, nz;        /* grid size, each >= 3 */

@@ -42,6 +42,10 @@ struct lbm_ctx {
     double sweep_ms;
     uint64_t sweeps;
     uint64_t h2d_bytes, d2h_bytes;   // host <-> device copies made by the library
+    // second stream and fork/join events of the concurrent bulk / boundary sweep
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+    bool side_ready;
 };
 
 namespace {
@@ -123,19 +127,6 @@ int status_code(uint32_t st) {
     return LBM_OK;
 }
 
-// kernels of one step, in the order of the method
-int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s) {
-    const Dev& d = c->d;
-    const int nxt = cur ^ 1;
-    launch_sweep(d, cur, s);
-    launch_conversions(d, nxt, s);
-    launch_bubbles(d, nxt, s);
-    if (d.kappa) launch_curvature(d, nxt, s);
-    launch_spheres(d, nxt, s);
-    launch_step_end(d, s);
-    return cuda_fail(cudaGetLastError());
-}
-
 // collect the elapsed time of a recorded (start, end) pair
 void prof_collect(lbm_ctx* c, int slot) {
     if (!c->ev_pending[slot]) return;
@@ -148,26 +139,31 @@ void prof_collect(lbm_ctx* c, int slot) {
     c->ev_pending[slot] = false;
 }
 
-// one step with the sweep bracketed by events (profiling mode, eager launches)
-int enqueue_step_timed(lbm_ctx* c, int cur, cudaStream_t s) {
+// kernels of one step, in the order of the method; with `timed`, the sweep (bulk and boundary
+// kernels together) is bracketed by a pair of events on its stream
+int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool timed = false) {
     const Dev& d = c->d;
     const int nxt = cur ^ 1;
-    const int slot = c->ev_slot;
-    c->ev_slot = (c->ev_slot + 1) % 64;
-    prof_collect(c, slot);
-    cudaEventRecord(c->ev[2 * slot], s);
-    launch_sweep(d, cur, s);
-    cudaEventRecord(c->ev[2 * slot + 1], s);
-    c->ev_pending[slot] = true;
+    int slot = 0;
+    if (timed) {
+        slot = c->ev_slot;
+        c->ev_slot = (c->ev_slot + 1) % 64;
+        prof_collect(c, slot);
+        cudaEventRecord(c->ev[2 * slot], s);
+    }
+    launch_sweep(d, cur, s, c->side, c->fork, c->join);
+    if (timed) {
+        cudaEventRecord(c->ev[2 * slot + 1], s);
+        c->ev_pending[slot] = true;
+    }
     launch_conversions(d, nxt, s);
-    launch_bubbles(d, nxt, s);
-    if (d.kappa) launch_curvature(d, nxt, s);
     launch_spheres(d, nxt, s);
-    launch_step_end(d, s);
+    launch_end_scan(d, nxt, 0, s);
+    if (d.kappa) launch_curvature(d, nxt, s);
     return cuda_fail(cudaGetLastError());
 }
 
-int count_per_step(const Dev& d) { return 2 + 6 + 1 + (d.kappa ? 1 : 0) + spheres_launches(d) + 1; }
+int count_per_step(const Dev& d) { return 2 + 1 + (d.kappa ? 1 : 0) + spheres_launches(d) + 1; }
 
 int first_step(lbm_ctx* c) {
     const lbm_params* p = &c->p;
@@ -228,6 +224,13 @@ int first_step(lbm_ctx* c) {
     c->geo_dev = (double*)(a + L.geo);
 
     cudaStream_t s = c->stream;
+    prepare_sphere_kernels();
+    if (!c->side_ready) {
+        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        c->side_ready = true;
+    }
     int rc = cuda_fail(cudaMemsetAsync(a, 0, L.total, s));
     if (rc) return rc;
     if (d.nbub > 0)
@@ -238,10 +241,9 @@ int first_step(lbm_ctx* c) {
     launch_bins_insert(d, s);
     launch_init(d, c->geo_dev, s);
     launch_bulk_all(d, s);
-    launch_bubbles(d, 0, s);
+    launch_end_scan(d, 0, 1, s);
     if (d.kappa) launch_curvature(d, 0, s);
-    launch_step_end_reference(d, s);
-    if ((rc = launched(c, (d.nsph > 0) + 4 + (d.kappa ? 1 : 0)))) return rc;
+    if ((rc = launched(c, (d.nsph > 0) + 3 + (d.kappa ? 1 : 0)))) return rc;
     c->cur = 0;
     c->per_step = count_per_step(d);
     c->started = true;
@@ -315,6 +317,7 @@ int lbm_init(const lbm_params* p, void* arena, size_t arena_bytes, void* cuda_st
     c->sweeps = 0;
     c->h2d_bytes = 0;
     c->d2h_bytes = 0;
+    c->side_ready = false;
     c->sph_stage = (Sphere*)std::malloc(sizeof(Sphere) * (size_t)p->max_spheres);
     c->sc_stage = (Scalars*)std::malloc(sizeof(Scalars));
     c->bub_stage = (Bubble*)std::malloc(sizeof(Bubble) * (size_t)p->max_bubbles);
@@ -364,7 +367,7 @@ int lbm_step(lbm_ctx* c, int nsteps) {
     int left = nsteps;
     if (c->profiling) {
         for (; left > 0; left--) {
-            if ((rc = enqueue_step_timed(c, c->cur, c->stream))) return rc;
+            if ((rc = enqueue_step(c, c->cur, c->stream, true))) return rc;
             c->launches += (uint64_t)c->per_step;
             c->cur ^= 1;
         }
@@ -516,6 +519,11 @@ int lbm_destroy(lbm_ctx* c) {
     if (c->graph_ready) cudaGraphExecDestroy(c->graph);
     if (c->ev_ready)
         for (int k = 0; k < 2 * 64; k++) cudaEventDestroy(c->ev[k]);
+    if (c->side_ready) {
+        cudaEventDestroy(c->fork);
+        cudaEventDestroy(c->join);
+        cudaStreamDestroy(c->side);
+    }
     std::free(c->sph_stage);
     std::free(c->sc_stage);
     std::free(c->bub_stage);

@@ -100,7 +100,8 @@ struct Scalars {
     uint32_t n_conv, n_newif, n_fromliq, n_touch, n_uncov;
     uint32_t bin_overflow;
     uint32_t n_slow;      // active cells the bulk sweep left to the boundary sweep
-    uint32_t pad1[6];
+    uint32_t ticket;      // blocks of the end-of-step scan that have finished
+    uint32_t pad1[5];
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
@@ -174,11 +175,13 @@ __device__ __forceinline__ bool bulk_of(const Dev& d, size_t i) {
     if ((d.flags[i] & F_TYPE) != F_LIQ) return false;
     int x, y, z;
     cell_xyz(d, i, x, y, z);
+    uint32_t ok = F_ACTIVE;   // all 18 neighbour loads are independent
+#pragma unroll
     for (int q = 1; q < kQ; q++) {
         size_t j;
-        if (nbr(d, x, y, z, cx(q), cy(q), cz(q), j) && !(d.flags[j] & F_ACTIVE)) return false;
+        if (nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) ok &= (d.flags[j] & F_ACTIVE) ? F_ACTIVE : 0u;
     }
-    return true;
+    return ok != 0;
 }
 __device__ __forceinline__ void set_bulk(const Dev& d, size_t i) {
     const uint8_t t = d.flags[i] & F_TYPE;
@@ -338,13 +341,14 @@ __device__ __forceinline__ uint32_t covering_sphere(const Dev& d, int x, int y, 
 }
 
 // kernels (defined in the .cu files), launched by lbm_capi.cu
-void launch_sweep(const Dev& d, int cur, cudaStream_t s);
+void launch_sweep(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+
 void launch_conversions(const Dev& d, int nxt, cudaStream_t s);
-void launch_bubbles(const Dev& d, int nxt, cudaStream_t s);
+void launch_end_scan(const Dev& d, int cur, int set_reference, cudaStream_t s);
 void launch_curvature(const Dev& d, int nxt, cudaStream_t s);
 void launch_spheres(const Dev& d, int nxt, cudaStream_t s);
-void launch_step_end(const Dev& d, cudaStream_t s);
-void launch_step_end_reference(const Dev& d, cudaStream_t s);
+void prepare_sphere_kernels();
+
 void launch_bins_insert(const Dev& d, cudaStream_t s);
 int spheres_launches(const Dev& d);
 void launch_init(const Dev& d, const double* bub_geom_dev, cudaStream_t s);

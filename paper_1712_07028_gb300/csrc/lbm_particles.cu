@@ -85,28 +85,35 @@ __global__ void sph_contact_kernel(const Dev d) {
     Sphere& s = d.sph[P];
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
     const int L[3] = {d.nx, d.ny, d.nz};
+    const uint32_t np = min(d.npairs[P], (uint32_t)kPairCap);
     if (finite3(s.x) && s.R > 0.0 && s.R < 64.0) {
-        for_partners(d, P, s.x, [&](uint32_t Q) {
+        for (uint32_t pk = 0; pk < np; pk++) {
+            const uint32_t Q = d.pairs[(size_t)P * kPairCap + pk];
             const Sphere& o = d.sph[Q];
-            if (!finite3(o.x) || !(o.R > 0.0 && o.R < 64.0)) return;
+            if (!finite3(o.x) || !(o.R > 0.0 && o.R < 64.0)) continue;
             double cq[3];   // Q's centre, unwrapped next to P
             for (int k = 0; k < 3; k++) cq[k] = s.x[k] + min_image(d, k, o.x[k], s.x[k]);
             const double dd2 = (cq[0] - s.x[0]) * (cq[0] - s.x[0]) + (cq[1] - s.x[1]) * (cq[1] - s.x[1]) + (cq[2] - s.x[2]) * (cq[2] - s.x[2]);
             const double reach = s.R + o.R + 2.0;
-            if (dd2 > reach * reach) return;
+            if (dd2 > reach * reach) continue;
             int lo[3], ext[3];
+            float oq[3], op[3];
             for (int k = 0; k < 3; k++) {
                 lo[k] = (int)floor(cq[k] - o.R);
                 ext[k] = (int)ceil(cq[k] + o.R) - lo[k] + 1;
+                oq[k] = (float)((double)lo[k] - cq[k]);
+                op[k] = (float)((double)lo[k] - s.x[k]);
             }
             const int total = ext[0] * ext[1] * ext[2];
-            const double RQ2 = o.R * o.R, RP2 = (s.R + 1.5) * (s.R + 1.5);
+            // a necessary condition only (the lattice's owners decide), with a margin for FP32
+            const float RQ2 = (float)(o.R * o.R) + 0.01f, RP2 = (float)((s.R + 1.5) * (s.R + 1.5)) + 0.01f;
             for (int e = threadIdx.x; e < total; e += blockDim.x) {
-                int w[3] = {lo[0] + e % ext[0], lo[1] + (e / ext[0]) % ext[1], lo[2] + e / (ext[0] * ext[1])};
-                double aq = 0, ap = 0;
+                const int ex[3] = {e % ext[0], (e / ext[0]) % ext[1], e / (ext[0] * ext[1])};
+                int w[3] = {lo[0] + ex[0], lo[1] + ex[1], lo[2] + ex[2]};
+                float aq = 0.f, ap = 0.f;
                 for (int k = 0; k < 3; k++) {
-                    aq += (w[k] - cq[k]) * (w[k] - cq[k]);
-                    ap += (w[k] - s.x[k]) * (w[k] - s.x[k]);
+                    aq += (oq[k] + ex[k]) * (oq[k] + ex[k]);
+                    ap += (op[k] + ex[k]) * (op[k] + ex[k]);
                 }
                 if (aq > RQ2 || ap > RP2) continue;
                 bool ok = true;
@@ -150,7 +157,7 @@ __global__ void sph_contact_kernel(const Dev d) {
                     T[2] += rp[0] * dj[1] - rp[1] * dj[0];
                 }
             }
-        });
+        }
     }
     __shared__ double red[6][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -170,9 +177,9 @@ __global__ void sph_contact_kernel(const Dev d) {
     }
 }
 
-// partners of sphere P within lubrication reach this step (centre distance below
-// R_P + R_Q + 2/3 + 1: the spheres move less than half a cell per step), one warp per sphere
-// with its lanes over the 27 neighbouring bins
+// partners of sphere P this step: centre distance below R_P + R_Q + 2, which covers the
+// lubrication reach (gap < 2/3, the spheres moving less than half a cell per step) and the
+// reach of links between obstacle nodes; one warp per sphere, lanes over the 27 bins
 __global__ void sph_pairs_kernel(const Dev d) {
     const uint32_t P = warp_id();
     const int lane = threadIdx.x & 31;
@@ -197,7 +204,7 @@ __global__ void sph_pairs_kernel(const Dev d) {
                 const double v = min_image(d, k, o.x[k], s.x[k]);
                 dd2 += v * v;
             }
-            const double reach = s.R + o.R + 2.0 / 3.0 + 1.0;
+            const double reach = s.R + o.R + 2.0;
             if (!(dd2 < reach * reach)) continue;
             const uint32_t slot = atomicAdd(&d.npairs[P], 1u);
             if (slot < (uint32_t)kPairCap) d.pairs[(size_t)P * kPairCap + slot] = Q;
@@ -253,16 +260,113 @@ __global__ void sph_substep_kernel(const Dev d, const Sphere* src, Sphere* dst, 
     if (P < d.nsph) substep_one(d, src, dst, dt, P);
 }
 
-// all sub-steps in one block (up to 1024 spheres): the block's barrier separates them
+// All sub-steps in one block (up to 1024 spheres, one per thread): positions and velocities
+// of every sphere live in shared memory (double-buffered), the block's barrier separates the
+// sub-steps; the same arithmetic as substep_one.  The sub-steps move a sphere by far less than
+// a quarter cell per step, so the pair prefilter uses the step-start centres.
 __global__ void sph_substeps_fused_kernel(const Dev d, const double dt) {
-    for (int k = 0; k < d.n_sub; k++) {
-        const Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
-        Sphere* dst = (k & 1) ? d.sph : d.sph_tmp;
-        for (int P = threadIdx.x; P < d.nsph; P += blockDim.x) substep_one(d, src, dst, dt, P);
+    extern __shared__ double smem[];
+    const int n = d.nsph;
+    double* xs[2] = {smem, smem + 3 * n};
+    double* us[2] = {smem + 6 * n, smem + 9 * n};
+    double* Rs = smem + 12 * n;
+    float* xf = reinterpret_cast<float*>(smem + 13 * n);   // FP32 copy of the centres for the pair prefilter
+    const int P = threadIdx.x;
+    const bool mine = P < n;
+    double x[3] = {0, 0, 0}, u[3] = {0, 0, 0}, w[3] = {0, 0, 0}, Fh[3] = {0, 0, 0}, Th[3] = {0, 0, 0}, Fl[3] = {0, 0, 0};
+    double m = 1.0, I = 1.0, R = 0.0;
+    if (mine) {
+        const Sphere& s = d.sph[P];
+        const bool hasp = s.hasp != 0.0;
+        for (int k = 0; k < 3; k++) {
+            x[k] = s.x[k]; u[k] = s.u[k]; w[k] = s.w[k];
+            Fh[k] = hasp ? 0.5 * (s.F[k] + s.Fp[k]) : s.F[k];
+            Th[k] = hasp ? 0.5 * (s.T[k] + s.Tp[k]) : s.T[k];
+            xs[0][3 * P + k] = x[k];
+            us[0][3 * P + k] = u[k];
+            xf[3 * P + k] = (float)x[k];
+        }
+        R = s.R;
+        Rs[P] = R;
+        m = s.rho * 4.0 / 3.0 * kPi * R * R * R;
+        I = 0.4 * m * R * R;
+    }
+    __syncthreads();
+    const double dc = 2.0 / 3.0, mu = ((double)d.tau - 0.5) / 3.0;
+    const int L[3] = {d.nx, d.ny, d.nz};
+    const uint32_t np = mine ? min(d.npairs[P], (uint32_t)kPairCap) : 0u;
+    // the sub-step increments without lubrication are the same every sub-step (the same
+    // expressions, so the same bits): computed once
+    double du0[3], dw0[3];
+    for (int k = 0; k < 3; k++) {
+        du0[k] = dt * (Fh[k] + 0.0 + m * d.gd[k]) / m;
+        dw0[k] = dt * Th[k] / I;
+    }
+    // FP32 prefilter on the step-start centres (they move far less than 0.25 per step), once
+    // per step: only partners that can come within 2/3 of touching are evaluated in FP64
+    uint32_t near[12];   // at most 12 equal spheres touch one (kissing number)
+    uint32_t nn = 0;
+    for (uint32_t k = 0; k < np; k++) {
+        const uint32_t Q = d.pairs[(size_t)P * kPairCap + k];
+        float g2 = 0.f;
+        for (int c = 0; c < 3; c++) {
+            float v = xf[3 * Q + c] - xf[3 * P + c];
+            if (d.bc[c]) {
+                const float Lc = (float)L[c];
+                v -= Lc * rintf(v / Lc);
+            }
+            g2 += v * v;
+        }
+        const float reach = (float)(R + Rs[Q]) + 2.f / 3.f + 0.5f;
+        if (g2 > reach * reach) continue;
+        if (nn < 12) near[nn] = Q;
+        else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
+        nn++;
+    }
+    if (nn > 12) nn = 12;
+    for (int sub = 0; sub < d.n_sub; sub++) {
+        const int a = sub & 1, b = a ^ 1;
+        Fl[0] = Fl[1] = Fl[2] = 0.0;
+        for (uint32_t k = 0; k < nn; k++) {
+            const uint32_t Q = near[k];
+            double dd[3];
+            for (int c = 0; c < 3; c++) dd[c] = min_image(d, c, xs[a][3 * Q + c], x[c]);
+            const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            double h = dist - R - Rs[Q];
+            if (!(h < dc) || dist <= 0.0) continue;
+            if (h < 0.2 * dc) h = 0.2 * dc;
+            const double rr = R * Rs[Q], rs = R + Rs[Q];
+            const double nn[3] = {dd[0] / dist, dd[1] / dist, dd[2] / dist};
+            const double vn = nn[0] * (u[0] - us[a][3 * Q]) + nn[1] * (u[1] - us[a][3 * Q + 1]) + nn[2] * (u[2] - us[a][3 * Q + 2]);
+            const double mag = -6.0 * kPi * mu * rr * rr / (rs * rs) * (1.0 / h - 1.0 / dc) * vn;
+            Fl[0] += mag * nn[0]; Fl[1] += mag * nn[1]; Fl[2] += mag * nn[2];
+        }
+        if (mine) {
+            const bool lub = Fl[0] != 0.0 || Fl[1] != 0.0 || Fl[2] != 0.0;
+            for (int k = 0; k < 3; k++) {
+                u[k] = u[k] + (lub ? dt * (Fh[k] + Fl[k] + m * d.gd[k]) / m : du0[k]);
+                w[k] = w[k] + dw0[k];
+            }
+            for (int k = 0; k < 3; k++) {
+                x[k] = x[k] + dt * u[k];
+                if (d.bc[k]) x[k] = wrap_pos(x[k], L[k]);
+                xs[b][3 * P + k] = x[k];
+                us[b][3 * P + k] = u[k];
+            }
+        }
         __syncthreads();
     }
-    if (d.n_sub & 1)
-        for (int P = threadIdx.x; P < d.nsph; P += blockDim.x) d.sph[P] = d.sph_tmp[P];
+    if (mine) {
+        Sphere& s = d.sph[P];
+        double mv = 0.0;
+        for (int k = 0; k < 3; k++) {
+            const double dk = min_image(d, k, x[k], s.x[k]);
+            mv += dk * dk;
+            s.x[k] = x[k]; s.u[k] = u[k]; s.w[k] = w[k]; s.Fl[k] = Fl[k];
+        }
+        // the pair prefilter and partner lists assume less than a quarter cell per step
+        if (!(mv <= 0.0625)) atomicOr(&d.sc->status, S_FAST_SPHERE);
+    }
 }
 
 __global__ void sph_prescribed_kernel(const Dev d) {
@@ -311,15 +415,35 @@ __global__ void cover_touch_kernel(const Dev d) {
     }
     const int total = ext[0] * ext[1] * ext[2];
     const double R2 = s.R * s.R;
+    // cell offsets from both centres in FP32 decide wherever |d^2 - R^2| clears their rounding
+    // error by far; the few cells closer to the sphere's surface are decided in FP64
+    float a0[3], a1[3];
+    for (int k = 0; k < 3; k++) {
+        a0[k] = (float)((double)lo[k] - s.x0[k]);
+        a1[k] = (float)((double)lo[k] - (s.x0[k] + off[k]));
+    }
+    const float R2f = (float)R2, band = 1e-3f * (1.f + R2f);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
-        int w[3] = {lo[0] + e % ext[0], lo[1] + (e / ext[0]) % ext[1], lo[2] + e / (ext[0] * ext[1])};
-        double d0 = 0, d1 = 0;
+        const int ex[3] = {e % ext[0], (e / ext[0]) % ext[1], e / (ext[0] * ext[1])};
+        int w[3] = {lo[0] + ex[0], lo[1] + ex[1], lo[2] + ex[2]};
+        float f0 = 0.f, f1 = 0.f;
         for (int k = 0; k < 3; k++) {
-            const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off[k]);
-            d0 += a * a;
-            d1 += b * b;
+            const float a = a0[k] + (float)ex[k], b = a1[k] + (float)ex[k];
+            f0 += a * a;
+            f1 += b * b;
         }
-        if ((d0 <= R2) == (d1 <= R2)) continue;
+        bool in0 = f0 <= R2f, in1 = f1 <= R2f;
+        if (fabsf(f0 - R2f) < band || fabsf(f1 - R2f) < band) {
+            double d0 = 0, d1 = 0;
+            for (int k = 0; k < 3; k++) {
+                const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off[k]);
+                d0 += a * a;
+                d1 += b * b;
+            }
+            in0 = d0 <= R2;
+            in1 = d1 <= R2;
+        }
+        if (in0 == in1) continue;
         bool ok = true;
         for (int k = 0; k < 3; k++) {
             if (w[k] < 0 || w[k] >= L[k]) {
@@ -373,7 +497,6 @@ __global__ void cover_apply_kernel(const Dev d, const int nxt) {
                 atomicAdd(&d.sc->S_cover, (double)(1.f + rl));
             } else if (t & F_IF) {
                 atomicAdd(&d.sc->S_cover, (double)d.mass[i]);
-                atomicSub(&d.sc->n_iface_acc, 1u);
             }
             d.flags[i] = F_OBS;
             d.owner[i] = own;
@@ -449,7 +572,6 @@ __global__ void cover_refill_kernel(const Dev d, const int nxt) {
             phi[i] = pb;
             d.mass[i] = pb * rb;
             atomicAdd(&d.sc->S_uncover, (double)(pb * rb));
-            atomicAdd(&d.sc->n_iface_acc, 1u);
         } else {
             d.flags[i] = F_LIQ;
             d.owner[i] = kNone;
@@ -474,13 +596,8 @@ __global__ void cover_finish_kernel(const Dev d) {
             if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
         }
         set_bulk(d, j);
+        if (lane == 0) d.mark[i] = 0;   // BULK reads types only, never marks
     }
-}
-
-// marks of the touched cells cleared once every BULK bit is final
-__global__ void cover_clear_kernel(const Dev d) {
-    const uint32_t n = min(*(volatile uint32_t*)&d.sc->n_touch, (uint32_t)d.wl_cap);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) d.mark[d.wl_touch[k]] = 0;
 }
 
 int spheres_launches(const Dev& d) {
@@ -488,20 +605,26 @@ int spheres_launches(const Dev& d) {
     int n = 3;  // prepare, contact, pairs
     if (d.sphere_mode == LBM_SPHERES_FREE) n += d.nsph <= 1024 ? 1 : d.n_sub + (d.n_sub & 1);
     else if (d.sphere_mode == LBM_SPHERES_PRESCRIBED) n += 1;
-    if (d.sphere_mode != LBM_SPHERES_FIXED) n += 5;
+    if (d.sphere_mode != LBM_SPHERES_FIXED) n += 4;
     return n;
+}
+
+void prepare_sphere_kernels() {
+    // the fused sub-step kernel keeps 13 doubles per sphere in shared memory (<= 1024 spheres)
+    cudaFuncSetAttribute(sph_substeps_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (13 * 8 + 3 * 4) * 1024);
 }
 
 void launch_spheres(const Dev& d, int nxt, cudaStream_t st) {
     if (d.nsph == 0) return;
     const int tb = 128, nb = (d.nsph + tb - 1) / tb;
     sph_prepare_kernel<<<nb, tb, 0, st>>>(d);
-    sph_contact_kernel<<<d.nsph, 128, 0, st>>>(d);
     sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
+    sph_contact_kernel<<<d.nsph, 128, 0, st>>>(d);
     if (d.sphere_mode == LBM_SPHERES_FREE) {
         const double dt = 1.0 / d.n_sub;
         if (d.nsph <= 1024) {
-            sph_substeps_fused_kernel<<<1, d.nsph <= 128 ? 128 : ((d.nsph + 31) / 32) * 32, 0, st>>>(d, dt);
+            const size_t shm = sizeof(double) * 13 * (size_t)d.nsph + sizeof(float) * 3 * (size_t)d.nsph;
+            sph_substeps_fused_kernel<<<1, d.nsph <= 128 ? 128 : ((d.nsph + 31) / 32) * 32, shm, st>>>(d, dt);
         } else {
             for (int k = 0; k < d.n_sub; k++) {
                 const Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
@@ -531,7 +654,6 @@ void launch_spheres(const Dev& d, int nxt, cudaStream_t st) {
             break;
     }
     cover_finish_kernel<<<lb, 128, 0, st>>>(d);
-    cover_clear_kernel<<<lb, 128, 0, st>>>(d);
 }
 
 }  // namespace lbm

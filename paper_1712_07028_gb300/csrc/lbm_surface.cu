@@ -74,10 +74,10 @@ __device__ __forceinline__ float warp_cell_rho(const Dev& d, const typename Stor
 }
 
 // (ii) filled cells: gas neighbours become new interface cells; emptied neighbours stay
-__global__ void conv_filled_kernel(const Dev d) {
+__device__ void conv_filled(const Dev& d, const uint32_t wid, const uint32_t nw) {
     const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+    for (uint32_t e = wid; e < n; e += nw) {
         const size_t i = d.wl_conv[e];
         if (!(d.mark[i] & K_FILLED) || lane == 0 || lane >= kQ) continue;
         int x, y, z;
@@ -97,12 +97,12 @@ __global__ void conv_filled_kernel(const Dev d) {
 // (iii) emptied cells: liquid neighbours become interface cells with m = rho; the smallest
 // bubble id among their emptied neighbours becomes theirs
 template <int S>
-__global__ void conv_emptied_kernel(const Dev d, const int nxt) {
+__device__ void conv_emptied(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(d.f[nxt]);
     const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+    for (uint32_t e = wid; e < n; e += nw) {
         const size_t i = d.wl_conv[e];
         if (!(d.mark[i] & K_EMPTIED) || lane == 0 || lane >= kQ) continue;
         const uint32_t b = d.owner[i];
@@ -124,12 +124,12 @@ __global__ void conv_emptied_kernel(const Dev d, const int nxt) {
 // (iv) new interface cells from gas: f* = e(mean rho, mean u) over the neighbours that carry
 // PDFs (liquid, interface not emptied, filled), m = 0
 template <int S>
-__global__ void conv_newif_kernel(const Dev d, const int nxt) {
+__device__ void conv_newif(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
     using T = typename Store<S>::T;
     T* f = static_cast<T*>(d.f[nxt]);
     const uint32_t n = list_len(&d.sc->n_newif, d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+    for (uint32_t e = wid; e < n; e += nw) {
         const size_t i = d.wl_newif[e];
         int x, y, z;
         cell_xyz(d, i, x, y, z);
@@ -156,13 +156,13 @@ __global__ void conv_newif_kernel(const Dev d, const int nxt) {
 // no neighbour can take it.  The Parker-Youngs gradient is taken over the 3x3x3 block, lane l
 // (0..26) holding the fill level of offset (l%3-1, l/3%3-1, l/9-1).
 template <int S>
-__global__ void conv_excess_kernel(const Dev d, const int nxt) {
+__device__ void conv_excess(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(d.f[nxt]);
     const float* phi = d.phi[nxt];
     const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+    for (uint32_t e = wid; e < n; e += nw) {
         const size_t i = d.wl_conv[e];
         const uint8_t mk = d.mark[i] & (K_FILLED | K_EMPTIED);
         if (!mk) continue;
@@ -213,7 +213,7 @@ __global__ void conv_excess_kernel(const Dev d, const int nxt) {
 
 // (vi) final types; fill level of every interface cell whose mass changed in this phase
 template <int S>
-__global__ void conv_finalize_kernel(const Dev d, const int nxt) {
+__device__ void conv_finalize(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(d.f[nxt]);
     float* phi = d.phi[nxt];
@@ -221,7 +221,7 @@ __global__ void conv_finalize_kernel(const Dev d, const int nxt) {
     const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
     const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n1 + n2 + n3; e += warp_count()) {
+    for (uint32_t e = wid; e < n1 + n2 + n3; e += nw) {
         if (e < n1) {
             const size_t i = d.wl_conv[e];
             const uint8_t mk = d.mark[i];
@@ -252,12 +252,12 @@ __global__ void conv_finalize_kernel(const Dev d, const int nxt) {
 }
 
 // (vii) BULK bits of every cell whose type changed and of its neighbours; marks cleared
-__global__ void conv_bulk_kernel(const Dev d) {
+__device__ void conv_bulk(const Dev& d, const uint32_t wid, const uint32_t nw) {
     const uint32_t n1 = list_len(&d.sc->n_conv, d.wl_cap);
     const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
     const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n1 + n2 + n3; e += warp_count()) {
+    for (uint32_t e = wid; e < n1 + n2 + n3; e += nw) {
         const size_t i = e < n1 ? d.wl_conv[e] : (e < n1 + n2 ? d.wl_newif[e - n1] : d.wl_fromliq[e - n1 - n2]);
         if (lane >= kQ) continue;
         size_t j = i;
@@ -271,67 +271,121 @@ __global__ void conv_bulk_kernel(const Dev d) {
     }
 }
 
-void launch_conversions(const Dev& d, int nxt, cudaStream_t s) {
-    const int blocks = 2 * 152;
-    conv_filled_kernel<<<blocks, kListThreads, 0, s>>>(d);
-    switch (d.storage) {
-        case LBM_STORE_F32:
-            conv_emptied_kernel<LBM_STORE_F32><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_newif_kernel<LBM_STORE_F32><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_excess_kernel<LBM_STORE_F32><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_finalize_kernel<LBM_STORE_F32><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            break;
-        case LBM_STORE_F16DEV:
-            conv_emptied_kernel<LBM_STORE_F16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_newif_kernel<LBM_STORE_F16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_excess_kernel<LBM_STORE_F16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_finalize_kernel<LBM_STORE_F16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            break;
-        default:
-            conv_emptied_kernel<LBM_STORE_BF16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_newif_kernel<LBM_STORE_BF16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_excess_kernel<LBM_STORE_BF16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            conv_finalize_kernel<LBM_STORE_BF16DEV><<<blocks, kListThreads, 0, s>>>(d, nxt);
-            break;
-    }
-    conv_bulk_kernel<<<blocks, kListThreads, 0, s>>>(d);
+// barrier of all threads of the thread-block cluster, ordering their global-memory writes
+// before the reads that follow (release / acquire at cluster scope); a hardware barrier, not a
+// spin on memory
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
-// ------------------------------------------------------------------- bubble model
-// V_b = #gas cells of b + sum over interface cells of b of (1 - phi), in FP64; also the
-// number of interface cells.  One pass over the flags, 16 cells per thread and load; each
-// thread keeps a running sum for the bubble it last saw and flushes it on a change.
-__global__ void bubble_reduce_kernel(const Dev d, const int nxt) {
+// all conversion phases in one launch: one cluster of kClusterCtas blocks, the phases separated
+// by cluster barriers (every thread reaches every barrier)
+constexpr int kClusterCtas = 8;
+constexpr int kClusterThreads = 1024;
+template <int S>
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads) conversions_kernel(const Dev d, const int nxt) {
+    const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    conv_filled(d, wid, nw);
+    cluster_sync();
+    conv_emptied<S>(d, nxt, wid, nw);
+    cluster_sync();
+    conv_newif<S>(d, nxt, wid, nw);
+    cluster_sync();
+    conv_excess<S>(d, nxt, wid, nw);
+    cluster_sync();
+    conv_finalize<S>(d, nxt, wid, nw);
+    cluster_sync();
+    conv_bulk(d, wid, nw);
+    // the boundary list of this step has been consumed by the sweep; the end-of-step scan
+    // fills it again
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.sc->n_slow = 0;
+}
+
+void launch_conversions(const Dev& d, int nxt, cudaStream_t s) {
+    switch (d.storage) {
+        case LBM_STORE_F32: conversions_kernel<LBM_STORE_F32><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt); break;
+        case LBM_STORE_F16DEV: conversions_kernel<LBM_STORE_F16DEV><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt); break;
+        default: conversions_kernel<LBM_STORE_BF16DEV><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt); break;
+    }
+}
+
+// --------------------------------------------------------- end of step: one scan
+// One pass over the cell types as the step leaves them: the active cells the bulk sweep
+// leaves to the boundary sweep are listed for the next step; each bubble's volume
+// V_b = #gas cells + sum over its interface cells of (1 - phi) is summed in FP64 (bubble
+// model, Sec. 2.2) and the interface cells are counted.  The last block to finish then
+// sets rho_g,b = rho_g0 V_b(0) / V_b (isothermal gas of conserved mass), moves the excess
+// pool and the share the next sweep spreads over the interface cells, and resets counters.
+__global__ void end_scan_kernel(const Dev d, const int cur, const int set_reference) {
     extern __shared__ unsigned char smem_raw[];
     double* sV = reinterpret_cast<double*>(smem_raw);
     unsigned long long* sG = reinterpret_cast<unsigned long long*>(sV + d.max_bub);
     __shared__ unsigned int sIf;
+    __shared__ bool last;
     for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) { sV[b] = 0.0; sG[b] = 0ull; }
     if (threadIdx.x == 0) sIf = 0;
     __syncthreads();
-    const float* phi = d.phi[nxt];
+    const float* phi = d.phi[cur];
     const size_t nvec = d.N / 16;
+    const size_t total = nvec + (d.N % 16 ? 1 : 0);
     const uint4* fl4 = reinterpret_cast<const uint4*>(d.flags);
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
     unsigned int nif = 0;
     uint32_t cb = kNone;
     double cv = 0.0;
     unsigned long long cg = 0ull;
-    for (size_t v = blockIdx.x * (size_t)blockDim.x + threadIdx.x; v < nvec + (d.N % 16 ? 1 : 0); v += (size_t)gridDim.x * blockDim.x) {
-        uint32_t w[4];
+    // every thread of the block runs the same number of rounds (warp collectives below)
+    for (size_t base = blockIdx.x * (size_t)blockDim.x; base < total; base += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = base + threadIdx.x;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
         if (v < nvec) {
             const uint4 p = fl4[v];
             w[0] = p.x; w[1] = p.y; w[2] = p.z; w[3] = p.w;
-        } else {
-            w[0] = w[1] = w[2] = w[3] = 0u;
+        } else if (v < total) {
             for (size_t c = v * 16; c < d.N; c++) w[(c - v * 16) / 4] |= (uint32_t)d.flags[c] << (8 * ((c - v * 16) % 4));
         }
-        const uint32_t any = (w[0] | w[1] | w[2] | w[3]) & 0x06060606u;  // interface or gas bits
-        if (!any) continue;
+        // boundary cells (active, not BULK): one append per warp
+        uint32_t sel = 0u;
+#pragma unroll
+        for (int c = 0; c < 16; c++) {
+            const uint32_t t = (w[c / 4] >> (8 * (c % 4))) & 0xffu;
+            sel |= ((t & F_ACTIVE) && !(t & F_BULK)) ? (1u << c) : 0u;
+        }
+        const uint32_t cnt = __popc(sel);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += y;
+        }
+        const uint32_t tot = __shfl_sync(full, incl, 31);
+        uint32_t base_slot = 0;
+        if (lane == 31 && tot) base_slot = atomicAdd(&d.sc->n_slow, tot);
+        base_slot = __shfl_sync(full, base_slot, 31);
+        uint32_t slot = base_slot + incl - cnt;
+        while (sel) {
+            const int c = __ffs(sel) - 1;
+            sel &= sel - 1;
+            if (slot < (uint32_t)d.N) d.wl_slow[slot] = (uint32_t)(v * 16 + c);
+            slot++;
+        }
+        // bubble volumes: owners and fill levels of the chunk's gas / interface cells
+        if (!((w[0] | w[1] | w[2] | w[3]) & 0x06060606u)) continue;
+        uint32_t ob[16];
+        float pv[16];
+#pragma unroll
+        for (int c = 0; c < 16; c++) {
+            const uint8_t t = (uint8_t)(w[c / 4] >> (8 * (c % 4)));
+            ob[c] = (t & (F_IF | F_GAS)) ? d.owner[v * 16 + c] : kNone;
+            pv[c] = (t & F_IF) ? phi[v * 16 + c] : 0.f;
+        }
+#pragma unroll
         for (int c = 0; c < 16; c++) {
             const uint8_t t = (uint8_t)(w[c / 4] >> (8 * (c % 4)));
             if (!(t & (F_IF | F_GAS))) continue;
-            const size_t i = v * 16 + c;
-            const uint32_t b = d.owner[i];
+            const uint32_t b = ob[c];
             if (t & F_IF) nif++;
             if (b >= (uint32_t)d.nbub) continue;
             if (b != cb) {
@@ -343,7 +397,7 @@ __global__ void bubble_reduce_kernel(const Dev d, const int nxt) {
                 cv = 0.0;
                 cg = 0ull;
             }
-            if (t & F_IF) cv += 1.0 - (double)phi[i];
+            if (t & F_IF) cv += 1.0 - (double)pv[c];
             else cg++;
         }
     }
@@ -352,63 +406,56 @@ __global__ void bubble_reduce_kernel(const Dev d, const int nxt) {
         if (cg) atomicAdd(&sG[cb], cg);
     }
     if (nif) atomicAdd(&sIf, nif);
+    // the spheres' bins of this step are emptied (filled again by the next step)
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < d.nsph && d.bin_cnt) {
+        const Sphere& sp = d.sph[t];
+        d.bin_cnt[bin_index(d, bin_coord(d, 0, sp.x0[0]), bin_coord(d, 1, sp.x0[1]), bin_coord(d, 2, sp.x0[2]))] = 0;
+    }
     __syncthreads();
     for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
         if (sV[b] != 0.0) atomicAdd(&d.bub[b].Vif, sV[b]);
         if (sG[b]) atomicAdd(&d.bub[b].ngas, sG[b]);
     }
     if (threadIdx.x == 0 && sIf) atomicAdd(&d.sc->n_iface_acc, sIf);
+    // the last block to finish sees every block's sums
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(&d.sc->ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
+        Bubble& B = d.bub[b];
+        const double V = (double)*(volatile unsigned long long*)&B.ngas + *(volatile double*)&B.Vif;
+        B.V = V;
+        if (set_reference) { B.V0 = V; B.rho_g = (double)d.rho_g0; }
+        else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
+        else atomicOr(&d.sc->status, S_BUBBLE_GONE);
+        B.ngas = 0ull;
+        B.Vif = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        Scalars& c = *d.sc;
+        if (c.share != 0.0) c.pool = 0.0;
+        c.pool += c.pool_acc;
+        c.pool_acc = 0.0;
+        c.n_iface = *(volatile uint32_t*)&c.n_iface_acc;
+        c.n_iface_acc = 0;
+        c.share = (c.pool != 0.0 && c.n_iface > 0) ? c.pool / (double)c.n_iface : 0.0;
+        c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
+        c.ticket = 0;
+    }
 }
 
-void launch_bubbles(const Dev& d, int nxt, cudaStream_t s) {
+void launch_end_scan(const Dev& d, int cur, int set_reference, cudaStream_t s) {
     const size_t shm = (size_t)d.max_bub * (sizeof(double) + sizeof(unsigned long long));
     const size_t nvec = d.N / 16 + 1;
     int blocks = (int)((nvec + 255) / 256);
     if (blocks > 152 * 8) blocks = 152 * 8;
-    bubble_reduce_kernel<<<blocks, 256, shm, s>>>(d, nxt);
-}
-
-// end of step: gas density per bubble (isothermal, conserved gas mass), excess pool and the
-// share the next sweep spreads over the interface cells, counters reset, sphere bins cleared
-__global__ void step_end_kernel(const Dev d, const int set_reference) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (blockIdx.x == 0) {
-        for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
-            Bubble& B = d.bub[b];
-            const double V = (double)B.ngas + B.Vif;
-            B.V = V;
-            if (set_reference) { B.V0 = V; B.rho_g = (double)d.rho_g0; }
-            else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
-            else atomicOr(&d.sc->status, S_BUBBLE_GONE);
-            B.ngas = 0ull;
-            B.Vif = 0.0;
-        }
-        if (threadIdx.x == 0) {
-            Scalars& c = *d.sc;
-            if (c.share != 0.0) c.pool = 0.0;
-            c.pool += c.pool_acc;
-            c.pool_acc = 0.0;
-            c.n_iface = c.n_iface_acc;
-            c.n_iface_acc = 0;
-            c.share = (c.pool != 0.0 && c.n_iface > 0) ? c.pool / (double)c.n_iface : 0.0;
-            c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
-            c.n_slow = 0;
-        }
-    }
-    if (t < d.nsph && d.bin_cnt) {  // bins of the spheres' start-of-step positions
-        const Sphere& sp = d.sph[t];
-        d.bin_cnt[bin_index(d, bin_coord(d, 0, sp.x0[0]), bin_coord(d, 1, sp.x0[1]), bin_coord(d, 2, sp.x0[2]))] = 0;
-    }
-}
-
-void launch_step_end(const Dev& d, cudaStream_t s) {
-    const int blocks = d.nsph > 256 ? (d.nsph + 255) / 256 : 1;
-    step_end_kernel<<<blocks, 256, 0, s>>>(d, 0);
-}
-
-void launch_step_end_reference(const Dev& d, cudaStream_t s) {
-    const int blocks = d.nsph > 256 ? (d.nsph + 255) / 256 : 1;
-    step_end_kernel<<<blocks, 256, 0, s>>>(d, 1);
+    const int need = (d.nsph + 255) / 256;   // one thread per sphere for the bin reset
+    if (blocks < need) blocks = need;
+    end_scan_kernel<<<blocks, 256, shm, s>>>(d, cur, set_reference);
 }
 
 // ---------------------------------------------------------------------- curvature

@@ -19,11 +19,13 @@
 //   and odd parts; u = (sum c f + rho g/2)/rho
 //   and the conversion candidates: phi >= 1 + eps (filled) / phi <= -eps (emptied).
 //
-// Two kernels share the work.  The bulk kernel streams and collides every liquid cell whose
-// 18 neighbours are liquid, interface or beyond a wall (wall links read the cell's own
-// opposite PDF by an index select), with few registers and no branches per link; every other
-// active cell is appended to a compact per-step list that the boundary kernel processes with
-// the full link logic.
+// Two kernels share the work and run concurrently (two streams, forked and joined by events,
+// captured into the step's CUDA graph).  The bulk kernel streams and collides every liquid
+// cell whose 18 neighbours are liquid, interface or beyond a wall (wall links read the cell's
+// own opposite PDF by an index select), with few registers and no branches per link: it is
+// bound by HBM bandwidth.  Every other active cell is on a compact list built at the end of
+// the previous step (the end-of-step scan), which the boundary kernel processes with the full link logic: it is
+// bound by memory latency, so it hides under the bulk kernel.
 //
 // Sphere force and torque are reduced in FP64 without cancellation loss: per link the
 // momentum is split into the constant part -2 w_q c_q (accumulated exactly as integers,
@@ -138,10 +140,7 @@ __global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int 
     const uint32_t i = (uint32_t)x + nx * (uint32_t)y + nxy * (uint32_t)z;
     const uint8_t fl = d.flags[i];
     if (!(fl & F_ACTIVE)) return;
-    if (!(fl & F_BULK)) {
-        wl_push(d.wl_slow, &d.sc->n_slow, (uint32_t)d.N, i, &d.sc->status);
-        return;
-    }
+    if (!(fl & F_BULK)) return;   // the boundary kernel's (listed at the end of the last step)
     // neighbour coordinates (periodic wrap) and the links whose source lies beyond a wall
     const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
     const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
@@ -166,7 +165,7 @@ __global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int 
 
 // every other active cell: walls, sphere links, gas links, interface mass exchange
 template <int S>
-__global__ void __launch_bounds__(128) sweep_boundary_kernel(const Dev d, const int cur) {
+__global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, const int cur) {
     using T = typename Store<S>::T;
     const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
     T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
@@ -189,12 +188,37 @@ __global__ void __launch_bounds__(128) sweep_boundary_kernel(const Dev d, const 
             const uint8_t fl = d.flags[i];
             int x, y, z;
             cell_xyz(d, i, x, y, z);
-            float fin[kQ];
+            const bool isIF = (fl & F_IF) != 0;
+            // every load is issued before any link is resolved: neighbour indices and types,
+            // then the pulled PDFs, owners and fill levels (predicated on the types)
             float fo[kQ];
+            uint32_t src[kQ];
+            uint32_t fsv[kQ];   // neighbour type, 0xff beyond a wall
+#pragma unroll
+            for (int q = 0; q < kQ; q++) fo[q] = Store<S>::get(fa, (size_t)q * N + i);
+#pragma unroll
+            for (int q = 1; q < kQ; q++) {
+                size_t j;
+                const bool in = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q), j);
+                src[q] = in ? (uint32_t)j : (uint32_t)i;
+                fsv[q] = in ? (uint32_t)d.flags[j] : 0xffu;
+            }
+            float fv[kQ];       // pulled PDF (active source) or the source's owner (bit pattern)
+            float phn[kQ];      // fill level of an interface source (interface cells only)
+#pragma unroll
+            for (int q = 1; q < kQ; q++) {
+                const uint32_t t = fsv[q];
+                fv[q] = 0.f;
+                phn[q] = 0.f;
+                if (t != 0xffu) {
+                    if (t & F_ACTIVE) fv[q] = Store<S>::get(fa, (size_t)q * N + src[q]);
+                    else fv[q] = __uint_as_float(d.owner[src[q]]);
+                    if (isIF && (t & F_IF)) phn[q] = phia[src[q]];
+                }
+            }
             float drho0 = 0.f, j0x = 0.f, j0y = 0.f, j0z = 0.f;
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
-                fo[q] = Store<S>::get(fa, (size_t)q * N + i);
                 drho0 += fo[q];
                 j0x += cx(q) * fo[q]; j0y += cy(q) * fo[q]; j0z += cz(q) * fo[q];
             }
@@ -203,28 +227,25 @@ __global__ void __launch_bounds__(128) sweep_boundary_kernel(const Dev d, const 
             const float u0y = (j0y - 0.5f * rho0 * gy) / rho0;
             const float u0z = (j0z - 0.5f * rho0 * gz) / rho0;
             const float u0sq = u0x * u0x + u0y * u0y + u0z * u0z;
-            const bool isIF = (fl & F_IF) != 0;
             const float phix = isIF ? phia[i] : 0.f;
             const float kap = (isIF && d.kappa) ? d.kappa[i] : 0.f;
+            float fin[kQ];
             float dm = 0.f;
             fin[0] = fo[0];
 #pragma unroll
             for (int q = 1; q < kQ; q++) {
                 const int qb = opp(q);
-                size_t src;
-                if (!nbr(d, x, y, z, -cx(q), -cy(q), -cz(q), src)) {
+                const uint32_t t = fsv[q];
+                if (t == 0xffu) {
                     fin[q] = fo[qb];                                    // no-slip wall
-                    continue;
-                }
-                const uint8_t fs = d.flags[src];
-                if (fs & F_ACTIVE) {
-                    fin[q] = Store<S>::get(fa, (size_t)q * N + src);  // Eq. LBE1
+                } else if (t & F_ACTIVE) {
+                    fin[q] = fv[q];                                     // Eq. LBE1
                     if (isIF) {  // link to the neighbour x + c_qb: s (f*_q(x+c_qb) - f*_qb(x))
-                        const float s = (fs & F_LIQ) ? 1.f : 0.5f * (phix + phia[src]);
-                        dm += s * (fin[q] - fo[qb]);
+                        const float sw = (t & F_LIQ) ? 1.f : 0.5f * (phix + phn[q]);
+                        dm += sw * (fin[q] - fo[qb]);
                     }
-                } else if (fs & F_OBS) {                                // Eq. bbrule
-                    const uint32_t P = d.owner[src];
+                } else if (t & F_OBS) {                                 // Eq. bbrule
+                    const uint32_t P = __float_as_uint(fv[q]);
                     if (P >= (uint32_t)d.nsph) { fin[q] = fo[qb]; continue; }
                     if (P != acc.pid) {
                         sph_flush_direct(d, acc);
@@ -244,8 +265,8 @@ __global__ void __launch_bounds__(128) sweep_boundary_kernel(const Dev d, const 
                     acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
                     if (fl & F_LIQ) sbb += corr;
                 } else {                                                // gas: Eq. fsk
-                    const uint32_t b = d.owner[src];
-                    const float rg = b < (uint32_t)d.nbub ? (float)d.bub[b].rho_g : d.rho_g0;
+                    const uint32_t bb = __float_as_uint(fv[q]);
+                    const float rg = bb < (uint32_t)d.nbub ? (float)d.bub[bb].rho_g : d.rho_g0;
                     const float rw = rg + 6.f * d.sigma * kap;
                     const float cu = cx(q) * u0x + cy(q) * u0y + cz(q) * u0z;
                     // -f*_qb + 2 e+_q, in deviations: 2 (e+_q - w_q) - (f*_qb - w_q)
@@ -327,26 +348,32 @@ __global__ void __launch_bounds__(128) sweep_boundary_kernel(const Dev d, const 
     }
 }
 
-void launch_sweep(const Dev& d, int cur, cudaStream_t s) {
+// the boundary kernel on `side`, forked from and joined back into `s` by two events, the bulk
+// kernel on `s`; both read grid cur and write disjoint cells of grid cur ^ 1
+void launch_sweep(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
     const int bx = d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
     const int by = 128 / bx;
     dim3 block(bx, by, 1);
     dim3 grid((d.nx + bx - 1) / bx, (d.ny + by - 1) / by, d.nz);
-    const int nb = 152 * 6;
+    const int nb = 152 * 2;
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(side, fork, 0);
     switch (d.storage) {
         case LBM_STORE_F32:
+            sweep_boundary_kernel<LBM_STORE_F32><<<nb, 128, 0, side>>>(d, cur);
             sweep_bulk_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur);
-            sweep_boundary_kernel<LBM_STORE_F32><<<nb, 128, 0, s>>>(d, cur);
             break;
         case LBM_STORE_F16DEV:
+            sweep_boundary_kernel<LBM_STORE_F16DEV><<<nb, 128, 0, side>>>(d, cur);
             sweep_bulk_kernel<LBM_STORE_F16DEV><<<grid, block, 0, s>>>(d, cur);
-            sweep_boundary_kernel<LBM_STORE_F16DEV><<<nb, 128, 0, s>>>(d, cur);
             break;
         default:
+            sweep_boundary_kernel<LBM_STORE_BF16DEV><<<nb, 128, 0, side>>>(d, cur);
             sweep_bulk_kernel<LBM_STORE_BF16DEV><<<grid, block, 0, s>>>(d, cur);
-            sweep_boundary_kernel<LBM_STORE_BF16DEV><<<nb, 128, 0, s>>>(d, cur);
             break;
     }
+    cudaEventRecord(join, side);
+    cudaStreamWaitEvent(s, join, 0);
 }
 
 }  // namespace lbm
