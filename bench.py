@@ -163,6 +163,41 @@ def _oracle_error(torch, lbm, W):
     return out
 
 
+def _cpu_baseline_leg(torch, lbm, W, wl):
+    return _cpu_baseline(wl, 20 if wl.cells <= 2_200_000 else 2), _oracle_error(torch, lbm, W)
+
+
+def _storage_run(torch, lbm, args, storage):
+    """MLUPS and sweep roofline of the benchmark workload with another PDF storage"""
+    wl = _workload(args.workload, storage)
+    sim = lbm.Sim(wl)
+    sim.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sim.profile(True)
+    sim.step(min(args.steps, 400))
+    torch.cuda.synchronize()
+    sweep_ms, nsw = sim.profile_read()
+    sim.profile(False)
+    fl = sim.fields()["flags"]
+    n_act = int(((fl == lbm.CELL_LIQUID) | (fl == lbm.CELL_INTERFACE)).sum().item())
+    per_launch = n_act * (38 * 2 + 1) + (wl.cells - n_act)
+    avg_s = sweep_ms / max(1, nsw) * 1e-3
+    peak, _ = _peak_hbm()
+    st = sim.status()
+    sim.close()
+    return {"value": wl.cells * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / args.steps,
+            "sweep_achieved_gbs": per_launch / avg_s / 1e9, "sweep_frac": per_launch / avg_s / 1e9 / peak,
+            "sweep_mlups": wl.cells / avg_s / 1e6, "status": st}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -268,7 +303,7 @@ def run_gpu(args):
         traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == _sweep_sha() else None
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
-                            "kernel": "sweep_kernel", "algorithmic_bytes_per_launch": per_launch,
+                            "kernel": "sweep (sweep_bulk_kernel + sweep_boundary_kernel, concurrent)", "algorithmic_bytes_per_launch": per_launch,
                             "active_cells": n_act, "avg_launch_ms": avg_s * 1e3, "launches_timed": nsw,
                             "sweep_mlups": wl.cells / avg_s / 1e6}
         sim.close()
@@ -296,8 +331,11 @@ def run_gpu(args):
                                    "(D2H of the sphere/bubble tables, sync), final fields D2H"}
         sim2.close()
         if rank == 0 and ws == 1:
-            line["cpu_baseline"] = _cpu_baseline(wl, 20 if wl.cells <= 2_200_000 else 2)
-            line["oracle_error"] = _oracle_error(torch, lbm, W)
+            # the same workload with PDFs stored as FP16 / BF16 deviations (collisions in FP32)
+            line["reduced_storage"] = {st: _storage_run(torch, lbm, args, st) for st in ("f16dev", "bf16dev")}
+            # the CPU-baseline leg: the FP64 oracle timed on a bounded sample of the workload,
+            # and the GPU path's error against it on the 32^3 column
+            line["cpu_baseline"], line["oracle_error"] = _cpu_baseline_leg(torch, lbm, W, wl)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

@@ -42,9 +42,10 @@ __global__ void sph_prepare_kernel(const Dev d) {
     s.hasp = s.stepped;
     s.stepped = 1.0;
     const double xK[3] = {s.x[1] * K[2] - s.x[2] * K[1], s.x[2] * K[0] - s.x[0] * K[2], s.x[0] * K[1] - s.x[1] * K[0]};
+    const double inv36 = 1.0 / 36.0;
     for (int k = 0; k < 3; k++) {
-        s.F[k] = a.J[k] + K[k] / 36.0;
-        s.T[k] = a.TJ[k] + (XK[k] - xK[k]) / 36.0;
+        s.F[k] = a.J[k] + K[k] * inv36;
+        s.T[k] = a.TJ[k] + (XK[k] - xK[k]) * inv36;
         a.J[k] = 0.0; a.TJ[k] = 0.0; a.K[k] = 0ull; a.XK[k] = 0ull;
         s.x0[k] = s.x[k];
     }
@@ -324,7 +325,22 @@ __global__ void sph_substeps_fused_kernel(const Dev d, const double dt) {
         nn++;
     }
     if (nn > 12) nn = 12;
-    for (int sub = 0; sub < d.n_sub; sub++) {
+    // a sphere with no partner within reach feels no lubrication: its sub-steps have constant
+    // increments, u_k = u_0 + k du, x_n = x_0 + dt (n u_0 + n(n+1)/2 du), w_n = w_0 + n dw
+    // (equal to the sub-step recurrence up to FP64 rounding)
+    if (mine && nn == 0) {
+        const double nsub = (double)d.n_sub, tri = 0.5 * nsub * (nsub + 1.0);
+        for (int k = 0; k < 3; k++) {
+            x[k] = x[k] + dt * (nsub * u[k] + tri * du0[k]);
+            if (d.bc[k]) x[k] = wrap_pos(x[k], L[k]);
+            u[k] = u[k] + nsub * du0[k];
+            w[k] = w[k] + nsub * dw0[k];
+        }
+    }
+    // the coupled spheres step through the sub-steps together (partners are symmetric: a
+    // coupled sphere reads only coupled spheres)
+    const int any_coupled = __syncthreads_or(mine && nn > 0);
+    for (int sub = 0; any_coupled && sub < d.n_sub; sub++) {
         const int a = sub & 1, b = a ^ 1;
         Fl[0] = Fl[1] = Fl[2] = 0.0;
         for (uint32_t k = 0; k < nn; k++) {
@@ -341,7 +357,7 @@ __global__ void sph_substeps_fused_kernel(const Dev d, const double dt) {
             const double mag = -6.0 * kPi * mu * rr * rr / (rs * rs) * (1.0 / h - 1.0 / dc) * vn;
             Fl[0] += mag * nn[0]; Fl[1] += mag * nn[1]; Fl[2] += mag * nn[2];
         }
-        if (mine) {
+        if (mine && nn > 0) {
             const bool lub = Fl[0] != 0.0 || Fl[1] != 0.0 || Fl[2] != 0.0;
             for (int k = 0; k < 3; k++) {
                 u[k] = u[k] + (lub ? dt * (Fh[k] + Fl[k] + m * d.gd[k]) / m : du0[k]);
@@ -422,7 +438,8 @@ __global__ void cover_touch_kernel(const Dev d) {
         a0[k] = (float)((double)lo[k] - s.x0[k]);
         a1[k] = (float)((double)lo[k] - (s.x0[k] + off[k]));
     }
-    const float R2f = (float)R2, band = 1e-3f * (1.f + R2f);
+    // FP32 squared distances below ~50 carry an error under 1e-5 here
+    const float R2f = (float)R2, band = 1e-4f * (1.f + R2f);
     for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int ex[3] = {e % ext[0], (e / ext[0]) % ext[1], e / (ext[0] * ext[1])};
         int w[3] = {lo[0] + ex[0], lo[1] + ex[1], lo[2] + ex[2]};

@@ -73,56 +73,55 @@ __device__ __forceinline__ float warp_cell_rho(const Dev& d, const typename Stor
     return 1.f + warp_sum(v);
 }
 
-// (ii) filled cells: gas neighbours become new interface cells; emptied neighbours stay
-__device__ void conv_filled(const Dev& d, const uint32_t wid, const uint32_t nw) {
-    const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
-    const int lane = threadIdx.x & 31;
-    for (uint32_t e = wid; e < n; e += nw) {
-        const size_t i = d.wl_conv[e];
-        if (!(d.mark[i] & K_FILLED) || lane == 0 || lane >= kQ) continue;
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        size_t j;
-        if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
-        const uint8_t t = d.flags[j] & F_TYPE;
-        if (t & F_GAS) {
-            const uint8_t old = mark_or(d.mark, j, K_NEWIF);
-            if (!(old & K_NEWIF)) wl_push(d.wl_newif, &d.sc->n_newif, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
-        } else if (t & F_IF) {
-            mark_and(d.mark, j, K_EMPTIED);
-        }
-    }
-}
-
-// (iii) emptied cells: liquid neighbours become interface cells with m = rho; the smallest
-// bubble id among their emptied neighbours becomes theirs
+// (ii) + (iii) in one phase.  Filled cells: gas neighbours become new interface cells (mass
+// 0 from the start).  Emptied cells: an emptied cell with a filled neighbour stays an
+// interface cell (filling wins: it clears its own mark); otherwise its liquid neighbours
+// become interface cells with m = rho, the smallest bubble id among their emptied neighbours
+// becoming theirs.  The filled marks are final before this phase (written by the sweep).
 template <int S>
-__device__ void conv_emptied(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
+__device__ void conv_filled_emptied(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(d.f[nxt]);
     const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
     const int lane = threadIdx.x & 31;
     for (uint32_t e = wid; e < n; e += nw) {
         const size_t i = d.wl_conv[e];
-        if (!(d.mark[i] & K_EMPTIED) || lane == 0 || lane >= kQ) continue;
-        const uint32_t b = d.owner[i];
+        const uint8_t mk = d.mark[i];
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        size_t j;
-        if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j) || !(d.flags[j] & F_LIQ)) continue;
-        const uint8_t old = mark_or(d.mark, j, K_FROMLIQ);
-        if (!(old & K_FROMLIQ)) {
-            float dr = 0.f;
-            for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + j);
-            d.mass[j] = 1.f + dr;
-            wl_push(d.wl_fromliq, &d.sc->n_fromliq, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
+        size_t j = 0;
+        const bool has = lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j);
+        if (mk & K_FILLED) {
+            if (!has) continue;
+            if (d.flags[j] & F_GAS) {
+                const uint8_t old = mark_or(d.mark, j, K_NEWIF);
+                if (!(old & K_NEWIF)) {
+                    d.mass[j] = 0.f;
+                    wl_push(d.wl_newif, &d.sc->n_newif, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
+                }
+            }
+        } else if (mk & K_EMPTIED) {
+            const bool filled_nbr = __any_sync(0xffffffffu, has && (d.mark[j] & K_FILLED));
+            if (filled_nbr) {
+                if (lane == 0) mark_and(d.mark, i, K_EMPTIED);
+                continue;
+            }
+            if (!has || !(d.flags[j] & F_LIQ)) continue;
+            const uint32_t b = d.owner[i];
+            const uint8_t old = mark_or(d.mark, j, K_FROMLIQ);
+            if (!(old & K_FROMLIQ)) {
+                float dr = 0.f;
+                for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + j);
+                d.mass[j] = 1.f + dr;
+                wl_push(d.wl_fromliq, &d.sc->n_fromliq, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
+            }
+            atomicMin(&d.owner[j], b);
         }
-        atomicMin(&d.owner[j], b);
     }
 }
 
 // (iv) new interface cells from gas: f* = e(mean rho, mean u) over the neighbours that carry
-// PDFs (liquid, interface not emptied, filled), m = 0
+// PDFs (liquid, interface not emptied, filled); their m = 0 was set when they were marked
 template <int S>
 __device__ void conv_newif(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
     using T = typename Store<S>::T;
@@ -146,7 +145,6 @@ __device__ void conv_newif(const Dev& d, const int nxt, const uint32_t wid, cons
         const float rb = cnt ? rs / cnt : 1.f;
         const float ub[3] = {cnt ? ux / cnt : 0.f, cnt ? uy / cnt : 0.f, cnt ? uz / cnt : 0.f};
         if (lane < kQ) Store<S>::put(f, (size_t)lane * d.N + i, equilibrium_dev(lane, rb, ub));
-        if (lane == 0) d.mass[i] = 0.f;
     }
 }
 
@@ -286,12 +284,11 @@ template <int S>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads) conversions_kernel(const Dev d, const int nxt) {
     const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    conv_filled(d, wid, nw);
+    conv_filled_emptied<S>(d, nxt, wid, nw);
     cluster_sync();
-    conv_emptied<S>(d, nxt, wid, nw);
-    cluster_sync();
+    // new-interface initialisation writes only the new cells' PDFs; the excess phase reads
+    // only converting cells' PDFs and adds to masses: the two share a phase
     conv_newif<S>(d, nxt, wid, nw);
-    cluster_sync();
     conv_excess<S>(d, nxt, wid, nw);
     cluster_sync();
     conv_finalize<S>(d, nxt, wid, nw);

@@ -41,6 +41,7 @@ struct SphAcc {
     int K[3];
     float r[3];     // x_img - x_P of this cell
     int xi[3];      // x_img
+    float u[3], w[3];   // the sphere's velocity and angular velocity, converted once per cell
 };
 
 __device__ __forceinline__ void sph_begin(const Dev& d, SphAcc& a, uint32_t P, int x, int y, int z) {
@@ -60,6 +61,8 @@ __device__ __forceinline__ void sph_begin(const Dev& d, SphAcc& a, uint32_t P, i
         }
         a.xi[k] = xi;
         a.r[k] = (float)((double)xi - sp.x[k]);
+        a.u[k] = (float)sp.u[k];
+        a.w[k] = (float)sp.w[k];
     }
 }
 
@@ -196,12 +199,24 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
             uint32_t fsv[kQ];   // neighbour type, 0xff beyond a wall
 #pragma unroll
             for (int q = 0; q < kQ; q++) fo[q] = Store<S>::get(fa, (size_t)q * N + i);
+            {   // neighbour indices with periodic wrap; sources beyond a wall flagged 0xff
+                const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+                const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+                const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
+                const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
+                const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
+                const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
+                const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
 #pragma unroll
-            for (int q = 1; q < kQ; q++) {
-                size_t j;
-                const bool in = nbr(d, x, y, z, -cx(q), -cy(q), -cz(q), j);
-                src[q] = in ? (uint32_t)j : (uint32_t)i;
-                fsv[q] = in ? (uint32_t)d.flags[j] : 0xffu;
+                for (int q = 1; q < kQ; q++) {
+                    const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
+                    const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
+                    const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
+                    const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
+                                      (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
+                    src[q] = wall ? (uint32_t)i : sx + sy + sz;
+                    fsv[q] = wall ? 0xffu : (uint32_t)d.flags[sx + sy + sz];
+                }
             }
             float fv[kQ];       // pulled PDF (active source) or the source's owner (bit pattern)
             float phn[kQ];      // fill level of an interface source (interface cells only)
@@ -251,12 +266,11 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                         sph_flush_direct(d, acc);
                         sph_begin(d, acc, P, x, y, z);
                     }
-                    const Sphere& sp = d.sph[P];
                     const float rx = acc.r[0] - 0.5f * cx(q), ry = acc.r[1] - 0.5f * cy(q), rz = acc.r[2] - 0.5f * cz(q);
-                    const float wx = (float)sp.w[0], wy = (float)sp.w[1], wz = (float)sp.w[2];
-                    const float uwx = (float)sp.u[0] + wy * rz - wz * ry;
-                    const float uwy = (float)sp.u[1] + wz * rx - wx * rz;
-                    const float uwz = (float)sp.u[2] + wx * ry - wy * rx;
+                    const float wx = acc.w[0], wy = acc.w[1], wz = acc.w[2];
+                    const float uwx = acc.u[0] + wy * rz - wz * ry;
+                    const float uwy = acc.u[1] + wz * rx - wx * rz;
+                    const float uwz = acc.u[2] + wx * ry - wy * rx;
                     const float corr = 6.f * wgt(q) * rho0 * (cx(q) * uwx + cy(q) * uwy + cz(q) * uwz);
                     fin[q] = fo[qb] + corr;
                     // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
