@@ -31,7 +31,7 @@ FALLBACK_HBM_GBS = 6800.0
 
 # dram bytes (read + write) per sweep launch on this workload from one ncu capture, with the
 # hash of the sweep source it was taken on (null once the kernel changes)
-NCU_TRAFFIC = {"sha1": None, "bytes_per_launch": None}
+NCU_TRAFFIC = {"sha1": "d5e986cc2ca845086e7ee77c54ce3a083df059ea", "bytes_per_launch": 297955328}
 
 
 def _args():

@@ -226,7 +226,11 @@ int first_step(lbm_ctx* c) {
     cudaStream_t s = c->stream;
     prepare_sphere_kernels();
     if (!c->side_ready) {
-        if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
+        // the boundary sweep is latency-bound and small: on a stream of the highest priority its
+        // blocks take their SM slots first and finish inside the bandwidth-bound bulk sweep
+        int lo_prio = 0, hi_prio = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         c->side_ready = true;
@@ -261,7 +265,8 @@ int build_graph(lbm_ctx* c) {
         enqueue_step(c, 1, cap);
         if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = LBM_ECUDA;
     }
-    if (!rc && cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) rc = LBM_ECUDA;
+    // per-node priorities: the boundary sweep keeps its stream's priority inside the graph
+    if (!rc && cudaGraphInstantiate(&c->graph, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) rc = LBM_ECUDA;
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
     cudaGetLastError();
