@@ -72,6 +72,9 @@ def lib():
         _lib.orc_curvature.argtypes = [pp, ps]
         _lib.orc_bubble_model.argtypes = [pp, ps]
         _lib.orc_velocity.argtypes = [ctypes.c_int, ctypes.c_int]
+        _lib.orc_tangent_window.argtypes = [pp, ps, _P(ctypes.c_double), _P(ctypes.c_double), ctypes.c_double,
+                                            _P(ctypes.c_double), _P(ctypes.c_double), ctypes.c_int,
+                                            _P(ctypes.c_double), _P(ctypes.c_double)]
     return _lib
 
 
@@ -184,6 +187,32 @@ class Sim:
 
     def bubble_model(self):
         lib().orc_bubble_model(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    def tangent_window(self, nsteps, dtau=0.0, dg=(0.0, 0.0, 0.0), jdir=(1.0, 0.0, 0.0)):
+        """advance nsteps steps of the frozen liquid window with the derivative along
+        (dtau, dg); returns (J, dJ), J = sum_t jdir . sum_P F_P(t).  The current state is
+        taken as independent of the parameters."""
+        df = np.zeros((19,) + self.shape)
+        dft = np.zeros((19,) + self.shape)
+        dgv = np.ascontiguousarray(dg, dtype=np.float64)
+        jd = np.ascontiguousarray(jdir, dtype=np.float64)
+        J = ctypes.c_double()
+        dJ = ctypes.c_double()
+        rc = lib().orc_tangent_window(ctypes.byref(self.p), ctypes.byref(self.s), _ptr(df, ctypes.c_double),
+                                      _ptr(dft, ctypes.c_double), float(dtau), _ptr(dgv, ctypes.c_double),
+                                      _ptr(jd, ctypes.c_double), int(nsteps), ctypes.byref(J), ctypes.byref(dJ))
+        if rc != 0:
+            raise ValueError("the tangent window needs a liquid-only state")
+        return J.value, dJ.value
+
+    def window_objective(self, nsteps, jdir=(1.0, 0.0, 0.0)):
+        """J = sum over nsteps ordinary steps of jdir . sum_P F_P(t)"""
+        J = 0.0
+        jd = np.asarray(jdir, dtype=np.float64)
+        for _ in range(nsteps):
+            self.step(1)
+            J += float(self.forces[0].sum(axis=0) @ jd)
+        return J
 
     @property
     def forces(self):

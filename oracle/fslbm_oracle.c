@@ -895,3 +895,126 @@ void orc_lubrication(const orc_params *p, orc_state *s, double *Fl) { lubricatio
 void orc_curvature(const orc_params *p, orc_state *s) { curvature(p, s); }
 void orc_bubble_model(const orc_params *p, orc_state *s) { bubble_model(p, s, 0); }
 int orc_velocity(int q, int k) { return k == 0 ? CX[q] : (k == 1 ? CY[q] : CZ[q]); }
+
+/* ------------------------------------------------ tangent-linear (forward-mode) gradient */
+
+/* One step of the sweep together with its derivative along a parameter direction
+ * (dtau, dg): the liquid-only case with frozen cell types (walls, periodic axes, spheres
+ * held fixed, their surface velocities as wall velocities), as the differentiated window
+ * runs it.  df holds d f* / d(theta) of the post-collision state; dJ accumulates the
+ * derivative of J = sum over steps and spheres of jdir . F_P (Eqs. netforce,
+ * momentum_transfer).  Every expression is the derivative of the corresponding line of
+ * sweep(). */
+static int tangent_sweep(const orc_params *p, orc_state *s, double *df, double *dft, double dtau, const double dg[3],
+                         const double jdir[3], double *J, double *dJ)
+{
+    const long N = ncell(p);
+    const double tau = p->tau, *g = p->g;
+    const double lp = -1.0 / tau, dlp = dtau / (tau * tau);
+    const double A = 1.0 / lp + 0.5, dA = -dtau;               /* 1/lambda_+ + 1/2 = 1/2 - tau */
+    const double B = (3.0 / 16.0) / A - 0.5, dB = -(3.0 / 16.0) / (A * A) * dA;
+    const double lm = 1.0 / B, dlm = -dB / (B * B);
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                const long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
+                const uint8_t t = s->flag[i];
+                if (t & (C_IF | C_GAS)) return -1;
+                if (!(t & C_LIQ)) continue;
+                double fo[NQ], dfo[NQ], fin[NQ], dfin[NQ];
+                double rho0 = 0.0, drho0 = 0.0;
+                for (int q = 0; q < NQ; q++) {
+                    fo[q] = s->f[(long)q * N + i];
+                    dfo[q] = df[(long)q * N + i];
+                    rho0 += fo[q];
+                    drho0 += dfo[q];
+                }
+                const double xc[3] = {(double)x, (double)y, (double)z};
+                for (int q = 0; q < NQ; q++) {
+                    const long src = nbr(p, x, y, z, -CX[q], -CY[q], -CZ[q]);
+                    if (src < 0) { fin[q] = fo[opp(q)]; dfin[q] = dfo[opp(q)]; continue; }
+                    if (s->flag[src] & C_LIQ) {
+                        fin[q] = s->f[(long)q * N + src];
+                        dfin[q] = df[(long)q * N + src];
+                        continue;
+                    }
+                    /* sphere link (Eq. bbrule), wall velocity of the fixed sphere */
+                    double *S = s->sph + (long)s->owner[src] * S_LEN;
+                    const double cq[3] = {CX[q], CY[q], CZ[q]};
+                    double xw[3] = {xc[0] - 0.5 * cq[0], xc[1] - 0.5 * cq[1], xc[2] - 0.5 * cq[2]};
+                    double d[3], wxd[3], uw[3];
+                    mindiff(p, xw, S + S_X, d);
+                    cross(S + S_W, d, wxd);
+                    for (int k = 0; k < 3; k++) uw[k] = S[S_U + k] + wxd[k];
+                    const double cu = cq[0] * uw[0] + cq[1] * uw[1] + cq[2] * uw[2];
+                    fin[q] = fo[opp(q)] + 6.0 * wq(q) * rho0 * cu;
+                    dfin[q] = dfo[opp(q)] + 6.0 * wq(q) * drho0 * cu;
+                    /* momentum into the sphere and its derivative */
+                    const double a = fo[opp(q)] + fin[q], da = dfo[opp(q)] + dfin[q];
+                    for (int k = 0; k < 3; k++) {
+                        *J += jdir[k] * (-cq[k] * a);
+                        *dJ += jdir[k] * (-cq[k] * da);
+                    }
+                }
+                double rho = 0, j[3] = {0, 0, 0}, drho = 0, dj[3] = {0, 0, 0};
+                for (int q = 0; q < NQ; q++) {
+                    rho += fin[q];
+                    drho += dfin[q];
+                    j[0] += CX[q] * fin[q]; j[1] += CY[q] * fin[q]; j[2] += CZ[q] * fin[q];
+                    dj[0] += CX[q] * dfin[q]; dj[1] += CY[q] * dfin[q]; dj[2] += CZ[q] * dfin[q];
+                }
+                double u[3], du[3];
+                for (int k = 0; k < 3; k++) {
+                    u[k] = (j[k] + 0.5 * rho * g[k]) / rho;
+                    du[k] = (dj[k] + 0.5 * drho * g[k] + 0.5 * rho * dg[k]) / rho - u[k] * drho / rho;
+                }
+                const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+                const double duu = 2.0 * (u[0] * du[0] + u[1] * du[1] + u[2] * du[2]);
+                const double ug = u[0] * g[0] + u[1] * g[1] + u[2] * g[2];
+                const double dug = du[0] * g[0] + du[1] * g[1] + du[2] * g[2] + u[0] * dg[0] + u[1] * dg[1] + u[2] * dg[2];
+                for (int q = 0; q < NQ; q++) {
+                    const int qb = opp(q);
+                    const double w = wq(q);
+                    const double cu = CX[q] * u[0] + CY[q] * u[1] + CZ[q] * u[2];
+                    const double dcu = CX[q] * du[0] + CY[q] * du[1] + CZ[q] * du[2];
+                    const double cg = CX[q] * g[0] + CY[q] * g[1] + CZ[q] * g[2];
+                    const double dcg = CX[q] * dg[0] + CY[q] * dg[1] + CZ[q] * dg[2];
+                    const double ep = w * rho * (1.0 + 4.5 * cu * cu - 1.5 * uu);
+                    const double dep = w * drho * (1.0 + 4.5 * cu * cu - 1.5 * uu) + w * rho * (9.0 * cu * dcu - 1.5 * duu);
+                    const double em = w * rho * 3.0 * cu, dem = 3.0 * w * (drho * cu + rho * dcu);
+                    const double fp = 0.5 * (fin[q] + fin[qb]), dfp = 0.5 * (dfin[q] + dfin[qb]);
+                    const double fm = 0.5 * (fin[q] - fin[qb]), dfm = 0.5 * (dfin[q] - dfin[qb]);
+                    const double Gp = w * rho * (9.0 * cu * cg - 3.0 * ug);
+                    const double dGp = w * drho * (9.0 * cu * cg - 3.0 * ug) + w * rho * (9.0 * (dcu * cg + cu * dcg) - 3.0 * dug);
+                    const double Gm = w * rho * 3.0 * cg, dGm = 3.0 * w * (drho * cg + rho * dcg);
+                    s->ft[(long)q * N + i] = fin[q] + lp * (fp - ep) + lm * (fm - em) + (1.0 + 0.5 * lp) * Gp + (1.0 + 0.5 * lm) * Gm;
+                    dft[(long)q * N + i] = dfin[q] + dlp * (fp - ep) + lp * (dfp - dep) + dlm * (fm - em) + lm * (dfm - dem)
+                                         + 0.5 * dlp * Gp + (1.0 + 0.5 * lp) * dGp + 0.5 * dlm * Gm + (1.0 + 0.5 * lm) * dGm;
+                }
+            }
+    memcpy(s->f, s->ft, sizeof(double) * (size_t)NQ * (size_t)N);
+    memcpy(df, dft, sizeof(double) * (size_t)NQ * (size_t)N);
+    return 0;
+}
+
+/* nsteps steps of the frozen liquid window from the current state with the derivative along
+ * (dtau, dg): *J = sum_t jdir . sum_P F_P(t) (links between obstacle nodes of two spheres
+ * included, constant in the parameters), *dJ its derivative.  df: [19][N] scratch, zero on
+ * entry for a state that does not depend on the parameters; dft: [19][N] scratch. */
+int orc_tangent_window(const orc_params *p, orc_state *s, double *df, double *dft, double dtau, const double *dg,
+                       const double *jdir, int nsteps, double *J, double *dJ)
+{
+    *J = 0.0;
+    *dJ = 0.0;
+    for (int it = 0; it < nsteps; it++) {
+        for (int a = 0; a < p->nsph; a++)
+            for (int k = 0; k < 6; k++) s->sph[(long)a * S_LEN + S_F + k] = 0.0;
+        if (tangent_sweep(p, s, df, dft, dtau, dg, jdir, J, dJ)) return -1;
+        contact_links(p, s);
+        double Fc = 0.0;   /* contact-link part of the forces (the sweep's part is in *J) */
+        for (int a = 0; a < p->nsph; a++)
+            for (int k = 0; k < 3; k++) Fc += jdir[k] * s->sph[(long)a * S_LEN + S_F + k];
+        *J += Fc;
+    }
+    return 0;
+}
