@@ -166,6 +166,30 @@ int lbm_mass_budget(lbm_ctx* ctx, double out[5]);
 /* Latched status bits (LBM_S_*) into *status (host).  Synchronises. */
 int lbm_status(lbm_ctx* ctx, uint32_t* status);
 
+/* ---- differentiation over a window with frozen cell types ------------------------------
+ * The window is liquid only (no bubbles), the spheres fixed (LBM_SPHERES_FIXED; their u and w
+ * still act as surface velocities) and the PDFs stored in FP32, so no cell changes type; else
+ * these calls return LBM_ESTATE.  States are post-collision PDFs as FP32 deviations
+ * f*_q - w_q, [19][N], device, in the D3Q19 order of lbm_export_state.  The objective is
+ * J = sum over the window's steps t of jdir . (sum over spheres of the momentum-exchange
+ * force F_P(t), Eqs. netforce and momentum_transfer). */
+
+/* One forward step of the window from f_in to f_out (device, distinct): streaming with
+ * bounce-back at walls and spheres, then the TRT/Guo collision (Eqs. LBE1, bbrule, LBE2), the
+ * same arithmetic as lbm_step.  Used to recompute states between checkpoints.  Asynchronous. */
+int lbm_forward_frozen(lbm_ctx* ctx, const float* f_in, float* f_out);
+
+/* One reverse step: given the forward state f_fwd = f*(t) and adj_in = dJ/df*(t+1), writes
+ * adj_out = dJ/df*(t) (device [19][N], distinct from adj_in; only liquid cells' entries are
+ * defined) = (d f*(t+1) / d f*(t))^T adj_in + d(jdir . F(t+1)) / d f*(t), and adds
+ * adj_in . d f*(t+1)/d theta, theta = (g, tau), to FP64 accumulators on the device, which it
+ * clears first unless accumulate != 0 (lambda_- follows tau through the magic relation).
+ * jdir[3]: host.  With dJdg and dJdtau NULL the call is asynchronous; with both non-NULL
+ * (host) it synchronises the stream and returns there the accumulated d/dg[3] and d/dtau.
+ * LBM_EINVAL for NULL device pointers, adj_in == adj_out or only one of dJdg, dJdtau NULL. */
+int lbm_adjoint_step(lbm_ctx* ctx, const float* f_fwd, const float* adj_in, float* adj_out, const double jdir[3],
+                     int accumulate, double dJdg[3], double* dJdtau);
+
 /* Timing of the sweep kernel (the dominant one): while on != 0, lbm_step launches steps
  * one by one (no CUDA graph) and records a CUDA event pair around each sweep launch on the
  * stream it runs on. */

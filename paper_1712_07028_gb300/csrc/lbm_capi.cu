@@ -26,6 +26,9 @@ struct lbm_ctx {
     uint64_t launches;
     int per_step;
     double* geo_dev;
+    float* adj_srho;
+    double* adj_part;
+    bool moving_walls;
     Sphere* sph_stage;
     Scalars* sc_stage;
     Bubble* bub_stage;
@@ -73,7 +76,8 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, acc, sc, wl[4], wl_slow, bin_cnt, bin_ids, npairs, pairs, geo, total;
+    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, acc, sc, wl[4], wl_slow, bin_cnt, bin_ids, npairs, pairs, geo,
+        adj_srho, adj_part, total;
     size_t N, wl_cap, nbins_max;
 };
 
@@ -106,6 +110,8 @@ Layout layout_of(const lbm_params* p) {
     L.npairs = take(4 * (size_t)p->max_spheres);
     L.pairs = take(4 * (size_t)p->max_spheres * kPairCap);
     L.geo = take(sizeof(double) * 4 * (size_t)p->max_bubbles);
+    L.adj_srho = take(4 * L.N);
+    L.adj_part = take(sizeof(double) * 5 * kAdjSlots);
     L.total = o;
     return L;
 }
@@ -222,6 +228,11 @@ int first_step(lbm_ctx* c) {
     d.npairs = (uint32_t*)(a + L.npairs);
     d.pairs = (uint32_t*)(a + L.pairs);
     c->geo_dev = (double*)(a + L.geo);
+    c->adj_srho = (float*)(a + L.adj_srho);
+    c->adj_part = (double*)(a + L.adj_part);
+    c->moving_walls = false;
+    for (const Sphere& sp : c->sph_init)
+        for (int k = 0; k < 3; k++) c->moving_walls |= sp.u[k] != 0.0 || sp.w[k] != 0.0;
 
     cudaStream_t s = c->stream;
     prepare_sphere_kernels();
@@ -479,6 +490,47 @@ int lbm_status(lbm_ctx* c, uint32_t* status) {
     int rc = sync_tables(c);
     if (rc) return rc;
     *status = c->sc_stage->status;
+    return LBM_OK;
+}
+
+// the frozen liquid window the adjoint differentiates: FP32 storage, no bubbles, fixed spheres
+static int adjoint_ready(lbm_ctx* c) {
+    if (!c->started) return LBM_ESTATE;
+    if (c->p.storage != LBM_STORE_F32 || c->d.nbub != 0 || c->p.sphere_mode != LBM_SPHERES_FIXED) return LBM_ESTATE;
+    return LBM_OK;
+}
+
+int lbm_forward_frozen(lbm_ctx* c, const float* f_in, float* f_out) {
+    if (!c || !f_in || !f_out || f_in == f_out) return LBM_EINVAL;
+    int rc = adjoint_ready(c);
+    if (rc) return rc;
+    launch_frozen_forward(c->d, f_in, f_out, c->stream);
+    return launched(c, 1);
+}
+
+int lbm_adjoint_step(lbm_ctx* c, const float* f_fwd, const float* adj_in, float* adj_out, const double jdir[3],
+                     int accumulate, double dJdg[3], double* dJdtau) {
+    if (!c || !f_fwd || !adj_in || !adj_out || !jdir || adj_in == adj_out || (!dJdg) != (!dJdtau)) return LBM_EINVAL;
+    int rc = adjoint_ready(c);
+    if (rc) return rc;
+    cudaStream_t s = c->stream;
+    if (!accumulate && (rc = cuda_fail(cudaMemsetAsync(c->adj_part, 0, sizeof(double) * 5 * kAdjSlots, s)))) return rc;
+    const float jd[3] = {(float)jdir[0], (float)jdir[1], (float)jdir[2]};
+    launch_adjoint(c->d, f_fwd, adj_in, adj_out, c->adj_srho, jd, c->adj_part, c->moving_walls, s);
+    if ((rc = launched(c, c->moving_walls ? 2 : 1))) return rc;
+    if (!dJdg) return LBM_OK;
+    double part[5 * kAdjSlots];
+    if ((rc = cuda_fail(cudaMemcpyAsync(part, c->adj_part, sizeof part, cudaMemcpyDeviceToHost, s)))) return rc;
+    c->d2h_bytes += sizeof part;
+    if ((rc = cuda_fail(cudaStreamSynchronize(s)))) return rc;
+    double sum[5] = {0, 0, 0, 0, 0};
+    for (int k = 0; k < kAdjSlots; k++)
+        for (int m = 0; m < 5; m++) sum[m] += part[5 * k + m];
+    // lambda_+ = -1/tau; lambda_- = 1/B, B = (3/16)/A - 1/2, A = 1/lambda_+ + 1/2 = 1/2 - tau
+    const double tau = c->p.tau, A = 0.5 - tau, B = (3.0 / 16.0) / A - 0.5;
+    const double dlp = 1.0 / (tau * tau), dlm = -(3.0 / 16.0) / (A * A * B * B);
+    for (int k = 0; k < 3; k++) dJdg[k] = sum[k];
+    *dJdtau = sum[3] * dlp + sum[4] * dlm;
     return LBM_OK;
 }
 

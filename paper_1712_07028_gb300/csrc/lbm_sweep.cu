@@ -83,51 +83,6 @@ __device__ __forceinline__ void sph_flush_direct(const Dev& d, const SphAcc& a) 
 }
 
 
-// moments, Guo-shifted velocity and the TRT collision of one cell, all on deviations f - w;
-// the post-collision deviations go to grid fb
-template <int S>
-__device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T* __restrict__ fb, size_t i, const float (&fin)[kQ]) {
-    const size_t N = d.N;
-    const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
-    float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
-#pragma unroll
-    for (int q = 0; q < kQ; q++) {
-        drho += fin[q];
-        jx += cx(q) * fin[q]; jy += cy(q) * fin[q]; jz += cz(q) * fin[q];
-    }
-    const float rho = 1.f + drho;
-    if (!(rho > 0.f)) atomicOr(&d.sc->status, S_UNSTABLE);
-    const float inv = 1.f / rho;
-    const float ux = (jx + 0.5f * rho * gx) * inv;
-    const float uy = (jy + 0.5f * rho * gy) * inv;
-    const float uz = (jz + 0.5f * rho * gz) * inv;
-    const float usq = ux * ux + uy * uy + uz * uz;
-    const float ug = ux * gx + uy * gy + uz * gz;
-    const float lp = d.lp, lm = d.lm;
-    const float cp = 1.f + 0.5f * lp, cm = 1.f + 0.5f * lm;
-    {
-        // q = 0: f+ = f, e+ - w = w (rho - 1 - 1.5 rho u.u), G+ = -3 w rho u.g
-        const float w = wgt(0);
-        const float ep = w * (drho - 1.5f * rho * usq);
-        Store<S>::put(fb, i, fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug)));
-    }
-#pragma unroll
-    for (int q = 1; q < kQ; q += 2) {
-        const int qb = q + 1;
-        const float w = wgt(q);
-        const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-        const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
-        const float ep = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));   // e+_q - w_q
-        const float em = w * rho * 3.f * cu;                                  // e-_q
-        const float fp = 0.5f * (fin[q] + fin[qb]);
-        const float fm = 0.5f * (fin[q] - fin[qb]);
-        const float a = lp * (fp - ep) + cp * (w * rho * (9.f * cu * cg - 3.f * ug));
-        const float b = lm * (fm - em) + cm * (w * rho * 3.f * cg);
-        Store<S>::put(fb, (size_t)q * N + i, fin[q] + a + b);
-        Store<S>::put(fb, (size_t)qb * N + i, fin[qb] + a - b);
-    }
-}
-
 // every liquid cell whose neighbours all carry PDFs or lie beyond a wall; other active cells
 // go to the boundary list
 template <int S>

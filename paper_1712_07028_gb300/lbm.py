@@ -23,7 +23,8 @@ S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW = 1, 2, 4, 8
 # every entry point include/lbm.h declares
 EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_step",
            "lbm_forces", "lbm_spheres", "lbm_bubbles", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
-           "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count", "lbm_bubble_volumes_noalloc", "lbm_destroy", "lbm_strerror")
+           "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count",
+           "lbm_bubble_volumes_noalloc", "lbm_forward_frozen", "lbm_adjoint_step", "lbm_destroy", "lbm_strerror")
 
 
 class Params(ctypes.Structure):
@@ -73,6 +74,8 @@ def load():
     L.lbm_copy_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.lbm_profile_read.argtypes = [vp, pd, ctypes.POINTER(ctypes.c_uint64)]
     L.lbm_bubble_volumes_noalloc.argtypes = [vp, vp, vp, sz, i32, vp, vp]
+    L.lbm_forward_frozen.argtypes = [vp, vp, vp]
+    L.lbm_adjoint_step.argtypes = [vp, vp, vp, vp, pd, i32, pd, pd]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_strerror.argtypes = [i32]
     L.lbm_strerror.restype = ctypes.c_char_p
@@ -228,6 +231,25 @@ class Sim:
         n = ctypes.c_uint64()
         _check("lbm_launch_count", load().lbm_launch_count(self.ctx, ctypes.byref(n)))
         return n.value
+
+    def forward_frozen(self, f_in, f_out):
+        """one step of the frozen liquid window on FP32 deviation tensors [19,z,y,x] (device)"""
+        self._bind_stream()
+        _check("lbm_forward_frozen", load().lbm_forward_frozen(self.ctx, ctypes.c_void_p(f_in.data_ptr()),
+                                                               ctypes.c_void_p(f_out.data_ptr())))
+
+    def adjoint_step(self, f_fwd, adj_in, adj_out, jdir, accumulate=True, read=False):
+        """one reverse step (adj_out = dJ/df*(t) from f_fwd = f*(t), adj_in = dJ/df*(t+1));
+        with read=True returns the accumulated (dJ/dg [3], dJ/dtau)"""
+        self._bind_stream()
+        jd = _v3(jdir)
+        dg = np.zeros(3)
+        dt = ctypes.c_double()
+        _check("lbm_adjoint_step", load().lbm_adjoint_step(
+            self.ctx, ctypes.c_void_p(f_fwd.data_ptr()), ctypes.c_void_p(adj_in.data_ptr()),
+            ctypes.c_void_p(adj_out.data_ptr()), _dp(jd), 1 if accumulate else 0, _dp(dg) if read else None,
+            ctypes.byref(dt) if read else None))
+        return (dg, dt.value) if read else None
 
     def close(self):
         if getattr(self, "ctx", None) and self.ctx.value:
