@@ -198,6 +198,79 @@ def _storage_run(torch, lbm, args, storage):
             "sweep_mlups": wl.cells / avg_s / 1e6, "status": st}
 
 
+def _adjoint_run(torch, lbm, W):
+    """the differentiation path on the 96^3 periodic array of 27 fixed spheres: per-launch
+    time and HBM roofline of the frozen replay step and of the reverse step, and the wall time
+    of a 500-step window gradient (forward with checkpoints every 50, replay, reverse)"""
+    from paper_1712_07028_gb300 import adjoint as A
+    wl = W.periodic_array_c2()
+    sim = lbm.Sim(wl)
+    sim.step(0)
+    st = sim.export_state()
+    n_liq = int((st["flags"] == lbm.CELL_LIQUID).sum().item())
+    # four states (268 MB, twice the L2) so that every call streams its operands from HBM
+    fs = [st["f"]] + [torch.empty_like(st["f"]) for _ in range(3)]
+    la, lb = torch.zeros_like(fs[0]), torch.zeros_like(fs[0])
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    k, reps = 50, 8
+
+    def timed(fn):
+        """seconds per call of fn (four of the timed steps): k calls captured in a
+        CUDA graph (the library forks its second stream inside the capture), replayed after
+        warm-up, so that host-side call overhead does not enter the kernel time"""
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            for _ in range(k):
+                fn()
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / (k * reps) * 1e-3
+
+    def fwd():
+        for j in range(4):
+            sim.forward_frozen(fs[j], fs[(j + 1) % 4])
+
+    def rev():
+        for j in range(4):
+            sim.adjoint_step(fs[3 - j], la if j % 2 == 0 else lb, lb if j % 2 == 0 else la, (1.0, 0.0, 0.0))
+
+    t_f = timed(fwd) / 4
+    t_r = timed(rev) / 4
+    peak, kind = _peak_hbm()
+    inactive = wl.cells - n_liq
+    by_f = n_liq * (2 * 19 * 4 + 1) + inactive
+    by_r = n_liq * (3 * 19 * 4 + 1) + inactive
+    sim.close()
+    n, every = 500, 50
+    sim = lbm.Sim(wl)
+    sim.step(0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    J, dtau, dg = A.window_gradient(sim, n, (1.0, 0.0, 0.0), every)
+    torch.cuda.synchronize()
+    t_win = time.perf_counter() - t0
+    sim.close()
+    return {"workload": wl.name, "liquid_cells": n_liq,
+            "replay_step": {"ms": t_f * 1e3, "bytes": by_f, "achieved": by_f / t_f / 1e9, "unit": "GB/s",
+                            "frac": by_f / t_f / 1e9 / peak, "peak_source": kind},
+            "reverse_step": {"ms": t_r * 1e3, "bytes": by_r, "achieved": by_r / t_r / 1e9, "unit": "GB/s",
+                             "frac": by_r / t_r / 1e9 / peak, "peak_source": kind},
+            "window": {"steps": n, "checkpoint_every": every, "seconds": t_win,
+                       "mlups": wl.cells * n / t_win / 1e6,
+                       "includes": "forward steps with per-step force read (sync) and checkpoints, replay, reverse",
+                       "J": J, "dJ_dtau": dtau, "dJ_dg": list(dg)}}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -333,6 +406,8 @@ def run_gpu(args):
         if rank == 0 and ws == 1:
             # the same workload with PDFs stored as FP16 / BF16 deviations (collisions in FP32)
             line["reduced_storage"] = {st: _storage_run(torch, lbm, args, st) for st in ("f16dev", "bf16dev")}
+            # the differentiation path (frozen liquid window) on its own workload
+            line["adjoint"] = _adjoint_run(torch, lbm, W)
             # the CPU-baseline leg: the FP64 oracle timed on a bounded sample of the workload,
             # and the GPU path's error against it on the 32^3 column
             line["cpu_baseline"], line["oracle_error"] = _cpu_baseline_leg(torch, lbm, W, wl)

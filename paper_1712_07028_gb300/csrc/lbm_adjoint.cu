@@ -75,19 +75,13 @@ __device__ __forceinline__ void frozen_pull(const Dev& d, const float* __restric
         if (P >= (uint32_t)d.nsph) { fin[q] = fo[opp(q)]; continue; }
         if (P != pid) {   // x - x_P with the image of the cell nearest to the centre
             pid = P;
-            const Sphere& sp = d.sph[P];
+            const SphLink l = d.sphl[P];
             const int c[3] = {x, y, z};
-            const int L[3] = {d.nx, d.ny, d.nz};
+            int img[3];
+            sph_offset(d, l, c, img, r);
             for (int k = 0; k < 3; k++) {
-                int xi = c[k];
-                if (d.bc[k]) {
-                    const double dd = sp.x[k] - (double)xi;
-                    if (dd > 0.5 * L[k]) xi += L[k];
-                    else if (dd < -0.5 * L[k]) xi -= L[k];
-                }
-                r[k] = (float)((double)xi - sp.x[k]);
-                us[k] = (float)sp.u[k];
-                ws[k] = (float)sp.w[k];
+                us[k] = l.u[k];
+                ws[k] = l.w[k];
             }
         }
         const float rx = r[0] - 0.5f * cx(q), ry = r[1] - 0.5f * cy(q), rz = r[2] - 0.5f * cz(q);
@@ -99,10 +93,16 @@ __device__ __forceinline__ void frozen_pull(const Dev& d, const float* __restric
     }
 }
 
-// one forward step of the frozen liquid window on FP32 deviation buffers (f_in -> f_out)
-__global__ void frozen_forward_kernel(const Dev d, const float* __restrict__ f_in, float* __restrict__ f_out) {
-    for (size_t ii = blockIdx.x * (size_t)blockDim.x + threadIdx.x; ii < d.N; ii += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t i = (uint32_t)ii;
+// the frozen window's cells split as in the forward sweep: BULK liquid cells (every neighbour
+// liquid or beyond a wall) in a lean kernel over the grid, the listed others (next to a sphere)
+// in a general one; the list is the one the last lbm_step built, valid while no cell changes type
+
+// the boundary cells' forward step (the bulk cells run the forward sweep's own bulk kernel)
+__global__ void __launch_bounds__(128) frozen_boundary_kernel(const Dev d, const float* __restrict__ f_in,
+                                                              float* __restrict__ f_out) {
+    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)d.N);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t i = d.wl_slow[k];
         if (!(d.flags[i] & F_LIQ)) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
@@ -114,24 +114,199 @@ __global__ void frozen_forward_kernel(const Dev d, const float* __restrict__ f_i
     }
 }
 
-void launch_frozen_forward(const Dev& d, const float* f_in, float* f_out, cudaStream_t s) {
-    frozen_forward_kernel<<<152 * 16, 256, 0, s>>>(d, f_in, f_out);
+void launch_frozen_forward(const Dev& d, const float* f_in, float* f_out, cudaStream_t s, cudaStream_t side,
+                           cudaEvent_t fork, cudaEvent_t join) {
+    Dev dd = d;   // the forward bulk kernel reads grid 0 and writes grid 1
+    dd.f[0] = const_cast<float*>(f_in);
+    dd.f[1] = f_out;
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(side, fork, 0);
+    frozen_boundary_kernel<<<152 * 2, 128, 0, side>>>(dd, f_in, f_out);
+    launch_sweep_bulk_f32(dd, 0, s);
+    cudaEventRecord(join, side);
+    cudaStreamWaitEvent(s, join, 0);
 }
 
-// reverse step; parameter-gradient partial sums go to kAdjSlots FP64 slots (block id mod
-// kAdjSlots, few blocks per slot): part[slot][0..2] = lam . dC/dg, part[slot][3] =
-// lam . dC/dlambda_+, part[slot][4] = lam . dC/dlambda_-
+// ---- reverse step -------------------------------------------------------------------------
+// Parameter-gradient partial sums go to kAdjSlots FP64 slots (block id mod kAdjSlots):
+// part[slot][0..2] = lam . dC/dg, part[slot][3] = lam . dC/dlambda_+, part[slot][4] = lam . dC/dlambda_-
 
-__global__ void adjoint_kernel(const Dev d, const float* __restrict__ f, const float* __restrict__ lam_in,
-                               float* __restrict__ lam_out, float* __restrict__ srho, const float jx, const float jy,
-                               const float jz, const int moving, double* part) {
-    const size_t N = d.N;
+// (dC/dfin)^T lam of the TRT + Guo collision of one cell, as dL/dfin_q = mu_q(lam) + base +
+// (Lu . c_q) inv, mu the direct (pair-local) part; the parameter terms are added to acc
+struct AdjOut {
+    float base, lx, ly, lz, inv;
+};
+
+__device__ __forceinline__ AdjOut collide_adjoint(const Dev& d, const float (&fin)[kQ], const float (&lam)[kQ],
+                                                  float (&acc)[5]) {
     const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
     const float lp = d.lp, lm = d.lm;
     const float cp = 1.f + 0.5f * lp, cm = 1.f + 0.5f * lm;
+    float drho = 0.f, jxm = 0.f, jym = 0.f, jzm = 0.f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        drho += fin[q];
+        jxm += cx(q) * fin[q]; jym += cy(q) * fin[q]; jzm += cz(q) * fin[q];
+    }
+    const float rho = 1.f + drho, inv = 1.f / rho;
+    const float ux = (jxm + 0.5f * rho * gx) * inv, uy = (jym + 0.5f * rho * gy) * inv, uz = (jzm + 0.5f * rho * gz) * inv;
+    const float usq = ux * ux + uy * uy + uz * uz, ug = ux * gx + uy * gy + uz * gz;
+    float Lrho, Lux, Luy, Luz;   // lam . dC/drho, lam . dC/du at fixed fin
+    float Gx, Gy, Gz;            // lam . dC/dg at fixed u
+    float Tp, Tm;                // lam . dC/dlambda_+, lam . dC/dlambda_-
+    {
+        const float w = wgt(0), L0 = lam[0];
+        const float ep = w * (drho - 1.5f * rho * usq), Gp = w * rho * (-3.f * ug);
+        Lrho = L0 * (-lp * w * (1.f - 1.5f * usq) + cp * w * (-3.f * ug));
+        const float a = L0 * w * rho * 3.f;
+        Lux = a * (lp * ux - cp * gx);
+        Luy = a * (lp * uy - cp * gy);
+        Luz = a * (lp * uz - cp * gz);
+        Gx = -a * cp * ux;
+        Gy = -a * cp * uy;
+        Gz = -a * cp * uz;
+        Tp = L0 * ((fin[0] - ep) + 0.5f * Gp);
+        Tm = 0.f;
+    }
+#pragma unroll
+    for (int q = 1; q < kQ; q += 2) {
+        const int qb = q + 1;
+        const float w = wgt(q);
+        const float Lp = lam[q] + lam[qb], Lm = lam[q] - lam[qb];
+        const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
+        const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
+        const float ep = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));
+        const float em = w * rho * 3.f * cu;
+        const float Gp = w * rho * (9.f * cu * cg - 3.f * ug), Gm = w * rho * 3.f * cg;
+        const float fp = 0.5f * (fin[q] + fin[qb]), fm = 0.5f * (fin[q] - fin[qb]);
+        // d/drho of e+, e-, G+, G-
+        Lrho += Lp * (-lp * w * (1.f + 4.5f * cu * cu - 1.5f * usq) + cp * w * (9.f * cu * cg - 3.f * ug)) +
+                Lm * (-lm * 3.f * w * cu + cm * 3.f * w * cg);
+        // d/du: e+ -> w rho (9 cu c - 3 u), e- -> 3 w rho c, G+ -> w rho (9 cg c - 3 g)
+        const float wr = w * rho;
+        const float ap = Lp * wr * 9.f * (cp * cg - lp * cu) - Lm * lm * 3.f * wr;   // along c_q
+        const float bp = Lp * wr * 3.f;                                                // along (lp u - cp g)
+        Lux += ap * cx(q) + bp * (lp * ux - cp * gx);
+        Luy += ap * cy(q) + bp * (lp * uy - cp * gy);
+        Luz += ap * cz(q) + bp * (lp * uz - cp * gz);
+        // d/dg at fixed u: G+ -> w rho (9 cu c - 3 u), G- -> 3 w rho c
+        const float ag = Lp * cp * wr * 9.f * cu + Lm * cm * 3.f * wr;
+        const float bg = -Lp * cp * wr * 3.f;
+        Gx += ag * cx(q) + bg * ux;
+        Gy += ag * cy(q) + bg * uy;
+        Gz += ag * cz(q) + bg * uz;
+        Tp += Lp * ((fp - ep) + 0.5f * Gp);
+        Tm += Lm * ((fm - em) + 0.5f * Gm);
+    }
+    // u = (j + rho g/2)/rho: du/dfin_k = (c_k + g/2 - u)/rho, du/dg = I/2
+    acc[0] += Gx + 0.5f * Lux;
+    acc[1] += Gy + 0.5f * Luy;
+    acc[2] += Gz + 0.5f * Luz;
+    acc[3] += Tp;
+    acc[4] += Tm;
+    AdjOut o;
+    o.base = Lrho + (Lux * (0.5f * gx - ux) + Luy * (0.5f * gy - uy) + Luz * (0.5f * gz - uz)) * inv;
+    o.lx = Lux * inv;
+    o.ly = Luy * inv;
+    o.lz = Luz * inv;
+    o.inv = inv;
+    return o;
+}
+
+// dL/dfin_q of a cell from its adjoint variables lam and the collision adjoint o
+__device__ __forceinline__ float adj_in_q(const Dev& d, int q, const float (&lam)[kQ], const AdjOut& o) {
+    float mu;
+    if (q == 0) {
+        mu = lam[0] * (1.f + d.lp);
+    } else {
+        const int qa = (q & 1) ? q : q - 1, qb = qa + 1;
+        const float Lp = lam[qa] + lam[qb], Lm = lam[qa] - lam[qb];
+        mu = lam[q] + 0.5f * d.lp * Lp + ((q & 1) ? 0.5f : -0.5f) * d.lm * Lm;
+    }
+    return mu + o.base + o.lx * cx(q) + o.ly * cy(q) + o.lz * cz(q);
+}
+
+// per-block sums of the five parameter terms into one of kAdjSlots FP64 slots
+__device__ __forceinline__ void adj_flush(float (&acc)[5], double* part) {
+    __shared__ float red[5][32];
+    const int lane = threadIdx.x & 31;
+    const int nthreads = blockDim.x * blockDim.y;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    const int wid = tid >> 5;
+#pragma unroll
+    for (int k = 0; k < 5; k++) {
+        const float v = warp_sum(acc[k]);
+        if ((tid & 31) == 0) red[k][wid] = v;
+    }
+    (void)lane;
+    __syncthreads();
+    if (tid < 5) {
+        double t = 0.0;
+        for (int w = 0; w < (nthreads + 31) >> 5; w++) t += (double)red[tid][w];
+        const unsigned blk = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+        if (t != 0.0) atomicAdd(&part[(blk % kAdjSlots) * 5 + tid], t);
+    }
+}
+
+// reverse step of the BULK cells: pull with the wall index select, collision adjoint, and the
+// transposed pull (push) with the same select; no sphere links
+__global__ void __launch_bounds__(128, 4) adjoint_bulk_kernel(const Dev d, const float* __restrict__ f,
+                                                           const float* __restrict__ lam_in,
+                                                           float* __restrict__ lam_out, double* part) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    for (size_t ii = blockIdx.x * (size_t)blockDim.x + threadIdx.x; ii < N; ii += (size_t)gridDim.x * blockDim.x) {
-        const uint32_t i = (uint32_t)ii;
+    if (x < d.nx && y < d.ny) {
+        const size_t N = d.N;
+        const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+        const uint32_t i = (uint32_t)x + nx * (uint32_t)y + nxy * (uint32_t)z;
+        const uint8_t fl = d.flags[i];
+        if ((fl & F_LIQ) && (fl & F_BULK)) {
+            const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+            const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
+            const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
+            const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
+            const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
+            const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
+            float fin[kQ], lam[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; q++) {
+                const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
+                const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
+                const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
+                const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
+                                  (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
+                fin[q] = f[(size_t)(wall ? opp(q) : q) * N + (wall ? i : sx + sy + sz)];
+                lam[q] = lam_in[(size_t)q * N + i];
+            }
+            const AdjOut o = collide_adjoint(d, fin, lam, acc);
+#pragma unroll
+            for (int q = 0; q < kQ; q++) {
+                const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
+                const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
+                const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
+                const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
+                                  (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
+                lam_out[(size_t)(wall ? opp(q) : q) * N + (wall ? i : sx + sy + sz)] = adj_in_q(d, q, lam, o);
+            }
+        }
+    }
+    adj_flush(acc, part);
+}
+
+// reverse step of the listed cells (next to a sphere): general links, the J source of the
+// sphere links and, for moving surfaces, the rho0 sums srho
+__global__ void __launch_bounds__(128) adjoint_boundary_kernel(const Dev d, const float* __restrict__ f,
+                                                               const float* __restrict__ lam_in,
+                                                               float* __restrict__ lam_out, float* __restrict__ srho,
+                                                               const float jx, const float jy, const float jz,
+                                                               const int moving, double* part) {
+    const size_t N = d.N;
+    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)N);
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t i = d.wl_slow[k];
         if (!(d.flags[i] & F_LIQ)) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
@@ -139,116 +314,56 @@ __global__ void adjoint_kernel(const Dev d, const float* __restrict__ f, const f
         uint8_t kind[kQ];
         uint32_t src[kQ];
         frozen_pull(d, f, i, x, y, z, fin, fo, kind, src, cw, rho0);
-        float drho = 0.f, jxm = 0.f, jym = 0.f, jzm = 0.f;
-#pragma unroll
-        for (int q = 0; q < kQ; q++) {
-            drho += fin[q];
-            jxm += cx(q) * fin[q]; jym += cy(q) * fin[q]; jzm += cz(q) * fin[q];
-        }
-        const float rho = 1.f + drho, inv = 1.f / rho;
-        const float ux = (jxm + 0.5f * rho * gx) * inv, uy = (jym + 0.5f * rho * gy) * inv, uz = (jzm + 0.5f * rho * gz) * inv;
-        const float usq = ux * ux + uy * uy + uz * uz, ug = ux * gx + uy * gy + uz * gz;
-        float lam[kQ], mu[kQ];
+        float lam[kQ];
 #pragma unroll
         for (int q = 0; q < kQ; q++) lam[q] = lam_in[(size_t)q * N + i];
-        // collision adjoint: direct part, then the parts through rho and u
-        float Lrho = 0.f, Lux = 0.f, Luy = 0.f, Luz = 0.f;   // lam . dH/drho, lam . dH/du
-        float Gx = 0.f, Gy = 0.f, Gz = 0.f;                  // lam . dH/dg at fixed u
-        float Tp = 0.f, Tm = 0.f;                            // lam . df*/dlambda_+, lam . df*/dlambda_-
-        {
-            const float w = wgt(0);
-            const float ep = w * (drho - 1.5f * rho * usq), Gp = w * rho * (-3.f * ug);
-            mu[0] = lam[0] * (1.f + lp);
-            Lrho += lam[0] * (-lp * w * (1.f - 1.5f * usq) + cp * w * (-3.f * ug));
-            Lux += lam[0] * (-lp * w * rho * (-3.f * ux) + cp * w * rho * (-3.f * gx));
-            Luy += lam[0] * (-lp * w * rho * (-3.f * uy) + cp * w * rho * (-3.f * gy));
-            Luz += lam[0] * (-lp * w * rho * (-3.f * uz) + cp * w * rho * (-3.f * gz));
-            Gx += lam[0] * cp * w * rho * (-3.f * ux);
-            Gy += lam[0] * cp * w * rho * (-3.f * uy);
-            Gz += lam[0] * cp * w * rho * (-3.f * uz);
-            Tp += lam[0] * ((fin[0] - ep) + 0.5f * Gp);
-        }
-#pragma unroll
-        for (int q = 1; q < kQ; q += 2) {
-            const int qb = q + 1;
-            const float w = wgt(q);
-            const float Lp = lam[q] + lam[qb], Lm = lam[q] - lam[qb];
-            mu[q] = lam[q] + 0.5f * lp * Lp + 0.5f * lm * Lm;
-            mu[qb] = lam[qb] + 0.5f * lp * Lp - 0.5f * lm * Lm;
-            const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-            const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
-            const float ep = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));
-            const float em = w * rho * 3.f * cu;
-            const float Gp = w * rho * (9.f * cu * cg - 3.f * ug), Gm = w * rho * 3.f * cg;
-            const float fp = 0.5f * (fin[q] + fin[qb]), fm = 0.5f * (fin[q] - fin[qb]);
-            // d/drho of e+, e-, G+, G-
-            Lrho += Lp * (-lp * w * (1.f + 4.5f * cu * cu - 1.5f * usq) + cp * w * (9.f * cu * cg - 3.f * ug)) +
-                    Lm * (-lm * 3.f * w * cu + cm * 3.f * w * cg);
-            // d/du: e+ -> w rho (9 cu c - 3 u), e- -> 3 w rho c, G+ -> w rho (9 cg c - 3 g)
-            const float ap = -lp * w * rho * 9.f * cu + cp * w * rho * 9.f * cg;
-            Lux += Lp * (ap * cx(q) + 3.f * lp * w * rho * ux - 3.f * cp * w * rho * gx) + Lm * (-lm * 3.f * w * rho * cx(q));
-            Luy += Lp * (ap * cy(q) + 3.f * lp * w * rho * uy - 3.f * cp * w * rho * gy) + Lm * (-lm * 3.f * w * rho * cy(q));
-            Luz += Lp * (ap * cz(q) + 3.f * lp * w * rho * uz - 3.f * cp * w * rho * gz) + Lm * (-lm * 3.f * w * rho * cz(q));
-            // d/dg at fixed u: G+ -> w rho (9 cu c - 3 u), G- -> 3 w rho c
-            Gx += Lp * cp * w * rho * (9.f * cu * cx(q) - 3.f * ux) + Lm * cm * 3.f * w * rho * cx(q);
-            Gy += Lp * cp * w * rho * (9.f * cu * cy(q) - 3.f * uy) + Lm * cm * 3.f * w * rho * cy(q);
-            Gz += Lp * cp * w * rho * (9.f * cu * cz(q) - 3.f * uz) + Lm * cm * 3.f * w * rho * cz(q);
-            Tp += Lp * ((fp - ep) + 0.5f * Gp);
-            Tm += Lm * ((fm - em) + 0.5f * Gm);
-        }
-        // u = (j + rho g/2)/rho: du/dfin_k = (c_k + g/2 - u)/rho, du/dg = I/2
-        const float ax = (0.5f * gx - ux) * inv, ay = (0.5f * gy - uy) * inv, az = (0.5f * gz - uz) * inv;
-        const float base = Lrho + Lux * ax + Luy * ay + Luz * az;
+        const AdjOut o = collide_adjoint(d, fin, lam, acc);
         float sr = 0.f;
 #pragma unroll
         for (int q = 0; q < kQ; q++) {
-            const float m = mu[q] + base + (Lux * cx(q) + Luy * cy(q) + Luz * cz(q)) * inv;
+            const float m = adj_in_q(d, q, lam, o);
             const float jc = jx * cx(q) + jy * cy(q) + jz * cz(q);
             if (q == 0 || kind[q] == L_FLUID) {
                 lam_out[(size_t)q * N + src[q]] = m;
             } else if (kind[q] == L_WALL) {
                 lam_out[(size_t)opp(q) * N + i] = m;
-            } else {
+            } else {   // F gets -c_q (f*_qbar(x) + fin_q(x)), fin_q = f*_qbar(x) + rho0 cw_q
                 lam_out[(size_t)opp(q) * N + i] = m - 2.f * jc;
                 sr += (m - jc) * cw[q];
             }
         }
-        if (moving) srho[i] = sr;
-        acc[0] += Gx + 0.5f * Lux;
-        acc[1] += Gy + 0.5f * Luy;
-        acc[2] += Gz + 0.5f * Luz;
-        acc[3] += Tp;
-        acc[4] += Tm;
+        if (moving) srho[k] = sr;
     }
-    // per-block sums into one of kAdjSlots FP64 slots
-    __shared__ float red[5][8];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int k = 0; k < 5; k++) {
-        const float v = warp_sum(acc[k]);
-        if (lane == 0) red[k][wid] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 5) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) t += (double)red[threadIdx.x][w];
-        atomicAdd(&part[(blockIdx.x % kAdjSlots) * 5 + threadIdx.x], t);
-    }
+    adj_flush(acc, part);
 }
 
 // the rho0 terms of sphere links with a moving surface, added once every link is scattered
 __global__ void adjoint_rho_kernel(const Dev d, const float* __restrict__ srho, float* __restrict__ lam_out) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)d.N);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t i = d.wl_slow[k];
         if (!(d.flags[i] & F_LIQ)) continue;
-        const float s = srho[i];
+        const float s = srho[k];
         if (s == 0.f) continue;
         for (int q = 0; q < kQ; q++) lam_out[(size_t)q * d.N + i] += s;
     }
 }
 
 void launch_adjoint(const Dev& d, const float* f_fwd, const float* lam_in, float* lam_out, float* srho, const float jdir[3],
-                    double* part, bool moving_walls, cudaStream_t s) {
-    adjoint_kernel<<<152 * 8, 256, 0, s>>>(d, f_fwd, lam_in, lam_out, srho, jdir[0], jdir[1], jdir[2], moving_walls ? 1 : 0, part);
-    if (moving_walls) adjoint_rho_kernel<<<152 * 8, 256, 0, s>>>(d, srho, lam_out);
+                    double* part, bool moving_walls, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
+                    cudaEvent_t join) {
+    const int bx = d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
+    const int by = 128 / bx;
+    const dim3 block(bx, by, 1);
+    const dim3 grid((d.nx + bx - 1) / bx, (d.ny + by - 1) / by, d.nz);
+    cudaEventRecord(fork, s);
+    cudaStreamWaitEvent(side, fork, 0);
+    adjoint_boundary_kernel<<<152 * 2, 128, 0, side>>>(d, f_fwd, lam_in, lam_out, srho, jdir[0], jdir[1], jdir[2],
+                                                       moving_walls ? 1 : 0, part);
+    adjoint_bulk_kernel<<<grid, block, 0, s>>>(d, f_fwd, lam_in, lam_out, part);
+    cudaEventRecord(join, side);
+    cudaStreamWaitEvent(s, join, 0);
+    if (moving_walls) adjoint_rho_kernel<<<152 * 2, 128, 0, s>>>(d, srho, lam_out);
 }
 
 }  // namespace lbm

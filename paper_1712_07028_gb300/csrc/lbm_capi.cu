@@ -21,6 +21,7 @@ struct lbm_ctx {
     size_t arena_bytes;
     std::vector<double> bub_geo;     // [nbub][4] centre, radius
     std::vector<Sphere> sph_init;
+    std::vector<SphLink> sphl_init;   // staging of the first upload of the link data
     bool started;
     int cur;
     uint64_t launches;
@@ -47,7 +48,7 @@ struct lbm_ctx {
     uint64_t h2d_bytes, d2h_bytes;   // host <-> device copies made by the library
     // second stream and fork/join events of the concurrent bulk / boundary sweep
     cudaStream_t side;
-    cudaEvent_t fork, join;
+    cudaEvent_t fork, join, fork2, join2;
     bool side_ready;
 };
 
@@ -76,7 +77,7 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, acc, sc, wl[4], wl_slow, bin_cnt, bin_ids, npairs, pairs, geo,
+    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, acc, sc, wl[4], wl_slow, bin_cnt, bin_ids, npairs, pairs, geo,
         adj_srho, adj_part, total;
     size_t N, wl_cap, nbins_max;
 };
@@ -101,6 +102,7 @@ Layout layout_of(const lbm_params* p) {
     L.bub = take(sizeof(Bubble) * (size_t)p->max_bubbles);
     L.sph = take(sizeof(Sphere) * (size_t)p->max_spheres);
     L.sph_tmp = take(sizeof(Sphere) * (size_t)p->max_spheres);
+    L.sphl = take(sizeof(SphLink) * (size_t)p->max_spheres);
     L.acc = take(sizeof(SphereAcc) * (size_t)p->max_spheres);
     L.sc = take(sizeof(Scalars));
     for (int k = 0; k < 4; k++) L.wl[k] = take(4 * L.wl_cap);
@@ -162,8 +164,18 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool timed = false) {
         cudaEventRecord(c->ev[2 * slot + 1], s);
         c->ev_pending[slot] = true;
     }
+    // the sphere motion on the side stream, concurrent with the conversions
+    if (d.nsph > 0) {
+        cudaEventRecord(c->fork2, s);
+        cudaStreamWaitEvent(c->side, c->fork2, 0);
+        launch_spheres_move(d, c->side);
+    }
     launch_conversions(d, nxt, s);
-    launch_spheres(d, nxt, s);
+    if (d.nsph > 0) {
+        cudaEventRecord(c->join2, c->side);
+        cudaStreamWaitEvent(s, c->join2, 0);
+    }
+    launch_spheres_cover(d, nxt, s);
     launch_end_scan(d, nxt, 0, s);
     if (d.kappa) launch_curvature(d, nxt, s);
     return cuda_fail(cudaGetLastError());
@@ -208,6 +220,7 @@ int first_step(lbm_ctx* c) {
     d.bub = (Bubble*)(a + L.bub);
     d.sph = (Sphere*)(a + L.sph);
     d.sph_tmp = (Sphere*)(a + L.sph_tmp);
+    d.sphl = (SphLink*)(a + L.sphl);
     d.acc = (SphereAcc*)(a + L.acc);
     d.sc = (Scalars*)(a + L.sc);
     d.wl_conv = (uint32_t*)(a + L.wl[0]);
@@ -244,6 +257,8 @@ int first_step(lbm_ctx* c) {
         if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi_prio) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->fork2, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         c->side_ready = true;
     }
     int rc = cuda_fail(cudaMemsetAsync(a, 0, L.total, s));
@@ -252,6 +267,12 @@ int first_step(lbm_ctx* c) {
         if ((rc = cuda_fail(cudaMemcpyAsync(c->geo_dev, c->bub_geo.data(), sizeof(double) * c->bub_geo.size(), cudaMemcpyHostToDevice, s)))) return rc;
     if (d.nsph > 0)
         if ((rc = cuda_fail(cudaMemcpyAsync(d.sph, c->sph_init.data(), sizeof(Sphere) * d.nsph, cudaMemcpyHostToDevice, s)))) return rc;
+    if (d.nsph > 0) {
+        c->sphl_init.resize(d.nsph);
+        for (int a2 = 0; a2 < d.nsph; a2++) c->sphl_init[a2] = sph_link_of(c->sph_init[a2]);
+        if ((rc = cuda_fail(cudaMemcpyAsync(d.sphl, c->sphl_init.data(), sizeof(SphLink) * d.nsph, cudaMemcpyHostToDevice, s)))) return rc;
+        c->h2d_bytes += sizeof(SphLink) * d.nsph;
+    }
     c->h2d_bytes += sizeof(double) * c->bub_geo.size() + sizeof(Sphere) * (size_t)d.nsph;
     launch_bins_insert(d, s);
     launch_init(d, c->geo_dev, s);
@@ -504,8 +525,8 @@ int lbm_forward_frozen(lbm_ctx* c, const float* f_in, float* f_out) {
     if (!c || !f_in || !f_out || f_in == f_out) return LBM_EINVAL;
     int rc = adjoint_ready(c);
     if (rc) return rc;
-    launch_frozen_forward(c->d, f_in, f_out, c->stream);
-    return launched(c, 1);
+    launch_frozen_forward(c->d, f_in, f_out, c->stream, c->side, c->fork, c->join);
+    return launched(c, 2);
 }
 
 int lbm_adjoint_step(lbm_ctx* c, const float* f_fwd, const float* adj_in, float* adj_out, const double jdir[3],
@@ -516,8 +537,9 @@ int lbm_adjoint_step(lbm_ctx* c, const float* f_fwd, const float* adj_in, float*
     cudaStream_t s = c->stream;
     if (!accumulate && (rc = cuda_fail(cudaMemsetAsync(c->adj_part, 0, sizeof(double) * 5 * kAdjSlots, s)))) return rc;
     const float jd[3] = {(float)jdir[0], (float)jdir[1], (float)jdir[2]};
-    launch_adjoint(c->d, f_fwd, adj_in, adj_out, c->adj_srho, jd, c->adj_part, c->moving_walls, s);
-    if ((rc = launched(c, c->moving_walls ? 2 : 1))) return rc;
+    launch_adjoint(c->d, f_fwd, adj_in, adj_out, c->adj_srho, jd, c->adj_part, c->moving_walls, s, c->side, c->fork,
+                   c->join);
+    if ((rc = launched(c, c->moving_walls ? 3 : 2))) return rc;
     if (!dJdg) return LBM_OK;
     double part[5 * kAdjSlots];
     if ((rc = cuda_fail(cudaMemcpyAsync(part, c->adj_part, sizeof part, cudaMemcpyDeviceToHost, s)))) return rc;
@@ -579,6 +601,8 @@ int lbm_destroy(lbm_ctx* c) {
     if (c->side_ready) {
         cudaEventDestroy(c->fork);
         cudaEventDestroy(c->join);
+        cudaEventDestroy(c->fork2);
+        cudaEventDestroy(c->join2);
         cudaStreamDestroy(c->side);
     }
     std::free(c->sph_stage);

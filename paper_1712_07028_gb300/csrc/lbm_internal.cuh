@@ -76,6 +76,26 @@ struct Sphere {          // FP64 state of one sphere
     double stepped;      // 1 after the first sphere update
     double pad[1];
 };
+// FP32 copy of what a link needs from its sphere, refreshed after every move: the centre as
+// an integer part and a fraction in [0, 1) (cell offsets x - x_P then come out of an exact
+// integer difference and one FP32 subtraction), the velocity and angular velocity.  Keeps FP64
+// arithmetic, slow on this GPU, out of the per-cell code of the sweep.
+struct SphLink {
+    int xi[3];
+    float xf[3];
+    float u[3], w[3];
+};
+__host__ __device__ inline SphLink sph_link_of(const Sphere& s) {
+    SphLink l;
+    for (int k = 0; k < 3; k++) {
+        const double fl = floor(s.x[k]);
+        l.xi[k] = (int)fl;
+        l.xf[k] = (float)(s.x[k] - fl);
+        l.u[k] = (float)s.u[k];
+        l.w[k] = (float)s.w[k];
+    }
+    return l;
+}
 struct SphereAcc {       // per-step momentum-exchange accumulators (zeroed by the sphere update)
     double J[3];         // sum of the deviation part of dj
     double TJ[3];        // sum of (x - x_P) x (deviation part of dj)
@@ -85,7 +105,9 @@ struct SphereAcc {       // per-step momentum-exchange accumulators (zeroed by t
 struct Bubble {
     double V0, V, rho_g, Vif;    // reference volume, volume, gas density, interface part of V
     unsigned long long ngas;     // gas cells
-    unsigned long long pad[3];
+    float rho_gf;                // FP32 copy of rho_g for the sweep
+    float padf;
+    unsigned long long pad[2];
 };
 struct Scalars {
     double pool;          // excess mass waiting to be spread over the interface cells
@@ -93,7 +115,8 @@ struct Scalars {
     double S_bb, S_cover, S_uncover;   // mass budget terms
     double share;         // pool / n_iface used by the current sweep
     double mass;          // scratch for the on-demand total-mass reduction
-    double pad0;
+    float share_f;        // FP32 copy of share for the sweep
+    float pad0;
     uint32_t n_iface;     // interface cells after the last conversion / covering
     uint32_t n_iface_acc;
     uint32_t status;      // LBM_S_* bits
@@ -134,6 +157,7 @@ struct Dev {
     Bubble* bub;              // [max_bub]
     Sphere* sph;              // [max_sph]
     Sphere* sph_tmp;          // [max_sph] sub-step double buffer
+    SphLink* sphl;            // [max_sph] FP32 link data of the current sphere state
     SphereAcc* acc;           // [max_sph]
     Scalars* sc;
     uint32_t* wl_conv;        // worklists [wl_cap]
@@ -186,6 +210,24 @@ __device__ __forceinline__ bool bulk_of(const Dev& d, size_t i) {
 __device__ __forceinline__ void set_bulk(const Dev& d, size_t i) {
     const uint8_t t = d.flags[i] & F_TYPE;
     d.flags[i] = (uint8_t)(t | (bulk_of(d, i) ? F_BULK : 0));
+}
+
+// image (per periodic axis, the one nearest to the sphere centre) of cell c and its offset
+// c_img - x_P, from the sphere's link data
+__device__ __forceinline__ void sph_offset(const Dev& d, const SphLink& l, const int (&c)[3], int (&img)[3],
+                                           float (&r)[3]) {
+    const int L[3] = {d.nx, d.ny, d.nz};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        int xi = c[k];
+        if (d.bc[k]) {
+            const float dd = (float)(l.xi[k] - xi) + l.xf[k];   // x_P - c
+            if (dd > 0.5f * (float)L[k]) xi += L[k];
+            else if (dd < -0.5f * (float)L[k]) xi -= L[k];
+        }
+        img[k] = xi;
+        r[k] = (float)(xi - l.xi[k]) - l.xf[k];
+    }
 }
 
 // byte-wise atomic OR / AND on the mark array (4-byte aligned base); returns the old byte
@@ -391,7 +433,8 @@ void launch_sweep(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cuda
 void launch_conversions(const Dev& d, int nxt, cudaStream_t s);
 void launch_end_scan(const Dev& d, int cur, int set_reference, cudaStream_t s);
 void launch_curvature(const Dev& d, int nxt, cudaStream_t s);
-void launch_spheres(const Dev& d, int nxt, cudaStream_t s);
+void launch_spheres_move(const Dev& d, cudaStream_t s);
+void launch_spheres_cover(const Dev& d, int nxt, cudaStream_t s);
 void prepare_sphere_kernels();
 
 void launch_bins_insert(const Dev& d, cudaStream_t s);
@@ -402,9 +445,12 @@ void launch_fields(const Dev& d, int cur, float* rho, float* u, float* phi, uint
 void launch_export(const Dev& d, int cur, float* f, uint8_t* flags, float* m, float* phi, int32_t* owner, float* kappa, cudaStream_t s);
 void launch_import(const Dev& d, int cur, const float* f, const uint8_t* flags, const float* m, const float* phi, const int32_t* owner, const float* kappa, cudaStream_t s);
 void launch_mass(const Dev& d, int cur, cudaStream_t s);
-void launch_frozen_forward(const Dev& d, const float* f_in, float* f_out, cudaStream_t s);
+void launch_frozen_forward(const Dev& d, const float* f_in, float* f_out, cudaStream_t s, cudaStream_t side,
+                           cudaEvent_t fork, cudaEvent_t join);
+void launch_sweep_bulk_f32(const Dev& d, int cur, cudaStream_t s);
 constexpr int kAdjSlots = 64;
 void launch_adjoint(const Dev& d, const float* f_fwd, const float* lam_in, float* lam_out, float* srho, const float jdir[3],
-                    double* part, bool moving_walls, cudaStream_t s);
+                    double* part, bool moving_walls, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
+                    cudaEvent_t join);
 
 }  // namespace lbm

@@ -408,6 +408,7 @@ __global__ void cover_touch_kernel(const Dev d) {
     const int P = blockIdx.x;
     if (P >= d.nsph) return;
     const Sphere& s = d.sph[P];
+    if (threadIdx.x == 0) d.sphl[P] = sph_link_of(s);   // the next sweep's link data
     if (s.x[0] == s.x0[0] && s.x[1] == s.x0[1] && s.x[2] == s.x0[2]) return;
     // a sphere whose centre is not finite or moved more than a cell in one step is left alone
     // (the fluid has gone unstable; the status word says so)
@@ -631,7 +632,10 @@ void prepare_sphere_kernels() {
     cudaFuncSetAttribute(sph_substeps_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (13 * 8 + 3 * 4) * 1024);
 }
 
-void launch_spheres(const Dev& d, int nxt, cudaStream_t st) {
+// forces of the step, lubrication partners, contact links and the sub-stepped motion: reads
+// only the sweep's force sums, the sphere table and obstacle cells, which the conversions
+// leave alone, so it may run concurrently with them
+void launch_spheres_move(const Dev& d, cudaStream_t st) {
     if (d.nsph == 0) return;
     const int tb = 128, nb = (d.nsph + tb - 1) / tb;
     sph_prepare_kernel<<<nb, tb, 0, st>>>(d);
@@ -653,7 +657,11 @@ void launch_spheres(const Dev& d, int nxt, cudaStream_t st) {
     } else if (d.sphere_mode == LBM_SPHERES_PRESCRIBED) {
         sph_prescribed_kernel<<<nb, tb, 0, st>>>(d);
     }
-    if (d.sphere_mode == LBM_SPHERES_FIXED) return;
+}
+
+// cells covered and uncovered by the moved spheres (after the conversions)
+void launch_spheres_cover(const Dev& d, int nxt, cudaStream_t st) {
+    if (d.nsph == 0 || d.sphere_mode == LBM_SPHERES_FIXED) return;
     cover_touch_kernel<<<d.nsph, 128, 0, st>>>(d);
     const int lb = 2 * 152;
     switch (d.storage) {

@@ -429,6 +429,7 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
         if (set_reference) { B.V0 = V; B.rho_g = (double)d.rho_g0; }
         else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
         else atomicOr(&d.sc->status, S_BUBBLE_GONE);
+        B.rho_gf = (float)B.rho_g;
         B.ngas = 0ull;
         B.Vif = 0.0;
     }
@@ -440,6 +441,7 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
         c.n_iface = *(volatile uint32_t*)&c.n_iface_acc;
         c.n_iface_acc = 0;
         c.share = (c.pool != 0.0 && c.n_iface > 0) ? c.pool / (double)c.n_iface : 0.0;
+        c.share_f = (float)c.share;
         c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
         c.ticket = 0;
     }

@@ -48,21 +48,13 @@ __device__ __forceinline__ void sph_begin(const Dev& d, SphAcc& a, uint32_t P, i
     a.pid = P;
     a.J[0] = a.J[1] = a.J[2] = 0.f;
     a.K[0] = a.K[1] = a.K[2] = 0;
-    const Sphere& sp = d.sph[P];
+    const SphLink l = d.sphl[P];
     const int c[3] = {x, y, z};
-    const int L[3] = {d.nx, d.ny, d.nz};
+    sph_offset(d, l, c, a.xi, a.r);
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-        int xi = c[k];
-        if (d.bc[k]) {   // image of the cell nearest to the sphere centre
-            const double dd = sp.x[k] - (double)xi;
-            if (dd > 0.5 * L[k]) xi += L[k];
-            else if (dd < -0.5 * L[k]) xi -= L[k];
-        }
-        a.xi[k] = xi;
-        a.r[k] = (float)((double)xi - sp.x[k]);
-        a.u[k] = (float)sp.u[k];
-        a.w[k] = (float)sp.w[k];
+        a.u[k] = l.u[k];
+        a.w[k] = l.w[k];
     }
 }
 
@@ -235,7 +227,7 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                     if (fl & F_LIQ) sbb += corr;
                 } else {                                                // gas: Eq. fsk
                     const uint32_t bb = __float_as_uint(fv[q]);
-                    const float rg = bb < (uint32_t)d.nbub ? (float)d.bub[bb].rho_g : d.rho_g0;
+                    const float rg = bb < (uint32_t)d.nbub ? d.bub[bb].rho_gf : d.rho_g0;
                     const float rw = rg + 6.f * d.sigma * kap;
                     const float cu = cx(q) * u0x + cy(q) * u0y + cz(q) * u0z;
                     // -f*_qb + 2 e+_q, in deviations: 2 (e+_q - w_q) - (f*_qb - w_q)
@@ -243,7 +235,7 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                 }
             }
             if (isIF) {
-                const float mnew = (d.mass[i] + (float)d.sc->share) + dm;
+                const float mnew = (d.mass[i] + d.sc->share_f) + dm;
                 float drho = 0.f;
 #pragma unroll
                 for (int q = 0; q < kQ; q++) drho += fin[q];
@@ -343,6 +335,15 @@ void launch_sweep(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cuda
     }
     cudaEventRecord(join, side);
     cudaStreamWaitEvent(s, join, 0);
+}
+
+// the bulk kernel alone on one stream (FP32 storage): the frozen window's replay step
+void launch_sweep_bulk_f32(const Dev& d, int cur, cudaStream_t s) {
+    const int bx = d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
+    const int by = 128 / bx;
+    dim3 block(bx, by, 1);
+    dim3 grid((d.nx + bx - 1) / bx, (d.ny + by - 1) / by, d.nz);
+    sweep_bulk_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur);
 }
 
 }  // namespace lbm
