@@ -126,7 +126,12 @@ int lbm_add_sphere(lbm_ctx* ctx, const double c[3], double r, double rho_p, cons
 
 /* Advance nsteps >= 0 time steps.  The first call initialises the fields on the device
  * (liquid at rest, bubbles, layer closure, spheres).  Asynchronous: problems found on the
- * device are latched in the status word and reported by lbm_status / lbm_forces. */
+ * device are latched in the status word and reported by lbm_status / lbm_forces.
+ * The end-of-step kernels of the last step (conversions, sphere motion, cover/uncover,
+ * bubble model) are left pending: the next lbm_step runs them concurrently with its bulk
+ * sweep, and every call that reads the state (lbm_forces, lbm_spheres, lbm_bubbles,
+ * lbm_fields, lbm_export_state, lbm_mass_budget, lbm_status and the window calls below)
+ * enqueues them first, so what a caller sees is always the complete step. */
 int lbm_step(lbm_ctx* ctx, int nsteps);
 
 /* Momentum-exchange force F[n][3] and torque T[n][3] (host, FP64) of the last step, for
@@ -190,14 +195,16 @@ int lbm_forward_frozen(lbm_ctx* ctx, const float* f_in, float* f_out);
 int lbm_adjoint_step(lbm_ctx* ctx, const float* f_fwd, const float* adj_in, float* adj_out, const double jdir[3],
                      int accumulate, double dJdg[3], double* dJdtau);
 
-/* Timing of the sweep kernel (the dominant one): while on != 0, lbm_step launches steps
- * one by one (no CUDA graph) and records a CUDA event pair around each sweep launch on the
- * stream it runs on. */
+/* Timing of the sweep: while on != 0, lbm_step launches steps one by one (no CUDA graph)
+ * and records CUDA event pairs on the library's stream around the bulk sweep kernel (the
+ * dominant one; it runs concurrently with the previous step's end-of-step kernels) and
+ * around the rest of the sweep (fix pass and boundary kernel, after those kernels). */
 int lbm_profile(lbm_ctx* ctx, int on);
 
-/* Sum of the recorded sweep durations in milliseconds (host *sweep_ms) and their number
- * (host *sweeps) since the last read; waits for the recorded events.  Resets both. */
-int lbm_profile_read(lbm_ctx* ctx, double* sweep_ms, uint64_t* sweeps);
+/* Sums of the recorded durations in milliseconds since the last read (host ms[0]: bulk
+ * sweep kernel, ms[1]: rest of the sweep) and their number (host *sweeps); waits for the
+ * recorded events.  Resets them. */
+int lbm_profile_read(lbm_ctx* ctx, double ms[2], uint64_t* sweeps);
 
 /* Bytes the library itself has copied host -> device (*h2d) and device -> host (*d2h)
  * so far (table uploads, copy-out calls), both host pointers. */

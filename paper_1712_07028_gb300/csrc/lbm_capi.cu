@@ -25,7 +25,6 @@ struct lbm_ctx {
     bool started;
     int cur;
     uint64_t launches;
-    int per_step;
     double* geo_dev;
     float* adj_srho;
     double* adj_part;
@@ -37,18 +36,23 @@ struct lbm_ctx {
     cudaGraphExec_t graph;
     bool graph_ready;
     bool use_graph;
-    // optional timing of the sweep kernel: CUDA events around each launch, on its stream
+    // optional timing of the sweep: CUDA events around the bulk kernel and around the rest
+    // (fix pass + boundary kernel), on the library's stream
     bool profiling;
-    cudaEvent_t ev[2 * 64];
+    cudaEvent_t ev[4 * 64];
     bool ev_ready;
     bool ev_pending[64];
     int ev_slot;
-    double sweep_ms;
+    double bulk_ms, rest_ms;
     uint64_t sweeps;
+    // the end-of-step kernels of the last step not enqueued yet: the next step runs them
+    // concurrently with its bulk sweep, any query runs them first
+    bool pending;
     uint64_t h2d_bytes, d2h_bytes;   // host <-> device copies made by the library
     // second stream and fork/join events of the concurrent bulk / boundary sweep
     cudaStream_t side;
-    cudaEvent_t fork, join, fork2, join2;
+    cudaEvent_t fork, join, fork2, join2, fork3, join3;
+    cudaStream_t epi;   // the end-of-step kernels when they overlap the next bulk sweep
     bool side_ready;
 };
 
@@ -77,7 +81,7 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, acc, sc, wl[4], wl_slow, bin_cnt, bin_ids, npairs, pairs, geo,
+    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
         adj_srho, adj_part, total;
     size_t N, wl_cap, nbins_max;
 };
@@ -107,6 +111,7 @@ Layout layout_of(const lbm_params* p) {
     L.sc = take(sizeof(Scalars));
     for (int k = 0; k < 4; k++) L.wl[k] = take(4 * L.wl_cap);
     L.wl_slow = take(4 * L.N);
+    L.wl_fix = take(4 * L.wl_cap);
     L.bin_cnt = take(4 * L.nbins_max);
     L.bin_ids = take(4 * L.nbins_max * kBinCap);
     L.npairs = take(4 * (size_t)p->max_spheres);
@@ -135,53 +140,81 @@ int status_code(uint32_t st) {
     return LBM_OK;
 }
 
-// collect the elapsed time of a recorded (start, end) pair
+// collect the elapsed times of a recorded slot (bulk start/end, rest start/end)
 void prof_collect(lbm_ctx* c, int slot) {
     if (!c->ev_pending[slot]) return;
-    cudaEventSynchronize(c->ev[2 * slot + 1]);
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev[2 * slot], c->ev[2 * slot + 1]) == cudaSuccess) {
-        c->sweep_ms += ms;
+    cudaEventSynchronize(c->ev[4 * slot + 3]);
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, c->ev[4 * slot], c->ev[4 * slot + 1]) == cudaSuccess &&
+        cudaEventElapsedTime(&b, c->ev[4 * slot + 2], c->ev[4 * slot + 3]) == cudaSuccess) {
+        c->bulk_ms += a;
+        c->rest_ms += b;
         c->sweeps++;
     }
     c->ev_pending[slot] = false;
 }
 
-// kernels of one step, in the order of the method; with `timed`, the sweep (bulk and boundary
-// kernels together) is bracketed by a pair of events on its stream
-int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool timed = false) {
+// end-of-step kernels of the step that wrote grid g (Sec. 2.2 conversions and bubble model,
+// Sec. 2.3 sphere motion and cover/uncover): the sphere motion on the side stream concurrent
+// with the conversions on `e`, then cover/uncover, the end-of-step scan and the curvature on `e`
+void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
     const Dev& d = c->d;
-    const int nxt = cur ^ 1;
+    if (d.nsph > 0) {
+        cudaEventRecord(c->fork2, e);
+        cudaStreamWaitEvent(c->side, c->fork2, 0);
+        launch_spheres_move(d, c->side);
+    }
+    launch_conversions(d, g, e);
+    if (d.nsph > 0) {
+        cudaEventRecord(c->join2, c->side);
+        cudaStreamWaitEvent(e, c->join2, 0);
+    }
+    launch_spheres_cover(d, g, e);
+    launch_end_scan(d, g, 0, e);
+    if (d.kappa) launch_curvature(d, g, e);
+}
+
+int epilogue_launches(const Dev& d) { return 1 + spheres_launches(d) + 1 + (d.kappa ? 1 : 0); }
+int step_launches(const Dev& d, bool overlap) { return 3 + (overlap ? epilogue_launches(d) : 0); }
+
+// one step reading grid cur: the bulk sweep on s and, with `overlap`, the end-of-step kernels
+// of the previous step concurrently on the epilogue stream; once both are done the fix pass
+// and the boundary sweep.  The step's own end-of-step kernels are left pending.  With `timed`,
+// event pairs bracket the bulk sweep and the rest on s.
+int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed = false) {
+    const Dev& d = c->d;
     int slot = 0;
     if (timed) {
         slot = c->ev_slot;
         c->ev_slot = (c->ev_slot + 1) % 64;
         prof_collect(c, slot);
-        cudaEventRecord(c->ev[2 * slot], s);
     }
-    launch_sweep(d, cur, s, c->side, c->fork, c->join);
+    if (overlap) {
+        cudaEventRecord(c->fork3, s);
+        cudaStreamWaitEvent(c->epi, c->fork3, 0);
+        enqueue_epilogue(c, cur, c->epi);
+        cudaEventRecord(c->join3, c->epi);
+    }
+    if (timed) cudaEventRecord(c->ev[4 * slot], s);
+    launch_sweep_bulk(d, cur, s);
+    if (timed) cudaEventRecord(c->ev[4 * slot + 1], s);
+    if (overlap) cudaStreamWaitEvent(s, c->join3, 0);
+    if (timed) cudaEventRecord(c->ev[4 * slot + 2], s);
+    launch_sweep_rest(d, cur, s, c->side, c->fork, c->join);
     if (timed) {
-        cudaEventRecord(c->ev[2 * slot + 1], s);
+        cudaEventRecord(c->ev[4 * slot + 3], s);
         c->ev_pending[slot] = true;
     }
-    // the sphere motion on the side stream, concurrent with the conversions
-    if (d.nsph > 0) {
-        cudaEventRecord(c->fork2, s);
-        cudaStreamWaitEvent(c->side, c->fork2, 0);
-        launch_spheres_move(d, c->side);
-    }
-    launch_conversions(d, nxt, s);
-    if (d.nsph > 0) {
-        cudaEventRecord(c->join2, c->side);
-        cudaStreamWaitEvent(s, c->join2, 0);
-    }
-    launch_spheres_cover(d, nxt, s);
-    launch_end_scan(d, nxt, 0, s);
-    if (d.kappa) launch_curvature(d, nxt, s);
     return cuda_fail(cudaGetLastError());
 }
 
-int count_per_step(const Dev& d) { return 2 + 1 + (d.kappa ? 1 : 0) + spheres_launches(d) + 1; }
+// enqueue the pending end-of-step kernels on the library's stream (before any query)
+int flush(lbm_ctx* c) {
+    if (!c->pending) return LBM_OK;
+    enqueue_epilogue(c, c->cur, c->stream);
+    c->pending = false;
+    return launched(c, epilogue_launches(c->d));
+}
 
 int first_step(lbm_ctx* c) {
     const lbm_params* p = &c->p;
@@ -228,6 +261,7 @@ int first_step(lbm_ctx* c) {
     d.wl_fromliq = (uint32_t*)(a + L.wl[2]);
     d.wl_touch = (uint32_t*)(a + L.wl[3]);
     d.wl_slow = (uint32_t*)(a + L.wl_slow);
+    d.wl_fix = (uint32_t*)(a + L.wl_fix);
     double rmax = 1.0;
     for (const Sphere& s : c->sph_init) rmax = std::fmax(rmax, s.R);
     d.bin_w = (int)std::ceil(2.0 * rmax + 2.0);
@@ -259,6 +293,9 @@ int first_step(lbm_ctx* c) {
         if (cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->fork2, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->join2, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->fork3, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->join3, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        if (cudaStreamCreateWithPriority(&c->epi, cudaStreamNonBlocking, hi_prio) != cudaSuccess) return LBM_ECUDA;
         c->side_ready = true;
     }
     int rc = cuda_fail(cudaMemsetAsync(a, 0, L.total, s));
@@ -281,7 +318,7 @@ int first_step(lbm_ctx* c) {
     if (d.kappa) launch_curvature(d, 0, s);
     if ((rc = launched(c, (d.nsph > 0) + 3 + (d.kappa ? 1 : 0)))) return rc;
     c->cur = 0;
-    c->per_step = count_per_step(d);
+    c->pending = false;
     c->started = true;
     return cuda_fail(cudaStreamSynchronize(s));
 }
@@ -293,8 +330,8 @@ int build_graph(lbm_ctx* c) {
     int rc = LBM_OK;
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = LBM_ECUDA;
     if (!rc) {
-        enqueue_step(c, 0, cap);
-        enqueue_step(c, 1, cap);
+        enqueue_step(c, 0, cap, true);
+        enqueue_step(c, 1, cap, true);
         if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = LBM_ECUDA;
     }
     // per-node priorities: the boundary sweep keeps its stream's priority inside the graph
@@ -350,8 +387,9 @@ int lbm_init(const lbm_params* p, void* arena, size_t arena_bytes, void* cuda_st
     c->ev_ready = false;
     for (int k = 0; k < 64; k++) c->ev_pending[k] = false;
     c->ev_slot = 0;
-    c->sweep_ms = 0.0;
+    c->bulk_ms = c->rest_ms = 0.0;
     c->sweeps = 0;
+    c->pending = false;
     c->h2d_bytes = 0;
     c->d2h_bytes = 0;
     c->side_ready = false;
@@ -402,38 +440,41 @@ int lbm_step(lbm_ctx* c, int nsteps) {
     int rc;
     if (!c->started && (rc = first_step(c))) return rc;
     int left = nsteps;
+    auto one = [&](bool timed) {
+        const bool ov = c->pending;
+        int r = enqueue_step(c, c->cur, c->stream, ov, timed);
+        if (r) return r;
+        c->launches += (uint64_t)step_launches(c->d, ov);
+        c->pending = true;
+        c->cur ^= 1;
+        return LBM_OK;
+    };
     if (c->profiling) {
-        for (; left > 0; left--) {
-            if ((rc = enqueue_step(c, c->cur, c->stream, true))) return rc;
-            c->launches += (uint64_t)c->per_step;
-            c->cur ^= 1;
-        }
+        for (; left > 0; left--)
+            if ((rc = one(true))) return rc;
         return LBM_OK;
     }
     if (c->use_graph && nsteps >= 2 && !c->graph_ready && (rc = build_graph(c))) c->use_graph = false;
     if (c->use_graph && c->graph_ready) {
-        if (c->cur == 1 && left > 0) {   // realign to an even grid parity
-            if ((rc = enqueue_step(c, 1, c->stream))) return rc;
-            c->launches += (uint64_t)c->per_step;
-            c->cur = 0;
+        // the graph holds two overlapped steps from grid 0: align the state to that first
+        while (left > 0 && (!c->pending || c->cur == 1)) {
+            if ((rc = one(false))) return rc;
             left--;
         }
         for (; left >= 2; left -= 2) {
             if ((rc = cuda_fail(cudaGraphLaunch(c->graph, c->stream)))) return rc;
-            c->launches += 2ull * (uint64_t)c->per_step;
+            c->launches += 2ull * (uint64_t)step_launches(c->d, true);
         }
     }
-    for (; left > 0; left--) {
-        if ((rc = enqueue_step(c, c->cur, c->stream))) return rc;
-        c->launches += (uint64_t)c->per_step;
-        c->cur ^= 1;
-    }
+    for (; left > 0; left--)
+        if ((rc = one(false))) return rc;
     return LBM_OK;
 }
 
 int lbm_forces(lbm_ctx* c, double* F, double* T, int n) {
     if (!c || n < 0 || (n > 0 && (!F || !T))) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
     if (n > c->d.nsph) return LBM_EINVAL;
     int rc = sync_tables(c);
     if (rc) return rc;
@@ -448,6 +489,7 @@ int lbm_forces(lbm_ctx* c, double* F, double* T, int n) {
 int lbm_spheres(lbm_ctx* c, double* x, double* u, double* w, int n) {
     if (!c || n < 0) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
     if (n > c->d.nsph) return LBM_EINVAL;
     int rc = sync_tables(c);
     if (rc) return rc;
@@ -463,6 +505,7 @@ int lbm_spheres(lbm_ctx* c, double* x, double* u, double* w, int n) {
 int lbm_bubbles(lbm_ctx* c, double* V0, double* V, double* rho_g, int n) {
     if (!c || n < 0) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
     if (n > c->d.nbub) return LBM_EINVAL;
     int rc = sync_tables(c);
     if (rc) return rc;
@@ -477,6 +520,7 @@ int lbm_bubbles(lbm_ctx* c, double* V0, double* V, double* rho_g, int n) {
 int lbm_fields(lbm_ctx* c, float* rho, float* u, float* phi, uint8_t* flags) {
     if (!c) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
     launch_fields(c->d, c->cur, rho, u, phi, flags, c->stream);
     return launched(c, 1);
 }
@@ -484,6 +528,7 @@ int lbm_fields(lbm_ctx* c, float* rho, float* u, float* phi, uint8_t* flags) {
 int lbm_export_state(lbm_ctx* c, float* f, uint8_t* flags, float* mass, float* phi, int32_t* owner, float* kappa) {
     if (!c) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
     launch_export(c->d, c->cur, f, flags, mass, phi, owner, kappa, c->stream);
     return launched(c, 1);
 }
@@ -491,6 +536,7 @@ int lbm_export_state(lbm_ctx* c, float* f, uint8_t* flags, float* mass, float* p
 int lbm_mass_budget(lbm_ctx* c, double out[5]) {
     if (!c || !out) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
     int rc;
     if ((rc = cuda_fail(cudaMemsetAsync(&c->d.sc->mass, 0, sizeof(double), c->stream)))) return rc;
     launch_mass(c->d, c->cur, c->stream);
@@ -508,7 +554,9 @@ int lbm_mass_budget(lbm_ctx* c, double out[5]) {
 int lbm_status(lbm_ctx* c, uint32_t* status) {
     if (!c || !status) return LBM_EINVAL;
     if (!c->started) { *status = 0; return LBM_OK; }
-    int rc = sync_tables(c);
+    int rc = flush(c);
+    if (rc) return rc;
+    rc = sync_tables(c);
     if (rc) return rc;
     *status = c->sc_stage->status;
     return LBM_OK;
@@ -518,7 +566,7 @@ int lbm_status(lbm_ctx* c, uint32_t* status) {
 static int adjoint_ready(lbm_ctx* c) {
     if (!c->started) return LBM_ESTATE;
     if (c->p.storage != LBM_STORE_F32 || c->d.nbub != 0 || c->p.sphere_mode != LBM_SPHERES_FIXED) return LBM_ESTATE;
-    return LBM_OK;
+    return flush(c);
 }
 
 int lbm_forward_frozen(lbm_ctx* c, const float* f_in, float* f_out) {
@@ -559,7 +607,7 @@ int lbm_adjoint_step(lbm_ctx* c, const float* f_fwd, const float* adj_in, float*
 int lbm_profile(lbm_ctx* c, int on) {
     if (!c) return LBM_EINVAL;
     if (on && !c->ev_ready) {
-        for (int k = 0; k < 2 * 64; k++)
+        for (int k = 0; k < 4 * 64; k++)
             if (cudaEventCreate(&c->ev[k]) != cudaSuccess) return LBM_ECUDA;
         c->ev_ready = true;
     }
@@ -569,13 +617,14 @@ int lbm_profile(lbm_ctx* c, int on) {
     return LBM_OK;
 }
 
-int lbm_profile_read(lbm_ctx* c, double* sweep_ms, uint64_t* sweeps) {
-    if (!c || !sweep_ms || !sweeps) return LBM_EINVAL;
+int lbm_profile_read(lbm_ctx* c, double ms[2], uint64_t* sweeps) {
+    if (!c || !ms || !sweeps) return LBM_EINVAL;
     if (c->ev_ready)
         for (int k = 0; k < 64; k++) prof_collect(c, k);
-    *sweep_ms = c->sweep_ms;
+    ms[0] = c->bulk_ms;
+    ms[1] = c->rest_ms;
     *sweeps = c->sweeps;
-    c->sweep_ms = 0.0;
+    c->bulk_ms = c->rest_ms = 0.0;
     c->sweeps = 0;
     return LBM_OK;
 }
@@ -597,13 +646,16 @@ int lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_EINVAL;
     if (c->graph_ready) cudaGraphExecDestroy(c->graph);
     if (c->ev_ready)
-        for (int k = 0; k < 2 * 64; k++) cudaEventDestroy(c->ev[k]);
+        for (int k = 0; k < 4 * 64; k++) cudaEventDestroy(c->ev[k]);
     if (c->side_ready) {
         cudaEventDestroy(c->fork);
         cudaEventDestroy(c->join);
         cudaEventDestroy(c->fork2);
         cudaEventDestroy(c->join2);
+        cudaEventDestroy(c->fork3);
+        cudaEventDestroy(c->join3);
         cudaStreamDestroy(c->side);
+        cudaStreamDestroy(c->epi);
     }
     std::free(c->sph_stage);
     std::free(c->sc_stage);

@@ -124,7 +124,9 @@ struct Scalars {
     uint32_t bin_overflow;
     uint32_t n_slow;      // active cells the bulk sweep left to the boundary sweep
     uint32_t ticket;      // blocks of the end-of-step scan that have finished
-    uint32_t pad1[5];
+    uint32_t n_fix;       // BULK cells the end of the last step changed or whose neighbours it changed
+    uint32_t fix_all;     // the fix list overflowed: the fix pass takes every BULK cell
+    uint32_t pad1[3];
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
@@ -165,6 +167,7 @@ struct Dev {
     uint32_t* wl_fromliq;
     uint32_t* wl_touch;
     uint32_t* wl_slow;        // [N] per-step list of active cells for the boundary sweep
+    uint32_t* wl_fix;         // [wl_cap] BULK cells to sweep again after the end-of-step kernels
     // uniform bins of sphere ids for the neighbour searches
     int bin_w, nbx, nby, nbz, bin_cap;
     uint32_t* bin_cnt;        // [nbins]
@@ -207,9 +210,25 @@ __device__ __forceinline__ bool bulk_of(const Dev& d, size_t i) {
     }
     return ok != 0;
 }
-__device__ __forceinline__ void set_bulk(const Dev& d, size_t i) {
+// BULK bit of cell i from its neighbourhood.  The end-of-step kernels call it for every cell
+// whose type or PDFs they changed and for those cells' neighbours, while the next step's bulk
+// sweep may already be running on the types and PDFs it read before: every cell that comes out
+// BULK goes to the fix list, whose cells the sweep takes again once these kernels are done.
+__device__ __forceinline__ void set_bulk(const Dev& d, size_t i, bool to_fix = true) {
     const uint8_t t = d.flags[i] & F_TYPE;
-    d.flags[i] = (uint8_t)(t | (bulk_of(d, i) ? F_BULK : 0));
+    const bool b = bulk_of(d, i);
+    d.flags[i] = (uint8_t)(t | (b ? F_BULK : 0));
+    if (b && to_fix) {
+        const unsigned act = __activemask();
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(act) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&d.sc->n_fix, (uint32_t)__popc(act));
+        base = __shfl_sync(act, base, leader);
+        const uint32_t slot = base + (uint32_t)__popc(act & ((1u << lane) - 1u));
+        if (slot < (uint32_t)d.wl_cap) d.wl_fix[slot] = (uint32_t)i;
+        else d.sc->fix_all = 1u;   // no fatal overflow: the fix pass then takes every BULK cell
+    }
 }
 
 // image (per periodic axis, the one nearest to the sphere centre) of cell c and its offset
@@ -428,7 +447,8 @@ __device__ __forceinline__ uint32_t covering_sphere(const Dev& d, int x, int y, 
 }
 
 // kernels (defined in the .cu files), launched by lbm_capi.cu
-void launch_sweep(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s);
+void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 
 void launch_conversions(const Dev& d, int nxt, cudaStream_t s);
 void launch_end_scan(const Dev& d, int cur, int set_reference, cudaStream_t s);
@@ -447,7 +467,7 @@ void launch_import(const Dev& d, int cur, const float* f, const uint8_t* flags, 
 void launch_mass(const Dev& d, int cur, cudaStream_t s);
 void launch_frozen_forward(const Dev& d, const float* f_in, float* f_out, cudaStream_t s, cudaStream_t side,
                            cudaEvent_t fork, cudaEvent_t join);
-void launch_sweep_bulk_f32(const Dev& d, int cur, cudaStream_t s);
+
 constexpr int kAdjSlots = 64;
 void launch_adjoint(const Dev& d, const float* f_fwd, const float* lam_in, float* lam_out, float* srho, const float jdir[3],
                     double* part, bool moving_walls, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,

@@ -10,7 +10,6 @@
 
 namespace lbm {
 
-constexpr int kListThreads = 128;
 
 __device__ __forceinline__ uint32_t list_len(const uint32_t* cnt, int cap) {
     const uint32_t n = *(volatile const uint32_t*)cnt;
@@ -284,6 +283,9 @@ template <int S>
 __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads) conversions_kernel(const Dev d, const int nxt) {
     const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    // the fix list of the last step has been consumed by the sweep's fix pass; this step's
+    // BULK updates (here and in the cover kernels after this launch) fill it again
+    if (blockIdx.x == 0 && threadIdx.x == 0) { d.sc->n_fix = 0; d.sc->fix_all = 0; }
     conv_filled_emptied<S>(d, nxt, wid, nw);
     cluster_sync();
     // new-interface initialisation writes only the new cells' PDFs; the excess phase reads
@@ -568,9 +570,9 @@ void launch_init(const Dev& d, const double* geo, cudaStream_t s) {
     }
 }
 
-__global__ void bulk_all_kernel(const Dev d) {
+__global__ void bulk_all_kernel(const Dev d) {   // initial BULK bits (nothing to fix)
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x)
-        set_bulk(d, i);
+        set_bulk(d, i, false);
 }
 
 void launch_bulk_all(const Dev& d, cudaStream_t s) { bulk_all_kernel<<<152 * 16, 256, 0, s>>>(d); }

@@ -75,23 +75,13 @@ __device__ __forceinline__ void sph_flush_direct(const Dev& d, const SphAcc& a) 
 }
 
 
-// every liquid cell whose neighbours all carry PDFs or lie beyond a wall; other active cells
-// go to the boundary list
+// pull-stream and collide one BULK cell (x, y, z) = i: every neighbour carries PDFs or lies
+// beyond a wall (halfway bounce-back by index select), no neighbour tests
 template <int S>
-__global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int cur) {
+__device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>::T* __restrict__ fa,
+                                          typename Store<S>::T* __restrict__ fb, int x, int y, int z, uint32_t i) {
     using T = typename Store<S>::T;
-    const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
-    T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= d.nx || y >= d.ny) return;
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
-    const uint32_t i = (uint32_t)x + nx * (uint32_t)y + nxy * (uint32_t)z;
-    const uint8_t fl = d.flags[i];
-    if (!(fl & F_ACTIVE)) return;
-    if (!(fl & F_BULK)) return;   // the boundary kernel's (listed at the end of the last step)
-    // neighbour coordinates (periodic wrap) and the links whose source lies beyond a wall
     const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
     const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
     const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
@@ -111,6 +101,44 @@ __global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int 
         fin[q] = Store<S>::get(plane, wall ? i : sx + sy + sz);
     }
     collide_store<S>(d, fb, i, fin);
+}
+
+// every liquid cell whose neighbours all carry PDFs or lie beyond a wall; other active cells
+// go to the boundary list.  It may run while the end-of-step kernels of the last step are
+// still changing types and PDFs near interfaces and spheres: the cells it then reads stale
+// inputs for are on the fix list (or leave BULK and go to the boundary list), and the fix pass
+// and the boundary sweep, which run after those kernels, overwrite their results.
+template <int S>
+__global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int cur) {
+    using T = typename Store<S>::T;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= d.nx || y >= d.ny) return;
+    const uint32_t i = (uint32_t)x + (uint32_t)d.nx * (uint32_t)y + (uint32_t)d.nx * (uint32_t)d.ny * (uint32_t)z;
+    const uint8_t fl = d.flags[i];
+    if (!(fl & F_ACTIVE)) return;
+    if (!(fl & F_BULK)) return;   // the boundary kernel's (listed at the end of the last step)
+    bulk_cell<S>(d, static_cast<const T*>(d.f[cur]), static_cast<T*>(d.f[cur ^ 1]), x, y, z, i);
+}
+
+// the fix pass: the listed BULK cells again (or every BULK cell when the list overflowed),
+// with the types and PDFs the end-of-step kernels left
+template <int S>
+__global__ void __launch_bounds__(128) sweep_fix_kernel(const Dev d, const int cur) {
+    using T = typename Store<S>::T;
+    const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
+    T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
+    const bool all = *(volatile const uint32_t*)&d.sc->fix_all != 0u;
+    const uint32_t n = all ? (uint32_t)d.N : min(*(volatile const uint32_t*)&d.sc->n_fix, (uint32_t)d.wl_cap);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t i = all ? k : d.wl_fix[k];
+        const uint8_t fl = d.flags[i];
+        if (!(fl & F_LIQ) || !(fl & F_BULK)) continue;
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        bulk_cell<S>(d, fa, fb, x, y, z, i);
+    }
 }
 
 // every other active cell: walls, sphere links, gas links, interface mass exchange
@@ -309,41 +337,42 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
     }
 }
 
-// the boundary kernel on `side`, forked from and joined back into `s` by two events, the bulk
-// kernel on `s`; both read grid cur and write disjoint cells of grid cur ^ 1
-void launch_sweep(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
+// the bulk sweep of grid cur on stream s
+void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s) {
     const int bx = d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
     const int by = 128 / bx;
     dim3 block(bx, by, 1);
     dim3 grid((d.nx + bx - 1) / bx, (d.ny + by - 1) / by, d.nz);
+    switch (d.storage) {
+        case LBM_STORE_F32: sweep_bulk_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur); break;
+        case LBM_STORE_F16DEV: sweep_bulk_kernel<LBM_STORE_F16DEV><<<grid, block, 0, s>>>(d, cur); break;
+        default: sweep_bulk_kernel<LBM_STORE_BF16DEV><<<grid, block, 0, s>>>(d, cur); break;
+    }
+}
+
+// the rest of the sweep once the end-of-step kernels are done: the boundary kernel on `side`,
+// forked from and joined back into `s` by two events, the fix pass on `s`; both read grid cur
+// and write disjoint cells of grid cur ^ 1
+void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
     const int nb = 152 * 2;
     cudaEventRecord(fork, s);
     cudaStreamWaitEvent(side, fork, 0);
     switch (d.storage) {
         case LBM_STORE_F32:
             sweep_boundary_kernel<LBM_STORE_F32><<<nb, 128, 0, side>>>(d, cur);
-            sweep_bulk_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur);
+            sweep_fix_kernel<LBM_STORE_F32><<<nb, 128, 0, s>>>(d, cur);
             break;
         case LBM_STORE_F16DEV:
             sweep_boundary_kernel<LBM_STORE_F16DEV><<<nb, 128, 0, side>>>(d, cur);
-            sweep_bulk_kernel<LBM_STORE_F16DEV><<<grid, block, 0, s>>>(d, cur);
+            sweep_fix_kernel<LBM_STORE_F16DEV><<<nb, 128, 0, s>>>(d, cur);
             break;
         default:
             sweep_boundary_kernel<LBM_STORE_BF16DEV><<<nb, 128, 0, side>>>(d, cur);
-            sweep_bulk_kernel<LBM_STORE_BF16DEV><<<grid, block, 0, s>>>(d, cur);
+            sweep_fix_kernel<LBM_STORE_BF16DEV><<<nb, 128, 0, s>>>(d, cur);
             break;
     }
     cudaEventRecord(join, side);
     cudaStreamWaitEvent(s, join, 0);
-}
-
-// the bulk kernel alone on one stream (FP32 storage): the frozen window's replay step
-void launch_sweep_bulk_f32(const Dev& d, int cur, cudaStream_t s) {
-    const int bx = d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
-    const int by = 128 / bx;
-    dim3 block(bx, by, 1);
-    dim3 grid((d.nx + bx - 1) / bx, (d.ny + by - 1) / by, d.nz);
-    sweep_bulk_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur);
 }
 
 }  // namespace lbm

@@ -72,7 +72,7 @@ def load():
     L.lbm_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64)]
     L.lbm_profile.argtypes = [vp, i32]
     L.lbm_copy_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
-    L.lbm_profile_read.argtypes = [vp, pd, ctypes.POINTER(ctypes.c_uint64)]
+    L.lbm_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]
     L.lbm_bubble_volumes_noalloc.argtypes = [vp, vp, vp, sz, i32, vp, vp]
     L.lbm_forward_frozen.argtypes = [vp, vp, vp]
     L.lbm_adjoint_step.argtypes = [vp, vp, vp, vp, pd, i32, pd, pd]
@@ -215,11 +215,12 @@ class Sim:
         _check("lbm_profile", load().lbm_profile(self.ctx, 1 if on else 0))
 
     def profile_read(self):
-        """(total sweep milliseconds, number of sweeps) recorded since the last read"""
-        ms = ctypes.c_double()
+        """(bulk sweep milliseconds, rest-of-sweep milliseconds, number of steps) recorded
+        since the last read"""
+        ms = (ctypes.c_double * 2)()
         n = ctypes.c_uint64()
-        _check("lbm_profile_read", load().lbm_profile_read(self.ctx, ctypes.byref(ms), ctypes.byref(n)))
-        return ms.value, n.value
+        _check("lbm_profile_read", load().lbm_profile_read(self.ctx, ms, ctypes.byref(n)))
+        return ms[0], ms[1], n.value
 
     def copy_bytes(self):
         """(host->device, device->host) bytes the library has copied so far"""
