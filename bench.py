@@ -54,6 +54,22 @@ def _workload(name, storage=None):
     return wl
 
 
+def _job_ms(dist, ms, device):
+    """the job's time: the maximum over ranks of each rank's timed region (milliseconds)"""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_mlups(cells_per_rank, steps, ws, ms):
+    """whole-job throughput: the cells all ranks updated over the job's time (weak scaling:
+    every rank runs its own replica of the workload)"""
+    return cells_per_rank * steps * ws / (ms * 1e-3) / 1e6
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -366,13 +382,9 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
     launches = sim.launches() - n0
-    ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = _job_ms(dist, e0.elapsed_time(e1), "cuda")
     st = sim.status()
-    value = wl.cells * args.steps * ws / (ms * 1e-3) / 1e6
+    value = _job_mlups(wl.cells, args.steps, ws, ms)
 
     line = {"metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
