@@ -27,6 +27,7 @@ def nvcc() -> str:
 def _deps():
     yield os.path.join(ROOT, "include", "lbm.h")
     yield os.path.join(CSRC, "lbm_internal.cuh")
+    yield os.path.join(CSRC, "lbm_conv.cuh")
 
 
 def _stale(obj: str, src: str) -> bool:

@@ -51,8 +51,9 @@ struct lbm_ctx {
     uint64_t h2d_bytes, d2h_bytes;   // host <-> device copies made by the library
     // second stream and fork/join events of the concurrent bulk / boundary sweep
     cudaStream_t side;
-    cudaEvent_t fork, join, fork2, join2, fork3, join3;
-    cudaStream_t epi;   // the end-of-step kernels when they overlap the next bulk sweep
+    cudaEvent_t fork, join, fork2, join2, fork3, join3, fork4, join4;
+    cudaStream_t epi;     // the end-of-step kernels when they overlap the next bulk sweep
+    cudaStream_t links;   // partner lists and obstacle-node links beside the sweep's rest
     bool side_ready;
 };
 
@@ -81,7 +82,7 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
+    size_t f[2], flags, mark, tmark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
         adj_srho, adj_part, total;
     size_t N, wl_cap, nbins_max;
 };
@@ -98,6 +99,7 @@ Layout layout_of(const lbm_params* p) {
     L.f[1] = take(19 * L.N * pdf_bytes(p));
     L.flags = take(L.N + 16);
     L.mark = take(L.N + 16);
+    L.tmark = take(L.N + 16);
     L.mass = take(4 * L.N);
     L.phi[0] = take(4 * L.N);
     L.phi[1] = take(4 * L.N);
@@ -160,14 +162,14 @@ void prof_collect(lbm_ctx* c, int slot) {
 void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
     const Dev& d = c->d;
     if (d.nsph > 0) {
-        cudaEventRecord(c->fork2, e);
-        cudaStreamWaitEvent(c->side, c->fork2, 0);
+        cudaEventRecord(c->fork4, e);
+        cudaStreamWaitEvent(c->side, c->fork4, 0);
         launch_spheres_move(d, c->side);
     }
     launch_conversions(d, g, e);
     if (d.nsph > 0) {
-        cudaEventRecord(c->join2, c->side);
-        cudaStreamWaitEvent(e, c->join2, 0);
+        cudaEventRecord(c->join4, c->side);
+        cudaStreamWaitEvent(e, c->join4, 0);
     }
     launch_spheres_cover(d, g, e);
     launch_end_scan(d, g, 0, e);
@@ -175,7 +177,9 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
 }
 
 int epilogue_launches(const Dev& d) { return 1 + spheres_launches(d) + 1 + (d.kappa ? 1 : 0); }
-int step_launches(const Dev& d, bool overlap) { return 3 + (overlap ? epilogue_launches(d) : 0); }
+int step_launches(const Dev& d, bool overlap) {
+    return 3 + spheres_links_launches(d) + (overlap ? epilogue_launches(d) : 0);
+}
 
 // one step reading grid cur: the bulk sweep on s and, with `overlap`, the end-of-step kernels
 // of the previous step concurrently on the epilogue stream; once both are done the fix pass
@@ -200,7 +204,14 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed =
     if (timed) cudaEventRecord(c->ev[4 * slot + 1], s);
     if (overlap) cudaStreamWaitEvent(s, c->join3, 0);
     if (timed) cudaEventRecord(c->ev[4 * slot + 2], s);
+    if (d.nsph > 0) {   // partner lists and obstacle-node links of this step, beside the sweep's rest
+        cudaEventRecord(c->fork2, s);
+        cudaStreamWaitEvent(c->links, c->fork2, 0);
+        launch_spheres_links(d, c->links);
+        cudaEventRecord(c->join2, c->links);
+    }
     launch_sweep_rest(d, cur, s, c->side, c->fork, c->join);
+    if (d.nsph > 0) cudaStreamWaitEvent(s, c->join2, 0);
     if (timed) {
         cudaEventRecord(c->ev[4 * slot + 3], s);
         c->ev_pending[slot] = true;
@@ -245,6 +256,7 @@ int first_step(lbm_ctx* c) {
     d.f[1] = a + L.f[1];
     d.flags = (uint8_t*)(a + L.flags);
     d.mark = (uint8_t*)(a + L.mark);
+    d.tmark = (uint8_t*)(a + L.tmark);
     d.mass = (float*)(a + L.mass);
     d.phi[0] = (float*)(a + L.phi[0]);
     d.phi[1] = (float*)(a + L.phi[1]);
@@ -296,6 +308,9 @@ int first_step(lbm_ctx* c) {
         if (cudaEventCreateWithFlags(&c->fork3, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->join3, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         if (cudaStreamCreateWithPriority(&c->epi, cudaStreamNonBlocking, hi_prio) != cudaSuccess) return LBM_ECUDA;
+        if (cudaStreamCreateWithPriority(&c->links, cudaStreamNonBlocking, hi_prio) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->fork4, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->join4, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         c->side_ready = true;
     }
     int rc = cuda_fail(cudaMemsetAsync(a, 0, L.total, s));
@@ -656,6 +671,9 @@ int lbm_destroy(lbm_ctx* c) {
         cudaEventDestroy(c->join3);
         cudaStreamDestroy(c->side);
         cudaStreamDestroy(c->epi);
+        cudaStreamDestroy(c->links);
+        cudaEventDestroy(c->fork4);
+        cudaEventDestroy(c->join4);
     }
     std::free(c->sph_stage);
     std::free(c->sc_stage);

@@ -101,6 +101,7 @@ struct SphereAcc {       // per-step momentum-exchange accumulators (zeroed by t
     double TJ[3];        // sum of (x - x_P) x (deviation part of dj)
     unsigned long long K[3];   // sum of the constant part of dj, times 36 (two's complement)
     unsigned long long XK[3];  // sum of x_img x (constant part), times 36
+    double C[3], TC[3];        // force and torque of the links between obstacle nodes of two spheres
 };
 struct Bubble {
     double V0, V, rho_g, Vif;    // reference volume, volume, gas density, interface part of V
@@ -151,7 +152,8 @@ struct Dev {
     float eps;
     void* f[2];               // PDF grids [19][N]
     uint8_t* flags;           // [N]
-    uint8_t* mark;            // [N] conversion / covering marks
+    uint8_t* mark;            // [N] conversion marks, zero between steps
+    uint8_t* tmark;           // [N] cover / uncover marks (K_TOUCH, K_UNCOV), zero between steps
     float* mass;              // [N]
     float* phi[2];            // [N] fill level, double-buffered with the PDFs
     uint32_t* owner;          // [N] bubble id of gas/interface cells, sphere id of obstacle cells
@@ -247,6 +249,13 @@ __device__ __forceinline__ void sph_offset(const Dev& d, const SphLink& l, const
         img[k] = xi;
         r[k] = (float)(xi - l.xi[k]) - l.xf[k];
     }
+}
+
+// barrier of all threads of the thread-block cluster, ordering their global-memory writes
+// before the reads that follow (release / acquire at cluster scope); a hardware barrier, not a
+// spin on memory
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
 
 // byte-wise atomic OR / AND on the mark array (4-byte aligned base); returns the old byte
@@ -453,12 +462,14 @@ void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side,
 void launch_conversions(const Dev& d, int nxt, cudaStream_t s);
 void launch_end_scan(const Dev& d, int cur, int set_reference, cudaStream_t s);
 void launch_curvature(const Dev& d, int nxt, cudaStream_t s);
+void launch_spheres_links(const Dev& d, cudaStream_t s);
 void launch_spheres_move(const Dev& d, cudaStream_t s);
 void launch_spheres_cover(const Dev& d, int nxt, cudaStream_t s);
 void prepare_sphere_kernels();
 
 void launch_bins_insert(const Dev& d, cudaStream_t s);
 int spheres_launches(const Dev& d);
+int spheres_links_launches(const Dev& d);
 void launch_init(const Dev& d, const double* bub_geom_dev, cudaStream_t s);
 void launch_bulk_all(const Dev& d, cudaStream_t s);
 void launch_fields(const Dev& d, int cur, float* rho, float* u, float* phi, uint8_t* flags, cudaStream_t s);

@@ -25,11 +25,10 @@ void launch_bins_insert(const Dev& d, cudaStream_t s) {
 }
 
 // Force and torque of the sweep from the split accumulators (constant part exact in
-// integers, times 36):  F = J + K/36,  T = TJ + (XK - x_P x K)/36.  Then the start-of-step
-// position is recorded and the sphere enters its bin.
-__global__ void sph_prepare_kernel(const Dev d) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= d.nsph) return;
+// integers, times 36), plus the links between obstacle nodes of two spheres:
+// F = J + K/36 + C,  T = TJ + (XK - x_P x K)/36 + TC.  Then the start-of-step position is
+// recorded.
+__device__ inline void sph_prepare_one(const Dev& d, const int P) {
     Sphere& s = d.sph[P];
     SphereAcc& a = d.acc[P];
     double K[3], XK[3];
@@ -44,15 +43,15 @@ __global__ void sph_prepare_kernel(const Dev d) {
     const double xK[3] = {s.x[1] * K[2] - s.x[2] * K[1], s.x[2] * K[0] - s.x[0] * K[2], s.x[0] * K[1] - s.x[1] * K[0]};
     const double inv36 = 1.0 / 36.0;
     for (int k = 0; k < 3; k++) {
-        s.F[k] = a.J[k] + K[k] * inv36;
-        s.T[k] = a.TJ[k] + (XK[k] - xK[k]) * inv36;
-        a.J[k] = 0.0; a.TJ[k] = 0.0; a.K[k] = 0ull; a.XK[k] = 0ull;
+        s.F[k] = (a.J[k] + K[k] * inv36) + a.C[k];
+        s.T[k] = (a.TJ[k] + (XK[k] - xK[k]) * inv36) + a.TC[k];
+        a.J[k] = 0.0; a.TJ[k] = 0.0; a.K[k] = 0ull; a.XK[k] = 0ull; a.C[k] = 0.0; a.TC[k] = 0.0;
         s.x0[k] = s.x[k];
     }
-    const size_t bi = bin_index(d, bin_coord(d, 0, s.x[0]), bin_coord(d, 1, s.x[1]), bin_coord(d, 2, s.x[2]));
-    const uint32_t slot = atomicAdd(&d.bin_cnt[bi], 1u);
-    if (slot < (uint32_t)d.bin_cap) d.bin_ids[bi * d.bin_cap + slot] = (uint32_t)P;
-    else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
+}
+__global__ void sph_prepare_kernel(const Dev d) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P < d.nsph) sph_prepare_one(d, P);
 }
 
 // visit every other sphere whose centre lies in the bins around sphere P
@@ -80,10 +79,11 @@ __device__ __forceinline__ void for_partners(const Dev& d, int P, const double* 
 // the momentum-exchange paragraph), reflected by Eq. bbrule with rho_w = 1 at P's surface.
 // One block per sphere P; its threads share the cells of each close partner's box, and only
 // cells that can be such a node (covered by Q, within R_P + 1.5 of P) are read.
-__global__ void sph_contact_kernel(const Dev d) {
-    const int P = blockIdx.x;
-    if (P >= d.nsph) return;
-    Sphere& s = d.sph[P];
+// links between obstacle nodes of sphere P and of its partners, by a group of nt threads
+// (a multiple of 32; t the thread's index in the group); the group's sums go to F_P, T_P with
+// one FP64 atomic per warp
+__device__ inline void sph_contact_one(const Dev& d, const int P, const int t, const int nt) {
+    const Sphere& s = d.sph[P];
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
     const int L[3] = {d.nx, d.ny, d.nz};
     const uint32_t np = min(d.npairs[P], (uint32_t)kPairCap);
@@ -108,7 +108,7 @@ __global__ void sph_contact_kernel(const Dev d) {
             const int total = ext[0] * ext[1] * ext[2];
             // a necessary condition only (the lattice's owners decide), with a margin for FP32
             const float RQ2 = (float)(o.R * o.R) + 0.01f, RP2 = (float)((s.R + 1.5) * (s.R + 1.5)) + 0.01f;
-            for (int e = threadIdx.x; e < total; e += blockDim.x) {
+            for (int e = t; e < total; e += nt) {
                 const int ex[3] = {e % ext[0], (e / ext[0]) % ext[1], e / (ext[0] * ext[1])};
                 int w[3] = {lo[0] + ex[0], lo[1] + ex[1], lo[2] + ex[2]};
                 float aq = 0.f, ap = 0.f;
@@ -160,31 +160,24 @@ __global__ void sph_contact_kernel(const Dev d) {
             }
         }
     }
-    __shared__ double red[6][32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (np == 0) return;   // (uniform over the group)
+    const int lane = t & 31;
     double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
-    for (int c = 0; c < 6; c++) {
-        v[c] = warp_sum(v[c]);
-        if (lane == 0) red[c][wid] = v[c];
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int c = 0; c < 6; c++) {
-            double t = 0.0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); k++) t += red[c][k];
-            if (c < 3) s.F[c] += t;
-            else s.T[c - 3] += t;
-        }
-    }
+    for (int c = 0; c < 6; c++) v[c] = warp_sum(v[c]);
+    SphereAcc& a = d.acc[P];
+    if (lane == 0)
+        for (int c = 0; c < 6; c++)
+            if (v[c] != 0.0) atomicAdd(c < 3 ? &a.C[c] : &a.TC[c - 3], v[c]);
+}
+
+__global__ void sph_contact_kernel(const Dev d) {
+    if (blockIdx.x < (unsigned)d.nsph) sph_contact_one(d, blockIdx.x, threadIdx.x, blockDim.x);
 }
 
 // partners of sphere P this step: centre distance below R_P + R_Q + 2, which covers the
 // lubrication reach (gap < 2/3, the spheres moving less than half a cell per step) and the
 // reach of links between obstacle nodes; one warp per sphere, lanes over the 27 bins
-__global__ void sph_pairs_kernel(const Dev d) {
-    const uint32_t P = warp_id();
-    const int lane = threadIdx.x & 31;
-    if (P >= (uint32_t)d.nsph) return;
+__device__ inline void sph_pairs_one(const Dev& d, const uint32_t P, const int lane) {
     const Sphere& s = d.sph[P];
     if (lane == 0) d.npairs[P] = 0;
     __syncwarp();
@@ -212,6 +205,11 @@ __global__ void sph_pairs_kernel(const Dev d) {
             else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
         }
     }
+}
+
+__global__ void sph_pairs_kernel(const Dev d) {
+    const uint32_t P = warp_id();
+    if (P < (uint32_t)d.nsph) sph_pairs_one(d, P, threadIdx.x & 31);
 }
 
 // one Newton-Euler sub-step of sphere P (Sec. 2.3): lubrication (Eq. lubrication, gap
@@ -265,8 +263,7 @@ __global__ void sph_substep_kernel(const Dev d, const Sphere* src, Sphere* dst, 
 // of every sphere live in shared memory (double-buffered), the block's barrier separates the
 // sub-steps; the same arithmetic as substep_one.  The sub-steps move a sphere by far less than
 // a quarter cell per step, so the pair prefilter uses the step-start centres.
-__global__ void sph_substeps_fused_kernel(const Dev d, const double dt) {
-    extern __shared__ double smem[];
+__device__ inline void sph_substeps_block(const Dev& d, const double dt, double* smem) {
     const int n = d.nsph;
     double* xs[2] = {smem, smem + 3 * n};
     double* us[2] = {smem + 6 * n, smem + 9 * n};
@@ -385,15 +382,26 @@ __global__ void sph_substeps_fused_kernel(const Dev d, const double dt) {
     }
 }
 
-__global__ void sph_prescribed_kernel(const Dev d) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P >= d.nsph) return;
+// the step's force and torque (sph_prepare_one) and all sub-steps in one block
+__global__ void sph_substeps_fused_kernel(const Dev d, const double dt) {
+    extern __shared__ double smem[];
+    if (threadIdx.x < (unsigned)d.nsph) sph_prepare_one(d, threadIdx.x);
+    __syncthreads();
+    sph_substeps_block(d, dt, smem);
+}
+
+__device__ inline void sph_prescribed_one(const Dev& d, const int P) {
     Sphere& s = d.sph[P];
     const int L[3] = {d.nx, d.ny, d.nz};
     for (int k = 0; k < 3; k++) {
         s.x[k] += s.u[k];
         if (d.bc[k]) s.x[k] = wrap_pos(s.x[k], L[k]);
     }
+}
+
+__global__ void sph_prescribed_kernel(const Dev d) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P < d.nsph) sph_prescribed_one(d, P);
 }
 
 __global__ void sph_copy_kernel(const Dev d) {
@@ -404,16 +412,15 @@ __global__ void sph_copy_kernel(const Dev d) {
 // ---------------------------------------------------------------- cover / uncover
 // One block per sphere: cells of the union of its old and new boxes whose coverage by this
 // sphere changed are touched (deduplicated into a worklist).
-__global__ void cover_touch_kernel(const Dev d) {
-    const int P = blockIdx.x;
-    if (P >= d.nsph) return;
+// by a group of nt threads (t the thread's index in the group)
+__device__ inline void cover_touch_one(const Dev& d, const int P, const int t, const int nt) {
     const Sphere& s = d.sph[P];
-    if (threadIdx.x == 0) d.sphl[P] = sph_link_of(s);   // the next sweep's link data
+    if (t == 0) d.sphl[P] = sph_link_of(s);   // the next sweep's link data
     if (s.x[0] == s.x0[0] && s.x[1] == s.x0[1] && s.x[2] == s.x0[2]) return;
     // a sphere whose centre is not finite or moved more than a cell in one step is left alone
     // (the fluid has gone unstable; the status word says so)
     if (!finite3(s.x) || !finite3(s.x0) || !(s.R > 0.0 && s.R < 64.0)) {
-        if (threadIdx.x == 0) atomicOr(&d.sc->status, S_UNSTABLE);
+        if (t == 0) atomicOr(&d.sc->status, S_UNSTABLE);
         return;
     }
     const int L[3] = {d.nx, d.ny, d.nz};
@@ -427,7 +434,7 @@ __global__ void cover_touch_kernel(const Dev d) {
     }
     const int lim = 2 * (int)ceil(s.R) + 8;
     if (ext[0] > lim || ext[1] > lim || ext[2] > lim) {
-        if (threadIdx.x == 0) atomicOr(&d.sc->status, S_UNSTABLE);
+        if (t == 0) atomicOr(&d.sc->status, S_UNSTABLE);
         return;
     }
     const int total = ext[0] * ext[1] * ext[2];
@@ -441,7 +448,7 @@ __global__ void cover_touch_kernel(const Dev d) {
     }
     // FP32 squared distances below ~50 carry an error under 1e-5 here
     const float R2f = (float)R2, band = 1e-4f * (1.f + R2f);
-    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    for (int e = t; e < total; e += nt) {
         const int ex[3] = {e % ext[0], (e / ext[0]) % ext[1], e / (ext[0] * ext[1])};
         int w[3] = {lo[0] + ex[0], lo[1] + ex[1], lo[2] + ex[2]};
         float f0 = 0.f, f1 = 0.f;
@@ -471,21 +478,25 @@ __global__ void cover_touch_kernel(const Dev d) {
         }
         if (!ok) continue;
         const size_t i = cell_index(d, w[0], w[1], w[2]);
-        const uint8_t old = mark_or(d.mark, i, K_TOUCH);
+        const uint8_t old = mark_or(d.tmark, i, K_TOUCH);
         if (!(old & K_TOUCH)) wl_push(d.wl_touch, &d.sc->n_touch, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
     }
+}
+
+__global__ void cover_touch_kernel(const Dev d) {
+    if (blockIdx.x < (unsigned)d.nsph) cover_touch_one(d, blockIdx.x, threadIdx.x, blockDim.x);
 }
 
 // touched cells: the lowest id of the spheres covering them now decides; obstacle cells no
 // sphere covers any more are uncovered; newly covered cells lose their fluid mass.  One warp
 // per cell, its lanes over the 27 neighbouring bins.
 template <int S>
-__global__ void cover_apply_kernel(const Dev d, const int nxt) {
+__device__ inline void cover_apply_dev(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
     using T = typename Store<S>::T;
     const T* f = static_cast<const T*>(d.f[nxt]);
     const uint32_t n = min(*(volatile uint32_t*)&d.sc->n_touch, (uint32_t)d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+    for (uint32_t e = wid; e < n; e += nw) {
         const size_t i = d.wl_touch[e];
         int x, y, z;
         cell_xyz(d, i, x, y, z);
@@ -508,7 +519,7 @@ __global__ void cover_apply_kernel(const Dev d, const int nxt) {
         const float rl = (t & F_LIQ) ? warp_sum(lane < kQ ? Store<S>::get_nc(f, (size_t)lane * d.N + i) : 0.f) : 0.f;
         if (lane != 0) continue;
         if (t & F_OBS) {
-            if (own == kNone) mark_or(d.mark, i, K_UNCOV);
+            if (own == kNone) mark_or(d.tmark, i, K_UNCOV);
             else d.owner[i] = own;
         } else if (own != kNone) {
             if (t & F_LIQ) {
@@ -527,22 +538,22 @@ __global__ void cover_apply_kernel(const Dev d, const int nxt) {
 // uncovered now: only gas -> gas; gas and liquid/interface -> interface with m = mean phi *
 // mean rho; else liquid.  f* = e(mean rho, u_P + w_P x (x - x_P)) of the sphere that left.
 template <int S>
-__global__ void cover_refill_kernel(const Dev d, const int nxt) {
+__device__ inline void cover_refill_dev(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
     using T = typename Store<S>::T;
     T* f = static_cast<T*>(d.f[nxt]);
     float* phi = d.phi[nxt];
     const uint32_t n = min(*(volatile uint32_t*)&d.sc->n_touch, (uint32_t)d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+    for (uint32_t e = wid; e < n; e += nw) {
         const size_t i = d.wl_touch[e];
-        if (!(d.mark[i] & K_UNCOV)) continue;
+        if (!(d.tmark[i] & K_UNCOV)) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
         int isgas = 0, isfl = 0;
         float r = 0.f, ph = 0.f;
         uint32_t myown = kNone;
         size_t j;
-        if (lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j) && !(d.mark[j] & K_UNCOV)) {
+        if (lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j) && !(d.tmark[j] & K_UNCOV)) {
             const uint8_t t = d.flags[j] & F_TYPE;
             if (t & F_GAS) {
                 isgas = 1;
@@ -601,10 +612,10 @@ __global__ void cover_refill_kernel(const Dev d, const int nxt) {
 }
 
 // BULK bits of every touched cell and its neighbours; marks cleared
-__global__ void cover_finish_kernel(const Dev d) {
+__device__ inline void cover_finish_dev(const Dev& d, const uint32_t wid, const uint32_t nw) {
     const uint32_t n = min(*(volatile uint32_t*)&d.sc->n_touch, (uint32_t)d.wl_cap);
     const int lane = threadIdx.x & 31;
-    for (uint32_t e = warp_id(); e < n; e += warp_count()) {
+    for (uint32_t e = wid; e < n; e += nw) {
         const size_t i = d.wl_touch[e];
         if (lane >= kQ) continue;
         size_t j = i;
@@ -614,16 +625,44 @@ __global__ void cover_finish_kernel(const Dev d) {
             if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
         }
         set_bulk(d, j);
-        if (lane == 0) d.mark[i] = 0;   // BULK reads types only, never marks
+        if (lane == 0) d.tmark[i] = 0;   // BULK reads types only, never marks
     }
 }
 
-int spheres_launches(const Dev& d) {
+// the bins of the step-start centres are emptied (the end-of-step scan bins the new ones)
+__device__ inline void bins_clear(const Dev& d, const uint32_t t, const uint32_t nt) {
+    for (uint32_t P = t; P < (uint32_t)d.nsph; P += nt) {
+        const Sphere& sp = d.sph[P];
+        d.bin_cnt[bin_index(d, bin_coord(d, 0, sp.x0[0]), bin_coord(d, 1, sp.x0[1]), bin_coord(d, 2, sp.x0[2]))] = 0;
+    }
+}
+
+// apply, refill and finish in one launch: one thread-block cluster, the phases separated by
+// cluster barriers (the touched cells are few: launches, not work, would set the time); with
+// no touched cell it only empties the bins
+constexpr int kCoverCtas = 8, kCoverThreads = 512;
+template <int S>
+__global__ void __cluster_dims__(kCoverCtas, 1, 1) __launch_bounds__(kCoverThreads) cover_cluster_kernel(const Dev d, const int nxt) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const uint32_t wid = t >> 5, nw = nt >> 5;
+    if (*(volatile const uint32_t*)&d.sc->n_touch != 0u) {   // the same value for every thread
+        cover_apply_dev<S>(d, nxt, wid, nw);   // reads the bins
+        cluster_sync();
+        cover_refill_dev<S>(d, nxt, wid, nw);
+        cluster_sync();
+        cover_finish_dev(d, wid, nw);
+    }
+    bins_clear(d, t, nt);
+}
+
+int spheres_links_launches(const Dev& d) { return d.nsph == 0 ? 0 : 2; }
+
+int spheres_launches(const Dev& d) {   // launch_spheres_move + launch_spheres_cover
     if (d.nsph == 0) return 0;
-    int n = 3;  // prepare, contact, pairs
-    if (d.sphere_mode == LBM_SPHERES_FREE) n += d.nsph <= 1024 ? 1 : d.n_sub + (d.n_sub & 1);
-    else if (d.sphere_mode == LBM_SPHERES_PRESCRIBED) n += 1;
-    if (d.sphere_mode != LBM_SPHERES_FIXED) n += 4;
+    int n;
+    if (d.sphere_mode == LBM_SPHERES_FREE) n = d.nsph <= 1024 ? 1 : 1 + d.n_sub + (d.n_sub & 1);
+    else n = 1 + (d.sphere_mode == LBM_SPHERES_PRESCRIBED ? 1 : 0);
+    if (d.sphere_mode != LBM_SPHERES_FIXED) n += 2;   // touch, cover cluster
     return n;
 }
 
@@ -635,50 +674,56 @@ void prepare_sphere_kernels() {
 // forces of the step, lubrication partners, contact links and the sub-stepped motion: reads
 // only the sweep's force sums, the sphere table and obstacle cells, which the conversions
 // leave alone, so it may run concurrently with them
+// the cells whose coverage the move changes (reads only the sphere table; its marks have an
+// array of their own, so it may run while the conversions do)
+void launch_cover_touch(const Dev& d, cudaStream_t st) {
+    if (d.sphere_mode != LBM_SPHERES_FIXED) cover_touch_kernel<<<d.nsph, 128, 0, st>>>(d);
+}
+
+// partner lists and the links between obstacle nodes of two spheres: they read only the
+// step-start centres (binned), the sphere table and obstacle cells, so they run while the
+// sweep's boundary kernel does (their sums wait in the accumulators for sph_prepare_one)
+void launch_spheres_links(const Dev& d, cudaStream_t st) {
+    if (d.nsph == 0) return;
+    sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
+    sph_contact_kernel<<<d.nsph, 128, 0, st>>>(d);
+}
+
+// the step's force and torque, then the motion: sub-stepped Newton-Euler (free spheres) or
+// the prescribed velocity
 void launch_spheres_move(const Dev& d, cudaStream_t st) {
     if (d.nsph == 0) return;
     const int tb = 128, nb = (d.nsph + tb - 1) / tb;
+    if (d.sphere_mode == LBM_SPHERES_FREE && d.nsph <= 1024) {
+        const double dt = 1.0 / d.n_sub;
+        const size_t shm = sizeof(double) * 13 * (size_t)d.nsph + sizeof(float) * 3 * (size_t)d.nsph;
+        sph_substeps_fused_kernel<<<1, d.nsph <= 128 ? 128 : ((d.nsph + 31) / 32) * 32, shm, st>>>(d, dt);
+        launch_cover_touch(d, st);
+        return;
+    }
     sph_prepare_kernel<<<nb, tb, 0, st>>>(d);
-    sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
-    sph_contact_kernel<<<d.nsph, 128, 0, st>>>(d);
     if (d.sphere_mode == LBM_SPHERES_FREE) {
         const double dt = 1.0 / d.n_sub;
-        if (d.nsph <= 1024) {
-            const size_t shm = sizeof(double) * 13 * (size_t)d.nsph + sizeof(float) * 3 * (size_t)d.nsph;
-            sph_substeps_fused_kernel<<<1, d.nsph <= 128 ? 128 : ((d.nsph + 31) / 32) * 32, shm, st>>>(d, dt);
-        } else {
-            for (int k = 0; k < d.n_sub; k++) {
-                const Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
-                Sphere* dst = (k & 1) ? d.sph : d.sph_tmp;
-                sph_substep_kernel<<<nb, tb, 0, st>>>(d, src, dst, dt);
-            }
-            if (d.n_sub & 1) sph_copy_kernel<<<nb, tb, 0, st>>>(d);
+        for (int k = 0; k < d.n_sub; k++) {
+            const Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
+            Sphere* dst = (k & 1) ? d.sph : d.sph_tmp;
+            sph_substep_kernel<<<nb, tb, 0, st>>>(d, src, dst, dt);
         }
+        if (d.n_sub & 1) sph_copy_kernel<<<nb, tb, 0, st>>>(d);
     } else if (d.sphere_mode == LBM_SPHERES_PRESCRIBED) {
         sph_prescribed_kernel<<<nb, tb, 0, st>>>(d);
     }
+    launch_cover_touch(d, st);
 }
 
 // cells covered and uncovered by the moved spheres (after the conversions)
 void launch_spheres_cover(const Dev& d, int nxt, cudaStream_t st) {
     if (d.nsph == 0 || d.sphere_mode == LBM_SPHERES_FIXED) return;
-    cover_touch_kernel<<<d.nsph, 128, 0, st>>>(d);
-    const int lb = 2 * 152;
     switch (d.storage) {
-        case LBM_STORE_F32:
-            cover_apply_kernel<LBM_STORE_F32><<<lb, 128, 0, st>>>(d, nxt);
-            cover_refill_kernel<LBM_STORE_F32><<<lb, 128, 0, st>>>(d, nxt);
-            break;
-        case LBM_STORE_F16DEV:
-            cover_apply_kernel<LBM_STORE_F16DEV><<<lb, 128, 0, st>>>(d, nxt);
-            cover_refill_kernel<LBM_STORE_F16DEV><<<lb, 128, 0, st>>>(d, nxt);
-            break;
-        default:
-            cover_apply_kernel<LBM_STORE_BF16DEV><<<lb, 128, 0, st>>>(d, nxt);
-            cover_refill_kernel<LBM_STORE_BF16DEV><<<lb, 128, 0, st>>>(d, nxt);
-            break;
+        case LBM_STORE_F32: cover_cluster_kernel<LBM_STORE_F32><<<kCoverCtas, kCoverThreads, 0, st>>>(d, nxt); break;
+        case LBM_STORE_F16DEV: cover_cluster_kernel<LBM_STORE_F16DEV><<<kCoverCtas, kCoverThreads, 0, st>>>(d, nxt); break;
+        default: cover_cluster_kernel<LBM_STORE_BF16DEV><<<kCoverCtas, kCoverThreads, 0, st>>>(d, nxt); break;
     }
-    cover_finish_kernel<<<lb, 128, 0, st>>>(d);
 }
 
 }  // namespace lbm

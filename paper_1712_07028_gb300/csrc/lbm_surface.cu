@@ -6,274 +6,10 @@
 // whose fill level crossed a threshold), so their cost scales with the number of converting
 // cells, not with the grid.  Marks live in a separate byte array that is all zero outside
 // this phase; every phase that a later phase depends on ends at a kernel boundary.
-#include "lbm_internal.cuh"
+#include "lbm_conv.cuh"
 
 namespace lbm {
 
-
-__device__ __forceinline__ uint32_t list_len(const uint32_t* cnt, int cap) {
-    const uint32_t n = *(volatile const uint32_t*)cnt;
-    return n < (uint32_t)cap ? n : (uint32_t)cap;
-}
-
-// fill level seen by the normal and curvature stencils: interface -> phi, liquid -> 1,
-// gas -> 0, obstacle and beyond a wall -> 1 (perfect wetting, Sec. 2.2)
-__device__ __forceinline__ float fill_seen(const Dev& d, const float* phi, int x, int y, int z, int dx, int dy, int dz) {
-    size_t j;
-    if (!nbr(d, x, y, z, dx, dy, dz, j)) return 1.f;
-    const uint8_t t = d.flags[j] & F_TYPE;
-    if (t & F_IF) return phi[j];
-    if (t & F_GAS) return 0.f;
-    return 1.f;
-}
-
-// Parker-Youngs gradient of the fill level (points into the liquid): central difference
-// smoothed with [1,2,1] x [1,2,1] / 16 over the 3x3x3 block
-__device__ void py_gradient(const Dev& d, const float* phi, int x, int y, int z, float n[3]) {
-    float v[27];
-#pragma unroll
-    for (int c = -1; c <= 1; c++)
-#pragma unroll
-        for (int b = -1; b <= 1; b++)
-#pragma unroll
-            for (int a = -1; a <= 1; a++)
-                v[(c + 1) * 9 + (b + 1) * 3 + (a + 1)] = (a == 0 && b == 0 && c == 0) ? 0.f : fill_seen(d, phi, x, y, z, a, b, c);
-    const float w1[3] = {1.f, 2.f, 1.f};
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-#pragma unroll
-    for (int p = 0; p < 3; p++)
-#pragma unroll
-        for (int r = 0; r < 3; r++) {
-            const float w = w1[p] * w1[r];
-            gx += w * (v[r * 9 + p * 3 + 2] - v[r * 9 + p * 3 + 0]);
-            gy += w * (v[r * 9 + 2 * 3 + p] - v[r * 9 + 0 * 3 + p]);
-            gz += w * (v[2 * 9 + r * 3 + p] - v[0 * 9 + r * 3 + p]);
-        }
-    n[0] = gx / 32.f;
-    n[1] = gy / 32.f;
-    n[2] = gz / 32.f;
-}
-
-template <int S>
-__device__ float cell_rho(const Dev& d, const typename Store<S>::T* f, size_t i) {
-    float dr = 0.f;
-#pragma unroll
-    for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + i);
-    return 1.f + dr;
-}
-
-// Every conversion kernel runs one warp per listed cell: lane q (1..18) handles the D3Q19
-// neighbour x + c_q, lane 0 the cell itself, and warp shuffles combine what they find.
-
-// density of cell i from grid f (deviations), summed over the warp's lanes 0..18
-template <int S>
-__device__ __forceinline__ float warp_cell_rho(const Dev& d, const typename Store<S>::T* f, size_t i, int lane) {
-    const float v = lane < kQ ? Store<S>::get_nc(f, (size_t)lane * d.N + i) : 0.f;
-    return 1.f + warp_sum(v);
-}
-
-// (ii) + (iii) in one phase.  Filled cells: gas neighbours become new interface cells (mass
-// 0 from the start).  Emptied cells: an emptied cell with a filled neighbour stays an
-// interface cell (filling wins: it clears its own mark); otherwise its liquid neighbours
-// become interface cells with m = rho, the smallest bubble id among their emptied neighbours
-// becoming theirs.  The filled marks are final before this phase (written by the sweep).
-template <int S>
-__device__ void conv_filled_emptied(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
-    using T = typename Store<S>::T;
-    const T* f = static_cast<const T*>(d.f[nxt]);
-    const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
-    const int lane = threadIdx.x & 31;
-    for (uint32_t e = wid; e < n; e += nw) {
-        const size_t i = d.wl_conv[e];
-        const uint8_t mk = d.mark[i];
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        size_t j = 0;
-        const bool has = lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j);
-        if (mk & K_FILLED) {
-            if (!has) continue;
-            if (d.flags[j] & F_GAS) {
-                const uint8_t old = mark_or(d.mark, j, K_NEWIF);
-                if (!(old & K_NEWIF)) {
-                    d.mass[j] = 0.f;
-                    wl_push(d.wl_newif, &d.sc->n_newif, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
-                }
-            }
-        } else if (mk & K_EMPTIED) {
-            const bool filled_nbr = __any_sync(0xffffffffu, has && (d.mark[j] & K_FILLED));
-            if (filled_nbr) {
-                if (lane == 0) mark_and(d.mark, i, K_EMPTIED);
-                continue;
-            }
-            if (!has || !(d.flags[j] & F_LIQ)) continue;
-            const uint32_t b = d.owner[i];
-            const uint8_t old = mark_or(d.mark, j, K_FROMLIQ);
-            if (!(old & K_FROMLIQ)) {
-                float dr = 0.f;
-                for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + j);
-                d.mass[j] = 1.f + dr;
-                wl_push(d.wl_fromliq, &d.sc->n_fromliq, (uint32_t)d.wl_cap, (uint32_t)j, &d.sc->status);
-            }
-            atomicMin(&d.owner[j], b);
-        }
-    }
-}
-
-// (iv) new interface cells from gas: f* = e(mean rho, mean u) over the neighbours that carry
-// PDFs (liquid, interface not emptied, filled); their m = 0 was set when they were marked
-template <int S>
-__device__ void conv_newif(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
-    using T = typename Store<S>::T;
-    T* f = static_cast<T*>(d.f[nxt]);
-    const uint32_t n = list_len(&d.sc->n_newif, d.wl_cap);
-    const int lane = threadIdx.x & 31;
-    for (uint32_t e = wid; e < n; e += nw) {
-        const size_t i = d.wl_newif[e];
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        float r = 0.f, u[3] = {0.f, 0.f, 0.f};
-        int c = 0;
-        size_t j;
-        if (lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j) &&
-            (d.flags[j] & F_ACTIVE) && !(d.mark[j] & K_EMPTIED)) {
-            post_moments<S>(d, f, j, r, u);
-            c = 1;
-        }
-        const int cnt = warp_sum(c);
-        const float rs = warp_sum(r), ux = warp_sum(u[0]), uy = warp_sum(u[1]), uz = warp_sum(u[2]);
-        const float rb = cnt ? rs / cnt : 1.f;
-        const float ub[3] = {cnt ? ux / cnt : 0.f, cnt ? uy / cnt : 0.f, cnt ? uz / cnt : 0.f};
-        if (lane < kQ) Store<S>::put(f, (size_t)lane * d.N + i, equilibrium_dev(lane, rb, ub));
-    }
-}
-
-// (v) excess mass of converting cells to the neighbours that will be interface cells,
-// weighted along the interface normal pointing into the gas (-grad phi): filled cells push
-// along it, emptied cells against it; uniform if all weights vanish; to the global pool if
-// no neighbour can take it.  The Parker-Youngs gradient is taken over the 3x3x3 block, lane l
-// (0..26) holding the fill level of offset (l%3-1, l/3%3-1, l/9-1).
-template <int S>
-__device__ void conv_excess(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
-    using T = typename Store<S>::T;
-    const T* f = static_cast<const T*>(d.f[nxt]);
-    const float* phi = d.phi[nxt];
-    const uint32_t n = list_len(&d.sc->n_conv, d.wl_cap);
-    const int lane = threadIdx.x & 31;
-    for (uint32_t e = wid; e < n; e += nw) {
-        const size_t i = d.wl_conv[e];
-        const uint8_t mk = d.mark[i] & (K_FILLED | K_EMPTIED);
-        if (!mk) continue;
-        int x, y, z;
-        cell_xyz(d, i, x, y, z);
-        // Parker-Youngs: central difference smoothed by [1,2,1] x [1,2,1] / 16 (into the liquid)
-        float gxl = 0.f, gyl = 0.f, gzl = 0.f;
-        if (lane < 27 && lane != 13) {
-            const int a = lane % 3 - 1, b = (lane / 3) % 3 - 1, c = lane / 9 - 1;
-            const float v = fill_seen(d, phi, x, y, z, a, b, c);
-            const float wa = a == 0 ? 2.f : 1.f, wb = b == 0 ? 2.f : 1.f, wc = c == 0 ? 2.f : 1.f;
-            gxl = a * wb * wc * v;
-            gyl = b * wa * wc * v;
-            gzl = c * wa * wb * v;
-        }
-        const float ngx = -warp_sum(gxl) / 32.f, ngy = -warp_sum(gyl) / 32.f, ngz = -warp_sum(gzl) / 32.f;
-        const float r = warp_cell_rho<S>(d, f, i, lane);
-        const float m0 = d.mass[i];
-        const float mex = (mk & K_FILLED) ? m0 - r : m0;
-        size_t j = 0;
-        bool rec = false;
-        float w = 0.f;
-        if (lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) {
-            const uint8_t mj = d.mark[j];
-            rec = ((d.flags[j] & F_IF) && !(mj & (K_FILLED | K_EMPTIED))) || (mj & (K_NEWIF | K_FROMLIQ));
-            if (rec) {
-                const float nc = ngx * cx(lane) + ngy * cy(lane) + ngz * cz(lane);
-                w = (mk & K_FILLED) ? fmaxf(nc, 0.f) : fmaxf(-nc, 0.f);
-            }
-        }
-        // the lanes' weights in q order, as a serial sum would take them
-        float W = 0.f;
-        int nr = 0;
-        for (int q = 1; q < kQ; q++) {
-            W += __shfl_sync(0xffffffffu, w, q);
-            nr += __shfl_sync(0xffffffffu, (int)rec, q);
-        }
-        if (lane == 0) {
-            d.mass[i] = (mk & K_FILLED) ? r : 0.f;
-            if (nr == 0) atomicAdd(&d.sc->pool_acc, (double)mex);
-        }
-        if (rec) {
-            atomicAdd(&d.mass[j], W > 0.f ? mex * (w / W) : mex / (float)nr);
-            mark_or(d.mark, j, K_RECV);
-        }
-    }
-}
-
-// (vi) final types; fill level of every interface cell whose mass changed in this phase
-template <int S>
-__device__ void conv_finalize(const Dev& d, const int nxt, const uint32_t wid, const uint32_t nw) {
-    using T = typename Store<S>::T;
-    const T* f = static_cast<const T*>(d.f[nxt]);
-    float* phi = d.phi[nxt];
-    const uint32_t n1 = list_len(&d.sc->n_conv, d.wl_cap);
-    const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
-    const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
-    const int lane = threadIdx.x & 31;
-    for (uint32_t e = wid; e < n1 + n2 + n3; e += nw) {
-        if (e < n1) {
-            const size_t i = d.wl_conv[e];
-            const uint8_t mk = d.mark[i];
-            if (lane == 0) {
-                if (mk & K_FILLED) { d.flags[i] = F_LIQ; d.owner[i] = kNone; }
-                else if (mk & K_EMPTIED) { d.flags[i] = F_GAS; }
-            }
-            if (lane == 0 || lane >= kQ) continue;
-            int x, y, z;
-            cell_xyz(d, i, x, y, z);
-            size_t j;
-            if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
-            const uint8_t mj = d.mark[j];
-            if ((mj & K_RECV) && !(mj & (K_NEWIF | K_FROMLIQ))) {
-                float dr = 0.f;
-                for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + j);
-                phi[j] = d.mass[j] / (1.f + dr);
-            }
-        } else {
-            const size_t i = e < n1 + n2 ? d.wl_newif[e - n1] : d.wl_fromliq[e - n1 - n2];
-            const float r = warp_cell_rho<S>(d, f, i, lane);
-            if (lane == 0) {
-                d.flags[i] = F_IF;
-                phi[i] = d.mass[i] / r;
-            }
-        }
-    }
-}
-
-// (vii) BULK bits of every cell whose type changed and of its neighbours; marks cleared
-__device__ void conv_bulk(const Dev& d, const uint32_t wid, const uint32_t nw) {
-    const uint32_t n1 = list_len(&d.sc->n_conv, d.wl_cap);
-    const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
-    const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
-    const int lane = threadIdx.x & 31;
-    for (uint32_t e = wid; e < n1 + n2 + n3; e += nw) {
-        const size_t i = e < n1 ? d.wl_conv[e] : (e < n1 + n2 ? d.wl_newif[e - n1] : d.wl_fromliq[e - n1 - n2]);
-        if (lane >= kQ) continue;
-        size_t j = i;
-        if (lane > 0) {
-            int x, y, z;
-            cell_xyz(d, i, x, y, z);
-            if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
-        }
-        set_bulk(d, j);
-        d.mark[j] = 0;
-    }
-}
-
-// barrier of all threads of the thread-block cluster, ordering their global-memory writes
-// before the reads that follow (release / acquire at cluster scope); a hardware barrier, not a
-// spin on memory
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
-}
 
 // all conversion phases in one launch: one cluster of kClusterCtas blocks, the phases separated
 // by cluster barriers (every thread reaches every barrier)
@@ -322,6 +58,8 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
     unsigned long long* sG = reinterpret_cast<unsigned long long*>(sV + d.max_bub);
     __shared__ unsigned int sIf;
     __shared__ bool last;
+    __shared__ uint32_t sWarp[32];
+    __shared__ uint32_t sBase;
     for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) { sV[b] = 0.0; sG[b] = 0ull; }
     if (threadIdx.x == 0) sIf = 0;
     __syncthreads();
@@ -359,11 +97,21 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
             const uint32_t y = __shfl_up_sync(full, incl, o);
             if (lane >= o) incl += y;
         }
-        const uint32_t tot = __shfl_sync(full, incl, 31);
-        uint32_t base_slot = 0;
-        if (lane == 31 && tot) base_slot = atomicAdd(&d.sc->n_slow, tot);
-        base_slot = __shfl_sync(full, base_slot, 31);
-        uint32_t slot = base_slot + incl - cnt;
+        // one append per block: warp totals -> block prefix -> one atomic on the list length
+        if (lane == 31) sWarp[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+                const uint32_t v = sWarp[k];
+                sWarp[k] = acc;
+                acc += v;
+            }
+            sBase = acc ? atomicAdd(&d.sc->n_slow, acc) : 0u;
+        }
+        __syncthreads();
+        uint32_t slot = sBase + sWarp[threadIdx.x >> 5] + incl - cnt;
+        __syncthreads();   // sWarp / sBase are rewritten in the next round
         while (sel) {
             const int c = __ffs(sel) - 1;
             sel &= sel - 1;
@@ -400,17 +148,32 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
             else cg++;
         }
     }
-    if (cb != kNone) {
+    // the lanes' last partial sums: summed over the warp first when the lanes agree on the
+    // bubble (the common case: one shared atomic per warp instead of one per lane)
+    const uint32_t lead = __reduce_min_sync(full, cb);
+    if (__all_sync(full, cb == lead || cb == kNone)) {
+        const double sv = warp_sum(cb == kNone ? 0.0 : cv);
+        const unsigned sg = __reduce_add_sync(full, cb == kNone ? 0u : (unsigned)cg);
+        if (lane == 0 && lead != kNone) {
+            if (sv != 0.0) atomicAdd(&sV[lead], sv);
+            if (sg) atomicAdd(&sG[lead], (unsigned long long)sg);
+        }
+    } else if (cb != kNone) {
         if (cv != 0.0) atomicAdd(&sV[cb], cv);
         if (cg) atomicAdd(&sG[cb], cg);
     }
-    if (nif) atomicAdd(&sIf, nif);
-    // the spheres' bins of this step are emptied (filled again by the next step)
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < d.nsph && d.bin_cnt) {
-        const Sphere& sp = d.sph[t];
-        d.bin_cnt[bin_index(d, bin_coord(d, 0, sp.x0[0]), bin_coord(d, 1, sp.x0[1]), bin_coord(d, 2, sp.x0[2]))] = 0;
-    }
+    const unsigned nifw = __reduce_add_sync(full, nif);
+    if (lane == 0 && nifw) atomicAdd(&sIf, nifw);
+    // moved spheres enter the bins of their new centres (emptied by the cover kernels), which
+    // the next step's partner search reads; fixed spheres keep the bins of the first step
+    if (!set_reference && d.sphere_mode != LBM_SPHERES_FIXED)
+        for (int P = blockIdx.x * blockDim.x + threadIdx.x; P < d.nsph; P += gridDim.x * blockDim.x) {
+            const Sphere& sp = d.sph[P];
+            const size_t bi = bin_index(d, bin_coord(d, 0, sp.x[0]), bin_coord(d, 1, sp.x[1]), bin_coord(d, 2, sp.x[2]));
+            const uint32_t slot = atomicAdd(&d.bin_cnt[bi], 1u);
+            if (slot < (uint32_t)d.bin_cap) d.bin_ids[bi * d.bin_cap + slot] = (uint32_t)P;
+            else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
+        }
     __syncthreads();
     for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
         if (sV[b] != 0.0) atomicAdd(&d.bub[b].Vif, sV[b]);
@@ -452,11 +215,9 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
 void launch_end_scan(const Dev& d, int cur, int set_reference, cudaStream_t s) {
     const size_t shm = (size_t)d.max_bub * (sizeof(double) + sizeof(unsigned long long));
     const size_t nvec = d.N / 16 + 1;
-    int blocks = (int)((nvec + 255) / 256);
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    const int need = (d.nsph + 255) / 256;   // one thread per sphere for the bin reset
-    if (blocks < need) blocks = need;
-    end_scan_kernel<<<blocks, 256, shm, s>>>(d, cur, set_reference);
+    int blocks = (int)((nvec + 511) / 512);
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    end_scan_kernel<<<blocks, 512, shm, s>>>(d, cur, set_reference);
 }
 
 // ---------------------------------------------------------------------- curvature

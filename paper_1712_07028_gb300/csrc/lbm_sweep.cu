@@ -82,13 +82,32 @@ __device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>:
                                           typename Store<S>::T* __restrict__ fb, int x, int y, int z, uint32_t i) {
     using T = typename Store<S>::T;
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+    float fin[kQ];
+    if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+        // y and z neighbours inside the grid (the same for a whole warp, which spans x): the
+        // source of direction q is i - c_q . (1, nx, nx ny), a grid-uniform offset, except
+        // across the x edges (periodic wrap, or bounce-back from a wall)
+        const bool edge0 = x == 0, edge1 = x == d.nx - 1;
+        const bool perx = d.bc[0] != 0;
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int32_t o = cx(q) + cy(q) * (int32_t)nx + cz(q) * (int32_t)nxy;
+            bool wall = false;
+            int32_t adj = 0;
+            if (cx(q) == 1 && edge0) { if (perx) adj = (int32_t)nx; else wall = true; }
+            if (cx(q) == -1 && edge1) { if (perx) adj = -(int32_t)nx; else wall = true; }
+            const T* plane = fa + (size_t)(wall ? opp(q) : q) * d.N;
+            fin[q] = Store<S>::get(plane, wall ? i : i - (uint32_t)o + (uint32_t)adj);   // modulo 2^32
+        }
+        collide_store<S>(d, fb, i, fin);
+        return;
+    }
     const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
     const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
     const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
     const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
     const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
     const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
-    float fin[kQ];
 #pragma unroll
     for (int q = 0; q < kQ; q++) {
         const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
