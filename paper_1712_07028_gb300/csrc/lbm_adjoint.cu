@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128) frozen_boundary_kernel(const Dev d, const
     const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)d.N);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const uint32_t i = d.wl_slow[k];
-        if (!(d.flags[i] & F_LIQ)) continue;
+        if (i == kNone || !(d.flags[i] & F_LIQ) || (d.flags[i] & F_BULK)) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
         float fin[kQ], fo[kQ], cw[kQ], rho0;
@@ -307,7 +307,10 @@ __global__ void __launch_bounds__(128) adjoint_boundary_kernel(const Dev d, cons
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const uint32_t i = d.wl_slow[k];
-        if (!(d.flags[i] & F_LIQ)) continue;
+        if (i == kNone || !(d.flags[i] & F_LIQ) || (d.flags[i] & F_BULK)) {
+            if (moving) srho[k] = 0.f;
+            continue;
+        }
         int x, y, z;
         cell_xyz(d, i, x, y, z);
         float fin[kQ], fo[kQ], cw[kQ], rho0;
@@ -342,16 +345,16 @@ __global__ void adjoint_rho_kernel(const Dev d, const float* __restrict__ srho, 
     const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)d.N);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
         const uint32_t i = d.wl_slow[k];
-        if (!(d.flags[i] & F_LIQ)) continue;
+        if (i == kNone || !(d.flags[i] & F_LIQ) || (d.flags[i] & F_BULK)) continue;
         const float s = srho[k];
         if (s == 0.f) continue;
         for (int q = 0; q < kQ; q++) lam_out[(size_t)q * d.N + i] += s;
     }
 }
 
-void launch_adjoint(const Dev& d, const float* f_fwd, const float* lam_in, float* lam_out, float* srho, const float jdir[3],
-                    double* part, bool moving_walls, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
-                    cudaEvent_t join) {
+void launch_adjoint(const Dev& d, const float* f_fwd, const float* lam_in, float* lam_out, float* srho,
+                    const float jdir[3], double* part, bool moving_walls, cudaStream_t s, cudaStream_t side,
+                    cudaEvent_t fork, cudaEvent_t join) {
     const int bx = d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
     const int by = 128 / bx;
     const dim3 block(bx, by, 1);

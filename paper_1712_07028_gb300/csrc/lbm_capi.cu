@@ -166,17 +166,19 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
         cudaStreamWaitEvent(c->side, c->fork4, 0);
         launch_spheres_move(d, c->side);
     }
-    launch_conversions(d, g, e);
+    // the conversions close the step themselves unless the cover kernel follows
+    const bool cover = d.nsph > 0 && d.sphere_mode != LBM_SPHERES_FIXED;
+    launch_conversions(d, g, !cover, e);
     if (d.nsph > 0) {
         cudaEventRecord(c->join4, c->side);
         cudaStreamWaitEvent(e, c->join4, 0);
     }
     launch_spheres_cover(d, g, e);
-    launch_end_scan(d, g, 0, e);
     if (d.kappa) launch_curvature(d, g, e);
+    launch_list_rescan(d, e);   // the next boundary sweep's list, from the final types
 }
 
-int epilogue_launches(const Dev& d) { return 1 + spheres_launches(d) + 1 + (d.kappa ? 1 : 0); }
+int epilogue_launches(const Dev& d) { return 1 + spheres_launches(d) + (d.kappa ? 1 : 0) + 1; }
 int step_launches(const Dev& d, bool overlap) {
     return 3 + spheres_links_launches(d) + (overlap ? epilogue_launches(d) : 0);
 }
@@ -329,7 +331,7 @@ int first_step(lbm_ctx* c) {
     launch_bins_insert(d, s);
     launch_init(d, c->geo_dev, s);
     launch_bulk_all(d, s);
-    launch_end_scan(d, 0, 1, s);
+    launch_init_scan(d, s);
     if (d.kappa) launch_curvature(d, 0, s);
     if ((rc = launched(c, (d.nsph > 0) + 3 + (d.kappa ? 1 : 0)))) return rc;
     c->cur = 0;

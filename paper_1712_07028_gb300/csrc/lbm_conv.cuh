@@ -217,37 +217,56 @@ __device__ void conv_finalize(const Dev& d, const int nxt, const uint32_t wid, c
     const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);
     const uint32_t n3 = list_len(&d.sc->n_fromliq, d.wl_cap);
     const int lane = threadIdx.x & 31;
+    // every change of type or fill level also updates the bubble volumes (interface part
+    // 1 - phi, gas cells) and the interface count
     for (uint32_t e = wid; e < n1 + n2 + n3; e += nw) {
         if (e < n1) {
             const size_t i = d.wl_conv[e];
             const uint8_t mk = d.mark[i];
-            if (lane == 0) {
-                if (mk & K_FILLED) { d.flags[i] = F_LIQ; d.owner[i] = kNone; }
-                else if (mk & K_EMPTIED) { d.flags[i] = F_GAS; }
+            if (lane == 0 && (mk & (K_FILLED | K_EMPTIED))) {
+                const uint32_t b = d.owner[i];
+                const double was = 1.0 - (double)phi[i];
+                if (mk & K_FILLED) {
+                    d.flags[i] = F_LIQ;
+                    d.owner[i] = kNone;
+                    vol_change(d, b, -was, 0, -1);
+                } else {
+                    d.flags[i] = F_GAS;
+                    vol_change(d, b, -was, 1, -1);
+                }
             }
             if (lane == 0 || lane >= kQ) continue;
             int x, y, z;
             cell_xyz(d, i, x, y, z);
             size_t j;
             if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
-            const uint8_t mj = d.mark[j];
+            // a receiving interface cell is claimed once (it may neighbour several converting
+            // cells): its fill level from its new mass
+            const uint8_t mj = mark_and(d.mark, j, K_RECV);
             if ((mj & K_RECV) && !(mj & (K_NEWIF | K_FROMLIQ))) {
                 float dr = 0.f;
                 for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + j);
-                phi[j] = d.mass[j] / (1.f + dr);
+                const float was = phi[j];
+                const float now = d.mass[j] / (1.f + dr);
+                phi[j] = now;
+                vol_change(d, d.owner[j], (double)was - (double)now, 0, 0);
             }
         } else {
-            const size_t i = e < n1 + n2 ? d.wl_newif[e - n1] : d.wl_fromliq[e - n1 - n2];
+            const bool newif = e < n1 + n2;
+            const size_t i = newif ? d.wl_newif[e - n1] : d.wl_fromliq[e - n1 - n2];
             const float r = warp_cell_rho<S>(d, f, i, lane);
             if (lane == 0) {
                 d.flags[i] = F_IF;
-                phi[i] = d.mass[i] / r;
+                const float now = d.mass[i] / r;
+                phi[i] = now;
+                vol_change(d, d.owner[i], 1.0 - (double)now, newif ? -1 : 0, 1);
             }
         }
     }
 }
 
-// (vii) BULK bits of every cell whose type changed and of its neighbours; marks cleared
+// (vii) BULK bits of every cell whose type changed and of its neighbours (the boundary list
+// and the fix list follow); marks cleared
 __device__ inline void conv_bulk(const Dev& d, const uint32_t wid, const uint32_t nw) {
     const uint32_t n1 = list_len(&d.sc->n_conv, d.wl_cap);
     const uint32_t n2 = list_len(&d.sc->n_newif, d.wl_cap);

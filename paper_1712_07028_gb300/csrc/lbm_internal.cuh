@@ -123,11 +123,11 @@ struct Scalars {
     uint32_t status;      // LBM_S_* bits
     uint32_t n_conv, n_newif, n_fromliq, n_touch, n_uncov;
     uint32_t bin_overflow;
-    uint32_t n_slow;      // active cells the bulk sweep left to the boundary sweep
+    uint32_t n_slow;      // boundary-list length
     uint32_t ticket;      // blocks of the end-of-step scan that have finished
     uint32_t n_fix;       // BULK cells the end of the last step changed or whose neighbours it changed
     uint32_t fix_all;     // the fix list overflowed: the fix pass takes every BULK cell
-    uint32_t pad1[3];
+    uint32_t pad1[2];
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
@@ -168,7 +168,7 @@ struct Dev {
     uint32_t* wl_newif;
     uint32_t* wl_fromliq;
     uint32_t* wl_touch;
-    uint32_t* wl_slow;        // [N] per-step list of active cells for the boundary sweep
+    uint32_t* wl_slow;        // [N] boundary list: every active cell that is not BULK, in scan order
     uint32_t* wl_fix;         // [wl_cap] BULK cells to sweep again after the end-of-step kernels
     // uniform bins of sphere ids for the neighbour searches
     int bin_w, nbx, nby, nbz, bin_cap;
@@ -212,27 +212,6 @@ __device__ __forceinline__ bool bulk_of(const Dev& d, size_t i) {
     }
     return ok != 0;
 }
-// BULK bit of cell i from its neighbourhood.  The end-of-step kernels call it for every cell
-// whose type or PDFs they changed and for those cells' neighbours, while the next step's bulk
-// sweep may already be running on the types and PDFs it read before: every cell that comes out
-// BULK goes to the fix list, whose cells the sweep takes again once these kernels are done.
-__device__ __forceinline__ void set_bulk(const Dev& d, size_t i, bool to_fix = true) {
-    const uint8_t t = d.flags[i] & F_TYPE;
-    const bool b = bulk_of(d, i);
-    d.flags[i] = (uint8_t)(t | (b ? F_BULK : 0));
-    if (b && to_fix) {
-        const unsigned act = __activemask();
-        const int lane = threadIdx.x & 31;
-        const int leader = __ffs(act) - 1;
-        uint32_t base = 0;
-        if (lane == leader) base = atomicAdd(&d.sc->n_fix, (uint32_t)__popc(act));
-        base = __shfl_sync(act, base, leader);
-        const uint32_t slot = base + (uint32_t)__popc(act & ((1u << lane) - 1u));
-        if (slot < (uint32_t)d.wl_cap) d.wl_fix[slot] = (uint32_t)i;
-        else d.sc->fix_all = 1u;   // no fatal overflow: the fix pass then takes every BULK cell
-    }
-}
-
 // image (per periodic axis, the one nearest to the sphere centre) of cell c and its offset
 // c_img - x_P, from the sphere's link data
 __device__ __forceinline__ void sph_offset(const Dev& d, const SphLink& l, const int (&c)[3], int (&img)[3],
@@ -270,6 +249,45 @@ __device__ __forceinline__ uint8_t mark_and(uint8_t* base, size_t i, uint8_t bit
     const uint32_t sh = (uint32_t)(i & 3) * 8u;
     const uint32_t old = atomicAnd(w, ~((uint32_t)bits << sh));
     return (uint8_t)(old >> sh);
+}
+
+// BULK bit of cell i from its neighbourhood, set at initialisation
+__device__ __forceinline__ void set_bulk_init(const Dev& d, size_t i) {
+    const uint8_t t = d.flags[i] & F_TYPE;
+    d.flags[i] = (uint8_t)(t | (bulk_of(d, i) ? F_BULK : 0));
+}
+
+// BULK bit of cell i from its neighbourhood; the end-of-step kernels call it for every cell
+// whose type or PDFs they changed and for those cells' neighbours.  Only that bit changes, by
+// an atomic byte AND / OR (other threads update other bytes of the word, or this one).
+// The next step's bulk sweep may already be running on the types and PDFs it read before:
+// every cell that comes out BULK goes to the fix list, whose cells the sweep takes again once
+// these kernels are done.
+__device__ __forceinline__ void set_bulk(const Dev& d, size_t i) {
+    const bool b = bulk_of(d, i);
+    if (b) mark_or(d.flags, i, F_BULK);
+    else mark_and(d.flags, i, F_BULK);
+    if (b) {
+        const unsigned act = __activemask();
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(act) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&d.sc->n_fix, (uint32_t)__popc(act));
+        base = __shfl_sync(act, base, leader);
+        const uint32_t slot = base + (uint32_t)__popc(act & ((1u << lane) - 1u));
+        if (slot < (uint32_t)d.wl_cap) d.wl_fix[slot] = (uint32_t)i;
+        else d.sc->fix_all = 1u;   // no fatal overflow: the fix pass then takes every BULK cell
+    }
+}
+
+// bubble b's volume bookkeeping when a cell changes: dv to the interface part, dg gas cells,
+// di interface cells (any sign)
+__device__ __forceinline__ void vol_change(const Dev& d, uint32_t b, double dv, int dg, int di) {
+    if (b < (uint32_t)d.nbub) {
+        if (dv != 0.0) atomicAdd(&d.bub[b].Vif, dv);
+        if (dg) atomicAdd(&d.bub[b].ngas, (unsigned long long)(long long)dg);
+    }
+    if (di) atomicAdd(&d.sc->n_iface_acc, (uint32_t)di);
 }
 
 // full-warp reductions (every lane gets the result)
@@ -456,11 +474,52 @@ __device__ __forceinline__ uint32_t covering_sphere(const Dev& d, int x, int y, 
 }
 
 // kernels (defined in the .cu files), launched by lbm_capi.cu
+// The bubble model and the bookkeeping that close a step (Sec. 2.2): V_b = gas cells of b +
+// sum over b's interface cells of (1 - phi), kept up to date by the sweep (the interface part,
+// afresh) and the end-of-step kernels (every change of type or fill level), then
+// rho_g,b = rho_g0 V_b(0) / V_b (isothermal gas of conserved mass); the excess pool and the
+// share the next sweep spreads over the interface cells; the per-step counters and the
+// boundary list are reset;
+// moved spheres enter the bins of their new centres.  Run by every thread (t of nt) of the
+// step's last kernel, after its last barrier.
+__device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t nt, const bool bin_spheres) {
+    for (uint32_t b = t; b < (uint32_t)d.nbub; b += nt) {
+        Bubble& B = d.bub[b];
+        const double V = (double)(long long)B.ngas + B.Vif;
+        B.V = V;
+        if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
+        else atomicOr(&d.sc->status, S_BUBBLE_GONE);
+        B.rho_gf = (float)B.rho_g;
+        B.Vif = 0.0;
+    }
+    if (t == 0) {
+        Scalars& c = *d.sc;
+        if (c.share != 0.0) c.pool = 0.0;
+        c.pool += c.pool_acc;
+        c.pool_acc = 0.0;
+        c.n_iface = c.n_iface_acc;
+        c.n_iface_acc = 0;
+        c.share = (c.pool != 0.0 && c.n_iface > 0) ? c.pool / (double)c.n_iface : 0.0;
+        c.share_f = (float)c.share;
+        c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
+        c.n_slow = 0;   // the boundary sweep has consumed its list; the list pass refills it
+    }
+    if (bin_spheres)
+        for (uint32_t P = t; P < (uint32_t)d.nsph; P += nt) {
+            const Sphere& sp = d.sph[P];
+            const size_t bi = bin_index(d, bin_coord(d, 0, sp.x[0]), bin_coord(d, 1, sp.x[1]), bin_coord(d, 2, sp.x[2]));
+            const uint32_t slot = atomicAdd(&d.bin_cnt[bi], 1u);
+            if (slot < (uint32_t)d.bin_cap) d.bin_ids[bi * d.bin_cap + slot] = P;
+            else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
+        }
+}
+
 void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s);
 void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
 
-void launch_conversions(const Dev& d, int nxt, cudaStream_t s);
-void launch_end_scan(const Dev& d, int cur, int set_reference, cudaStream_t s);
+void launch_conversions(const Dev& d, int nxt, bool close, cudaStream_t s);
+void launch_init_scan(const Dev& d, cudaStream_t s);
+void launch_list_rescan(const Dev& d, cudaStream_t s);
 void launch_curvature(const Dev& d, int nxt, cudaStream_t s);
 void launch_spheres_links(const Dev& d, cudaStream_t s);
 void launch_spheres_move(const Dev& d, cudaStream_t s);
@@ -480,8 +539,8 @@ void launch_frozen_forward(const Dev& d, const float* f_in, float* f_out, cudaSt
                            cudaEvent_t fork, cudaEvent_t join);
 
 constexpr int kAdjSlots = 64;
-void launch_adjoint(const Dev& d, const float* f_fwd, const float* lam_in, float* lam_out, float* srho, const float jdir[3],
-                    double* part, bool moving_walls, cudaStream_t s, cudaStream_t side, cudaEvent_t fork,
-                    cudaEvent_t join);
+void launch_adjoint(const Dev& d, const float* f_fwd, const float* lam_in, float* lam_out, float* srho,
+                    const float jdir[3], double* part, bool moving_walls, cudaStream_t s, cudaStream_t side,
+                    cudaEvent_t fork, cudaEvent_t join);
 
 }  // namespace lbm

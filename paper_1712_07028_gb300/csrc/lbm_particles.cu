@@ -526,6 +526,9 @@ __device__ inline void cover_apply_dev(const Dev& d, const int nxt, const uint32
                 atomicAdd(&d.sc->S_cover, (double)(1.f + rl));
             } else if (t & F_IF) {
                 atomicAdd(&d.sc->S_cover, (double)d.mass[i]);
+                vol_change(d, d.owner[i], -(1.0 - (double)d.phi[nxt][i]), 0, -1);
+            } else if (t & F_GAS) {
+                vol_change(d, d.owner[i], 0.0, -1, 0);
             }
             d.flags[i] = F_OBS;
             d.owner[i] = own;
@@ -588,6 +591,7 @@ __device__ inline void cover_refill_dev(const Dev& d, const int nxt, const uint3
                 d.owner[i] = gown;
                 d.mass[i] = 0.f;
                 phi[i] = 0.f;
+                vol_change(d, gown, 0.0, 1, 0);
             }
             continue;
         }
@@ -601,6 +605,7 @@ __device__ inline void cover_refill_dev(const Dev& d, const int nxt, const uint3
             phi[i] = pb;
             d.mass[i] = pb * rb;
             atomicAdd(&d.sc->S_uncover, (double)(pb * rb));
+            vol_change(d, gown, 1.0 - (double)pb, 0, 1);
         } else {
             d.flags[i] = F_LIQ;
             d.owner[i] = kNone;
@@ -639,7 +644,7 @@ __device__ inline void bins_clear(const Dev& d, const uint32_t t, const uint32_t
 
 // apply, refill and finish in one launch: one thread-block cluster, the phases separated by
 // cluster barriers (the touched cells are few: launches, not work, would set the time); with
-// no touched cell it only empties the bins
+// no touched cell it only empties the bins; then the step is closed
 constexpr int kCoverCtas = 8, kCoverThreads = 512;
 template <int S>
 __global__ void __cluster_dims__(kCoverCtas, 1, 1) __launch_bounds__(kCoverThreads) cover_cluster_kernel(const Dev d, const int nxt) {
@@ -653,6 +658,9 @@ __global__ void __cluster_dims__(kCoverCtas, 1, 1) __launch_bounds__(kCoverThrea
         cover_finish_dev(d, wid, nw);
     }
     bins_clear(d, t, nt);
+    cluster_sync();
+    // the last end-of-step kernel: it closes the step (bubble model, counters, new bins)
+    step_close(d, t, nt, true);
 }
 
 int spheres_links_launches(const Dev& d) { return d.nsph == 0 ? 0 : 2; }

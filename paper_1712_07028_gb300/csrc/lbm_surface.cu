@@ -16,12 +16,18 @@ namespace lbm {
 constexpr int kClusterCtas = 8;
 constexpr int kClusterThreads = 1024;
 template <int S>
-__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads) conversions_kernel(const Dev d, const int nxt) {
+__global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterThreads) conversions_kernel(const Dev d, const int nxt, const int close) {
     const uint32_t wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     // the fix list of the last step has been consumed by the sweep's fix pass; this step's
     // BULK updates (here and in the cover kernels after this launch) fill it again
     if (blockIdx.x == 0 && threadIdx.x == 0) { d.sc->n_fix = 0; d.sc->fix_all = 0; }
+    // no interface cell crossed a threshold: nothing converts (every thread reads the same
+    // count: it is reset only by a step close, which no thread reaches before all have read it)
+    if (*(volatile const uint32_t*)&d.sc->n_conv == 0u) {
+        if (close) step_close(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, false);
+        return;
+    }
     conv_filled_emptied<S>(d, nxt, wid, nw);
     cluster_sync();
     // new-interface initialisation writes only the new cells' PDFs; the excess phase reads
@@ -32,27 +38,27 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
     conv_finalize<S>(d, nxt, wid, nw);
     cluster_sync();
     conv_bulk(d, wid, nw);
-    // the boundary list of this step has been consumed by the sweep; the end-of-step scan
-    // fills it again
-    if (blockIdx.x == 0 && threadIdx.x == 0) d.sc->n_slow = 0;
-}
-
-void launch_conversions(const Dev& d, int nxt, cudaStream_t s) {
-    switch (d.storage) {
-        case LBM_STORE_F32: conversions_kernel<LBM_STORE_F32><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt); break;
-        case LBM_STORE_F16DEV: conversions_kernel<LBM_STORE_F16DEV><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt); break;
-        default: conversions_kernel<LBM_STORE_BF16DEV><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt); break;
+    if (close) {   // no cover kernel follows: this launch closes the step (the same for all threads)
+        cluster_sync();
+        step_close(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, false);
     }
 }
 
-// --------------------------------------------------------- end of step: one scan
-// One pass over the cell types as the step leaves them: the active cells the bulk sweep
-// leaves to the boundary sweep are listed for the next step; each bubble's volume
-// V_b = #gas cells + sum over its interface cells of (1 - phi) is summed in FP64 (bubble
-// model, Sec. 2.2) and the interface cells are counted.  The last block to finish then
-// sets rho_g,b = rho_g0 V_b(0) / V_b (isothermal gas of conserved mass), moves the excess
-// pool and the share the next sweep spreads over the interface cells, and resets counters.
-__global__ void end_scan_kernel(const Dev d, const int cur, const int set_reference) {
+void launch_conversions(const Dev& d, int nxt, bool close, cudaStream_t s) {
+    const int c = close ? 1 : 0;
+    switch (d.storage) {
+        case LBM_STORE_F32: conversions_kernel<LBM_STORE_F32><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt, c); break;
+        case LBM_STORE_F16DEV: conversions_kernel<LBM_STORE_F16DEV><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt, c); break;
+        default: conversions_kernel<LBM_STORE_BF16DEV><<<kClusterCtas, kClusterThreads, 0, s>>>(d, nxt, c); break;
+    }
+}
+
+// --------------------------------------------------------- initial scan
+// One pass over the initial cell types: the active cells the bulk sweep leaves to the
+// boundary sweep form the first boundary list; each bubble's gas cells are counted and V_b(0) = #gas cells + sum over its interface cells
+// of (1 - phi) is summed in FP64 (bubble model, Sec. 2.2); the interface cells are counted.
+// The last block to finish sets the reference volumes and rho_g = rho_g0.
+__global__ void init_scan_kernel(const Dev d) {
     extern __shared__ unsigned char smem_raw[];
     double* sV = reinterpret_cast<double*>(smem_raw);
     unsigned long long* sG = reinterpret_cast<unsigned long long*>(sV + d.max_bub);
@@ -63,7 +69,7 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
     for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) { sV[b] = 0.0; sG[b] = 0ull; }
     if (threadIdx.x == 0) sIf = 0;
     __syncthreads();
-    const float* phi = d.phi[cur];
+    const float* phi = d.phi[0];
     const size_t nvec = d.N / 16;
     const size_t total = nvec + (d.N % 16 ? 1 : 0);
     const uint4* fl4 = reinterpret_cast<const uint4*>(d.flags);
@@ -164,16 +170,6 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
     }
     const unsigned nifw = __reduce_add_sync(full, nif);
     if (lane == 0 && nifw) atomicAdd(&sIf, nifw);
-    // moved spheres enter the bins of their new centres (emptied by the cover kernels), which
-    // the next step's partner search reads; fixed spheres keep the bins of the first step
-    if (!set_reference && d.sphere_mode != LBM_SPHERES_FIXED)
-        for (int P = blockIdx.x * blockDim.x + threadIdx.x; P < d.nsph; P += gridDim.x * blockDim.x) {
-            const Sphere& sp = d.sph[P];
-            const size_t bi = bin_index(d, bin_coord(d, 0, sp.x[0]), bin_coord(d, 1, sp.x[1]), bin_coord(d, 2, sp.x[2]));
-            const uint32_t slot = atomicAdd(&d.bin_cnt[bi], 1u);
-            if (slot < (uint32_t)d.bin_cap) d.bin_ids[bi * d.bin_cap + slot] = (uint32_t)P;
-            else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
-        }
     __syncthreads();
     for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
         if (sV[b] != 0.0) atomicAdd(&d.bub[b].Vif, sV[b]);
@@ -191,33 +187,94 @@ __global__ void end_scan_kernel(const Dev d, const int cur, const int set_refere
         Bubble& B = d.bub[b];
         const double V = (double)*(volatile unsigned long long*)&B.ngas + *(volatile double*)&B.Vif;
         B.V = V;
-        if (set_reference) { B.V0 = V; B.rho_g = (double)d.rho_g0; }
-        else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
-        else atomicOr(&d.sc->status, S_BUBBLE_GONE);
+        B.V0 = V;
+        B.rho_g = (double)d.rho_g0;
         B.rho_gf = (float)B.rho_g;
-        B.ngas = 0ull;
-        B.Vif = 0.0;
+        B.Vif = 0.0;   // the gas count carries over; the sweep sums the interface part afresh
     }
     if (threadIdx.x == 0) {
         Scalars& c = *d.sc;
-        if (c.share != 0.0) c.pool = 0.0;
-        c.pool += c.pool_acc;
-        c.pool_acc = 0.0;
         c.n_iface = *(volatile uint32_t*)&c.n_iface_acc;
         c.n_iface_acc = 0;
-        c.share = (c.pool != 0.0 && c.n_iface > 0) ? c.pool / (double)c.n_iface : 0.0;
-        c.share_f = (float)c.share;
-        c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
+        c.share = 0.0;
+        c.share_f = 0.f;
         c.ticket = 0;
     }
 }
 
-void launch_end_scan(const Dev& d, int cur, int set_reference, cudaStream_t s) {
+void launch_init_scan(const Dev& d, cudaStream_t s) {
     const size_t shm = (size_t)d.max_bub * (sizeof(double) + sizeof(unsigned long long));
     const size_t nvec = d.N / 16 + 1;
     int blocks = (int)((nvec + 511) / 512);
     if (blocks > 152 * 4) blocks = 152 * 4;
-    end_scan_kernel<<<blocks, 512, shm, s>>>(d, cur, set_reference);
+    init_scan_kernel<<<blocks, 512, shm, s>>>(d);
+}
+
+// --------------------------------------------------------- boundary list
+// One pass over the cell types as the step leaves them: the active cells that are not BULK,
+// in scan order (blocks of 8192 consecutive cells appended whole), are the next boundary
+// sweep's list.  Scan order keeps the boundary sweep's accesses local: a list kept by
+// appending cells in the order they changed made it ~40 % slower.  The list length is zero
+// on entry (the step close resets it).
+__global__ void list_rescan_kernel(const Dev d) {
+    __shared__ uint32_t sWarp[32];
+    __shared__ uint32_t sBase;
+    const size_t nvec = d.N / 16;
+    const size_t total = nvec + (d.N % 16 ? 1 : 0);
+    const uint4* fl4 = reinterpret_cast<const uint4*>(d.flags);
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    // every thread of the block runs the same number of rounds (block collectives below)
+    for (size_t base = blockIdx.x * (size_t)blockDim.x; base < total; base += (size_t)gridDim.x * blockDim.x) {
+        const size_t v = base + threadIdx.x;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (v < nvec) {
+            const uint4 p = fl4[v];
+            w[0] = p.x; w[1] = p.y; w[2] = p.z; w[3] = p.w;
+        } else if (v < total) {
+            for (size_t c = v * 16; c < d.N; c++) w[(c - v * 16) / 4] |= (uint32_t)d.flags[c] << (8 * ((c - v * 16) % 4));
+        }
+        uint32_t sel = 0u;
+#pragma unroll
+        for (int c = 0; c < 16; c++) {
+            const uint32_t t = (w[c / 4] >> (8 * (c % 4))) & 0xffu;
+            sel |= ((t & F_ACTIVE) && !(t & F_BULK)) ? (1u << c) : 0u;
+        }
+        const uint32_t cnt = __popc(sel);
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(full, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) sWarp[threadIdx.x >> 5] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t acc = 0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+                const uint32_t x = sWarp[k];
+                sWarp[k] = acc;
+                acc += x;
+            }
+            sBase = acc ? atomicAdd(&d.sc->n_slow, acc) : 0u;
+        }
+        __syncthreads();
+        uint32_t slot = sBase + sWarp[threadIdx.x >> 5] + incl - cnt;
+        __syncthreads();
+        while (sel) {
+            const int c = __ffs(sel) - 1;
+            sel &= sel - 1;
+            if (slot < (uint32_t)d.N) d.wl_slow[slot] = (uint32_t)(v * 16 + c);
+            slot++;
+        }
+    }
+}
+
+void launch_list_rescan(const Dev& d, cudaStream_t s) {   // after the step close (list length 0)
+    const size_t nvec = d.N / 16 + 1;
+    int blocks = (int)((nvec + 511) / 512);
+    if (blocks > 152 * 4) blocks = 152 * 4;
+    list_rescan_kernel<<<blocks, 512, 0, s>>>(d);
 }
 
 // ---------------------------------------------------------------------- curvature
@@ -333,7 +390,7 @@ void launch_init(const Dev& d, const double* geo, cudaStream_t s) {
 
 __global__ void bulk_all_kernel(const Dev d) {   // initial BULK bits (nothing to fix)
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x)
-        set_bulk(d, i, false);
+        set_bulk_init(d, i);
 }
 
 void launch_bulk_all(const Dev& d, cudaStream_t s) { bulk_all_kernel<<<152 * 16, 256, 0, s>>>(d); }

@@ -170,22 +170,30 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
     float* __restrict__ phib = d.phi[cur ^ 1];
     const size_t N = d.N;
     const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)N);
+    const uint32_t* __restrict__ list = d.wl_slow;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
+    __shared__ uint32_t sNif[4], sVb[4];
+    __shared__ double sV[4];
+    __shared__ float sS[4];
 
-    // every thread of the block runs the same number of rounds (warp collectives below)
+    // every thread of the block runs the same number of rounds (block and warp collectives)
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const uint32_t k = base + threadIdx.x;
         SphAcc acc;
         acc.pid = kNone;
         float sbb = 0.f;
+        uint32_t vb = kNone;      // the cell's bubble, for an interface cell
+        float vphi = 1.f;         // and its new fill level
+        bool isIFc = false;
         if (k < n) {
-            const size_t i = d.wl_slow[k];
+            const size_t i = list[k];
             const uint8_t fl = d.flags[i];
             int x, y, z;
             cell_xyz(d, i, x, y, z);
             const bool isIF = (fl & F_IF) != 0;
+            isIFc = isIF;
             // every load is issued before any link is resolved: neighbour indices and types,
             // then the pulled PDFs, owners and fill levels (predicated on the types)
             float fo[kQ];
@@ -289,6 +297,8 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                 const float rho = 1.f + drho;
                 d.mass[i] = mnew;
                 phib[i] = mnew / rho;
+                vb = d.owner[i];
+                vphi = mnew / rho;
                 // phi >= 1 + eps  <=>  m - rho >= eps rho, taken as (m - 1) - drho so that a
                 // density deviation below FP32's resolution of 1 still decides it;
                 // phi <= -eps  <=>  m <= -eps rho
@@ -302,6 +312,51 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
             }
             collide_store<S>(d, fb, i, fin);
         }
+
+        // ---- per-warp partial sums: interface part of the bubble volumes (1 - phi, FP64),
+        // interface count and bounce-back mass; folded per block below (one atomic each)
+        const unsigned nifw = __popc(__ballot_sync(full, isIFc));
+        const uint32_t lead = __reduce_min_sync(full, vb);
+        double vsum = 0.0;
+        uint32_t vbub = kNone;
+        if (lead < (uint32_t)d.nbub) {
+            if (__all_sync(full, vb == lead || vb == kNone)) {
+                vsum = warp_sum(vb == lead ? 1.0 - (double)vphi : 0.0);
+                vbub = lead;
+            } else if (vb < (uint32_t)d.nbub) {   // lanes of several bubbles (rare)
+                atomicAdd(&d.bub[vb].Vif, 1.0 - (double)vphi);
+            }
+        }
+        const float sbbw = warp_sum(sbb);
+        if (lane == 0) {
+            const int w = threadIdx.x >> 5;
+            sNif[w] = nifw;
+            sV[w] = vsum;
+            sVb[w] = vbub;
+            sS[w] = sbbw;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t ni = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) ni += sNif[w];
+            if (ni) atomicAdd(&d.sc->n_iface_acc, ni);
+            double v = 0.0;
+            uint32_t vb0 = kNone;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+                if (sVb[w] == kNone) continue;
+                if (vb0 != kNone && sVb[w] != vb0) {
+                    atomicAdd(&d.bub[vb0].Vif, v);
+                    v = 0.0;
+                }
+                vb0 = sVb[w];
+                v += sV[w];
+            }
+            if (vb0 != kNone) atomicAdd(&d.bub[vb0].Vif, v);
+            double sb = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); w++) sb += (double)sS[w];
+            if (sb != 0.0) atomicAdd(&d.sc->S_bb, sb);
+        }
+        if (base + gridDim.x * blockDim.x < n) __syncthreads();   // shared slots reused next round
 
         // ---- warp reduction of the sphere accumulators (every lane takes part)
         float TJ[3] = {0.f, 0.f, 0.f};
@@ -347,11 +402,6 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                     atomicAdd(&g.XK[c], (unsigned long long)(long long)iv[3 + c]);
                 }
             }
-        }
-        if (__any_sync(full, sbb != 0.f)) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sbb += __shfl_xor_sync(full, sbb, o);
-            if (lane == 0) atomicAdd(&d.sc->S_bb, (double)sbb);
         }
     }
 }
