@@ -45,23 +45,31 @@ constexpr uint32_t kNone = 0xffffffffu;
 // the kernels compute in deviation form too, so densities and velocities of a nearly
 // uniform liquid are not rounded against the O(1) weights.
 template <int S> struct Store;
+// get_cs / put_cs: streaming accesses (evict first) for the bulk sweep, which passes each PDF
+// through once per step; the smaller arrays the latency-bound kernels reuse stay in L2
 template <> struct Store<LBM_STORE_F32> {
     using T = float;
     static __device__ __forceinline__ float get(const T* p, size_t i) { return __ldg(p + i); }
+    static __device__ __forceinline__ float get_cs(const T* p, size_t i) { return __ldcs(p + i); }
     static __device__ __forceinline__ float get_nc(const T* p, size_t i) { return p[i]; }
     static __device__ __forceinline__ void put(T* p, size_t i, float v) { p[i] = v; }
+    static __device__ __forceinline__ void put_cs(T* p, size_t i, float v) { __stcs(p + i, v); }
 };
 template <> struct Store<LBM_STORE_F16DEV> {
     using T = __half;
     static __device__ __forceinline__ float get(const T* p, size_t i) { return __half2float(__ldg(p + i)); }
+    static __device__ __forceinline__ float get_cs(const T* p, size_t i) { return __half2float(__ldcs(p + i)); }
     static __device__ __forceinline__ float get_nc(const T* p, size_t i) { return __half2float(p[i]); }
     static __device__ __forceinline__ void put(T* p, size_t i, float v) { p[i] = __float2half_rn(v); }
+    static __device__ __forceinline__ void put_cs(T* p, size_t i, float v) { __stcs(p + i, __float2half_rn(v)); }
 };
 template <> struct Store<LBM_STORE_BF16DEV> {
     using T = __nv_bfloat16;
     static __device__ __forceinline__ float get(const T* p, size_t i) { return __bfloat162float(__ldg(p + i)); }
+    static __device__ __forceinline__ float get_cs(const T* p, size_t i) { return __bfloat162float(__ldcs(p + i)); }
     static __device__ __forceinline__ float get_nc(const T* p, size_t i) { return __bfloat162float(p[i]); }
     static __device__ __forceinline__ void put(T* p, size_t i, float v) { p[i] = __float2bfloat16_rn(v); }
+    static __device__ __forceinline__ void put_cs(T* p, size_t i, float v) { __stcs(p + i, __float2bfloat16_rn(v)); }
 };
 
 // ----------------------------------------------------------------- device-side records
@@ -356,7 +364,7 @@ __device__ __forceinline__ float equilibrium_dev(int q, float rho, const float u
 
 // moments, Guo-shifted velocity and the TRT collision of one cell, all on deviations f - w;
 // the post-collision deviations go to grid fb
-template <int S>
+template <int S, bool CS = false>
 __device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T* __restrict__ fb, size_t i, const float (&fin)[kQ]) {
     const size_t N = d.N;
     const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
@@ -380,7 +388,7 @@ __device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T
         // q = 0: f+ = f, e+ - w = w (rho - 1 - 1.5 rho u.u), G+ = -3 w rho u.g
         const float w = wgt(0);
         const float ep = w * (drho - 1.5f * rho * usq);
-        Store<S>::put(fb, i, fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug)));
+        (CS ? Store<S>::put_cs : Store<S>::put)(fb, i, fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug)));
     }
 #pragma unroll
     for (int q = 1; q < kQ; q += 2) {
@@ -394,8 +402,8 @@ __device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T
         const float fm = 0.5f * (fin[q] - fin[qb]);
         const float a = lp * (fp - ep) + cp * (w * rho * (9.f * cu * cg - 3.f * ug));
         const float b = lm * (fm - em) + cm * (w * rho * 3.f * cg);
-        Store<S>::put(fb, (size_t)q * N + i, fin[q] + a + b);
-        Store<S>::put(fb, (size_t)qb * N + i, fin[qb] + a - b);
+        (CS ? Store<S>::put_cs : Store<S>::put)(fb, (size_t)q * N + i, fin[q] + a + b);
+        (CS ? Store<S>::put_cs : Store<S>::put)(fb, (size_t)qb * N + i, fin[qb] + a - b);
     }
 }
 

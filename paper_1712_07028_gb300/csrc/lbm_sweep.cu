@@ -97,9 +97,9 @@ __device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>:
             if (cx(q) == 1 && edge0) { if (perx) adj = (int32_t)nx; else wall = true; }
             if (cx(q) == -1 && edge1) { if (perx) adj = -(int32_t)nx; else wall = true; }
             const T* plane = fa + (size_t)(wall ? opp(q) : q) * d.N;
-            fin[q] = Store<S>::get(plane, wall ? i : i - (uint32_t)o + (uint32_t)adj);   // modulo 2^32
+            fin[q] = Store<S>::get_cs(plane, wall ? i : i - (uint32_t)o + (uint32_t)adj);   // modulo 2^32
         }
-        collide_store<S>(d, fb, i, fin);
+        collide_store<S, true>(d, fb, i, fin);
         return;
     }
     const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
@@ -117,9 +117,9 @@ __device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>:
                           (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
         // halfway bounce-back: the cell's own post-collision PDF of the opposite direction
         const T* plane = fa + (size_t)(wall ? opp(q) : q) * d.N;
-        fin[q] = Store<S>::get(plane, wall ? i : sx + sy + sz);
+        fin[q] = Store<S>::get_cs(plane, wall ? i : sx + sy + sz);
     }
-    collide_store<S>(d, fb, i, fin);
+    collide_store<S, true>(d, fb, i, fin);
 }
 
 // every liquid cell whose neighbours all carry PDFs or lie beyond a wall; other active cells
