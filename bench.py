@@ -29,9 +29,10 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and HBM-roofline fraction, FP32 / FP16-store vs FP64 oracle error"
 FALLBACK_HBM_GBS = 6800.0
 
-# dram bytes (read + write) per sweep launch on this workload from one ncu capture, with the
-# hash of the sweep source it was taken on (null once the kernel changes)
-NCU_TRAFFIC = {"sha1": "d5e986cc2ca845086e7ee77c54ce3a083df059ea", "bytes_per_launch": 297955328}
+# dram bytes (read + write) per bulk-sweep launch on the 128^3 column from one ncu capture
+# (mean of three launches), with the hash of the sweep source it was taken on (null once the
+# kernel changes)
+NCU_TRAFFIC = {"sha1": "6a7d057eafd386e19180639de5000907e9358e61", "bytes_per_launch": 268327339}
 
 
 def _args():
@@ -43,6 +44,8 @@ def _args():
     ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c3", "c4"])
     ap.add_argument("--storage", default=None, choices=[None, "f32", "f16dev", "bf16dev"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed region (for profilers)")
+    ap.add_argument("--only", default=None, choices=[None, "adjoint"],
+                    help="time only the differentiation path (the adjoint object of the full line)")
     return ap.parse_args()
 
 
@@ -239,7 +242,7 @@ def _storage_run(torch, lbm, args, storage):
             "bulk_kernel_ms": avg_s * 1e3, "rest_of_sweep_ms": rest_ms / max(1, nsw), "status": st}
 
 
-def _adjoint_run(torch, lbm, W):
+def _adjoint_run(torch, lbm, W, window=True, graphs=True):
     """the differentiation path on the 96^3 periodic array of 27 fixed spheres: per-launch
     time and HBM roofline of the frozen replay step and of the reverse step, and the wall time
     of a 500-step window gradient (forward with checkpoints every 50, replay, reverse)"""
@@ -264,6 +267,8 @@ def _adjoint_run(torch, lbm, W):
         for _ in range(5):
             fn()
         torch.cuda.synchronize()
+        if not graphs:   # a few plain calls only (for a profiler's launch list)
+            return float("nan")
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
             for _ in range(k):
@@ -292,6 +297,13 @@ def _adjoint_run(torch, lbm, W):
     by_f = n_liq * (2 * 19 * 4 + 1) + inactive
     by_r = n_liq * (3 * 19 * 4 + 1) + inactive
     sim.close()
+    out = {"workload": wl.name, "liquid_cells": n_liq,
+           "replay_step": {"ms": t_f * 1e3, "bytes": by_f, "achieved": by_f / t_f / 1e9, "unit": "GB/s",
+                           "frac": by_f / t_f / 1e9 / peak, "peak_source": kind},
+           "reverse_step": {"ms": t_r * 1e3, "bytes": by_r, "achieved": by_r / t_r / 1e9, "unit": "GB/s",
+                            "frac": by_r / t_r / 1e9 / peak, "peak_source": kind}}
+    if not window:
+        return out
     n, every = 500, 50
     sim = lbm.Sim(wl)
     sim.step(0)
@@ -301,15 +313,10 @@ def _adjoint_run(torch, lbm, W):
     torch.cuda.synchronize()
     t_win = time.perf_counter() - t0
     sim.close()
-    return {"workload": wl.name, "liquid_cells": n_liq,
-            "replay_step": {"ms": t_f * 1e3, "bytes": by_f, "achieved": by_f / t_f / 1e9, "unit": "GB/s",
-                            "frac": by_f / t_f / 1e9 / peak, "peak_source": kind},
-            "reverse_step": {"ms": t_r * 1e3, "bytes": by_r, "achieved": by_r / t_r / 1e9, "unit": "GB/s",
-                             "frac": by_r / t_r / 1e9 / peak, "peak_source": kind},
-            "window": {"steps": n, "checkpoint_every": every, "seconds": t_win,
-                       "mlups": wl.cells * n / t_win / 1e6,
-                       "includes": "forward steps with per-step force read (sync) and checkpoints, replay, reverse",
-                       "J": J, "dJ_dtau": dtau, "dJ_dg": list(dg)}}
+    out["window"] = {"steps": n, "checkpoint_every": every, "seconds": t_win, "mlups": wl.cells * n / t_win / 1e6,
+                     "includes": "forward steps with per-step force read (sync) and checkpoints, replay, reverse",
+                     "J": J, "dJ_dtau": dtau, "dJ_dg": list(dg)}
+    return out
 
 
 def run_reference(args):
@@ -466,6 +473,13 @@ def main():
     args = _args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.only == "adjoint":
+        import torch
+        from paper_1712_07028_gb300 import lbm
+        from paper_1712_07028_gb300 import workloads as W
+        lbm.load()
+        print(json.dumps(_adjoint_run(torch, lbm, W, window=not args.no_extras, graphs=not args.no_extras)))
+        return 0
     return run_gpu(args)
 
 

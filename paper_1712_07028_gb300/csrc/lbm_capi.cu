@@ -48,6 +48,9 @@ struct lbm_ctx {
     // the end-of-step kernels of the last step not enqueued yet: the next step runs them
     // concurrently with its bulk sweep, any query runs them first
     bool pending;
+    // the next step's partner lists / obstacle-node links: not enqueued yet, enqueued on the
+    // links stream (to be joined by the sweep's rest), or enqueued and already joined
+    int links_state;
     uint64_t h2d_bytes, d2h_bytes;   // host <-> device copies made by the library
     // second stream and fork/join events of the concurrent bulk / boundary sweep
     cudaStream_t side;
@@ -59,6 +62,7 @@ struct lbm_ctx {
 
 namespace {
 
+enum { kLinksNone = 0, kLinksForked = 1, kLinksJoined = 2 };
 constexpr size_t kAlign = 256;
 constexpr int kBinCap = 16;
 
@@ -174,6 +178,16 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
         cudaStreamWaitEvent(e, c->join4, 0);
     }
     launch_spheres_cover(d, g, e);
+    // the next step's partner lists and obstacle-node links need only the moved spheres, their
+    // bins and obstacle cells, all final now: they run beside the rest of these kernels and
+    // the next bulk sweep, and the next step's sweep joins them
+    if (d.nsph > 0) {
+        cudaEventRecord(c->fork2, e);
+        cudaStreamWaitEvent(c->links, c->fork2, 0);
+        launch_spheres_links(d, c->links);
+        cudaEventRecord(c->join2, c->links);
+        c->links_state = kLinksForked;
+    }
     if (d.kappa) launch_curvature(d, g, e);
     launch_list_rescan(d, e);   // the next boundary sweep's list, from the final types
 }
@@ -206,14 +220,18 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed =
     if (timed) cudaEventRecord(c->ev[4 * slot + 1], s);
     if (overlap) cudaStreamWaitEvent(s, c->join3, 0);
     if (timed) cudaEventRecord(c->ev[4 * slot + 2], s);
-    if (d.nsph > 0) {   // partner lists and obstacle-node links of this step, beside the sweep's rest
+    if (d.nsph > 0 && c->links_state == kLinksNone) {   // the first step: nothing forked them
         cudaEventRecord(c->fork2, s);
         cudaStreamWaitEvent(c->links, c->fork2, 0);
         launch_spheres_links(d, c->links);
         cudaEventRecord(c->join2, c->links);
+        c->links_state = kLinksForked;
     }
     launch_sweep_rest(d, cur, s, c->side, c->fork, c->join);
-    if (d.nsph > 0) cudaStreamWaitEvent(s, c->join2, 0);
+    // the step's force sums need the links (an event recorded in this same call: a graph
+    // capture in between would leave an earlier record unusable)
+    if (d.nsph > 0 && c->links_state == kLinksForked) cudaStreamWaitEvent(s, c->join2, 0);
+    c->links_state = kLinksNone;
     if (timed) {
         cudaEventRecord(c->ev[4 * slot + 3], s);
         c->ev_pending[slot] = true;
@@ -225,6 +243,11 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed =
 int flush(lbm_ctx* c) {
     if (!c->pending) return LBM_OK;
     enqueue_epilogue(c, c->cur, c->stream);
+    // what the caller reads next is ordered after every kernel the library enqueued
+    if (c->links_state == kLinksForked) {
+        cudaStreamWaitEvent(c->stream, c->join2, 0);
+        c->links_state = kLinksJoined;
+    }
     c->pending = false;
     return launched(c, epilogue_launches(c->d));
 }
@@ -336,6 +359,7 @@ int first_step(lbm_ctx* c) {
     if ((rc = launched(c, (d.nsph > 0) + 3 + (d.kappa ? 1 : 0)))) return rc;
     c->cur = 0;
     c->pending = false;
+    c->links_state = kLinksNone;
     c->started = true;
     return cuda_fail(cudaStreamSynchronize(s));
 }
@@ -345,10 +369,12 @@ int build_graph(lbm_ctx* c) {
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
     cudaGraph_t g = nullptr;
     int rc = LBM_OK;
+    const int links_state = c->links_state;   // host bookkeeping only: captured, not run
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = LBM_ECUDA;
     if (!rc) {
         enqueue_step(c, 0, cap, true);
         enqueue_step(c, 1, cap, true);
+        c->links_state = links_state;
         if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = LBM_ECUDA;
     }
     // per-node priorities: the boundary sweep keeps its stream's priority inside the graph
@@ -665,6 +691,10 @@ int lbm_destroy(lbm_ctx* c) {
     if (c->ev_ready)
         for (int k = 0; k < 4 * 64; k++) cudaEventDestroy(c->ev[k]);
     if (c->side_ready) {
+        // nothing of this simulation may still run once the caller frees the arena
+        cudaStreamSynchronize(c->side);
+        cudaStreamSynchronize(c->epi);
+        cudaStreamSynchronize(c->links);
         cudaEventDestroy(c->fork);
         cudaEventDestroy(c->join);
         cudaEventDestroy(c->fork2);
