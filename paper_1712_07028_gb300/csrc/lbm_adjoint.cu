@@ -250,7 +250,7 @@ __device__ __forceinline__ void adj_flush(float (&acc)[5], double* part) {
 
 // reverse step of the BULK cells: pull with the wall index select, collision adjoint, and the
 // transposed pull (push) with the same select; no sphere links
-__global__ void __launch_bounds__(128, 4) adjoint_bulk_kernel(const Dev d, const float* __restrict__ f,
+__global__ void __launch_bounds__(128, 6) adjoint_bulk_kernel(const Dev d, const float* __restrict__ f,
                                                            const float* __restrict__ lam_in,
                                                            float* __restrict__ lam_out, double* part) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -263,32 +263,50 @@ __global__ void __launch_bounds__(128, 4) adjoint_bulk_kernel(const Dev d, const
         const uint32_t i = (uint32_t)x + nx * (uint32_t)y + nxy * (uint32_t)z;
         const uint8_t fl = d.flags[i];
         if ((fl & F_LIQ) && (fl & F_BULK)) {
+            // source of direction q: i - c_q . (1, nx, nx ny) (a grid-uniform offset) where y
+            // and z stay inside the grid (the same for a whole warp); x edges wrap or bounce
+            const bool inner = y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+            const bool edge0 = x == 0, edge1 = x == d.nx - 1, perx = d.bc[0] != 0;
             const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
             const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
             const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
             const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
             const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
             const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
+            // (plane, index) of the PDF direction q pulls: its own opposite PDF beyond a wall
+            auto link = [&](int q, uint32_t& plane, uint32_t& idx) {
+                if (inner) {
+                    const int32_t o = cx(q) + cy(q) * (int32_t)nx + cz(q) * (int32_t)nxy;
+                    bool wall = false;
+                    int32_t adj = 0;
+                    if (cx(q) == 1 && edge0) { if (perx) adj = (int32_t)nx; else wall = true; }
+                    if (cx(q) == -1 && edge1) { if (perx) adj = -(int32_t)nx; else wall = true; }
+                    plane = wall ? (uint32_t)opp(q) : (uint32_t)q;
+                    idx = wall ? i : i - (uint32_t)o + (uint32_t)adj;   // modulo 2^32
+                } else {
+                    const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
+                    const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
+                    const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
+                    const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
+                                      (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
+                    plane = wall ? (uint32_t)opp(q) : (uint32_t)q;
+                    idx = wall ? i : sx + sy + sz;
+                }
+            };
             float fin[kQ], lam[kQ];
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
-                const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
-                const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
-                const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
-                const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
-                                  (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
-                fin[q] = f[(size_t)(wall ? opp(q) : q) * N + (wall ? i : sx + sy + sz)];
+                uint32_t pl, ix;
+                link(q, pl, ix);
+                fin[q] = f[(size_t)pl * N + ix];
                 lam[q] = lam_in[(size_t)q * N + i];
             }
             const AdjOut o = collide_adjoint(d, fin, lam, acc);
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
-                const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
-                const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
-                const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
-                const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
-                                  (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
-                lam_out[(size_t)(wall ? opp(q) : q) * N + (wall ? i : sx + sy + sz)] = adj_in_q(d, q, lam, o);
+                uint32_t pl, ix;
+                link(q, pl, ix);
+                lam_out[(size_t)pl * N + ix] = adj_in_q(d, q, lam, o);
             }
         }
     }
