@@ -265,6 +265,22 @@ static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
         }
     }
     s->scal[SC_NIF] = (double)nif;
+    /* bubbles that touch (a gas or interface cell next to a gas or interface cell of another
+     * bubble) would have to merge (the paper's bubble model joins them); that is not modelled
+     * here: the state is flagged */
+    for (int z = 0; z < p->nz; z++)
+        for (int y = 0; y < p->ny; y++)
+            for (int x = 0; x < p->nx; x++) {
+                const long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
+                const int b = s->owner[i];
+                if (!(s->flag[i] & (C_IF | C_GAS)) || b < 0 || b >= p->nbub) continue;
+                for (int q = 1; q < NQ; q++) {
+                    const long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+                    if (j < 0 || !(s->flag[j] & (C_IF | C_GAS))) continue;
+                    const int bj = s->owner[j];
+                    if (bj >= 0 && bj < p->nbub && bj != b) s->scal[SC_STATUS] = (double)((int)s->scal[SC_STATUS] | ST_MERGE);
+                }
+            }
     for (int b = 0; b < p->nbub; b++) {
         double *B = s->bub + b * B_LEN;
         if (set_reference) {

@@ -361,3 +361,20 @@ def test_light_free_sphere_stays_at_rest(orc, rho, R):
     assert np.abs(u).max() < 1e-12
     assert np.abs(s.sph[0, orc.S_U:orc.S_U + 3]).max() < 1e-12
     assert np.abs(s.sph[0, orc.S_W:orc.S_W + 3]).max() < 1e-12
+
+
+@pytest.mark.parametrize("c2,touching", [(15.0, True), (17.0, False)])
+def test_touching_bubbles_are_flagged(orc, c2, touching):
+    """Bubbles whose gas/interface cells touch would have to merge (the paper's bubble model
+    joins them); the oracle does not merge them but flags the state.  Two r = 4 bubbles: at
+    centre distance 8 their interface layers overlap, at 10 one liquid cell separates them."""
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.Workload(name="two", nx=24, ny=16, nz=16, tau=0.7, g=(0, 0, 0), sphere_mode=W.SPHERES_FIXED,
+                    bubbles=[W.Bubble((7.0, 8.0, 8.0), 4.0), W.Bubble((c2, 8.0, 8.0), 4.0)])
+    o = orc.Sim(wl)
+    o.step(5)
+    flagged = (int(o.scal[orc.SC_STATUS]) & 4) != 0
+    assert flagged == touching
+    # the separating liquid layer: on the line between the centres x = 12 stays liquid
+    if not touching:
+        assert o.flag[8, 8, 12] == orc.LIQ
