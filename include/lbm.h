@@ -49,6 +49,8 @@ extern "C" {
 #define LBM_ECUDA (-3)       /* a CUDA runtime call failed */
 #define LBM_EUNSTABLE (-4)   /* a cell's density became non-positive or NaN */
 #define LBM_EOVERFLOW (-5)   /* a conversion worklist or a sphere bin overflowed */
+#define LBM_EMERGE (-6)      /* two bubbles' gas / interface regions touch (Sec. 2.2: they would
+                                merge; merging is not modelled, the state is flagged) */
 
 /* per-axis boundary kind */
 #define LBM_BC_WALL 0        /* no-slip wall halfway beyond the outermost cells */
@@ -75,6 +77,7 @@ extern "C" {
 #define LBM_S_OVERFLOW 2u        /* a conversion / covering worklist overflowed */
 #define LBM_S_BUBBLE_GONE 4u     /* a bubble's volume reached zero */
 #define LBM_S_BIN_OVERFLOW 8u    /* more spheres in a neighbour-search bin than it holds */
+#define LBM_S_MERGE 64u          /* a gas or interface cell of one bubble next to one of another */
 #define LBM_S_FAST_SPHERE 32u    /* a sphere moved more than a quarter cell in one step (the
                                     per-step partner searches assume less) */
 

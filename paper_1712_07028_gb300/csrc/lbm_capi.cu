@@ -143,6 +143,7 @@ int launched(lbm_ctx* c, int n) {
 int status_code(uint32_t st) {
     if (st & S_UNSTABLE) return LBM_EUNSTABLE;
     if (st & (S_OVERFLOW | S_BIN_OVERFLOW)) return LBM_EOVERFLOW;
+    if (st & S_MERGE) return LBM_EMERGE;
     return LBM_OK;
 }
 
@@ -722,6 +723,7 @@ const char* lbm_strerror(int code) {
         case LBM_ECUDA: return "CUDA runtime error";
         case LBM_EUNSTABLE: return "density became non-positive or NaN";
         case LBM_EOVERFLOW: return "worklist or neighbour bin overflow";
+        case LBM_EMERGE: return "two bubbles touch (merging is not modelled)";
         default: return "unknown error";
     }
 }

@@ -280,6 +280,7 @@ __device__ inline void conv_bulk(const Dev& d, const uint32_t wid, const uint32_
             int x, y, z;
             cell_xyz(d, i, x, y, z);
             if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
+            merge_check(d, i, j);   // a changed cell against each neighbour
         }
         set_bulk(d, j);
         d.mark[j] = 0;

@@ -139,7 +139,8 @@ struct Scalars {
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
-enum : uint32_t { S_UNSTABLE = 1, S_OVERFLOW = 2, S_BUBBLE_GONE = 4, S_BIN_OVERFLOW = 8, S_BAD_OWNER = 16, S_FAST_SPHERE = 32 };
+enum : uint32_t { S_UNSTABLE = 1, S_OVERFLOW = 2, S_BUBBLE_GONE = 4, S_BIN_OVERFLOW = 8, S_BAD_OWNER = 16, S_FAST_SPHERE = 32,
+                  S_MERGE = 64 };
 
 // all device pointers of one simulation; passed by value to every kernel
 struct Dev {
@@ -243,6 +244,14 @@ __device__ __forceinline__ void sph_offset(const Dev& d, const SphLink& l, const
 // spin on memory
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+}
+
+// two adjacent cells i, j of two bubbles' gas / interface regions: the bubbles touch (they
+// would have to merge, which is not modelled; the status word records it)
+__device__ __forceinline__ void merge_check(const Dev& d, size_t i, size_t j) {
+    if (!(d.flags[i] & (F_IF | F_GAS)) || !(d.flags[j] & (F_IF | F_GAS))) return;
+    const uint32_t a = d.owner[i], b = d.owner[j];
+    if (a < (uint32_t)d.nbub && b < (uint32_t)d.nbub && a != b) atomicOr(&d.sc->status, S_MERGE);
 }
 
 // byte-wise atomic OR / AND on the mark array (4-byte aligned base); returns the old byte

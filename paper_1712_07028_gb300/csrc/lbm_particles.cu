@@ -628,6 +628,7 @@ __device__ inline void cover_finish_dev(const Dev& d, const uint32_t wid, const 
             int x, y, z;
             cell_xyz(d, i, x, y, z);
             if (!nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j)) continue;
+            merge_check(d, i, j);   // a touched cell against each neighbour
         }
         set_bulk(d, j);
         if (lane == 0) d.tmark[i] = 0;   // BULK reads types only, never marks

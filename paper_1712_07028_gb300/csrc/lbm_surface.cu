@@ -126,6 +126,19 @@ __global__ void init_scan_kernel(const Dev d) {
         }
         // bubble volumes: owners and fill levels of the chunk's gas / interface cells
         if (!((w[0] | w[1] | w[2] | w[3]) & 0x06060606u)) continue;
+        // bubbles that touch from the start (the steps check every cell that changes)
+#pragma unroll 1
+        for (int c = 0; c < 16; c++) {
+            const uint8_t t = (uint8_t)(w[c / 4] >> (8 * (c % 4)));
+            if (!(t & (F_IF | F_GAS))) continue;
+            const size_t ic = v * 16 + c;
+            int x, y, z;
+            cell_xyz(d, ic, x, y, z);
+            for (int q = 1; q < kQ; q++) {
+                size_t j;
+                if (nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) merge_check(d, ic, j);
+            }
+        }
         uint32_t ob[16];
         float pv[16];
 #pragma unroll

@@ -16,9 +16,9 @@ from . import workloads as _wl
 
 _lib = None
 
-LBM_OK, LBM_EINVAL, LBM_ESTATE, LBM_ECUDA, LBM_EUNSTABLE, LBM_EOVERFLOW = 0, -1, -2, -3, -4, -5
+LBM_OK, LBM_EINVAL, LBM_ESTATE, LBM_ECUDA, LBM_EUNSTABLE, LBM_EOVERFLOW, LBM_EMERGE = 0, -1, -2, -3, -4, -5, -6
 CELL_LIQUID, CELL_INTERFACE, CELL_GAS, CELL_OBSTACLE = 1, 2, 4, 8
-S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW = 1, 2, 4, 8
+S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW, S_FAST_SPHERE, S_MERGE = 1, 2, 4, 8, 32, 64
 
 # every entry point include/lbm.h declares
 EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_step",

@@ -280,3 +280,50 @@ def test_launch_count(lbm):
     n1 = sim.launches()
     sim.step(10)
     assert (sim.launches() - n1) % 10 == 0 and sim.launches() > n1
+
+
+def _two_bubbles(c2=None, g=0.0):
+    if c2 is not None:   # side by side at rest
+        return W.Workload(name="two", nx=24, ny=16, nz=16, tau=0.7, g=(0, 0, 0), sphere_mode=W.SPHERES_FIXED,
+                          bubbles=[W.Bubble((7.0, 8.0, 8.0), 4.0), W.Bubble((c2, 8.0, 8.0), 4.0)])
+    # a large bubble rising into a small one
+    return W.Workload(name="two_rising", nx=16, ny=16, nz=40, tau=0.7, g=(0, 0, -g), sphere_mode=W.SPHERES_FIXED,
+                      bubbles=[W.Bubble((8.0, 8.0, 10.0), 5.0), W.Bubble((8.0, 8.0, 22.0), 3.0)])
+
+
+@pytest.mark.parametrize("c2,touching", [(15.0, True), (17.0, False)])
+def test_touching_bubbles_flagged_like_the_oracle(lbm, c2, touching):
+    """bubbles whose gas / interface cells touch are flagged (LBM_S_MERGE; lbm_forces returns
+    LBM_EMERGE), as the oracle flags them"""
+    wl = _two_bubbles(c2)
+    sim = lbm.Sim(wl)
+    sim.step(5)
+    o = oracle.Sim(wl)
+    o.step(5)
+    assert bool(sim.status() & lbm.S_MERGE) == touching == bool(int(o.scal[oracle.SC_STATUS]) & 4)
+    if touching:
+        with pytest.raises(lbm.LBMError) as e:
+            sim.forces()
+        assert e.value.code == lbm.LBM_EMERGE
+
+
+def test_bubbles_meeting_during_the_run_flagged_like_the_oracle(lbm):
+    """a large bubble rising into a small one: the step at which their regions first touch
+    (a conversion next to the other bubble) agrees with the oracle's to a few steps (FP32 vs
+    FP64 conversions near the threshold)"""
+    wl = _two_bubbles(g=3e-4)
+    sim = lbm.Sim(wl)
+    o = oracle.Sim(wl)
+    first_gpu = first_orc = None
+    for k in range(1, 501):
+        sim.step(1)
+        o.step(1)
+        if first_gpu is None and sim.status() & lbm.S_MERGE:
+            first_gpu = k
+        if first_orc is None and int(o.scal[oracle.SC_STATUS]) & 4:
+            first_orc = k
+        if first_gpu is not None and first_orc is not None:
+            break
+    print("bubbles first touch: GPU step %s, oracle step %s" % (first_gpu, first_orc))
+    assert first_orc is not None and first_gpu is not None
+    assert abs(first_gpu - first_orc) <= 5
