@@ -17,7 +17,7 @@
  *   - interface / liquid / gas conversions with layer closure, equilibrium initialisation
  *     of new interface cells and excess-mass redistribution (Sec. 2.2, Fig.
  *     cellConversions);
- *   - the bubble model (per-bubble volume -> gas density, Sec. 2.2);
+ *   - the bubble model (per-bubble volume -> gas density; touching bubbles merge, Sec. 2.2);
  *   - sphere update: lubrication correction (Eq. lubrication) and Newton-Euler sub-steps
  *     (Sec. 2.3), then cells covered / uncovered by the moved spheres and PDF refill.
  *
@@ -49,8 +49,8 @@ extern "C" {
 #define LBM_ECUDA (-3)       /* a CUDA runtime call failed */
 #define LBM_EUNSTABLE (-4)   /* a cell's density became non-positive or NaN */
 #define LBM_EOVERFLOW (-5)   /* a conversion worklist or a sphere bin overflowed */
-#define LBM_EMERGE (-6)      /* two bubbles' gas / interface regions touch (Sec. 2.2: they would
-                                merge; merging is not modelled, the state is flagged) */
+#define LBM_EMERGE (-6)      /* more distinct pairs of bubbles met in one step than the merge
+                                table holds (1024); the pairs beyond it were not merged */
 
 /* per-axis boundary kind */
 #define LBM_BC_WALL 0        /* no-slip wall halfway beyond the outermost cells */
@@ -77,7 +77,7 @@ extern "C" {
 #define LBM_S_OVERFLOW 2u        /* a conversion / covering worklist overflowed */
 #define LBM_S_BUBBLE_GONE 4u     /* a bubble's volume reached zero */
 #define LBM_S_BIN_OVERFLOW 8u    /* more spheres in a neighbour-search bin than it holds */
-#define LBM_S_MERGE 64u          /* a gas or interface cell of one bubble next to one of another */
+#define LBM_S_MERGE 64u          /* the merge table overflowed (see LBM_EMERGE) */
 #define LBM_S_FAST_SPHERE 32u    /* a sphere moved more than a quarter cell in one step (the
                                     per-step partner searches assume less) */
 
@@ -146,8 +146,21 @@ int lbm_forces(lbm_ctx* ctx, double* F, double* T, int n);
 int lbm_spheres(lbm_ctx* ctx, double* x, double* u, double* w, int n);
 
 /* Bubble table (host, FP64; any may be NULL): reference volume V0[n], volume V[n], gas
- * density rho_g[n].  Synchronises. */
+ * density rho_g[n] for bubble ids 0..n-1.  An id that has merged into a larger bubble
+ * reports the merged bubble's values.  Synchronises.
+ *
+ * Bubble merging (Sec. 2.2: a bubble is a connected gas region).  When a gas or interface
+ * cell of one bubble lies next to one of another (D3Q19 neighbourhood), the two are one bubble
+ * from the end of that step on: the larger root id joins the smaller, the gas masses add
+ * (rho_g0 V0 each, so the V0 add), V is the sum over all ids of the bubble and every id gets
+ * rho_g = rho_g0 V0 / V.  Cells keep the id they were created with.  Bubbles that touch
+ * from the start are merged at lbm_step(ctx, 0). */
 int lbm_bubbles(lbm_ctx* ctx, double* V0, double* V, double* rho_g, int n);
+
+/* Root id root[n] (host; NULL allowed) of bubble ids 0..n-1 -- the smallest id of the bubble
+ * each belongs to, itself if it never merged -- and the number of merges so far (*n_merges,
+ * NULL allowed).  Synchronises. */
+int lbm_bubble_roots(lbm_ctx* ctx, int32_t* root, int n, int* n_merges);
 
 /* Macroscopic fields into caller device buffers (any may be NULL): rho[N] and u[3][N]
  * (post-collision moments, u = (sum c f* - rho g / 2) / rho, the velocity the collision

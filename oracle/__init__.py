@@ -21,8 +21,8 @@ _lib = None
 # the oracle's cell-type codes and record layouts (fslbm_oracle.c)
 LIQ, IFACE, GAS, OBS = 1, 2, 4, 8
 S_X, S_U, S_W, S_R, S_RHO, S_F, S_T, S_FLUB, S_FP, S_TP, S_HASP, S_LEN = 0, 3, 6, 9, 10, 11, 14, 17, 20, 23, 26, 32
-B_C, B_R, B_V0, B_V, B_RHOG, B_LEN = 0, 3, 4, 5, 6, 8
-SC_POOL, SC_NIF, SC_SBB, SC_SCOV, SC_SUNC, SC_STEPS, SC_STATUS, SC_LEN = 0, 1, 2, 3, 4, 5, 6, 16
+B_C, B_R, B_V0, B_V, B_RHOG, B_ROOT, B_LEN = 0, 3, 4, 5, 6, 7, 8
+SC_POOL, SC_NIF, SC_SBB, SC_SCOV, SC_SUNC, SC_STEPS, SC_STATUS, SC_NMERGE, SC_LEN = 0, 1, 2, 3, 4, 5, 6, 7, 16
 
 
 def build(force: bool = False) -> str:
@@ -132,6 +132,7 @@ class Sim:
         self.nown = np.zeros(self.shape, np.int32)
         self.near = np.zeros(self.shape, np.int32)
         self.bub = np.zeros((max(1, len(bubbles)), B_LEN))
+        self.bub[:, B_ROOT] = np.arange(self.bub.shape[0])
         for b, (cx, cy, cz, r) in enumerate(bubbles):
             self.bub[b, B_C:B_C + 3] = (cx, cy, cz)
             self.bub[b, B_R] = r
@@ -229,6 +230,16 @@ class Sim:
     @property
     def volumes(self):
         return self.bub[: self.p.nbub, B_V].copy()
+
+    @property
+    def roots(self):
+        """root id of each bubble id (the smallest id of the merged bubble it belongs to)"""
+        up = self.bub[: self.p.nbub, B_ROOT].astype(np.int64)
+        r = up.copy()
+        for b in range(len(r)):
+            while up[r[b]] != r[b]:
+                r[b] = up[r[b]]
+        return r
 
     def momentum(self, with_positions=False):
         """total first moment sum_x sum_q c_q f*_q over active cells; optionally also the

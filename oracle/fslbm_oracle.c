@@ -62,11 +62,11 @@ enum { M_FILLED = 1, M_EMPTIED = 2, M_NEWIF = 4, M_FROMLIQ = 8, M_UNCOV = 16, M_
 enum { S_X = 0, S_U = 3, S_W = 6, S_R = 9, S_RHO = 10, S_F = 11, S_T = 14, S_FLUB = 17, S_FP = 20, S_TP = 23,
        S_HASP = 26, S_LEN = 32 };
 /* bubble record layout, doubles */
-enum { B_C = 0, B_R = 3, B_V0 = 4, B_V = 5, B_RHOG = 6, B_LEN = 8 };
+enum { B_C = 0, B_R = 3, B_V0 = 4, B_V = 5, B_RHOG = 6, B_ROOT = 7, B_LEN = 8 };
 /* scalar slots */
-enum { SC_POOL = 0, SC_NIF = 1, SC_SBB = 2, SC_SCOV = 3, SC_SUNC = 4, SC_STEPS = 5, SC_STATUS = 6, SC_LEN = 16 };
+enum { SC_POOL = 0, SC_NIF = 1, SC_SBB = 2, SC_SCOV = 3, SC_SUNC = 4, SC_STEPS = 5, SC_STATUS = 6, SC_NMERGE = 7, SC_LEN = 16 };
 /* status bits */
-enum { ST_UNSTABLE = 1, ST_BUBBLE_GONE = 2, ST_MERGE = 4 };
+enum { ST_UNSTABLE = 1, ST_BUBBLE_GONE = 2 };
 
 typedef struct {
     int32_t nx, ny, nz;
@@ -247,51 +247,83 @@ static void curvature(const orc_params *p, orc_state *s)
 
 /* ---------------------------------------------------------------- step 3: bubble model */
 
-/* V_b = #gas cells of bubble b + sum over its interface cells of (1 - phi);
- * isothermal ideal gas of conserved mass: rho_g,b = rho_g0 V_b(0) / V_b(t). */
+/* A bubble is a connected gas region (Sec. 2.2).  Every gas or interface cell carries the id
+ * of the bubble it was created in; when the regions of two bubbles touch (a gas or interface
+ * cell next to one of another bubble) they are one bubble from then on: the ids are joined,
+ * the smaller id being the root of the merged bubble.  The merged bubble's gas mass is the sum
+ * of the two (rho_g0 V0 each, so the reference volumes add), its volume the sum of its
+ * members' volumes.  Splitting is not modelled.
+ *
+ * V = #gas cells + sum over the interface cells of (1 - phi) of all ids of the bubble;
+ * isothermal ideal gas of conserved mass: rho_g = rho_g0 V0 / V.  Every id of a merged bubble
+ * holds the merged bubble's V0, V and rho_g. */
+static int bubble_root(const orc_state *s, int b)
+{
+    while ((int)s->bub[b * B_LEN + B_ROOT] != b) b = (int)s->bub[b * B_LEN + B_ROOT];
+    return b;
+}
+
 static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
 {
     const long N = ncell(p);
+    const int nb = p->nbub;
+    if (nb <= 0) {
+        long nif = 0;
+        for (long i = 0; i < N; i++) nif += (s->flag[i] & C_IF) != 0;
+        s->scal[SC_NIF] = (double)nif;
+        return;
+    }
+    double *own = calloc((size_t)nb, sizeof(double));   /* volume of the cells carrying id b */
+    double *Vr = calloc((size_t)nb, sizeof(double));    /* volume of the bubble rooted at b */
     long nif = 0;
-    for (int b = 0; b < p->nbub; b++) s->bub[b * B_LEN + B_V] = 0.0;
     for (long i = 0; i < N; i++) {
         uint8_t t = s->flag[i];
         int b = s->owner[i];
         if (t & C_IF) {
             nif++;
-            if (b >= 0 && b < p->nbub) s->bub[b * B_LEN + B_V] += 1.0 - s->phi[i];
+            if (b >= 0 && b < nb) own[b] += 1.0 - s->phi[i];
         } else if (t & C_GAS) {
-            if (b >= 0 && b < p->nbub) s->bub[b * B_LEN + B_V] += 1.0;
+            if (b >= 0 && b < nb) own[b] += 1.0;
         }
     }
     s->scal[SC_NIF] = (double)nif;
-    /* bubbles that touch (a gas or interface cell next to a gas or interface cell of another
-     * bubble) would have to merge (the paper's bubble model joins them); that is not modelled
-     * here: the state is flagged */
+    if (set_reference)
+        for (int b = 0; b < nb; b++) s->bub[b * B_LEN + B_V0] = own[b];
     for (int z = 0; z < p->nz; z++)
         for (int y = 0; y < p->ny; y++)
             for (int x = 0; x < p->nx; x++) {
                 const long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
                 const int b = s->owner[i];
-                if (!(s->flag[i] & (C_IF | C_GAS)) || b < 0 || b >= p->nbub) continue;
+                if (!(s->flag[i] & (C_IF | C_GAS)) || b < 0 || b >= nb) continue;
                 for (int q = 1; q < NQ; q++) {
                     const long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
                     if (j < 0 || !(s->flag[j] & (C_IF | C_GAS))) continue;
                     const int bj = s->owner[j];
-                    if (bj >= 0 && bj < p->nbub && bj != b) s->scal[SC_STATUS] = (double)((int)s->scal[SC_STATUS] | ST_MERGE);
+                    if (bj < 0 || bj >= nb) continue;
+                    const int ra = bubble_root(s, b), rb = bubble_root(s, bj);
+                    if (ra == rb) continue;
+                    const int lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
+                    s->bub[hi * B_LEN + B_ROOT] = (double)lo;
+                    s->bub[lo * B_LEN + B_V0] += s->bub[hi * B_LEN + B_V0];
+                    s->scal[SC_NMERGE] += 1.0;
                 }
             }
-    for (int b = 0; b < p->nbub; b++) {
+    for (int b = 0; b < nb; b++) Vr[bubble_root(s, b)] += own[b];
+    for (int b = 0; b < nb; b++) {
         double *B = s->bub + b * B_LEN;
+        const int r = bubble_root(s, b);
+        B[B_V0] = s->bub[r * B_LEN + B_V0];
+        B[B_V] = Vr[r];
         if (set_reference) {
-            B[B_V0] = B[B_V];
             B[B_RHOG] = p->rho_g0;
-        } else if (B[B_V] > 0.0) {
-            B[B_RHOG] = p->rho_g0 * B[B_V0] / B[B_V];
+        } else if (Vr[r] > 0.0) {
+            B[B_RHOG] = p->rho_g0 * B[B_V0] / Vr[r];
         } else {
             s->scal[SC_STATUS] = (double)((int)s->scal[SC_STATUS] | ST_BUBBLE_GONE);
         }
     }
+    free(own);
+    free(Vr);
 }
 
 /* ------------------------------------------------------------------ step 1: the sweep */
@@ -769,6 +801,7 @@ static void cover_uncover(const orc_params *p, orc_state *s)
 int orc_init(const orc_params *p, orc_state *s)
 {
     const long N = ncell(p);
+    for (int b = 0; b < p->nbub; b++) s->bub[b * B_LEN + B_ROOT] = (double)b;
     for (int z = 0; z < p->nz; z++)
         for (int y = 0; y < p->ny; y++)
             for (int x = 0; x < p->nx; x++) {

@@ -87,7 +87,7 @@ size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 :
 
 struct Layout {
     size_t f[2], flags, mark, tmark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
-        adj_srho, adj_part, total;
+        adj_srho, adj_part, merge_keys, merge_list, total;
     size_t N, wl_cap, nbins_max;
 };
 
@@ -125,6 +125,8 @@ Layout layout_of(const lbm_params* p) {
     L.geo = take(sizeof(double) * 4 * (size_t)p->max_bubbles);
     L.adj_srho = take(4 * L.N);
     L.adj_part = take(sizeof(double) * 5 * kAdjSlots);
+    L.merge_keys = take(sizeof(unsigned long long) * kMergeCap);
+    L.merge_list = take(sizeof(uint32_t) * kMergeCap);
     L.total = o;
     return L;
 }
@@ -312,6 +314,8 @@ int first_step(lbm_ctx* c) {
     d.bin_ids = (uint32_t*)(a + L.bin_ids);
     d.npairs = (uint32_t*)(a + L.npairs);
     d.pairs = (uint32_t*)(a + L.pairs);
+    d.merge_keys = (unsigned long long*)(a + L.merge_keys);
+    d.merge_list = (uint32_t*)(a + L.merge_list);
     c->geo_dev = (double*)(a + L.geo);
     c->adj_srho = (float*)(a + L.adj_srho);
     c->adj_part = (double*)(a + L.adj_part);
@@ -561,6 +565,19 @@ int lbm_bubbles(lbm_ctx* c, double* V0, double* V, double* rho_g, int n) {
     return LBM_OK;
 }
 
+int lbm_bubble_roots(lbm_ctx* c, int32_t* root, int n, int* n_merges) {
+    if (!c || n < 0) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
+    if (n > c->d.nbub) return LBM_EINVAL;
+    int rc = sync_tables(c);
+    if (rc) return rc;
+    for (int b = 0; b < n; b++)
+        if (root) root[b] = c->bub_stage[b].root;
+    if (n_merges) *n_merges = (int)c->sc_stage->n_merges;
+    return LBM_OK;
+}
+
 int lbm_fields(lbm_ctx* c, float* rho, float* u, float* phi, uint8_t* flags) {
     if (!c) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;
@@ -723,7 +740,7 @@ const char* lbm_strerror(int code) {
         case LBM_ECUDA: return "CUDA runtime error";
         case LBM_EUNSTABLE: return "density became non-positive or NaN";
         case LBM_EOVERFLOW: return "worklist or neighbour bin overflow";
-        case LBM_EMERGE: return "two bubbles touch (merging is not modelled)";
+        case LBM_EMERGE: return "more pairs of bubbles met in one step than the merge table holds";
         default: return "unknown error";
     }
 }

@@ -111,13 +111,18 @@ struct SphereAcc {       // per-step momentum-exchange accumulators (zeroed by t
     unsigned long long XK[3];  // sum of x_img x (constant part), times 36
     double C[3], TC[3];        // force and torque of the links between obstacle nodes of two spheres
 };
+// one record per bubble id; ids of bubbles that have merged share a root (the smallest id of
+// the merged bubble) and hold the merged bubble's V0, V and rho_g
 struct Bubble {
-    double V0, V, rho_g, Vif;    // reference volume, volume, gas density, interface part of V
-    unsigned long long ngas;     // gas cells
+    double V0, V, rho_g, Vif;    // reference volume, volume, gas density, interface part of this id's volume
+    unsigned long long ngas;     // gas cells carrying this id
     float rho_gf;                // FP32 copy of rho_g for the sweep
-    float padf;
-    unsigned long long pad[2];
+    int root;                    // root id (itself until the bubble merges)
+    double Vtot[2];              // merged-volume sums at a root, alternating between step closes
 };
+static_assert(sizeof(Bubble) == 64, "bubble record size");
+// distinct pairs of bubbles that may meet in one step (open-addressing table of pairs)
+constexpr int kMergeCap = 1024;
 struct Scalars {
     double pool;          // excess mass waiting to be spread over the interface cells
     double pool_acc;      // excess of this step that found no receiving neighbour
@@ -135,7 +140,10 @@ struct Scalars {
     uint32_t ticket;      // blocks of the end-of-step scan that have finished
     uint32_t n_fix;       // BULK cells the end of the last step changed or whose neighbours it changed
     uint32_t fix_all;     // the fix list overflowed: the fix pass takes every BULK cell
-    uint32_t pad1[2];
+    uint32_t n_merge;     // distinct pairs of touching bubbles recorded since the last close
+    uint32_t merged;      // some bubbles have merged: the close sums volumes per root
+    uint32_t vpar;        // which Vtot slot the next close sums into
+    uint32_t n_merges;    // merges so far
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
@@ -185,6 +193,8 @@ struct Dev {
     uint32_t* bin_ids;        // [nbins][bin_cap]
     uint32_t* npairs;         // [max_sph] partners within lubrication reach this step
     uint32_t* pairs;          // [max_sph][kPairCap]
+    unsigned long long* merge_keys;   // [kMergeCap] pairs (lo + 1) << 32 | hi of touching roots, 0 = free
+    uint32_t* merge_list;     // [kMergeCap] slots of merge_keys in use, in insertion order
 };
 constexpr int kPairCap = 32;
 
@@ -245,13 +255,35 @@ __device__ __forceinline__ void sph_offset(const Dev& d, const SphLink& l, const
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;\n" ::: "memory");
 }
+struct ClusterSync {
+    __device__ void operator()() const { cluster_sync(); }
+};
+struct BlockSync {
+    __device__ void operator()() const { __syncthreads(); }
+};
 
-// two adjacent cells i, j of two bubbles' gas / interface regions: the bubbles touch (they
-// would have to merge, which is not modelled; the status word records it)
+// two adjacent cells i, j of two bubbles' gas / interface regions: the bubbles touch and are one
+// connected gas region from now on (Sec. 2.2: a bubble is a connected gas region).  The pair of
+// roots is recorded once per step (the table is probed from a hash of the pair); the step's
+// close joins them.  Roots change only at a close, so they are stable here.
 __device__ __forceinline__ void merge_check(const Dev& d, size_t i, size_t j) {
     if (!(d.flags[i] & (F_IF | F_GAS)) || !(d.flags[j] & (F_IF | F_GAS))) return;
     const uint32_t a = d.owner[i], b = d.owner[j];
-    if (a < (uint32_t)d.nbub && b < (uint32_t)d.nbub && a != b) atomicOr(&d.sc->status, S_MERGE);
+    if (a >= (uint32_t)d.nbub || b >= (uint32_t)d.nbub || a == b) return;
+    const uint32_t ra = (uint32_t)d.bub[a].root, rb = (uint32_t)d.bub[b].root;
+    if (ra == rb) return;
+    const uint32_t lo = min(ra, rb), hi = max(ra, rb);
+    const unsigned long long key = ((unsigned long long)(lo + 1u) << 32) | hi;
+    uint32_t h = (lo * 0x9E3779B1u ^ hi * 0x85EBCA77u) & (kMergeCap - 1);
+    for (int k = 0; k < kMergeCap; k++, h = (h + 1) & (kMergeCap - 1)) {
+        const unsigned long long old = atomicCAS(&d.merge_keys[h], 0ull, key);
+        if (old == key) return;   // recorded already
+        if (old == 0ull) {
+            d.merge_list[atomicAdd(&d.sc->n_merge, 1u)] = h;   // at most kMergeCap insertions
+            return;
+        }
+    }
+    atomicOr(&d.sc->status, S_MERGE);   // more distinct pairs in one step than the table holds
 }
 
 // byte-wise atomic OR / AND on the mark array (4-byte aligned base); returns the old byte
@@ -499,16 +531,85 @@ __device__ __forceinline__ uint32_t covering_sphere(const Dev& d, int x, int y, 
 // boundary list are reset;
 // moved spheres enter the bins of their new centres.  Run by every thread (t of nt) of the
 // step's last kernel, after its last barrier.
-__device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t nt, const bool bin_spheres) {
+// joins the recorded pairs of touching roots (one thread): the larger root joins the smaller
+// and passes on its reference volume (the gas mass over rho_g0: masses add); then every id
+// points at its root directly (roots are never larger than the ids below them, so one pass in
+// increasing id order suffices)
+__device__ inline void merge_apply(const Dev& d, const uint32_t n) {
+    Bubble* B = d.bub;
+    auto find = [&](int b) { while (B[b].root != b) b = B[b].root; return b; };   // roots: this thread's writes
+    for (uint32_t k = 0; k < min(n, (uint32_t)kMergeCap); k++) {
+        const uint32_t h = __ldcg(&d.merge_list[k]);
+        const unsigned long long key = __ldcg(&d.merge_keys[h]);
+        d.merge_keys[h] = 0ull;
+        const int ra = find((int)(key >> 32) - 1), rb = find((int)(key & 0xffffffffu));
+        if (ra == rb) continue;
+        const int lo = min(ra, rb), hi = max(ra, rb);
+        B[hi].root = lo;
+        B[lo].V0 = __ldcg(&B[lo].V0) + __ldcg(&B[hi].V0);
+        d.sc->n_merges++;
+    }
+    for (int b = 0; b < d.nbub; b++) B[b].root = B[B[b].root].root;
+    d.sc->n_merge = 0;
+    d.sc->merged = 1;
+}
+
+// the bubble model at the end of a step (Sec. 2.2): V of each bubble = its gas cells + the
+// interface part the sweep summed (both kept per id), rho_g = rho_g0 V0 / V; with init, V0 = V
+// and rho_g = rho_g0 instead.  Threads t of nt; sync() is a barrier over all of them.  Until
+// the first merge every id is its own bubble and no barrier is needed.
+template <class Sync>
+__device__ inline void bubbles_close(const Dev& d, const uint32_t t, const uint32_t nt, const bool init, Sync sync) {
+    Scalars& c = *d.sc;
+    // written only by merge_check before the caller's last barrier and by this close's thread 0
+    // after the barriers below: every thread reads the same values here
+    const uint32_t nm = *(volatile uint32_t*)&c.n_merge;
+    if (nm == 0u && *(volatile uint32_t*)&c.merged == 0u) {
+        for (uint32_t b = t; b < (uint32_t)d.nbub; b += nt) {
+            Bubble& B = d.bub[b];
+            const double V = (double)(long long)__ldcg(&B.ngas) + __ldcg(&B.Vif);
+            B.V = V;
+            if (init) { B.V0 = V; B.rho_g = (double)d.rho_g0; }
+            else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
+            else atomicOr(&c.status, S_BUBBLE_GONE);
+            B.rho_gf = (float)B.rho_g;
+            B.Vif = 0.0;
+        }
+        return;
+    }
+    const uint32_t par = *(volatile uint32_t*)&c.vpar;
     for (uint32_t b = t; b < (uint32_t)d.nbub; b += nt) {
         Bubble& B = d.bub[b];
-        const double V = (double)(long long)B.ngas + B.Vif;
-        B.V = V;
-        if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
-        else atomicOr(&d.sc->status, S_BUBBLE_GONE);
-        B.rho_gf = (float)B.rho_g;
+        B.V = (double)(long long)__ldcg(&B.ngas) + __ldcg(&B.Vif);   // this id's part
         B.Vif = 0.0;
+        if (init) B.V0 = B.V;
+        B.Vtot[par ^ 1u] = 0.0;   // read by the last close; summed into by the next
     }
+    sync();
+    if (t == 0 && nm != 0u) merge_apply(d, nm);
+    sync();
+    // every thread handles the same ids in every loop: B.V below is its own write
+    for (uint32_t b = t; b < (uint32_t)d.nbub; b += nt) atomicAdd(&d.bub[__ldcg(&d.bub[b].root)].Vtot[par], d.bub[b].V);
+    sync();
+    for (uint32_t b = t; b < (uint32_t)d.nbub; b += nt) {
+        Bubble& B = d.bub[b];
+        const Bubble& R = d.bub[__ldcg(&B.root)];
+        const double V = __ldcg(&R.Vtot[par]);
+        B.V = V;
+        B.V0 = __ldcg(&R.V0);
+        if (init) B.rho_g = (double)d.rho_g0;
+        else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
+        else atomicOr(&c.status, S_BUBBLE_GONE);
+        B.rho_gf = (float)B.rho_g;
+    }
+    if (t == 0) c.vpar = par ^ 1u;
+}
+
+// the end of a step: bubble model, excess pool and counters, new sphere bins.  Every thread of
+// the launch (nt of them) calls it; sync() is a barrier over all of them.
+template <class Sync>
+__device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t nt, const bool bin_spheres, Sync sync) {
+    bubbles_close(d, t, nt, false, sync);
     if (t == 0) {
         Scalars& c = *d.sc;
         if (c.share != 0.0) c.pool = 0.0;

@@ -661,7 +661,7 @@ __global__ void __cluster_dims__(kCoverCtas, 1, 1) __launch_bounds__(kCoverThrea
     bins_clear(d, t, nt);
     cluster_sync();
     // the last end-of-step kernel: it closes the step (bubble model, counters, new bins)
-    step_close(d, t, nt, true);
+    step_close(d, t, nt, true, ClusterSync{});
 }
 
 int spheres_links_launches(const Dev& d) { return d.nsph == 0 ? 0 : 2; }

@@ -25,7 +25,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
     // no interface cell crossed a threshold: nothing converts (every thread reads the same
     // count: it is reset only by a step close, which no thread reaches before all have read it)
     if (*(volatile const uint32_t*)&d.sc->n_conv == 0u) {
-        if (close) step_close(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, false);
+        if (close) step_close(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, false, ClusterSync{});
         return;
     }
     conv_filled_emptied<S>(d, nxt, wid, nw);
@@ -40,7 +40,7 @@ __global__ void __cluster_dims__(kClusterCtas, 1, 1) __launch_bounds__(kClusterT
     conv_bulk(d, wid, nw);
     if (close) {   // no cover kernel follows: this launch closes the step (the same for all threads)
         cluster_sync();
-        step_close(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, false);
+        step_close(d, blockIdx.x * blockDim.x + threadIdx.x, gridDim.x * blockDim.x, false, ClusterSync{});
     }
 }
 
@@ -196,15 +196,9 @@ __global__ void init_scan_kernel(const Dev d) {
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) {
-        Bubble& B = d.bub[b];
-        const double V = (double)*(volatile unsigned long long*)&B.ngas + *(volatile double*)&B.Vif;
-        B.V = V;
-        B.V0 = V;
-        B.rho_g = (double)d.rho_g0;
-        B.rho_gf = (float)B.rho_g;
-        B.Vif = 0.0;   // the gas count carries over; the sweep sums the interface part afresh
-    }
+    // V0 = V and rho_g = rho_g0; bubbles that touch from the start are merged.  The gas count
+    // carries over; the sweep sums the interface part afresh
+    bubbles_close(d, threadIdx.x, blockDim.x, true, BlockSync{});
     if (threadIdx.x == 0) {
         Scalars& c = *d.sc;
         c.n_iface = *(volatile uint32_t*)&c.n_iface_acc;
@@ -358,6 +352,7 @@ template <int S>
 __global__ void init_kernel(const Dev d, const double* geo) {
     using T = typename Store<S>::T;
     T* f = static_cast<T*>(d.f[0]);
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.nbub; b += gridDim.x * blockDim.x) d.bub[b].root = b;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
         cell_xyz(d, i, x, y, z);

@@ -22,7 +22,7 @@ S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW, S_FAST_SPHERE, S_MERGE = 
 
 # every entry point include/lbm.h declares
 EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_step",
-           "lbm_forces", "lbm_spheres", "lbm_bubbles", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
+           "lbm_forces", "lbm_spheres", "lbm_bubbles", "lbm_bubble_roots", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
            "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count",
            "lbm_bubble_volumes_noalloc", "lbm_forward_frozen", "lbm_adjoint_step", "lbm_destroy", "lbm_strerror")
 
@@ -65,6 +65,7 @@ def load():
     L.lbm_forces.argtypes = [vp, pd, pd, i32]
     L.lbm_spheres.argtypes = [vp, pd, pd, pd, i32]
     L.lbm_bubbles.argtypes = [vp, pd, pd, pd, i32]
+    L.lbm_bubble_roots.argtypes = [vp, ctypes.POINTER(i32), i32, ctypes.POINTER(i32)]
     L.lbm_fields.argtypes = [vp, vp, vp, vp, vp]
     L.lbm_export_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.lbm_mass_budget.argtypes = [vp, pd]
@@ -171,6 +172,15 @@ class Sim:
         V0, V, rg = (np.zeros(max(1, self.nbub)) for _ in range(3))
         _check("lbm_bubbles", load().lbm_bubbles(self.ctx, _dp(V0), _dp(V), _dp(rg), self.nbub))
         return V0[: self.nbub], V[: self.nbub], rg[: self.nbub]
+
+    def bubble_roots(self):
+        """(root id of every bubble id, number of merges so far)"""
+        self._bind_stream()
+        root = np.zeros(max(1, self.nbub), dtype=np.int32)
+        nm = ctypes.c_int(0)
+        _check("lbm_bubble_roots", load().lbm_bubble_roots(self.ctx, root.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                                                           self.nbub, ctypes.byref(nm)))
+        return root[: self.nbub].astype(np.int64), nm.value
 
     def fields(self):
         """dict of torch tensors on the device: rho [z,y,x], u [3,z,y,x], phi, flags"""

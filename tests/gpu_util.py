@@ -19,9 +19,10 @@ def gpu_state(sim):
     st["u"] = fl["u"].cpu().numpy().astype(np.float64)
     x, u, w = sim.spheres()
     V0, V, rg = sim.bubbles()
+    roots, n_merges = sim.bubble_roots()
     M, sbb, scov, sunc, pool = sim.mass_budget()
     F, T = sim.forces()
-    st.update(sx=x, su=u, sw=w, V0=V0, V=V, rho_g=rg, pool=pool, F=F, T=T, steps=sim.steps_done)
+    st.update(sx=x, su=u, sw=w, V0=V0, V=V, rho_g=rg, roots=roots, n_merges=n_merges, pool=pool, F=F, T=T, steps=sim.steps_done)
     return st
 
 
@@ -38,6 +39,7 @@ def oracle_from_state(wl: W.Workload, st, near_tol=1e-5):
         o.bub[b, oracle.B_V0] = st["V0"][b]
         o.bub[b, oracle.B_V] = st["V"][b]
         o.bub[b, oracle.B_RHOG] = st["rho_g"][b]
+        o.bub[b, oracle.B_ROOT] = st["roots"][b]
     for a in range(len(wl.spheres)):
         o.sph[a, oracle.S_X:oracle.S_X + 3] = st["sx"][a]
         o.sph[a, oracle.S_U:oracle.S_U + 3] = st["su"][a]

@@ -291,39 +291,124 @@ def _two_bubbles(c2=None, g=0.0):
                       bubbles=[W.Bubble((8.0, 8.0, 10.0), 5.0), W.Bubble((8.0, 8.0, 22.0), 3.0)])
 
 
+def _gas_volume(st, ids):
+    """V of a set of bubble ids from exported cell fields: gas cells + sum over interface cells
+    of (1 - phi), in FP64"""
+    sel = np.isin(st["owner"], list(ids))
+    return float(((st["flags"] == oracle.GAS) & sel).sum() + (1.0 - st["phi"][(st["flags"] == oracle.IFACE) & sel].astype(np.float64)).sum())
+
+
 @pytest.mark.parametrize("c2,touching", [(15.0, True), (17.0, False)])
-def test_touching_bubbles_flagged_like_the_oracle(lbm, c2, touching):
-    """bubbles whose gas / interface cells touch are flagged (LBM_S_MERGE; lbm_forces returns
-    LBM_EMERGE), as the oracle flags them"""
+def test_touching_bubbles_merge_like_the_oracle(lbm, c2, touching):
+    """bubbles whose gas / interface cells touch from the start are one bubble (Sec. 2.2):
+    the same roots, merge count, V0, V and rho_g as the oracle's"""
     wl = _two_bubbles(c2)
     sim = lbm.Sim(wl)
     sim.step(5)
     o = oracle.Sim(wl)
     o.step(5)
-    assert bool(sim.status() & lbm.S_MERGE) == touching == bool(int(o.scal[oracle.SC_STATUS]) & 4)
-    if touching:
-        with pytest.raises(lbm.LBMError) as e:
-            sim.forces()
-        assert e.value.code == lbm.LBM_EMERGE
+    roots, nm = sim.bubble_roots()
+    assert list(roots) == list(o.roots) == ([0, 0] if touching else [0, 1])
+    assert nm == o.scal[oracle.SC_NMERGE] == (1 if touching else 0)
+    V0, V, rg = sim.bubbles()
+    # FP32 fill levels summed in FP64 on both sides of the comparison
+    assert np.abs(V0 - o.bub[:2, oracle.B_V0]).max() <= 1e-5 * V0.max()
+    assert np.abs(V - o.volumes).max() <= 1e-5 * V.max()
+    assert np.abs(rg - o.rho_gas).max() <= 1e-6
+    assert sim.status() == 0
+    st = U.gpu_state(sim)
+    for r in set(roots):
+        ids = [b for b in range(2) if roots[b] == r]
+        assert abs(V[r] - _gas_volume(st, ids)) <= 1e-9 * V[r]
 
 
-def test_bubbles_meeting_during_the_run_flagged_like_the_oracle(lbm):
-    """a large bubble rising into a small one: the step at which their regions first touch
-    (a conversion next to the other bubble) agrees with the oracle's to a few steps (FP32 vs
-    FP64 conversions near the threshold)"""
+def _bubble_lattice(n, sp, r, chains):
+    """n^3 bubbles of radius r on a periodic lattice of spacing sp; with chains the lattice is
+    stretched to 2 sp across x, so that only x-neighbours touch (one chain of n bubbles per
+    (y, z))"""
+    spy = 2 * sp if chains else sp
+    L = (n * sp, n * spy, n * spy)
+    bubs = [W.Bubble((sp * i + sp / 2 - 0.5, spy * j + spy / 2 - 0.5, spy * k + spy / 2 - 0.5), r)
+            for k in range(n) for j in range(n) for i in range(n)]
+    return W.Workload(name="lattice", nx=L[0], ny=L[1], nz=L[2], tau=0.7, g=(0, 0, 0), bc=(W.PERIODIC,) * 3,
+                      sphere_mode=W.SPHERES_FIXED, bubbles=bubs)
+
+
+def test_bubble_chains_merge_at_initialisation(lbm):
+    """64 chains of 8 touching bubbles each (512 bubbles, 512 touching pairs): every chain is
+    one bubble rooted at its smallest id, as the oracle's; its V0 is the chain's gas volume"""
+    wl = _bubble_lattice(8, 3, 1.6, chains=True)
+    sim = lbm.Sim(wl)
+    sim.step(0)
+    roots, nm = sim.bubble_roots()
+    n = 8
+    expect = np.array([(b // n) * n for b in range(n ** 3)])   # ids run along x fastest
+    assert (roots == expect).all()
+    assert nm == n ** 3 - n ** 2
+    o = oracle.Sim(wl)
+    assert (o.roots == expect).all() and o.scal[oracle.SC_NMERGE] == nm
+    V0, V, rg = sim.bubbles()
+    st = U.gpu_state(sim)
+    for c in range(0, n ** 3, n * 7):   # a sample of the chains
+        v = _gas_volume(st, range(c, c + n))
+        assert abs(V0[c] - v) <= 1e-9 * v and (V0[c:c + n] == V0[c]).all() and (V[c:c + n] == V0[c]).all()
+    assert np.abs(V0 - o.bub[: n ** 3, oracle.B_V0]).max() <= 1e-5 * V0.max()
+    assert (rg == 1.0).all() and sim.status() == 0
+
+
+def test_merge_table_overflow_is_reported(lbm):
+    """a packed lattice where every bubble touches its 18 D3Q19 neighbours: 1944 distinct pairs
+    meet at once, more than the merge table holds: the state is flagged (LBM_S_MERGE) and the
+    calls that read it return LBM_EMERGE"""
+    wl = _bubble_lattice(6, 3, 1.5, chains=False)
+    sim = lbm.Sim(wl)
+    sim.step(0)
+    assert sim.status() & lbm.S_MERGE
+    with pytest.raises(lbm.LBMError) as e:
+        sim.forces()
+    assert e.value.code == lbm.LBM_EMERGE
+
+
+def test_bubbles_merging_during_the_run_like_the_oracle(lbm):
+    """a large bubble rising into a small one: the step at which they merge agrees with the
+    oracle's to a few steps (FP32 vs FP64 conversions near the threshold); after it they are one
+    bubble whose gas mass is the sum of the two initial masses (rho_g V = rho_g0 (V0_a + V0_b),
+    V from the exported cells), with the oracle's gas density"""
     wl = _two_bubbles(g=3e-4)
     sim = lbm.Sim(wl)
     o = oracle.Sim(wl)
+    sim.step(0)
+    m0 = sim.bubbles()[0].copy()   # rho_g0 = 1
     first_gpu = first_orc = None
     for k in range(1, 501):
         sim.step(1)
         o.step(1)
-        if first_gpu is None and sim.status() & lbm.S_MERGE:
+        if first_gpu is None and sim.bubble_roots()[1] > 0:
             first_gpu = k
-        if first_orc is None and int(o.scal[oracle.SC_STATUS]) & 4:
+        if first_orc is None and o.scal[oracle.SC_NMERGE] > 0:
             first_orc = k
         if first_gpu is not None and first_orc is not None:
             break
-    print("bubbles first touch: GPU step %s, oracle step %s" % (first_gpu, first_orc))
+    print("bubbles merge: GPU step %s, oracle step %s" % (first_gpu, first_orc))
     assert first_orc is not None and first_gpu is not None
     assert abs(first_gpu - first_orc) <= 5
+    sim.step(20)
+    o.step(20)
+    roots, nm = sim.bubble_roots()
+    assert list(roots) == [0, 0] and nm == 1
+    V0, V, rg = sim.bubbles()
+    assert V0[0] == V0[1] and abs(V0[0] - m0.sum()) <= 1e-12 * m0.sum()
+    st = U.gpu_state(sim)
+    Vf = _gas_volume(st, [0, 1])
+    assert abs(rg[0] * Vf - m0.sum()) <= 1e-9 * m0.sum()
+    assert rg[0] == rg[1]
+    assert abs(rg[0] - o.rho_gas[0]) <= 1e-4 * abs(o.rho_gas[0] - 1.0) + 1e-6
+    assert sim.status() == 0
+
+
+def test_one_step_from_merged_state(lbm):
+    """every part of one step with two merged bubbles rising: the oracle steps the GPU's own
+    merged state once (roots, V0 and rho_g copied over)"""
+    wl = _two_bubbles(15.0)
+    wl.g = (0.0, 0.0, -2e-4)
+    _one_step_check(lbm, wl, 30, 2e-6, 2e-6)

@@ -363,18 +363,87 @@ def test_light_free_sphere_stays_at_rest(orc, rho, R):
     assert np.abs(s.sph[0, orc.S_W:orc.S_W + 3]).max() < 1e-12
 
 
-@pytest.mark.parametrize("c2,touching", [(15.0, True), (17.0, False)])
-def test_touching_bubbles_are_flagged(orc, c2, touching):
-    """Bubbles whose gas/interface cells touch would have to merge (the paper's bubble model
-    joins them); the oracle does not merge them but flags the state.  Two r = 4 bubbles: at
-    centre distance 8 their interface layers overlap, at 10 one liquid cell separates them."""
+def _gas_volume(orc, o, ids=None):
+    """V of a set of bubble ids from the cell fields alone: gas cells + sum over interface cells
+    of (1 - phi) (bubble model, Sec. 2.2)"""
+    sel = np.ones(o.flag.shape, bool) if ids is None else np.isin(o.owner, list(ids))
+    gas = (o.flag == orc.GAS) & sel
+    itf = (o.flag == orc.IFACE) & sel
+    return gas.sum() + (1.0 - o.phi[itf]).sum()
+
+
+def _side_by_side(c2, g=(0, 0, 0)):
     from paper_1712_07028_gb300 import workloads as W
-    wl = W.Workload(name="two", nx=24, ny=16, nz=16, tau=0.7, g=(0, 0, 0), sphere_mode=W.SPHERES_FIXED,
-                    bubbles=[W.Bubble((7.0, 8.0, 8.0), 4.0), W.Bubble((c2, 8.0, 8.0), 4.0)])
-    o = orc.Sim(wl)
+    return W.Workload(name="two", nx=24, ny=16, nz=16, tau=0.7, g=g, sphere_mode=W.SPHERES_FIXED,
+                      bubbles=[W.Bubble((7.0, 8.0, 8.0), 4.0), W.Bubble((c2, 8.0, 8.0), 4.0)])
+
+
+@pytest.mark.parametrize("c2,touching", [(15.0, True), (17.0, False)])
+def test_touching_bubbles_merge(orc, c2, touching):
+    """Sec. 2.2: a bubble is a connected gas region, so two bubbles whose gas / interface cells
+    touch are one.  Two r = 4 bubbles: at centre distance 8 their interface layers overlap and
+    they merge at initialisation (one root, V0 = V = the gas volume of all their cells); at 10
+    one liquid cell separates them and each keeps its own volume."""
+    o = orc.Sim(_side_by_side(c2))
     o.step(5)
-    flagged = (int(o.scal[orc.SC_STATUS]) & 4) != 0
-    assert flagged == touching
-    # the separating liquid layer: on the line between the centres x = 12 stays liquid
-    if not touching:
-        assert o.flag[8, 8, 12] == orc.LIQ
+    if touching:
+        assert list(o.roots) == [0, 0] and o.scal[orc.SC_NMERGE] == 1
+        V = _gas_volume(orc, o)
+        assert np.allclose(o.bub[:2, orc.B_V0], V, rtol=1e-13)
+        assert np.allclose(o.volumes, V, rtol=1e-13)
+    else:
+        assert list(o.roots) == [0, 1] and o.scal[orc.SC_NMERGE] == 0
+        for b in range(2):
+            assert np.isclose(o.volumes[b], _gas_volume(orc, o, [b]), rtol=1e-13)
+        assert o.flag[8, 8, 12] == orc.LIQ   # the separating liquid layer
+    assert np.allclose(o.rho_gas, 1.0, rtol=1e-13)
+    assert int(o.scal[orc.SC_STATUS]) == 0
+
+
+def test_merged_bubbles_evolve_as_one_bubble(orc):
+    """Merging two touching bubbles is the same as giving all their cells one id: two r = 4
+    bubbles at centre distance 8 rising under gravity against the same state with every cell of
+    bubble 1 relabelled 0 and bubble 0 given the whole gas volume.  The fields agree to the
+    rounding of the volume sums (summed per id, then per root, in the merged run)."""
+    wl = _side_by_side(15.0, g=(0.0, 0.0, -2e-4))
+    a = orc.Sim(wl)
+    b = orc.Sim(wl)
+    b.owner[b.owner == 1] = 0
+    b.bub[0, orc.B_V0] = b.bub[0, orc.B_V] = _gas_volume(orc, b)
+    b.bub[1, orc.B_V0] = 0.0
+    a.step(60)
+    b.step(60)
+    assert list(a.roots) == [0, 0]
+    assert (a.flag == b.flag).all()
+    assert np.abs(a.f - b.f).max() < 1e-12
+    assert np.abs(a.phi - b.phi).max() < 1e-12
+    assert abs(a.rho_gas[0] - b.rho_gas[0]) < 1e-13 and abs(a.rho_gas[1] - a.rho_gas[0]) == 0.0
+    # the moving interface did change the gas density
+    assert abs(a.rho_gas[0] - 1.0) > 1e-6
+
+
+def test_bubble_merging_during_the_run_conserves_the_gas_mass(orc):
+    """A large bubble rising into a small one: once their regions touch they are one bubble
+    (one root, one merge) whose gas mass is the sum of the two initial masses,
+    rho_g V = rho_g0 (V0_a + V0_b), V measured from the cell fields (isothermal ideal gas of
+    conserved mass, Sec. 2.2)."""
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.Workload(name="two_rising", nx=16, ny=16, nz=40, tau=0.7, g=(0, 0, -3e-4), sphere_mode=W.SPHERES_FIXED,
+                    bubbles=[W.Bubble((8.0, 8.0, 10.0), 5.0), W.Bubble((8.0, 8.0, 22.0), 3.0)])
+    o = orc.Sim(wl)
+    m0 = o.bub[:2, orc.B_V0].copy()   # rho_g0 = 1: the initial gas masses
+    merged_at = None
+    for k in range(1, 501):
+        o.step(1)
+        if merged_at is None and o.scal[orc.SC_NMERGE] > 0:
+            merged_at = k
+        if merged_at is None:
+            for b in range(2):   # separate: each keeps its own mass
+                assert abs(o.rho_gas[b] * _gas_volume(orc, o, [b]) - m0[b]) <= 1e-11 * m0[b]
+        elif k >= merged_at + 20:
+            break
+    assert merged_at is not None and list(o.roots) == [0, 0] and o.scal[orc.SC_NMERGE] == 1
+    V = _gas_volume(orc, o, [0, 1])
+    assert abs(o.rho_gas[0] * V - m0.sum()) <= 1e-11 * m0.sum()
+    assert o.rho_gas[0] == o.rho_gas[1] and o.volumes[0] == o.volumes[1]
+    assert int(o.scal[orc.SC_STATUS]) == 0
