@@ -75,6 +75,31 @@ __device__ __forceinline__ void sph_flush_direct(const Dev& d, const SphAcc& a) 
 }
 
 
+// one link of cell (x, y, z) into an obstacle cell of sphere P that is not the cell's first
+// sphere (a cell between two spheres): Eq. bbrule and the link's momentum exchange, summed
+// straight into P's accumulators.  Returns the bounce-back correction (f_q(x, t+1) is
+// fob + the correction).  Out of line: it is rare.
+__device__ __noinline__ float sph_link_other(const Dev& d, int q, uint32_t P, int x, int y, int z, float rho0, float fob) {
+    SphAcc a;
+    sph_begin(d, a, P, x, y, z);
+    const int c[3] = {cx(q), cy(q), cz(q)};
+    const float wq = q <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f);
+    const int w72q = q <= 6 ? 4 : 2;
+    // c_q . u_w at the link midpoint x - c_q/2 equals c_q . (u_P + w_P x r): c_q . (w x c_q) = 0
+    const float ucx = a.u[0] + a.w[1] * a.r[2] - a.w[2] * a.r[1];
+    const float ucy = a.u[1] + a.w[2] * a.r[0] - a.w[0] * a.r[2];
+    const float ucz = a.u[2] + a.w[0] * a.r[1] - a.w[1] * a.r[0];
+    const float corr = 6.f * wq * rho0 * (c[0] * ucx + c[1] * ucy + c[2] * ucz);
+    const float dev = 2.f * fob + corr;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        a.J[k] = -c[k] * dev;
+        a.K[k] = -w72q * c[k];
+    }
+    sph_flush_direct(d, a);
+    return corr;
+}
+
 // pull-stream and collide one BULK cell (x, y, z) = i: every neighbour carries PDFs or lies
 // beyond a wall (halfway bounce-back by index select), no neighbour tests
 template <int S>
@@ -246,6 +271,21 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
             const float u0sq = u0x * u0x + u0y * u0y + u0z * u0z;
             const float phix = isIF ? phia[i] : 0.f;
             const float kap = (isIF && d.kappa) ? d.kappa[i] : 0.f;
+            // the cell's sphere: the owner of its first obstacle link (links into a second
+            // sphere take sph_link_other); the wall velocity is needed only as c_q . u_w, and
+            // c_q . u_w at the link midpoint x - c_q/2 equals c_q . (u_P + w_P x r), r = x - x_P
+            // (c_q . (w_P x c_q) = 0): one cell-centre velocity serves every link
+            uint32_t P0 = kNone;
+#pragma unroll
+            for (int q = kQ - 1; q >= 1; q--)
+                if (fsv[q] != 0xffu && (fsv[q] & F_OBS)) P0 = __float_as_uint(fv[q]);
+            float ucx = 0.f, ucy = 0.f, ucz = 0.f;
+            if (P0 < (uint32_t)d.nsph) {
+                sph_begin(d, acc, P0, x, y, z);
+                ucx = acc.u[0] + acc.w[1] * acc.r[2] - acc.w[2] * acc.r[1];
+                ucy = acc.u[1] + acc.w[2] * acc.r[0] - acc.w[0] * acc.r[2];
+                ucz = acc.u[2] + acc.w[0] * acc.r[1] - acc.w[1] * acc.r[0];
+            }
             float fin[kQ];
             float dm = 0.f;
             fin[0] = fo[0];
@@ -263,23 +303,21 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                     }
                 } else if (t & F_OBS) {                                 // Eq. bbrule
                     const uint32_t P = __float_as_uint(fv[q]);
-                    if (P >= (uint32_t)d.nsph) { fin[q] = fo[qb]; continue; }
-                    if (P != acc.pid) {
-                        sph_flush_direct(d, acc);
-                        sph_begin(d, acc, P, x, y, z);
+                    if (P == P0) {
+                        const float corr = 6.f * wgt(q) * rho0 * (cx(q) * ucx + cy(q) * ucy + cz(q) * ucz);
+                        fin[q] = fo[qb] + corr;
+                        // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
+                        const float dev = 2.f * fo[qb] + corr;
+                        acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
+                        acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
+                        if (fl & F_LIQ) sbb += corr;
+                    } else if (P < (uint32_t)d.nsph) {
+                        const float corr = sph_link_other(d, q, P, x, y, z, rho0, fo[qb]);
+                        fin[q] = fo[qb] + corr;
+                        if (fl & F_LIQ) sbb += corr;
+                    } else {
+                        fin[q] = fo[qb];
                     }
-                    const float rx = acc.r[0] - 0.5f * cx(q), ry = acc.r[1] - 0.5f * cy(q), rz = acc.r[2] - 0.5f * cz(q);
-                    const float wx = acc.w[0], wy = acc.w[1], wz = acc.w[2];
-                    const float uwx = acc.u[0] + wy * rz - wz * ry;
-                    const float uwy = acc.u[1] + wz * rx - wx * rz;
-                    const float uwz = acc.u[2] + wx * ry - wy * rx;
-                    const float corr = 6.f * wgt(q) * rho0 * (cx(q) * uwx + cy(q) * uwy + cz(q) * uwz);
-                    fin[q] = fo[qb] + corr;
-                    // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
-                    const float dev = 2.f * fo[qb] + corr;
-                    acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
-                    acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
-                    if (fl & F_LIQ) sbb += corr;
                 } else {                                                // gas: Eq. fsk
                     const uint32_t bb = __float_as_uint(fv[q]);
                     const float rg = bb < (uint32_t)d.nbub ? d.bub[bb].rho_gf : d.rho_g0;
