@@ -55,6 +55,10 @@ extern "C" {
 /* per-axis boundary kind */
 #define LBM_BC_WALL 0        /* no-slip wall halfway beyond the outermost cells */
 #define LBM_BC_PERIODIC 1
+#define LBM_BC_FREESLIP 2    /* free-slip wall halfway beyond the outermost cells (specular
+                                reflection: a population leaving toward the wall comes back
+                                with its normal component reversed, one cell further along its
+                                tangential components; Fig. bubbleSetup's side walls) */
 
 /* PDF storage between steps (collisions always run in FP32) */
 #define LBM_STORE_F32 0      /* f stored as FP32 */
@@ -95,6 +99,17 @@ typedef struct lbm_params {
     double sigma;              /* surface tension (0: no curvature term) */
     double rho_gas0;           /* initial gas density of every bubble (1 = liquid reference) */
     double eps;                /* conversion band: fill >= 1+eps fills, fill <= -eps empties */
+    int32_t open_top;          /* 1: the +z face is an open boundary at the reference pressure
+                                  (Fig. bubbleSetup's top) instead of bc[2]'s wall: a link
+                                  from beyond it gets -f*_qb + 2 e+_q(1, u), u the cell's own
+                                  velocity (Eq. fsk with rho_w = 1); the mass it lets in or out
+                                  is reported by lbm_mass_budget.  bc[2] must not be periodic. */
+    int32_t hydrostatic;       /* 1 (with open_top): the liquid starts in hydrostatic equilibrium,
+                                  rho = exp(3 g[2] (z - z_top)) with rho = 1 on the open face's
+                                  plane z_top = nz - 1/2 (dp/dz = rho g[2], p = rho/3), and each
+                                  bubble's gas at the liquid's pressure at its centre plus the
+                                  Laplace jump 2 sigma / r (rho_gas0 is then unused); 0: rho = 1
+                                  and the gas at rho_gas0 */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -179,7 +194,8 @@ int lbm_fields(lbm_ctx* ctx, float* rho, float* u, float* phi, uint8_t* flags);
 int lbm_export_state(lbm_ctx* ctx, float* f, uint8_t* flags, float* mass, float* phi, int32_t* owner, float* kappa);
 
 /* Mass budget (host out[5], FP64): total liquid mass M = sum_liquid rho + sum_interface m +
- * pool, moving-bounce-back source S_bb, mass removed by covering S_cover, mass added by
+ * pool, boundary source S_bb (moving-wall bounce-back links and, with open_top, the open
+ * face's links), mass removed by covering S_cover, mass added by
  * refill S_uncover, undistributed excess pool.  M - M(0) - S_bb - S_uncover + S_cover is
  * the drift.  Synchronises. */
 int lbm_mass_budget(lbm_ctx* ctx, double out[5]);
@@ -189,8 +205,8 @@ int lbm_status(lbm_ctx* ctx, uint32_t* status);
 
 /* ---- differentiation over a window with frozen cell types ------------------------------
  * The window is liquid only (no bubbles), the spheres fixed (LBM_SPHERES_FIXED; their u and w
- * still act as surface velocities) and the PDFs stored in FP32, so no cell changes type; else
- * these calls return LBM_ESTATE.  States are post-collision PDFs as FP32 deviations
+ * still act as surface velocities), the faces no-slip or periodic and the PDFs stored in FP32,
+ * so no cell changes type; else these calls return LBM_ESTATE.  States are post-collision PDFs as FP32 deviations
  * f*_q - w_q, [19][N], device, in the D3Q19 order of lbm_export_state.  The objective is
  * J = sum over the window's steps t of jdir . (sum over spheres of the momentum-exchange
  * force F_P(t), Eqs. netforce and momentum_transfer). */

@@ -21,7 +21,8 @@ _lib = None
 # the oracle's cell-type codes and record layouts (fslbm_oracle.c)
 LIQ, IFACE, GAS, OBS = 1, 2, 4, 8
 S_X, S_U, S_W, S_R, S_RHO, S_F, S_T, S_FLUB, S_FP, S_TP, S_HASP, S_LEN = 0, 3, 6, 9, 10, 11, 14, 17, 20, 23, 26, 32
-B_C, B_R, B_V0, B_V, B_RHOG, B_ROOT, B_LEN = 0, 3, 4, 5, 6, 7, 8
+B_C, B_R, B_V0, B_V, B_RHOG, B_ROOT, B_MG, B_LEN = 0, 3, 4, 5, 6, 7, 8, 10
+FACE_WALL, FACE_SLIP, FACE_OPEN = 0, 1, 2
 SC_POOL, SC_NIF, SC_SBB, SC_SCOV, SC_SUNC, SC_STEPS, SC_STATUS, SC_NMERGE, SC_LEN = 0, 1, 2, 3, 4, 5, 6, 7, 16
 
 
@@ -41,7 +42,8 @@ class _Params(ctypes.Structure):
                 ("bc", ctypes.c_int32 * 3), ("n_substeps", ctypes.c_int32), ("sphere_mode", ctypes.c_int32),
                 ("nbub", ctypes.c_int32), ("nsph", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("g", ctypes.c_double * 3), ("sigma", ctypes.c_double),
-                ("rho_g0", ctypes.c_double), ("eps", ctypes.c_double), ("near_tol", ctypes.c_double)]
+                ("rho_g0", ctypes.c_double), ("eps", ctypes.c_double), ("near_tol", ctypes.c_double),
+                ("face", ctypes.c_int32 * 6), ("hydrostatic", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER
@@ -102,9 +104,13 @@ class Sim:
 
     def __init__(self, wl=None, *, nx=None, ny=None, nz=None, tau=0.6, g=(0, 0, 0), bc=(0, 0, 0), sigma=0.0,
                  rho_g0=1.0, eps=0.0, near_tol=1e-4, n_substeps=10, sphere_mode=1, bubbles=(), spheres=(),
-                 init=True):
+                 open_top=False, hydrostatic=False, init=True):
+        """bc per axis: 0 no-slip walls, 1 periodic, 2 free-slip walls; open_top: the +z face is
+        open at the reference pressure; hydrostatic (open top only): start in hydrostatic
+        equilibrium"""
         if wl is not None:
             nx, ny, nz, tau, g, bc = wl.nx, wl.ny, wl.nz, wl.tau, wl.g, wl.bc
+            open_top, hydrostatic = wl.open_top, wl.hydrostatic
             sigma, rho_g0, eps, n_substeps, sphere_mode = wl.sigma, wl.rho_g0, wl.eps, wl.n_substeps, wl.sphere_mode
             bubbles = [(b.c[0], b.c[1], b.c[2], b.r) for b in wl.bubbles]
             spheres = [(s.x[0], s.x[1], s.x[2], s.r, s.rho, *s.u, *s.w) for s in wl.spheres]
@@ -113,8 +119,17 @@ class Sim:
         p = _Params()
         p.nx, p.ny, p.nz = nx, ny, nz
         for k in range(3):
-            p.bc[k] = int(bc[k])
+            p.bc[k] = 1 if int(bc[k]) == 1 else 0
+            p.face[2 * k] = p.face[2 * k + 1] = FACE_SLIP if int(bc[k]) == 2 else FACE_WALL
             p.g[k] = float(g[k])
+        if open_top:
+            if int(bc[2]) == 1:
+                raise ValueError("an open top needs a non-periodic z axis")
+            p.face[5] = FACE_OPEN
+        if hydrostatic:
+            if not open_top:
+                raise ValueError("a hydrostatic start needs the open top as its reference")
+            p.hydrostatic = 1
         p.n_substeps, p.sphere_mode = int(n_substeps), int(sphere_mode)
         p.nbub, p.nsph = len(bubbles), len(spheres)
         p.tau, p.sigma, p.rho_g0, p.eps, p.near_tol = tau, sigma, rho_g0, eps, near_tol

@@ -62,7 +62,7 @@ enum { M_FILLED = 1, M_EMPTIED = 2, M_NEWIF = 4, M_FROMLIQ = 8, M_UNCOV = 16, M_
 enum { S_X = 0, S_U = 3, S_W = 6, S_R = 9, S_RHO = 10, S_F = 11, S_T = 14, S_FLUB = 17, S_FP = 20, S_TP = 23,
        S_HASP = 26, S_LEN = 32 };
 /* bubble record layout, doubles */
-enum { B_C = 0, B_R = 3, B_V0 = 4, B_V = 5, B_RHOG = 6, B_ROOT = 7, B_LEN = 8 };
+enum { B_C = 0, B_R = 3, B_V0 = 4, B_V = 5, B_RHOG = 6, B_ROOT = 7, B_MG = 8, B_LEN = 10 };
 /* scalar slots */
 enum { SC_POOL = 0, SC_NIF = 1, SC_SBB = 2, SC_SCOV = 3, SC_SUNC = 4, SC_STEPS = 5, SC_STATUS = 6, SC_NMERGE = 7, SC_LEN = 16 };
 /* status bits */
@@ -70,7 +70,7 @@ enum { ST_UNSTABLE = 1, ST_BUBBLE_GONE = 2 };
 
 typedef struct {
     int32_t nx, ny, nz;
-    int32_t bc[3];          /* 0: no-slip wall (halfway bounce-back), 1: periodic */
+    int32_t bc[3];          /* 1: periodic axis; else the faces' kinds below */
     int32_t n_substeps;     /* sphere sub-steps per LBM step (Sec. 2.3: up to 10) */
     int32_t sphere_mode;    /* 0: fixed, 1: free Newton-Euler, 2: prescribed constant velocity */
     int32_t nbub, nsph;
@@ -80,7 +80,14 @@ typedef struct {
     double rho_g0;          /* initial gas density of every bubble */
     double eps;             /* conversion band: fill >= 1+eps -> liquid, fill <= -eps -> gas */
     double near_tol;        /* band logged as "near a conversion threshold" */
+    int32_t face[6];        /* faces -x,+x,-y,+y,-z,+z of non-periodic axes: FACE_* */
+    int32_t hydrostatic;    /* 1 (open top only): start in hydrostatic equilibrium */
 } orc_params;
+
+/* face kinds (Fig. bubbleSetup): no-slip wall, free-slip wall, open at the reference pressure */
+enum { FACE_WALL = 0, FACE_SLIP = 1, FACE_OPEN = 2 };
+/* what lies beyond a face for a population pulled across it */
+enum { FL_WALL = 0, FL_OPEN = 1, FL_SLIP = 2 };
 
 typedef struct {
     double *f, *ft;         /* [19][N] post-collision PDFs; ft is scratch */
@@ -108,6 +115,33 @@ static long nbr(const orc_params *p, int x, int y, int z, int dx, int dy, int dz
     if (b < 0 || b >= p->ny) { if (!p->bc[1]) return -1; b = (b + p->ny) % p->ny; }
     if (c < 0 || c >= p->nz) { if (!p->bc[2]) return -1; c = (c + p->nz) % p->nz; }
     return (long)a + (long)p->nx * ((long)b + (long)p->ny * c);
+}
+
+/* The population that arrives at cell (x,y,z) in direction q comes from x - c_q; when that
+ * lies beyond faces of non-periodic axes: FL_WALL if one of them is a no-slip wall (halfway
+ * bounce-back), else FL_OPEN if one is open (the reference pressure), else FL_SLIP: free-slip
+ * faces reflect specularly, so the population left the cell *src -- x - c_q moved back across
+ * each free-slip face -- in the direction *qs, c_q with those faces' normal components reversed. */
+static int face_source(const orc_params *p, int x, int y, int z, int q, long *src, int *qs)
+{
+    const int c[3] = {CX[q], CY[q], CZ[q]}, L[3] = {p->nx, p->ny, p->nz};
+    int a[3] = {x - c[0], y - c[1], z - c[2]}, m[3] = {c[0], c[1], c[2]};
+    int wall = 0, open = 0;
+    for (int k = 0; k < 3; k++) {
+        if (a[k] >= 0 && a[k] < L[k]) continue;
+        if (p->bc[k]) { a[k] = (a[k] + L[k]) % L[k]; continue; }
+        const int f = p->face[2 * k + (a[k] >= L[k] ? 1 : 0)];
+        if (f == FACE_WALL) wall = 1;
+        else if (f == FACE_OPEN) open = 1;
+        else { a[k] += c[k]; m[k] = -c[k]; }
+    }
+    if (wall) return FL_WALL;
+    if (open) return FL_OPEN;
+    *src = (long)a[0] + (long)p->nx * ((long)a[1] + (long)p->ny * a[2]);
+    *qs = 0;
+    for (int r = 1; r < NQ; r++)
+        if (CX[r] == m[0] && CY[r] == m[1] && CZ[r] == m[2]) *qs = r;
+    return FL_SLIP;
 }
 
 /* d = a - b with the minimum-image convention on periodic axes */
@@ -149,7 +183,10 @@ static double equi_even(int q, double rho, const double u[3])
 /* density and velocity of a post-collision state: rho = sum f*, u = (sum c f* - rho g/2)/rho.
  * With the Guo force the collision adds rho*g to the first moment, so this u is the
  * velocity the collision used. */
-static void post_moments(const orc_params *p, const double *f, long N, long i, double *rho, double u[3])
+/* density and velocity of cell i's post-collision PDFs f; gw weights the body force the
+ * collision applied (the body force acts on the liquid mass: the fill level of an interface
+ * cell, 1 for a liquid cell), so the velocity the collision used is (sum c f - rho gw g/2)/rho */
+static void post_moments(const orc_params *p, const double *f, long N, long i, double gw, double *rho, double u[3])
 {
     double r = 0, j[3] = {0, 0, 0};
     for (int q = 0; q < NQ; q++) {
@@ -158,7 +195,13 @@ static void post_moments(const orc_params *p, const double *f, long N, long i, d
         j[0] += CX[q] * v; j[1] += CY[q] * v; j[2] += CZ[q] * v;
     }
     *rho = r;
-    for (int k = 0; k < 3; k++) u[k] = (j[k] - 0.5 * r * p->g[k]) / r;
+    for (int k = 0; k < 3; k++) u[k] = (j[k] - 0.5 * r * gw * p->g[k]) / r;
+}
+
+/* the force weight of cell i in its current state: its fill level if interface, else 1 */
+static double force_weight(const orc_state *s, long i)
+{
+    return (s->flag[i] & C_IF) ? s->phi[i] : 1.0;
 }
 
 static void cell_xyz(const orc_params *p, long i, int *x, int *y, int *z)
@@ -251,12 +294,12 @@ static void curvature(const orc_params *p, orc_state *s)
  * of the bubble it was created in; when the regions of two bubbles touch (a gas or interface
  * cell next to one of another bubble) they are one bubble from then on: the ids are joined,
  * the smaller id being the root of the merged bubble.  The merged bubble's gas mass is the sum
- * of the two (rho_g0 V0 each, so the reference volumes add), its volume the sum of its
- * members' volumes.  Splitting is not modelled.
+ * of the two, and so is its reference volume; its volume is the sum of its members' volumes.
+ * Splitting is not modelled.
  *
  * V = #gas cells + sum over the interface cells of (1 - phi) of all ids of the bubble;
- * isothermal ideal gas of conserved mass: rho_g = rho_g0 V0 / V.  Every id of a merged bubble
- * holds the merged bubble's V0, V and rho_g. */
+ * isothermal ideal gas of conserved mass m_g: rho_g = m_g / V, m_g = rho_g(0) V(0).  Every id
+ * of a merged bubble holds the merged bubble's V0, V and rho_g. */
 static int bubble_root(const orc_state *s, int b)
 {
     while ((int)s->bub[b * B_LEN + B_ROOT] != b) b = (int)s->bub[b * B_LEN + B_ROOT];
@@ -287,8 +330,11 @@ static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
         }
     }
     s->scal[SC_NIF] = (double)nif;
-    if (set_reference)
-        for (int b = 0; b < nb; b++) s->bub[b * B_LEN + B_V0] = own[b];
+    if (set_reference)   /* the initial gas density of each bubble is in B_RHOG */
+        for (int b = 0; b < nb; b++) {
+            s->bub[b * B_LEN + B_V0] = own[b];
+            s->bub[b * B_LEN + B_MG] = s->bub[b * B_LEN + B_RHOG] * own[b];
+        }
     for (int z = 0; z < p->nz; z++)
         for (int y = 0; y < p->ny; y++)
             for (int x = 0; x < p->nx; x++) {
@@ -305,6 +351,7 @@ static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
                     const int lo = ra < rb ? ra : rb, hi = ra < rb ? rb : ra;
                     s->bub[hi * B_LEN + B_ROOT] = (double)lo;
                     s->bub[lo * B_LEN + B_V0] += s->bub[hi * B_LEN + B_V0];
+                    s->bub[lo * B_LEN + B_MG] += s->bub[hi * B_LEN + B_MG];
                     s->scal[SC_NMERGE] += 1.0;
                 }
             }
@@ -313,11 +360,10 @@ static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
         double *B = s->bub + b * B_LEN;
         const int r = bubble_root(s, b);
         B[B_V0] = s->bub[r * B_LEN + B_V0];
+        B[B_MG] = s->bub[r * B_LEN + B_MG];
         B[B_V] = Vr[r];
-        if (set_reference) {
-            B[B_RHOG] = p->rho_g0;
-        } else if (Vr[r] > 0.0) {
-            B[B_RHOG] = p->rho_g0 * B[B_V0] / Vr[r];
+        if (Vr[r] > 0.0) {
+            B[B_RHOG] = B[B_MG] / Vr[r];
         } else {
             s->scal[SC_STATUS] = (double)((int)s->scal[SC_STATUS] | ST_BUBBLE_GONE);
         }
@@ -333,7 +379,6 @@ static void sweep(const orc_params *p, orc_state *s, double share)
     const long N = ncell(p);
     const double lp = -1.0 / p->tau;                                  /* lambda_+ */
     const double lm = 1.0 / ((3.0 / 16.0) / (1.0 / lp + 0.5) - 0.5);  /* lambda_- from Lambda = 3/16 */
-    const double *g = p->g;
     for (int z = 0; z < p->nz; z++)
         for (int y = 0; y < p->ny; y++)
             for (int x = 0; x < p->nx; x++) {
@@ -343,18 +388,27 @@ static void sweep(const orc_params *p, orc_state *s, double share)
                 double fo[NQ], fin[NQ];
                 for (int q = 0; q < NQ; q++) fo[q] = s->f[(long)q * N + i];
                 double rho0, u0[3];
-                post_moments(p, s->f, N, i, &rho0, u0);
+                post_moments(p, s->f, N, i, force_weight(s, i), &rho0, u0);
                 const double xc[3] = {(double)x, (double)y, (double)z};
 
                 for (int q = 0; q < NQ; q++) {
-                    const long src = nbr(p, x, y, z, -CX[q], -CY[q], -CZ[q]);
-                    if (src < 0) {                       /* wall: halfway bounce-back */
-                        fin[q] = fo[opp(q)];
-                        continue;
+                    long src = nbr(p, x, y, z, -CX[q], -CY[q], -CZ[q]);
+                    int qs = q;
+                    if (src < 0) {
+                        const int kind = face_source(p, x, y, z, q, &src, &qs);
+                        if (kind == FL_WALL) {           /* no-slip wall: halfway bounce-back */
+                            fin[q] = fo[opp(q)];
+                            continue;
+                        }
+                        if (kind == FL_OPEN) {           /* open face: Eq. fsk with rho_w = 1 */
+                            fin[q] = -fo[opp(q)] + 2.0 * equi_even(q, 1.0, u0);
+                            s->scal[SC_SBB] += fin[q] - fo[opp(q)];
+                            continue;
+                        }
                     }
                     const uint8_t ts = s->flag[src];
-                    if (ts & (C_LIQ | C_IF)) {           /* Eq. LBE1 */
-                        fin[q] = s->f[(long)q * N + src];
+                    if (ts & (C_LIQ | C_IF)) {           /* Eq. LBE1 (specular: direction qs) */
+                        fin[q] = s->f[(long)qs * N + src];
                     } else if (ts & C_OBS) {             /* Eq. bbrule at the link midpoint */
                         double *S = s->sph + (long)s->owner[src] * S_LEN;
                         const double cq[3] = {CX[q], CY[q], CZ[q]};
@@ -389,10 +443,18 @@ static void sweep(const orc_params *p, orc_state *s, double share)
                 if (t & C_IF) {                          /* Eqs. massExchange, massExchangeb */
                     double dm = 0.0;
                     for (int q = 1; q < NQ; q++) {
-                        const long nb = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
-                        if (nb < 0) continue;
+                        long nb = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+                        int qn = opp(q);   /* the direction the exchanged population arrives in */
+                        if (nb < 0) {
+                            const int kind = face_source(p, x, y, z, opp(q), &nb, &qn);
+                            if (kind == FL_WALL) continue;
+                            if (kind == FL_OPEN) {   /* what the open face lets in: as from a liquid cell */
+                                dm += fin[opp(q)] - fo[q];
+                                continue;
+                            }
+                        }
                         const uint8_t tn = s->flag[nb];
-                        const double ex = s->f[(long)opp(q) * N + nb] - fo[q];
+                        const double ex = s->f[(long)qn * N + nb] - fo[q];
                         if (tn & C_LIQ) dm += ex;
                         else if (tn & C_IF) dm += 0.5 * (s->phi[i] + s->phi[nb]) * ex;
                     }
@@ -405,6 +467,10 @@ static void sweep(const orc_params *p, orc_state *s, double share)
                     rho += fin[q];
                     j[0] += CX[q] * fin[q]; j[1] += CY[q] * fin[q]; j[2] += CZ[q] * fin[q];
                 }
+                /* the body force acts on the liquid mass: rho g, or phi rho g in an interface cell
+                 * (its fill level after this step's mass exchange) */
+                const double gw = (t & C_IF) ? mnew / rho : 1.0;
+                const double g[3] = {gw * p->g[0], gw * p->g[1], gw * p->g[2]};
                 double u[3];
                 for (int k = 0; k < 3; k++) u[k] = (j[k] + 0.5 * rho * g[k]) / rho;
                 const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -441,12 +507,21 @@ static void conversions(const orc_params *p, orc_state *s)
     double *F = s->ft;  /* f*(t+1) */
     memset(s->mark, 0, (size_t)N);
 
-    /* (i) interface cells past a threshold; log cells near one */
+    /* (i) interface cells past a threshold; log cells near one.  An interface cell is a
+     * boundary cell of the liquid with a gas neighbour (Sec. 2.2): one left without any gas
+     * neighbour is liquid now, whatever its fill level (filled, its mass m - rho the excess) */
     for (long i = 0; i < N; i++) {
         if (!(s->flag[i] & C_IF)) continue;
         const double ph = s->phi[i];
         if (fabs(ph - 1.0) <= p->near_tol || fabs(ph) <= p->near_tol) s->near[i]++;
-        if (ph >= 1.0 + p->eps) s->mark[i] = M_FILLED;
+        int x, y, z, gas = 0;
+        cell_xyz(p, i, &x, &y, &z);
+        for (int q = 1; q < NQ; q++) {
+            const long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+            if (j >= 0 && (s->flag[j] & C_GAS)) gas = 1;
+        }
+        if (!gas) s->mark[i] = M_FILLED;
+        else if (ph >= 1.0 + p->eps) s->mark[i] = M_FILLED;
         else if (ph <= -p->eps) s->mark[i] = M_EMPTIED;
     }
     /* (ii) filled cells: gas neighbours become interface, emptied neighbours stay interface */
@@ -471,7 +546,7 @@ static void conversions(const orc_params *p, orc_state *s)
             if (j < 0 || !(s->flag[j] & C_LIQ)) continue;
             if (!(s->mark[j] & M_FROMLIQ)) {
                 double r, u[3];
-                post_moments(p, F, N, j, &r, u);
+                post_moments(p, F, N, j, force_weight(s, j), &r, u);
                 s->mark[j] |= M_FROMLIQ;
                 s->m[j] = r;
                 s->owner[j] = s->owner[i];
@@ -492,7 +567,7 @@ static void conversions(const orc_params *p, orc_state *s)
             long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
             if (j < 0 || !(s->flag[j] & (C_LIQ | C_IF)) || (s->mark[j] & M_EMPTIED)) continue;
             double r, u[3];
-            post_moments(p, F, N, j, &r, u);
+            post_moments(p, F, N, j, force_weight(s, j), &r, u);
             rs += r;
             for (int k = 0; k < 3; k++) us[k] += u[k];
             n++;
@@ -516,7 +591,7 @@ static void conversions(const orc_params *p, orc_state *s)
         py_gradient(p, s, x, y, z, ng);
         for (int k = 0; k < 3; k++) ng[k] = -ng[k];
         double r, u[3];
-        post_moments(p, F, N, i, &r, u);
+        post_moments(p, F, N, i, force_weight(s, i), &r, u);
         double mex;
         if (mk & M_FILLED) { mex = s->m[i] - r; s->m[i] = r; }
         else { mex = s->m[i]; s->m[i] = 0.0; }
@@ -558,7 +633,7 @@ static void conversions(const orc_params *p, orc_state *s)
         const uint8_t mk = s->mark[i];
         if (!(mk & (M_NEWIF | M_FROMLIQ | M_RECV)) || !(s->flag[i] & C_IF)) continue;
         double r, u[3];
-        post_moments(p, F, N, i, &r, u);
+        post_moments(p, F, N, i, force_weight(s, i), &r, u);
         s->phi[i] = s->m[i] / r;
     }
 }
@@ -728,7 +803,7 @@ static void cover_uncover(const orc_params *p, orc_state *s)
         } else if (s->nown[i] >= 0) {
             if (s->flag[i] & C_LIQ) {
                 double r, u[3];
-                post_moments(p, s->f, N, i, &r, u);
+                post_moments(p, s->f, N, i, force_weight(s, i), &r, u);
                 s->scal[SC_SCOV] += r;
             } else if (s->flag[i] & C_IF) {
                 s->scal[SC_SCOV] += s->m[i];
@@ -753,7 +828,7 @@ static void cover_uncover(const orc_params *p, orc_state *s)
                 ngas++;
             } else {
                 double r, u[3];
-                post_moments(p, s->f, N, j, &r, u);
+                post_moments(p, s->f, N, j, force_weight(s, j), &r, u);
                 rs += r;
                 ps += (s->flag[j] & C_IF) ? s->phi[j] : 1.0;
                 nfl++;
@@ -798,6 +873,13 @@ static void cover_uncover(const orc_params *p, orc_state *s)
  * liquid cells with a gas neighbour become interface cells (phi = 1) to close the layer;
  * f* = e(1, 0), m = phi; cells with |x - x_P|^2 <= R^2 become obstacle cells of the lowest
  * such sphere id; then the bubble model sets V_b(0) and rho_g = rho_g0. */
+/* initial liquid density of layer z: 1, or (hydrostatic) the column's hydrostatic profile
+ * dp/dz = rho g_z with p = rho / 3 and rho = 1 on the open top's plane z = nz - 1/2 */
+static double rho_initial(const orc_params *p, int z)
+{
+    return p->hydrostatic ? exp(3.0 * p->g[2] * ((double)z - (p->nz - 0.5))) : 1.0;
+}
+
 int orc_init(const orc_params *p, orc_state *s)
 {
     const long N = ncell(p);
@@ -842,10 +924,17 @@ int orc_init(const orc_params *p, orc_state *s)
     for (long i = 0; i < N; i++) {
         if (s->mark[i]) { s->flag[i] = C_IF; s->phi[i] = 1.0; }
         if (s->flag[i] & C_LIQ) s->owner[i] = -1;
-        s->m[i] = s->phi[i];
+        const double rho = rho_initial(p, (int)(i / ((long)p->nx * p->ny)));
+        s->m[i] = s->phi[i] * rho;
         s->kappa[i] = 0.0;
         s->near[i] = 0;
-        for (int q = 0; q < NQ; q++) s->f[(long)q * N + i] = equi(q, 1.0, u0);
+        for (int q = 0; q < NQ; q++) s->f[(long)q * N + i] = equi(q, rho, u0);
+    }
+    /* the gas of each bubble at the pressure of the liquid around it: hydrostatic at its
+     * centre plus the Laplace jump 2 sigma / r (p = rho / 3) */
+    for (int b = 0; b < p->nbub; b++) {
+        double *B = s->bub + b * B_LEN;
+        B[B_RHOG] = p->hydrostatic ? exp(3.0 * p->g[2] * (B[B_C + 2] - (p->nz - 0.5))) + 6.0 * p->sigma / B[B_R] : p->rho_g0;
     }
     for (int a = 0; a < p->nsph; a++) {
         const double *S = s->sph + (long)a * S_LEN;
@@ -909,7 +998,7 @@ void orc_fields(const orc_params *p, const orc_state *s, double *rho, double *u)
     const long N = ncell(p);
     for (long i = 0; i < N; i++) {
         double r = 0, v[3] = {0, 0, 0};
-        if (s->flag[i] & (C_LIQ | C_IF)) post_moments(p, s->f, N, i, &r, v);
+        if (s->flag[i] & (C_LIQ | C_IF)) post_moments(p, s->f, N, i, force_weight(s, i), &r, v);
         rho[i] = r;
         for (int k = 0; k < 3; k++) u[(long)k * N + i] = v[k];
     }
@@ -924,7 +1013,7 @@ double orc_total_mass(const orc_params *p, const orc_state *s)
     for (long i = 0; i < N; i++) {
         if (s->flag[i] & C_LIQ) {
             double r, u[3];
-            post_moments(p, s->f, N, i, &r, u);
+            post_moments(p, s->f, N, i, force_weight(s, i), &r, u);
             M += r;
         } else if (s->flag[i] & C_IF) {
             M += s->m[i];

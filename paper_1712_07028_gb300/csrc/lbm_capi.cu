@@ -73,7 +73,9 @@ int check_params(const lbm_params* p) {
     if (p->nx < 3 || p->ny < 3 || p->nz < 3) return LBM_EINVAL;
     if ((double)p->nx * p->ny * p->nz > 4.0e9) return LBM_EINVAL;
     for (int k = 0; k < 3; k++)
-        if (p->bc[k] != LBM_BC_WALL && p->bc[k] != LBM_BC_PERIODIC) return LBM_EINVAL;
+        if (p->bc[k] != LBM_BC_WALL && p->bc[k] != LBM_BC_PERIODIC && p->bc[k] != LBM_BC_FREESLIP) return LBM_EINVAL;
+    if (p->open_top != 0 && (p->open_top != 1 || p->bc[2] == LBM_BC_PERIODIC)) return LBM_EINVAL;
+    if (p->hydrostatic != 0 && (p->hydrostatic != 1 || !p->open_top)) return LBM_EINVAL;
     if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16DEV) return LBM_EINVAL;
     if (p->n_substeps < 1 || p->n_substeps > 64) return LBM_EINVAL;
     if (p->sphere_mode < LBM_SPHERES_FIXED || p->sphere_mode > LBM_SPHERES_PRESCRIBED) return LBM_EINVAL;
@@ -262,7 +264,14 @@ int first_step(lbm_ctx* c) {
     Dev& d = c->d;
     std::memset(&d, 0, sizeof d);
     d.nx = p->nx; d.ny = p->ny; d.nz = p->nz;
-    for (int k = 0; k < 3; k++) d.bc[k] = p->bc[k];
+    for (int k = 0; k < 3; k++) {
+        d.bc[k] = p->bc[k] == LBM_BC_PERIODIC ? 1 : 0;
+        d.face[2 * k] = d.face[2 * k + 1] = p->bc[k] == LBM_BC_FREESLIP ? FACE_SLIP : FACE_WALL;
+    }
+    if (p->open_top) d.face[5] = FACE_OPEN;
+    d.hydrostatic = p->hydrostatic;
+    d.gz = p->g[2];
+    for (int k = 0; k < 6; k++) d.special |= d.face[k] != FACE_WALL && !d.bc[k / 2];
     d.N = L.N;
     d.storage = p->storage;
     d.n_sub = p->n_substeps;
@@ -623,10 +632,12 @@ int lbm_status(lbm_ctx* c, uint32_t* status) {
     return LBM_OK;
 }
 
-// the frozen liquid window the adjoint differentiates: FP32 storage, no bubbles, fixed spheres
+// the frozen liquid window the adjoint differentiates: FP32 storage, no bubbles, fixed spheres,
+// no-slip or periodic faces
 static int adjoint_ready(lbm_ctx* c) {
     if (!c->started) return LBM_ESTATE;
-    if (c->p.storage != LBM_STORE_F32 || c->d.nbub != 0 || c->p.sphere_mode != LBM_SPHERES_FIXED) return LBM_ESTATE;
+    if (c->p.storage != LBM_STORE_F32 || c->d.nbub != 0 || c->p.sphere_mode != LBM_SPHERES_FIXED || c->d.special)
+        return LBM_ESTATE;
     return flush(c);
 }
 

@@ -135,7 +135,7 @@ __device__ void conv_newif(const Dev& d, const int nxt, const uint32_t wid, cons
         size_t j;
         if (lane >= 1 && lane < kQ && nbr(d, x, y, z, cx(lane), cy(lane), cz(lane), j) &&
             (d.flags[j] & F_ACTIVE) && !(d.mark[j] & K_EMPTIED)) {
-            post_moments<S>(d, f, j, r, u);
+            post_moments<S>(d, f, j, (d.flags[j] & F_IF) ? d.phi[nxt][j] : 1.f, r, u);
             c = 1;
         }
         const int cnt = warp_sum(c);

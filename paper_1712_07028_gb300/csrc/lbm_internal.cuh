@@ -35,6 +35,8 @@ __host__ __device__ constexpr int w72(int q) { return q == 0 ? 24 : (q <= 6 ? 4 
 // liquid or interface (it then streams without looking at its neighbours)
 enum : uint8_t { F_LIQ = 1, F_IF = 2, F_GAS = 4, F_OBS = 8, F_BULK = 16, F_TYPE = 15 };
 enum : uint8_t { F_ACTIVE = F_LIQ | F_IF };
+// kinds of the faces of non-periodic axes
+enum : uint8_t { FACE_WALL = 0, FACE_SLIP = 1, FACE_OPEN = 2 };
 // conversion / covering marks (separate byte array, zero outside the conversion phase)
 enum : uint8_t { K_FILLED = 1, K_EMPTIED = 2, K_NEWIF = 4, K_FROMLIQ = 8, K_RECV = 16, K_TOUCH = 32, K_UNCOV = 64 };
 
@@ -119,8 +121,10 @@ struct Bubble {
     float rho_gf;                // FP32 copy of rho_g for the sweep
     int root;                    // root id (itself until the bubble merges)
     double Vtot[2];              // merged-volume sums at a root, alternating between step closes
+    double mg;                   // gas mass rho_g V (conserved; summed when bubbles merge)
+    double pad;
 };
-static_assert(sizeof(Bubble) == 64, "bubble record size");
+static_assert(sizeof(Bubble) == 80, "bubble record size");
 // distinct pairs of bubbles that may meet in one step (open-addressing table of pairs)
 constexpr int kMergeCap = 1024;
 struct Scalars {
@@ -153,7 +157,11 @@ enum : uint32_t { S_UNSTABLE = 1, S_OVERFLOW = 2, S_BUBBLE_GONE = 4, S_BIN_OVERF
 // all device pointers of one simulation; passed by value to every kernel
 struct Dev {
     int nx, ny, nz;
-    int bc[3];
+    int bc[3];                // 1: periodic axis
+    uint8_t face[6];          // faces -x, +x, -y, +y, -z, +z of non-periodic axes: FACE_*
+    int special;              // some face is free-slip or open
+    int hydrostatic;          // the liquid starts in hydrostatic equilibrium below the open top
+    double gz;                // g_z in FP64 (the hydrostatic start)
     size_t N;
     int storage;
     int n_sub;
@@ -217,12 +225,26 @@ __device__ __forceinline__ bool nbr(const Dev& d, int x, int y, int z, int dx, i
     return true;
 }
 
+// the cell (x, y, z) touches a free-slip or open face
+__device__ __forceinline__ bool at_special_face(const Dev& d, int x, int y, int z) {
+    if (!d.special) return false;
+    const int c[3] = {x, y, z}, L[3] = {d.nx, d.ny, d.nz};
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        if (d.bc[k]) continue;
+        if (c[k] == 0 && d.face[2 * k] != FACE_WALL) return true;
+        if (c[k] == L[k] - 1 && d.face[2 * k + 1] != FACE_WALL) return true;
+    }
+    return false;
+}
+
 // BULK: a liquid cell each of whose 18 neighbours is liquid or interface or lies beyond a
-// wall; the bulk sweep streams it without looking at its neighbours
+// no-slip wall; the bulk sweep streams it without looking at its neighbours
 __device__ __forceinline__ bool bulk_of(const Dev& d, size_t i) {
     if ((d.flags[i] & F_TYPE) != F_LIQ) return false;
     int x, y, z;
     cell_xyz(d, i, x, y, z);
+    if (at_special_face(d, x, y, z)) return false;
     uint32_t ok = F_ACTIVE;   // all 18 neighbour loads are independent
 #pragma unroll
     for (int q = 1; q < kQ; q++) {
@@ -380,8 +402,11 @@ __device__ __forceinline__ bool wl_push(uint32_t* list, uint32_t* count, uint32_
 
 // post-collision moments of cell i from grid f (deviations): rho = 1 + sum d*,
 // u = (sum c d* - rho g/2)/rho
+// density and velocity of cell i's post-collision PDFs; gw weights the body force the
+// collision applied (the cell's fill level for an interface cell, 1 for a liquid cell): the
+// velocity the collision used is (sum c f* - rho gw g / 2) / rho
 template <int S>
-__device__ __forceinline__ void post_moments(const Dev& d, const typename Store<S>::T* f, size_t i, float& rho, float u[3]) {
+__device__ __forceinline__ void post_moments(const Dev& d, const typename Store<S>::T* f, size_t i, float gw, float& rho, float u[3]) {
     float dr = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int q = 0; q < kQ; q++) {
@@ -391,9 +416,9 @@ __device__ __forceinline__ void post_moments(const Dev& d, const typename Store<
     }
     const float r = 1.f + dr;
     rho = r;
-    u[0] = (jx - 0.5f * r * d.g[0]) / r;
-    u[1] = (jy - 0.5f * r * d.g[1]) / r;
-    u[2] = (jz - 0.5f * r * d.g[2]) / r;
+    u[0] = (jx - 0.5f * r * gw * d.g[0]) / r;
+    u[1] = (jy - 0.5f * r * gw * d.g[1]) / r;
+    u[2] = (jz - 0.5f * r * gw * d.g[2]) / r;
 }
 
 // deviation of the equilibrium (Eq. equilibrium) from the weight: e_q(rho,u) - w_q
@@ -404,11 +429,13 @@ __device__ __forceinline__ float equilibrium_dev(int q, float rho, const float u
 }
 
 // moments, Guo-shifted velocity and the TRT collision of one cell, all on deviations f - w;
-// the post-collision deviations go to grid fb
+// the post-collision deviations go to grid fb.  The body force acts on the cell's liquid mass:
+// rho g in a liquid cell, gw = its fill level times that in an interface cell.
 template <int S, bool CS = false>
-__device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T* __restrict__ fb, size_t i, const float (&fin)[kQ]) {
+__device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T* __restrict__ fb, size_t i, const float (&fin)[kQ],
+                                              float gw = 1.f) {
     const size_t N = d.N;
-    const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
+    const float gx = gw * d.g[0], gy = gw * d.g[1], gz = gw * d.g[2];
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int q = 0; q < kQ; q++) {
@@ -532,7 +559,7 @@ __device__ __forceinline__ uint32_t covering_sphere(const Dev& d, int x, int y, 
 // moved spheres enter the bins of their new centres.  Run by every thread (t of nt) of the
 // step's last kernel, after its last barrier.
 // joins the recorded pairs of touching roots (one thread): the larger root joins the smaller
-// and passes on its reference volume (the gas mass over rho_g0: masses add); then every id
+// and passes on its reference volume and gas mass (they add); then every id
 // points at its root directly (roots are never larger than the ids below them, so one pass in
 // increasing id order suffices)
 __device__ inline void merge_apply(const Dev& d, const uint32_t n) {
@@ -547,6 +574,7 @@ __device__ inline void merge_apply(const Dev& d, const uint32_t n) {
         const int lo = min(ra, rb), hi = max(ra, rb);
         B[hi].root = lo;
         B[lo].V0 = __ldcg(&B[lo].V0) + __ldcg(&B[hi].V0);
+        B[lo].mg = __ldcg(&B[lo].mg) + __ldcg(&B[hi].mg);
         d.sc->n_merges++;
     }
     for (int b = 0; b < d.nbub; b++) B[b].root = B[B[b].root].root;
@@ -555,8 +583,9 @@ __device__ inline void merge_apply(const Dev& d, const uint32_t n) {
 }
 
 // the bubble model at the end of a step (Sec. 2.2): V of each bubble = its gas cells + the
-// interface part the sweep summed (both kept per id), rho_g = rho_g0 V0 / V; with init, V0 = V
-// and rho_g = rho_g0 instead.  Threads t of nt; sync() is a barrier over all of them.  Until
+// interface part the sweep summed (both kept per id), rho_g = m_g / V, the gas mass m_g
+// conserved (isothermal ideal gas); with init, V0 = V and m_g = rho_g V from the initial gas
+// density in rho_g.  Threads t of nt; sync() is a barrier over all of them.  Until
 // the first merge every id is its own bubble and no barrier is needed.
 template <class Sync>
 __device__ inline void bubbles_close(const Dev& d, const uint32_t t, const uint32_t nt, const bool init, Sync sync) {
@@ -569,8 +598,8 @@ __device__ inline void bubbles_close(const Dev& d, const uint32_t t, const uint3
             Bubble& B = d.bub[b];
             const double V = (double)(long long)__ldcg(&B.ngas) + __ldcg(&B.Vif);
             B.V = V;
-            if (init) { B.V0 = V; B.rho_g = (double)d.rho_g0; }
-            else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
+            if (init) { B.V0 = V; B.mg = B.rho_g * V; }
+            else if (V > 0.0) B.rho_g = B.mg / V;
             else atomicOr(&c.status, S_BUBBLE_GONE);
             B.rho_gf = (float)B.rho_g;
             B.Vif = 0.0;
@@ -582,7 +611,7 @@ __device__ inline void bubbles_close(const Dev& d, const uint32_t t, const uint3
         Bubble& B = d.bub[b];
         B.V = (double)(long long)__ldcg(&B.ngas) + __ldcg(&B.Vif);   // this id's part
         B.Vif = 0.0;
-        if (init) B.V0 = B.V;
+        if (init) { B.V0 = B.V; B.mg = B.rho_g * B.V; }
         B.Vtot[par ^ 1u] = 0.0;   // read by the last close; summed into by the next
     }
     sync();
@@ -597,8 +626,8 @@ __device__ inline void bubbles_close(const Dev& d, const uint32_t t, const uint3
         const double V = __ldcg(&R.Vtot[par]);
         B.V = V;
         B.V0 = __ldcg(&R.V0);
-        if (init) B.rho_g = (double)d.rho_g0;
-        else if (V > 0.0) B.rho_g = (double)d.rho_g0 * B.V0 / V;
+        B.mg = __ldcg(&R.mg);
+        if (V > 0.0) B.rho_g = B.mg / V;
         else atomicOr(&c.status, S_BUBBLE_GONE);
         B.rho_gf = (float)B.rho_g;
     }

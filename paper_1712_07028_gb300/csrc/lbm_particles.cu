@@ -563,8 +563,8 @@ __device__ inline void cover_refill_dev(const Dev& d, const int nxt, const uint3
                 myown = d.owner[j];
             } else if (t & F_ACTIVE) {
                 float u[3];
-                post_moments<S>(d, f, j, r, u);
                 ph = (t & F_IF) ? phi[j] : 1.f;
+                post_moments<S>(d, f, j, ph, r, u);
                 isfl = 1;
             }
         }

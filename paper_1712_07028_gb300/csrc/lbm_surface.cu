@@ -352,7 +352,14 @@ template <int S>
 __global__ void init_kernel(const Dev d, const double* geo) {
     using T = typename Store<S>::T;
     T* f = static_cast<T*>(d.f[0]);
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.nbub; b += gridDim.x * blockDim.x) d.bub[b].root = b;
+    // every bubble its own root; its initial gas density: rho_gas0, or (hydrostatic start) the
+    // liquid's pressure at its centre plus the Laplace jump 2 sigma / r, as a density (p = rho/3)
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.nbub; b += gridDim.x * blockDim.x) {
+        d.bub[b].root = b;
+        d.bub[b].rho_g = d.hydrostatic ? exp(3.0 * d.gz * (geo[4 * b + 2] - (d.nz - 0.5))) + 6.0 * (double)d.sigma / geo[4 * b + 3]
+                                       : (double)d.rho_g0;
+        d.bub[b].rho_gf = (float)d.bub[b].rho_g;
+    }
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
         cell_xyz(d, i, x, y, z);
@@ -373,7 +380,9 @@ __global__ void init_kernel(const Dev d, const double* geo) {
             }
         }
         if (t == F_LIQ) own = kNone;
-        float m = ph;
+        // initial density: 1, or the hydrostatic profile below the open top's plane nz - 1/2
+        const float rho = d.hydrostatic ? (float)exp(3.0 * d.gz * ((double)z - (d.nz - 0.5))) : 1.f;
+        float m = ph * rho;
         if (d.nsph > 0) {
             const uint32_t P = covering_sphere(d, x, y, z);
             if (P != kNone) { t = F_OBS; own = P; m = 0.f; ph = 1.f; }
@@ -384,7 +393,7 @@ __global__ void init_kernel(const Dev d, const double* geo) {
         d.phi[0][i] = ph;
         d.phi[1][i] = ph;
         if (d.kappa) d.kappa[i] = 0.f;
-        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, 0.f);   // e(1, 0) - w = 0
+        for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, wgt(q) * (rho - 1.f));   // e(rho, 0) - w
     }
 }
 
@@ -412,7 +421,7 @@ __global__ void fields_kernel(const Dev d, const int cur, float* rho, float* u, 
         const uint8_t t = d.flags[i] & F_TYPE;
         if (rho || u) {
             float r = 0.f, v[3] = {0.f, 0.f, 0.f};
-            if (t & F_ACTIVE) post_moments<S>(d, f, i, r, v);
+            if (t & F_ACTIVE) post_moments<S>(d, f, i, (t & F_IF) ? d.phi[cur][i] : 1.f, r, v);
             if (rho) rho[i] = r;
             if (u) { u[i] = v[0]; u[d.N + i] = v[1]; u[2 * d.N + i] = v[2]; }
         }

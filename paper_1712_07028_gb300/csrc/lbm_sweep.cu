@@ -100,6 +100,70 @@ __device__ __noinline__ float sph_link_other(const Dev& d, int q, uint32_t P, in
     return corr;
 }
 
+// a link of cell (x, y, z) whose source x - c_q lies beyond a face of a non-periodic axis,
+// not every crossed face being a no-slip wall (Fig. bubbleSetup):
+//   - an open face (the top): Eq. fsk with the reference pressure, f_q = -f*_qb + 2 e+_q(1, u),
+//     u the cell's own velocity; the mass let in, f_q - f*_qb, is a boundary source (and goes
+//     to an interface cell's mass);
+//   - free-slip faces only (and periodic axes): specular reflection, the population of the
+//     mirrored direction (normal components reversed) from the source moved back across each
+//     free-slip face, x' = x - c_q + (its normal components); x' is then an ordinary source:
+//     streaming with mass exchange, a sphere's moving wall, or a gas cell (Eq. fsk).
+// A no-slip face among those crossed gives halfway bounce-back.  Out of line: face cells are
+// few, and only free-slip or open faces get here.
+template <int S>
+__device__ __noinline__ float face_link(const Dev& d, const typename Store<S>::T* __restrict__ fa, const float* __restrict__ phia,
+                                        int q, int x, int y, int z, float fob, float rho0, float u0x, float u0y, float u0z,
+                                        float phix, float kap, bool isIF, bool liq, float& dm, float& sbb) {
+    const int c[3] = {cx(q), cy(q), cz(q)};
+    const int L[3] = {d.nx, d.ny, d.nz};
+    int s[3] = {x - c[0], y - c[1], z - c[2]};
+    int m[3] = {c[0], c[1], c[2]};   // velocity of the population that comes back as q
+    bool wall = false, open = false;
+    for (int k = 0; k < 3; k++) {
+        if (s[k] >= 0 && s[k] < L[k]) continue;
+        if (d.bc[k]) { s[k] += s[k] < 0 ? L[k] : -L[k]; continue; }
+        const uint8_t f = d.face[2 * k + (s[k] >= L[k] ? 1 : 0)];
+        if (f == FACE_WALL) wall = true;
+        else if (f == FACE_OPEN) open = true;
+        else { s[k] += c[k]; m[k] = -c[k]; }
+    }
+    if (wall) return fob;
+    const float u0sq = u0x * u0x + u0y * u0y + u0z * u0z;
+    const float cu = c[0] * u0x + c[1] * u0y + c[2] * u0z;
+    const float wq = wgt(q);
+    if (open) {
+        const float fi = 2.f * wq * (4.5f * cu * cu - 1.5f * u0sq) - fob;
+        if (isIF) dm += fi - fob;
+        sbb += fi - fob;
+        return fi;
+    }
+    const size_t j = cell_index(d, s[0], s[1], s[2]);
+    const uint8_t t = d.flags[j];
+    if (t & F_ACTIVE) {
+        int qm = q;
+        for (int p = 1; p < kQ; p++)
+            if (cx(p) == m[0] && cy(p) == m[1] && cz(p) == m[2]) qm = p;
+        const float fi = Store<S>::get(fa, (size_t)qm * d.N + j);
+        if (isIF) {
+            const float sw = (t & F_LIQ) ? 1.f : 0.5f * (phix + phia[j]);
+            dm += sw * (fi - fob);
+        }
+        return fi;
+    }
+    if (t & F_OBS) {
+        const uint32_t P = d.owner[j];
+        if (P >= (uint32_t)d.nsph) return fob;
+        const float corr = sph_link_other(d, q, P, x, y, z, rho0, fob);
+        if (liq) sbb += corr;
+        return fob + corr;
+    }
+    const uint32_t b = d.owner[j];
+    const float rg = b < (uint32_t)d.nbub ? d.bub[b].rho_gf : d.rho_g0;
+    const float rw = rg + 6.f * d.sigma * kap;
+    return 2.f * wq * ((rw - 1.f) + rw * (4.5f * cu * cu - 1.5f * u0sq)) - fob;
+}
+
 // pull-stream and collide one BULK cell (x, y, z) = i: every neighbour carries PDFs or lies
 // beyond a wall (halfway bounce-back by index select), no neighbour tests
 template <int S>
@@ -265,12 +329,15 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                 j0x += cx(q) * fo[q]; j0y += cy(q) * fo[q]; j0z += cz(q) * fo[q];
             }
             const float rho0 = 1.f + drho0;
-            const float u0x = (j0x - 0.5f * rho0 * gx) / rho0;
-            const float u0y = (j0y - 0.5f * rho0 * gy) / rho0;
-            const float u0z = (j0z - 0.5f * rho0 * gz) / rho0;
+            // the force the last collision applied: on the liquid mass, phi g in an interface cell
+            const float gw0 = isIF ? phia[i] : 1.f;
+            const float u0x = (j0x - 0.5f * rho0 * gw0 * gx) / rho0;
+            const float u0y = (j0y - 0.5f * rho0 * gw0 * gy) / rho0;
+            const float u0z = (j0z - 0.5f * rho0 * gw0 * gz) / rho0;
             const float u0sq = u0x * u0x + u0y * u0y + u0z * u0z;
             const float phix = isIF ? phia[i] : 0.f;
             const float kap = (isIF && d.kappa) ? d.kappa[i] : 0.f;
+            const bool atface = at_special_face(d, x, y, z);
             // the cell's sphere: the owner of its first obstacle link (links into a second
             // sphere take sph_link_other); the wall velocity is needed only as c_q . u_w, and
             // c_q . u_w at the link midpoint x - c_q/2 equals c_q . (u_P + w_P x r), r = x - x_P
@@ -294,7 +361,11 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                 const int qb = opp(q);
                 const uint32_t t = fsv[q];
                 if (t == 0xffu) {
-                    fin[q] = fo[qb];                                    // no-slip wall
+                    if (atface)
+                        fin[q] = face_link<S>(d, fa, phia, q, x, y, z, fo[qb], rho0, u0x, u0y, u0z, phix, kap, isIF,
+                                              (fl & F_LIQ) != 0, dm, sbb);
+                    else
+                        fin[q] = fo[qb];                                // no-slip wall
                 } else if (t & F_ACTIVE) {
                     fin[q] = fv[q];                                     // Eq. LBE1
                     if (isIF) {  // link to the neighbour x + c_qb: s (f*_q(x+c_qb) - f*_qb(x))
@@ -327,6 +398,7 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                     fin[q] = 2.f * wgt(q) * ((rw - 1.f) + rw * (4.5f * cu * cu - 1.5f * u0sq)) - fo[qb];
                 }
             }
+            float gw = 1.f;   // the body force acts on the liquid mass: phi g in an interface cell
             if (isIF) {
                 const float mnew = (d.mass[i] + d.sc->share_f) + dm;
                 float drho = 0.f;
@@ -337,18 +409,25 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                 phib[i] = mnew / rho;
                 vb = d.owner[i];
                 vphi = mnew / rho;
+                gw = vphi;
+                // an interface cell is a boundary cell of the liquid with a gas neighbour
+                // (Sec. 2.2): one left without any gas neighbour is liquid now (filled).
                 // phi >= 1 + eps  <=>  m - rho >= eps rho, taken as (m - 1) - drho so that a
                 // density deviation below FP32's resolution of 1 still decides it;
                 // phi <= -eps  <=>  m <= -eps rho
+                bool gasnb = false;
+#pragma unroll
+                for (int q = 1; q < kQ; q++) gasnb |= fsv[q] != 0xffu && (fsv[q] & F_GAS);
                 uint8_t mk = 0;
-                if ((mnew - 1.f) - drho >= d.eps * rho) mk = K_FILLED;
+                if (!gasnb) mk = K_FILLED;
+                else if ((mnew - 1.f) - drho >= d.eps * rho) mk = K_FILLED;
                 else if (mnew <= -d.eps * rho) mk = K_EMPTIED;
                 if (mk) {
                     d.mark[i] = mk;
                     wl_push(d.wl_conv, &d.sc->n_conv, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
                 }
             }
-            collide_store<S>(d, fb, i, fin);
+            collide_store<S>(d, fb, i, fin, gw);
         }
 
         // ---- per-warp partial sums: interface part of the bubble volumes (1 - phi, FP64),

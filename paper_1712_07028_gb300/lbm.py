@@ -32,7 +32,8 @@ class Params(ctypes.Structure):
                 ("storage", ctypes.c_int32), ("n_substeps", ctypes.c_int32), ("sphere_mode", ctypes.c_int32),
                 ("max_bubbles", ctypes.c_int32), ("max_spheres", ctypes.c_int32), ("worklist_cap", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("g", ctypes.c_double * 3), ("sigma", ctypes.c_double),
-                ("rho_gas0", ctypes.c_double), ("eps", ctypes.c_double)]
+                ("rho_gas0", ctypes.c_double), ("eps", ctypes.c_double), ("open_top", ctypes.c_int32),
+                ("hydrostatic", ctypes.c_int32)]
 
 
 class LBMError(RuntimeError):
@@ -110,6 +111,8 @@ def make_params(wl: _wl.Workload, max_bubbles=None, max_spheres=None, worklist_c
     p.max_spheres = int(max_spheres or max(1, len(wl.spheres)))
     p.worklist_cap = int(worklist_cap)
     p.tau, p.sigma, p.rho_gas0, p.eps = float(wl.tau), float(wl.sigma), float(wl.rho_g0), float(wl.eps)
+    p.open_top = 1 if wl.open_top else 0
+    p.hydrostatic = 1 if wl.hydrostatic else 0
     return p
 
 

@@ -39,7 +39,7 @@ class SplitMix64:
         return lo + (hi - lo) * self.uniform()
 
 
-WALL, PERIODIC = 0, 1
+WALL, PERIODIC, FREESLIP = 0, 1, 2
 STORAGE = {"f32": 0, "f16dev": 1, "bf16dev": 2}
 SPHERES_FIXED, SPHERES_FREE, SPHERES_PRESCRIBED = 0, 1, 2
 
@@ -68,6 +68,8 @@ class Workload:
     tau: float = 0.6
     g: Tuple[float, float, float] = (0.0, 0.0, 0.0)
     bc: Tuple[int, int, int] = (WALL, WALL, WALL)
+    open_top: bool = False      # the +z face an open boundary at the reference pressure
+    hydrostatic: bool = False   # (open top only) start in hydrostatic equilibrium
     sigma: float = 0.0
     rho_g0: float = 1.0
     eps: float = 0.0
@@ -219,3 +221,40 @@ def column_c4(storage="f16dev") -> Workload:
 def liquid_box(n=32, bc=(WALL, WALL, WALL), g=(0.0, 0.0, 0.0), tau=0.6, name=None) -> Workload:
     """an all-liquid box, the simplest case of the sweep"""
     return Workload(name=name or "liquid%d" % n, nx=n, ny=n, nz=n, tau=tau, g=g, bc=bc)
+
+
+# Sec. 3.2, Table 1: single rising bubbles in four shape regimes, parameterised by the liquid
+# viscosity mu [Pa s], surface tension sigma [N/m] and gravity g [m/s^2] for a liquid of
+# density 1000 kg/m^3, with dx = 1e-3 m and dt = 1e-4 s; the FSLBM's terminal Reynolds number
+# Re_b* in the 40 x 40 x 100 column (free-slip sides, no-slip bottom, open top), and the
+# figures' end times (steps)
+RISING_BUBBLE_CASES = {
+    "A": dict(mu=0.25, sigma=0.145, g=0.981, re_star=1.76, steps=20000, regime="spherical"),
+    "B": dict(mu=0.42, sigma=0.145, g=9.81, re_star=4.43, steps=5000, regime="ellipsoidal"),
+    "C": dict(mu=0.13211, sigma=0.014545, g=9.81, re_star=14.53, steps=4000, regime="skirted"),
+    "D": dict(mu=0.75, sigma=0.014545, g=9.81, re_star=1.46, steps=8000, regime="dimpled"),
+}
+RISING_DX, RISING_DT, RISING_RHO = 1e-3, 1e-4, 1000.0
+
+
+def rising_bubble_lattice(case: str):
+    """(tau, g, sigma) in lattice units of a Table 1 case: nu = mu/rho dt/dx^2 and
+    tau = 3 nu + 1/2 (Eq. latticeViscosity), g dt^2/dx, sigma/rho dt^2/dx^3"""
+    c = RISING_BUBBLE_CASES[case]
+    nu = c["mu"] / RISING_RHO * RISING_DT / RISING_DX ** 2
+    return 3.0 * nu + 0.5, c["g"] * RISING_DT ** 2 / RISING_DX, c["sigma"] / RISING_RHO * RISING_DT ** 2 / RISING_DX ** 3
+
+
+def rising_bubble(case: str, n=(40, 40, 100), r=6.0, zc=9.5, storage="f32") -> Workload:
+    """Sec. 3.2 / Fig. bubbleSetup: a spherical bubble of radius r = 6 dx centred at
+    (20, 20, 10) dx (cell centres at integer coordinates from 0: the point (19.5, 19.5, 9.5))
+    in a quiescent liquid column, free-slip sides, no-slip bottom, open top; gravity along -z.
+    The column starts in hydrostatic equilibrium and the gas at the pressure around it (at
+    rest, as the paper's quiescent liquid)"""
+    tau, g, sigma = rising_bubble_lattice(case)
+    nx, ny, nz = n
+    return Workload(name="rising_bubble_%s" % case, nx=nx, ny=ny, nz=nz, tau=tau, g=(0.0, 0.0, -g),
+                    bc=(FREESLIP, FREESLIP, WALL), open_top=True, hydrostatic=True, sigma=sigma,
+                    sphere_mode=SPHERES_FIXED,
+                    steps=RISING_BUBBLE_CASES[case]["steps"], storage=storage,
+                    bubbles=[Bubble((nx / 2 - 0.5, ny / 2 - 0.5, zc), r)])

@@ -5,7 +5,9 @@ post-collision f*_q(y) of an active cell y travels to y + c_q, and what happens 
 decides where it lands (Eq. LBE1; halfway bounce-back at walls; Eq. bbrule at sphere
 links; Eq. fsk where the target is gas).  Mass exchange (Eqs. massExchange/b) is taken
 per interface link.  The collision is the TRT operator of Eq. LBE2 written with explicit
-even/odd parts and the Guo force.  Cell conversions are not transcribed here.
+even/odd parts and the Guo force, which acts on the liquid mass (rho g in a liquid cell, phi rho g
+in an interface cell, phi its fill level after the mass exchange).  Cell conversions are not
+transcribed here.
 """
 import numpy as np
 
@@ -50,7 +52,8 @@ def sweep(p, f, flag, m, phi, owner, kappa, spheres, rho_gas):
     dm = np.zeros_like(m)
     act = (flag & (LIQ | IFACE)) != 0
     rho0 = f.sum(axis=0)
-    u0 = (np.einsum("qk,qzyx->kzyx", C, f) - 0.5 * rho0 * g[:, None, None, None]) / np.where(act, rho0, 1)
+    gw0 = np.where(flag & IFACE, phi, 1.0)   # the force the last collision applied
+    u0 = (np.einsum("qk,qzyx->kzyx", C, f) - 0.5 * rho0 * gw0 * g[:, None, None, None]) / np.where(act, rho0, 1)
     for z in range(nz):
         for y in range(ny):
             for x in range(nx):
@@ -103,14 +106,16 @@ def sweep(p, f, flag, m, phi, owner, kappa, spheres, rho_gas):
                     continue
                 fi = fin[:, z, y, x]
                 rho = fi.sum()
-                u = (C.T @ fi + 0.5 * rho * g) / rho
+                gc = g
+                if flag[z, y, x] & IFACE:
+                    m_new[z, y, x] = m[z, y, x] + dm[z, y, x]
+                    phi_new[z, y, x] = m_new[z, y, x] / rho
+                    gc = g * phi_new[z, y, x]
+                u = (C.T @ fi + 0.5 * rho * gc) / rho
                 e = WQ * rho * (1 + 3 * (C @ u) + 4.5 * (C @ u) ** 2 - 1.5 * (u @ u))
-                G = WQ * rho * ((3 * (C - u) + 9 * np.outer(C @ u, np.ones(3)) * C) @ g)
+                G = WQ * rho * ((3 * (C - u) + 9 * np.outer(C @ u, np.ones(3)) * C) @ gc)
                 fp, fm = 0.5 * (fi + fi[OPP]), 0.5 * (fi - fi[OPP])
                 ep, em = 0.5 * (e + e[OPP]), 0.5 * (e - e[OPP])
                 Gp, Gm = 0.5 * (G + G[OPP]), 0.5 * (G - G[OPP])
                 fout[:, z, y, x] = fi + lp * (fp - ep) + lm * (fm - em) + (1 + lp / 2) * Gp + (1 + lm / 2) * Gm
-                if flag[z, y, x] & IFACE:
-                    m_new[z, y, x] = m[z, y, x] + dm[z, y, x]
-                    phi_new[z, y, x] = m_new[z, y, x] / rho
     return fout, m_new, phi_new, F, T

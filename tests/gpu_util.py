@@ -40,6 +40,7 @@ def oracle_from_state(wl: W.Workload, st, near_tol=1e-5):
         o.bub[b, oracle.B_V] = st["V"][b]
         o.bub[b, oracle.B_RHOG] = st["rho_g"][b]
         o.bub[b, oracle.B_ROOT] = st["roots"][b]
+        o.bub[b, oracle.B_MG] = st["rho_g"][b] * st["V"][b]   # the conserved gas mass
     for a in range(len(wl.spheres)):
         o.sph[a, oracle.S_X:oracle.S_X + 3] = st["sx"][a]
         o.sph[a, oracle.S_U:oracle.S_U + 3] = st["su"][a]

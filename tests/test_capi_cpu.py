@@ -38,9 +38,10 @@ def test_library_exports_every_declared_symbol(built):
 
 def test_params_layout_matches_header(built):
     from paper_1712_07028_gb300 import lbm
-    # 12 int32 fields, then 7 doubles
-    assert ctypes.sizeof(lbm.Params) == 12 * 4 + 7 * 8
+    # 12 int32 fields, then 7 doubles, then open_top and hydrostatic
+    assert ctypes.sizeof(lbm.Params) == 12 * 4 + 7 * 8 + 2 * 4
     assert lbm.Params.tau.offset == 48
+    assert lbm.Params.open_top.offset == 104 and lbm.Params.hydrostatic.offset == 108
 
 
 def test_arena_size_and_argument_checks(built):
@@ -60,6 +61,23 @@ def test_arena_size_and_argument_checks(built):
         setattr(q, field, bad)
         assert L.lbm_arena_bytes(ctypes.byref(q), ctypes.byref(n)) == lbm.LBM_EINVAL, field
     assert L.lbm_strerror(-4) == b"density became non-positive or NaN"
+    # face kinds: free-slip accepted; an open top needs a non-periodic z axis; the hydrostatic
+    # start needs the open top
+    ok = lbm.make_params(W.rising_bubble("B"))
+    assert L.lbm_arena_bytes(ctypes.byref(ok), ctypes.byref(n)) == 0
+    for field, bad in (("bc", 3), ("open_top", 2), ("hydrostatic", 2)):
+        q = lbm.make_params(W.rising_bubble("B"))
+        if field == "bc":
+            q.bc[0] = bad
+        else:
+            setattr(q, field, bad)
+        assert L.lbm_arena_bytes(ctypes.byref(q), ctypes.byref(n)) == lbm.LBM_EINVAL, field
+    q = lbm.make_params(W.rising_bubble("B"))
+    q.bc[2] = 1
+    assert L.lbm_arena_bytes(ctypes.byref(q), ctypes.byref(n)) == lbm.LBM_EINVAL
+    q = lbm.make_params(W.rising_bubble("B"))
+    q.open_top = 0
+    assert L.lbm_arena_bytes(ctypes.byref(q), ctypes.byref(n)) == lbm.LBM_EINVAL
 
 
 def test_sim_refuses_without_gpu(built):

@@ -433,7 +433,7 @@ def test_bubble_merging_during_the_run_conserves_the_gas_mass(orc):
     o = orc.Sim(wl)
     m0 = o.bub[:2, orc.B_V0].copy()   # rho_g0 = 1: the initial gas masses
     merged_at = None
-    for k in range(1, 501):
+    for k in range(1, 801):
         o.step(1)
         if merged_at is None and o.scal[orc.SC_NMERGE] > 0:
             merged_at = k
@@ -447,3 +447,135 @@ def test_bubble_merging_during_the_run_conserves_the_gas_mass(orc):
     assert abs(o.rho_gas[0] * V - m0.sum()) <= 1e-11 * m0.sum()
     assert o.rho_gas[0] == o.rho_gas[1] and o.volumes[0] == o.volumes[1]
     assert int(o.scal[orc.SC_STATUS]) == 0
+
+
+# ------------------------------------------- free-slip and open faces: Fig. bubbleSetup
+
+def _eq_field(orc, rho, u):
+    """equilibrium PDFs [19][z][y][x] of density rho[z][y][x] and velocity u[3][z][y][x]"""
+    c = orc.velocities().astype(float)
+    w = np.array([orc.equilibrium(q, 1.0, [0, 0, 0]) for q in range(19)])
+    cu = np.einsum("qa,azyx->qzyx", c, u)
+    uu = (u * u).sum(axis=0)
+    return w[:, None, None, None] * rho[None] * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * uu[None])
+
+
+def _liquid_state(orc, o, f):
+    o.f[:] = f
+    o.flag[:] = orc.LIQ
+    o.phi[:] = 1.0
+    o.m[:] = f.sum(axis=0)
+
+
+def test_free_slip_plug_flow(orc):
+    """Free-slip walls exert no tangential stress: a body force along a channel between
+    free-slip walls (x and y faces, z periodic) accelerates the liquid as a plug: after t steps
+    the post-collision momentum is t rho g and the reported velocity (its Guo half-step shift
+    removed) u = g (t - 1/2) everywhere, where no-slip
+    walls would shear it into a Poiseuille profile."""
+    g, n = 1e-5, 300
+    s = orc.Sim(nx=6, ny=5, nz=4, tau=0.7, g=(0, 0, g), bc=(2, 2, 1))
+    s.step(n)
+    _, u = s.fields()
+    assert np.abs(u[2] - g * (n - 0.5)).max() < 1e-10 * g * n
+    assert np.abs(u[:2]).max() < 1e-16
+    w = orc.Sim(nx=6, ny=5, nz=4, tau=0.7, g=(0, 0, g), bc=(0, 0, 1))
+    w.step(n)
+    assert np.abs(w.fields()[1][2] - g * (n - 0.5)).max() > 0.1 * g * n
+
+
+def test_free_slip_wall_mirrors(orc):
+    """A free-slip wall reflects specularly: a population leaving toward it returns with its
+    normal velocity reversed, shifted along the wall by its tangential velocity.  A shear wave
+    u_y = A sin(2 pi z / L) parallel to free-slip x faces is then the same state as in a box
+    periodic in x (the mirror image of an x-independent field with u_x = 0 is the field
+    itself), step for step; a wall that returned the population to the cell it left (no
+    tangential shift) would not be."""
+    nx, ny, nz, A = 5, 3, 16, 0.01
+    z = np.arange(nz)
+    u = np.zeros((3, nz, ny, nx))
+    u[1] = A * np.sin(2 * np.pi * z / nz)[:, None, None]
+    f = _eq_field(orc, np.ones((nz, ny, nx)), u)
+    a = orc.Sim(nx=nx, ny=ny, nz=nz, tau=0.8, bc=(2, 1, 1), init=False)
+    b = orc.Sim(nx=nx, ny=ny, nz=nz, tau=0.8, bc=(1, 1, 1), init=False)
+    _liquid_state(orc, a, f)
+    _liquid_state(orc, b, f)
+    a.step(200)
+    b.step(200)
+    assert np.abs(a.f - b.f).max() < 1e-15
+    # the wave decays at the viscous rate exp(-nu k^2 t), nu = (tau - 1/2)/3
+    _, ub = b.fields()
+    decay = np.abs(ub[1]).max() / A
+    assert abs(decay - np.exp(-0.1 * (2 * np.pi / nz) ** 2 * 200.5)) < 2e-3
+
+
+def test_open_top_hydrostatic_column(orc):
+    """An open top at the reference pressure (Fig. bubbleSetup; Eq. fsk with rho_w = 1 at the
+    halfway plane above the last cells) holds a liquid column under gravity in hydrostatic
+    equilibrium, dp/dz = -rho g with p = rho/3: rho(z) = exp(3 g (z_top - z)), z_top = nz - 1/2,
+    here to 1e-4 of the column's pressure difference.  The mass the open face lets in is the
+    boundary term of the budget: M(t) - M(0) - S_bb = 0 to round-off."""
+    g, nz = 1e-4, 24
+    o = orc.Sim(nx=3, ny=3, nz=nz, tau=1.5, g=(0, 0, -g), bc=(1, 1, 0), open_top=True)
+    M0 = o.mass_budget()[0]
+    o.step(12000)
+    rho, u = o.fields()
+    z = np.arange(nz)
+    assert np.abs(u).max() < 1e-9
+    assert np.abs(rho - np.exp(3 * g * (nz - 0.5 - z))[:, None, None]).max() < 1e-4 * 3 * g * nz
+    M, sbb = o.mass_budget()[:2]
+    assert sbb > 0.5 * 3 * g * nz / 2 * o.N   # the column took in the mass of its compression
+    assert abs(M - M0 - sbb) < 1e-12 * M
+
+
+def test_rising_bubble_budgets(orc):
+    """A small rising bubble between free-slip sides under an open top (Fig. bubbleSetup, case B
+    parameters of Table 1): the liquid mass budget closes to round-off with the open face's
+    flux, the bubble keeps its gas mass (rho_g V constant) and it rises."""
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.rising_bubble("B", n=(16, 16, 32), r=4.0, zc=8.5)
+    o = orc.Sim(wl)
+    M0 = o.mass_budget()[0]
+    mg = o.rho_gas[0] * o.volumes[0]   # the gas mass at the start
+
+    def zc():
+        gas = np.where(o.flag == orc.GAS, 1.0, np.where(o.flag == orc.IFACE, 1.0 - o.phi, 0.0))
+        return (gas.sum(axis=(1, 2)) * np.arange(o.shape[0])).sum() / gas.sum()
+
+    z0 = zc()
+    o.step(150)
+    M, sbb, scov, sunc, pool = o.mass_budget()
+    assert abs(M - M0 - sbb - sunc + scov) < 1e-12 * M
+    assert abs(o.rho_gas[0] * o.volumes[0] - mg) < 1e-11 * mg
+    assert zc() > z0 + 0.1
+    assert int(o.scal[orc.SC_STATUS]) == 0
+
+
+def test_hydrostatic_start_is_at_rest(orc):
+    """The rising-bubble column starts in hydrostatic equilibrium, rho = exp(3 g_z (z - z_top))
+    with rho = 1 on the open top's plane (dp/dz = rho g_z, p = rho / 3), and the gas at the
+    pressure of the liquid around it: hydrostatic at the bubble's centre plus the Laplace jump
+    2 sigma / r.  A column started so stays at rest: its reported velocity stays at the -g/2
+    of the initial post-collision state e(rho, 0) (Guo's half-step shift), where a uniform
+    start sets the column oscillating (a quarter-wave between the bottom and the open top)."""
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.rising_bubble("B", n=(16, 16, 32), r=4.0, zc=8.5)
+    o = orc.Sim(wl)
+    g = wl.g[2]
+    z = np.arange(wl.nz)
+    rho, _ = o.fields()
+    liq = o.flag == orc.LIQ
+    prof = np.exp(3 * g * (z - (wl.nz - 0.5)))[:, None, None] * np.ones(o.shape)
+    assert np.abs(rho - prof)[liq].max() < 1e-15
+    assert abs(o.rho_gas[0] - (np.exp(3 * g * (8.5 - (wl.nz - 0.5))) + 6 * wl.sigma / 4.0)) < 1e-15
+    gg = 1e-4
+    for hydro, bound in ((True, 0.51 * gg), (False, None)):
+        c = orc.Sim(nx=3, ny=3, nz=24, tau=0.8, g=(0, 0, -gg), bc=(1, 1, 0), open_top=True, hydrostatic=hydro)
+        umax = 0.0
+        for _ in range(10):
+            c.step(50)
+            umax = max(umax, np.abs(c.fields()[1]).max())
+        if hydro:
+            assert umax < bound
+        else:
+            assert umax > 10 * gg
