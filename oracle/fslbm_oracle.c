@@ -374,6 +374,31 @@ static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
 
 /* ------------------------------------------------------------------ step 1: the sweep */
 
+/* The gas presses on the part of a sphere's surface it touches (the links of the sweep come
+ * from liquid and interface cells only, and the uniform part of their momentum exchange, the
+ * reference pressure, cancels only over a closed surface): a gas cell y beside an obstacle cell
+ * of sphere a (y - c_q covered by a) transfers the momentum of the gas at rest into a, as a
+ * link from y would: dj = -2 w_q rho_g c_q, rho_g of y's bubble (p = rho / 3), arm y - x_a. */
+static void gas_on_spheres(const orc_params *p, orc_state *s, int x, int y, int z, long i)
+{
+    const int b = s->owner[i];
+    const double rg = (b >= 0 && b < p->nbub) ? s->bub[(long)b * B_LEN + B_RHOG] : p->rho_g0;
+    const double xc[3] = {(double)x, (double)y, (double)z};
+    for (int q = 1; q < NQ; q++) {
+        const long src = nbr(p, x, y, z, -CX[q], -CY[q], -CZ[q]);
+        if (src < 0 || !(s->flag[src] & C_OBS)) continue;
+        double *S = s->sph + (long)s->owner[src] * S_LEN;
+        const double a = 2.0 * wq(q) * rg;
+        double dj[3] = {-a * CX[q], -a * CY[q], -a * CZ[q]}, r[3], rxj[3];
+        mindiff(p, xc, S + S_X, r);
+        cross(r, dj, rxj);
+        for (int k = 0; k < 3; k++) {
+            S[S_F + k] += dj[k];
+            S[S_T + k] += rxj[k];
+        }
+    }
+}
+
 static void sweep(const orc_params *p, orc_state *s, double share)
 {
     const long N = ncell(p);
@@ -384,6 +409,7 @@ static void sweep(const orc_params *p, orc_state *s, double share)
             for (int x = 0; x < p->nx; x++) {
                 const long i = (long)x + (long)p->nx * ((long)y + (long)p->ny * z);
                 const uint8_t t = s->flag[i];
+                if ((t & C_GAS) && p->nsph > 0) gas_on_spheres(p, s, x, y, z, i);
                 if (!(t & (C_LIQ | C_IF))) continue;
                 double fo[NQ], fin[NQ];
                 for (int q = 0; q < NQ; q++) fo[q] = s->f[(long)q * N + i];

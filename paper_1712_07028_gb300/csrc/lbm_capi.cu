@@ -88,7 +88,7 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, tmark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
+    size_t f[2], flags, mark, tmark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
         adj_srho, adj_part, merge_keys, merge_list, total;
     size_t N, wl_cap, nbins_max;
 };
@@ -115,6 +115,7 @@ Layout layout_of(const lbm_params* p) {
     L.sph = take(sizeof(Sphere) * (size_t)p->max_spheres);
     L.sph_tmp = take(sizeof(Sphere) * (size_t)p->max_spheres);
     L.sphl = take(sizeof(SphLink) * (size_t)p->max_spheres);
+    L.gasflag = take(sizeof(uint32_t) * 2 * (size_t)p->max_spheres);
     L.acc = take(sizeof(SphereAcc) * (size_t)p->max_spheres);
     L.sc = take(sizeof(Scalars));
     for (int k = 0; k < 4; k++) L.wl[k] = take(4 * L.wl_cap);
@@ -189,7 +190,7 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
     if (d.nsph > 0) {
         cudaEventRecord(c->fork2, e);
         cudaStreamWaitEvent(c->links, c->fork2, 0);
-        launch_spheres_links(d, c->links);
+        launch_spheres_links(d, g, c->links);
         cudaEventRecord(c->join2, c->links);
         c->links_state = kLinksForked;
     }
@@ -228,7 +229,7 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed =
     if (d.nsph > 0 && c->links_state == kLinksNone) {   // the first step: nothing forked them
         cudaEventRecord(c->fork2, s);
         cudaStreamWaitEvent(c->links, c->fork2, 0);
-        launch_spheres_links(d, c->links);
+        launch_spheres_links(d, cur, c->links);
         cudaEventRecord(c->join2, c->links);
         c->links_state = kLinksForked;
     }
@@ -302,6 +303,7 @@ int first_step(lbm_ctx* c) {
     d.bub = (Bubble*)(a + L.bub);
     d.sph = (Sphere*)(a + L.sph);
     d.sph_tmp = (Sphere*)(a + L.sph_tmp);
+    d.gasflag = (uint32_t*)(a + L.gasflag);
     d.sphl = (SphLink*)(a + L.sphl);
     d.acc = (SphereAcc*)(a + L.acc);
     d.sc = (Scalars*)(a + L.sc);

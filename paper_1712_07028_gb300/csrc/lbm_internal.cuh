@@ -187,6 +187,7 @@ struct Dev {
     Sphere* sph;              // [max_sph]
     Sphere* sph_tmp;          // [max_sph] sub-step double buffer
     SphLink* sphl;            // [max_sph] FP32 link data of the current sphere state
+    uint32_t* gasflag;        // [2][max_sph] spheres the gas-pressure pass scans, by grid parity
     SphereAcc* acc;           // [max_sph]
     Scalars* sc;
     uint32_t* wl_conv;        // worklists [wl_cap]
@@ -668,7 +669,7 @@ void launch_conversions(const Dev& d, int nxt, bool close, cudaStream_t s);
 void launch_init_scan(const Dev& d, cudaStream_t s);
 void launch_list_rescan(const Dev& d, cudaStream_t s);
 void launch_curvature(const Dev& d, int nxt, cudaStream_t s);
-void launch_spheres_links(const Dev& d, cudaStream_t s);
+void launch_spheres_links(const Dev& d, int g, cudaStream_t s);
 void launch_spheres_move(const Dev& d, cudaStream_t s);
 void launch_spheres_cover(const Dev& d, int nxt, cudaStream_t s);
 void prepare_sphere_kernels();

@@ -14,6 +14,7 @@ __global__ void bins_insert_kernel(const Dev d) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= d.nsph) return;
     const Sphere& s = d.sph[P];
+    d.gasflag[P] = d.gasflag[d.max_sph + P] = 1u;   // the first gas-pressure pass scans every sphere
     const size_t bi = bin_index(d, bin_coord(d, 0, s.x0[0]), bin_coord(d, 1, s.x0[1]), bin_coord(d, 2, s.x0[2]));
     const uint32_t slot = atomicAdd(&d.bin_cnt[bi], 1u);
     if (slot < (uint32_t)d.bin_cap) d.bin_ids[bi * d.bin_cap + slot] = (uint32_t)P;
@@ -172,6 +173,81 @@ __device__ inline void sph_contact_one(const Dev& d, const int P, const int t, c
 
 __global__ void sph_contact_kernel(const Dev d) {
     if (blockIdx.x < (unsigned)d.nsph) sph_contact_one(d, blockIdx.x, threadIdx.x, blockDim.x);
+}
+
+// The gas's pressure on the sphere surface the gas touches.  The sweep's links come from
+// liquid and interface cells only, and the uniform part of their momentum exchange
+// (-2 w_q c_q per link, the reference pressure) cancels over a closed surface; where the gas
+// covers part of the surface that part would be missing and the rest of the reference pressure
+// would push the sphere.  Every gas cell y beside an obstacle cell o of sphere P (y = o + c_q)
+// therefore transfers the momentum of the gas at rest, dj = -2 w_q rho_g c_q into P (rho_g of
+// y's bubble, p = rho/3), with the arm y - x_P, as a link from y would.
+// Only spheres flagged in flags_in are scanned: those with an interface cell beside them in the
+// last sweep (set by the boundary kernel) or gas beside them in the last pass (set here), since
+// a cell next to a sphere turns gas only from an interface cell and a sphere covers cells next
+// to its surface; the pass clears the flags it read.  One block per sphere.
+__global__ void sph_gas_kernel(const Dev d, const int g) {
+    const int P = blockIdx.x;
+    if (P >= d.nsph) return;
+    uint32_t* flags_in = d.gasflag + (size_t)(g ^ 1) * d.max_sph;
+    uint32_t* flags_out = d.gasflag + (size_t)g * d.max_sph;
+    __shared__ int found;
+    const bool scan = flags_in[P] != 0u;
+    if (threadIdx.x == 0) found = 0;
+    __syncthreads();   // every thread has read the flag before it is cleared
+    if (!scan) return;
+    const Sphere& s = d.sph[P];
+    if (!finite3(s.x) || !(s.R > 0.0 && s.R < 64.0)) return;
+    const int L[3] = {d.nx, d.ny, d.nz};
+    int lo[3], ext[3];
+    for (int k = 0; k < 3; k++) {
+        lo[k] = (int)floor(s.x[k] - s.R) - 1;
+        ext[k] = (int)ceil(s.x[k] + s.R) + 1 - lo[k] + 1;
+    }
+    double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
+    const int total = ext[0] * ext[1] * ext[2];
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        int w[3] = {lo[0] + e % ext[0], lo[1] + (e / ext[0]) % ext[1], lo[2] + e / (ext[0] * ext[1])};
+        bool ok = true;
+        for (int k = 0; k < 3; k++) {
+            if (w[k] < 0 || w[k] >= L[k]) {
+                if (!d.bc[k]) { ok = false; break; }
+                w[k] = ((w[k] % L[k]) + L[k]) % L[k];
+            }
+        }
+        if (!ok) continue;
+        const size_t oi = cell_index(d, w[0], w[1], w[2]);
+        if (!(d.flags[oi] & F_OBS) || d.owner[oi] != (uint32_t)P) continue;
+        for (int q = 1; q < kQ; q++) {
+            size_t yi;
+            if (!nbr(d, w[0], w[1], w[2], cx(q), cy(q), cz(q), yi)) continue;
+            if (!(d.flags[yi] & F_GAS)) continue;
+            found = 1;
+            const uint32_t b = d.owner[yi];
+            const double rg = b < (uint32_t)d.nbub ? d.bub[b].rho_g : (double)d.rho_g0;
+            const double a = 2.0 * (double)w72(q) / 72.0 * rg;
+            const double dj[3] = {-a * cx(q), -a * cy(q), -a * cz(q)};
+            int y[3];
+            cell_xyz(d, yi, y[0], y[1], y[2]);
+            double r[3];
+            for (int k = 0; k < 3; k++) r[k] = min_image(d, k, (double)y[k], s.x[k]);
+            F[0] += dj[0]; F[1] += dj[1]; F[2] += dj[2];
+            T[0] += r[1] * dj[2] - r[2] * dj[1];
+            T[1] += r[2] * dj[0] - r[0] * dj[2];
+            T[2] += r[0] * dj[1] - r[1] * dj[0];
+        }
+    }
+    double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
+    for (int c = 0; c < 6; c++) v[c] = warp_sum(v[c]);
+    SphereAcc& acc = d.acc[P];
+    if ((threadIdx.x & 31) == 0)
+        for (int c = 0; c < 6; c++)
+            if (v[c] != 0.0) atomicAdd(c < 3 ? &acc.C[c] : &acc.TC[c - 3], v[c]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        flags_in[P] = 0u;
+        if (found) flags_out[P] = 1u;
+    }
 }
 
 // partners of sphere P this step: centre distance below R_P + R_Q + 2, which covers the
@@ -664,7 +740,7 @@ __global__ void __cluster_dims__(kCoverCtas, 1, 1) __launch_bounds__(kCoverThrea
     step_close(d, t, nt, true, ClusterSync{});
 }
 
-int spheres_links_launches(const Dev& d) { return d.nsph == 0 ? 0 : 2; }
+int spheres_links_launches(const Dev& d) { return d.nsph == 0 ? 0 : 3; }
 
 int spheres_launches(const Dev& d) {   // launch_spheres_move + launch_spheres_cover
     if (d.nsph == 0) return 0;
@@ -692,10 +768,11 @@ void launch_cover_touch(const Dev& d, cudaStream_t st) {
 // partner lists and the links between obstacle nodes of two spheres: they read only the
 // step-start centres (binned), the sphere table and obstacle cells, so they run while the
 // sweep's boundary kernel does (their sums wait in the accumulators for sph_prepare_one)
-void launch_spheres_links(const Dev& d, cudaStream_t st) {
+void launch_spheres_links(const Dev& d, int g, cudaStream_t st) {
     if (d.nsph == 0) return;
     sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
     sph_contact_kernel<<<d.nsph, 128, 0, st>>>(d);
+    sph_gas_kernel<<<d.nsph, 128, 0, st>>>(d, g);
 }
 
 // the step's force and torque, then the motion: sub-stepped Newton-Euler (free spheres) or

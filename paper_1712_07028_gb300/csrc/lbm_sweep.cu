@@ -113,8 +113,8 @@ __device__ __noinline__ float sph_link_other(const Dev& d, int q, uint32_t P, in
 // few, and only free-slip or open faces get here.
 template <int S>
 __device__ __noinline__ float face_link(const Dev& d, const typename Store<S>::T* __restrict__ fa, const float* __restrict__ phia,
-                                        int q, int x, int y, int z, float fob, float rho0, float u0x, float u0y, float u0z,
-                                        float phix, float kap, bool isIF, bool liq, float& dm, float& sbb) {
+                                        int cur, int q, int x, int y, int z, float fob, float rho0, float u0x, float u0y,
+                                        float u0z, float phix, float kap, bool isIF, bool liq, float& dm, float& sbb) {
     const int c[3] = {cx(q), cy(q), cz(q)};
     const int L[3] = {d.nx, d.ny, d.nz};
     int s[3] = {x - c[0], y - c[1], z - c[2]};
@@ -154,6 +154,7 @@ __device__ __noinline__ float face_link(const Dev& d, const typename Store<S>::T
     if (t & F_OBS) {
         const uint32_t P = d.owner[j];
         if (P >= (uint32_t)d.nsph) return fob;
+        if (isIF) d.gasflag[(size_t)cur * d.max_sph + P] = 1u;
         const float corr = sph_link_other(d, q, P, x, y, z, rho0, fob);
         if (liq) sbb += corr;
         return fob + corr;
@@ -362,7 +363,7 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                 const uint32_t t = fsv[q];
                 if (t == 0xffu) {
                     if (atface)
-                        fin[q] = face_link<S>(d, fa, phia, q, x, y, z, fo[qb], rho0, u0x, u0y, u0z, phix, kap, isIF,
+                        fin[q] = face_link<S>(d, fa, phia, cur, q, x, y, z, fo[qb], rho0, u0x, u0y, u0z, phix, kap, isIF,
                                               (fl & F_LIQ) != 0, dm, sbb);
                     else
                         fin[q] = fo[qb];                                // no-slip wall
@@ -374,6 +375,8 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                     }
                 } else if (t & F_OBS) {                                 // Eq. bbrule
                     const uint32_t P = __float_as_uint(fv[q]);
+                    // a sphere beside an interface cell: the next gas-pressure pass scans it
+                    if (isIF && P < (uint32_t)d.nsph) d.gasflag[(size_t)cur * d.max_sph + P] = 1u;
                     if (P == P0) {
                         const float corr = 6.f * wgt(q) * rho0 * (cx(q) * ucx + cy(q) * ucy + cz(q) * ucz);
                         fin[q] = fo[qb] + corr;

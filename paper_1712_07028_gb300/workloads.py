@@ -258,3 +258,46 @@ def rising_bubble(case: str, n=(40, 40, 100), r=6.0, zc=9.5, storage="f32") -> W
                     sphere_mode=SPHERES_FIXED,
                     steps=RISING_BUBBLE_CASES[case]["steps"], storage=storage,
                     bubbles=[Bubble((nx / 2 - 0.5, ny / 2 - 0.5, zc), r)])
+
+
+# Sec. 4.1, Fig. bubbleParticle: a bubble of radius 0.01 m rising through a homogeneous bed of
+# spheres of radius 8e-4 m (5 cells per diameter at dx = 8e-5 m, as the paper resolves them),
+# solid density 3000 kg/m^3, sigma 0.145 N/m, g 0.981 m/s^2, liquid 1000 kg/m^3 and
+# mu 0.25 kg/(m s); the paper's dimensionless terminal rise velocity u (rho/(sigma g))^(1/4)
+# at bed solid fractions Phi = N V_P / (V - V_b)
+BUBBLE_BED_VELOCITY = {0.0: 0.53687069058757, 0.01: 0.54376978332139, 0.03: 0.52166135018381,
+                       0.05: 0.50675825176692, 0.075: 0.48794013951139, 0.1: 0.47890956185243}
+BED = dict(R=0.01, R_P=8e-4, rho=1000.0, rho_s=3000.0, mu=0.25, sigma=0.145, g=0.981, dx=8e-5,
+           n=(500, 500, 1300), c=(250, 250, 250))
+
+
+def bubble_bed_lattice(scale: int, dt: float):
+    """(dx, tau, g, sigma) in lattice units of the bed run coarsened `scale` times (dx grows,
+    the bubble and the domain keep their sizes in metres), time step dt [s]"""
+    dx = BED["dx"] * scale
+    nu = BED["mu"] / BED["rho"] * dt / dx ** 2
+    return dx, 3.0 * nu + 0.5, BED["g"] * dt ** 2 / dx, BED["sigma"] / BED["rho"] * dt ** 2 / dx ** 3
+
+
+def bubble_in_bed(phi: float, scale: int = 5, dt: float = 1.36e-4, r_p_cells: float = 2.5, seed: int = 7,
+                  storage: str = "f32") -> Workload:
+    """Fig. bubbleParticle's run coarsened `scale` times: the domain (500 x 500 x 1300 cells at
+    dx = 8e-5 m) and the bubble (radius 0.01 m at (250, 250, 250) dx) keep their sizes in metres;
+    the particles keep the paper's resolution of 5 cells per diameter (radius r_p_cells), so
+    their radius in metres grows with the scale.  N = Phi (V - V_b) / V_P spheres (the paper's
+    Phi), placed uniformly at random (seeded, rejection as in the columns); free spheres of
+    density 3, the column's boundaries and start those of the rising-bubble runs (free-slip
+    sides, no-slip bottom, open top, hydrostatic start).  dt sets the lattice viscosity and
+    the expected rise velocity (1.36e-4 s at scale 5: tau = 1.14, u ~ 0.02 cells per step)."""
+    dx, tau, g, sigma = bubble_bed_lattice(scale, dt)
+    nx, ny, nz = (v // scale for v in BED["n"])
+    R = BED["R"] / dx
+    c = tuple(float(v) / scale - 0.5 for v in BED["c"])
+    bub = Bubble(c, R)
+    V = nx * ny * nz - 4.0 / 3.0 * math.pi * R ** 3
+    n = int(round(phi * V / (4.0 / 3.0 * math.pi * r_p_cells ** 3)))
+    rng = SplitMix64(seed)
+    sph = place_spheres(rng, n, r_p_cells, BED["rho_s"] / BED["rho"], (nx, ny, nz), [bub]) if n else []
+    return Workload(name="bubble_bed_phi%g" % phi, nx=nx, ny=ny, nz=nz, tau=tau, g=(0.0, 0.0, -g),
+                    bc=(FREESLIP, FREESLIP, WALL), open_top=True, hydrostatic=True, sigma=sigma,
+                    sphere_mode=SPHERES_FREE, storage=storage, bubbles=[bub], spheres=sph)

@@ -3,7 +3,8 @@
 Written in *push* form, per link, independently of the C oracle (which pulls): every
 post-collision f*_q(y) of an active cell y travels to y + c_q, and what happens there
 decides where it lands (Eq. LBE1; halfway bounce-back at walls; Eq. bbrule at sphere
-links; Eq. fsk where the target is gas).  Mass exchange (Eqs. massExchange/b) is taken
+links; Eq. fsk where the target is gas); the gas at rest reflected from a sphere's surface
+presses on the sphere.  Mass exchange (Eqs. massExchange/b) is taken
 per interface link.  The collision is the TRT operator of Eq. LBE2 written with explicit
 even/odd parts and the Guo force, which acts on the liquid mass (rho g in a liquid cell, phi rho g
 in an interface cell, phi its fill level after the mass exchange).  Cell conversions are not
@@ -57,6 +58,14 @@ def sweep(p, f, flag, m, phi, owner, kappa, spheres, rho_gas):
     for z in range(nz):
         for y in range(ny):
             for x in range(nx):
+                if flag[z, y, x] & GAS and len(spheres):   # the gas at rest presses on spheres
+                    for q in range(1, 19):
+                        t = _target(p, x, y, z, C[q])
+                        if t is not None and flag[t[2], t[1], t[0]] & OBS:
+                            k = owner[t[2], t[1], t[0]]
+                            dj = 2 * WQ[q] * rho_gas[owner[z, y, x]] * C[q]
+                            F[k] += dj
+                            T[k] += np.cross(_mind(p, (x, y, z), spheres[k]["x"]), dj)
                 if not act[z, y, x]:
                     continue
                 for q in range(19):

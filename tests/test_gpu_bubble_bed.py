@@ -1,0 +1,72 @@
+"""A bubble rising through a bed of heavier particles (Sec. 4.1, Fig. bubbleParticle): the
+dimensionless terminal velocity u (rho / (sigma g))^(1/4) at bed solid fractions 0 - 10 %
+against the paper's printed values.
+
+The run is the paper's coarsened five times (100 x 100 x 260 cells, dx = 4e-4 m, bubble radius
+25 cells; `workloads.bubble_in_bed`): the bubble and the column keep their sizes in metres and
+the particles the paper's resolution of 5 cells per diameter.  Free spheres of density 3,
+free-slip sides, no-slip bottom, open top, hydrostatic start, dt = 1.36e-4 s (tau = 1.14,
+u ~ 0.02 cells per step).  The velocity is the gas centroid's rise over the last third of
+8000 steps.  Bounds: 10 % on the velocities themselves (the paper's own model accuracy is
+quoted near 10 %) and 4 % on the velocities relative to the bed-free run, the quantity the
+figure is about (the bed's effect: slightly faster at 1 %, slower beyond).
+"""
+import numpy as np
+import pytest
+
+from paper_1712_07028_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PHIS = (0.0, 0.01, 0.03, 0.05, 0.075, 0.1)
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("these tests need the GPU")
+    from paper_1712_07028_gb300 import lbm as L
+    L.load()
+    return L
+
+
+@pytest.fixture(scope="module")
+def velocities(lbm):
+    from tests.test_gpu_rising_bubble import gas_centroid_z
+    out = {}
+    for phi in PHIS:
+        wl = W.bubble_in_bed(phi)
+        sim = lbm.Sim(wl, max_spheres=max(1, len(wl.spheres)))
+        sim.step(0)
+        ts, zs = [0.0], [gas_centroid_z(sim)]
+        for t in range(400, 8001, 400):
+            sim.step(400)
+            ts.append(float(t))
+            zs.append(gas_centroid_z(sim))
+        assert sim.status() == 0, (phi, sim.status())
+        sim.close()
+        ts, zs = np.array(ts), np.array(zs)
+        keep = zs < wl.nz - 45   # the bubble (radius 25) well below the open top
+        t, z = ts[keep], zs[keep]
+        sel = t >= t[-1] - (t[-1] - t[0]) / 3.0
+        u = np.polyfit(t[sel], z[sel], 1)[0]
+        out[phi] = u * (1.0 / (wl.sigma * abs(wl.g[2]))) ** 0.25
+        print("Phi %5.3f: %d particles, u~ = %.4f (paper %.4f, %+.1f %%)" % (
+            phi, len(wl.spheres), out[phi], W.BUBBLE_BED_VELOCITY[phi], 100 * (out[phi] / W.BUBBLE_BED_VELOCITY[phi] - 1)))
+    return out
+
+
+def test_terminal_velocities(velocities):
+    for phi, u in velocities.items():
+        ref = W.BUBBLE_BED_VELOCITY[phi]
+        assert abs(u / ref - 1) <= 0.10, (phi, u, ref)
+
+
+def test_velocity_relative_to_the_bed_free_run(velocities):
+    u0, r0 = velocities[0.0], W.BUBBLE_BED_VELOCITY[0.0]
+    for phi, u in velocities.items():
+        ours, paper = u / u0, W.BUBBLE_BED_VELOCITY[phi] / r0
+        assert abs(ours - paper) <= 0.04, (phi, ours, paper)
+    # the bed slows the bubble: monotone beyond 1 %
+    assert velocities[0.1] < velocities[0.075] < velocities[0.05] < velocities[0.03] < velocities[0.01]

@@ -109,8 +109,10 @@ def _one_step_check(lbm, wl, pre_steps, f_tol, phi_tol):
     assert dphi <= phi_tol and dm <= phi_tol, (dphi, dm)
     if wl.spheres:
         Fo, To = o.forces
+        # the links' deviation parts are summed from FP32 per cell (~1e-8 per component over a
+        # sphere's few hundred links), the torque with arms of a few cells
         assert np.abs(st1["F"] - Fo).max() <= 1e-6 * max(1e-3, np.abs(Fo).max())
-        assert np.abs(st1["T"] - To).max() <= 1e-6 * max(1e-2, np.abs(To).max())
+        assert np.abs(st1["T"] - To).max() <= 1e-6 * max(1e-1, np.abs(To).max())
         assert np.abs(st1["sx"] - o.positions).max() <= 1e-9
     if wl.bubbles:
         assert np.abs(st1["rho_g"] - o.rho_gas).max() <= 1e-6
@@ -468,3 +470,18 @@ def test_rising_bubble_steps_like_the_oracle(lbm, at_wall):
     Mo, sbbo = o.mass_budget()[:2]
     assert abs(sbb - sbbo) <= 2e-3 * abs(sbbo)
     assert sim.status() == 0
+
+
+@pytest.mark.parametrize("where", ["inside", "straddling"])
+def test_one_step_sphere_touching_gas(lbm, where):
+    """a free sphere inside a bubble, or straddling a bubble's interface, under gravity: the gas
+    pressure on its dry surface (the GPU's pass over the spheres flagged beside interface cells
+    or gas) against the oracle's, from the GPU's state"""
+    if where == "inside":
+        bub, c = W.Bubble((12.0, 12.0, 12.0), 10.0), (12.3, 11.8, 12.4)
+    else:
+        bub, c = W.Bubble((12.0, 12.0, -20.0), 32.0), (12.0, 12.0, 12.0)
+    wl = W.Workload(name="sphere_gas_" + where, nx=24, ny=24, nz=24, tau=0.7, g=(0, 0, -1e-5),
+                    sphere_mode=W.SPHERES_FREE, bubbles=[bub], spheres=[W.Sphere(c, 4.0, 2.0)])
+    for pre in (0, 15):
+        _one_step_check(lbm, wl, pre, 2e-6, 2e-6)

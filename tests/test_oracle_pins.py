@@ -579,3 +579,30 @@ def test_hydrostatic_start_is_at_rest(orc):
             assert umax < bound
         else:
             assert umax > 10 * gg
+
+
+@pytest.mark.parametrize("where", ["inside", "straddling"])
+def test_gas_pressure_on_a_sphere(orc, where):
+    """The gas presses on the part of a sphere's surface it touches (the links from liquid and
+    interface cells carry the reference pressure, whose uniform part cancels only over a
+    closed surface).  At uniform pressure (no gravity, no surface tension, gas and liquid at
+    rho = 1) the net force and torque on a sphere vanish: exactly for a sphere inside a bubble
+    (the gas links close the surface), and for one straddling a near-flat interface -- where the
+    liquid links alone would push it with the reference pressure on half its surface,
+    (1/3) pi R^2 ~ 17 -- to round-off."""
+    from paper_1712_07028_gb300 import workloads as W
+    R = 4.0
+    if where == "inside":
+        bub, c = W.Bubble((12.0, 12.0, 12.0), 10.0), (12.3, 11.8, 12.4)
+    else:
+        bub, c = W.Bubble((12.0, 12.0, -20.0), 32.0), (12.0, 12.0, 12.0)
+    wl = W.Workload(name="gas_on_sphere", nx=24, ny=24, nz=24, tau=0.7, g=(0, 0, 0), sphere_mode=W.SPHERES_FIXED,
+                    bubbles=[bub], spheres=[W.Sphere(c, R, 2.0)])
+    o = orc.Sim(wl)
+    o.step(10)
+    F, T = o.forces
+    assert np.abs(F).max() < 1e-12 and np.abs(T).max() < 1e-12
+    if where == "straddling":
+        # liquid above the sphere, gas below it
+        assert ((o.flag == orc.LIQ) | (o.flag == orc.IFACE))[17:21, 12, 12].all()
+        assert (o.flag == orc.GAS)[4:8, 12, 12].all()
