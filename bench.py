@@ -32,7 +32,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per bulk-sweep launch on the 128^3 column from one ncu capture
 # (mean of three launches), with the hash of the sweep source it was taken on (null once the
 # kernel changes)
-NCU_TRAFFIC = {"sha1": "ba7e008c6b550d888be8aa9c553ce3a36a4775eb", "bytes_per_launch": 268476075}
+NCU_TRAFFIC = {"sha1": "8bfe953ae9d792d56cd4e22675e2ba6be8d503b2", "bytes_per_launch": 268272555}
 
 
 def _args():
