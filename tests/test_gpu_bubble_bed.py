@@ -45,6 +45,12 @@ def velocities(lbm):
             ts.append(float(t))
             zs.append(gas_centroid_z(sim))
         assert sim.status() == 0, (phi, sim.status())
+        # splitting is not modelled: the bubble's gas region must still be one connected piece
+        # (D3Q19 neighbourhood, the connectivity the merging uses)
+        from scipy import ndimage
+        fl = sim.fields()["flags"].cpu().numpy()
+        _, ncomp = ndimage.label((fl == 2) | (fl == 4), structure=ndimage.generate_binary_structure(3, 2))
+        assert ncomp == 1, (phi, ncomp)
         sim.close()
         ts, zs = np.array(ts), np.array(zs)
         keep = zs < wl.nz - 45   # the bubble (radius 25) well below the open top
