@@ -429,13 +429,10 @@ __device__ __forceinline__ float equilibrium_dev(int q, float rho, const float u
     return wgt(q) * ((rho - 1.f) + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
 }
 
-// moments, Guo-shifted velocity and the TRT collision of one cell, all on deviations f - w;
-// the post-collision deviations go to grid fb.  The body force acts on the cell's liquid mass:
-// rho g in a liquid cell, gw = its fill level times that in an interface cell.
-template <int S, bool CS = false>
-__device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T* __restrict__ fb, size_t i, const float (&fin)[kQ],
-                                              float gw = 1.f) {
-    const size_t N = d.N;
+// moments, Guo-shifted velocity and the TRT collision of one cell, all on deviations f - w:
+// the post-collision deviations out[].  The body force acts on the cell's liquid mass: rho g in
+// a liquid cell, gw = its fill level times that in an interface cell.
+__device__ __forceinline__ void trt_collide(const Dev& d, const float (&fin)[kQ], float gw, float (&out)[kQ]) {
     const float gx = gw * d.g[0], gy = gw * d.g[1], gz = gw * d.g[2];
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -457,7 +454,7 @@ __device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T
         // q = 0: f+ = f, e+ - w = w (rho - 1 - 1.5 rho u.u), G+ = -3 w rho u.g
         const float w = wgt(0);
         const float ep = w * (drho - 1.5f * rho * usq);
-        (CS ? Store<S>::put_cs : Store<S>::put)(fb, i, fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug)));
+        out[0] = fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug));
     }
 #pragma unroll
     for (int q = 1; q < kQ; q += 2) {
@@ -471,9 +468,19 @@ __device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T
         const float fm = 0.5f * (fin[q] - fin[qb]);
         const float a = lp * (fp - ep) + cp * (w * rho * (9.f * cu * cg - 3.f * ug));
         const float b = lm * (fm - em) + cm * (w * rho * 3.f * cg);
-        (CS ? Store<S>::put_cs : Store<S>::put)(fb, (size_t)q * N + i, fin[q] + a + b);
-        (CS ? Store<S>::put_cs : Store<S>::put)(fb, (size_t)qb * N + i, fin[qb] + a - b);
+        out[q] = fin[q] + a + b;
+        out[qb] = fin[qb] + a - b;
     }
+}
+
+// the collision of one cell, its post-collision deviations stored to grid fb (CS: streaming stores)
+template <int S, bool CS = false>
+__device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T* __restrict__ fb, size_t i, const float (&fin)[kQ],
+                                              float gw = 1.f) {
+    float out[kQ];
+    trt_collide(d, fin, gw, out);
+#pragma unroll
+    for (int q = 0; q < kQ; q++) (CS ? Store<S>::put_cs : Store<S>::put)(fb, (size_t)q * d.N + i, out[q]);
 }
 
 // minimum-image difference a - b along axis k (beyond 4 periods, or not finite, the value is
