@@ -485,3 +485,44 @@ def test_one_step_sphere_touching_gas(lbm, where):
                     sphere_mode=W.SPHERES_FREE, bubbles=[bub], spheres=[W.Sphere(c, 4.0, 2.0)])
     for pre in (0, 15):
         _one_step_check(lbm, wl, pre, 2e-6, 2e-6)
+
+
+# ------------------------------------------------------------ degenerate and ragged inputs
+
+def test_smallest_grid(lbm):
+    """the smallest grid the ABI takes (3^3, every cell at a wall), liquid under gravity:
+    40 steps against the oracle"""
+    wl = W.Workload(name="min3", nx=3, ny=3, nz=3, tau=0.8, g=(1e-4, -2e-4, 3e-4), sphere_mode=W.SPHERES_FIXED)
+    sim = lbm.Sim(wl)
+    o = oracle.Sim(wl)
+    sim.step(40)
+    o.step(40)
+    drho, du, _ = U.compare_fields(o, U.gpu_state(sim))
+    assert drho <= 1e-6 and du <= 1e-7, (drho, du)
+    assert sim.status() == 0
+
+
+def test_all_gas_domain(lbm):
+    """a bubble larger than the box: no liquid and no interface cell at all; the steps have
+    nothing to stream, convert or cover, and the bubble keeps the box's volume"""
+    wl = W.Workload(name="all_gas", nx=8, ny=7, nz=9, tau=0.7, g=(0, 0, -1e-4), sphere_mode=W.SPHERES_FIXED,
+                    bubbles=[W.Bubble((4.0, 3.0, 4.0), 30.0)])
+    sim = lbm.Sim(wl)
+    sim.step(10)
+    fl = sim.fields()["flags"].cpu().numpy()
+    o = oracle.Sim(wl)
+    o.step(10)
+    assert (fl == oracle.GAS).all() and (o.flag == oracle.GAS).all()
+    V0, V, rg = sim.bubbles()
+    assert V[0] == wl.cells and abs(o.volumes[0] - wl.cells) < 1e-12
+    assert sim.status() == 0
+
+
+@pytest.mark.parametrize("pre", [0, 25])
+def test_ragged_grid_one_step(lbm, pre):
+    """a grid of odd sizes (37 x 29 x 23: partial thread blocks in x, a boundary list that
+    ends inside a block) with a bubble and a free sphere, one step from the GPU's state"""
+    wl = W.Workload(name="ragged", nx=37, ny=29, nz=23, tau=0.65, g=(0, 0, -1e-5),
+                    bubbles=[W.Bubble((18.0, 14.0, 9.0), 5.0)],
+                    spheres=[W.Sphere((9.0, 8.0, 16.0), 3.0, 1.8)])
+    _one_step_check(lbm, wl, pre, 2e-6, 2e-6)
