@@ -100,9 +100,10 @@ __device__ __forceinline__ void frozen_pull(const Dev& d, const float* __restric
 // the boundary cells' forward step (the bulk cells run the forward sweep's own bulk kernel)
 __global__ void __launch_bounds__(128) frozen_boundary_kernel(const Dev d, const float* __restrict__ f_in,
                                                               float* __restrict__ f_out) {
-    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)d.N);
+    uint32_t ngen;
+    const uint32_t n = blist_len(d, ngen);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const uint32_t i = d.wl_slow[k];
+        const uint32_t i = blist_cell(d, k, ngen);
         if (i == kNone || !(d.flags[i] & F_LIQ) || (d.flags[i] & F_BULK)) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
@@ -321,10 +322,11 @@ __global__ void __launch_bounds__(128) adjoint_boundary_kernel(const Dev d, cons
                                                                const float jx, const float jy, const float jz,
                                                                const int moving, double* part) {
     const size_t N = d.N;
-    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)N);
+    uint32_t ngen;
+    const uint32_t n = blist_len(d, ngen);
     float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const uint32_t i = d.wl_slow[k];
+        const uint32_t i = blist_cell(d, k, ngen);
         if (i == kNone || !(d.flags[i] & F_LIQ) || (d.flags[i] & F_BULK)) {
             if (moving) srho[k] = 0.f;
             continue;
@@ -360,9 +362,10 @@ __global__ void __launch_bounds__(128) adjoint_boundary_kernel(const Dev d, cons
 
 // the rho0 terms of sphere links with a moving surface, added once every link is scattered
 __global__ void adjoint_rho_kernel(const Dev d, const float* __restrict__ srho, float* __restrict__ lam_out) {
-    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)d.N);
+    uint32_t ngen;
+    const uint32_t n = blist_len(d, ngen);
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const uint32_t i = d.wl_slow[k];
+        const uint32_t i = blist_cell(d, k, ngen);
         if (i == kNone || !(d.flags[i] & F_LIQ) || (d.flags[i] & F_BULK)) continue;
         const float s = srho[k];
         if (s == 0.f) continue;

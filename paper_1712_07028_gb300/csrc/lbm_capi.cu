@@ -53,8 +53,8 @@ struct lbm_ctx {
     int links_state;
     uint64_t h2d_bytes, d2h_bytes;   // host <-> device copies made by the library
     // second stream and fork/join events of the concurrent bulk / boundary sweep
-    cudaStream_t side;
-    cudaEvent_t fork, join, fork2, join2, fork3, join3, fork4, join4;
+    cudaStream_t side, side2;   // the general and the lean boundary sweep
+    cudaEvent_t fork, join, fork2, join2, fork3, join3, fork4, join4, join5;
     cudaStream_t epi;     // the end-of-step kernels when they overlap the next bulk sweep
     cudaStream_t links;   // partner lists and obstacle-node links beside the sweep's rest
     bool side_ready;
@@ -200,7 +200,7 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
 
 int epilogue_launches(const Dev& d) { return 1 + spheres_launches(d) + (d.kappa ? 1 : 0) + 1; }
 int step_launches(const Dev& d, bool overlap) {
-    return 3 + spheres_links_launches(d) + (overlap ? epilogue_launches(d) : 0);
+    return 3 + d.split_liq + spheres_links_launches(d) + (overlap ? epilogue_launches(d) : 0);
 }
 
 // one step reading grid cur: the bulk sweep on s and, with `overlap`, the end-of-step kernels
@@ -233,7 +233,7 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed =
         cudaEventRecord(c->join2, c->links);
         c->links_state = kLinksForked;
     }
-    launch_sweep_rest(d, cur, s, c->side, c->fork, c->join);
+    launch_sweep_rest(d, cur, s, c->side, c->side2, c->fork, c->join, c->join5);
     // the step's force sums need the links (an event recorded in this same call: a graph
     // capture in between would leave an earlier record unusable)
     if (d.nsph > 0 && c->links_state == kLinksForked) cudaStreamWaitEvent(s, c->join2, 0);
@@ -279,6 +279,12 @@ int first_step(lbm_ctx* c) {
     d.sphere_mode = p->sphere_mode;
     d.nbub = (int)(c->bub_geo.size() / 4);
     d.nsph = (int)c->sph_init.size();
+    {   // the liquid cells beside the spheres, about 4 pi (R + 1)^2 each: the lean kernel pays
+        // for its extra graph branch once they outnumber one round of the general grid
+        double shell = 0.0;
+        for (const Sphere& sp : c->sph_init) shell += 4.0 * 3.14159265358979 * (sp.R + 1.0) * (sp.R + 1.0);
+        d.split_liq = shell > (double)kBoundaryGrid * 128.0 ? 1 : 0;
+    }
     d.max_bub = p->max_bubbles;
     d.max_sph = p->max_spheres;
     d.wl_cap = (int)L.wl_cap;
@@ -352,6 +358,8 @@ int first_step(lbm_ctx* c) {
         if (cudaStreamCreateWithPriority(&c->links, cudaStreamNonBlocking, hi_prio) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->fork4, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         if (cudaEventCreateWithFlags(&c->join4, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
+        if (cudaStreamCreateWithPriority(&c->side2, cudaStreamNonBlocking, hi_prio) != cudaSuccess) return LBM_ECUDA;
+        if (cudaEventCreateWithFlags(&c->join5, cudaEventDisableTiming) != cudaSuccess) return LBM_ECUDA;
         c->side_ready = true;
     }
     int rc = cuda_fail(cudaMemsetAsync(a, 0, L.total, s));
@@ -724,6 +732,7 @@ int lbm_destroy(lbm_ctx* c) {
     if (c->side_ready) {
         // nothing of this simulation may still run once the caller frees the arena
         cudaStreamSynchronize(c->side);
+        cudaStreamSynchronize(c->side2);
         cudaStreamSynchronize(c->epi);
         cudaStreamSynchronize(c->links);
         cudaEventDestroy(c->fork);
@@ -737,6 +746,8 @@ int lbm_destroy(lbm_ctx* c) {
         cudaStreamDestroy(c->links);
         cudaEventDestroy(c->fork4);
         cudaEventDestroy(c->join4);
+        cudaStreamDestroy(c->side2);
+        cudaEventDestroy(c->join5);
     }
     std::free(c->sph_stage);
     std::free(c->sc_stage);

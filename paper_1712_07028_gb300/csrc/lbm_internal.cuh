@@ -140,7 +140,8 @@ struct Scalars {
     uint32_t status;      // LBM_S_* bits
     uint32_t n_conv, n_newif, n_fromliq, n_touch, n_uncov;
     uint32_t bin_overflow;
-    uint32_t n_slow;      // boundary-list length
+    uint32_t n_slow;      // boundary-list length: general cells, at the front of wl_slow
+    uint32_t n_liq;       // and liquid cells, at the back
     uint32_t ticket;      // blocks of the end-of-step scan that have finished
     uint32_t n_fix;       // BULK cells the end of the last step changed or whose neighbours it changed
     uint32_t fix_all;     // the fix list overflowed: the fix pass takes every BULK cell
@@ -160,6 +161,7 @@ struct Dev {
     int bc[3];                // 1: periodic axis
     uint8_t face[6];          // faces -x, +x, -y, +y, -z, +z of non-periodic axes: FACE_*
     int special;              // some face is free-slip or open
+    int split_liq;            // the liquid boundary segment has its own (lean) sweep kernel
     int hydrostatic;          // the liquid starts in hydrostatic equilibrium below the open top
     double gz;                // g_z in FP64 (the hydrostatic start)
     size_t N;
@@ -194,7 +196,8 @@ struct Dev {
     uint32_t* wl_newif;
     uint32_t* wl_fromliq;
     uint32_t* wl_touch;
-    uint32_t* wl_slow;        // [N] boundary list: every active cell that is not BULK, in scan order
+    uint32_t* wl_slow;        // [N] boundary list: every active cell that is not BULK, in scan order;
+                              // liquid cells off the free-slip and open faces from the back
     uint32_t* wl_fix;         // [wl_cap] BULK cells to sweep again after the end-of-step kernels
     // uniform bins of sphere ids for the neighbour searches
     int bin_w, nbx, nby, nbz, bin_cap;
@@ -206,6 +209,7 @@ struct Dev {
     uint32_t* merge_list;     // [kMergeCap] slots of merge_keys in use, in insertion order
 };
 constexpr int kPairCap = 32;
+constexpr int kBoundaryGrid = 152 * 2;   // blocks of the general boundary sweep when it runs alone
 
 __device__ __forceinline__ size_t cell_index(const Dev& d, int x, int y, int z) {
     return (size_t)x + (size_t)d.nx * ((size_t)y + (size_t)d.ny * (size_t)z);
@@ -237,6 +241,18 @@ __device__ __forceinline__ bool at_special_face(const Dev& d, int x, int y, int 
         if (c[k] == L[k] - 1 && d.face[2 * k + 1] != FACE_WALL) return true;
     }
     return false;
+}
+
+// the boundary list in one [N] buffer: the general cells (interface cells and cells on a
+// free-slip or open face) from the front, slots [0, n_slow), and the other liquid cells from
+// the back, slot N - 1 - k for the k-th (they never overlap: together they are at most N cells)
+__device__ __forceinline__ uint32_t blist_len(const Dev& d, uint32_t& ngen) {
+    ngen = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)d.N);
+    const uint32_t nliq = min(*(volatile const uint32_t*)&d.sc->n_liq, (uint32_t)d.N - ngen);
+    return ngen + nliq;
+}
+__device__ __forceinline__ uint32_t blist_cell(const Dev& d, uint32_t k, uint32_t ngen) {
+    return k < ngen ? d.wl_slow[k] : d.wl_slow[(uint32_t)d.N - 1u - (k - ngen)];
 }
 
 // BULK: a liquid cell each of whose 18 neighbours is liquid or interface or lies beyond a
@@ -658,6 +674,7 @@ __device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t
         c.share_f = (float)c.share;
         c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
         c.n_slow = 0;   // the boundary sweep has consumed its list; the list pass refills it
+        c.n_liq = 0;
     }
     if (bin_spheres)
         for (uint32_t P = t; P < (uint32_t)d.nsph; P += nt) {
@@ -670,7 +687,8 @@ __device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t
 }
 
 void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s);
-void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join);
+void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaStream_t side2, cudaEvent_t fork,
+                       cudaEvent_t join, cudaEvent_t join2);
 
 void launch_conversions(const Dev& d, int nxt, bool close, cudaStream_t s);
 void launch_init_scan(const Dev& d, cudaStream_t s);

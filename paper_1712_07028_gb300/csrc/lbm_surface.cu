@@ -53,6 +53,69 @@ void launch_conversions(const Dev& d, int nxt, bool close, cudaStream_t s) {
     }
 }
 
+// --------------------------------------------------------- boundary list
+// Append the boundary cells (active, not BULK) of the 16 cells from v * 16, whose types are
+// the bytes of w, to the boundary list: interface cells and cells on a free-slip or open face
+// to the general segment, the other liquid cells to the liquid segment (from the back).  The
+// two counts of a thread are packed in one word (16 bits each: a block of at most 1024
+// threads has at most 16384 cells of each kind), scanned over the warp, summed over the block
+// and appended with one atomic per segment and block.  Every thread of the block calls it.
+__device__ __forceinline__ void blist_append(const Dev& d, size_t v, const uint32_t (&w)[4], uint32_t* sWarp, uint32_t* sBase) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    uint32_t sg = 0u, sl = 0u;
+#pragma unroll
+    for (int c = 0; c < 16; c++) {
+        const uint32_t t = (w[c / 4] >> (8 * (c % 4))) & 0xffu;
+        if (!(t & F_ACTIVE) || (t & F_BULK)) continue;
+        bool liq = (t & F_LIQ) != 0;
+        if (liq && d.special) {
+            int x, y, z;
+            cell_xyz(d, v * 16 + c, x, y, z);
+            liq = !at_special_face(d, x, y, z);
+        }
+        if (liq) sl |= 1u << c;
+        else sg |= 1u << c;
+    }
+    const uint32_t cnt = (uint32_t)__popc(sg) | ((uint32_t)__popc(sl) << 16);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) sWarp[threadIdx.x >> 5] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t acc = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
+            const uint32_t x = sWarp[k];
+            sWarp[k] = acc;
+            acc += x;
+        }
+        sBase[0] = (acc & 0xffffu) ? atomicAdd(&d.sc->n_slow, acc & 0xffffu) : 0u;
+        sBase[1] = (acc >> 16) ? atomicAdd(&d.sc->n_liq, acc >> 16) : 0u;
+    }
+    __syncthreads();
+    const uint32_t pre = sWarp[threadIdx.x >> 5] + incl - cnt;
+    uint32_t slot = sBase[0] + (pre & 0xffffu);
+    uint32_t slotl = sBase[1] + (pre >> 16);
+    __syncthreads();   // sWarp / sBase are rewritten by the next call
+    const uint32_t N = (uint32_t)d.N;
+    while (sg) {
+        const int c = __ffs(sg) - 1;
+        sg &= sg - 1;
+        if (slot < N) d.wl_slow[slot] = (uint32_t)(v * 16 + c);
+        slot++;
+    }
+    while (sl) {
+        const int c = __ffs(sl) - 1;
+        sl &= sl - 1;
+        if (slotl < N) d.wl_slow[N - 1u - slotl] = (uint32_t)(v * 16 + c);
+        slotl++;
+    }
+}
+
 // --------------------------------------------------------- initial scan
 // One pass over the initial cell types: the active cells the bulk sweep leaves to the
 // boundary sweep form the first boundary list; each bubble's gas cells are counted and V_b(0) = #gas cells + sum over its interface cells
@@ -65,7 +128,7 @@ __global__ void init_scan_kernel(const Dev d) {
     __shared__ unsigned int sIf;
     __shared__ bool last;
     __shared__ uint32_t sWarp[32];
-    __shared__ uint32_t sBase;
+    __shared__ uint32_t sBase[2];
     for (int b = threadIdx.x; b < d.nbub; b += blockDim.x) { sV[b] = 0.0; sG[b] = 0ull; }
     if (threadIdx.x == 0) sIf = 0;
     __syncthreads();
@@ -89,41 +152,7 @@ __global__ void init_scan_kernel(const Dev d) {
         } else if (v < total) {
             for (size_t c = v * 16; c < d.N; c++) w[(c - v * 16) / 4] |= (uint32_t)d.flags[c] << (8 * ((c - v * 16) % 4));
         }
-        // boundary cells (active, not BULK): one append per warp
-        uint32_t sel = 0u;
-#pragma unroll
-        for (int c = 0; c < 16; c++) {
-            const uint32_t t = (w[c / 4] >> (8 * (c % 4))) & 0xffu;
-            sel |= ((t & F_ACTIVE) && !(t & F_BULK)) ? (1u << c) : 0u;
-        }
-        const uint32_t cnt = __popc(sel);
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(full, incl, o);
-            if (lane >= o) incl += y;
-        }
-        // one append per block: warp totals -> block prefix -> one atomic on the list length
-        if (lane == 31) sWarp[threadIdx.x >> 5] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t acc = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
-                const uint32_t v = sWarp[k];
-                sWarp[k] = acc;
-                acc += v;
-            }
-            sBase = acc ? atomicAdd(&d.sc->n_slow, acc) : 0u;
-        }
-        __syncthreads();
-        uint32_t slot = sBase + sWarp[threadIdx.x >> 5] + incl - cnt;
-        __syncthreads();   // sWarp / sBase are rewritten in the next round
-        while (sel) {
-            const int c = __ffs(sel) - 1;
-            sel &= sel - 1;
-            if (slot < (uint32_t)d.N) d.wl_slow[slot] = (uint32_t)(v * 16 + c);
-            slot++;
-        }
+        blist_append(d, v, w, sWarp, sBase);   // boundary cells
         // bubble volumes: owners and fill levels of the chunk's gas / interface cells
         if (!((w[0] | w[1] | w[2] | w[3]) & 0x06060606u)) continue;
         // bubbles that touch from the start (the steps check every cell that changes)
@@ -217,20 +246,17 @@ void launch_init_scan(const Dev& d, cudaStream_t s) {
     init_scan_kernel<<<blocks, 512, shm, s>>>(d);
 }
 
-// --------------------------------------------------------- boundary list
 // One pass over the cell types as the step leaves them: the active cells that are not BULK,
 // in scan order (blocks of 8192 consecutive cells appended whole), are the next boundary
-// sweep's list.  Scan order keeps the boundary sweep's accesses local: a list kept by
+// sweep's list, split into its general and liquid segments.  Scan order keeps the boundary sweep's accesses local: a list kept by
 // appending cells in the order they changed made it ~40 % slower.  The list length is zero
 // on entry (the step close resets it).
 __global__ void list_rescan_kernel(const Dev d) {
     __shared__ uint32_t sWarp[32];
-    __shared__ uint32_t sBase;
+    __shared__ uint32_t sBase[2];
     const size_t nvec = d.N / 16;
     const size_t total = nvec + (d.N % 16 ? 1 : 0);
     const uint4* fl4 = reinterpret_cast<const uint4*>(d.flags);
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
     // every thread of the block runs the same number of rounds (block collectives below)
     for (size_t base = blockIdx.x * (size_t)blockDim.x; base < total; base += (size_t)gridDim.x * blockDim.x) {
         const size_t v = base + threadIdx.x;
@@ -241,39 +267,7 @@ __global__ void list_rescan_kernel(const Dev d) {
         } else if (v < total) {
             for (size_t c = v * 16; c < d.N; c++) w[(c - v * 16) / 4] |= (uint32_t)d.flags[c] << (8 * ((c - v * 16) % 4));
         }
-        uint32_t sel = 0u;
-#pragma unroll
-        for (int c = 0; c < 16; c++) {
-            const uint32_t t = (w[c / 4] >> (8 * (c % 4))) & 0xffu;
-            sel |= ((t & F_ACTIVE) && !(t & F_BULK)) ? (1u << c) : 0u;
-        }
-        const uint32_t cnt = __popc(sel);
-        uint32_t incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(full, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) sWarp[threadIdx.x >> 5] = incl;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t acc = 0;
-            for (int k = 0; k < (int)(blockDim.x >> 5); k++) {
-                const uint32_t x = sWarp[k];
-                sWarp[k] = acc;
-                acc += x;
-            }
-            sBase = acc ? atomicAdd(&d.sc->n_slow, acc) : 0u;
-        }
-        __syncthreads();
-        uint32_t slot = sBase + sWarp[threadIdx.x >> 5] + incl - cnt;
-        __syncthreads();
-        while (sel) {
-            const int c = __ffs(sel) - 1;
-            sel &= sel - 1;
-            if (slot < (uint32_t)d.N) d.wl_slow[slot] = (uint32_t)(v * 16 + c);
-            slot++;
-        }
+        blist_append(d, v, w, sWarp, sBase);
     }
 }
 

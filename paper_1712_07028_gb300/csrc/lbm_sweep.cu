@@ -75,6 +75,57 @@ __device__ __forceinline__ void sph_flush_direct(const Dev& d, const SphAcc& a) 
 }
 
 
+// the lanes' sphere accumulators summed over the warp, sphere by sphere, then one FP64 atomic per
+// warp and sphere (every lane of the warp takes part)
+__device__ __forceinline__ void sph_acc_warp_reduce(const Dev& d, const SphAcc& acc) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    float TJ[3] = {0.f, 0.f, 0.f};
+    int XK[3] = {0, 0, 0};
+    if (acc.pid != kNone) {
+        TJ[0] = acc.r[1] * acc.J[2] - acc.r[2] * acc.J[1];
+        TJ[1] = acc.r[2] * acc.J[0] - acc.r[0] * acc.J[2];
+        TJ[2] = acc.r[0] * acc.J[1] - acc.r[1] * acc.J[0];
+        XK[0] = acc.xi[1] * acc.K[2] - acc.xi[2] * acc.K[1];
+        XK[1] = acc.xi[2] * acc.K[0] - acc.xi[0] * acc.K[2];
+        XK[2] = acc.xi[0] * acc.K[1] - acc.xi[1] * acc.K[0];
+    }
+    unsigned todo = __ballot_sync(full, acc.pid != kNone);
+    while (todo) {
+        const int leader = __ffs(todo) - 1;
+        const uint32_t P = __shfl_sync(full, acc.pid, leader);
+        const bool mine = acc.pid == P;
+        todo &= ~__ballot_sync(full, mine);
+        float v[6];
+        int iv[6];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            v[c] = mine ? acc.J[c] : 0.f;
+            v[3 + c] = mine ? TJ[c] : 0.f;
+            iv[c] = mine ? acc.K[c] : 0;
+            iv[3 + c] = mine ? XK[c] : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int c = 0; c < 6; c++) {
+                v[c] += __shfl_xor_sync(full, v[c], o);
+                iv[c] += __shfl_xor_sync(full, iv[c], o);
+            }
+        }
+        if (lane == leader) {
+            SphereAcc& g = d.acc[P];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                atomicAdd(&g.J[c], (double)v[c]);
+                atomicAdd(&g.TJ[c], (double)v[3 + c]);
+                atomicAdd(&g.K[c], (unsigned long long)(long long)iv[c]);
+                atomicAdd(&g.XK[c], (unsigned long long)(long long)iv[3 + c]);
+            }
+        }
+    }
+}
+
 // one link of cell (x, y, z) into an obstacle cell of sphere P that is not the cell's first
 // sphere (a cell between two spheres): Eq. bbrule and the link's momentum exchange, summed
 // straight into P's accumulators.  Returns the bounce-back correction (f_q(x, t+1) is
@@ -250,16 +301,24 @@ __global__ void __launch_bounds__(128) sweep_fix_kernel(const Dev d, const int c
     }
 }
 
-// every other active cell: walls, sphere links, gas links, interface mass exchange
-template <int S>
-__global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, const int cur) {
+// every other active cell: walls, sphere links, gas links, interface mass exchange.  Two
+// instances: the general one takes the general segment of the list (interface cells and cells
+// on a free-slip or open face); the lean one (Lean) the liquid segment, cells whose links are
+// streaming, wall and sphere links only (and gas links, should a gas cell sit beside one): no
+// mass exchange, no face links, a quarter of the registers, four times the resident warps.
+template <int S, bool Lean>
+__global__ void __launch_bounds__(128, Lean ? 4 : 1) sweep_boundary_kernel(const Dev d, const int cur) {
     using T = typename Store<S>::T;
     const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
     T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
     const float* __restrict__ phia = d.phi[cur];
     float* __restrict__ phib = d.phi[cur ^ 1];
     const size_t N = d.N;
-    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)N);
+    // the general kernel takes both segments when no lean kernel runs
+    uint32_t ngen = 0, n;
+    if (Lean) n = min(*(volatile const uint32_t*)&d.sc->n_liq, (uint32_t)N);
+    else if (d.split_liq) n = ngen = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)N);
+    else n = blist_len(d, ngen);
     const uint32_t* __restrict__ list = d.wl_slow;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -267,6 +326,7 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
     __shared__ uint32_t sNif[4], sVb[4];
     __shared__ double sV[4];
     __shared__ float sS[4];
+    float sbb_t = 0.f;   // Lean: the thread's bounce-back mass over all its rounds
 
     // every thread of the block runs the same number of rounds (block and warp collectives)
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
@@ -278,11 +338,12 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
         float vphi = 1.f;         // and its new fill level
         bool isIFc = false;
         if (k < n) {
-            const size_t i = list[k];
+            const size_t i = Lean ? list[(uint32_t)N - 1u - k] : blist_cell(d, k, ngen);
             const uint8_t fl = d.flags[i];
             int x, y, z;
             cell_xyz(d, i, x, y, z);
-            const bool isIF = (fl & F_IF) != 0;
+            const bool isIF = !Lean && (fl & F_IF) != 0;
+            const bool liqc = Lean || (fl & F_LIQ) != 0;
             isIFc = isIF;
             // every load is issued before any link is resolved: neighbour indices and types,
             // then the pulled PDFs, owners and fill levels (predicated on the types)
@@ -338,7 +399,7 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
             const float u0sq = u0x * u0x + u0y * u0y + u0z * u0z;
             const float phix = isIF ? phia[i] : 0.f;
             const float kap = (isIF && d.kappa) ? d.kappa[i] : 0.f;
-            const bool atface = at_special_face(d, x, y, z);
+            const bool atface = !Lean && at_special_face(d, x, y, z);
             // the cell's sphere: the owner of its first obstacle link (links into a second
             // sphere take sph_link_other); the wall velocity is needed only as c_q . u_w, and
             // c_q . u_w at the link midpoint x - c_q/2 equals c_q . (u_P + w_P x r), r = x - x_P
@@ -364,7 +425,7 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                 if (t == 0xffu) {
                     if (atface)
                         fin[q] = face_link<S>(d, fa, phia, cur, q, x, y, z, fo[qb], rho0, u0x, u0y, u0z, phix, kap, isIF,
-                                              (fl & F_LIQ) != 0, dm, sbb);
+                                              liqc, dm, sbb);
                     else
                         fin[q] = fo[qb];                                // no-slip wall
                 } else if (t & F_ACTIVE) {
@@ -384,11 +445,11 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
                         const float dev = 2.f * fo[qb] + corr;
                         acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
                         acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
-                        if (fl & F_LIQ) sbb += corr;
+                        if (liqc) sbb += corr;
                     } else if (P < (uint32_t)d.nsph) {
                         const float corr = sph_link_other(d, q, P, x, y, z, rho0, fo[qb]);
                         fin[q] = fo[qb] + corr;
-                        if (fl & F_LIQ) sbb += corr;
+                        if (liqc) sbb += corr;
                     } else {
                         fin[q] = fo[qb];
                     }
@@ -433,6 +494,11 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
             collide_store<S>(d, fb, i, fin, gw);
         }
 
+        if (Lean) {
+            sbb_t += sbb;
+            sph_acc_warp_reduce(d, acc);
+            continue;
+        }
         // ---- per-warp partial sums: interface part of the bubble volumes (1 - phi, FP64),
         // interface count and bounce-back mass; folded per block below (one atomic each)
         const unsigned nifw = __popc(__ballot_sync(full, isIFc));
@@ -478,51 +544,11 @@ __global__ void __launch_bounds__(128, 1) sweep_boundary_kernel(const Dev d, con
         }
         if (base + gridDim.x * blockDim.x < n) __syncthreads();   // shared slots reused next round
 
-        // ---- warp reduction of the sphere accumulators (every lane takes part)
-        float TJ[3] = {0.f, 0.f, 0.f};
-        int XK[3] = {0, 0, 0};
-        if (acc.pid != kNone) {
-            TJ[0] = acc.r[1] * acc.J[2] - acc.r[2] * acc.J[1];
-            TJ[1] = acc.r[2] * acc.J[0] - acc.r[0] * acc.J[2];
-            TJ[2] = acc.r[0] * acc.J[1] - acc.r[1] * acc.J[0];
-            XK[0] = acc.xi[1] * acc.K[2] - acc.xi[2] * acc.K[1];
-            XK[1] = acc.xi[2] * acc.K[0] - acc.xi[0] * acc.K[2];
-            XK[2] = acc.xi[0] * acc.K[1] - acc.xi[1] * acc.K[0];
-        }
-        unsigned todo = __ballot_sync(full, acc.pid != kNone);
-        while (todo) {
-            const int leader = __ffs(todo) - 1;
-            const uint32_t P = __shfl_sync(full, acc.pid, leader);
-            const bool mine = acc.pid == P;
-            todo &= ~__ballot_sync(full, mine);
-            float v[6];
-            int iv[6];
-#pragma unroll
-            for (int c = 0; c < 3; c++) {
-                v[c] = mine ? acc.J[c] : 0.f;
-                v[3 + c] = mine ? TJ[c] : 0.f;
-                iv[c] = mine ? acc.K[c] : 0;
-                iv[3 + c] = mine ? XK[c] : 0;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                for (int c = 0; c < 6; c++) {
-                    v[c] += __shfl_xor_sync(full, v[c], o);
-                    iv[c] += __shfl_xor_sync(full, iv[c], o);
-                }
-            }
-            if (lane == leader) {
-                SphereAcc& g = d.acc[P];
-#pragma unroll
-                for (int c = 0; c < 3; c++) {
-                    atomicAdd(&g.J[c], (double)v[c]);
-                    atomicAdd(&g.TJ[c], (double)v[3 + c]);
-                    atomicAdd(&g.K[c], (unsigned long long)(long long)iv[c]);
-                    atomicAdd(&g.XK[c], (unsigned long long)(long long)iv[3 + c]);
-                }
-            }
-        }
+        sph_acc_warp_reduce(d, acc);
+    }
+    if (Lean) {
+        const double sw = warp_sum((double)sbb_t);
+        if (lane == 0 && sw != 0.0) atomicAdd(&d.sc->S_bb, sw);
     }
 }
 
@@ -539,29 +565,34 @@ void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s) {
     }
 }
 
-// the rest of the sweep once the end-of-step kernels are done: the boundary kernel on `side`,
-// forked from and joined back into `s` by two events, the fix pass on `s`; both read grid cur
-// and write disjoint cells of grid cur ^ 1
-void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaEvent_t fork, cudaEvent_t join) {
-    const int nb = 152 * 2;
+// the rest of the sweep once the end-of-step kernels are done: the general boundary kernel on
+// `side` and the lean one on `side2`, forked from and joined back into `s` by events, the fix
+// pass on `s`; all three read grid cur and write disjoint cells of grid cur ^ 1
+// (with the lean kernel, one general block per SM, 200 registers a thread: the lean kernel's
+// blocks fit beside it)
+template <int S>
+static void sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaStream_t side2) {
+    sweep_boundary_kernel<S, false><<<d.split_liq ? 152 : kBoundaryGrid, 128, 0, side>>>(d, cur);
+    if (d.split_liq) sweep_boundary_kernel<S, true><<<152 * 4, 128, 0, side2>>>(d, cur);
+    sweep_fix_kernel<S><<<152 * 2, 128, 0, s>>>(d, cur);
+}
+
+void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaStream_t side2, cudaEvent_t fork,
+                       cudaEvent_t join, cudaEvent_t join2) {
     cudaEventRecord(fork, s);
     cudaStreamWaitEvent(side, fork, 0);
+    if (d.split_liq) cudaStreamWaitEvent(side2, fork, 0);
     switch (d.storage) {
-        case LBM_STORE_F32:
-            sweep_boundary_kernel<LBM_STORE_F32><<<nb, 128, 0, side>>>(d, cur);
-            sweep_fix_kernel<LBM_STORE_F32><<<nb, 128, 0, s>>>(d, cur);
-            break;
-        case LBM_STORE_F16DEV:
-            sweep_boundary_kernel<LBM_STORE_F16DEV><<<nb, 128, 0, side>>>(d, cur);
-            sweep_fix_kernel<LBM_STORE_F16DEV><<<nb, 128, 0, s>>>(d, cur);
-            break;
-        default:
-            sweep_boundary_kernel<LBM_STORE_BF16DEV><<<nb, 128, 0, side>>>(d, cur);
-            sweep_fix_kernel<LBM_STORE_BF16DEV><<<nb, 128, 0, s>>>(d, cur);
-            break;
+        case LBM_STORE_F32: sweep_rest<LBM_STORE_F32>(d, cur, s, side, side2); break;
+        case LBM_STORE_F16DEV: sweep_rest<LBM_STORE_F16DEV>(d, cur, s, side, side2); break;
+        default: sweep_rest<LBM_STORE_BF16DEV>(d, cur, s, side, side2); break;
     }
     cudaEventRecord(join, side);
     cudaStreamWaitEvent(s, join, 0);
+    if (d.split_liq) {
+        cudaEventRecord(join2, side2);
+        cudaStreamWaitEvent(s, join2, 0);
+    }
 }
 
 }  // namespace lbm

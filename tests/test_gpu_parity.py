@@ -526,3 +526,28 @@ def test_ragged_grid_one_step(lbm, pre):
                     bubbles=[W.Bubble((18.0, 14.0, 9.0), 5.0)],
                     spheres=[W.Sphere((9.0, 8.0, 16.0), 3.0, 1.8)])
     _one_step_check(lbm, wl, pre, 2e-6, 2e-6)
+
+
+def _sphere_bed(nsph):
+    """64x64x96 column, a bubble r=8 and nsph free spheres r=4 (seed 5)"""
+    dims = (64, 64, 96)
+    bubbles = [W.Bubble((32.0, 32.0, 20.0), 8.0)]
+    spheres = W.place_spheres(W.SplitMix64(5), nsph, 4, 1.5, dims, bubbles)
+    return W.Workload(name="bed%d" % nsph, nx=64, ny=64, nz=96, tau=0.6, g=(0.0, 0.0, -2e-5), bubbles=bubbles,
+                      spheres=spheres)
+
+
+def test_lean_boundary_kernel_runs_and_steps_like_the_oracle(lbm):
+    """enough spheres that the liquid cells beside them (about 4 pi (R+1)^2 each) outnumber one
+    round of the general boundary kernel: they get the lean kernel, one more launch per step
+    than with fewer spheres, and a step from the GPU's state matches the oracle's"""
+    def per_step(wl):
+        sim = lbm.Sim(wl)
+        sim.step(1)
+        n1 = sim.launches()
+        sim.step(10)
+        return (sim.launches() - n1) // 10
+
+    assert per_step(_sphere_bed(150)) == per_step(_sphere_bed(100)) + 1
+    for pre in (0, 30):
+        _one_step_check(lbm, _sphere_bed(150), pre, 2e-6, 2e-6)
