@@ -98,15 +98,18 @@ __device__ inline void sph_contact_one(const Dev& d, const int P, const int t, c
             const double dd2 = (cq[0] - s.x[0]) * (cq[0] - s.x[0]) + (cq[1] - s.x[1]) * (cq[1] - s.x[1]) + (cq[2] - s.x[2]) * (cq[2] - s.x[2]);
             const double reach = s.R + o.R + 2.0;
             if (dd2 > reach * reach) continue;
+            // the box of the cells both within R_Q of Q's centre and within R_P + 1.5 of P's:
+            // the overlap of the two spheres' boxes (a cell or so thick where they nearly touch)
             int lo[3], ext[3];
             float oq[3], op[3];
+            int total = 1;
             for (int k = 0; k < 3; k++) {
-                lo[k] = (int)floor(cq[k] - o.R);
-                ext[k] = (int)ceil(cq[k] + o.R) - lo[k] + 1;
+                lo[k] = (int)floor(fmax(cq[k] - o.R, s.x[k] - (s.R + 1.5)));
+                ext[k] = max(0, (int)ceil(fmin(cq[k] + o.R, s.x[k] + (s.R + 1.5))) - lo[k] + 1);
                 oq[k] = (float)((double)lo[k] - cq[k]);
                 op[k] = (float)((double)lo[k] - s.x[k]);
+                total *= ext[k];
             }
-            const int total = ext[0] * ext[1] * ext[2];
             // a necessary condition only (the lattice's owners decide), with a margin for FP32
             const float RQ2 = (float)(o.R * o.R) + 0.01f, RP2 = (float)((s.R + 1.5) * (s.R + 1.5)) + 0.01f;
             for (int e = t; e < total; e += nt) {
@@ -513,7 +516,6 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int t, c
         if (t == 0) atomicOr(&d.sc->status, S_UNSTABLE);
         return;
     }
-    const int total = ext[0] * ext[1] * ext[2];
     const double R2 = s.R * s.R;
     // cell offsets from both centres in FP32 decide wherever |d^2 - R^2| clears their rounding
     // error by far; the few cells closer to the sphere's surface are decided in FP64
@@ -524,38 +526,41 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int t, c
     }
     // FP32 squared distances below ~50 carry an error under 1e-5 here
     const float R2f = (float)R2, band = 1e-4f * (1.f + R2f);
-    for (int e = t; e < total; e += nt) {
-        const int ex[3] = {e % ext[0], (e / ext[0]) % ext[1], e / (ext[0] * ext[1])};
-        int w[3] = {lo[0] + ex[0], lo[1] + ex[1], lo[2] + ex[2]};
-        float f0 = 0.f, f1 = 0.f;
-        for (int k = 0; k < 3; k++) {
-            const float a = a0[k] + (float)ex[k], b = a1[k] + (float)ex[k];
-            f0 += a * a;
-            f1 += b * b;
-        }
-        bool in0 = f0 <= R2f, in1 = f1 <= R2f;
-        if (fabsf(f0 - R2f) < band || fabsf(f1 - R2f) < band) {
-            double d0 = 0, d1 = 0;
+    // each thread takes columns (x, y) of the box and walks them along z
+    const int nxy = ext[0] * ext[1];
+    for (int exy = t; exy < nxy; exy += nt) {
+        const int ex0 = exy % ext[0], ex1 = exy / ext[0];
+        const float ax = a0[0] + (float)ex0, ay = a0[1] + (float)ex1;
+        const float bx = a1[0] + (float)ex0, by = a1[1] + (float)ex1;
+        const float pxy0 = ax * ax + ay * ay, pxy1 = bx * bx + by * by;
+        for (int ex2 = 0; ex2 < ext[2]; ex2++) {
+            int w[3] = {lo[0] + ex0, lo[1] + ex1, lo[2] + ex2};
+            const float az = a0[2] + (float)ex2, bz = a1[2] + (float)ex2;
+            const float f0 = pxy0 + az * az, f1 = pxy1 + bz * bz;
+            bool in0 = f0 <= R2f, in1 = f1 <= R2f;
+            if (fabsf(f0 - R2f) < band || fabsf(f1 - R2f) < band) {
+                double d0 = 0, d1 = 0;
+                for (int k = 0; k < 3; k++) {
+                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off[k]);
+                    d0 += a * a;
+                    d1 += b * b;
+                }
+                in0 = d0 <= R2;
+                in1 = d1 <= R2;
+            }
+            if (in0 == in1) continue;
+            bool ok = true;
             for (int k = 0; k < 3; k++) {
-                const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off[k]);
-                d0 += a * a;
-                d1 += b * b;
+                if (w[k] < 0 || w[k] >= L[k]) {
+                    if (!d.bc[k]) { ok = false; break; }
+                    w[k] = ((w[k] % L[k]) + L[k]) % L[k];
+                }
             }
-            in0 = d0 <= R2;
-            in1 = d1 <= R2;
+            if (!ok) continue;
+            const size_t i = cell_index(d, w[0], w[1], w[2]);
+            const uint8_t old = mark_or(d.tmark, i, K_TOUCH);
+            if (!(old & K_TOUCH)) wl_push(d.wl_touch, &d.sc->n_touch, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
         }
-        if (in0 == in1) continue;
-        bool ok = true;
-        for (int k = 0; k < 3; k++) {
-            if (w[k] < 0 || w[k] >= L[k]) {
-                if (!d.bc[k]) { ok = false; break; }
-                w[k] = ((w[k] % L[k]) + L[k]) % L[k];
-            }
-        }
-        if (!ok) continue;
-        const size_t i = cell_index(d, w[0], w[1], w[2]);
-        const uint8_t old = mark_or(d.tmark, i, K_TOUCH);
-        if (!(old & K_TOUCH)) wl_push(d.wl_touch, &d.sc->n_touch, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
     }
 }
 
