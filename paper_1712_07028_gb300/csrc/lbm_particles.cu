@@ -82,36 +82,54 @@ __device__ __forceinline__ void for_partners(const Dev& d, int P, const double* 
 // cells that can be such a node (covered by Q, within R_P + 1.5 of P) are read.
 // links between obstacle nodes of sphere P and of its partners, by a group of nt threads
 // (a multiple of 32; t the thread's index in the group); the group's sums go to F_P, T_P with
-// one FP64 atomic per warp
+// one FP64 atomic per warp that has a link.
+// The group is the whole block (its shared memory holds each partner's box, set up by one
+// thread: FP64 issue is scarce on this GPU, and every thread doing it cost more than the scan).
 __device__ inline void sph_contact_one(const Dev& d, const int P, const int t, const int nt) {
+    __shared__ int sTotal, sLo[3], sExt[3];
+    __shared__ float sOq[3], sOp[3], sRQ2, sRP2;
     const Sphere& s = d.sph[P];
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
     const int L[3] = {d.nx, d.ny, d.nz};
     const uint32_t np = min(d.npairs[P], (uint32_t)kPairCap);
-    if (finite3(s.x) && s.R > 0.0 && s.R < 64.0) {
-        for (uint32_t pk = 0; pk < np; pk++) {
-            const uint32_t Q = d.pairs[(size_t)P * kPairCap + pk];
-            const Sphere& o = d.sph[Q];
-            if (!finite3(o.x) || !(o.R > 0.0 && o.R < 64.0)) continue;
-            double cq[3];   // Q's centre, unwrapped next to P
-            for (int k = 0; k < 3; k++) cq[k] = s.x[k] + min_image(d, k, o.x[k], s.x[k]);
-            const double dd2 = (cq[0] - s.x[0]) * (cq[0] - s.x[0]) + (cq[1] - s.x[1]) * (cq[1] - s.x[1]) + (cq[2] - s.x[2]) * (cq[2] - s.x[2]);
-            const double reach = s.R + o.R + 2.0;
-            if (dd2 > reach * reach) continue;
-            // the box of the cells both within R_Q of Q's centre and within R_P + 1.5 of P's:
-            // the overlap of the two spheres' boxes (a cell or so thick where they nearly touch)
-            int lo[3], ext[3];
-            float oq[3], op[3];
-            int total = 1;
-            for (int k = 0; k < 3; k++) {
-                lo[k] = (int)floor(fmax(cq[k] - o.R, s.x[k] - (s.R + 1.5)));
-                ext[k] = max(0, (int)ceil(fmin(cq[k] + o.R, s.x[k] + (s.R + 1.5))) - lo[k] + 1);
-                oq[k] = (float)((double)lo[k] - cq[k]);
-                op[k] = (float)((double)lo[k] - s.x[k]);
-                total *= ext[k];
+    const bool valid = finite3(s.x) && s.R > 0.0 && s.R < 64.0;
+    for (uint32_t pk = 0; valid && pk < np; pk++) {
+        const uint32_t Q = d.pairs[(size_t)P * kPairCap + pk];
+        const Sphere& o = d.sph[Q];
+        if (t == 0) {
+            int total = 0;
+            if (finite3(o.x) && o.R > 0.0 && o.R < 64.0) {
+                double cq[3];   // Q's centre, unwrapped next to P
+                for (int k = 0; k < 3; k++) cq[k] = s.x[k] + min_image(d, k, o.x[k], s.x[k]);
+                const double dd2 = (cq[0] - s.x[0]) * (cq[0] - s.x[0]) + (cq[1] - s.x[1]) * (cq[1] - s.x[1]) + (cq[2] - s.x[2]) * (cq[2] - s.x[2]);
+                const double reach = s.R + o.R + 2.0;
+                if (dd2 <= reach * reach) {
+                    // the box of the cells both within R_Q of Q's centre and within R_P + 1.5 of
+                    // P's: the overlap of the two spheres' boxes (a cell or so thick where they
+                    // nearly touch)
+                    total = 1;
+                    for (int k = 0; k < 3; k++) {
+                        sLo[k] = (int)floor(fmax(cq[k] - o.R, s.x[k] - (s.R + 1.5)));
+                        sExt[k] = max(0, (int)ceil(fmin(cq[k] + o.R, s.x[k] + (s.R + 1.5))) - sLo[k] + 1);
+                        sOq[k] = (float)((double)sLo[k] - cq[k]);
+                        sOp[k] = (float)((double)sLo[k] - s.x[k]);
+                        total *= sExt[k];
+                    }
+                    // a necessary condition only (the lattice's owners decide), with a margin
+                    // for FP32
+                    sRQ2 = (float)(o.R * o.R) + 0.01f;
+                    sRP2 = (float)((s.R + 1.5) * (s.R + 1.5)) + 0.01f;
+                }
             }
-            // a necessary condition only (the lattice's owners decide), with a margin for FP32
-            const float RQ2 = (float)(o.R * o.R) + 0.01f, RP2 = (float)((s.R + 1.5) * (s.R + 1.5)) + 0.01f;
+            sTotal = total;
+        }
+        __syncthreads();
+        const int total = sTotal;
+        const int lo[3] = {sLo[0], sLo[1], sLo[2]}, ext[3] = {sExt[0], sExt[1], sExt[2]};
+        const float oq[3] = {sOq[0], sOq[1], sOq[2]}, op[3] = {sOp[0], sOp[1], sOp[2]};
+        const float RQ2 = sRQ2, RP2 = sRP2;
+        __syncthreads();   // thread 0 rewrites the box for the next partner
+        {
             for (int e = t; e < total; e += nt) {
                 const int ex[3] = {e % ext[0], (e / ext[0]) % ext[1], e / (ext[0] * ext[1])};
                 int w[3] = {lo[0] + ex[0], lo[1] + ex[1], lo[2] + ex[2]};
@@ -164,7 +182,9 @@ __device__ inline void sph_contact_one(const Dev& d, const int P, const int t, c
             }
         }
     }
-    if (np == 0) return;   // (uniform over the group)
+    // (uniform over each warp: only warps with a link sum)
+    const bool any = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0 || T[0] != 0.0 || T[1] != 0.0 || T[2] != 0.0;
+    if (np == 0 || !__any_sync(0xffffffffu, any)) return;
     const int lane = t & 31;
     double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
     for (int c = 0; c < 6; c++) v[c] = warp_sum(v[c]);
@@ -493,39 +513,47 @@ __global__ void sph_copy_kernel(const Dev d) {
 // sphere changed are touched (deduplicated into a worklist).
 // by a group of nt threads (t the thread's index in the group)
 __device__ inline void cover_touch_one(const Dev& d, const int P, const int t, const int nt) {
+    // the box and the cell offsets from both centres, set up by one thread (FP64 issue is
+    // scarce on this GPU: the whole block doing it cost more than the box scan)
+    __shared__ int sGo, sLo[3], sExt[3];
+    __shared__ float sA0[3], sA1[3], sR2f;
+    __shared__ double sOff[3];
     const Sphere& s = d.sph[P];
-    if (t == 0) d.sphl[P] = sph_link_of(s);   // the next sweep's link data
-    if (s.x[0] == s.x0[0] && s.x[1] == s.x0[1] && s.x[2] == s.x0[2]) return;
-    // a sphere whose centre is not finite or moved more than a cell in one step is left alone
-    // (the fluid has gone unstable; the status word says so)
-    if (!finite3(s.x) || !finite3(s.x0) || !(s.R > 0.0 && s.R < 64.0)) {
-        if (t == 0) atomicOr(&d.sc->status, S_UNSTABLE);
-        return;
+    if (t == 0) {
+        d.sphl[P] = sph_link_of(s);   // the next sweep's link data
+        int go = 0;
+        if (s.x[0] != s.x0[0] || s.x[1] != s.x0[1] || s.x[2] != s.x0[2]) {
+            // a sphere whose centre is not finite or moved more than a cell in one step is left
+            // alone (the fluid has gone unstable; the status word says so)
+            if (!finite3(s.x) || !finite3(s.x0) || !(s.R > 0.0 && s.R < 64.0)) {
+                atomicOr(&d.sc->status, S_UNSTABLE);
+            } else {
+                const int lim = 2 * (int)ceil(s.R) + 8;
+                go = 1;
+                for (int k = 0; k < 3; k++) {
+                    sOff[k] = min_image(d, k, s.x[k], s.x0[k]);   // new centre relative to the old
+                    const double a = s.x0[k], b = s.x0[k] + sOff[k];
+                    sLo[k] = (int)floor(fmin(a, b) - s.R) - 1;
+                    sExt[k] = (int)ceil(fmax(a, b) + s.R) + 1 - sLo[k] + 1;
+                    if (sExt[k] > lim) go = 0;
+                    sA0[k] = (float)((double)sLo[k] - s.x0[k]);
+                    sA1[k] = (float)((double)sLo[k] - (s.x0[k] + sOff[k]));
+                }
+                if (!go) atomicOr(&d.sc->status, S_UNSTABLE);
+                sR2f = (float)(s.R * s.R);
+            }
+        }
+        sGo = go;
     }
+    __syncthreads();
+    if (!sGo) return;
     const int L[3] = {d.nx, d.ny, d.nz};
-    int lo[3], ext[3];
-    double off[3];
-    for (int k = 0; k < 3; k++) {
-        off[k] = min_image(d, k, s.x[k], s.x0[k]);           // new centre relative to the old
-        const double a = s.x0[k], b = s.x0[k] + off[k];
-        lo[k] = (int)floor(fmin(a, b) - s.R) - 1;
-        ext[k] = (int)ceil(fmax(a, b) + s.R) + 1 - lo[k] + 1;
-    }
-    const int lim = 2 * (int)ceil(s.R) + 8;
-    if (ext[0] > lim || ext[1] > lim || ext[2] > lim) {
-        if (t == 0) atomicOr(&d.sc->status, S_UNSTABLE);
-        return;
-    }
-    const double R2 = s.R * s.R;
+    const int lo[3] = {sLo[0], sLo[1], sLo[2]}, ext[3] = {sExt[0], sExt[1], sExt[2]};
+    const float a0[3] = {sA0[0], sA0[1], sA0[2]}, a1[3] = {sA1[0], sA1[1], sA1[2]};
     // cell offsets from both centres in FP32 decide wherever |d^2 - R^2| clears their rounding
     // error by far; the few cells closer to the sphere's surface are decided in FP64
-    float a0[3], a1[3];
-    for (int k = 0; k < 3; k++) {
-        a0[k] = (float)((double)lo[k] - s.x0[k]);
-        a1[k] = (float)((double)lo[k] - (s.x0[k] + off[k]));
-    }
     // FP32 squared distances below ~50 carry an error under 1e-5 here
-    const float R2f = (float)R2, band = 1e-4f * (1.f + R2f);
+    const float R2f = sR2f, band = 1e-4f * (1.f + R2f);
     // each thread takes columns (x, y) of the box and walks them along z
     const int nxy = ext[0] * ext[1];
     for (int exy = t; exy < nxy; exy += nt) {
@@ -539,9 +567,10 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int t, c
             const float f0 = pxy0 + az * az, f1 = pxy1 + bz * bz;
             bool in0 = f0 <= R2f, in1 = f1 <= R2f;
             if (fabsf(f0 - R2f) < band || fabsf(f1 - R2f) < band) {
+                const double R2 = s.R * s.R;
                 double d0 = 0, d1 = 0;
                 for (int k = 0; k < 3; k++) {
-                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off[k]);
+                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + sOff[k]);
                     d0 += a * a;
                     d1 += b * b;
                 }

@@ -19,13 +19,14 @@
 //   and odd parts; u = (sum c f + rho g/2)/rho
 //   and the conversion candidates: phi >= 1 + eps (filled) / phi <= -eps (emptied).
 //
-// Two kernels share the work and run concurrently (two streams, forked and joined by events,
-// captured into the step's CUDA graph).  The bulk kernel streams and collides every liquid
-// cell whose 18 neighbours are liquid, interface or beyond a wall (wall links read the cell's
-// own opposite PDF by an index select), with few registers and no branches per link: it is
-// bound by HBM bandwidth.  Every other active cell is on a compact list built at the end of
-// the previous step (the end-of-step scan), which the boundary kernel processes with the full link logic: it is
-// bound by memory latency, so it hides under the bulk kernel.
+// The bulk kernel streams and collides every liquid cell whose 18 neighbours are liquid,
+// interface or beyond a wall (wall links read the cell's own opposite PDF by an index select),
+// with few registers and no branches per link: it is bound by HBM bandwidth, and runs beside
+// the previous step's end-of-step kernels.  Every other active cell is on a compact list built
+// at the end of the previous step (general and liquid segments), which the boundary kernel
+// processes with the full link logic once those kernels are done, beside the fix pass (and,
+// for long lists, a lean instance on the liquid segment; streams forked and joined by events,
+// captured into the step's CUDA graph): it is bound by memory latency and instruction issue.
 //
 // Sphere force and torque are reduced in FP64 without cancellation loss: per link the
 // momentum is split into the constant part -2 w_q c_q (accumulated exactly as integers,
@@ -305,7 +306,7 @@ __global__ void __launch_bounds__(128) sweep_fix_kernel(const Dev d, const int c
 // instances: the general one takes the general segment of the list (interface cells and cells
 // on a free-slip or open face); the lean one (Lean) the liquid segment, cells whose links are
 // streaming, wall and sphere links only (and gas links, should a gas cell sit beside one): no
-// mass exchange, no face links, a quarter of the registers, four times the resident warps.
+// mass exchange, no face links; 128 registers a thread against 200, twice the resident warps.
 template <int S, bool Lean>
 __global__ void __launch_bounds__(128, Lean ? 4 : 1) sweep_boundary_kernel(const Dev d, const int cur) {
     using T = typename Store<S>::T;
