@@ -32,7 +32,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per bulk-sweep launch on the 128^3 column from one ncu capture
 # (mean of three launches), with the hash of the sweep source it was taken on (null once the
 # kernel changes)
-NCU_TRAFFIC = {"sha1": "8bfe953ae9d792d56cd4e22675e2ba6be8d503b2", "bytes_per_launch": 268272555}
+NCU_TRAFFIC = {"sha1": "5a23cd3fe7c25872f45fdd3cabe33cd01537a433", "bytes_per_launch": 268223317}
 
 
 def _args():
