@@ -23,7 +23,9 @@ LIQ, IFACE, GAS, OBS = 1, 2, 4, 8
 S_X, S_U, S_W, S_R, S_RHO, S_F, S_T, S_FLUB, S_FP, S_TP, S_HASP, S_LEN = 0, 3, 6, 9, 10, 11, 14, 17, 20, 23, 26, 32
 B_C, B_R, B_V0, B_V, B_RHOG, B_ROOT, B_MG, B_LEN = 0, 3, 4, 5, 6, 7, 8, 10
 FACE_WALL, FACE_SLIP, FACE_OPEN = 0, 1, 2
-SC_POOL, SC_NIF, SC_SBB, SC_SCOV, SC_SUNC, SC_STEPS, SC_STATUS, SC_NMERGE, SC_LEN = 0, 1, 2, 3, 4, 5, 6, 7, 16
+SC_POOL, SC_NIF, SC_SBB, SC_SCOV, SC_SUNC, SC_STEPS, SC_STATUS, SC_NMERGE, SC_NBUB, SC_NSPLIT, SC_LEN = (
+    0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 16)
+ST_UNSTABLE, ST_BUBBLE_GONE, ST_SPLIT_FULL = 1, 2, 4
 
 
 def build(force: bool = False) -> str:
@@ -43,7 +45,8 @@ class _Params(ctypes.Structure):
                 ("nbub", ctypes.c_int32), ("nsph", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("g", ctypes.c_double * 3), ("sigma", ctypes.c_double),
                 ("rho_g0", ctypes.c_double), ("eps", ctypes.c_double), ("near_tol", ctypes.c_double),
-                ("face", ctypes.c_int32 * 6), ("hydrostatic", ctypes.c_int32)]
+                ("face", ctypes.c_int32 * 6), ("hydrostatic", ctypes.c_int32),
+                ("max_bub", ctypes.c_int32), ("split_every", ctypes.c_int32)]
 
 
 _P = ctypes.POINTER
@@ -73,6 +76,7 @@ def lib():
         _lib.orc_lubrication.argtypes = [pp, ps, _P(ctypes.c_double)]
         _lib.orc_curvature.argtypes = [pp, ps]
         _lib.orc_bubble_model.argtypes = [pp, ps]
+        _lib.orc_bubble_model_split.argtypes = [pp, ps]
         _lib.orc_velocity.argtypes = [ctypes.c_int, ctypes.c_int]
         _lib.orc_tangent_window.argtypes = [pp, ps, _P(ctypes.c_double), _P(ctypes.c_double), ctypes.c_double,
                                             _P(ctypes.c_double), _P(ctypes.c_double), ctypes.c_int,
@@ -104,13 +108,16 @@ class Sim:
 
     def __init__(self, wl=None, *, nx=None, ny=None, nz=None, tau=0.6, g=(0, 0, 0), bc=(0, 0, 0), sigma=0.0,
                  rho_g0=1.0, eps=0.0, near_tol=1e-4, n_substeps=10, sphere_mode=1, bubbles=(), spheres=(),
-                 open_top=False, hydrostatic=False, init=True):
+                 open_top=False, hydrostatic=False, max_bubbles=0, split_every=0, init=True):
         """bc per axis: 0 no-slip walls, 1 periodic, 2 free-slip walls; open_top: the +z face is
         open at the reference pressure; hydrostatic (open top only): start in hydrostatic
-        equilibrium"""
+        equilibrium; max_bubbles: rows of the bubble table (room for the bubbles splitting
+        makes); split_every > 0: bubbles split into their connected parts every split_every
+        steps"""
         if wl is not None:
             nx, ny, nz, tau, g, bc = wl.nx, wl.ny, wl.nz, wl.tau, wl.g, wl.bc
             open_top, hydrostatic = wl.open_top, wl.hydrostatic
+            max_bubbles, split_every = getattr(wl, "max_bubbles", 0), getattr(wl, "split_every", 0)
             sigma, rho_g0, eps, n_substeps, sphere_mode = wl.sigma, wl.rho_g0, wl.eps, wl.n_substeps, wl.sphere_mode
             bubbles = [(b.c[0], b.c[1], b.c[2], b.r) for b in wl.bubbles]
             spheres = [(s.x[0], s.x[1], s.x[2], s.r, s.rho, *s.u, *s.w) for s in wl.spheres]
@@ -132,6 +139,7 @@ class Sim:
             p.hydrostatic = 1
         p.n_substeps, p.sphere_mode = int(n_substeps), int(sphere_mode)
         p.nbub, p.nsph = len(bubbles), len(spheres)
+        p.max_bub, p.split_every = max(int(max_bubbles), len(bubbles)), int(split_every)
         p.tau, p.sigma, p.rho_g0, p.eps, p.near_tol = tau, sigma, rho_g0, eps, near_tol
         self.p = p
         N = self.N
@@ -146,7 +154,7 @@ class Sim:
         self.owner = np.full(self.shape, -1, np.int32)
         self.nown = np.zeros(self.shape, np.int32)
         self.near = np.zeros(self.shape, np.int32)
-        self.bub = np.zeros((max(1, len(bubbles)), B_LEN))
+        self.bub = np.zeros((max(1, len(bubbles), int(max_bubbles)), B_LEN))
         self.bub[:, B_ROOT] = np.arange(self.bub.shape[0])
         for b, (cx, cy, cz, r) in enumerate(bubbles):
             self.bub[b, B_C:B_C + 3] = (cx, cy, cz)
@@ -162,6 +170,7 @@ class Sim:
             self.sph[a, S_R] = r
             self.sph[a, S_RHO] = rho
         self.scal = np.zeros(SC_LEN)
+        self.scal[SC_NBUB] = len(bubbles)
         self._bind()
         if init:
             lib().orc_init(ctypes.byref(self.p), ctypes.byref(self.s))
@@ -201,8 +210,16 @@ class Sim:
     def curvature(self):
         lib().orc_curvature(ctypes.byref(self.p), ctypes.byref(self.s))
 
-    def bubble_model(self):
-        lib().orc_bubble_model(ctypes.byref(self.p), ctypes.byref(self.s))
+    def bubble_model(self, split=False):
+        """the bubble model on the current cells (volumes, gas densities, merging; with split,
+        splitting too)"""
+        f = lib().orc_bubble_model_split if split else lib().orc_bubble_model
+        f(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    @property
+    def n_bubbles(self) -> int:
+        """bubble ids in use (those given at the start and those splitting made)"""
+        return int(self.scal[SC_NBUB])
 
     def tangent_window(self, nsteps, dtau=0.0, dg=(0.0, 0.0, 0.0), jdir=(1.0, 0.0, 0.0)):
         """advance nsteps steps of the frozen liquid window with the derivative along
@@ -240,16 +257,16 @@ class Sim:
 
     @property
     def rho_gas(self):
-        return self.bub[: self.p.nbub, B_RHOG].copy()
+        return self.bub[: self.n_bubbles, B_RHOG].copy()
 
     @property
     def volumes(self):
-        return self.bub[: self.p.nbub, B_V].copy()
+        return self.bub[: self.n_bubbles, B_V].copy()
 
     @property
     def roots(self):
         """root id of each bubble id (the smallest id of the merged bubble it belongs to)"""
-        up = self.bub[: self.p.nbub, B_ROOT].astype(np.int64)
+        up = self.bub[: self.n_bubbles, B_ROOT].astype(np.int64)
         r = up.copy()
         for b in range(len(r)):
             while up[r[b]] != r[b]:

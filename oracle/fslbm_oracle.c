@@ -64,9 +64,10 @@ enum { S_X = 0, S_U = 3, S_W = 6, S_R = 9, S_RHO = 10, S_F = 11, S_T = 14, S_FLU
 /* bubble record layout, doubles */
 enum { B_C = 0, B_R = 3, B_V0 = 4, B_V = 5, B_RHOG = 6, B_ROOT = 7, B_MG = 8, B_LEN = 10 };
 /* scalar slots */
-enum { SC_POOL = 0, SC_NIF = 1, SC_SBB = 2, SC_SCOV = 3, SC_SUNC = 4, SC_STEPS = 5, SC_STATUS = 6, SC_NMERGE = 7, SC_LEN = 16 };
+enum { SC_POOL = 0, SC_NIF = 1, SC_SBB = 2, SC_SCOV = 3, SC_SUNC = 4, SC_STEPS = 5, SC_STATUS = 6, SC_NMERGE = 7,
+       SC_NBUB = 8, SC_NSPLIT = 9, SC_LEN = 16 };
 /* status bits */
-enum { ST_UNSTABLE = 1, ST_BUBBLE_GONE = 2 };
+enum { ST_UNSTABLE = 1, ST_BUBBLE_GONE = 2, ST_SPLIT_FULL = 4 };
 
 typedef struct {
     int32_t nx, ny, nz;
@@ -82,6 +83,8 @@ typedef struct {
     double near_tol;        /* band logged as "near a conversion threshold" */
     int32_t face[6];        /* faces -x,+x,-y,+y,-z,+z of non-periodic axes: FACE_* */
     int32_t hydrostatic;    /* 1 (open top only): start in hydrostatic equilibrium */
+    int32_t max_bub;        /* rows of the bubble table (>= nbub): room for bubbles made by splitting */
+    int32_t split_every;    /* > 0: bubbles split every split_every steps (R39); 0: never */
 } orc_params;
 
 /* face kinds (Fig. bubbleSetup): no-slip wall, free-slip wall, open at the reference pressure */
@@ -98,7 +101,7 @@ typedef struct {
     int32_t *owner;         /* [N] bubble id (gas / interface) or sphere id (obstacle), -1 none */
     int32_t *nown;          /* [N] scratch */
     int32_t *near;          /* [N] steps at which this interface cell was near a threshold */
-    double *bub;            /* [nbub][B_LEN] */
+    double *bub;            /* [max(nbub, max_bub)][B_LEN]; rows in use: scal[SC_NBUB] */
     double *sph;            /* [nsph][S_LEN] */
     double *scal;           /* [SC_LEN] */
 } orc_state;
@@ -106,6 +109,9 @@ typedef struct {
 /* ------------------------------------------------------------------------- helpers */
 
 static long ncell(const orc_params *p) { return (long)p->nx * p->ny * p->nz; }
+/* rows of the bubble table; ids at or above scal[SC_NBUB] (one past the highest id ever used)
+ * carry no cells */
+static int bub_cap(const orc_params *p) { return p->max_bub > p->nbub ? p->max_bub : p->nbub; }
 
 /* neighbour of (x,y,z) displaced by (dx,dy,dz); periodic axes wrap, wall axes give -1 */
 static long nbr(const orc_params *p, int x, int y, int z, int dx, int dy, int dz)
@@ -295,7 +301,9 @@ static void curvature(const orc_params *p, orc_state *s)
  * cell next to one of another bubble) they are one bubble from then on: the ids are joined,
  * the smaller id being the root of the merged bubble.  The merged bubble's gas mass is the sum
  * of the two, and so is its reference volume; its volume is the sum of its members' volumes.
- * Splitting is not modelled.
+ * With split_every > 0, every split_every steps a bubble whose gas and interface cells form
+ * several connected parts (the same D3Q19 adjacency that merges two bubbles) is split
+ * (split_bubbles below).
  *
  * V = #gas cells + sum over the interface cells of (1 - phi) of all ids of the bubble;
  * isothermal ideal gas of conserved mass m_g: rho_g = m_g / V, m_g = rho_g(0) V(0).  Every id
@@ -306,10 +314,12 @@ static int bubble_root(const orc_state *s, int b)
     return b;
 }
 
-static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
+static void split_bubbles(const orc_params *p, orc_state *s);
+
+static void bubble_model(const orc_params *p, orc_state *s, int set_reference, int split)
 {
     const long N = ncell(p);
-    const int nb = p->nbub;
+    const int nb = bub_cap(p);
     if (nb <= 0) {
         long nif = 0;
         for (long i = 0; i < N; i++) nif += (s->flag[i] & C_IF) != 0;
@@ -364,12 +374,136 @@ static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
         B[B_V] = Vr[r];
         if (Vr[r] > 0.0) {
             B[B_RHOG] = B[B_MG] / Vr[r];
-        } else {
+        } else if (B[B_MG] > 0.0) {   /* (a free record holds no gas) */
             s->scal[SC_STATUS] = (double)((int)s->scal[SC_STATUS] | ST_BUBBLE_GONE);
         }
     }
     free(own);
     free(Vr);
+    if (split) split_bubbles(p, s);
+}
+
+/* R39, splitting (the inverse of the merge above).  First every gas and interface cell takes
+ * the id of its bubble's root, so that a bubble carries one id; the ids then left without a
+ * cell are free (their records reset).  The cells of each bubble are grouped into connected
+ * parts: two cells are in the same part when they are D3Q19 neighbours (or are linked through
+ * a chain of such neighbours).  A part is found from its lowest cell index (scanning cells in
+ * index order), its volume V_c = #gas cells + sum of (1 - phi) over its interface cells.  If a
+ * bubble has several parts, the largest keeps the id (a tie goes to the part with the lower
+ * lowest index) and every other part, in the order of their lowest indices, becomes a new
+ * bubble with the lowest free id; its cells take that id.  Gas mass and reference volume are
+ * divided in proportion to the parts' volumes, so every part leaves with the gas density of
+ * the whole.  A part of zero volume (interface cells that are full) stays with its bubble, and
+ * so does a part for which no free id is left (the status says so). */
+typedef struct { long rep; int root; double V; } orc_part;
+
+static void split_bubbles(const orc_params *p, orc_state *s)
+{
+    const long N = ncell(p);
+    const int cap = bub_cap(p);
+    int32_t *part = s->nown;   /* scratch: the part of each gas / interface cell, -1 elsewhere */
+    long *stack = malloc(sizeof(long) * (size_t)N);
+    int *root = malloc(sizeof(int) * (size_t)cap), *used = calloc((size_t)cap, sizeof(int));
+    long nparts = 0, cparts = 64;
+    orc_part *P = malloc(sizeof(orc_part) * (size_t)cparts);
+    /* one id per bubble; ids without a cell are free */
+    for (int b = 0; b < cap; b++) root[b] = bubble_root(s, b);
+    for (long i = 0; i < N; i++) {
+        const int b = s->owner[i];
+        if (!(s->flag[i] & (C_IF | C_GAS)) || b < 0 || b >= cap) continue;
+        s->owner[i] = root[b];
+        used[root[b]] = 1;
+    }
+    for (int b = 0; b < cap; b++) {
+        if (used[b]) continue;
+        double *B = s->bub + (long)b * B_LEN;
+        for (int k = 0; k < B_LEN; k++) B[k] = 0.0;
+        B[B_ROOT] = (double)b;
+        B[B_RHOG] = p->rho_g0;
+    }
+    for (long i = 0; i < N; i++) part[i] = -1;
+    for (long i0 = 0; i0 < N; i0++) {
+        const int r = s->owner[i0];
+        if (!(s->flag[i0] & (C_IF | C_GAS)) || r < 0 || r >= cap || part[i0] >= 0) continue;
+        if (nparts == cparts) {
+            cparts *= 2;
+            P = realloc(P, sizeof(orc_part) * (size_t)cparts);
+        }
+        P[nparts].rep = i0;
+        P[nparts].root = r;
+        P[nparts].V = 0.0;
+        long top = 0;
+        stack[top++] = i0;
+        part[i0] = (int32_t)nparts;
+        while (top > 0) {   /* depth-first over the part */
+            const long i = stack[--top];
+            P[nparts].V += (s->flag[i] & C_GAS) ? 1.0 : 1.0 - s->phi[i];
+            int x, y, z;
+            cell_xyz(p, i, &x, &y, &z);
+            for (int q = 1; q < NQ; q++) {
+                const long j = nbr(p, x, y, z, CX[q], CY[q], CZ[q]);
+                if (j < 0 || part[j] >= 0 || !(s->flag[j] & (C_IF | C_GAS)) || s->owner[j] != r) continue;
+                part[j] = (int32_t)nparts;
+                stack[top++] = j;
+            }
+        }
+        nparts++;
+    }
+    int *newid = malloc(sizeof(int) * (size_t)(nparts > 0 ? nparts : 1));
+    for (long c = 0; c < nparts; c++) newid[c] = -1;
+    int next_free = 0;
+    for (long c = 0; c < nparts; c++) {
+        const int r = P[c].root;
+        /* the first part of bubble r in index order decides for all of r's parts */
+        int first = 1;
+        for (long e = 0; e < c; e++) first &= P[e].root != r;
+        if (!first) continue;
+        long keep = c;
+        double Vr = 0.0;
+        int count = 0;
+        for (long e = c; e < nparts; e++) {
+            if (P[e].root != r) continue;
+            count++;
+            Vr += P[e].V;
+            if (P[e].V > P[keep].V) keep = e;
+        }
+        if (count < 2 || !(Vr > 0.0)) continue;
+        double *R = s->bub + (long)r * B_LEN;
+        const double V0r = R[B_V0], mgr = R[B_MG];
+        double kept_share = 1.0;
+        for (long e = c; e < nparts; e++) {
+            if (P[e].root != r || e == keep || !(P[e].V > 0.0)) continue;
+            while (next_free < cap && used[next_free]) next_free++;
+            if (next_free >= cap) {
+                s->scal[SC_STATUS] = (double)((int)s->scal[SC_STATUS] | ST_SPLIT_FULL);
+                continue;
+            }
+            const int id = next_free;
+            used[id] = 1;
+            const double a = P[e].V / Vr;
+            double *F = s->bub + (long)id * B_LEN;
+            F[B_ROOT] = (double)id;
+            F[B_V0] = V0r * a;
+            F[B_MG] = mgr * a;
+            F[B_V] = P[e].V;
+            F[B_RHOG] = F[B_MG] / F[B_V];
+            newid[e] = id;
+            kept_share -= a;
+            if (id + 1 > (int)s->scal[SC_NBUB]) s->scal[SC_NBUB] = (double)(id + 1);
+            s->scal[SC_NSPLIT] += 1.0;
+        }
+        R[B_V0] = V0r * kept_share;
+        R[B_MG] = mgr * kept_share;
+        R[B_V] = Vr * kept_share;
+        if (R[B_V] > 0.0) R[B_RHOG] = R[B_MG] / R[B_V];
+    }
+    for (long i = 0; i < N; i++)
+        if (part[i] >= 0 && newid[part[i]] >= 0) s->owner[i] = newid[part[i]];
+    free(newid);
+    free(P);
+    free(used);
+    free(root);
+    free(stack);
 }
 
 /* ------------------------------------------------------------------ step 1: the sweep */
@@ -382,7 +516,7 @@ static void bubble_model(const orc_params *p, orc_state *s, int set_reference)
 static void gas_on_spheres(const orc_params *p, orc_state *s, int x, int y, int z, long i)
 {
     const int b = s->owner[i];
-    const double rg = (b >= 0 && b < p->nbub) ? s->bub[(long)b * B_LEN + B_RHOG] : p->rho_g0;
+    const double rg = (b >= 0 && b < bub_cap(p)) ? s->bub[(long)b * B_LEN + B_RHOG] : p->rho_g0;
     const double xc[3] = {(double)x, (double)y, (double)z};
     for (int q = 1; q < NQ; q++) {
         const long src = nbr(p, x, y, z, -CX[q], -CY[q], -CZ[q]);
@@ -459,7 +593,7 @@ static void sweep(const orc_params *p, orc_state *s, double share)
                         if (t & C_LIQ) s->scal[SC_SBB] += 6.0 * wq(q) * rho0 * cu;
                     } else {                             /* gas: Eq. fsk */
                         const int b = s->owner[src];
-                        const double rg = (b >= 0 && b < p->nbub) ? s->bub[(long)b * B_LEN + B_RHOG] : p->rho_g0;
+                        const double rg = (b >= 0 && b < bub_cap(p)) ? s->bub[(long)b * B_LEN + B_RHOG] : p->rho_g0;
                         const double rw = rg + 6.0 * p->sigma * s->kappa[i];
                         fin[q] = -fo[opp(q)] + 2.0 * equi_even(q, rw, u0);
                     }
@@ -909,7 +1043,7 @@ static double rho_initial(const orc_params *p, int z)
 int orc_init(const orc_params *p, orc_state *s)
 {
     const long N = ncell(p);
-    for (int b = 0; b < p->nbub; b++) s->bub[b * B_LEN + B_ROOT] = (double)b;
+    for (int b = 0; b < bub_cap(p); b++) s->bub[b * B_LEN + B_ROOT] = (double)b;
     for (int z = 0; z < p->nz; z++)
         for (int y = 0; y < p->ny; y++)
             for (int x = 0; x < p->nx; x++) {
@@ -980,7 +1114,8 @@ int orc_init(const orc_params *p, orc_state *s)
                 }
     }
     for (int k = 0; k < SC_LEN; k++) s->scal[k] = 0.0;
-    bubble_model(p, s, 1);
+    s->scal[SC_NBUB] = (double)p->nbub;
+    bubble_model(p, s, 1, 0);
     if (p->sigma > 0.0) curvature(p, s);
     return 0;
 }
@@ -1011,7 +1146,9 @@ int orc_step(const orc_params *p, orc_state *s, int nsteps)
         move_spheres(p, s);
         for (int a = 0; a < p->nsph; a++) s->sph[(long)a * S_LEN + S_HASP] = 1.0;
         if (p->sphere_mode != 0 && p->nsph > 0) cover_uncover(p, s); /* 4 */
-        bubble_model(p, s, 0);                                     /* 5 */
+        /* (R39: every split_every steps the bubbles split into their connected parts) */
+        const int split = p->split_every > 0 && ((long)s->scal[SC_STEPS] + 1) % p->split_every == 0;
+        bubble_model(p, s, 0, split);                              /* 5 */
         if (p->sigma > 0.0) curvature(p, s);                       /* 6 */
         s->scal[SC_STEPS] += 1.0;
     }
@@ -1057,7 +1194,8 @@ double orc_lambda_minus(double tau)
 }
 void orc_lubrication(const orc_params *p, orc_state *s, double *Fl) { lubrication(p, s, Fl); }
 void orc_curvature(const orc_params *p, orc_state *s) { curvature(p, s); }
-void orc_bubble_model(const orc_params *p, orc_state *s) { bubble_model(p, s, 0); }
+void orc_bubble_model(const orc_params *p, orc_state *s) { bubble_model(p, s, 0, 0); }
+void orc_bubble_model_split(const orc_params *p, orc_state *s) { bubble_model(p, s, 0, 1); }
 int orc_velocity(int q, int k) { return k == 0 ? CX[q] : (k == 1 ? CY[q] : CZ[q]); }
 
 /* ------------------------------------------------ tangent-linear (forward-mode) gradient */

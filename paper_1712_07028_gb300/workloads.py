@@ -70,6 +70,8 @@ class Workload:
     bc: Tuple[int, int, int] = (WALL, WALL, WALL)
     open_top: bool = False      # the +z face an open boundary at the reference pressure
     hydrostatic: bool = False   # (open top only) start in hydrostatic equilibrium
+    split_every: int = 0        # > 0: bubbles split into their connected parts every so many steps
+    max_bubbles: int = 0        # rows of the bubble table (0: the given bubbles); room for splits
     sigma: float = 0.0
     rho_g0: float = 1.0
     eps: float = 0.0

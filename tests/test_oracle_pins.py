@@ -606,3 +606,119 @@ def test_gas_pressure_on_a_sphere(orc, where):
         # liquid above the sphere, gas below it
         assert ((o.flag == orc.LIQ) | (o.flag == orc.IFACE))[17:21, 12, 12].all()
         assert (o.flag == orc.GAS)[4:8, 12, 12].all()
+
+
+def _two_parts_one_bubble(orc, r0, r1, c1=17.0, max_bubbles=4, nx=26):
+    """two separate bubbles (radii r0 at x = 7, r1 at x = c1) made into one bubble with two
+    disconnected parts, as a merge leaves them: id 1 joined to root 0, the root holding the sum
+    of the reference volumes and gas masses"""
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.Workload(name="parts", nx=nx, ny=16, nz=16, tau=0.7, g=(0, 0, 0), sphere_mode=W.SPHERES_FIXED,
+                    bubbles=[W.Bubble((7.0, 8.0, 8.0), r0), W.Bubble((c1, 8.0, 8.0), r1)],
+                    max_bubbles=max_bubbles, split_every=0)
+    o = orc.Sim(wl)
+    V = [_gas_volume(orc, o, [b]) for b in range(2)]
+    o.bub[1, orc.B_ROOT] = 0
+    for b in range(2):
+        o.bub[b, orc.B_V0] = V[0] + V[1]
+        o.bub[b, orc.B_MG] = 1.3 * (V[0] + V[1])   # rho_g = 1.3
+    return o, V
+
+
+@pytest.mark.parametrize("r0,r1", [(3.0, 5.0), (5.0, 3.0)])
+def test_bubble_split_into_its_connected_parts(orc, r0, r1):
+    """R39: a bubble whose gas and interface cells form two connected parts is split.  Its cells
+    first take the root's id (id 1 is then free); the larger part keeps the root, the other
+    becomes a bubble with the lowest free id (1) and its cells are relabelled; gas mass and
+    reference volume go in proportion to the parts' volumes (counted here from the cell
+    fields), so both leave with the gas density of the whole."""
+    o, V = _two_parts_one_bubble(orc, r0, r1)
+    own0 = o.owner.copy()
+    o.bubble_model(split=True)
+    big, small = (1, 0) if V[1] > V[0] else (0, 1)
+    assert o.n_bubbles == 2 and o.scal[orc.SC_NSPLIT] == 1
+    assert list(o.roots) == [0, 1]
+    assert (o.owner[own0 == small] == 1).all() and (o.owner[own0 == big] == 0).all()
+    assert (o.owner[own0 < 0] == -1).all()
+    Vt = V[0] + V[1]
+    assert np.isclose(o.volumes[1], V[small], rtol=1e-13) and np.isclose(o.volumes[0], V[big], rtol=1e-13)
+    assert np.isclose(o.bub[1, orc.B_MG], 1.3 * V[small], rtol=1e-12)
+    assert np.isclose(o.bub[0, orc.B_MG], 1.3 * V[big], rtol=1e-12)
+    assert np.isclose(o.bub[1, orc.B_V0], V[small], rtol=1e-12)
+    assert np.allclose(o.rho_gas, 1.3, rtol=1e-12)
+    # the gas mass is conserved by the split
+    assert np.isclose(o.bub[0, orc.B_MG] + o.bub[1, orc.B_MG], 1.3 * Vt, rtol=1e-13)
+    assert int(o.scal[orc.SC_STATUS]) == 0
+
+
+def test_bubble_split_tie_and_full_table(orc):
+    """Two parts of equal volume (mirror images about x = 12.5): the part with the lower lowest
+    cell index (x = 7) keeps the root.  With no free row in the bubble table (two rows, both
+    bubbles holding cells) the parts stay one bubble and the status says so."""
+    o, V = _two_parts_one_bubble(orc, 4.0, 4.0, c1=18.0)
+    assert V[0] == V[1]
+    own0 = o.owner.copy()
+    o.bubble_model(split=True)
+    assert (o.owner[own0 == 0] == 0).all() and (o.owner[own0 == 1] == 1).all()
+    assert o.scal[orc.SC_NSPLIT] == 1
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.Workload(name="three", nx=30, ny=14, nz=14, tau=0.7, g=(0, 0, 0), sphere_mode=W.SPHERES_FIXED,
+                    bubbles=[W.Bubble((5.0, 7.0, 7.0), 3.0), W.Bubble((14.0, 7.0, 7.0), 3.0),
+                             W.Bubble((23.0, 7.0, 7.0), 3.0)])
+    o = orc.Sim(wl)
+    o.owner[o.owner == 2] = 0    # bubble 0 in two parts; the table cut to two rows
+    o.p.nbub = o.p.max_bub = 2
+    own0 = o.owner.copy()
+    o.bubble_model(split=True)
+    assert (o.owner == own0).all() and o.scal[orc.SC_NSPLIT] == 0
+    assert int(o.scal[orc.SC_STATUS]) & orc.ST_SPLIT_FULL
+
+
+def test_bubble_split_then_evolves_as_two_bubbles(orc):
+    """Splitting is the inverse of merging: after the split the state steps exactly like one
+    built with two bubbles of those cells, volumes and gas masses from the start (same fields,
+    same gas densities).  The parts start 6 cells apart and stay apart while their gas expands
+    from rho_g = 1.3 towards the liquid's pressure."""
+    o, V = _two_parts_one_bubble(orc, 3.0, 5.0, c1=21.0, nx=30)
+    o.bubble_model(split=True)
+    ref, _ = _two_parts_one_bubble(orc, 3.0, 5.0, c1=21.0, nx=30)
+    ref.bub[1, orc.B_ROOT] = 1   # two bubbles, each with its own mass and reference volume
+    for b in range(2):
+        ref.bub[b, orc.B_V0] = V[b]
+        ref.bub[b, orc.B_MG] = 1.3 * V[b]
+    ref.bubble_model()
+    o.p.split_every = ref.p.split_every = 1
+    o.step(30)
+    ref.step(30)
+    # ids differ (the small part is 1 in o, 0 in ref); compare fields and per-part densities
+    assert (o.flag == ref.flag).all()
+    assert np.abs(o.f - ref.f).max() < 1e-12 and np.abs(o.phi - ref.phi).max() < 1e-12
+    assert np.isclose(o.rho_gas[1], ref.rho_gas[0], rtol=1e-12) and np.isclose(o.rho_gas[0], ref.rho_gas[1], rtol=1e-12)
+    assert abs(o.rho_gas[0] - 1.3) > 1e-7   # the densities did move
+    assert o.scal[orc.SC_NSPLIT] == 1 and o.n_bubbles == 2 and o.scal[orc.SC_NMERGE] == 0
+
+
+def test_bubbles_pinching_off_and_merging_again(orc):
+    """A small bubble rising into a larger one: they merge, and the thin gas necks of the merged
+    region pinch off and touch again over the following steps.  Splitting every step, after
+    every step each bubble's cells form exactly one D3Q19-connected region (scipy's
+    18-connectivity labelling), the total gas mass is conserved, and the ids in use stay within
+    the table (8 rows) although merges and splits repeat."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.Workload(name="pinch", nx=20, ny=20, nz=56, tau=0.7, g=(0, 0, -3e-4), sphere_mode=W.SPHERES_FIXED,
+                    bubbles=[W.Bubble((10.0, 10.0, 24.0), 6.0), W.Bubble((10.0, 10.0, 12.0), 3.5)],
+                    split_every=1, max_bubbles=8)
+    o = orc.Sim(wl)
+    st = ndimage.generate_binary_structure(3, 2)
+    mg0 = o.bub[:2, orc.B_MG].sum()
+    for k in range(600):
+        o.step(1)
+        act = (o.flag & (orc.GAS | orc.IFACE)) != 0
+        live = [b for b in range(8) if (act & (o.owner == b)).any()]
+        for b in live:
+            assert o.roots[b] == b if b < o.n_bubbles else False
+            assert ndimage.label(act & (o.owner == b), st)[1] == 1, (k, b)
+        assert np.isclose(sum(o.bub[b, orc.B_MG] for b in live), mg0, rtol=1e-12), k
+        assert int(o.scal[orc.SC_STATUS]) == 0, k
+    assert o.scal[orc.SC_NMERGE] >= 2 and o.scal[orc.SC_NSPLIT] >= 2
