@@ -51,6 +51,9 @@ extern "C" {
 #define LBM_EOVERFLOW (-5)   /* a conversion worklist or a sphere bin overflowed */
 #define LBM_EMERGE (-6)      /* more distinct pairs of bubbles met in one step than the merge
                                 table holds (1024); the pairs beyond it were not merged */
+#define LBM_ESPLIT (-7)      /* a bubble could not be split: no free row in the bubble table, or
+                                more connected parts at a split step than the part table holds
+                                (4096); the parts stayed one bubble */
 
 /* per-axis boundary kind */
 #define LBM_BC_WALL 0        /* no-slip wall halfway beyond the outermost cells */
@@ -82,6 +85,7 @@ extern "C" {
 #define LBM_S_BUBBLE_GONE 4u     /* a bubble's volume reached zero */
 #define LBM_S_BIN_OVERFLOW 8u    /* more spheres in a neighbour-search bin than it holds */
 #define LBM_S_MERGE 64u          /* the merge table overflowed (see LBM_EMERGE) */
+#define LBM_S_SPLIT 128u         /* a bubble could not be split (see LBM_ESPLIT) */
 #define LBM_S_FAST_SPHERE 32u    /* a sphere moved more than a quarter cell in one step (the
                                     per-step partner searches assume less) */
 
@@ -110,6 +114,18 @@ typedef struct lbm_params {
                                   bubble's gas at the liquid's pressure at its centre plus the
                                   Laplace jump 2 sigma / r (rho_gas0 is then unused); 0: rho = 1
                                   and the gas at rho_gas0 */
+    int32_t split_every;       /* > 0: every split_every steps, at the end of the step, bubbles
+                                  split into their connected parts (a bubble is a connected gas
+                                  region, Sec. 2.2): every gas / interface cell first takes its
+                                  bubble's root id (ids left without cells become free rows);
+                                  a bubble whose cells form several D3Q19-connected parts keeps
+                                  its largest part (equal volumes to within 1e-9: the part with
+                                  the lowest cell index) and every other part of non-zero volume,
+                                  in the order of the parts' lowest cell indices, becomes a
+                                  bubble with the lowest free id, gas mass and reference volume
+                                  divided in proportion to the parts' volumes (the gas density
+                                  carries over).  Bubble ids then range over the whole table
+                                  (max_bubbles rows).  0: bubbles never split. */
 } lbm_params;
 
 typedef struct lbm_ctx lbm_ctx;
@@ -176,6 +192,12 @@ int lbm_bubbles(lbm_ctx* ctx, double* V0, double* V, double* rho_g, int n);
  * each belongs to, itself if it never merged -- and the number of merges so far (*n_merges,
  * NULL allowed).  Synchronises. */
 int lbm_bubble_roots(lbm_ctx* ctx, int32_t* root, int n, int* n_merges);
+
+/* With splitting on (lbm_params.split_every > 0): *n_ids (NULL allowed) one past the highest
+ * bubble id that ever carried cells -- lbm_bubbles and lbm_bubble_roots take n up to
+ * max_bubbles -- and *n_splits (NULL allowed) the parts split off so far.  Without splitting
+ * *n_ids is the number of bubbles added and *n_splits 0.  Synchronises. */
+int lbm_bubble_splits(lbm_ctx* ctx, int* n_ids, int* n_splits);
 
 /* Macroscopic fields into caller device buffers (any may be NULL): rho[N] and u[3][N]
  * (post-collision moments, u = (sum c f* - rho g / 2) / rho, the velocity the collision

@@ -389,9 +389,11 @@ static void bubble_model(const orc_params *p, orc_state *s, int set_reference, i
  * parts: two cells are in the same part when they are D3Q19 neighbours (or are linked through
  * a chain of such neighbours).  A part is found from its lowest cell index (scanning cells in
  * index order), its volume V_c = #gas cells + sum of (1 - phi) over its interface cells.  If a
- * bubble has several parts, the largest keeps the id (a tie goes to the part with the lower
- * lowest index) and every other part, in the order of their lowest indices, becomes a new
- * bubble with the lowest free id; its cells take that id.  Gas mass and reference volume are
+ * bubble has several parts, the largest keeps the id (volumes equal to within 1e-9 of each
+ * other count as a tie, which goes to the part with the lower lowest index: a sum's rounding
+ * depends on its order) and every other part, in the order of their lowest indices, becomes a new
+ * bubble with the lowest free id (bubbles taken in increasing id order); its cells take that
+ * id.  Gas mass and reference volume are
  * divided in proportion to the parts' volumes, so every part leaves with the gas density of
  * the whole.  A part of zero volume (interface cells that are full) stays with its bubble, and
  * so does a part for which no free id is left (the status says so). */
@@ -452,12 +454,11 @@ static void split_bubbles(const orc_params *p, orc_state *s)
     int *newid = malloc(sizeof(int) * (size_t)(nparts > 0 ? nparts : 1));
     for (long c = 0; c < nparts; c++) newid[c] = -1;
     int next_free = 0;
-    for (long c = 0; c < nparts; c++) {
-        const int r = P[c].root;
-        /* the first part of bubble r in index order decides for all of r's parts */
-        int first = 1;
-        for (long e = 0; e < c; e++) first &= P[e].root != r;
-        if (!first) continue;
+    for (int r = 0; r < cap; r++) {   /* bubbles in increasing id order */
+        long c = -1;   /* r's first part */
+        for (long e = 0; e < nparts && c < 0; e++)
+            if (P[e].root == r) c = e;
+        if (c < 0) continue;
         long keep = c;
         double Vr = 0.0;
         int count = 0;
@@ -465,7 +466,7 @@ static void split_bubbles(const orc_params *p, orc_state *s)
             if (P[e].root != r) continue;
             count++;
             Vr += P[e].V;
-            if (P[e].V > P[keep].V) keep = e;
+            if (P[e].V > P[keep].V * (1.0 + 1e-9)) keep = e;   /* (equal to 1e-9: lower index) */
         }
         if (count < 2 || !(Vr > 0.0)) continue;
         double *R = s->bub + (long)r * B_LEN;

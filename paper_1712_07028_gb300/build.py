@@ -12,7 +12,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "liblbm_gb300.so")
-SOURCES = ["lbm_sweep.cu", "lbm_surface.cu", "lbm_particles.cu", "lbm_capi.cu", "lbm_noalloc.cu", "lbm_adjoint.cu"]
+SOURCES = ["lbm_sweep.cu", "lbm_surface.cu", "lbm_particles.cu", "lbm_capi.cu", "lbm_noalloc.cu", "lbm_adjoint.cu",
+           "lbm_split.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

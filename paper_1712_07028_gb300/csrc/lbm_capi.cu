@@ -76,6 +76,7 @@ int check_params(const lbm_params* p) {
         if (p->bc[k] != LBM_BC_WALL && p->bc[k] != LBM_BC_PERIODIC && p->bc[k] != LBM_BC_FREESLIP) return LBM_EINVAL;
     if (p->open_top != 0 && (p->open_top != 1 || p->bc[2] == LBM_BC_PERIODIC)) return LBM_EINVAL;
     if (p->hydrostatic != 0 && (p->hydrostatic != 1 || !p->open_top)) return LBM_EINVAL;
+    if (p->split_every < 0) return LBM_EINVAL;
     if (p->storage < LBM_STORE_F32 || p->storage > LBM_STORE_BF16DEV) return LBM_EINVAL;
     if (p->n_substeps < 1 || p->n_substeps > 64) return LBM_EINVAL;
     if (p->sphere_mode < LBM_SPHERES_FIXED || p->sphere_mode > LBM_SPHERES_PRESCRIBED) return LBM_EINVAL;
@@ -89,7 +90,7 @@ size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 :
 
 struct Layout {
     size_t f[2], flags, mark, tmark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
-        adj_srho, adj_part, merge_keys, merge_list, total;
+        adj_srho, adj_part, merge_keys, merge_list, lab, part_key, part_root, part_V, part_new, bub_cnt, total;
     size_t N, wl_cap, nbins_max;
 };
 
@@ -130,6 +131,14 @@ Layout layout_of(const lbm_params* p) {
     L.adj_part = take(sizeof(double) * 5 * kAdjSlots);
     L.merge_keys = take(sizeof(unsigned long long) * kMergeCap);
     L.merge_list = take(sizeof(uint32_t) * kMergeCap);
+    if (p->split_every > 0) {   // bubble splitting: union-find labels, the part table, counts per id
+        L.lab = take(4 * L.N);
+        L.part_key = take(sizeof(uint32_t) * kPartCap);
+        L.part_root = take(sizeof(uint32_t) * kPartCap);
+        L.part_V = take(sizeof(double) * kPartCap);
+        L.part_new = take(sizeof(int32_t) * kPartCap);
+        L.bub_cnt = take(sizeof(uint32_t) * (size_t)p->max_bubbles);
+    }
     L.total = o;
     return L;
 }
@@ -148,6 +157,7 @@ int launched(lbm_ctx* c, int n) {
 int status_code(uint32_t st) {
     if (st & S_UNSTABLE) return LBM_EUNSTABLE;
     if (st & (S_OVERFLOW | S_BIN_OVERFLOW)) return LBM_EOVERFLOW;
+    if (st & S_SPLIT) return LBM_ESPLIT;
     if (st & S_MERGE) return LBM_EMERGE;
     return LBM_OK;
 }
@@ -184,6 +194,7 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
         cudaStreamWaitEvent(e, c->join4, 0);
     }
     launch_spheres_cover(d, g, e);
+    launch_split(d, g, e);   // (split steps only; the step is closed)
     // the next step's partner lists and obstacle-node links need only the moved spheres, their
     // bins and obstacle cells, all final now: they run beside the rest of these kernels and
     // the next bulk sweep, and the next step's sweep joins them
@@ -198,7 +209,9 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
     launch_list_rescan(d, e);   // the next boundary sweep's list, from the final types
 }
 
-int epilogue_launches(const Dev& d) { return 1 + spheres_launches(d) + (d.kappa ? 1 : 0) + 1; }
+int epilogue_launches(const Dev& d) {
+    return 1 + spheres_launches(d) + (d.kappa ? 1 : 0) + 1 + (d.split_every > 0 ? kSplitLaunches : 0);
+}
 int step_launches(const Dev& d, bool overlap) {
     return 3 + d.split_liq + spheres_links_launches(d) + (overlap ? epilogue_launches(d) : 0);
 }
@@ -277,7 +290,10 @@ int first_step(lbm_ctx* c) {
     d.storage = p->storage;
     d.n_sub = p->n_substeps;
     d.sphere_mode = p->sphere_mode;
-    d.nbub = (int)(c->bub_geo.size() / 4);
+    d.ngeo = (int)(c->bub_geo.size() / 4);
+    d.split_every = p->split_every;
+    // with splitting, new bubbles take free rows: every row of the table is a bubble id
+    d.nbub = p->split_every > 0 ? std::max(p->max_bubbles, d.ngeo) : d.ngeo;
     d.nsph = (int)c->sph_init.size();
     {   // the liquid cells beside the spheres, about 4 pi (R + 1)^2 each: the lean kernel pays
         // for its extra graph branch once they outnumber one round of the general grid
@@ -333,6 +349,14 @@ int first_step(lbm_ctx* c) {
     d.pairs = (uint32_t*)(a + L.pairs);
     d.merge_keys = (unsigned long long*)(a + L.merge_keys);
     d.merge_list = (uint32_t*)(a + L.merge_list);
+    if (p->split_every > 0) {
+        d.lab = (uint32_t*)(a + L.lab);
+        d.part_key = (uint32_t*)(a + L.part_key);
+        d.part_root = (uint32_t*)(a + L.part_root);
+        d.part_V = (double*)(a + L.part_V);
+        d.part_new = (int32_t*)(a + L.part_new);
+        d.bub_cnt = (uint32_t*)(a + L.bub_cnt);
+    }
     c->geo_dev = (double*)(a + L.geo);
     c->adj_srho = (float*)(a + L.adj_srho);
     c->adj_part = (double*)(a + L.adj_part);
@@ -597,6 +621,18 @@ int lbm_bubble_roots(lbm_ctx* c, int32_t* root, int n, int* n_merges) {
     return LBM_OK;
 }
 
+
+int lbm_bubble_splits(lbm_ctx* c, int* n_ids, int* n_splits) {
+    if (!c) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
+    int rc = sync_tables(c);
+    if (rc) return rc;
+    if (n_ids) *n_ids = c->d.split_every > 0 ? (int)c->sc_stage->nbub_hw : c->d.nbub;
+    if (n_splits) *n_splits = (int)c->sc_stage->n_split;
+    return LBM_OK;
+}
+
 int lbm_fields(lbm_ctx* c, float* rho, float* u, float* phi, uint8_t* flags) {
     if (!c) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;
@@ -765,6 +801,7 @@ const char* lbm_strerror(int code) {
         case LBM_EUNSTABLE: return "density became non-positive or NaN";
         case LBM_EOVERFLOW: return "worklist or neighbour bin overflow";
         case LBM_EMERGE: return "more pairs of bubbles met in one step than the merge table holds";
+        case LBM_ESPLIT: return "a bubble could not be split (no free row in the bubble table, or the part table is full)";
         default: return "unknown error";
     }
 }

@@ -127,6 +127,8 @@ struct Bubble {
 static_assert(sizeof(Bubble) == 80, "bubble record size");
 // distinct pairs of bubbles that may meet in one step (open-addressing table of pairs)
 constexpr int kMergeCap = 1024;
+// connected parts of bubbles one split step can handle (open-addressing table)
+constexpr int kPartCap = 4096;
 struct Scalars {
     double pool;          // excess mass waiting to be spread over the interface cells
     double pool_acc;      // excess of this step that found no receiving neighbour
@@ -149,11 +151,15 @@ struct Scalars {
     uint32_t merged;      // some bubbles have merged: the close sums volumes per root
     uint32_t vpar;        // which Vtot slot the next close sums into
     uint32_t n_merges;    // merges so far
+    uint32_t steps;       // steps closed so far (the split schedule)
+    uint32_t n_split;     // parts split off so far
+    uint32_t nbub_hw;     // one past the highest bubble id that ever carried cells
+    uint32_t split_fail;  // this split step cannot split (part table full, or a find ran too long)
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
 enum : uint32_t { S_UNSTABLE = 1, S_OVERFLOW = 2, S_BUBBLE_GONE = 4, S_BIN_OVERFLOW = 8, S_BAD_OWNER = 16, S_FAST_SPHERE = 32,
-                  S_MERGE = 64 };
+                  S_MERGE = 64, S_SPLIT = 128 };
 
 // all device pointers of one simulation; passed by value to every kernel
 struct Dev {
@@ -162,6 +168,15 @@ struct Dev {
     uint8_t face[6];          // faces -x, +x, -y, +y, -z, +z of non-periodic axes: FACE_*
     int special;              // some face is free-slip or open
     int split_liq;            // the liquid boundary segment has its own (lean) sweep kernel
+    int ngeo;                 // bubbles given at the start (their geometry); nbub is the table's
+                              // size when bubbles split, else ngeo
+    int split_every;          // > 0: bubbles split into their connected parts every so many steps
+    uint32_t* lab;            // [N] (splitting only) union-find labels of gas / interface cells
+    uint32_t* part_key;       // [kPartCap] (splitting only) lowest cell index + 1 of each part, 0 free
+    uint32_t* part_root;      // [kPartCap] the part's bubble
+    double* part_V;           // [kPartCap] the part's volume
+    int32_t* part_new;        // [kPartCap] the id the part's cells take, -1: they keep theirs
+    uint32_t* bub_cnt;        // [nbub] (splitting only) gas / interface cells per id
     int hydrostatic;          // the liquid starts in hydrostatic equilibrium below the open top
     double gz;                // g_z in FP64 (the hydrostatic start)
     size_t N;
@@ -624,7 +639,7 @@ __device__ inline void bubbles_close(const Dev& d, const uint32_t t, const uint3
             B.V = V;
             if (init) { B.V0 = V; B.mg = B.rho_g * V; }
             else if (V > 0.0) B.rho_g = B.mg / V;
-            else atomicOr(&c.status, S_BUBBLE_GONE);
+            else if (B.mg > 0.0) atomicOr(&c.status, S_BUBBLE_GONE);   // (a free row holds no gas)
             B.rho_gf = (float)B.rho_g;
             B.Vif = 0.0;
         }
@@ -652,7 +667,7 @@ __device__ inline void bubbles_close(const Dev& d, const uint32_t t, const uint3
         B.V0 = __ldcg(&R.V0);
         B.mg = __ldcg(&R.mg);
         if (V > 0.0) B.rho_g = B.mg / V;
-        else atomicOr(&c.status, S_BUBBLE_GONE);
+        else if (B.mg > 0.0) atomicOr(&c.status, S_BUBBLE_GONE);
         B.rho_gf = (float)B.rho_g;
     }
     if (t == 0) c.vpar = par ^ 1u;
@@ -675,6 +690,7 @@ __device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t
         c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
         c.n_slow = 0;   // the boundary sweep has consumed its list; the list pass refills it
         c.n_liq = 0;
+        c.steps++;
     }
     if (bin_spheres)
         for (uint32_t P = t; P < (uint32_t)d.nsph; P += nt) {
@@ -691,6 +707,8 @@ void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side,
                        cudaEvent_t join, cudaEvent_t join2);
 
 void launch_conversions(const Dev& d, int nxt, bool close, cudaStream_t s);
+void launch_split(const Dev& d, int g, cudaStream_t s);
+constexpr int kSplitLaunches = 6;
 void launch_init_scan(const Dev& d, cudaStream_t s);
 void launch_list_rescan(const Dev& d, cudaStream_t s);
 void launch_curvature(const Dev& d, int nxt, cudaStream_t s);

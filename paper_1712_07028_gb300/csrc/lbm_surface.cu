@@ -330,7 +330,7 @@ void launch_curvature(const Dev& d, int nxt, cudaStream_t s) {
 __device__ void bubble_fill(const Dev& d, const double* geo, int x, int y, int z, float& ph, uint32_t& own) {
     double v = 1.0;
     own = kNone;
-    for (int b = 0; b < d.nbub; b++) {
+    for (int b = 0; b < d.ngeo; b++) {
         const double ddx = min_image(d, 0, (double)x, geo[4 * b + 0]);
         const double ddy = min_image(d, 1, (double)y, geo[4 * b + 1]);
         const double ddz = min_image(d, 2, (double)z, geo[4 * b + 2]);
@@ -348,12 +348,15 @@ __global__ void init_kernel(const Dev d, const double* geo) {
     T* f = static_cast<T*>(d.f[0]);
     // every bubble its own root; its initial gas density: rho_gas0, or (hydrostatic start) the
     // liquid's pressure at its centre plus the Laplace jump 2 sigma / r, as a density (p = rho/3)
+    // (rows beyond the given bubbles, room for splitting, start free: no cells, no gas)
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < d.nbub; b += gridDim.x * blockDim.x) {
         d.bub[b].root = b;
-        d.bub[b].rho_g = d.hydrostatic ? exp(3.0 * d.gz * (geo[4 * b + 2] - (d.nz - 0.5))) + 6.0 * (double)d.sigma / geo[4 * b + 3]
-                                       : (double)d.rho_g0;
+        d.bub[b].rho_g = d.hydrostatic && b < d.ngeo
+                             ? exp(3.0 * d.gz * (geo[4 * b + 2] - (d.nz - 0.5))) + 6.0 * (double)d.sigma / geo[4 * b + 3]
+                             : (double)d.rho_g0;
         d.bub[b].rho_gf = (float)d.bub[b].rho_g;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) d.sc->nbub_hw = (uint32_t)d.ngeo;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
         cell_xyz(d, i, x, y, z);

@@ -16,13 +16,13 @@ from . import workloads as _wl
 
 _lib = None
 
-LBM_OK, LBM_EINVAL, LBM_ESTATE, LBM_ECUDA, LBM_EUNSTABLE, LBM_EOVERFLOW, LBM_EMERGE = 0, -1, -2, -3, -4, -5, -6
+LBM_OK, LBM_EINVAL, LBM_ESTATE, LBM_ECUDA, LBM_EUNSTABLE, LBM_EOVERFLOW, LBM_EMERGE, LBM_ESPLIT = 0, -1, -2, -3, -4, -5, -6, -7
 CELL_LIQUID, CELL_INTERFACE, CELL_GAS, CELL_OBSTACLE = 1, 2, 4, 8
-S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW, S_FAST_SPHERE, S_MERGE = 1, 2, 4, 8, 32, 64
+S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW, S_FAST_SPHERE, S_MERGE, S_SPLIT = 1, 2, 4, 8, 32, 64, 128
 
 # every entry point include/lbm.h declares
 EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_step",
-           "lbm_forces", "lbm_spheres", "lbm_bubbles", "lbm_bubble_roots", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
+           "lbm_forces", "lbm_spheres", "lbm_bubbles", "lbm_bubble_roots", "lbm_bubble_splits", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
            "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count",
            "lbm_bubble_volumes_noalloc", "lbm_forward_frozen", "lbm_adjoint_step", "lbm_destroy", "lbm_strerror")
 
@@ -33,7 +33,7 @@ class Params(ctypes.Structure):
                 ("max_bubbles", ctypes.c_int32), ("max_spheres", ctypes.c_int32), ("worklist_cap", ctypes.c_int32),
                 ("tau", ctypes.c_double), ("g", ctypes.c_double * 3), ("sigma", ctypes.c_double),
                 ("rho_gas0", ctypes.c_double), ("eps", ctypes.c_double), ("open_top", ctypes.c_int32),
-                ("hydrostatic", ctypes.c_int32)]
+                ("hydrostatic", ctypes.c_int32), ("split_every", ctypes.c_int32)]
 
 
 class LBMError(RuntimeError):
@@ -67,6 +67,7 @@ def load():
     L.lbm_spheres.argtypes = [vp, pd, pd, pd, i32]
     L.lbm_bubbles.argtypes = [vp, pd, pd, pd, i32]
     L.lbm_bubble_roots.argtypes = [vp, ctypes.POINTER(i32), i32, ctypes.POINTER(i32)]
+    L.lbm_bubble_splits.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
     L.lbm_fields.argtypes = [vp, vp, vp, vp, vp]
     L.lbm_export_state.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.lbm_mass_budget.argtypes = [vp, pd]
@@ -107,12 +108,13 @@ def make_params(wl: _wl.Workload, max_bubbles=None, max_spheres=None, worklist_c
     p.storage = _wl.STORAGE[wl.storage]
     p.n_substeps = int(wl.n_substeps)
     p.sphere_mode = int(wl.sphere_mode)
-    p.max_bubbles = int(max_bubbles or max(1, len(wl.bubbles)))
+    p.max_bubbles = int(max_bubbles or max(1, len(wl.bubbles), int(wl.max_bubbles)))
     p.max_spheres = int(max_spheres or max(1, len(wl.spheres)))
     p.worklist_cap = int(worklist_cap)
     p.tau, p.sigma, p.rho_gas0, p.eps = float(wl.tau), float(wl.sigma), float(wl.rho_g0), float(wl.eps)
     p.open_top = 1 if wl.open_top else 0
     p.hydrostatic = 1 if wl.hydrostatic else 0
+    p.split_every = int(wl.split_every)
     return p
 
 
@@ -142,7 +144,8 @@ class Sim:
             _check("lbm_add_sphere", L.lbm_add_sphere(self.ctx, _dp(_v3(s.x)), float(s.r), float(s.rho), _dp(_v3(s.u)),
                                                       _dp(_v3(s.w)), None))
         self.nsph = len(wl.spheres)
-        self.nbub = len(wl.bubbles)
+        # bubble ids: the bubbles given, or with splitting every row of the table
+        self.nbub = int(self.params.max_bubbles) if wl.split_every > 0 else len(wl.bubbles)
         self.steps_done = 0
 
     def _stream(self) -> int:
@@ -175,6 +178,13 @@ class Sim:
         V0, V, rg = (np.zeros(max(1, self.nbub)) for _ in range(3))
         _check("lbm_bubbles", load().lbm_bubbles(self.ctx, _dp(V0), _dp(V), _dp(rg), self.nbub))
         return V0[: self.nbub], V[: self.nbub], rg[: self.nbub]
+
+    def bubble_splits(self):
+        """(bubble ids in use: one past the highest id that carried cells, parts split off so far)"""
+        self._bind_stream()
+        n, ns = ctypes.c_int(0), ctypes.c_int(0)
+        _check("lbm_bubble_splits", load().lbm_bubble_splits(self.ctx, ctypes.byref(n), ctypes.byref(ns)))
+        return n.value, ns.value
 
     def bubble_roots(self):
         """(root id of every bubble id, number of merges so far)"""

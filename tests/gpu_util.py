@@ -20,9 +20,10 @@ def gpu_state(sim):
     x, u, w = sim.spheres()
     V0, V, rg = sim.bubbles()
     roots, n_merges = sim.bubble_roots()
+    n_ids, n_splits = sim.bubble_splits()
     M, sbb, scov, sunc, pool = sim.mass_budget()
     F, T = sim.forces()
-    st.update(sx=x, su=u, sw=w, V0=V0, V=V, rho_g=rg, roots=roots, n_merges=n_merges, pool=pool, F=F, T=T, steps=sim.steps_done)
+    st.update(sx=x, su=u, sw=w, V0=V0, V=V, rho_g=rg, roots=roots, n_merges=n_merges, n_ids=n_ids, n_splits=n_splits, pool=pool, F=F, T=T, steps=sim.steps_done)
     return st
 
 
@@ -35,12 +36,13 @@ def oracle_from_state(wl: W.Workload, st, near_tol=1e-5):
     o.phi[:] = st["phi"].astype(np.float64)
     o.owner[:] = st["owner"]
     o.kappa[:] = st["kappa"].astype(np.float64)
-    for b in range(len(wl.bubbles)):
+    for b in range(len(st["V0"])):   # (with splitting: every row of the table)
         o.bub[b, oracle.B_V0] = st["V0"][b]
         o.bub[b, oracle.B_V] = st["V"][b]
         o.bub[b, oracle.B_RHOG] = st["rho_g"][b]
         o.bub[b, oracle.B_ROOT] = st["roots"][b]
         o.bub[b, oracle.B_MG] = st["rho_g"][b] * st["V"][b]   # the conserved gas mass
+    o.scal[oracle.SC_NBUB] = st["n_ids"]
     for a in range(len(wl.spheres)):
         o.sph[a, oracle.S_X:oracle.S_X + 3] = st["sx"][a]
         o.sph[a, oracle.S_U:oracle.S_U + 3] = st["su"][a]

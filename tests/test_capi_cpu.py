@@ -38,10 +38,11 @@ def test_library_exports_every_declared_symbol(built):
 
 def test_params_layout_matches_header(built):
     from paper_1712_07028_gb300 import lbm
-    # 12 int32 fields, then 7 doubles, then open_top and hydrostatic
-    assert ctypes.sizeof(lbm.Params) == 12 * 4 + 7 * 8 + 2 * 4
+    # 12 int32 fields, then 7 doubles, then open_top, hydrostatic and split_every (padded to 8)
+    assert ctypes.sizeof(lbm.Params) == 12 * 4 + 7 * 8 + 4 * 4
     assert lbm.Params.tau.offset == 48
     assert lbm.Params.open_top.offset == 104 and lbm.Params.hydrostatic.offset == 108
+    assert lbm.Params.split_every.offset == 112
 
 
 def test_arena_size_and_argument_checks(built):
@@ -78,6 +79,18 @@ def test_arena_size_and_argument_checks(built):
     q = lbm.make_params(W.rising_bubble("B"))
     q.open_top = 0
     assert L.lbm_arena_bytes(ctypes.byref(q), ctypes.byref(n)) == lbm.LBM_EINVAL
+    # splitting: a negative interval is refused; the labels (4 B a cell) and the part table
+    # are in the arena only when bubbles split
+    q = lbm.make_params(W.column_c0())
+    q.split_every = -1
+    assert L.lbm_arena_bytes(ctypes.byref(q), ctypes.byref(n)) == lbm.LBM_EINVAL
+    q.split_every = 5
+    ns = ctypes.c_size_t()
+    assert L.lbm_arena_bytes(ctypes.byref(q), ctypes.byref(ns)) == 0
+    q.split_every = 0
+    assert L.lbm_arena_bytes(ctypes.byref(q), ctypes.byref(n)) == 0
+    assert ns.value >= n.value + 4 * 32 ** 3
+    assert L.lbm_strerror(lbm.LBM_ESPLIT).startswith(b"a bubble could not be split")
 
 
 def test_sim_refuses_without_gpu(built):
