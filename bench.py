@@ -242,6 +242,35 @@ def _storage_run(torch, lbm, args, storage):
             "bulk_kernel_ms": avg_s * 1e3, "rest_of_sweep_ms": rest_ms / max(1, nsw), "status": st}
 
 
+def _split_run(torch, lbm, args):
+    """step time of the benchmark workload with bubble splitting every step and every 10 steps
+    (the six labelling launches run on those steps; on the others they return at once), against
+    the same workload without splitting timed alongside"""
+    import dataclasses
+    out = {}
+    for every in (0, 1, 10):
+        wl = dataclasses.replace(_workload(args.workload), split_every=every, max_bubbles=16 if every else 0)
+        sim = lbm.Sim(wl)
+        sim.step(max(3, args.warmup))
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        n = min(args.steps, 2000)
+        e0.record(stream)
+        sim.step(n)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        out["every_%d" % every if every else "off"] = {"ms_per_step": ms, "status": sim.status(),
+                                                       "splits": sim.bubble_splits()[1] if every else 0}
+        sim.close()
+    off = out["off"]["ms_per_step"]
+    for k in ("every_1", "every_10"):
+        out[k]["overhead_ms"] = out[k]["ms_per_step"] - off
+    return out
+
+
 def _adjoint_run(torch, lbm, W, window=True, graphs=True):
     """the differentiation path on the 96^3 periodic array of 27 fixed spheres: per-launch
     time and HBM roofline of the frozen replay step and of the reverse step, and the wall time
@@ -456,6 +485,8 @@ def run_gpu(args):
         if rank == 0 and ws == 1:
             # the same workload with PDFs stored as FP16 / BF16 deviations (collisions in FP32)
             line["reduced_storage"] = {st: _storage_run(torch, lbm, args, st) for st in ("f16dev", "bf16dev")}
+            # bubble splitting (connected-component labelling) on the same workload
+            line["split"] = _split_run(torch, lbm, args)
             # the differentiation path (frozen liquid window) on its own workload
             line["adjoint"] = _adjoint_run(torch, lbm, W)
             # the CPU-baseline leg: the FP64 oracle timed on a bounded sample of the workload,
