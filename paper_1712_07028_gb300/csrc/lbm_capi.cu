@@ -33,8 +33,11 @@ struct lbm_ctx {
     Scalars* sc_stage;
     Bubble* bub_stage;
     // graph of two consecutive steps (cur = 0 then 1)
-    cudaGraphExec_t graph;
-    bool graph_ready;
+    // two overlapped steps as a CUDA graph; with bubble splitting one graph per combination of
+    // the two captured end-of-step passes splitting or not (bit 0: the first, bit 1: the second)
+    cudaGraphExec_t graph[4];
+    bool graph_ready[4];
+    uint64_t closed;   // end-of-step passes enqueued so far (the steps they close)
     bool use_graph;
     // optional timing of the sweep: CUDA events around the bulk kernel and around the rest
     // (fix pass + boundary kernel), on the library's stream
@@ -179,7 +182,10 @@ void prof_collect(lbm_ctx* c, int slot) {
 // end-of-step kernels of the step that wrote grid g (Sec. 2.2 conversions and bubble model,
 // Sec. 2.3 sphere motion and cover/uncover): the sphere motion on the side stream concurrent
 // with the conversions on `e`, then cover/uncover, the end-of-step scan and the curvature on `e`
-void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
+// the end-of-step pass that closes step k splits bubbles
+bool split_due_host(const lbm_ctx* c, uint64_t k) { return c->d.split_every > 0 && k % (uint64_t)c->d.split_every == 0; }
+
+void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e, bool split) {
     const Dev& d = c->d;
     if (d.nsph > 0) {
         cudaEventRecord(c->fork4, e);
@@ -194,7 +200,7 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
         cudaStreamWaitEvent(e, c->join4, 0);
     }
     launch_spheres_cover(d, g, e);
-    launch_split(d, g, e);   // (split steps only; the step is closed)
+    if (split) launch_split(d, g, e);   // (the step is closed)
     // the next step's partner lists and obstacle-node links need only the moved spheres, their
     // bins and obstacle cells, all final now: they run beside the rest of these kernels and
     // the next bulk sweep, and the next step's sweep joins them
@@ -209,18 +215,18 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e) {
     launch_list_rescan(d, e);   // the next boundary sweep's list, from the final types
 }
 
-int epilogue_launches(const Dev& d) {
-    return 1 + spheres_launches(d) + (d.kappa ? 1 : 0) + 1 + (d.split_every > 0 ? kSplitLaunches : 0);
+int epilogue_launches(const Dev& d, bool split) {
+    return 1 + spheres_launches(d) + (d.kappa ? 1 : 0) + 1 + (split ? kSplitLaunches : 0);
 }
-int step_launches(const Dev& d, bool overlap) {
-    return 3 + d.split_liq + spheres_links_launches(d) + (overlap ? epilogue_launches(d) : 0);
+int step_launches(const Dev& d, bool overlap, bool split) {
+    return 3 + d.split_liq + spheres_links_launches(d) + (overlap ? epilogue_launches(d, split) : 0);
 }
 
 // one step reading grid cur: the bulk sweep on s and, with `overlap`, the end-of-step kernels
 // of the previous step concurrently on the epilogue stream; once both are done the fix pass
 // and the boundary sweep.  The step's own end-of-step kernels are left pending.  With `timed`,
 // event pairs bracket the bulk sweep and the rest on s.
-int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed = false) {
+int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed = false, bool split = false) {
     const Dev& d = c->d;
     int slot = 0;
     if (timed) {
@@ -231,7 +237,7 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed =
     if (overlap) {
         cudaEventRecord(c->fork3, s);
         cudaStreamWaitEvent(c->epi, c->fork3, 0);
-        enqueue_epilogue(c, cur, c->epi);
+        enqueue_epilogue(c, cur, c->epi, split);
         cudaEventRecord(c->join3, c->epi);
     }
     if (timed) cudaEventRecord(c->ev[4 * slot], s);
@@ -261,14 +267,16 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed =
 // enqueue the pending end-of-step kernels on the library's stream (before any query)
 int flush(lbm_ctx* c) {
     if (!c->pending) return LBM_OK;
-    enqueue_epilogue(c, c->cur, c->stream);
+    const bool split = split_due_host(c, c->closed + 1);
+    enqueue_epilogue(c, c->cur, c->stream, split);
+    c->closed++;
     // what the caller reads next is ordered after every kernel the library enqueued
     if (c->links_state == kLinksForked) {
         cudaStreamWaitEvent(c->stream, c->join2, 0);
         c->links_state = kLinksJoined;
     }
     c->pending = false;
-    return launched(c, epilogue_launches(c->d));
+    return launched(c, epilogue_launches(c->d, split));
 }
 
 int first_step(lbm_ctx* c) {
@@ -412,7 +420,7 @@ int first_step(lbm_ctx* c) {
     return cuda_fail(cudaStreamSynchronize(s));
 }
 
-int build_graph(lbm_ctx* c) {
+int build_graph(lbm_ctx* c, int variant) {
     cudaStream_t cap;
     if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return LBM_ECUDA;
     cudaGraph_t g = nullptr;
@@ -420,17 +428,18 @@ int build_graph(lbm_ctx* c) {
     const int links_state = c->links_state;   // host bookkeeping only: captured, not run
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = LBM_ECUDA;
     if (!rc) {
-        enqueue_step(c, 0, cap, true);
-        enqueue_step(c, 1, cap, true);
+        enqueue_step(c, 0, cap, true, false, (variant & 1) != 0);
+        enqueue_step(c, 1, cap, true, false, (variant & 2) != 0);
         c->links_state = links_state;
         if (cudaStreamEndCapture(cap, &g) != cudaSuccess) rc = LBM_ECUDA;
     }
     // per-node priorities: the boundary sweep keeps its stream's priority inside the graph
-    if (!rc && cudaGraphInstantiate(&c->graph, g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess) rc = LBM_ECUDA;
+    if (!rc && cudaGraphInstantiate(&c->graph[variant], g, cudaGraphInstantiateFlagUseNodePriority) != cudaSuccess)
+        rc = LBM_ECUDA;
     if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
     cudaGetLastError();
-    c->graph_ready = rc == LBM_OK;
+    c->graph_ready[variant] = rc == LBM_OK;
     return rc;
 }
 
@@ -472,7 +481,8 @@ int lbm_init(const lbm_params* p, void* arena, size_t arena_bytes, void* cuda_st
     c->started = false;
     c->cur = 0;
     c->launches = 0;
-    c->graph_ready = false;
+    for (int v = 0; v < 4; v++) c->graph_ready[v] = false;
+    c->closed = 0;
     c->use_graph = std::getenv("LBM_NO_GRAPH") == nullptr;
     c->profiling = false;
     c->ev_ready = false;
@@ -533,9 +543,11 @@ int lbm_step(lbm_ctx* c, int nsteps) {
     int left = nsteps;
     auto one = [&](bool timed) {
         const bool ov = c->pending;
-        int r = enqueue_step(c, c->cur, c->stream, ov, timed);
+        const bool split = ov && split_due_host(c, c->closed + 1);
+        int r = enqueue_step(c, c->cur, c->stream, ov, timed, split);
         if (r) return r;
-        c->launches += (uint64_t)step_launches(c->d, ov);
+        c->launches += (uint64_t)step_launches(c->d, ov, split);
+        if (ov) c->closed++;
         c->pending = true;
         c->cur ^= 1;
         return LBM_OK;
@@ -545,16 +557,22 @@ int lbm_step(lbm_ctx* c, int nsteps) {
             if ((rc = one(true))) return rc;
         return LBM_OK;
     }
-    if (c->use_graph && nsteps >= 2 && !c->graph_ready && (rc = build_graph(c))) c->use_graph = false;
-    if (c->use_graph && c->graph_ready) {
+    if (c->use_graph && nsteps >= 2) {
         // the graph holds two overlapped steps from grid 0: align the state to that first
         while (left > 0 && (!c->pending || c->cur == 1)) {
             if ((rc = one(false))) return rc;
             left--;
         }
-        for (; left >= 2; left -= 2) {
-            if ((rc = cuda_fail(cudaGraphLaunch(c->graph, c->stream)))) return rc;
-            c->launches += 2ull * (uint64_t)step_launches(c->d, true);
+        for (; left >= 2 && c->use_graph; left -= 2) {
+            const bool s1 = split_due_host(c, c->closed + 1), s2 = split_due_host(c, c->closed + 2);
+            const int v = (s1 ? 1 : 0) | (s2 ? 2 : 0);
+            if (!c->graph_ready[v] && build_graph(c, v)) {
+                c->use_graph = false;
+                break;
+            }
+            if ((rc = cuda_fail(cudaGraphLaunch(c->graph[v], c->stream)))) return rc;
+            c->launches += (uint64_t)step_launches(c->d, true, s1) + (uint64_t)step_launches(c->d, true, s2);
+            c->closed += 2;
         }
     }
     for (; left > 0; left--)
@@ -762,7 +780,8 @@ int lbm_launch_count(lbm_ctx* c, uint64_t* launches) {
 
 int lbm_destroy(lbm_ctx* c) {
     if (!c) return LBM_EINVAL;
-    if (c->graph_ready) cudaGraphExecDestroy(c->graph);
+    for (int v = 0; v < 4; v++)
+        if (c->graph_ready[v]) cudaGraphExecDestroy(c->graph[v]);
     if (c->ev_ready)
         for (int k = 0; k < 4 * 64; k++) cudaEventDestroy(c->ev[k]);
     if (c->side_ready) {
