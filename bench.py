@@ -32,7 +32,7 @@ FALLBACK_HBM_GBS = 6800.0
 # dram bytes (read + write) per bulk-sweep launch on the 128^3 column from one ncu capture
 # (mean of three launches), with the hash of the sweep source it was taken on (null once the
 # kernel changes)
-NCU_TRAFFIC = {"sha1": "c40f742a3d66d1108bb09990e868eed1f18bfec5", "bytes_per_launch": 268553643}
+NCU_TRAFFIC = {"sha1": "bcdc930348761b21a69221b7c229552a0f66237a", "bytes_per_launch": 268280576}
 
 
 def _args():

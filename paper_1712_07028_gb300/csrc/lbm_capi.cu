@@ -93,7 +93,7 @@ size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 :
 
 struct Layout {
     size_t f[2], flags, mark, tmark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
-        adj_srho, adj_part, merge_keys, merge_list, lab, part_key, part_root, part_V, part_new, bub_cnt, total;
+        adj_srho, adj_part, merge_keys, merge_list, lab, split_list, part_key, part_root, part_V, part_new, bub_cnt, total;
     size_t N, wl_cap, nbins_max;
 };
 
@@ -136,6 +136,7 @@ Layout layout_of(const lbm_params* p) {
     L.merge_list = take(sizeof(uint32_t) * kMergeCap);
     if (p->split_every > 0) {   // bubble splitting: union-find labels, the part table, counts per id
         L.lab = take(4 * L.N);
+        L.split_list = take(4 * L.N);
         L.part_key = take(sizeof(uint32_t) * kPartCap);
         L.part_root = take(sizeof(uint32_t) * kPartCap);
         L.part_V = take(sizeof(double) * kPartCap);
@@ -359,6 +360,7 @@ int first_step(lbm_ctx* c) {
     d.merge_list = (uint32_t*)(a + L.merge_list);
     if (p->split_every > 0) {
         d.lab = (uint32_t*)(a + L.lab);
+        d.split_list = (uint32_t*)(a + L.split_list);
         d.part_key = (uint32_t*)(a + L.part_key);
         d.part_root = (uint32_t*)(a + L.part_root);
         d.part_V = (double*)(a + L.part_V);

@@ -155,6 +155,7 @@ struct Scalars {
     uint32_t n_split;     // parts split off so far
     uint32_t nbub_hw;     // one past the highest bubble id that ever carried cells
     uint32_t split_fail;  // this split step cannot split (part table full, or a find ran too long)
+    uint32_t n_split_cells;   // gas and interface cells listed by this split step
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
@@ -172,6 +173,7 @@ struct Dev {
                               // size when bubbles split, else ngeo
     int split_every;          // > 0: bubbles split into their connected parts every so many steps
     uint32_t* lab;            // [N] (splitting only) union-find labels of gas / interface cells
+    uint32_t* split_list;     // [N] (splitting only) the gas and interface cells of a split step
     uint32_t* part_key;       // [kPartCap] (splitting only) lowest cell index + 1 of each part, 0 free
     uint32_t* part_root;      // [kPartCap] the part's bubble
     double* part_V;           // [kPartCap] the part's volume

@@ -3,8 +3,8 @@
 // Every split_every steps, after the step close (the bubble model), six launches on the
 // end-of-step stream; on the other steps each returns at once.
 //   canon    every gas / interface cell takes its bubble's root id (its gas count moves with
-//            it) and becomes its own union-find label; cells per id are counted; the part
-//            table is cleared
+//            it), becomes its own union-find label and is listed; cells per id are counted;
+//            the part table is cleared (the passes below walk the list)
 //   hook     each pair of D3Q19 neighbours of one bubble is joined: union-find over the cell
 //            indices, the larger root linked under the smaller by compare-and-swap, finds
 //            with path halving, so a part's final label is its lowest cell index
@@ -102,10 +102,7 @@ __global__ void split_canon_kernel(const Dev d) {
     const int lane = threadIdx.x & 31;
     for (size_t i = t0; i < d.N; i += nt) {
         const uint32_t b = split_owner(d, i);
-        if (b == kNone) {
-            d.lab[i] = kNone;
-            continue;
-        }
+        if (b == kNone) continue;
         uint32_t r = b;
         for (int it = 0; it < 64 && d.bub[r].root != (int)r; it++) r = (uint32_t)d.bub[r].root;
         if (r != b) {
@@ -118,12 +115,19 @@ __global__ void split_canon_kernel(const Dev d) {
         d.lab[i] = (uint32_t)i;
         const unsigned same = __match_any_sync(__activemask(), r);   // one atomic per bubble and warp
         if (lane == __ffs(same) - 1) atomicAdd(&d.bub_cnt[r], (uint32_t)__popc(same));
+        wl_push(d.split_list, &d.sc->n_split_cells, (uint32_t)d.N, (uint32_t)i, &d.sc->status);
     }
+}
+
+__device__ __forceinline__ uint32_t split_cells(const Dev& d) {
+    return min(*(volatile const uint32_t*)&d.sc->n_split_cells, (uint32_t)d.N);
 }
 
 __global__ void split_hook_kernel(const Dev d) {
     if (!split_due(d)) return;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t n = split_cells(d);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t i = d.split_list[k];
         const uint32_t r = split_owner(d, i);
         if (r == kNone) continue;
         int x, y, z;
@@ -139,7 +143,9 @@ __global__ void split_hook_kernel(const Dev d) {
 
 __global__ void split_compress_kernel(const Dev d) {
     if (!split_due(d)) return;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t n = split_cells(d);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t i = d.split_list[k];
         const uint32_t r = split_owner(d, i);
         if (r == kNone) continue;
         const uint32_t rep = uf_root(d.lab, (uint32_t)i, &d.sc->split_fail);
@@ -165,11 +171,13 @@ __global__ void split_volume_kernel(const Dev d, const int g) {
     const int lane = threadIdx.x & 31;
     // every warp runs the same number of rounds: a warp whose cells all belong to one part (the
     // common case) sums them first, one FP64 atomic instead of 32 on the same address
-    for (size_t base = blockIdx.x * (size_t)blockDim.x; base < d.N; base += (size_t)gridDim.x * blockDim.x) {
-        const size_t i = base + threadIdx.x;
+    const uint32_t n = split_cells(d);
+    for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const uint32_t k = base + threadIdx.x;
+        const size_t i = k < n ? d.split_list[k] : 0;
         int s = -1;
         double v = 0.0;
-        if (i < d.N && split_owner(d, i) != kNone) {
+        if (k < n && split_owner(d, i) != kNone) {
             s = part_slot(d, __ldcg(&d.lab[i]));
             if (s >= 0) v = (d.flags[i] & F_GAS) ? 1.0 : 1.0 - (double)phi[i];
         }
@@ -186,7 +194,7 @@ __global__ void split_volume_kernel(const Dev d, const int g) {
 }
 
 // one block of kDecideThreads threads
-constexpr int kDecideThreads = 1024;
+constexpr int kDecideThreads = 256;
 __global__ void __launch_bounds__(kDecideThreads) split_decide_kernel(const Dev d) {
     if (!split_due(d)) return;
     __shared__ uint32_t sSlot[kPartCap];    // used slots, then in (bubble, lowest index) order
@@ -285,7 +293,9 @@ __global__ void __launch_bounds__(kDecideThreads) split_decide_kernel(const Dev 
 
 __global__ void split_relabel_kernel(const Dev d) {
     if (!split_due(d) || *(volatile const uint32_t*)&d.sc->split_fail) return;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t n = split_cells(d);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const size_t i = d.split_list[k];
         const uint32_t b = split_owner(d, i);
         if (b == kNone) continue;
         const int s = part_slot(d, __ldcg(&d.lab[i]));
@@ -303,13 +313,16 @@ __global__ void split_relabel_kernel(const Dev d) {
 // the split step's kernels on stream s (grid g: the one the step wrote)
 void launch_split(const Dev& d, int g, cudaStream_t s) {
     if (d.split_every <= 0) return;
-    const int nb = 152 * 8, tb = 256;
-    split_canon_kernel<<<nb, tb, 0, s>>>(d);
-    split_hook_kernel<<<nb, tb, 0, s>>>(d);
-    split_compress_kernel<<<nb, tb, 0, s>>>(d);
-    split_volume_kernel<<<nb, tb, 0, s>>>(d, g);
+    // small grids: these passes run beside the bulk sweep, whose blocks hold most SM slots, and
+    // a grid of a few hundred blocks gets its slots sooner than one of thousands
+    const int tb = 256;
+    cudaMemsetAsync(&d.sc->n_split_cells, 0, sizeof(uint32_t), s);   // the canon pass lists afresh
+    split_canon_kernel<<<152 * 2, tb, 0, s>>>(d);
+    split_hook_kernel<<<152, tb, 0, s>>>(d);
+    split_compress_kernel<<<152, tb, 0, s>>>(d);
+    split_volume_kernel<<<152, tb, 0, s>>>(d, g);
     split_decide_kernel<<<1, kDecideThreads, 0, s>>>(d);
-    split_relabel_kernel<<<nb, tb, 0, s>>>(d);
+    split_relabel_kernel<<<152, tb, 0, s>>>(d);
 }
 
 }  // namespace lbm
