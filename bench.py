@@ -44,6 +44,8 @@ def _args():
     ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c3", "c4"])
     ap.add_argument("--storage", default=None, choices=[None, "f32", "f16dev", "bf16dev"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed region (for profilers)")
+    ap.add_argument("--split-every", type=int, default=0,
+                    help="bubbles split into their connected parts every so many steps (0: never)")
     ap.add_argument("--only", default=None, choices=[None, "adjoint"],
                     help="time only the differentiation path (the adjoint object of the full line)")
     return ap.parse_args()
@@ -393,6 +395,8 @@ def run_gpu(args):
     from paper_1712_07028_gb300 import workloads as W
     lbm.load()
     wl = _workload(args.workload, args.storage)
+    if args.split_every > 0:
+        wl.split_every, wl.max_bubbles = args.split_every, max(16, len(wl.bubbles))
     s_bytes = 4 if wl.storage == "f32" else 2
 
     def barrier():

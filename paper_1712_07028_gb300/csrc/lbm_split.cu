@@ -3,8 +3,9 @@
 // Every split_every steps, after the step close (the bubble model), six launches on the
 // end-of-step stream; on the other steps each returns at once.
 //   canon    every gas / interface cell takes its bubble's root id (its gas count moves with
-//            it), becomes its own union-find label and is listed; cells per id are counted;
-//            the part table is cleared (the passes below walk the list)
+//            it) and is listed; its union-find label starts at its lowest-indexed neighbour of
+//            the same bubble (or itself); cells per id are counted; the part table is cleared
+//            (the passes below walk the list)
 //   hook     each pair of D3Q19 neighbours of one bubble is joined: union-find over the cell
 //            indices, the larger root linked under the smaller by compare-and-swap, finds
 //            with path halving, so a part's final label is its lowest cell index
@@ -112,7 +113,21 @@ __global__ void split_canon_kernel(const Dev d) {
                 atomicAdd(&d.bub[r].ngas, 1ull);
             }
         }
-        d.lab[i] = (uint32_t)i;
+        // the first label: the lowest-indexed neighbour of the same bubble, if lower than the cell
+        // (a real link of the part, so the forest starts mostly joined and the hook pass finds
+        // most pairs already together; neighbours may still carry a member id of the bubble)
+        uint32_t l = (uint32_t)i;
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        for (int q = 1; q < kQ; q++) {
+            size_t j;
+            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j) || j >= l) continue;
+            uint32_t rj = split_owner(d, j);
+            if (rj == kNone) continue;
+            for (int it = 0; it < 64 && d.bub[rj].root != (int)rj; it++) rj = (uint32_t)d.bub[rj].root;
+            if (rj == r) l = (uint32_t)j;
+        }
+        d.lab[i] = l;
         const unsigned same = __match_any_sync(__activemask(), r);   // one atomic per bubble and warp
         if (lane == __ffs(same) - 1) atomicAdd(&d.bub_cnt[r], (uint32_t)__popc(same));
         wl_push(d.split_list, &d.sc->n_split_cells, (uint32_t)d.N, (uint32_t)i, &d.sc->status);
