@@ -138,21 +138,22 @@ __device__ __forceinline__ uint32_t split_cells(const Dev& d) {
     return min(*(volatile const uint32_t*)&d.sc->n_split_cells, (uint32_t)d.N);
 }
 
+// one thread per listed cell and direction: a union is a chain of dependent loads, so the
+// pairs are spread over threads rather than walked one after another by each cell's thread
 __global__ void split_hook_kernel(const Dev d) {
     if (!split_due(d)) return;
-    const uint32_t n = split_cells(d);
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const size_t i = d.split_list[k];
+    const uint64_t n = (uint64_t)split_cells(d) * (kQ - 1);
+    for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < n; k += (uint64_t)gridDim.x * blockDim.x) {
+        const size_t i = d.split_list[k / (kQ - 1)];
+        const int q = 1 + (int)(k % (kQ - 1));
         const uint32_t r = split_owner(d, i);
         if (r == kNone) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        for (int q = 1; q < kQ; q++) {
-            size_t j;
-            if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j) || j <= i) continue;   // each pair once
-            if (split_owner(d, j) != r) continue;
-            uf_union(d.lab, (uint32_t)i, (uint32_t)j, &d.sc->split_fail);
-        }
+        size_t j;
+        if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j) || j <= i) continue;   // each pair once
+        if (split_owner(d, j) != r) continue;
+        uf_union(d.lab, (uint32_t)i, (uint32_t)j, &d.sc->split_fail);
     }
 }
 
@@ -332,8 +333,8 @@ void launch_split(const Dev& d, int g, cudaStream_t s) {
     // a grid of a few hundred blocks gets its slots sooner than one of thousands
     const int tb = 256;
     cudaMemsetAsync(&d.sc->n_split_cells, 0, sizeof(uint32_t), s);   // the canon pass lists afresh
-    split_canon_kernel<<<152 * 2, tb, 0, s>>>(d);
-    split_hook_kernel<<<152, tb, 0, s>>>(d);
+    split_canon_kernel<<<152 * 4, tb, 0, s>>>(d);
+    split_hook_kernel<<<152 * 4, tb, 0, s>>>(d);
     split_compress_kernel<<<152, tb, 0, s>>>(d);
     split_volume_kernel<<<152, tb, 0, s>>>(d, g);
     split_decide_kernel<<<1, kDecideThreads, 0, s>>>(d);
