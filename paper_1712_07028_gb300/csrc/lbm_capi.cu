@@ -398,7 +398,7 @@ int first_step(lbm_ctx* c) {
     }
     int rc = cuda_fail(cudaMemsetAsync(a, 0, L.total, s));
     if (rc) return rc;
-    if (d.nbub > 0)
+    if (d.ngeo > 0)
         if ((rc = cuda_fail(cudaMemcpyAsync(c->geo_dev, c->bub_geo.data(), sizeof(double) * c->bub_geo.size(), cudaMemcpyHostToDevice, s)))) return rc;
     if (d.nsph > 0)
         if ((rc = cuda_fail(cudaMemcpyAsync(d.sph, c->sph_init.data(), sizeof(Sphere) * d.nsph, cudaMemcpyHostToDevice, s)))) return rc;
@@ -702,7 +702,7 @@ int lbm_status(lbm_ctx* c, uint32_t* status) {
 // no-slip or periodic faces
 static int adjoint_ready(lbm_ctx* c) {
     if (!c->started) return LBM_ESTATE;
-    if (c->p.storage != LBM_STORE_F32 || c->d.nbub != 0 || c->p.sphere_mode != LBM_SPHERES_FIXED || c->d.special)
+    if (c->p.storage != LBM_STORE_F32 || c->d.ngeo != 0 || c->p.sphere_mode != LBM_SPHERES_FIXED || c->d.special)
         return LBM_ESTATE;
     return flush(c);
 }
