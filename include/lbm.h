@@ -17,7 +17,8 @@
  *   - interface / liquid / gas conversions with layer closure, equilibrium initialisation
  *     of new interface cells and excess-mass redistribution (Sec. 2.2, Fig.
  *     cellConversions);
- *   - the bubble model (per-bubble volume -> gas density; touching bubbles merge, Sec. 2.2);
+ *   - the bubble model (per-bubble volume -> gas density; touching bubbles merge, and with
+ *     lbm_params.split_every > 0 a bubble whose region breaks apart splits, Sec. 2.2);
  *   - sphere update: lubrication correction (Eq. lubrication) and Newton-Euler sub-steps
  *     (Sec. 2.3), then cells covered / uncovered by the moved spheres and PDF refill.
  *

@@ -27,7 +27,8 @@
  *      correction (Eq. lubrication) and n_substeps Newton-Euler sub-steps (Sec. 2.3);
  *   4. cells covered / uncovered by the moved spheres, refill of uncovered cells;
  *   5. bubble model: per-bubble volume and gas density (Sec. 2.2, last paragraph), on the
- *      cells as the step leaves them, for the next step's reconstruction;
+ *      cells as the step leaves them, for the next step's reconstruction; touching bubbles
+ *      merge, and every split_every steps a bubble in several connected parts splits;
  *   6. curvature from fill levels, Parker-Youngs normals (Sec. 2.2, only if sigma > 0).
  *
  * Parity: pinned by the tests (Poiseuille profile, rest-state invariance, exact per-step
