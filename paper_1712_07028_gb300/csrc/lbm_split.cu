@@ -41,11 +41,13 @@ __device__ __forceinline__ uint32_t split_owner(const Dev& d, size_t i) {
     return b < (uint32_t)d.nbub ? b : kNone;
 }
 
+// (plain, L1-cached loads: a stale label is still an ancestor, and a stale root is corrected by
+// the union's compare-and-swap, which goes to L2 and returns the root's current parent)
 __device__ uint32_t uf_find(uint32_t* lab, uint32_t x, uint32_t* fail) {
     for (uint32_t it = 0; it < kFindBound; it++) {
-        const uint32_t p = __ldcg(lab + x);
+        const uint32_t p = lab[x];
         if (p == x) return x;
-        const uint32_t gp = __ldcg(lab + p);
+        const uint32_t gp = lab[p];
         if (gp != p) __stcg(lab + x, gp);   // path halving: gp is an ancestor of x
         x = gp;
     }
