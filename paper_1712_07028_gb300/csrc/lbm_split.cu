@@ -1,7 +1,8 @@
 // lbm_split.cu -- bubble splitting: a bubble is one connected gas region (Sec. 2.2).
 //
 // Every split_every steps, after the step close (the bubble model), six launches on the
-// end-of-step stream; on the other steps each returns at once.
+// end-of-step stream (the host enqueues them only in the steps that split; each also checks
+// the step counter and returns at once on any other step).
 //   canon    every gas / interface cell takes its bubble's root id (its gas count moves with
 //            it) and is listed; its union-find label starts at its lowest-indexed neighbour of
 //            the same bubble (or itself); cells per id are counted; the part table is cleared
