@@ -722,3 +722,34 @@ def test_bubbles_pinching_off_and_merging_again(orc):
         assert np.isclose(sum(o.bub[b, orc.B_MG] for b in live), mg0, rtol=1e-12), k
         assert int(o.scal[orc.SC_STATUS]) == 0, k
     assert o.scal[orc.SC_NMERGE] >= 2 and o.scal[orc.SC_NSPLIT] >= 2
+
+
+def test_bubble_across_a_periodic_face_is_not_split(orc):
+    """a bubble centred on a periodic face has its cells on both sides of the grid: they are
+    D3Q19 neighbours through the wrap, so the bubble is one connected region and splitting
+    leaves it whole (scipy's labelling without the wrap sees two pieces)"""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.Workload(name="wrap", nx=24, ny=14, nz=14, tau=0.7, g=(0, 0, 0), bc=(W.PERIODIC, W.WALL, W.WALL),
+                    sphere_mode=W.SPHERES_FIXED, bubbles=[W.Bubble((0.0, 7.0, 7.0), 4.0)],
+                    split_every=1, max_bubbles=4)
+    o = orc.Sim(wl)
+    act = (o.flag & (orc.GAS | orc.IFACE)) != 0
+    assert ndimage.label(act, ndimage.generate_binary_structure(3, 2))[1] == 2
+    o.step(5)
+    assert o.scal[orc.SC_NSPLIT] == 0 and o.n_bubbles == 1
+    assert (o.owner[(o.flag & (orc.GAS | orc.IFACE)) != 0] == 0).all()
+
+
+def test_bubble_part_of_zero_volume_stays(orc):
+    """R39: a part made only of full interface cells (phi = 1, no gas: zero volume) holds no gas
+    to divide; it stays with its bubble, and the other part keeps the whole gas mass"""
+    o, V = _two_parts_one_bubble(orc, 3.0, 5.0)
+    small = o.owner == 0
+    o.flag[small & ((o.flag & (orc.GAS | orc.IFACE)) != 0)] = orc.IFACE
+    o.phi[small] = 1.0
+    mg = o.bub[0, orc.B_MG]
+    o.bubble_model(split=True)
+    assert o.scal[orc.SC_NSPLIT] == 0 and o.n_bubbles == 2
+    assert (o.owner[small] == 0).all()
+    assert np.isclose(o.bub[0, orc.B_MG], mg, rtol=1e-15)
