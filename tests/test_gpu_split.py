@@ -93,3 +93,18 @@ def test_split_steps_match_the_oracle(lbm):
                 break
         prev = cur
     assert checked == 2
+
+
+def test_bubble_across_a_periodic_face_is_not_split(lbm):
+    """a bubble centred on a periodic face: its cells on both sides of the grid are neighbours
+    through the wrap, so splitting every step leaves it one bubble"""
+    wl = W.Workload(name="wrap", nx=24, ny=14, nz=14, tau=0.7, g=(0, 0, 0), bc=(W.PERIODIC, W.WALL, W.WALL),
+                    sphere_mode=W.SPHERES_FIXED, bubbles=[W.Bubble((0.0, 7.0, 7.0), 4.0)],
+                    split_every=1, max_bubbles=4)
+    sim = lbm.Sim(wl)
+    sim.step(20)
+    ex = sim.export_state()
+    flags, owner = ex["flags"].cpu().numpy(), ex["owner"].cpu().numpy()
+    assert sim.bubble_splits() == (1, 0)
+    assert (owner[(flags & (oracle.GAS | oracle.IFACE)) != 0] == 0).all()
+    assert sim.status() == 0
