@@ -186,7 +186,10 @@ int lbm_spheres(lbm_ctx* ctx, double* x, double* u, double* w, int n);
  * from the end of that step on: the larger root id joins the smaller, the gas masses add
  * (rho_g0 V0 each, so the V0 add), V is the sum over all ids of the bubble and every id gets
  * rho_g = rho_g0 V0 / V.  Cells keep the id they were created with.  Bubbles that touch
- * from the start are merged at lbm_step(ctx, 0). */
+ * from the start are merged at lbm_step(ctx, 0).  With splitting on
+ * (lbm_params.split_every > 0) n may be up to max_bubbles: at each split step every cell takes
+ * its bubble's root id, rows left without cells are reset (V0 = V = 0, rho_g = rho_gas0) and
+ * reused for the parts split off (lbm_bubble_splits). */
 int lbm_bubbles(lbm_ctx* ctx, double* V0, double* V, double* rho_g, int n);
 
 /* Root id root[n] (host; NULL allowed) of bubble ids 0..n-1 -- the smallest id of the bubble
