@@ -753,3 +753,54 @@ def test_bubble_part_of_zero_volume_stays(orc):
     assert o.scal[orc.SC_NSPLIT] == 0 and o.n_bubbles == 2
     assert (o.owner[small] == 0).all()
     assert np.isclose(o.bub[0, orc.B_MG], mg, rtol=1e-15)
+
+
+def test_bubble_split_against_a_scipy_restatement(orc):
+    """R39 restated with scipy's 18-connectivity labelling (no wrap: walls) on a bubble in three
+    parts (ids 0, 1, 2 joined to root 0, radii 3, 4.5, 3.5) beside a separate bubble (id 3):
+    the parts' lowest indices order them, the largest keeps id 0, the others take the lowest
+    free ids (1, 2) in that order, gas masses in proportion to the volumes"""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    from paper_1712_07028_gb300 import workloads as W
+    wl = W.Workload(name="parts3", nx=40, ny=16, nz=16, tau=0.7, g=(0, 0, 0), sphere_mode=W.SPHERES_FIXED,
+                    bubbles=[W.Bubble((30.0, 8.0, 8.0), 3.0), W.Bubble((8.0, 8.0, 8.0), 4.5),
+                             W.Bubble((19.0, 6.0, 9.0), 3.5), W.Bubble((25.0, 12.0, 3.0), 1.6)],
+                    max_bubbles=6)
+    o = orc.Sim(wl)
+    assert list(o.roots) == [0, 1, 2, 3]   # four separate bubbles to start with
+    for b in (1, 2):
+        o.bub[b, orc.B_ROOT] = 0
+    mg_family = 1.1 * sum(_gas_volume(orc, o, [b]) for b in range(3))
+    for b in range(3):
+        o.bub[b, orc.B_MG] = mg_family
+        o.bub[b, orc.B_V0] = mg_family / 1.1
+    act = (o.flag & (orc.GAS | orc.IFACE)) != 0
+    fam = act & np.isin(o.owner, [0, 1, 2])
+    lab, n = ndimage.label(fam, ndimage.generate_binary_structure(3, 2))
+    assert n == 3
+    vol = np.where(o.flag == orc.GAS, 1.0, 1.0 - o.phi)
+    flat = lab.ravel()
+    parts = []
+    for c in range(1, n + 1):
+        idx = np.flatnonzero(flat == c)
+        parts.append((idx.min(), vol.ravel()[idx].sum(), c))
+    parts.sort()
+    keep = max(range(3), key=lambda k: (parts[k][1], -parts[k][0]))
+    expect = np.where(act, o.owner, -1).copy()
+    expect[fam] = 0
+    free = iter([1, 2, 4, 5])
+    Vt = sum(p[1] for p in parts)
+    mg_new = {}
+    for k, (rep, V, c) in enumerate(parts):
+        if k == keep:
+            mg_new[0] = mg_family * V / Vt
+            continue
+        nid = next(free)
+        expect[lab == c] = nid
+        mg_new[nid] = mg_family * V / Vt
+    o.bubble_model(split=True)
+    assert (np.where(act, o.owner, -1) == expect).all()
+    assert o.scal[orc.SC_NSPLIT] == 2 and o.n_bubbles == 4
+    for b, m in mg_new.items():
+        assert np.isclose(o.bub[b, orc.B_MG], m, rtol=1e-12), (b, o.bub[b, orc.B_MG], m)
+    assert list(o.roots) == [0, 1, 2, 3]
