@@ -33,8 +33,9 @@
  *
  * Parity: pinned by the tests (Poiseuille profile, rest-state invariance, exact per-step
  * mass, momentum and angular-momentum balances, Stokes drag in a periodic array, the
- * Laplace pressure jump, the layer invariant and brute-force comparison with a NumPy
- * transcription on tiny grids).  The conversion details of step 2 (new-interface
+ * Laplace pressure jump, the layer invariant, brute-force comparison with a NumPy
+ * transcription on tiny grids, and bubble splitting against a restatement with scipy's
+ * connectivity labelling).  The conversion details of step 2 (new-interface
  * initialisation, excess weights) and the refill rule of step 6 have no published
  * numeric check: parity unpinned for those beyond conservation and invariants.
  */
