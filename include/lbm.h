@@ -274,18 +274,26 @@ int lbm_launch_count(lbm_ctx* ctx, uint64_t* launches);
 /* Bubble volumes for callers that cannot allocate device memory.  Some callers cannot call
  * cudaMalloc at all (code inside an allocator hook or a host callback, real-time sections,
  * programs whose device memory is fully handed out before they start); this entry point
- * allocates nothing, neither directly nor through any library.  The paper has no
- * counterpart: it is the bubble-volume reduction of lbm_step (V_b = number of gas cells of
- * bubble b + sum over its interface cells of (1 - phi), FP64) offered on its own.
+ * allocates nothing, neither directly nor through any library, once its set-up on a device is
+ * done (below).  The paper has no counterpart: it offers the two per-id sums of lbm_step's
+ * bubble model on their own, V_id = number of gas cells carrying bubble id `id` + sum over the
+ * interface cells carrying `id` of (1 - phi), FP64.  Cells keep the id they were created with,
+ * so after bubbles merge these are per-id parts: the merged bubble's V (what lbm_bubbles
+ * reports for each of its ids) is the sum of volumes[id] over the ids with the same root
+ * (lbm_bubble_roots).
  *   flags[n_cells], owner[n_cells], phi[n_cells]: device, in the layout lbm_export_state
  *     writes (LBM_CELL_* types, bubble id or -1, fill level);
- *   volumes[n_bubbles]: device, FP64 output;
- *   n_bubbles: 1..1024, else LBM_EINVAL;
+ *   volumes[n_bubbles]: device, FP64 output, one entry per id 0..n_bubbles-1;
+ *   n_bubbles: 1..1024, else LBM_EINVAL (nothing is enqueued);
  *   cuda_stream: the cudaStream_t the work goes to (asynchronous).
  * Its scratch is a 16 KB static device array that every device using the library holds
  * until the process exits, shared by all calls: calls whose work overlaps on the GPU (e.g.
- * on two streams) race and must be ordered by the caller.  The first call on a device looks
- * up that array's device address; make it before any stream capture. */
+ * on two streams) race and must be ordered by the caller.  Each call clears the part it uses.
+ * The first call on a device is its set-up: it looks up that array's device address and the
+ * device's multiprocessor count and loads the call's two kernels (under CUDA's lazy loading a
+ * kernel's code is loaded on first use, which takes device memory).  Make that first call
+ * outside any section where allocation is forbidden, and before any stream capture.
+ * LBM_ECUDA if the set-up or a launch fails. */
 int lbm_bubble_volumes_noalloc(const uint8_t* flags, const int32_t* owner, const float* phi, size_t n_cells,
                                int n_bubbles, double* volumes, void* cuda_stream);
 

@@ -3,8 +3,8 @@
 // Some callers cannot call cudaMalloc: code running where allocation is forbidden or
 // deferred (inside an allocator hook, a signal-safe or real-time section, a host callback),
 // or a host program whose memory budget is fixed and fully handed out before it starts.
-// lbm_bubble_volumes_noalloc serves them: it is a variant of the bubble-volume reduction of
-// lbm_step whose scratch (per-bubble partial sums) is a file-scope static device array, so
+// lbm_bubble_volumes_noalloc serves them: the bubble-volume sums of lbm_step's bubble model,
+// per bubble id, whose scratch (per-id partial sums) is a file-scope static device array, so
 // the call itself allocates nothing.  The caller still passes its inputs and the output.
 #include <cstdio>
 #include <mutex>
@@ -20,10 +20,16 @@ constexpr int kNoallocMaxDevices = 64;
 static __device__ __align__(256) unsigned long long g_bubble_scratch[2 * kNoallocMaxBubbles];
 
 std::mutex g_setup_mutex;
-unsigned long long* g_scratch_addr[kNoallocMaxDevices] = {nullptr};
+struct DeviceSetup {
+    unsigned long long* scratch;   // device address of g_bubble_scratch on this device
+    int sms;                       // its multiprocessor count (grid size of the reduction)
+};
+DeviceSetup g_setup[kNoallocMaxDevices] = {};
 
-// Same sums as the step's bubble model: V_b = #gas cells of b + sum over interface cells of b
-// of (1 - phi), FP64, from canonical inputs (types LBM_CELL_*, owner -1 for none).
+// Per bubble id b: V_b = #gas cells carrying id b + sum over the interface cells carrying id b
+// of (1 - phi), FP64, from canonical inputs (types LBM_CELL_*, owner -1 for none) -- the two
+// sums the step's bubble model keeps per id.  Cells keep the id they were created with, so the
+// volume of a merged bubble is the sum of these per-id volumes over its ids (one root).
 __global__ void bubble_volumes_static_kernel(const uint8_t* __restrict__ flags, const int32_t* __restrict__ owner,
                                              const float* __restrict__ phi, size_t n, int nbub,
                                              unsigned long long* scratch) {
@@ -62,22 +68,44 @@ __global__ void bubble_volumes_static_finish(int nbub, const unsigned long long*
         volumes[b] = (double)ngas[b] + vif[b];
 }
 
-// device address of the static scratch for the current device, looked up once per device
-int scratch_for_current_device(unsigned long long** out) {
+// once per device, with it current: the device address of the static scratch, the device's
+// multiprocessor count, and both kernels loaded (under CUDA's lazy module loading a kernel's
+// code is loaded at its first use, which takes device memory: done here, at set-up)
+int setup_current_device(DeviceSetup* out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices) return LBM_ECUDA;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    DeviceSetup& s = g_setup[dev];
+    if (!s.scratch) {
         void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_bubble_scratch);
+        cudaError_t e = cudaGetSymbolAddress(&p, g_bubble_scratch);
         if (e != cudaSuccess || !p) {
             std::fprintf(stderr, "lbm: cudaGetSymbolAddress failed: %s\n", cudaGetErrorString(e));
             return LBM_ECUDA;
         }
-        g_scratch_addr[dev] = static_cast<unsigned long long*>(p);
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess || sms < 1) {
+            std::fprintf(stderr, "lbm: multiprocessor count query failed: %s\n", cudaGetErrorString(e));
+            return LBM_ECUDA;
+        }
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, bubble_volumes_static_kernel)) != cudaSuccess ||
+            (e = cudaFuncGetAttributes(&fa, bubble_volumes_static_finish)) != cudaSuccess) {
+            std::fprintf(stderr, "lbm: kernel load failed: %s\n", cudaGetErrorString(e));
+            return LBM_ECUDA;
+        }
+        s.sms = sms;
+        s.scratch = static_cast<unsigned long long*>(p);
     }
-    *out = g_scratch_addr[dev];
+    *out = s;
     return LBM_OK;
+}
+
+int launch_error(cudaError_t e) {
+    if (e == cudaSuccess) return LBM_OK;
+    std::fprintf(stderr, "lbm_bubble_volumes_noalloc: launch failed: %s\n", cudaGetErrorString(e));
+    return LBM_ECUDA;
 }
 
 }  // namespace
@@ -90,17 +118,28 @@ extern "C" int lbm_bubble_volumes_noalloc(const uint8_t* flags, const int32_t* o
                      kNoallocMaxBubbles);
         return LBM_EINVAL;
     }
-    unsigned long long* scratch = nullptr;
-    int rc = scratch_for_current_device(&scratch);
+    DeviceSetup dev;
+    int rc = setup_current_device(&dev);
     if (rc) return rc;
+    unsigned long long* scratch = dev.scratch;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     // the scratch keeps the previous call's sums: clear the part this call uses
     if (cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * n_bubbles, s) != cudaSuccess) return LBM_ECUDA;
     if (cudaMemsetAsync(scratch + kNoallocMaxBubbles, 0, sizeof(unsigned long long) * n_bubbles, s) != cudaSuccess)
         return LBM_ECUDA;
     size_t blocks = (n_cells + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    bubble_volumes_static_kernel<<<(unsigned)blocks, 256, 0, s>>>(flags, owner, phi, n_cells, n_bubbles, scratch);
-    bubble_volumes_static_finish<<<(n_bubbles + 127) / 128, 128, 0, s>>>(n_bubbles, scratch, volumes);
-    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ECUDA;
+    if (blocks > (size_t)dev.sms * 8) blocks = (size_t)dev.sms * 8;   // grid-stride beyond 8 blocks per SM
+    // each launch's own error (the return value), not an earlier one still pending on this thread
+    {
+        void* args[] = {(void*)&flags, (void*)&owner, (void*)&phi, (void*)&n_cells, (void*)&n_bubbles, (void*)&scratch};
+        if ((rc = launch_error(cudaLaunchKernel((const void*)bubble_volumes_static_kernel, dim3((unsigned)blocks),
+                                                dim3(256), args, 0, s))))
+            return rc;
+    }
+    {
+        const unsigned long long* cs = scratch;
+        void* args[] = {(void*)&n_bubbles, (void*)&cs, (void*)&volumes};
+        return launch_error(cudaLaunchKernel((const void*)bubble_volumes_static_finish, dim3((n_bubbles + 127) / 128),
+                                             dim3(128), args, 0, s));
+    }
 }
