@@ -78,6 +78,8 @@ def lib():
         _lib.orc_bubble_model.argtypes = [pp, ps]
         _lib.orc_bubble_model_split.argtypes = [pp, ps]
         _lib.orc_velocity.argtypes = [ctypes.c_int, ctypes.c_int]
+        _lib.orc_conversions.argtypes = [pp, ps]
+        _lib.orc_cover_uncover.argtypes = [pp, ps]
         _lib.orc_tangent_window.argtypes = [pp, ps, _P(ctypes.c_double), _P(ctypes.c_double), ctypes.c_double,
                                             _P(ctypes.c_double), _P(ctypes.c_double), ctypes.c_int,
                                             _P(ctypes.c_double), _P(ctypes.c_double)]
@@ -215,6 +217,16 @@ class Sim:
         splitting too)"""
         f = lib().orc_bubble_model_split if split else lib().orc_bubble_model
         f(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    def conversions(self):
+        """the cell conversions alone (step 2) on the current state, taken as the sweep's
+        result: types, fill levels, masses and PDFs f*(t+1)"""
+        lib().orc_conversions(ctypes.byref(self.p), ctypes.byref(self.s))
+
+    def cover_uncover(self):
+        """cells covered and uncovered by the spheres at their current centres (step 4), with
+        the refill of uncovered cells"""
+        lib().orc_cover_uncover(ctypes.byref(self.p), ctypes.byref(self.s))
 
     @property
     def n_bubbles(self) -> int:

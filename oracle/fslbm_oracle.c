@@ -35,9 +35,10 @@
  * mass, momentum and angular-momentum balances, Stokes drag in a periodic array, the
  * Laplace pressure jump, the layer invariant, brute-force comparison with a NumPy
  * transcription on tiny grids, and bubble splitting against a restatement with scipy's
- * connectivity labelling).  The conversion details of step 2 (new-interface
- * initialisation, excess weights) and the refill rule of step 6 have no published
- * numeric check: parity unpinned for those beyond conservation and invariants.
+ * connectivity labelling).  The conversion details of step 2 (filling wins, layer closure,
+ * new-interface initialisation, excess weights along the normal, equal shares, the pool) and
+ * the covering / refill rule of step 4 are pinned against an independent set-form NumPy
+ * transcription on random states and against values worked out by hand on a flat interface.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1200,6 +1201,17 @@ void orc_curvature(const orc_params *p, orc_state *s) { curvature(p, s); }
 void orc_bubble_model(const orc_params *p, orc_state *s) { bubble_model(p, s, 0, 0); }
 void orc_bubble_model_split(const orc_params *p, orc_state *s) { bubble_model(p, s, 0, 1); }
 int orc_velocity(int q, int k) { return k == 0 ? CX[q] : (k == 1 ? CY[q] : CZ[q]); }
+/* step 2 alone, on the state as it stands: f holds the sweep's result f*(t+1), phi and m its
+ * fill levels and masses, flag its types (the conversions work on ft, then f takes it) */
+void orc_conversions(const orc_params *p, orc_state *s)
+{
+    const size_t bytes = sizeof(double) * (size_t)NQ * (size_t)ncell(p);
+    memcpy(s->ft, s->f, bytes);
+    conversions(p, s);
+    memcpy(s->f, s->ft, bytes);
+}
+/* step 4 alone: cells covered and uncovered by the spheres at their current centres */
+void orc_cover_uncover(const orc_params *p, orc_state *s) { cover_uncover(p, s); }
 
 /* ------------------------------------------------ tangent-linear (forward-mode) gradient */
 
