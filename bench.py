@@ -1,15 +1,18 @@
 #!/usr/bin/env python
-"""Throughput of the fused free-surface LBM step (MLUPS) on the 128^3 bubble-particle column.
+"""Throughput of the fused free-surface LBM step (MLUPS) on the 512x512x1024 bubble-particle
+column, the largest single-GPU workload.
 
 One step = the whole per-step hot path: sweep (stream, bounce-back, gas reconstruction,
 mass exchange, TRT collision), cell conversions, bubble model, sphere update and
-cover/uncover.  Workload: 128^3 cells, walls, tau 0.6, gravity 1e-6 along -z, one gas
-bubble r=16 at (64,64,32), 64 spheres r=4 of density 1.5 placed by seeded rejection
-sampling, FP32 PDFs (two grids of 19 x 8 MB planes: inputs larger than L2).
+cover/uncover.  Headline workload: 512 x 512 x 1024 cells (268 M), walls, tau 0.6, gravity
+1e-6 along -z, 32 gas bubbles r=24 and 100 000 free spheres r=4 of density 1.5 placed by
+seeded rejection sampling, PDFs stored as FP16 deviations (two grids of 10.2 GB: inputs far
+larger than L2).  Extra objects: the 256x256x512 column in FP32 and FP16 deviations (the
+FP32-vs-FP16 configuration) and the 128^3 column.
 
-Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead.
-Under torchrun every rank runs an independent replica (the method needs no exchange
-between replicas; one GPU per domain).
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle instead (on a
+bounded sub-box of the large columns).  Under torchrun every rank runs an independent
+replica (the method needs no exchange between replicas; one GPU per domain).
 """
 from __future__ import annotations
 
@@ -29,19 +32,18 @@ sys.path.insert(0, ROOT)
 METRIC = "MLUPS and HBM-roofline fraction, FP32 / FP16-store vs FP64 oracle error"
 FALLBACK_HBM_GBS = 6800.0
 
-# dram bytes (read + write) per bulk-sweep launch on the 128^3 column from one ncu capture
-# (mean of three launches), with the hash of the sweep source it was taken on (null once the
-# kernel changes)
-NCU_TRAFFIC = {"sha1": "bcdc930348761b21a69221b7c229552a0f66237a", "bytes_per_launch": 268280576}
+# dram bytes (read + write) per bulk-sweep launch, per workload and storage, from one ncu
+# capture, with the hash of the sweep source it was taken on (null once the kernel changes)
+NCU_TRAFFIC = {}
 
 
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="c1", choices=["c0", "c1", "c3", "c4"])
+    ap.add_argument("--workload", default="c4", choices=["c0", "c1", "c3", "c4"])
     ap.add_argument("--storage", default=None, choices=[None, "f32", "f16dev", "bf16dev"])
     ap.add_argument("--no-extras", action="store_true", help="only the timed region (for profilers)")
     ap.add_argument("--split-every", type=int, default=0,
@@ -51,12 +53,32 @@ def _args():
     return ap.parse_args()
 
 
+_WL_CACHE = {}
+
+
 def _workload(name, storage=None):
+    """the named column (generated once per process; callers get their own copy)"""
+    import dataclasses
     from paper_1712_07028_gb300 import workloads as W
-    wl = {"c0": W.column_c0, "c1": W.column_c1, "c3": W.column_c3, "c4": W.column_c4}[name]()
+    if name not in _WL_CACHE:
+        _WL_CACHE[name] = {"c0": W.column_c0, "c1": W.column_c1, "c3": W.column_c3, "c4": W.column_c4}[name]()
+    wl = dataclasses.replace(_WL_CACHE[name])
     if storage:
         wl.storage = storage
     return wl
+
+
+def _cpu_sample(name):
+    """the workload the CPU oracle steps for a column: the column itself up to ~2 M cells,
+    else a 128 x 128 x 256 sub-box of it at the column's sphere and bubble densities"""
+    from paper_1712_07028_gb300 import workloads as W
+    wl = _workload(name)
+    if wl.cells <= 2_200_000:
+        return wl
+    b = wl.bubbles[0].c
+    size = (128, 128, 256)
+    lo = tuple(int(min(max(0, round(b[k]) - size[k] // 2), (wl.nx, wl.ny, wl.nz)[k] - size[k])) for k in range(3))
+    return W.sub_box(wl, lo, size)
 
 
 def _job_ms(dist, ms, device):
@@ -167,18 +189,47 @@ def _sweep_sha():
     return h.hexdigest()
 
 
-def _cpu_baseline(wl, steps):
-    """the FP64 oracle as it stands, single thread, on a bounded sample of the workload"""
+def _cpu_baseline(name, budget_s=15.0):
+    """the FP64 oracle as it stands, single thread, on a bounded sample of the workload: whole
+    steps of the column (or of its sub-box) until about budget_s seconds have passed"""
     import oracle
     oracle.build()
+    wl = _cpu_sample(name)
     t0 = time.perf_counter()
     o = oracle.Sim(wl)
     t1 = time.perf_counter()
-    o.step(steps)
+    o.step(1)
     t2 = time.perf_counter()
-    return {"value": wl.cells * steps / (t2 - t1) / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "FP64 oracle, %s (%d cells): init (%.1f s) + %d full steps timed (%.1f s)"
-                      % (wl.name, wl.cells, t1 - t0, steps, t2 - t1)}
+    k = max(1, min(50, int(budget_s / max(t2 - t1, 1e-3))))
+    o.step(k)
+    t3 = time.perf_counter()
+    full = _workload(name)
+    what = ("the whole column" if wl.cells == full.cells else
+            "a %dx%dx%d sub-box of the %dx%dx%d column (%d bubbles, %d spheres inside it, walls on its faces)"
+            % (wl.nx, wl.ny, wl.nz, full.nx, full.ny, full.nz, len(wl.bubbles), len(wl.spheres)))
+    return {"value": wl.cells * k / (t3 - t2) / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "cpu": _cpu_model(), "nproc": os.cpu_count(),
+            "sample": "FP64 oracle, single thread, on %s: init (%.1f s), 1 warm-up step, %d full steps timed (%.1f s)"
+                      % (what, t1 - t0, k, t3 - t2)}
+
+
+def _cpu_model():
+    """the host CPU's model name (lscpu, else /proc/cpuinfo)"""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part", "hardware")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def _oracle_error(torch, lbm, W):
@@ -209,49 +260,53 @@ def _oracle_error(torch, lbm, W):
     return out
 
 
-def _cpu_baseline_leg(torch, lbm, W, wl):
-    return _cpu_baseline(wl, 20 if wl.cells <= 2_200_000 else 2), _oracle_error(torch, lbm, W)
-
-
-def _storage_run(torch, lbm, args, storage):
-    """MLUPS and sweep roofline of the benchmark workload with another PDF storage"""
-    wl = _workload(args.workload, storage)
+def _config_run(torch, lbm, name, storage, steps, warmup):
+    """MLUPS of one column and PDF storage, the bulk sweep's roofline from CUDA events around
+    its launches, and the whole step against the sweep's algorithmic bytes"""
+    wl = _workload(name, storage)
+    s_bytes = 4 if wl.storage == "f32" else 2
     sim = lbm.Sim(wl)
-    sim.step(max(3, args.warmup))
+    sim.step(max(3, warmup))
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    sim.step(args.steps)
+    sim.step(steps)
     e1.record(stream)
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = e0.elapsed_time(e1) / steps
     sim.profile(True)
-    sim.step(min(args.steps, 400))
+    sim.step(min(steps, 100))
     torch.cuda.synchronize()
     bulk_ms, rest_ms, nsw = sim.profile_read()
     sim.profile(False)
     fl = sim.fields()["flags"]
+    n_act = int(((fl == lbm.CELL_LIQUID) | (fl == lbm.CELL_INTERFACE)).sum().item())
     n_bulk = _bulk_cells(torch, lbm, fl, wl.bc)
-    per_launch = n_bulk * (38 * 2 + 1) + (wl.cells - n_bulk)
+    del fl
+    per_launch = n_bulk * (38 * s_bytes + 1) + (wl.cells - n_bulk)
+    step_bytes = n_act * (38 * s_bytes + 1) + (wl.cells - n_act)
     avg_s = bulk_ms / max(1, nsw) * 1e-3
     peak, _ = _peak_hbm()
     st = sim.status()
     sim.close()
-    return {"value": wl.cells * args.steps / (ms * 1e-3) / 1e6, "unit": "MLUPS", "ms_per_step": ms / args.steps,
+    torch.cuda.synchronize()
+    return {"workload": wl.name, "storage": wl.storage, "value": wl.cells / (ms * 1e-3) / 1e6, "unit": "MLUPS",
+            "ms_per_step": ms, "steps": steps, "bulk_kernel_ms": avg_s * 1e3,
             "bulk_kernel_achieved_gbs": per_launch / avg_s / 1e9, "bulk_kernel_frac": per_launch / avg_s / 1e9 / peak,
-            "bulk_kernel_ms": avg_s * 1e3, "rest_of_sweep_ms": rest_ms / max(1, nsw), "status": st}
+            "rest_of_sweep_ms": rest_ms / max(1, nsw), "active_cells": n_act, "bulk_cells": n_bulk,
+            "step_sweep_bytes": step_bytes, "step_frac": step_bytes / (ms * 1e-3) / 1e9 / peak, "status": st}
 
 
 def _split_run(torch, lbm, args):
-    """step time of the benchmark workload with bubble splitting every step and every 10 steps
+    """step time of the 128^3 column with bubble splitting every step and every 10 steps
     (the six labelling launches run on those steps; on the others they return at once), against
     the same workload without splitting timed alongside"""
     import dataclasses
     out = {}
     for every in (0, 1, 10):
-        wl = dataclasses.replace(_workload(args.workload), split_every=every, max_bubbles=16 if every else 0)
+        wl = dataclasses.replace(_workload("c1"), split_every=every, max_bubbles=16 if every else 0)
         sim = lbm.Sim(wl)
         sim.step(max(3, args.warmup))
         torch.cuda.synchronize()
@@ -356,9 +411,11 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    wl = _workload(args.workload)
-    # each timed step is one full oracle step of the workload; the number of executed steps is
-    # capped so the whole run stays within about a minute
+    full = _workload(args.workload, args.storage)
+    wl = _cpu_sample(args.workload)
+    # each timed step is one full oracle step of the sample (the column, or its sub-box at the
+    # column's densities); the number of executed steps is capped so the run stays within
+    # about a minute
     o = oracle.Sim(wl)
     t = time.perf_counter()
     o.step(1)
@@ -370,14 +427,18 @@ def run_reference(args):
     o.step(k)
     dt = time.perf_counter() - t0
     v = wl.cells * k / dt / 1e6
+    what = ("the whole column" if wl.cells == full.cells else "a %dx%dx%d sub-box of the column (%d bubbles, %d spheres)"
+            % (wl.nx, wl.ny, wl.nz, len(wl.bubbles), len(wl.spheres)))
     line = {"metric": METRIC, "value": v, "unit": "MLUPS", "impl": "reference", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / k * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "grid": [wl.nx, wl.ny, wl.nz], "bubbles": len(wl.bubbles),
-                       "spheres": len(wl.spheres), "storage": "f64 (oracle)", "parallelism": "replicas"},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "%d of %d requested steps executed after %d warm-up (each a full FP64 oracle step of %d cells)"
-                                       % (k, args.steps, warm + 1, wl.cells)},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / k * 1e3 * full.cells / wl.cells,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": full.name, "grid": [full.nx, full.ny, full.nz], "bubbles": len(full.bubbles),
+                       "spheres": len(full.spheres), "storage": "f64 (oracle)", "parallelism": "replicas"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle", "cpu": _cpu_model(),
+                             "nproc": os.cpu_count(),
+                             "sample": "%d of %d requested steps of %s executed after %d warm-up (each a full FP64 "
+                                       "oracle step of %d cells); ms_per_step scaled to the column's %d cells"
+                                       % (k, args.steps, what, warm + 1, wl.cells, full.cells)},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -439,7 +500,7 @@ def run_gpu(args):
     if not args.no_extras:
         # roofline of the dominant kernel (the bulk sweep): CUDA events around each launch
         sim.profile(True)
-        kp = min(args.steps, 400)
+        kp = min(args.steps, 100)
         sim.step(kp)
         torch.cuda.synchronize()
         bulk_ms, rest_ms, nsw = sim.profile_read()
@@ -447,12 +508,14 @@ def run_gpu(args):
         fl = sim.fields()["flags"]
         n_act = int(((fl == lbm.CELL_LIQUID) | (fl == lbm.CELL_INTERFACE)).sum().item())
         n_bulk = _bulk_cells(torch, lbm, fl, wl.bc)
+        del fl
         per_launch = n_bulk * (38 * s_bytes + 1) + (wl.cells - n_bulk) * 1
         avg_s = bulk_ms / max(1, nsw) * 1e-3
         rest_s = rest_ms / max(1, nsw) * 1e-3
         peak, peak_kind = _peak_hbm()
         achieved = per_launch / avg_s / 1e9
-        traffic = NCU_TRAFFIC["bytes_per_launch"] if NCU_TRAFFIC["sha1"] == _sweep_sha() else None
+        tr = NCU_TRAFFIC.get(wl.name + "/" + wl.storage)
+        traffic = tr["bytes_per_launch"] if tr and tr["sha1"] == _sweep_sha() else None
         step_bytes = n_act * (38 * s_bytes + 1) + (wl.cells - n_act)
         line["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                             "frac": achieved / peak, "traffic": traffic, "peak_source": peak_kind,
@@ -469,7 +532,7 @@ def run_gpu(args):
         # end to end through the public API from host inputs: context and tables from the host,
         # every step followed by the device->host read of the sphere forces (synchronising), the
         # fields copied to host at the end
-        ke = min(args.steps, 1000)
+        ke = min(args.steps, 1000 if wl.cells <= 2_200_000 else 100)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim2 = lbm.Sim(wl)
@@ -481,21 +544,31 @@ def run_gpu(args):
         t1 = time.perf_counter()
         h2d, d2h = sim2.copy_bytes()
         d2h += sum(v.numel() * v.element_size() for v in fields.values())
+        del fields
         line["e2e"] = {"value": wl.cells * ke * ws / (t1 - t0) / 1e6, "unit": "MLUPS",
                        "h2d_bytes_per_step": h2d / ke, "d2h_bytes_per_step": d2h / ke, "steps": ke,
                        "includes": "context + table upload + field init, per step lbm_step + lbm_forces "
                                    "(D2H of the sphere/bubble tables, sync), final fields D2H"}
         sim2.close()
+        del sim2
+        torch.cuda.synchronize()
         if rank == 0 and ws == 1:
-            # the same workload with PDFs stored as FP16 / BF16 deviations (collisions in FP32)
-            line["reduced_storage"] = {st: _storage_run(torch, lbm, args, st) for st in ("f16dev", "bf16dev")}
-            # bubble splitting (connected-component labelling) on the same workload
+            # the other columns: the 256x256x512 column in FP32 and FP16 deviations (the
+            # FP32-vs-FP16 configuration) and the 128^3 column
+            line["configs"] = {}
+            for name, storage, k in (("c3", "f32", 300), ("c3", "f16dev", 300), ("c1", "f32", 2000),
+                                     ("c1", "f16dev", 2000)):
+                if name == args.workload and storage == wl.storage:
+                    continue
+                line["configs"]["%s_%s" % (_workload(name).name, storage)] = _config_run(torch, lbm, name, storage, k, 5)
+            # bubble splitting (connected-component labelling) on the 128^3 column
             line["split"] = _split_run(torch, lbm, args)
             # the differentiation path (frozen liquid window) on its own workload
             line["adjoint"] = _adjoint_run(torch, lbm, W)
             # the CPU-baseline leg: the FP64 oracle timed on a bounded sample of the workload,
             # and the GPU path's error against it on the 32^3 column
-            line["cpu_baseline"], line["oracle_error"] = _cpu_baseline_leg(torch, lbm, W, wl)
+            line["cpu_baseline"] = _cpu_baseline(args.workload)
+            line["oracle_error"] = _oracle_error(torch, lbm, W)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:

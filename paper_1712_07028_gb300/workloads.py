@@ -303,3 +303,18 @@ def bubble_in_bed(phi: float, scale: int = 5, dt: float = 1.36e-4, r_p_cells: fl
     return Workload(name="bubble_bed_phi%g" % phi, nx=nx, ny=ny, nz=nz, tau=tau, g=(0.0, 0.0, -g),
                     bc=(FREESLIP, FREESLIP, WALL), open_top=True, hydrostatic=True, sigma=sigma,
                     sphere_mode=SPHERES_FREE, storage=storage, bubbles=[bub], spheres=sph)
+
+
+def sub_box(wl: Workload, lo: Tuple[int, int, int], size: Tuple[int, int, int], name: str = None) -> Workload:
+    """the part of a column inside the box [lo, lo + size) as a workload of its own (walls on
+    every face): the spheres whose centres keep the placement margin R + 1 inside the box and
+    the bubbles whose centres keep r + 2, shifted by -lo; the same densities of spheres and
+    bubbles as the column, at a size a CPU can step (a bounded sample of a large column)"""
+    def inside(c, m):
+        return all(lo[k] + m <= c[k] <= lo[k] + size[k] - 1 - m for k in range(3))
+
+    sph = [dataclasses.replace(s, x=tuple(s.x[k] - lo[k] for k in range(3))) for s in wl.spheres if inside(s.x, s.r + 1)]
+    bub = [Bubble(tuple(b.c[k] - lo[k] for k in range(3)), b.r) for b in wl.bubbles if inside(b.c, b.r + 2)]
+    return dataclasses.replace(wl, name=name or "%s_box%dx%dx%d" % (wl.name, *size), nx=size[0], ny=size[1], nz=size[2],
+                               bc=(WALL, WALL, WALL), bubbles=bub, spheres=sph)
+
