@@ -177,6 +177,12 @@ int lbm_forces(lbm_ctx* ctx, double* F, double* T, int n);
 /* Sphere state x[n][3], u[n][3], w[n][3] (host, FP64; any may be NULL).  Synchronises. */
 int lbm_spheres(lbm_ctx* ctx, double* x, double* u, double* w, int n);
 
+/* Lubrication force Fl[n][3] (host, FP64) of the first n spheres in the last sub-step of the
+ * last step (Sec. 2.3, Eq. lubrication: pairs closer than 2/3 of a cell, the gap floored at
+ * 0.2 x 2/3, mu = (tau - 1/2)/3, +F on one sphere and -F on the other); zero for spheres with
+ * no partner that close.  Synchronises. */
+int lbm_lubrication(lbm_ctx* ctx, double* Fl, int n);
+
 /* Bubble table (host, FP64; any may be NULL): reference volume V0[n], volume V[n], gas
  * density rho_g[n] for bubble ids 0..n-1.  An id that has merged into a larger bubble
  * reports the merged bubble's values.  Synchronises.

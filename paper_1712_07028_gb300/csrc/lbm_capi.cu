@@ -613,6 +613,18 @@ int lbm_spheres(lbm_ctx* c, double* x, double* u, double* w, int n) {
     return LBM_OK;
 }
 
+int lbm_lubrication(lbm_ctx* c, double* Fl, int n) {
+    if (!c || n < 0 || (n > 0 && !Fl)) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    if (int rf = flush(c)) return rf;
+    if (n > c->d.nsph) return LBM_EINVAL;
+    int rc = sync_tables(c);
+    if (rc) return rc;
+    for (int a = 0; a < n; a++)
+        for (int k = 0; k < 3; k++) Fl[3 * a + k] = c->sph_stage[a].Fl[k];
+    return LBM_OK;
+}
+
 int lbm_bubbles(lbm_ctx* c, double* V0, double* V, double* rho_g, int n) {
     if (!c || n < 0) return LBM_EINVAL;
     if (!c->started) return LBM_ESTATE;

@@ -22,7 +22,7 @@ S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW, S_FAST_SPHERE, S_MERGE, S
 
 # every entry point include/lbm.h declares
 EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_step",
-           "lbm_forces", "lbm_spheres", "lbm_bubbles", "lbm_bubble_roots", "lbm_bubble_splits", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
+           "lbm_forces", "lbm_spheres", "lbm_lubrication", "lbm_bubbles", "lbm_bubble_roots", "lbm_bubble_splits", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
            "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count",
            "lbm_bubble_volumes_noalloc", "lbm_forward_frozen", "lbm_adjoint_step", "lbm_destroy", "lbm_strerror")
 
@@ -65,6 +65,7 @@ def load():
     L.lbm_step.argtypes = [vp, i32]
     L.lbm_forces.argtypes = [vp, pd, pd, i32]
     L.lbm_spheres.argtypes = [vp, pd, pd, pd, i32]
+    L.lbm_lubrication.argtypes = [vp, pd, i32]
     L.lbm_bubbles.argtypes = [vp, pd, pd, pd, i32]
     L.lbm_bubble_roots.argtypes = [vp, ctypes.POINTER(i32), i32, ctypes.POINTER(i32)]
     L.lbm_bubble_splits.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
@@ -172,6 +173,13 @@ class Sim:
         x, u, w = (np.zeros((max(1, self.nsph), 3)) for _ in range(3))
         _check("lbm_spheres", load().lbm_spheres(self.ctx, _dp(x), _dp(u), _dp(w), self.nsph))
         return x[: self.nsph], u[: self.nsph], w[: self.nsph]
+
+    def lubrication(self):
+        """Fl [n][3]: the lubrication force of the last sub-step of the last step"""
+        self._bind_stream()
+        Fl = np.zeros((max(1, self.nsph), 3))
+        _check("lbm_lubrication", load().lbm_lubrication(self.ctx, _dp(Fl), self.nsph))
+        return Fl[: self.nsph]
 
     def bubbles(self):
         self._bind_stream()

@@ -67,7 +67,12 @@ def test_poiseuille_gpu(lbm):
 @pytest.mark.parametrize("nsph", [1, 2])
 def test_sphere_links_forces(lbm, nsph):
     """moving-wall bounce-back and momentum exchange (Eqs. bbrule, netforce, torque) with a
-    translating + rotating sphere, or two touching ones (links between obstacle nodes)"""
+    translating + rotating sphere, or two touching ones (links between obstacle nodes).
+    Bound 1e-5 relative, from the FP32 error budget of a link sum: the FP32 state differs from
+    the FP64 oracle's by eps_f ~ 5e-10 per PDF after 10-30 steps (the field check below:
+    |d rho| ~ 1e-8 over 19 PDFs); F and T sum N_l = 1098 links (r = 4), each with 2 eps_f,
+    so |dF| lies between sqrt(N_l) 2 eps_f ~ 3e-8 (incoherent) and N_l 2 eps_f ~ 1e-6 (coherent),
+    i.e. 3e-7 .. 1e-4 of the |F| ~ 0.01 - 0.1 here; measured up to 1.3e-6 relative"""
     if nsph == 1:
         sph = [W.Sphere((10.3, 11.6, 12.2), 4.0, 1.5, (0.01, -0.004, 0.002), (0.001, 0.002, -0.003))]
     else:
@@ -174,8 +179,7 @@ def test_c0_200_steps(lbm):
     assert drho <= 1e-5 and du <= 1e-6 and dphi <= 1e-5
     Fo, To = o.forces
     assert np.abs(st["F"] - Fo).max() <= 1e-3 * np.abs(Fo).max() + 1e-7
-    disp = np.abs(o.positions - np.array([s.x for s in wl.spheres])).max()
-    assert np.abs(st["sx"] - o.positions).max() <= 1e-3 * disp + 1e-7
+    assert np.abs(st["sx"] - o.positions).max() <= 1e-6
 
 
 @pytest.mark.parametrize("wl_name", ["c0", "cross"])
