@@ -63,7 +63,8 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
         list(ex.map(run, jobs))
     if jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp%d" % os.getpid()
-        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        # (-z defs: an undefined symbol fails the link instead of the first load)
+        run([cc, *ARCH, "-shared", "-Xlinker", "-z,defs", "-o", tmp, *objs, "-lcudart"])
         os.replace(tmp, LIB)
     return LIB
 

@@ -296,6 +296,8 @@ int first_step(lbm_ctx* c) {
     d.gz = p->g[2];
     for (int k = 0; k < 6; k++) d.special |= d.face[k] != FACE_WALL && !d.bc[k / 2];
     d.N = L.N;
+    d.div_nx = make_fastdiv((uint32_t)p->nx);
+    d.div_ny = make_fastdiv((uint32_t)p->ny);
     d.storage = p->storage;
     d.n_sub = p->n_substeps;
     d.sphere_mode = p->sphere_mode;
@@ -310,6 +312,7 @@ int first_step(lbm_ctx* c) {
         for (const Sphere& sp : c->sph_init) shell += 4.0 * 3.14159265358979 * (sp.R + 1.0) * (sp.R + 1.0);
         d.split_liq = shell > (double)kBoundaryGrid * 128.0 ? 1 : 0;
     }
+
     d.max_bub = p->max_bubbles;
     d.max_sph = p->max_spheres;
     d.wl_cap = (int)L.wl_cap;

@@ -162,6 +162,29 @@ struct Scalars {
 enum : uint32_t { S_UNSTABLE = 1, S_OVERFLOW = 2, S_BUBBLE_GONE = 4, S_BIN_OVERFLOW = 8, S_BAD_OWNER = 16, S_FAST_SPHERE = 32,
                   S_MERGE = 64, S_SPLIT = 128 };
 
+// division of a 32-bit unsigned integer by an invariant divisor d (1 <= d < 2^31) by a
+// multiply-high and shifts (Granlund and Montgomery, "Division by invariant integers using
+// multiplication", 1994, the round-up method with the n - t1 correction): exact for every
+// 32-bit dividend.  With l = ceil(log2 d): m = floor(2^32 (2^l - d) / d) + 1, s1 = min(l, 1),
+// s2 = max(l - 1, 0); n / d = (t + ((n - t) >> s1)) >> s2, t = mulhi(m, n).
+struct FastDiv {
+    uint32_t m;
+    int s1, s2;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+    int l = 0;
+    while ((1ull << l) < d) l++;
+    FastDiv f;
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1ull);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l - 1 > 0 ? l - 1 : 0;
+    return f;
+}
+__device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
+    const uint32_t t = __umulhi(f.m, n);
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 // all device pointers of one simulation; passed by value to every kernel
 struct Dev {
     int nx, ny, nz;
@@ -181,7 +204,8 @@ struct Dev {
     uint32_t* bub_cnt;        // [nbub] (splitting only) gas / interface cells per id
     int hydrostatic;          // the liquid starts in hydrostatic equilibrium below the open top
     double gz;                // g_z in FP64 (the hydrostatic start)
-    size_t N;
+    size_t N;                 // cells (< 2^32)
+    FastDiv div_nx, div_ny;   // cell index -> coordinates
     int storage;
     int n_sub;
     int sphere_mode;
@@ -231,11 +255,14 @@ constexpr int kBoundaryGrid = 152 * 2;   // blocks of the general boundary sweep
 __device__ __forceinline__ size_t cell_index(const Dev& d, int x, int y, int z) {
     return (size_t)x + (size_t)d.nx * ((size_t)y + (size_t)d.ny * (size_t)z);
 }
+// coordinates of cell i (N < 2^32: 32-bit division by the grid's invariant extents)
 __device__ __forceinline__ void cell_xyz(const Dev& d, size_t i, int& x, int& y, int& z) {
-    x = (int)(i % (size_t)d.nx);
-    size_t r = i / (size_t)d.nx;
-    y = (int)(r % (size_t)d.ny);
-    z = (int)(r / (size_t)d.ny);
+    const uint32_t n = (uint32_t)i;
+    const uint32_t r = fast_div(n, d.div_nx);
+    x = (int)(n - r * (uint32_t)d.nx);
+    const uint32_t q = fast_div(r, d.div_ny);
+    y = (int)(r - q * (uint32_t)d.ny);
+    z = (int)q;
 }
 // neighbour index of (x,y,z)+(dx,dy,dz); periodic axes wrap; beyond a wall: returns false
 __device__ __forceinline__ bool nbr(const Dev& d, int x, int y, int z, int dx, int dy, int dz, size_t& j) {

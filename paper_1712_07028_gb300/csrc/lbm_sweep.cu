@@ -103,16 +103,14 @@ __device__ __forceinline__ void sph_acc_warp_reduce(const Dev& d, const SphAcc& 
         for (int c = 0; c < 3; c++) {
             v[c] = mine ? acc.J[c] : 0.f;
             v[3 + c] = mine ? TJ[c] : 0.f;
-            iv[c] = mine ? acc.K[c] : 0;
-            iv[3 + c] = mine ? XK[c] : 0;
+            // the integer parts: one hardware warp reduction each
+            iv[c] = __reduce_add_sync(full, mine ? acc.K[c] : 0);
+            iv[3 + c] = __reduce_add_sync(full, mine ? XK[c] : 0);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int c = 0; c < 6; c++) {
-                v[c] += __shfl_xor_sync(full, v[c], o);
-                iv[c] += __shfl_xor_sync(full, iv[c], o);
-            }
+            for (int c = 0; c < 6; c++) v[c] += __shfl_xor_sync(full, v[c], o);
         }
         if (lane == leader) {
             SphereAcc& g = d.acc[P];
@@ -217,14 +215,14 @@ __device__ __noinline__ float face_link(const Dev& d, const typename Store<S>::T
     return 2.f * wq * ((rw - 1.f) + rw * (4.5f * cu * cu - 1.5f * u0sq)) - fob;
 }
 
-// pull-stream and collide one BULK cell (x, y, z) = i: every neighbour carries PDFs or lies
-// beyond a wall (halfway bounce-back by index select), no neighbour tests
-template <int S>
-__device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>::T* __restrict__ fa,
-                                          typename Store<S>::T* __restrict__ fb, int x, int y, int z, uint32_t i) {
+// the pulled PDFs fin of one BULK cell (x, y, z) = i: every neighbour carries PDFs or lies
+// beyond a wall (halfway bounce-back by index select), no neighbour tests.  CS: streaming
+// (evict-first) loads.
+template <int S, bool CS>
+__device__ __forceinline__ void bulk_load(const Dev& d, const typename Store<S>::T* __restrict__ fa, int x, int y, int z,
+                                          uint32_t i, float (&fin)[kQ]) {
     using T = typename Store<S>::T;
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
-    float fin[kQ];
     if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
         // y and z neighbours inside the grid (the same for a whole warp, which spans x): the
         // source of direction q is i - c_q . (1, nx, nx ny), a grid-uniform offset, except
@@ -239,9 +237,9 @@ __device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>:
             if (cx(q) == 1 && edge0) { if (perx) adj = (int32_t)nx; else wall = true; }
             if (cx(q) == -1 && edge1) { if (perx) adj = -(int32_t)nx; else wall = true; }
             const T* plane = fa + (size_t)(wall ? opp(q) : q) * d.N;
-            fin[q] = Store<S>::get_cs(plane, wall ? i : i - (uint32_t)o + (uint32_t)adj);   // modulo 2^32
+            const uint32_t src = wall ? i : i - (uint32_t)o + (uint32_t)adj;   // modulo 2^32
+            fin[q] = CS ? Store<S>::get_cs(plane, src) : Store<S>::get(plane, src);
         }
-        collide_store<S, true>(d, fb, i, fin);
         return;
     }
     const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
@@ -259,8 +257,17 @@ __device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>:
                           (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
         // halfway bounce-back: the cell's own post-collision PDF of the opposite direction
         const T* plane = fa + (size_t)(wall ? opp(q) : q) * d.N;
-        fin[q] = Store<S>::get_cs(plane, wall ? i : sx + sy + sz);
+        const uint32_t src = wall ? i : sx + sy + sz;
+        fin[q] = CS ? Store<S>::get_cs(plane, src) : Store<S>::get(plane, src);
     }
+}
+
+// pull-stream and collide one BULK cell (x, y, z) = i
+template <int S>
+__device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>::T* __restrict__ fa,
+                                          typename Store<S>::T* __restrict__ fb, int x, int y, int z, uint32_t i) {
+    float fin[kQ];
+    bulk_load<S, true>(d, fa, x, y, z, i, fin);
     collide_store<S, true>(d, fb, i, fin);
 }
 
@@ -302,6 +309,173 @@ __global__ void __launch_bounds__(128) sweep_fix_kernel(const Dev d, const int c
     }
 }
 
+// one active cell that is not BULK: walls, sphere links, gas links, interface mass exchange,
+// and the collision (the general instance); with Lean a liquid cell whose links are streaming,
+// wall and sphere links (and gas links, should a gas cell sit beside one): no mass exchange,
+// no face links.  Sphere sums go to acc, the liquid cells' bounce-back mass to sbb; an
+// interface cell reports its bubble (vb) and new fill level (vphi).
+template <int S, bool Lean>
+__device__ __forceinline__ void boundary_cell(const Dev& d, const typename Store<S>::T* __restrict__ fa,
+                                              typename Store<S>::T* __restrict__ fb, const float* __restrict__ phia,
+                                              float* __restrict__ phib, const int cur, const size_t i, SphAcc& acc,
+                                              float& sbb, uint32_t& vb, float& vphi, bool& isIFc) {
+    const size_t N = d.N;
+    const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
+    const uint8_t fl = d.flags[i];
+    int x, y, z;
+    cell_xyz(d, i, x, y, z);
+    const bool isIF = !Lean && (fl & F_IF) != 0;
+    const bool liqc = Lean || (fl & F_LIQ) != 0;
+    isIFc = isIF;
+    // every load is issued before any link is resolved: neighbour indices and types,
+    // then the pulled PDFs, owners and fill levels (predicated on the types)
+    float fo[kQ];
+    uint32_t src[kQ];
+    uint32_t fsv[kQ];   // neighbour type, 0xff beyond a wall
+#pragma unroll
+    for (int q = 0; q < kQ; q++) fo[q] = Store<S>::get(fa, (size_t)q * N + i);
+    {   // neighbour indices with periodic wrap; sources beyond a wall flagged 0xff
+        const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+        const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+        const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
+        const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
+        const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
+        const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
+        const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
+#pragma unroll
+        for (int q = 1; q < kQ; q++) {
+            const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
+            const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
+            const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
+            const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
+                              (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
+            src[q] = wall ? (uint32_t)i : sx + sy + sz;
+            fsv[q] = wall ? 0xffu : (uint32_t)d.flags[sx + sy + sz];
+        }
+    }
+    float fv[kQ];       // pulled PDF (active source) or the source's owner (bit pattern)
+    float phn[kQ];      // fill level of an interface source (interface cells only)
+#pragma unroll
+    for (int q = 1; q < kQ; q++) {
+        const uint32_t t = fsv[q];
+        fv[q] = 0.f;
+        phn[q] = 0.f;
+        if (t != 0xffu) {
+            if (t & F_ACTIVE) fv[q] = Store<S>::get(fa, (size_t)q * N + src[q]);
+            else fv[q] = __uint_as_float(d.owner[src[q]]);
+            if (isIF && (t & F_IF)) phn[q] = phia[src[q]];
+        }
+    }
+    float drho0 = 0.f, j0x = 0.f, j0y = 0.f, j0z = 0.f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) {
+        drho0 += fo[q];
+        j0x += cx(q) * fo[q]; j0y += cy(q) * fo[q]; j0z += cz(q) * fo[q];
+    }
+    const float rho0 = 1.f + drho0;
+    // the force the last collision applied: on the liquid mass, phi g in an interface cell
+    const float gw0 = isIF ? phia[i] : 1.f;
+    const float u0x = (j0x - 0.5f * rho0 * gw0 * gx) / rho0;
+    const float u0y = (j0y - 0.5f * rho0 * gw0 * gy) / rho0;
+    const float u0z = (j0z - 0.5f * rho0 * gw0 * gz) / rho0;
+    const float u0sq = u0x * u0x + u0y * u0y + u0z * u0z;
+    const float phix = isIF ? phia[i] : 0.f;
+    const float kap = (isIF && d.kappa) ? d.kappa[i] : 0.f;
+    const bool atface = !Lean && at_special_face(d, x, y, z);
+    // the cell's sphere: the owner of its first obstacle link (links into a second
+    // sphere take sph_link_other); the wall velocity is needed only as c_q . u_w, and
+    // c_q . u_w at the link midpoint x - c_q/2 equals c_q . (u_P + w_P x r), r = x - x_P
+    // (c_q . (w_P x c_q) = 0): one cell-centre velocity serves every link
+    uint32_t P0 = kNone;
+#pragma unroll
+    for (int q = kQ - 1; q >= 1; q--)
+        if (fsv[q] != 0xffu && (fsv[q] & F_OBS)) P0 = __float_as_uint(fv[q]);
+    float ucx = 0.f, ucy = 0.f, ucz = 0.f;
+    if (P0 < (uint32_t)d.nsph) {
+        sph_begin(d, acc, P0, x, y, z);
+        ucx = acc.u[0] + acc.w[1] * acc.r[2] - acc.w[2] * acc.r[1];
+        ucy = acc.u[1] + acc.w[2] * acc.r[0] - acc.w[0] * acc.r[2];
+        ucz = acc.u[2] + acc.w[0] * acc.r[1] - acc.w[1] * acc.r[0];
+    }
+    float fin[kQ];
+    float dm = 0.f;
+    fin[0] = fo[0];
+#pragma unroll
+    for (int q = 1; q < kQ; q++) {
+        const int qb = opp(q);
+        const uint32_t t = fsv[q];
+        if (t == 0xffu) {
+            if (atface)
+                fin[q] = face_link<S>(d, fa, phia, cur, q, x, y, z, fo[qb], rho0, u0x, u0y, u0z, phix, kap, isIF,
+                                      liqc, dm, sbb);
+            else
+                fin[q] = fo[qb];                                // no-slip wall
+        } else if (t & F_ACTIVE) {
+            fin[q] = fv[q];                                     // Eq. LBE1
+            if (isIF) {  // link to the neighbour x + c_qb: s (f*_q(x+c_qb) - f*_qb(x))
+                const float sw = (t & F_LIQ) ? 1.f : 0.5f * (phix + phn[q]);
+                dm += sw * (fin[q] - fo[qb]);
+            }
+        } else if (t & F_OBS) {                                 // Eq. bbrule
+            const uint32_t P = __float_as_uint(fv[q]);
+            // a sphere beside an interface cell: the next gas-pressure pass scans it
+            if (isIF && P < (uint32_t)d.nsph) d.gasflag[(size_t)cur * d.max_sph + P] = 1u;
+            if (P == P0) {
+                const float corr = 6.f * wgt(q) * rho0 * (cx(q) * ucx + cy(q) * ucy + cz(q) * ucz);
+                fin[q] = fo[qb] + corr;
+                // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
+                const float dev = 2.f * fo[qb] + corr;
+                acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
+                acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
+                if (liqc) sbb += corr;
+            } else if (P < (uint32_t)d.nsph) {
+                const float corr = sph_link_other(d, q, P, x, y, z, rho0, fo[qb]);
+                fin[q] = fo[qb] + corr;
+                if (liqc) sbb += corr;
+            } else {
+                fin[q] = fo[qb];
+            }
+        } else {                                                // gas: Eq. fsk
+            const uint32_t bb = __float_as_uint(fv[q]);
+            const float rg = bb < (uint32_t)d.nbub ? d.bub[bb].rho_gf : d.rho_g0;
+            const float rw = rg + 6.f * d.sigma * kap;
+            const float cu = cx(q) * u0x + cy(q) * u0y + cz(q) * u0z;
+            // -f*_qb + 2 e+_q, in deviations: 2 (e+_q - w_q) - (f*_qb - w_q)
+            fin[q] = 2.f * wgt(q) * ((rw - 1.f) + rw * (4.5f * cu * cu - 1.5f * u0sq)) - fo[qb];
+        }
+    }
+    float gw = 1.f;   // the body force acts on the liquid mass: phi g in an interface cell
+    if (isIF) {
+        const float mnew = (d.mass[i] + d.sc->share_f) + dm;
+        float drho = 0.f;
+#pragma unroll
+        for (int q = 0; q < kQ; q++) drho += fin[q];
+        const float rho = 1.f + drho;
+        d.mass[i] = mnew;
+        phib[i] = mnew / rho;
+        vb = d.owner[i];
+        vphi = mnew / rho;
+        gw = vphi;
+        // an interface cell is a boundary cell of the liquid with a gas neighbour
+        // (Sec. 2.2): one left without any gas neighbour is liquid now (filled).
+        // phi >= 1 + eps  <=>  m - rho >= eps rho, taken as (m - 1) - drho so that a
+        // density deviation below FP32's resolution of 1 still decides it;
+        // phi <= -eps  <=>  m <= -eps rho
+        bool gasnb = false;
+#pragma unroll
+        for (int q = 1; q < kQ; q++) gasnb |= fsv[q] != 0xffu && (fsv[q] & F_GAS);
+        uint8_t mk = 0;
+        if (!gasnb) mk = K_FILLED;
+        else if ((mnew - 1.f) - drho >= d.eps * rho) mk = K_FILLED;
+        else if (mnew <= -d.eps * rho) mk = K_EMPTIED;
+        if (mk) {
+            d.mark[i] = mk;
+            wl_push(d.wl_conv, &d.sc->n_conv, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
+        }
+    }
+    collide_store<S>(d, fb, i, fin, gw);
+}
+
 // every other active cell: walls, sphere links, gas links, interface mass exchange.  Two
 // instances: the general one takes the general segment of the list (interface cells and cells
 // on a free-slip or open face); the lean one (Lean) the liquid segment, cells whose links are
@@ -323,7 +497,6 @@ __global__ void __launch_bounds__(128, Lean ? 4 : 1) sweep_boundary_kernel(const
     const uint32_t* __restrict__ list = d.wl_slow;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
     __shared__ uint32_t sNif[4], sVb[4];
     __shared__ double sV[4];
     __shared__ float sS[4];
@@ -340,159 +513,7 @@ __global__ void __launch_bounds__(128, Lean ? 4 : 1) sweep_boundary_kernel(const
         bool isIFc = false;
         if (k < n) {
             const size_t i = Lean ? list[(uint32_t)N - 1u - k] : blist_cell(d, k, ngen);
-            const uint8_t fl = d.flags[i];
-            int x, y, z;
-            cell_xyz(d, i, x, y, z);
-            const bool isIF = !Lean && (fl & F_IF) != 0;
-            const bool liqc = Lean || (fl & F_LIQ) != 0;
-            isIFc = isIF;
-            // every load is issued before any link is resolved: neighbour indices and types,
-            // then the pulled PDFs, owners and fill levels (predicated on the types)
-            float fo[kQ];
-            uint32_t src[kQ];
-            uint32_t fsv[kQ];   // neighbour type, 0xff beyond a wall
-#pragma unroll
-            for (int q = 0; q < kQ; q++) fo[q] = Store<S>::get(fa, (size_t)q * N + i);
-            {   // neighbour indices with periodic wrap; sources beyond a wall flagged 0xff
-                const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
-                const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
-                const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
-                const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
-                const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
-                const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
-                const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
-#pragma unroll
-                for (int q = 1; q < kQ; q++) {
-                    const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
-                    const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
-                    const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
-                    const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
-                                      (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
-                    src[q] = wall ? (uint32_t)i : sx + sy + sz;
-                    fsv[q] = wall ? 0xffu : (uint32_t)d.flags[sx + sy + sz];
-                }
-            }
-            float fv[kQ];       // pulled PDF (active source) or the source's owner (bit pattern)
-            float phn[kQ];      // fill level of an interface source (interface cells only)
-#pragma unroll
-            for (int q = 1; q < kQ; q++) {
-                const uint32_t t = fsv[q];
-                fv[q] = 0.f;
-                phn[q] = 0.f;
-                if (t != 0xffu) {
-                    if (t & F_ACTIVE) fv[q] = Store<S>::get(fa, (size_t)q * N + src[q]);
-                    else fv[q] = __uint_as_float(d.owner[src[q]]);
-                    if (isIF && (t & F_IF)) phn[q] = phia[src[q]];
-                }
-            }
-            float drho0 = 0.f, j0x = 0.f, j0y = 0.f, j0z = 0.f;
-#pragma unroll
-            for (int q = 0; q < kQ; q++) {
-                drho0 += fo[q];
-                j0x += cx(q) * fo[q]; j0y += cy(q) * fo[q]; j0z += cz(q) * fo[q];
-            }
-            const float rho0 = 1.f + drho0;
-            // the force the last collision applied: on the liquid mass, phi g in an interface cell
-            const float gw0 = isIF ? phia[i] : 1.f;
-            const float u0x = (j0x - 0.5f * rho0 * gw0 * gx) / rho0;
-            const float u0y = (j0y - 0.5f * rho0 * gw0 * gy) / rho0;
-            const float u0z = (j0z - 0.5f * rho0 * gw0 * gz) / rho0;
-            const float u0sq = u0x * u0x + u0y * u0y + u0z * u0z;
-            const float phix = isIF ? phia[i] : 0.f;
-            const float kap = (isIF && d.kappa) ? d.kappa[i] : 0.f;
-            const bool atface = !Lean && at_special_face(d, x, y, z);
-            // the cell's sphere: the owner of its first obstacle link (links into a second
-            // sphere take sph_link_other); the wall velocity is needed only as c_q . u_w, and
-            // c_q . u_w at the link midpoint x - c_q/2 equals c_q . (u_P + w_P x r), r = x - x_P
-            // (c_q . (w_P x c_q) = 0): one cell-centre velocity serves every link
-            uint32_t P0 = kNone;
-#pragma unroll
-            for (int q = kQ - 1; q >= 1; q--)
-                if (fsv[q] != 0xffu && (fsv[q] & F_OBS)) P0 = __float_as_uint(fv[q]);
-            float ucx = 0.f, ucy = 0.f, ucz = 0.f;
-            if (P0 < (uint32_t)d.nsph) {
-                sph_begin(d, acc, P0, x, y, z);
-                ucx = acc.u[0] + acc.w[1] * acc.r[2] - acc.w[2] * acc.r[1];
-                ucy = acc.u[1] + acc.w[2] * acc.r[0] - acc.w[0] * acc.r[2];
-                ucz = acc.u[2] + acc.w[0] * acc.r[1] - acc.w[1] * acc.r[0];
-            }
-            float fin[kQ];
-            float dm = 0.f;
-            fin[0] = fo[0];
-#pragma unroll
-            for (int q = 1; q < kQ; q++) {
-                const int qb = opp(q);
-                const uint32_t t = fsv[q];
-                if (t == 0xffu) {
-                    if (atface)
-                        fin[q] = face_link<S>(d, fa, phia, cur, q, x, y, z, fo[qb], rho0, u0x, u0y, u0z, phix, kap, isIF,
-                                              liqc, dm, sbb);
-                    else
-                        fin[q] = fo[qb];                                // no-slip wall
-                } else if (t & F_ACTIVE) {
-                    fin[q] = fv[q];                                     // Eq. LBE1
-                    if (isIF) {  // link to the neighbour x + c_qb: s (f*_q(x+c_qb) - f*_qb(x))
-                        const float sw = (t & F_LIQ) ? 1.f : 0.5f * (phix + phn[q]);
-                        dm += sw * (fin[q] - fo[qb]);
-                    }
-                } else if (t & F_OBS) {                                 // Eq. bbrule
-                    const uint32_t P = __float_as_uint(fv[q]);
-                    // a sphere beside an interface cell: the next gas-pressure pass scans it
-                    if (isIF && P < (uint32_t)d.nsph) d.gasflag[(size_t)cur * d.max_sph + P] = 1u;
-                    if (P == P0) {
-                        const float corr = 6.f * wgt(q) * rho0 * (cx(q) * ucx + cy(q) * ucy + cz(q) * ucz);
-                        fin[q] = fo[qb] + corr;
-                        // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
-                        const float dev = 2.f * fo[qb] + corr;
-                        acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
-                        acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
-                        if (liqc) sbb += corr;
-                    } else if (P < (uint32_t)d.nsph) {
-                        const float corr = sph_link_other(d, q, P, x, y, z, rho0, fo[qb]);
-                        fin[q] = fo[qb] + corr;
-                        if (liqc) sbb += corr;
-                    } else {
-                        fin[q] = fo[qb];
-                    }
-                } else {                                                // gas: Eq. fsk
-                    const uint32_t bb = __float_as_uint(fv[q]);
-                    const float rg = bb < (uint32_t)d.nbub ? d.bub[bb].rho_gf : d.rho_g0;
-                    const float rw = rg + 6.f * d.sigma * kap;
-                    const float cu = cx(q) * u0x + cy(q) * u0y + cz(q) * u0z;
-                    // -f*_qb + 2 e+_q, in deviations: 2 (e+_q - w_q) - (f*_qb - w_q)
-                    fin[q] = 2.f * wgt(q) * ((rw - 1.f) + rw * (4.5f * cu * cu - 1.5f * u0sq)) - fo[qb];
-                }
-            }
-            float gw = 1.f;   // the body force acts on the liquid mass: phi g in an interface cell
-            if (isIF) {
-                const float mnew = (d.mass[i] + d.sc->share_f) + dm;
-                float drho = 0.f;
-#pragma unroll
-                for (int q = 0; q < kQ; q++) drho += fin[q];
-                const float rho = 1.f + drho;
-                d.mass[i] = mnew;
-                phib[i] = mnew / rho;
-                vb = d.owner[i];
-                vphi = mnew / rho;
-                gw = vphi;
-                // an interface cell is a boundary cell of the liquid with a gas neighbour
-                // (Sec. 2.2): one left without any gas neighbour is liquid now (filled).
-                // phi >= 1 + eps  <=>  m - rho >= eps rho, taken as (m - 1) - drho so that a
-                // density deviation below FP32's resolution of 1 still decides it;
-                // phi <= -eps  <=>  m <= -eps rho
-                bool gasnb = false;
-#pragma unroll
-                for (int q = 1; q < kQ; q++) gasnb |= fsv[q] != 0xffu && (fsv[q] & F_GAS);
-                uint8_t mk = 0;
-                if (!gasnb) mk = K_FILLED;
-                else if ((mnew - 1.f) - drho >= d.eps * rho) mk = K_FILLED;
-                else if (mnew <= -d.eps * rho) mk = K_EMPTIED;
-                if (mk) {
-                    d.mark[i] = mk;
-                    wl_push(d.wl_conv, &d.sc->n_conv, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
-                }
-            }
-            collide_store<S>(d, fb, i, fin, gw);
+            boundary_cell<S, Lean>(d, fa, fb, phia, phib, cur, i, acc, sbb, vb, vphi, isIFc);
         }
 
         if (Lean) {
