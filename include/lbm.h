@@ -243,6 +243,28 @@ int lbm_status(lbm_ctx* ctx, uint32_t* status);
  * J = sum over the window's steps t of jdir . (sum over spheres of the momentum-exchange
  * force F_P(t), Eqs. netforce and momentum_transfer). */
 
+/* Set the relaxation time tau (> 1/2; lambda_+ = -1/tau, lambda_- from the magic relation,
+ * Sec. 2.1) and the body force g[3] (host) of the steps that follow, so that a window can be
+ * evaluated at other parameters.  Between steps only: the last step's end-of-step kernels are
+ * run first with the parameters it had.  Synchronises.  LBM_EINVAL for tau <= 1/2 or a
+ * non-finite g. */
+int lbm_set_params(lbm_ctx* ctx, double tau, const double g[3]);
+
+/* Replace the current post-collision PDFs by f[19][N] (device, FP32 deviations f*_q - w_q in
+ * the layout lbm_export_state writes): the start state of a window.  The cell types, masses and
+ * spheres stay.  Window conditions as below (else LBM_ESTATE).  Asynchronous. */
+int lbm_import_state(lbm_ctx* ctx, const float* f);
+
+/* The objective of a window accumulated on the device: from this call on, every step adds
+ * jdir . (sum over spheres of the momentum-exchange force F_P of the step, Eqs. netforce and
+ * momentum_transfer) to an FP64 scalar, which this call resets to 0 (jdir[3]: host; NULL stops
+ * the accumulation).  The last step's force is not counted.  Synchronises. */
+int lbm_objective(lbm_ctx* ctx, const double jdir[3]);
+
+/* The objective accumulated since lbm_objective, including the last step's force, into *J
+ * (host).  Synchronises. */
+int lbm_objective_read(lbm_ctx* ctx, double* J);
+
 /* One forward step of the window from f_in to f_out (device, distinct): streaming with
  * bounce-back at walls and spheres, then the TRT/Guo collision (Eqs. LBE1, bbrule, LBE2), the
  * same arithmetic as lbm_step.  Used to recompute states between checkpoints.  Asynchronous. */

@@ -27,19 +27,21 @@ def _state_like(sim):
 
 def forward_window(sim: _lbm.Sim, nsteps: int, jdir, every: int):
     """run nsteps ordinary steps from the current state; returns (J, checkpoints), the
-    checkpoints being f* at steps 0, every, 2 every, ... (FP32 deviation tensors)"""
+    checkpoints being f* at steps 0, every, 2 every, ... (FP32 deviation tensors).  J is
+    accumulated on the device (lbm_objective) and read once at the end."""
     if every < 1 or nsteps < 1:
         raise ValueError("nsteps and the checkpoint interval must be positive")
-    jd = np.asarray(jdir, dtype=np.float64).reshape(3)
     sim.step(0)
+    sim.objective(jdir)
     ckpts = []
-    J = 0.0
-    for t in range(nsteps):
-        if t % every == 0:
-            ckpts.append(sim.export_state()["f"])
-        sim.step(1)
-        F, _ = sim.forces()
-        J += float(F.sum(axis=0) @ jd)
+    t = 0
+    while t < nsteps:
+        ckpts.append(sim.export_state()["f"])
+        k = min(every, nsteps - t)
+        sim.step(k)
+        t += k
+    J = sim.objective_read()
+    sim.objective(None)
     return J, ckpts
 
 
@@ -82,24 +84,36 @@ def window_gradient(sim: _lbm.Sim, nsteps: int, jdir=(1.0, 0.0, 0.0), every: int
 
 
 class LBMWindow(torch.autograd.Function):
-    """J(tau, g) of a frozen liquid window as a differentiable torch function.
+    """J(tau, g, f0) of a frozen liquid window as a differentiable torch function.
 
-    ``LBMWindow.apply(tau, g, sim, nsteps, jdir, every)``: tau a 0-d and g a 3-vector float64
-    tensor, equal to the simulation's parameters (the library runs with the parameters it was
-    created with; the tensors mark what to differentiate).  Returns J as a 0-d float64 tensor;
-    backward gives dJ/dtau and dJ/dg from the adjoint, with checkpoints every ``every`` steps."""
+    ``LBMWindow.apply(tau, g, f0, sim, nsteps, jdir, every)``: tau a 0-d and g a 3-vector
+    float64 tensor, f0 the window's start state (FP32 deviations [19,z,y,x] on the device, as
+    ``sim.export_state()["f"]`` gives it).  Every call sets the simulation's relaxation time and
+    body force to (tau, g), imports f0 and runs the window, so J can be evaluated at any point
+    (finite differences, optimisation loops).  Returns J as a 0-d float64 tensor; backward
+    gives dJ/dtau, dJ/dg and dJ/df0 from the adjoint, with checkpoints every ``every`` steps."""
 
     @staticmethod
-    def forward(ctx, tau, g, sim, nsteps, jdir, every):
+    def forward(ctx, tau, g, f0, sim, nsteps, jdir, every):
+        tv, gv = float(tau), [float(v) for v in g]
         p = sim.params
-        if abs(float(tau) - p.tau) > 1e-12 * abs(p.tau) or any(abs(float(g[k]) - p.g[k]) > 1e-15 for k in range(3)):
-            raise ValueError("tau and g must equal the simulation's parameters")
+        if tv != p.tau or any(gv[k] != p.g[k] for k in range(3)):
+            sim.set_params(tv, gv)
+        sim.step(0)
+        sim.import_state(f0.detach())
         J, ck = forward_window(sim, int(nsteps), jdir, int(every))
         ctx.sim, ctx.nsteps, ctx.jdir, ctx.every, ctx.ckpts = sim, int(nsteps), jdir, int(every), ck
+        ctx.params = (tv, gv)
         return torch.tensor(J, dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, gJ):
-        dtau, dg, _ = backward_window(ctx.sim, ctx.nsteps, ctx.jdir, ctx.every, ctx.ckpts)
+        sim = ctx.sim
+        tv, gv = ctx.params
+        p = sim.params
+        if tv != p.tau or any(gv[k] != p.g[k] for k in range(3)):   # another evaluation ran since
+            sim.set_params(tv, gv)
+        dtau, dg, lam = backward_window(sim, ctx.nsteps, ctx.jdir, ctx.every, ctx.ckpts)
         ctx.ckpts = None
-        return gJ * dtau, gJ * torch.tensor(dg, dtype=torch.float64), None, None, None, None
+        gf0 = (gJ.to(lam.dtype) * lam) if ctx.needs_input_grad[2] else None
+        return gJ * dtau, gJ * torch.tensor(dg, dtype=torch.float64), gf0, None, None, None, None

@@ -294,20 +294,22 @@ __global__ void __launch_bounds__(128, 6) adjoint_bulk_kernel(const Dev d, const
                     idx = wall ? i : sx + sy + sz;
                 }
             };
+            // each value is read and written once per reverse step: streaming (evict-first)
+            // accesses, which keep the small arrays of the boundary kernel beside it in L2
             float fin[kQ], lam[kQ];
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
                 uint32_t pl, ix;
                 link(q, pl, ix);
-                fin[q] = f[(size_t)pl * N + ix];
-                lam[q] = lam_in[(size_t)q * N + i];
+                fin[q] = __ldcs(f + (size_t)pl * N + ix);
+                lam[q] = __ldcs(lam_in + (size_t)q * N + i);
             }
             const AdjOut o = collide_adjoint(d, fin, lam, acc);
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
                 uint32_t pl, ix;
                 link(q, pl, ix);
-                lam_out[(size_t)pl * N + ix] = adj_in_q(d, q, lam, o);
+                __stcs(lam_out + (size_t)pl * N + ix, adj_in_q(d, q, lam, o));
             }
         }
     }

@@ -55,6 +55,7 @@ struct lbm_ctx {
     // links stream (to be joined by the sweep's rest), or enqueued and already joined
     int links_state;
     uint64_t h2d_bytes, d2h_bytes;   // host <-> device copies made by the library
+    struct { uint32_t on; double j[3]; } obj_stage;   // host side of lbm_objective's upload
     // second stream and fork/join events of the concurrent bulk / boundary sweep
     cudaStream_t side, side2;   // the general and the lean boundary sweep
     cudaEvent_t fork, join, fork2, join2, fork3, join3, fork4, join4, join5;
@@ -720,6 +721,66 @@ static int adjoint_ready(lbm_ctx* c) {
     if (c->p.storage != LBM_STORE_F32 || c->d.ngeo != 0 || c->p.sphere_mode != LBM_SPHERES_FIXED || c->d.special)
         return LBM_ESTATE;
     return flush(c);
+}
+
+int lbm_import_state(lbm_ctx* c, const float* f) {
+    if (!c || !f) return LBM_EINVAL;
+    int rc = adjoint_ready(c);
+    if (rc) return rc;
+    const size_t bytes = sizeof(float) * kQ * c->d.N;
+    return cuda_fail(cudaMemcpyAsync(c->d.f[c->cur], f, bytes, cudaMemcpyDeviceToDevice, c->stream));
+}
+
+int lbm_set_params(lbm_ctx* c, double tau, const double g[3]) {
+    if (!c || !g || !(tau > 0.5) || !(tau < 100.0)) return LBM_EINVAL;
+    for (int k = 0; k < 3; k++)
+        if (!std::isfinite(g[k])) return LBM_EINVAL;
+    c->p.tau = tau;
+    for (int k = 0; k < 3; k++) c->p.g[k] = g[k];
+    if (!c->started) return LBM_OK;   // first_step takes them from p
+    int rc = flush(c);   // the last step's end-of-step kernels run with the parameters it had
+    if (rc) return rc;
+    if ((rc = cuda_fail(cudaStreamSynchronize(c->stream)))) return rc;
+    Dev& d = c->d;
+    d.tau = (float)tau;
+    const double lp = -1.0 / tau;
+    d.lp = (float)lp;
+    d.lm = (float)(1.0 / ((3.0 / 16.0) / (1.0 / lp + 0.5) - 0.5));
+    for (int k = 0; k < 3; k++) { d.g[k] = (float)g[k]; d.gd[k] = g[k]; }
+    // the step graphs hold the kernels' arguments: instantiate them again at the next step
+    for (int v = 0; v < 4; v++)
+        if (c->graph_ready[v]) {
+            cudaGraphExecDestroy(c->graph[v]);
+            c->graph_ready[v] = false;
+        }
+    return LBM_OK;
+}
+
+int lbm_objective(lbm_ctx* c, const double jdir[3]) {
+    if (!c) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    int rc = flush(c);   // the last step's force belongs to no window opened now
+    if (rc) return rc;
+    c->obj_stage.on = jdir ? 1u : 0u;
+    for (int k = 0; k < 3; k++) c->obj_stage.j[k] = jdir ? jdir[k] : 0.0;
+    Scalars* sc = c->d.sc;
+    cudaStream_t s = c->stream;
+    const double zero = 0.0;
+    if ((rc = cuda_fail(cudaMemcpyAsync(&sc->obj_on, &c->obj_stage.on, sizeof(uint32_t), cudaMemcpyHostToDevice, s)))) return rc;
+    if ((rc = cuda_fail(cudaMemcpyAsync(sc->obj_j, c->obj_stage.j, sizeof(double) * 3, cudaMemcpyHostToDevice, s)))) return rc;
+    if ((rc = cuda_fail(cudaMemcpyAsync(&sc->obj, &zero, sizeof(double), cudaMemcpyHostToDevice, s)))) return rc;
+    c->h2d_bytes += sizeof(uint32_t) + 4 * sizeof(double);
+    return cuda_fail(cudaStreamSynchronize(s));   // (the host sources are gone after return)
+}
+
+int lbm_objective_read(lbm_ctx* c, double* J) {
+    if (!c || !J) return LBM_EINVAL;
+    if (!c->started) return LBM_ESTATE;
+    int rc = flush(c);   // the last step's force
+    if (rc) return rc;
+    if ((rc = cuda_fail(cudaMemcpyAsync(J, &c->d.sc->obj, sizeof(double), cudaMemcpyDeviceToHost, c->stream)))) return rc;
+    c->d2h_bytes += sizeof(double);
+    return cuda_fail(cudaStreamSynchronize(c->stream));
 }
 
 int lbm_forward_frozen(lbm_ctx* c, const float* f_in, float* f_out) {

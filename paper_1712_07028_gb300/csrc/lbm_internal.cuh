@@ -156,6 +156,9 @@ struct Scalars {
     uint32_t nbub_hw;     // one past the highest bubble id that ever carried cells
     uint32_t split_fail;  // this split step cannot split (part table full, or a find ran too long)
     uint32_t n_split_cells;   // gas and interface cells listed by this split step
+    uint32_t obj_on;      // each step adds obj_j . (sum over spheres of F) to obj (lbm_objective)
+    double obj_j[3];
+    double obj;
 };
 
 // status bits (latched; reported through lbm_status and the copy-out calls)
@@ -753,12 +756,11 @@ void launch_init(const Dev& d, const double* bub_geom_dev, cudaStream_t s);
 void launch_bulk_all(const Dev& d, cudaStream_t s);
 void launch_fields(const Dev& d, int cur, float* rho, float* u, float* phi, uint8_t* flags, cudaStream_t s);
 void launch_export(const Dev& d, int cur, float* f, uint8_t* flags, float* m, float* phi, int32_t* owner, float* kappa, cudaStream_t s);
-void launch_import(const Dev& d, int cur, const float* f, const uint8_t* flags, const float* m, const float* phi, const int32_t* owner, const float* kappa, cudaStream_t s);
 void launch_mass(const Dev& d, int cur, cudaStream_t s);
 void launch_frozen_forward(const Dev& d, const float* f_in, float* f_out, cudaStream_t s, cudaStream_t side,
                            cudaEvent_t fork, cudaEvent_t join);
 
-constexpr int kAdjSlots = 64;
+constexpr int kAdjSlots = 512;   // FP64 slots of the adjoint's parameter sums (block id mod slots)
 void launch_adjoint(const Dev& d, const float* f_fwd, const float* lam_in, float* lam_out, float* srho,
                     const float jdir[3], double* part, bool moving_walls, cudaStream_t s, cudaStream_t side,
                     cudaEvent_t fork, cudaEvent_t join);

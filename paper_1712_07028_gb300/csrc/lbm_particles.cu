@@ -49,6 +49,9 @@ __device__ inline void sph_prepare_one(const Dev& d, const int P) {
         a.J[k] = 0.0; a.TJ[k] = 0.0; a.K[k] = 0ull; a.XK[k] = 0ull; a.C[k] = 0.0; a.TC[k] = 0.0;
         s.x0[k] = s.x[k];
     }
+    // a differentiated window's objective: jdir . F summed over spheres and steps, on the device
+    const Scalars& c = *d.sc;
+    if (c.obj_on) atomicAdd(&d.sc->obj, c.obj_j[0] * s.F[0] + c.obj_j[1] * s.F[1] + c.obj_j[2] * s.F[2]);
 }
 __global__ void sph_prepare_kernel(const Dev d) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;

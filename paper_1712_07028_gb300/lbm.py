@@ -24,7 +24,8 @@ S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW, S_FAST_SPHERE, S_MERGE, S
 EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_step",
            "lbm_forces", "lbm_spheres", "lbm_lubrication", "lbm_bubbles", "lbm_bubble_roots", "lbm_bubble_splits", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
            "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count",
-           "lbm_bubble_volumes_noalloc", "lbm_forward_frozen", "lbm_adjoint_step", "lbm_destroy", "lbm_strerror")
+           "lbm_bubble_volumes_noalloc", "lbm_set_params", "lbm_import_state", "lbm_objective", "lbm_objective_read",
+           "lbm_forward_frozen", "lbm_adjoint_step", "lbm_destroy", "lbm_strerror")
 
 
 class Params(ctypes.Structure):
@@ -78,6 +79,10 @@ def load():
     L.lbm_copy_bytes.argtypes = [vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     L.lbm_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]
     L.lbm_bubble_volumes_noalloc.argtypes = [vp, vp, vp, sz, i32, vp, vp]
+    L.lbm_set_params.argtypes = [vp, d, pd]
+    L.lbm_import_state.argtypes = [vp, vp]
+    L.lbm_objective.argtypes = [vp, pd]
+    L.lbm_objective_read.argtypes = [vp, pd]
     L.lbm_forward_frozen.argtypes = [vp, vp, vp]
     L.lbm_adjoint_step.argtypes = [vp, vp, vp, vp, pd, i32, pd, pd]
     L.lbm_destroy.argtypes = [vp]
@@ -263,6 +268,30 @@ class Sim:
         n = ctypes.c_uint64()
         _check("lbm_launch_count", load().lbm_launch_count(self.ctx, ctypes.byref(n)))
         return n.value
+
+    def set_params(self, tau, g):
+        """relaxation time and body force of the steps that follow"""
+        self._bind_stream()
+        _check("lbm_set_params", load().lbm_set_params(self.ctx, float(tau), _dp(_v3(g))))
+        self.params.tau = float(tau)
+        for k in range(3):
+            self.params.g[k] = float(g[k])
+
+    def import_state(self, f):
+        """replace the post-collision PDFs (FP32 deviations [19,z,y,x], device) of a window"""
+        self._bind_stream()
+        _check("lbm_import_state", load().lbm_import_state(self.ctx, ctypes.c_void_p(f.data_ptr())))
+
+    def objective(self, jdir=None):
+        """from now on accumulate jdir . sum_P F_P of every step on the device (None: stop)"""
+        self._bind_stream()
+        _check("lbm_objective", load().lbm_objective(self.ctx, _dp(_v3(jdir)) if jdir is not None else None))
+
+    def objective_read(self) -> float:
+        self._bind_stream()
+        J = ctypes.c_double()
+        _check("lbm_objective_read", load().lbm_objective_read(self.ctx, ctypes.byref(J)))
+        return J.value
 
     def forward_frozen(self, f_in, f_out):
         """one step of the frozen liquid window on FP32 deviation tensors [19,z,y,x] (device)"""

@@ -7,7 +7,8 @@ J = sum over the window's steps of jdir . (total momentum-exchange force on the 
 magic relation) and the body force g (Guo forcing).
 
 Tolerances.  The GPU runs the forward and the reverse sweep in FP32 (PDFs stored as FP32
-deviations); the oracle is FP64.  A reverse step's rounding error is a few FP32 ulps of the
+deviations); the oracle is FP64 (on the 96^3 window through a stored golden value, written by a
+script that runs only the oracle).  A reverse step's rounding error is a few FP32 ulps of the
 adjoint variables, which are O(|jdir|) and grow at most linearly over the window, so over T
 steps the gradient is good to about T x 1e-6 relative to its largest component: the bound is
 2e-4 relative for the 40-step windows here.  The GPU's own finite differences carry the FP32
@@ -151,33 +152,81 @@ def test_adjoint_rejects_unfrozen_windows(lbm):
         A.window_gradient(sim, 3)
 
 
-def test_autograd_window_vs_gpu_finite_differences_c2(lbm):
-    """96^3 periodic array of 27 spheres, 500-step window, checkpoints every 50: the gradient
-    of the summed drag through torch.autograd against central differences of the GPU forward"""
+def _golden_c2():
+    """the FP64 oracle's tangent-linear gradient of the 96^3 window (tests/golden, written by
+    make_c2_window_gradient.py from the oracle alone)"""
+    import os
+    vals = {}
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", "c2_window_gradient.txt")):
+        if line.strip() and not line.startswith("#"):
+            k, v = line.split()
+            vals[k] = float(v)
+    return vals["J"], vals["dJ_dtau"], np.array([vals["dJ_dgx"], vals["dJ_dgy"], vals["dJ_dgz"]])
+
+
+def test_autograd_window_c2_against_oracle_and_finite_differences(lbm):
+    """96^3 periodic array of 27 spheres, 500-step window, checkpoints every 50, through
+    torch.autograd: J and its gradient against the FP64 oracle's tangent-linear window
+    (1e-5 and 1e-3 relative: FP32 forward and reverse over 500 steps, T x 1e-6), and against
+    central differences of the GPU forward evaluated by the same Function at shifted
+    parameters (1e-2: the FP32 rounding noise of J over the step h)"""
     import torch
     from paper_1712_07028_gb300 import adjoint as A
     wl = W.periodic_array_c2()
     n, every, jdir = 500, 50, (1.0, 0.0, 0.0)
     sim = _started(lbm, wl)
+    f0 = sim.export_state()["f"].clone()
     tau = torch.tensor(wl.tau, dtype=torch.float64, requires_grad=True)
     g = torch.tensor(wl.g, dtype=torch.float64, requires_grad=True)
-    J = A.LBMWindow.apply(tau, g, sim, n, jdir, every)
+    J = A.LBMWindow.apply(tau, g, f0, sim, n, jdir, every)
     J.backward()
+    Jo, dtau_o, dg_o = _golden_c2()
+    print("C2 window: J %.10g (oracle %.10g); dJ/dtau %.6g (%.6g); dJ/dg %s (%s)"
+          % (J.item(), Jo, tau.grad.item(), dtau_o, g.grad.numpy(), dg_o))
+    assert abs(J.item() - Jo) <= 1e-5 * abs(Jo)
+    assert abs(tau.grad.item() - dtau_o) <= 1e-3 * abs(dtau_o)
+    assert abs(g.grad[0].item() - dg_o[0]) <= 1e-3 * abs(dg_o[0])
+    assert np.abs(g.grad.numpy() - dg_o).max() <= 1e-3 * np.abs(dg_o).max()
 
     def J_of(tau_, g_):
-        w2 = W.periodic_array_c2()
-        w2.tau, w2.g = tau_, tuple(g_)
-        return A.forward_window(_started(lbm, w2), n, jdir, n)[0]
+        with torch.no_grad():
+            return A.LBMWindow.apply(torch.tensor(tau_, dtype=torch.float64), torch.tensor(g_, dtype=torch.float64),
+                                     f0, sim, n, jdir, n).item()
 
     ht = 1e-3
     fd_tau = (J_of(wl.tau + ht, wl.g) - J_of(wl.tau - ht, wl.g)) / (2 * ht)
     hg = 1e-6
-    fd_g = []
-    for k in range(3):
-        e = np.eye(3)[k] * hg
-        fd_g.append((J_of(wl.tau, np.add(wl.g, e)) - J_of(wl.tau, np.subtract(wl.g, e))) / (2 * hg))
-    fd_g = np.array(fd_g)
+    fd_g = np.array([(J_of(wl.tau, np.add(wl.g, np.eye(3)[k] * hg)) - J_of(wl.tau, np.subtract(wl.g, np.eye(3)[k] * hg)))
+                     / (2 * hg) for k in range(3)])
     assert abs(J.item() - J_of(wl.tau, wl.g)) <= 1e-8 * abs(J.item())
     assert abs(tau.grad.item() - fd_tau) <= 1e-2 * abs(fd_tau), (tau.grad.item(), fd_tau)
-    gg = g.grad.numpy()
-    assert np.abs(gg - fd_g).max() <= 1e-2 * np.abs(fd_g).max(), (gg, fd_g)
+    assert np.abs(g.grad.numpy() - fd_g).max() <= 1e-2 * np.abs(fd_g).max(), (g.grad.numpy(), fd_g)
+
+
+def test_set_params_and_import_reproduce_a_fresh_simulation(lbm):
+    """J of a window after lbm_set_params + lbm_import_state equals J of a simulation created
+    with those parameters (the same state); the objective accumulated on the device equals the
+    per-step sum of the forces read to the host"""
+    from paper_1712_07028_gb300 import adjoint as A
+    wl = _periodic()
+    n, jdir = 25, (0.4, -0.3, 0.9)
+    sim = _started(lbm, wl)
+    f0 = sim.export_state()["f"].clone()
+    J0, _ = A.forward_window(sim, n, jdir, 10)
+    tau2, g2 = wl.tau + 0.07, (2e-5, -4e-6, 1e-6)
+    sim.set_params(tau2, g2)
+    sim.import_state(f0)
+    J1, _ = A.forward_window(sim, n, jdir, 10)
+    w2 = _periodic(tau=tau2, g=g2)
+    fresh = _started(lbm, w2)
+    Jf = 0.0
+    for _ in range(n):
+        fresh.step(1)
+        F, _ = fresh.forces()
+        Jf += float(F.sum(axis=0) @ np.asarray(jdir))
+    assert abs(J1 - Jf) <= 1e-9 * abs(Jf), (J1, Jf)
+    assert abs(J1 - J0) > 1e-3 * abs(J0)   # the parameters changed the window
+    sim.set_params(wl.tau, wl.g)
+    sim.import_state(f0)
+    J0b, _ = A.forward_window(sim, n, jdir, 10)
+    assert abs(J0b - J0) <= 1e-9 * abs(J0)
