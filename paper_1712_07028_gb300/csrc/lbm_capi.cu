@@ -93,7 +93,7 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, tmark, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
+    size_t f[2], flags, mark, tmark, wl_link, wl_rare, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
         adj_srho, adj_part, merge_keys, merge_list, lab, split_list, part_key, part_root, part_V, part_new, bub_cnt, total;
     size_t N, wl_cap, nbins_max;
 };
@@ -126,6 +126,9 @@ Layout layout_of(const lbm_params* p) {
     for (int k = 0; k < 4; k++) L.wl[k] = take(4 * L.wl_cap);
     L.wl_slow = take(4 * L.N);
     L.wl_fix = take(4 * L.wl_cap);
+    // the lean kernel's link words (only a simulation with many spheres has a liquid segment)
+    L.wl_link = p->max_spheres > 32 ? take(8 * L.N) : 0;
+    L.wl_rare = p->max_spheres > 32 ? take(4 * L.wl_cap) : 0;
     L.bin_cnt = take(4 * L.nbins_max);
     L.bin_ids = take(4 * L.nbins_max * kBinCap);
     L.npairs = take(4 * (size_t)p->max_spheres);
@@ -215,13 +218,15 @@ void enqueue_epilogue(lbm_ctx* c, int g, cudaStream_t e, bool split) {
     }
     if (d.kappa) launch_curvature(d, g, e);
     launch_list_rescan(d, e);   // the next boundary sweep's list, from the final types
+    // the liquid segment's links, classified while the next bulk sweep runs
+    if (d.split_liq && d.wl_link) launch_link_classify(d, e);
 }
 
 int epilogue_launches(const Dev& d, bool split) {
-    return 1 + spheres_launches(d) + (d.kappa ? 1 : 0) + 1 + (split ? kSplitLaunches : 0);
+    return 1 + spheres_launches(d) + (d.kappa ? 1 : 0) + 1 + (split ? kSplitLaunches : 0) + (d.split_liq && d.wl_link ? 1 : 0);
 }
 int step_launches(const Dev& d, bool overlap, bool split) {
-    return 3 + d.split_liq + spheres_links_launches(d) + (overlap ? epilogue_launches(d, split) : 0);
+    return 3 + d.split_liq + (d.split_liq && d.wl_link ? 1 : 0) + spheres_links_launches(d) + (overlap ? epilogue_launches(d, split) : 0);
 }
 
 // one step reading grid cur: the bulk sweep on s and, with `overlap`, the end-of-step kernels
@@ -348,6 +353,8 @@ int first_step(lbm_ctx* c) {
     d.wl_touch = (uint32_t*)(a + L.wl[3]);
     d.wl_slow = (uint32_t*)(a + L.wl_slow);
     d.wl_fix = (uint32_t*)(a + L.wl_fix);
+    d.wl_link = p->max_spheres > 32 ? (uint2*)(a + L.wl_link) : nullptr;
+    d.wl_rare = p->max_spheres > 32 ? (uint32_t*)(a + L.wl_rare) : nullptr;
     double rmax = 1.0;
     for (const Sphere& s : c->sph_init) rmax = std::fmax(rmax, s.R);
     d.bin_w = (int)std::ceil(2.0 * rmax + 2.0);
@@ -417,8 +424,9 @@ int first_step(lbm_ctx* c) {
     launch_init(d, c->geo_dev, s);
     launch_bulk_all(d, s);
     launch_init_scan(d, s);
+    if (d.split_liq && d.wl_link) launch_link_classify(d, s);
     if (d.kappa) launch_curvature(d, 0, s);
-    if ((rc = launched(c, (d.nsph > 0) + 3 + (d.kappa ? 1 : 0)))) return rc;
+    if ((rc = launched(c, (d.nsph > 0) + 3 + (d.kappa ? 1 : 0) + (d.split_liq && d.wl_link ? 1 : 0)))) return rc;
     c->cur = 0;
     c->pending = false;
     c->links_state = kLinksNone;

@@ -144,6 +144,7 @@ struct Scalars {
     uint32_t bin_overflow;
     uint32_t n_slow;      // boundary-list length: general cells, at the front of wl_slow
     uint32_t n_liq;       // and liquid cells, at the back
+    uint32_t n_rare;      // liquid cells with links into two spheres or into gas (wl_rare)
     uint32_t ticket;      // blocks of the end-of-step scan that have finished
     uint32_t n_fix;       // BULK cells the end of the last step changed or whose neighbours it changed
     uint32_t fix_all;     // the fix list overflowed: the fix pass takes every BULK cell
@@ -243,6 +244,10 @@ struct Dev {
     uint32_t* wl_slow;        // [N] boundary list: every active cell that is not BULK, in scan order;
                               // liquid cells off the free-slip and open faces from the back
     uint32_t* wl_fix;         // [wl_cap] BULK cells to sweep again after the end-of-step kernels
+    uint2* wl_link;           // [N] (many spheres) per liquid-segment entry k: the sphere links of the
+                              // cell (bit q: x - c_q is an obstacle cell; bit 31: a link into a second
+                              // sphere or a gas cell) and its first sphere; written after the list pass
+    uint32_t* wl_rare;        // [wl_cap] the liquid-segment cells with bit 31 (their own sweep)
     // uniform bins of sphere ids for the neighbour searches
     int bin_w, nbx, nby, nbz, bin_cap;
     uint32_t* bin_cnt;        // [nbins]
@@ -722,6 +727,7 @@ __device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t
         c.n_conv = c.n_newif = c.n_fromliq = c.n_touch = c.n_uncov = 0;
         c.n_slow = 0;   // the boundary sweep has consumed its list; the list pass refills it
         c.n_liq = 0;
+        c.n_rare = 0;
         c.steps++;
     }
     if (bin_spheres)
@@ -743,6 +749,7 @@ void launch_split(const Dev& d, int g, cudaStream_t s);
 constexpr int kSplitLaunches = 6;
 void launch_init_scan(const Dev& d, cudaStream_t s);
 void launch_list_rescan(const Dev& d, cudaStream_t s);
+void launch_link_classify(const Dev& d, cudaStream_t s);
 void launch_curvature(const Dev& d, int nxt, cudaStream_t s);
 void launch_spheres_links(const Dev& d, int g, cudaStream_t s);
 void launch_spheres_move(const Dev& d, cudaStream_t s);

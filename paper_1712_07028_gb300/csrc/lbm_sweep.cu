@@ -476,13 +476,137 @@ __device__ __forceinline__ void boundary_cell(const Dev& d, const typename Store
     collide_store<S>(d, fb, i, fin, gw);
 }
 
+// ------------------------------------------------ link words of the liquid segment
+// The liquid segment's cells (in practice the spheres' shells) are classified once the list
+// pass is done, while the next bulk sweep runs: per entry k, bit q of the word says that the
+// link source x - c_q is an obstacle cell, bit 31 that the cell has a link into a second sphere,
+// into an obstacle cell of no valid sphere or into a gas cell (it then takes the full path), and
+// the second word holds the cell's first sphere (the owner of its lowest-q obstacle link).  The
+// lean kernel then needs neither the neighbours' types nor their owners.
+constexpr uint32_t kLinkRare = 1u << 31;
+__global__ void __launch_bounds__(256) link_classify_kernel(const Dev d) {
+    const uint32_t N = (uint32_t)d.N;
+    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_liq, N);
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        const uint32_t i = d.wl_slow[N - 1u - k];
+        int x, y, z;
+        cell_xyz(d, i, x, y, z);
+        const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+        const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+        const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
+        const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
+        const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
+        const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
+        const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
+        uint8_t t[kQ];
+        uint32_t src[kQ];
+#pragma unroll
+        for (int q = 1; q < kQ; q++) {   // every type load first
+            const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
+            const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
+            const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
+            const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
+                              (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
+            src[q] = sx + sy + sz;
+            t[q] = wall ? (uint8_t)F_ACTIVE : d.flags[src[q]];   // (a wall link streams from the cell itself)
+        }
+        uint32_t mask = 0u, P0 = kNone, first = kNone;
+        bool rare = false;
+#pragma unroll
+        for (int q = kQ - 1; q >= 1; q--) {
+            if (t[q] & F_ACTIVE) continue;
+            if (t[q] & F_OBS) {
+                const uint32_t P = d.owner[src[q]];
+                mask |= 1u << q;
+                P0 = P;
+                if (first == kNone) first = P;
+                else if (P != first) rare = true;
+                if (P >= (uint32_t)d.nsph) rare = true;
+            } else {
+                rare = true;   // a gas link
+            }
+        }
+        d.wl_link[k] = make_uint2(mask | (rare ? kLinkRare : 0u), P0);
+        if (rare) wl_push(d.wl_rare, &d.sc->n_rare, (uint32_t)d.wl_cap, i, &d.sc->status);
+    }
+}
+
+void launch_link_classify(const Dev& d, cudaStream_t s) { link_classify_kernel<<<152 * 8, 256, 0, s>>>(d); }
+
+// a liquid-segment cell whose obstacle links all go into its first sphere P0 (mask: bit q set
+// for a link from an obstacle cell), the others streaming or beyond a no-slip wall: the lean
+// instance of boundary_cell without any neighbour type or owner load, the same arithmetic
+template <int S>
+__device__ __forceinline__ void lean_cell(const Dev& d, const typename Store<S>::T* __restrict__ fa,
+                                          typename Store<S>::T* __restrict__ fb, const size_t i, const uint32_t mask,
+                                          const uint32_t P0, SphAcc& acc, float& sbb) {
+    const size_t N = d.N;
+    int x, y, z;
+    cell_xyz(d, i, x, y, z);
+    const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+    const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
+    const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
+    const uint32_t zm = (z == 0 ? d.nz - 1 : z - 1) * nxy, zp = (z == d.nz - 1 ? 0 : z + 1) * nxy, z0 = z * nxy;
+    const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
+    const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
+    const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
+    float fo[kQ], fin[kQ];
+    uint32_t wl = 0u;   // bit q: the link comes from beyond a wall
+#pragma unroll
+    for (int q = 0; q < kQ; q++) fo[q] = Store<S>::get(fa, (size_t)q * N + i);
+    fin[0] = fo[0];
+#pragma unroll
+    for (int q = 1; q < kQ; q++) {   // the streaming links' pulled PDFs
+        const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
+        const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
+        const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
+        const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
+                          (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
+        wl |= wall ? 1u << q : 0u;
+        fin[q] = (!wall && !(mask & (1u << q))) ? Store<S>::get(fa, (size_t)q * N + (sx + sy + sz)) : 0.f;
+    }
+    float drho0 = 0.f;
+#pragma unroll
+    for (int q = 0; q < kQ; q++) drho0 += fo[q];
+    const float rho0 = 1.f + drho0;
+    float ucx = 0.f, ucy = 0.f, ucz = 0.f;
+    if (mask) {
+        // c_q . u_w at the link midpoint equals c_q . (u_P + w_P x r) at the cell centre
+        sph_begin(d, acc, P0, x, y, z);
+        ucx = acc.u[0] + acc.w[1] * acc.r[2] - acc.w[2] * acc.r[1];
+        ucy = acc.u[1] + acc.w[2] * acc.r[0] - acc.w[0] * acc.r[2];
+        ucz = acc.u[2] + acc.w[0] * acc.r[1] - acc.w[1] * acc.r[0];
+    }
+#pragma unroll
+    for (int q = 1; q < kQ; q++) {
+        const int qb = opp(q);
+        if (wl & (1u << q)) {
+            fin[q] = fo[qb];                                        // no-slip wall
+        } else if (mask & (1u << q)) {                              // Eq. bbrule
+            const float corr = 6.f * wgt(q) * rho0 * (cx(q) * ucx + cy(q) * ucy + cz(q) * ucz);
+            fin[q] = fo[qb] + corr;
+            // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
+            const float dev = 2.f * fo[qb] + corr;
+            acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
+            acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
+            sbb += corr;
+        }
+    }
+    collide_store<S>(d, fb, i, fin, 1.f);
+}
+
 // every other active cell: walls, sphere links, gas links, interface mass exchange.  Two
 // instances: the general one takes the general segment of the list (interface cells and cells
 // on a free-slip or open face); the lean one (Lean) the liquid segment, cells whose links are
 // streaming, wall and sphere links only (and gas links, should a gas cell sit beside one): no
 // mass exchange, no face links; 128 registers a thread against 200, twice the resident warps.
-template <int S, bool Lean>
-__global__ void __launch_bounds__(128, Lean ? 4 : 1) sweep_boundary_kernel(const Dev d, const int cur) {
+// Mode: kBndGeneral (the general segment, or both), kBndLean (the liquid segment, full link
+// logic), kBndLeanFast (the liquid segment's classified cells with links into one sphere
+// only), kBndRare (the classified cells with links into two spheres or into gas)
+enum { kBndGeneral = 0, kBndLean = 1, kBndLeanFast = 2, kBndRare = 3 };
+template <int S, int Mode>
+__global__ void __launch_bounds__(128, Mode == kBndLeanFast ? 6 : (Mode != kBndGeneral ? 4 : 1)) sweep_boundary_kernel(const Dev d, const int cur) {
+    constexpr bool Lean = Mode != kBndGeneral;
     using T = typename Store<S>::T;
     const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
     T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
@@ -491,7 +615,8 @@ __global__ void __launch_bounds__(128, Lean ? 4 : 1) sweep_boundary_kernel(const
     const size_t N = d.N;
     // the general kernel takes both segments when no lean kernel runs
     uint32_t ngen = 0, n;
-    if (Lean) n = min(*(volatile const uint32_t*)&d.sc->n_liq, (uint32_t)N);
+    if (Mode == kBndRare) n = min(*(volatile const uint32_t*)&d.sc->n_rare, (uint32_t)d.wl_cap);
+    else if (Lean) n = min(*(volatile const uint32_t*)&d.sc->n_liq, (uint32_t)N);
     else if (d.split_liq) n = ngen = min(*(volatile const uint32_t*)&d.sc->n_slow, (uint32_t)N);
     else n = blist_len(d, ngen);
     const uint32_t* __restrict__ list = d.wl_slow;
@@ -512,8 +637,15 @@ __global__ void __launch_bounds__(128, Lean ? 4 : 1) sweep_boundary_kernel(const
         float vphi = 1.f;         // and its new fill level
         bool isIFc = false;
         if (k < n) {
-            const size_t i = Lean ? list[(uint32_t)N - 1u - k] : blist_cell(d, k, ngen);
-            boundary_cell<S, Lean>(d, fa, fb, phia, phib, cur, i, acc, sbb, vb, vphi, isIFc);
+            if (Mode == kBndLeanFast) {
+                // a classified liquid cell with links into one sphere only: no neighbour loads
+                // (the others are the rare instance's)
+                const uint2 lk = d.wl_link[k];
+                if (!(lk.x & kLinkRare)) lean_cell<S>(d, fa, fb, list[(uint32_t)N - 1u - k], lk.x, lk.y, acc, sbb);
+            } else {
+                const size_t i = Mode == kBndRare ? d.wl_rare[k] : (Lean ? list[(uint32_t)N - 1u - k] : blist_cell(d, k, ngen));
+                boundary_cell<S, Lean>(d, fa, fb, phia, phib, cur, i, acc, sbb, vb, vphi, isIFc);
+            }
         }
 
         if (Lean) {
@@ -594,8 +726,13 @@ void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s) {
 // blocks fit beside it)
 template <int S>
 static void sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaStream_t side2) {
-    sweep_boundary_kernel<S, false><<<d.split_liq ? 152 : kBoundaryGrid, 128, 0, side>>>(d, cur);
-    if (d.split_liq) sweep_boundary_kernel<S, true><<<152 * 4, 128, 0, side2>>>(d, cur);
+    sweep_boundary_kernel<S, kBndGeneral><<<d.split_liq ? 152 : kBoundaryGrid, 128, 0, side>>>(d, cur);
+    if (d.split_liq && d.wl_link) {   // classified: the one-sphere cells, then the rare ones
+        sweep_boundary_kernel<S, kBndLeanFast><<<152 * 6, 128, 0, side2>>>(d, cur);
+        sweep_boundary_kernel<S, kBndRare><<<152, 128, 0, side2>>>(d, cur);
+    } else if (d.split_liq) {
+        sweep_boundary_kernel<S, kBndLean><<<152 * 4, 128, 0, side2>>>(d, cur);
+    }
     sweep_fix_kernel<S><<<152 * 2, 128, 0, s>>>(d, cur);
 }
 
