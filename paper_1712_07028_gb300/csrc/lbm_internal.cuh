@@ -145,6 +145,7 @@ struct Scalars {
     uint32_t n_slow;      // boundary-list length: general cells, at the front of wl_slow
     uint32_t n_liq;       // and liquid cells, at the back
     uint32_t n_rare;      // liquid cells with links into two spheres or into gas (wl_rare)
+    uint32_t n_paired;    // spheres with partners this step (sph_list)
     uint32_t ticket;      // blocks of the end-of-step scan that have finished
     uint32_t n_fix;       // BULK cells the end of the last step changed or whose neighbours it changed
     uint32_t fix_all;     // the fix list overflowed: the fix pass takes every BULK cell
@@ -253,6 +254,7 @@ struct Dev {
     uint32_t* bin_cnt;        // [nbins]
     uint32_t* bin_ids;        // [nbins][bin_cap]
     uint32_t* npairs;         // [max_sph] partners within lubrication reach this step
+    uint32_t* sph_list;       // [max_sph] the spheres with partners this step (n_paired of them)
     uint32_t* pairs;          // [max_sph][kPairCap]
     unsigned long long* merge_keys;   // [kMergeCap] pairs (lo + 1) << 32 | hi of touching roots, 0 = free
     uint32_t* merge_list;     // [kMergeCap] slots of merge_keys in use, in insertion order
@@ -728,6 +730,7 @@ __device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t
         c.n_slow = 0;   // the boundary sweep has consumed its list; the list pass refills it
         c.n_liq = 0;
         c.n_rare = 0;
+        c.n_paired = 0;
         c.steps++;
     }
     if (bin_spheres)

@@ -197,8 +197,10 @@ __device__ inline void sph_contact_one(const Dev& d, const int P, const int t, c
             if (v[c] != 0.0) atomicAdd(c < 3 ? &a.C[c] : &a.TC[c - 3], v[c]);
 }
 
+// blocks over the spheres with partners (listed by the pair pass; block-uniform loop)
 __global__ void sph_contact_kernel(const Dev d) {
-    if (blockIdx.x < (unsigned)d.nsph) sph_contact_one(d, blockIdx.x, threadIdx.x, blockDim.x);
+    const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_paired, (uint32_t)d.nsph);
+    for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) sph_contact_one(d, (int)d.sph_list[k], threadIdx.x, blockDim.x);
 }
 
 // The gas's pressure on the sphere surface the gas touches.  The sweep's links come from
@@ -307,6 +309,9 @@ __device__ inline void sph_pairs_one(const Dev& d, const uint32_t P, const int l
             else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
         }
     }
+    // the spheres with partners: the only ones the contact-link pass visits
+    __syncwarp();
+    if (lane == 0 && *(volatile uint32_t*)&d.npairs[P] > 0u) d.sph_list[atomicAdd(&d.sc->n_paired, 1u)] = P;
 }
 
 __global__ void sph_pairs_kernel(const Dev d) {
@@ -512,17 +517,19 @@ __global__ void sph_copy_kernel(const Dev d) {
 }
 
 // ---------------------------------------------------------------- cover / uncover
-// One block per sphere: cells of the union of its old and new boxes whose coverage by this
+// One warp per sphere: cells of the union of its old and new boxes whose coverage by this
 // sphere changed are touched (deduplicated into a worklist).
-// by a group of nt threads (t the thread's index in the group)
-__device__ inline void cover_touch_one(const Dev& d, const int P, const int t, const int nt) {
-    // the box and the cell offsets from both centres, set up by one thread (FP64 issue is
-    // scarce on this GPU: the whole block doing it cost more than the box scan)
-    __shared__ int sGo, sLo[3], sExt[3];
-    __shared__ float sA0[3], sA1[3], sR2f;
-    __shared__ double sOff[3];
+constexpr int kTouchWarps = 4;   // spheres per block of the touch kernel
+__device__ inline void cover_touch_one(const Dev& d, const int P, const int lane) {
+    // the box and the cell offsets from both centres, set up by one lane (FP64 issue is scarce
+    // on this GPU: every lane doing it cost more than the box scan) and shared through the
+    // warp's slots of shared memory
+    __shared__ int sGo[kTouchWarps], sLo[kTouchWarps][3], sExt[kTouchWarps][3];
+    __shared__ float sA0[kTouchWarps][3], sA1[kTouchWarps][3], sR2f[kTouchWarps];
+    __shared__ double sOff[kTouchWarps][3];
+    const int wb = threadIdx.x >> 5;
     const Sphere& s = d.sph[P];
-    if (t == 0) {
+    if (lane == 0) {
         d.sphl[P] = sph_link_of(s);   // the next sweep's link data
         int go = 0;
         if (s.x[0] != s.x0[0] || s.x[1] != s.x0[1] || s.x[2] != s.x0[2]) {
@@ -534,32 +541,33 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int t, c
                 const int lim = 2 * (int)ceil(s.R) + 8;
                 go = 1;
                 for (int k = 0; k < 3; k++) {
-                    sOff[k] = min_image(d, k, s.x[k], s.x0[k]);   // new centre relative to the old
-                    const double a = s.x0[k], b = s.x0[k] + sOff[k];
-                    sLo[k] = (int)floor(fmin(a, b) - s.R) - 1;
-                    sExt[k] = (int)ceil(fmax(a, b) + s.R) + 1 - sLo[k] + 1;
-                    if (sExt[k] > lim) go = 0;
-                    sA0[k] = (float)((double)sLo[k] - s.x0[k]);
-                    sA1[k] = (float)((double)sLo[k] - (s.x0[k] + sOff[k]));
+                    sOff[wb][k] = min_image(d, k, s.x[k], s.x0[k]);   // new centre relative to the old
+                    const double a = s.x0[k], b = s.x0[k] + sOff[wb][k];
+                    sLo[wb][k] = (int)floor(fmin(a, b) - s.R) - 1;
+                    sExt[wb][k] = (int)ceil(fmax(a, b) + s.R) + 1 - sLo[wb][k] + 1;
+                    if (sExt[wb][k] > lim) go = 0;
+                    sA0[wb][k] = (float)((double)sLo[wb][k] - s.x0[k]);
+                    sA1[wb][k] = (float)((double)sLo[wb][k] - (s.x0[k] + sOff[wb][k]));
                 }
                 if (!go) atomicOr(&d.sc->status, S_UNSTABLE);
-                sR2f = (float)(s.R * s.R);
+                sR2f[wb] = (float)(s.R * s.R);
             }
         }
-        sGo = go;
+        sGo[wb] = go;
     }
-    __syncthreads();
-    if (!sGo) return;
+    __syncwarp();
+    if (!sGo[wb]) return;   // (uniform over the warp)
     const int L[3] = {d.nx, d.ny, d.nz};
-    const int lo[3] = {sLo[0], sLo[1], sLo[2]}, ext[3] = {sExt[0], sExt[1], sExt[2]};
-    const float a0[3] = {sA0[0], sA0[1], sA0[2]}, a1[3] = {sA1[0], sA1[1], sA1[2]};
+    const int lo[3] = {sLo[wb][0], sLo[wb][1], sLo[wb][2]}, ext[3] = {sExt[wb][0], sExt[wb][1], sExt[wb][2]};
+    const float a0[3] = {sA0[wb][0], sA0[wb][1], sA0[wb][2]}, a1[3] = {sA1[wb][0], sA1[wb][1], sA1[wb][2]};
+    const double off[3] = {sOff[wb][0], sOff[wb][1], sOff[wb][2]};
     // cell offsets from both centres in FP32 decide wherever |d^2 - R^2| clears their rounding
     // error by far; the few cells closer to the sphere's surface are decided in FP64
     // FP32 squared distances below ~50 carry an error under 1e-5 here
-    const float R2f = sR2f, band = 1e-4f * (1.f + R2f);
-    // each thread takes columns (x, y) of the box and walks them along z
+    const float R2f = sR2f[wb], band = 1e-4f * (1.f + R2f);
+    // each lane takes columns (x, y) of the box and walks them along z
     const int nxy = ext[0] * ext[1];
-    for (int exy = t; exy < nxy; exy += nt) {
+    for (int exy = lane; exy < nxy; exy += 32) {
         const int ex0 = exy % ext[0], ex1 = exy / ext[0];
         const float ax = a0[0] + (float)ex0, ay = a0[1] + (float)ex1;
         const float bx = a1[0] + (float)ex0, by = a1[1] + (float)ex1;
@@ -573,7 +581,7 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int t, c
                 const double R2 = s.R * s.R;
                 double d0 = 0, d1 = 0;
                 for (int k = 0; k < 3; k++) {
-                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + sOff[k]);
+                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off[k]);
                     d0 += a * a;
                     d1 += b * b;
                 }
@@ -596,8 +604,9 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int t, c
     }
 }
 
-__global__ void cover_touch_kernel(const Dev d) {
-    if (blockIdx.x < (unsigned)d.nsph) cover_touch_one(d, blockIdx.x, threadIdx.x, blockDim.x);
+__global__ void __launch_bounds__(32 * kTouchWarps) cover_touch_kernel(const Dev d) {
+    const int P = blockIdx.x * kTouchWarps + (threadIdx.x >> 5);
+    if (P < d.nsph) cover_touch_one(d, P, threadIdx.x & 31);
 }
 
 // touched cells: the lowest id of the spheres covering them now decides; obstacle cells no
@@ -799,7 +808,8 @@ void prepare_sphere_kernels() {
 // the cells whose coverage the move changes (reads only the sphere table; its marks have an
 // array of their own, so it may run while the conversions do)
 void launch_cover_touch(const Dev& d, cudaStream_t st) {
-    if (d.sphere_mode != LBM_SPHERES_FIXED) cover_touch_kernel<<<d.nsph, 128, 0, st>>>(d);
+    if (d.sphere_mode != LBM_SPHERES_FIXED)
+        cover_touch_kernel<<<(d.nsph + kTouchWarps - 1) / kTouchWarps, 32 * kTouchWarps, 0, st>>>(d);
 }
 
 // partner lists and the links between obstacle nodes of two spheres: they read only the
@@ -808,7 +818,7 @@ void launch_cover_touch(const Dev& d, cudaStream_t st) {
 void launch_spheres_links(const Dev& d, int g, cudaStream_t st) {
     if (d.nsph == 0) return;
     sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
-    sph_contact_kernel<<<d.nsph, 128, 0, st>>>(d);
+    sph_contact_kernel<<<d.nsph < 152 * 8 ? d.nsph : 152 * 8, 128, 0, st>>>(d);
     sph_gas_kernel<<<d.nsph, 128, 0, st>>>(d, g);
 }
 

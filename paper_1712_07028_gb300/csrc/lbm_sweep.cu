@@ -729,7 +729,7 @@ static void sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side,
     sweep_boundary_kernel<S, kBndGeneral><<<d.split_liq ? 152 : kBoundaryGrid, 128, 0, side>>>(d, cur);
     if (d.split_liq && d.wl_link) {   // classified: the one-sphere cells, then the rare ones
         sweep_boundary_kernel<S, kBndLeanFast><<<152 * 6, 128, 0, side2>>>(d, cur);
-        sweep_boundary_kernel<S, kBndRare><<<152, 128, 0, side2>>>(d, cur);
+        sweep_boundary_kernel<S, kBndRare><<<152 * 4, 128, 0, side2>>>(d, cur);
     } else if (d.split_liq) {
         sweep_boundary_kernel<S, kBndLean><<<152 * 4, 128, 0, side2>>>(d, cur);
     }
