@@ -123,7 +123,7 @@ void launch_frozen_forward(const Dev& d, const float* f_in, float* f_out, cudaSt
     cudaEventRecord(fork, s);
     cudaStreamWaitEvent(side, fork, 0);
     frozen_boundary_kernel<<<152 * 2, 128, 0, side>>>(dd, f_in, f_out);
-    launch_sweep_bulk(dd, 0, s);
+    launch_sweep_bulk(dd, 0, s, false);   // its boundary kernel runs beside it
     cudaEventRecord(join, side);
     cudaStreamWaitEvent(s, join, 0);
 }

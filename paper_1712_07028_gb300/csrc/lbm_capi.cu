@@ -249,7 +249,7 @@ int enqueue_step(lbm_ctx* c, int cur, cudaStream_t s, bool overlap, bool timed =
         cudaEventRecord(c->join3, c->epi);
     }
     if (timed) cudaEventRecord(c->ev[4 * slot], s);
-    launch_sweep_bulk(d, cur, s);
+    launch_sweep_bulk(d, cur, s, true);
     if (timed) cudaEventRecord(c->ev[4 * slot + 1], s);
     if (overlap) cudaStreamWaitEvent(s, c->join3, 0);
     if (timed) cudaEventRecord(c->ev[4 * slot + 2], s);

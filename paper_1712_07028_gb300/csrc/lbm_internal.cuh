@@ -743,7 +743,9 @@ __device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t
         }
 }
 
-void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s);
+// the bulk sweep of grid cur; `whole`: every warp that holds a BULK cell writes all the cells
+// it spans (only where the fix pass and the boundary sweep run after it)
+void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s, bool whole);
 void launch_sweep_rest(const Dev& d, int cur, cudaStream_t s, cudaStream_t side, cudaStream_t side2, cudaEvent_t fork,
                        cudaEvent_t join, cudaEvent_t join2);
 

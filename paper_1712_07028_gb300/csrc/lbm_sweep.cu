@@ -276,18 +276,41 @@ __device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>:
 // still changing types and PDFs near interfaces and spheres: the cells it then reads stale
 // inputs for are on the fix list (or leave BULK and go to the boundary list), and the fix pass
 // and the boundary sweep, which run after those kernels, overwrite their results.
-template <int S>
+// With Whole (the forward step, whose fix pass and boundary sweep follow it on the stream), a
+// warp that holds a BULK cell writes every cell it spans, so that each 32-byte sector of the
+// destination is written whole: a sector written in part costs the memory a read of the
+// sector before the write, and in a sphere-dense column most sectors hold a cell beside a
+// sphere (16 cells a sector at two bytes a PDF).  The warp's other active cells get a
+// provisional update that the fix pass or the boundary sweep replaces; its gas and obstacle
+// cells, whose PDFs nothing reads, get the update of a resting population.  Without Whole
+// (the adjoint's frozen step, whose boundary kernel runs at the same time) only BULK cells
+// are written.
+template <int S, bool Whole>
 __global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int cur) {
     using T = typename Store<S>::T;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    if (x >= d.nx || y >= d.ny) return;
+    const bool in = x < d.nx && y < d.ny;
     const uint32_t i = (uint32_t)x + (uint32_t)d.nx * (uint32_t)y + (uint32_t)d.nx * (uint32_t)d.ny * (uint32_t)z;
-    const uint8_t fl = d.flags[i];
-    if (!(fl & F_ACTIVE)) return;
-    if (!(fl & F_BULK)) return;   // the boundary kernel's (listed at the end of the last step)
-    bulk_cell<S>(d, static_cast<const T*>(d.f[cur]), static_cast<T*>(d.f[cur ^ 1]), x, y, z, i);
+    const uint8_t fl = in ? d.flags[i] : (uint8_t)0;
+    const bool bulk = (fl & F_ACTIVE) && (fl & F_BULK);
+    const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
+    T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
+    if (!Whole) {
+        if (bulk) bulk_cell<S>(d, fa, fb, x, y, z, i);
+        return;
+    }
+    // (all 32 lanes reach the vote: blocks are whole warps and nothing returned before it)
+    if (!__any_sync(0xffffffffu, bulk) || !in) return;
+    float fin[kQ];
+    if (fl & F_ACTIVE) {
+        bulk_load<S, true>(d, fa, x, y, z, i, fin);
+    } else {
+#pragma unroll
+        for (int q = 0; q < kQ; q++) fin[q] = 0.f;
+    }
+    collide_store<S, true>(d, fb, i, fin);
 }
 
 // the fix pass: the listed BULK cells again (or every BULK cell when the list overflowed),
@@ -707,16 +730,21 @@ __global__ void __launch_bounds__(128, Mode == kBndLeanFast ? 6 : (Mode != kBndG
 }
 
 // the bulk sweep of grid cur on stream s
-void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s) {
+template <bool Whole>
+static void sweep_bulk(const Dev& d, int cur, cudaStream_t s) {
     const int bx = d.nx >= 128 ? 128 : ((d.nx + 31) / 32) * 32;
     const int by = 128 / bx;
     dim3 block(bx, by, 1);
     dim3 grid((d.nx + bx - 1) / bx, (d.ny + by - 1) / by, d.nz);
     switch (d.storage) {
-        case LBM_STORE_F32: sweep_bulk_kernel<LBM_STORE_F32><<<grid, block, 0, s>>>(d, cur); break;
-        case LBM_STORE_F16DEV: sweep_bulk_kernel<LBM_STORE_F16DEV><<<grid, block, 0, s>>>(d, cur); break;
-        default: sweep_bulk_kernel<LBM_STORE_BF16DEV><<<grid, block, 0, s>>>(d, cur); break;
+        case LBM_STORE_F32: sweep_bulk_kernel<LBM_STORE_F32, Whole><<<grid, block, 0, s>>>(d, cur); break;
+        case LBM_STORE_F16DEV: sweep_bulk_kernel<LBM_STORE_F16DEV, Whole><<<grid, block, 0, s>>>(d, cur); break;
+        default: sweep_bulk_kernel<LBM_STORE_BF16DEV, Whole><<<grid, block, 0, s>>>(d, cur); break;
     }
+}
+void launch_sweep_bulk(const Dev& d, int cur, cudaStream_t s, bool whole) {
+    if (whole) sweep_bulk<true>(d, cur, s);
+    else sweep_bulk<false>(d, cur, s);
 }
 
 // the rest of the sweep once the end-of-step kernels are done: the general boundary kernel on
