@@ -328,6 +328,7 @@ int first_step(lbm_ctx* c) {
     d.lp = (float)lp;
     d.lm = (float)(1.0 / ((3.0 / 16.0) / (1.0 / lp + 0.5) - 0.5));
     for (int k = 0; k < 3; k++) { d.g[k] = (float)p->g[k]; d.gd[k] = p->g[k]; }
+    set_collision_consts(d);
     d.sigma = (float)p->sigma;
     d.rho_g0 = (float)p->rho_gas0;
     d.eps = (float)p->eps;
@@ -757,6 +758,7 @@ int lbm_set_params(lbm_ctx* c, double tau, const double g[3]) {
     d.lp = (float)lp;
     d.lm = (float)(1.0 / ((3.0 / 16.0) / (1.0 / lp + 0.5) - 0.5));
     for (int k = 0; k < 3; k++) { d.g[k] = (float)g[k]; d.gd[k] = g[k]; }
+    set_collision_consts(d);
     // the step graphs hold the kernels' arguments: instantiate them again at the next step
     for (int v = 0; v < 4; v++)
         if (c->graph_ready[v]) {

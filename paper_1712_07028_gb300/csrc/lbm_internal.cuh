@@ -31,6 +31,21 @@ __host__ __device__ constexpr float wgt(int q) { return q == 0 ? (1.0f / 3.0f) :
 // 72 w_q as an integer (24, 4, 2): the constant part of a bounce-back link's momentum
 __host__ __device__ constexpr int w72(int q) { return q == 0 ? 24 : (q <= 6 ? 4 : 2); }
 
+// c_q . v, and a + c v for one component c of c_q, with the zero components of c_q left out.
+// Under IEEE rules a product with 0.0f cannot be folded away (it turns a NaN or an infinity
+// into a NaN), so the plain forms cost a multiply-add per zero component; these cost only the
+// additions the lattice needs.  For finite operands the results are those of the plain forms
+// (products with +-1 are exact), up to the sign of a zero.
+__device__ __forceinline__ float cdot(int q, float vx, float vy, float vz) {
+    float r = 0.f;
+    bool any = false;
+    if (cx(q) != 0) { r = cx(q) > 0 ? vx : -vx; any = true; }
+    if (cy(q) != 0) { r = any ? (cy(q) > 0 ? r + vy : r - vy) : (cy(q) > 0 ? vy : -vy); any = true; }
+    if (cz(q) != 0) r = any ? (cz(q) > 0 ? r + vz : r - vz) : (cz(q) > 0 ? vz : -vz);
+    return r;
+}
+__device__ __forceinline__ float cacc(int c, float a, float v) { return c > 0 ? a + v : (c < 0 ? a - v : a); }
+
 // cell flag byte: type bits, plus BULK = liquid cell whose 18 neighbours all exist and are
 // liquid or interface (it then streams without looking at its neighbours)
 enum : uint8_t { F_LIQ = 1, F_IF = 2, F_GAS = 4, F_OBS = 8, F_BULK = 16, F_TYPE = 15 };
@@ -220,6 +235,16 @@ struct Dev {
     float tau, lp, lm;        // tau, lambda_+, lambda_-
     float g[3];
     double gd[3];
+    // grid-uniform factors of the collision, from lp, lm and g (set_collision_consts); as kernel
+    // arguments they cost the per-cell arithmetic nothing
+    struct CollisionConsts {
+        float c0;            // 1 + lambda_+ (the rest population)
+        float c1, c2;        // 1 + (lambda_+ + lambda_-)/2 and (lambda_+ - lambda_-)/2
+        float lp15, cp3;     // 1.5 lambda_+ and 3 (1 + lambda_+/2)
+        float lp45;          // 4.5 lambda_+
+        float hg[3];         // g / 2
+        float K[9], M[9];    // per opposite pair (q = 2k+1, 2k+2): 9 (1 + lambda_+/2) c_q.g, (1 + lambda_-/2) c_q.g
+    } cc;
     float sigma;
     float rho_g0;
     float eps;
@@ -483,7 +508,7 @@ __device__ __forceinline__ void post_moments(const Dev& d, const typename Store<
     for (int q = 0; q < kQ; q++) {
         const float v = Store<S>::get_nc(f, (size_t)q * d.N + i);
         dr += v;
-        jx += cx(q) * v; jy += cy(q) * v; jz += cz(q) * v;
+        jx = cacc(cx(q), jx, v); jy = cacc(cy(q), jy, v); jz = cacc(cz(q), jz, v);
     }
     const float r = 1.f + dr;
     rho = r;
@@ -494,52 +519,72 @@ __device__ __forceinline__ void post_moments(const Dev& d, const typename Store<
 
 // deviation of the equilibrium (Eq. equilibrium) from the weight: e_q(rho,u) - w_q
 __device__ __forceinline__ float equilibrium_dev(int q, float rho, const float u[3]) {
-    const float cu = cx(q) * u[0] + cy(q) * u[1] + cz(q) * u[2];
+    const float cu = cdot(q, u[0], u[1], u[2]);
     const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     return wgt(q) * ((rho - 1.f) + rho * (3.f * cu + 4.5f * cu * cu - 1.5f * uu));
+}
+
+// the collision's grid-uniform factors (Dev::cc) from d.lp, d.lm and d.g; called wherever those change
+inline void set_collision_consts(Dev& d) {
+    const double lp = d.lp, lm = d.lm, cp = 1.0 + 0.5 * lp, cm = 1.0 + 0.5 * lm;
+    Dev::CollisionConsts& k = d.cc;
+    k.c0 = (float)(1.0 + lp);
+    k.c1 = (float)(1.0 + 0.5 * (lp + lm));
+    k.c2 = (float)(0.5 * (lp - lm));
+    k.lp15 = (float)(1.5 * lp);
+    k.cp3 = (float)(3.0 * cp);
+    k.lp45 = (float)(4.5 * lp);
+    for (int a = 0; a < 3; a++) k.hg[a] = (float)(0.5 * (double)d.g[a]);
+    for (int p = 0; p < 9; p++) {
+        const int q = 2 * p + 1;
+        const double cg = cx(q) * (double)d.g[0] + cy(q) * (double)d.g[1] + cz(q) * (double)d.g[2];
+        k.K[p] = (float)(9.0 * cp * cg);
+        k.M[p] = (float)(cm * cg);
+    }
 }
 
 // moments, Guo-shifted velocity and the TRT collision of one cell, all on deviations f - w:
 // the post-collision deviations out[].  The body force acts on the cell's liquid mass: rho g in
 // a liquid cell, gw = its fill level times that in an interface cell.
+// Per opposite pair (q, qb) the relaxation of the symmetric part towards e+ and of the
+// antisymmetric part towards e-, with Guo's source split the same way, is gathered as
+//   out_q  = c1 f_q + c2 f_qb + alpha + beta,   out_qb = c1 f_qb + c2 f_q + alpha - beta,
+//   alpha = w (-lambda_+ drho + rho (1.5 lambda_+ u.u - 3 c+ u.G)) + w rho cu (9 c+ cg - 4.5 lambda_+ cu),
+//   beta  = 3 w rho (c- cg - lambda_- cu),
+// cu = c_q.u, cg = c_q.G, G = gw g, c+- = 1 + lambda_+-/2, c1 = 1 + (lambda_+ + lambda_-)/2,
+// c2 = (lambda_+ - lambda_-)/2: the same collision as f + lambda_+ (f+ - e+) + lambda_- (f- - e-)
+// + c+ G+ + c- G- written out per pair, with the grid-uniform factors computed on the host.
 __device__ __forceinline__ void trt_collide(const Dev& d, const float (&fin)[kQ], float gw, float (&out)[kQ]) {
-    const float gx = gw * d.g[0], gy = gw * d.g[1], gz = gw * d.g[2];
+    const Dev::CollisionConsts& k = d.cc;
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
     for (int q = 0; q < kQ; q++) {
         drho += fin[q];
-        jx += cx(q) * fin[q]; jy += cy(q) * fin[q]; jz += cz(q) * fin[q];
+        jx = cacc(cx(q), jx, fin[q]); jy = cacc(cy(q), jy, fin[q]); jz = cacc(cz(q), jz, fin[q]);
     }
     const float rho = 1.f + drho;
     if (!(rho > 0.f)) atomicOr(&d.sc->status, S_UNSTABLE);
     const float inv = 1.f / rho;
-    const float ux = (jx + 0.5f * rho * gx) * inv;
-    const float uy = (jy + 0.5f * rho * gy) * inv;
-    const float uz = (jz + 0.5f * rho * gz) * inv;
+    const float ux = fmaf(jx, inv, gw * k.hg[0]);   // (j + rho G/2) / rho
+    const float uy = fmaf(jy, inv, gw * k.hg[1]);
+    const float uz = fmaf(jz, inv, gw * k.hg[2]);
     const float usq = ux * ux + uy * uy + uz * uz;
-    const float ug = ux * gx + uy * gy + uz * gz;
-    const float lp = d.lp, lm = d.lm;
-    const float cp = 1.f + 0.5f * lp, cm = 1.f + 0.5f * lm;
-    {
-        // q = 0: f+ = f, e+ - w = w (rho - 1 - 1.5 rho u.u), G+ = -3 w rho u.g
-        const float w = wgt(0);
-        const float ep = w * (drho - 1.5f * rho * usq);
-        out[0] = fin[0] + lp * (fin[0] - ep) + cp * (w * rho * (-3.f * ug));
-    }
+    const float ug = gw * (ux * d.g[0] + uy * d.g[1] + uz * d.g[2]);
+    // the part common to every direction of one weight, over that weight
+    const float inner = fmaf(-d.lp, drho, rho * (k.lp15 * usq - k.cp3 * ug));
+    out[0] = fmaf(k.c0, fin[0], wgt(0) * inner);
+    const float af = wgt(1) * inner, ae = wgt(7) * inner;
+    const float wrf = wgt(1) * rho, wre = wgt(7) * rho;
+    const float wrf3 = 3.f * wrf, wre3 = 3.f * wre;
 #pragma unroll
-    for (int q = 1; q < kQ; q += 2) {
-        const int qb = q + 1;
-        const float w = wgt(q);
-        const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-        const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
-        const float ep = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));   // e+_q - w_q
-        const float em = w * rho * 3.f * cu;                                  // e-_q
-        const float fp = 0.5f * (fin[q] + fin[qb]);
-        const float fm = 0.5f * (fin[q] - fin[qb]);
-        const float a = lp * (fp - ep) + cp * (w * rho * (9.f * cu * cg - 3.f * ug));
-        const float b = lm * (fm - em) + cm * (w * rho * 3.f * cg);
-        out[q] = fin[q] + a + b;
-        out[qb] = fin[qb] + a - b;
+    for (int p = 0; p < 9; p++) {
+        const int q = 2 * p + 1, qb = q + 1;
+        const bool face = q <= 6;
+        const float cu = cdot(q, ux, uy, uz);
+        const float al = fmaf((face ? wrf : wre) * cu, fmaf(-k.lp45, cu, gw * k.K[p]), face ? af : ae);
+        const float be = (face ? wrf3 : wre3) * fmaf(-d.lm, cu, gw * k.M[p]);
+        out[q] = fmaf(k.c1, fin[q], fmaf(k.c2, fin[qb], al + be));
+        out[qb] = fmaf(k.c1, fin[qb], fmaf(k.c2, fin[q], al - be));
     }
 }
 

@@ -223,6 +223,18 @@ __device__ __forceinline__ void bulk_load(const Dev& d, const typename Store<S>:
                                           uint32_t i, float (&fin)[kQ]) {
     using T = typename Store<S>::T;
     const uint32_t nx = (uint32_t)d.nx, nxy = (uint32_t)d.nx * (uint32_t)d.ny;
+    if ((x & ~31) > 0 && (x | 31) < d.nx - 1 && y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
+        // every neighbour inside the grid: the source of direction q is i - c_q . (1, nx, nx ny).
+        // Tested on the 32-aligned run of x around x, the warp of the bulk sweep, so that a
+        // warp takes one of the two branches (any x in that run is at least 1 and below nx - 1)
+#pragma unroll
+        for (int q = 0; q < kQ; q++) {
+            const int32_t o = cx(q) + cy(q) * (int32_t)nx + cz(q) * (int32_t)nxy;
+            const T* plane = fa + (size_t)q * d.N;
+            fin[q] = CS ? Store<S>::get_cs(plane, i - (uint32_t)o) : Store<S>::get(plane, i - (uint32_t)o);
+        }
+        return;
+    }
     if (y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1) {
         // y and z neighbours inside the grid (the same for a whole warp, which spans x): the
         // source of direction q is i - c_q . (1, nx, nx ny), a grid-uniform offset, except
@@ -393,7 +405,7 @@ __device__ __forceinline__ void boundary_cell(const Dev& d, const typename Store
 #pragma unroll
     for (int q = 0; q < kQ; q++) {
         drho0 += fo[q];
-        j0x += cx(q) * fo[q]; j0y += cy(q) * fo[q]; j0z += cz(q) * fo[q];
+        j0x = cacc(cx(q), j0x, fo[q]); j0y = cacc(cy(q), j0y, fo[q]); j0z = cacc(cz(q), j0z, fo[q]);
     }
     const float rho0 = 1.f + drho0;
     // the force the last collision applied: on the liquid mass, phi g in an interface cell
@@ -444,11 +456,11 @@ __device__ __forceinline__ void boundary_cell(const Dev& d, const typename Store
             // a sphere beside an interface cell: the next gas-pressure pass scans it
             if (isIF && P < (uint32_t)d.nsph) d.gasflag[(size_t)cur * d.max_sph + P] = 1u;
             if (P == P0) {
-                const float corr = 6.f * wgt(q) * rho0 * (cx(q) * ucx + cy(q) * ucy + cz(q) * ucz);
+                const float corr = 6.f * wgt(q) * rho0 * cdot(q, ucx, ucy, ucz);
                 fin[q] = fo[qb] + corr;
                 // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
                 const float dev = 2.f * fo[qb] + corr;
-                acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
+                acc.J[0] = cacc(-cx(q), acc.J[0], dev); acc.J[1] = cacc(-cy(q), acc.J[1], dev); acc.J[2] = cacc(-cz(q), acc.J[2], dev);
                 acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
                 if (liqc) sbb += corr;
             } else if (P < (uint32_t)d.nsph) {
@@ -462,7 +474,7 @@ __device__ __forceinline__ void boundary_cell(const Dev& d, const typename Store
             const uint32_t bb = __float_as_uint(fv[q]);
             const float rg = bb < (uint32_t)d.nbub ? d.bub[bb].rho_gf : d.rho_g0;
             const float rw = rg + 6.f * d.sigma * kap;
-            const float cu = cx(q) * u0x + cy(q) * u0y + cz(q) * u0z;
+            const float cu = cdot(q, u0x, u0y, u0z);
             // -f*_qb + 2 e+_q, in deviations: 2 (e+_q - w_q) - (f*_qb - w_q)
             fin[q] = 2.f * wgt(q) * ((rw - 1.f) + rw * (4.5f * cu * cu - 1.5f * u0sq)) - fo[qb];
         }
@@ -606,11 +618,11 @@ __device__ __forceinline__ void lean_cell(const Dev& d, const typename Store<S>:
         if (wl & (1u << q)) {
             fin[q] = fo[qb];                                        // no-slip wall
         } else if (mask & (1u << q)) {                              // Eq. bbrule
-            const float corr = 6.f * wgt(q) * rho0 * (cx(q) * ucx + cy(q) * ucy + cz(q) * ucz);
+            const float corr = 6.f * wgt(q) * rho0 * cdot(q, ucx, ucy, ucz);
             fin[q] = fo[qb] + corr;
             // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
             const float dev = 2.f * fo[qb] + corr;
-            acc.J[0] -= cx(q) * dev; acc.J[1] -= cy(q) * dev; acc.J[2] -= cz(q) * dev;
+            acc.J[0] = cacc(-cx(q), acc.J[0], dev); acc.J[1] = cacc(-cy(q), acc.J[1], dev); acc.J[2] = cacc(-cz(q), acc.J[2], dev);
             acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
             sbb += corr;
         }
