@@ -523,14 +523,18 @@ constexpr int kTouchWarps = 4;   // spheres per block of the touch kernel
 __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane) {
     // the box and the cell offsets from both centres, set up by one lane (FP64 issue is scarce
     // on this GPU: every lane doing it cost more than the box scan) and shared through the
-    // warp's slots of shared memory
+    // warp's slots of shared memory.  FP64 only splits each centre into an integer cell and an
+    // FP32 fraction (as the sweep's link data does); the box bounds and offsets follow in
+    // integer and FP32 arithmetic (the box has a cell of margin on every side, far beyond their
+    // rounding), and FP64 decides again only the cells whose FP32 distance is near R.
     __shared__ int sGo[kTouchWarps], sLo[kTouchWarps][3], sExt[kTouchWarps][3];
     __shared__ float sA0[kTouchWarps][3], sA1[kTouchWarps][3], sR2f[kTouchWarps];
-    __shared__ double sOff[kTouchWarps][3];
     const int wb = threadIdx.x >> 5;
     const Sphere& s = d.sph[P];
+    const int L[3] = {d.nx, d.ny, d.nz};
     if (lane == 0) {
-        d.sphl[P] = sph_link_of(s);   // the next sweep's link data
+        const SphLink ln = sph_link_of(s);
+        d.sphl[P] = ln;   // the next sweep's link data
         int go = 0;
         if (s.x[0] != s.x0[0] || s.x[1] != s.x0[1] || s.x[2] != s.x0[2]) {
             // a sphere whose centre is not finite or moved more than a cell in one step is left
@@ -538,16 +542,26 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
             if (!finite3(s.x) || !finite3(s.x0) || !(s.R > 0.0 && s.R < 64.0)) {
                 atomicOr(&d.sc->status, S_UNSTABLE);
             } else {
-                const int lim = 2 * (int)ceil(s.R) + 8;
+                const float Rf = (float)s.R;
+                const int lim = 2 * (int)ceilf(Rf) + 8;
                 go = 1;
                 for (int k = 0; k < 3; k++) {
-                    sOff[wb][k] = min_image(d, k, s.x[k], s.x0[k]);   // new centre relative to the old
-                    const double a = s.x0[k], b = s.x0[k] + sOff[wb][k];
-                    sLo[wb][k] = (int)floor(fmin(a, b) - s.R) - 1;
-                    sExt[wb][k] = (int)ceil(fmax(a, b) + s.R) + 1 - sLo[wb][k] + 1;
-                    if (sExt[wb][k] > lim) go = 0;
-                    sA0[wb][k] = (float)((double)sLo[wb][k] - s.x0[k]);
-                    sA1[wb][k] = (float)((double)sLo[wb][k] - (s.x0[k] + sOff[wb][k]));
+                    const double f0 = floor(s.x0[k]);
+                    const int i0 = (int)f0;
+                    const float x0f = (float)(s.x0[k] - f0);   // old centre = i0 + x0f
+                    int di = ln.xi[k] - i0;                     // new centre - old: di + (xf - x0f), minimum image
+                    if (d.bc[k]) {
+                        if (2 * di > L[k]) di -= L[k];
+                        else if (2 * di < -L[k]) di += L[k];
+                    }
+                    const float off = (float)di + (ln.xf[k] - x0f);
+                    const int lo = i0 + (int)floorf(fminf(x0f, x0f + off) - Rf) - 1;
+                    const int hi = i0 + (int)ceilf(fmaxf(x0f, x0f + off) + Rf) + 1;
+                    sLo[wb][k] = lo;
+                    sExt[wb][k] = hi - lo + 1;
+                    if (hi - lo + 1 > lim) go = 0;
+                    sA0[wb][k] = (float)(lo - i0) - x0f;        // cell lo minus the old centre
+                    sA1[wb][k] = sA0[wb][k] - off;              // ... minus the new centre
                 }
                 if (!go) atomicOr(&d.sc->status, S_UNSTABLE);
                 sR2f[wb] = (float)(s.R * s.R);
@@ -557,10 +571,8 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
     }
     __syncwarp();
     if (!sGo[wb]) return;   // (uniform over the warp)
-    const int L[3] = {d.nx, d.ny, d.nz};
     const int lo[3] = {sLo[wb][0], sLo[wb][1], sLo[wb][2]}, ext[3] = {sExt[wb][0], sExt[wb][1], sExt[wb][2]};
     const float a0[3] = {sA0[wb][0], sA0[wb][1], sA0[wb][2]}, a1[3] = {sA1[wb][0], sA1[wb][1], sA1[wb][2]};
-    const double off[3] = {sOff[wb][0], sOff[wb][1], sOff[wb][2]};
     // cell offsets from both centres in FP32 decide wherever |d^2 - R^2| clears their rounding
     // error by far; the few cells closer to the sphere's surface are decided in FP64
     // FP32 squared distances below ~50 carry an error under 1e-5 here
@@ -581,7 +593,8 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
                 const double R2 = s.R * s.R;
                 double d0 = 0, d1 = 0;
                 for (int k = 0; k < 3; k++) {
-                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off[k]);
+                    const double off = min_image(d, k, s.x[k], s.x0[k]);   // new centre relative to the old
+                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off);
                     d0 += a * a;
                     d1 += b * b;
                 }
