@@ -34,7 +34,11 @@ FALLBACK_HBM_GBS = 6800.0
 
 # dram bytes (read + write) per bulk-sweep launch, per workload and storage, from one ncu
 # capture, with the hash of the sweep source it was taken on (null once the kernel changes)
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # one-pass capture of two launches on that column (mean)
+    "column512x512x1024_32bubbles_100000spheres/f16dev": {"sha1": "c9225d3665af5f7c6d438b483d6feaf18880c34d",
+                                                           "bytes_per_launch": 20746279936},
+}
 
 
 def _args():
