@@ -88,8 +88,8 @@ __device__ __forceinline__ void frozen_pull(const Dev& d, const float* __restric
         const float uwx = us[0] + ws[1] * rz - ws[2] * ry;
         const float uwy = us[1] + ws[2] * rx - ws[0] * rz;
         const float uwz = us[2] + ws[0] * ry - ws[1] * rx;
-        cw[q] = 6.f * wgt(q) * (cx(q) * uwx + cy(q) * uwy + cz(q) * uwz);
-        fin[q] = fo[opp(q)] + 6.f * wgt(q) * rho0 * (cx(q) * uwx + cy(q) * uwy + cz(q) * uwz);
+        cw[q] = 6.f * wgt(q) * cdot(q, uwx, uwy, uwz);
+        fin[q] = fo[opp(q)] + 6.f * wgt(q) * rho0 * cdot(q, uwx, uwy, uwz);
     }
 }
 
@@ -140,14 +140,20 @@ struct AdjOut {
 
 __device__ __forceinline__ AdjOut collide_adjoint(const Dev& d, const float (&fin)[kQ], const float (&lam)[kQ],
                                                   float (&acc)[5]) {
+    const Dev::CollisionConsts& k = d.cc;
     const float gx = d.g[0], gy = d.g[1], gz = d.g[2];
     const float lp = d.lp, lm = d.lm;
     const float cp = 1.f + 0.5f * lp, cm = 1.f + 0.5f * lm;
-    float drho = 0.f, jxm = 0.f, jym = 0.f, jzm = 0.f;
+    // moments from the sums and differences of opposite pairs (reused below)
+    float fsum[9], fdif[9];
+    float drho = fin[0], jxm = 0.f, jym = 0.f, jzm = 0.f;
 #pragma unroll
-    for (int q = 0; q < kQ; q++) {
-        drho += fin[q];
-        jxm += cx(q) * fin[q]; jym += cy(q) * fin[q]; jzm += cz(q) * fin[q];
+    for (int p = 0; p < 9; p++) {
+        const int q = 2 * p + 1;
+        fsum[p] = fin[q] + fin[q + 1];
+        fdif[p] = fin[q] - fin[q + 1];
+        drho += fsum[p];
+        jxm = cacc(cx(q), jxm, fdif[p]); jym = cacc(cy(q), jym, fdif[p]); jzm = cacc(cz(q), jzm, fdif[p]);
     }
     const float rho = 1.f + drho, inv = 1.f / rho;
     const float ux = (jxm + 0.5f * rho * gx) * inv, uy = (jym + 0.5f * rho * gy) * inv, uz = (jzm + 0.5f * rho * gz) * inv;
@@ -169,36 +175,53 @@ __device__ __forceinline__ AdjOut collide_adjoint(const Dev& d, const float (&fi
         Tp = L0 * ((fin[0] - ep) + 0.5f * Gp);
         Tm = 0.f;
     }
+    // The pairs (q, qb), with Lp = lam_q + lam_qb, Lm = lam_q - lam_qb, A = c_q.u, B = c_q.g,
+    // s = w rho and R0 = -lp (1 - 1.5 u.u) - 3 cp u.g:
+    //   d/drho:  w (Lp (R0 + A (9 cp B - 4.5 lp A)) + 3 Lm (cm B - lm A))
+    //   d/du:    c_q s (Lp (9 cp B - 9 lp A) - 3 lm Lm) + 3 s Lp (lp u - cp g)
+    //   d/dg:    c_q s (9 cp A Lp + 3 cm Lm) - 3 cp s Lp u
+    //   d/dlp:   Lp ((f_q + f_qb)/2 - w drho + s (4.5 A (B - A) + 1.5 (u.u - u.g)))
+    //   d/dlm:   Lm ((f_q - f_qb)/2 + 1.5 s (B - 2 A))
+    // the terms that do not depend on the pair's direction are summed per weight and applied once
+    const float R0 = -lp * (1.f - 1.5f * usq) - 3.f * cp * ug;
+    const float lp45 = 4.5f * lp, lp9 = 9.f * lp, lm3 = 3.f * lm, cp9 = 9.f * cp, cm3 = 3.f * cm;
+    const float sf = wgt(1) * rho, se = wgt(7) * rho;
+    float rxf = 0.f, rxe = 0.f, ryf = 0.f, rye = 0.f;   // sums of Lp (R0 + ...), Lm (cm B - lm A)
+    float slf = 0.f, sle = 0.f;                         // sums of Lp
+    float taf = 0.f, tae = 0.f, tbf = 0.f, tbe = 0.f;   // sums of Lp A (B - A), Lm (B - 2 A)
+    float tfp = 0.f, tfm = 0.f;                         // sums of Lp (f_q + f_qb), Lm (f_q - f_qb)
 #pragma unroll
-    for (int q = 1; q < kQ; q += 2) {
-        const int qb = q + 1;
-        const float w = wgt(q);
+    for (int p = 0; p < 9; p++) {
+        const int q = 2 * p + 1, qb = q + 1;
+        const bool face = q <= 6;
+        const float s = face ? sf : se;
         const float Lp = lam[q] + lam[qb], Lm = lam[q] - lam[qb];
-        const float cu = cx(q) * ux + cy(q) * uy + cz(q) * uz;
-        const float cg = cx(q) * gx + cy(q) * gy + cz(q) * gz;
-        const float ep = w * (drho + rho * (4.5f * cu * cu - 1.5f * usq));
-        const float em = w * rho * 3.f * cu;
-        const float Gp = w * rho * (9.f * cu * cg - 3.f * ug), Gm = w * rho * 3.f * cg;
-        const float fp = 0.5f * (fin[q] + fin[qb]), fm = 0.5f * (fin[q] - fin[qb]);
-        // d/drho of e+, e-, G+, G-
-        Lrho += Lp * (-lp * w * (1.f + 4.5f * cu * cu - 1.5f * usq) + cp * w * (9.f * cu * cg - 3.f * ug)) +
-                Lm * (-lm * 3.f * w * cu + cm * 3.f * w * cg);
-        // d/du: e+ -> w rho (9 cu c - 3 u), e- -> 3 w rho c, G+ -> w rho (9 cg c - 3 g)
-        const float wr = w * rho;
-        const float ap = Lp * wr * 9.f * (cp * cg - lp * cu) - Lm * lm * 3.f * wr;   // along c_q
-        const float bp = Lp * wr * 3.f;                                                // along (lp u - cp g)
-        Lux += ap * cx(q) + bp * (lp * ux - cp * gx);
-        Luy += ap * cy(q) + bp * (lp * uy - cp * gy);
-        Luz += ap * cz(q) + bp * (lp * uz - cp * gz);
-        // d/dg at fixed u: G+ -> w rho (9 cu c - 3 u), G- -> 3 w rho c
-        const float ag = Lp * cp * wr * 9.f * cu + Lm * cm * 3.f * wr;
-        const float bg = -Lp * cp * wr * 3.f;
-        Gx += ag * cx(q) + bg * ux;
-        Gy += ag * cy(q) + bg * uy;
-        Gz += ag * cz(q) + bg * uz;
-        Tp += Lp * ((fp - ep) + 0.5f * Gp);
-        Tm += Lm * ((fm - em) + 0.5f * Gm);
+        const float A = cdot(q, ux, uy, uz), B = k.cg[p];
+        const float X = fmaf(A, fmaf(-lp45, A, k.K[p]), R0);
+        const float Y = fmaf(-lm, A, k.M[p]);
+        if (face) { rxf = fmaf(Lp, X, rxf); ryf = fmaf(Lm, Y, ryf); slf += Lp; }
+        else { rxe = fmaf(Lp, X, rxe); rye = fmaf(Lm, Y, rye); sle += Lp; }
+        const float ap = s * fmaf(-lm3, Lm, Lp * fmaf(-lp9, A, k.K[p]));
+        Lux = cacc(cx(q), Lux, ap); Luy = cacc(cy(q), Luy, ap); Luz = cacc(cz(q), Luz, ap);
+        const float ag = s * fmaf(cp9 * A, Lp, cm3 * Lm);
+        Gx = cacc(cx(q), Gx, ag); Gy = cacc(cy(q), Gy, ag); Gz = cacc(cz(q), Gz, ag);
+        const float ta = Lp * (A * (B - A)), tb = Lm * fmaf(-2.f, A, B);
+        if (face) { taf += ta; tbf += tb; }
+        else { tae += ta; tbe += tb; }
+        tfp = fmaf(Lp, fsum[p], tfp);
+        tfm = fmaf(Lm, fdif[p], tfm);
     }
+    Lrho += wgt(1) * fmaf(3.f, ryf, rxf) + wgt(7) * fmaf(3.f, rye, rxe);
+    const float S3 = 3.f * (sf * slf + se * sle);
+    Lux += S3 * (lp * ux - cp * gx);
+    Luy += S3 * (lp * uy - cp * gy);
+    Luz += S3 * (lp * uz - cp * gz);
+    Gx -= cp * S3 * ux;
+    Gy -= cp * S3 * uy;
+    Gz -= cp * S3 * uz;
+    const float c15 = 1.5f * (usq - ug);
+    Tp += 0.5f * tfp - drho * (wgt(1) * slf + wgt(7) * sle) + sf * fmaf(4.5f, taf, c15 * slf) + se * fmaf(4.5f, tae, c15 * sle);
+    Tm += 0.5f * tfm + 1.5f * (sf * tbf + se * tbe);
     // u = (j + rho g/2)/rho: du/dfin_k = (c_k + g/2 - u)/rho, du/dg = I/2
     acc[0] += Gx + 0.5f * Lux;
     acc[1] += Gy + 0.5f * Luy;
@@ -224,7 +247,23 @@ __device__ __forceinline__ float adj_in_q(const Dev& d, int q, const float (&lam
         const float Lp = lam[qa] + lam[qb], Lm = lam[qa] - lam[qb];
         mu = lam[q] + 0.5f * d.lp * Lp + ((q & 1) ? 0.5f : -0.5f) * d.lm * Lm;
     }
-    return mu + o.base + o.lx * cx(q) + o.ly * cy(q) + o.lz * cz(q);
+    return mu + o.base + cdot(q, o.lx, o.ly, o.lz);
+}
+
+// the same for all 19 directions, pair by pair: out_q = lam_q + (lp Lp + lm Lm)/2 + base + c_q.l,
+// out_qb = lam_qb + (lp Lp - lm Lm)/2 + base - c_q.l
+__device__ __forceinline__ void adj_in_all(const Dev& d, const float (&lam)[kQ], const AdjOut& o, float (&out)[kQ]) {
+    const float hlp = 0.5f * d.lp, hlm = 0.5f * d.lm;
+    out[0] = fmaf(lam[0], 1.f + d.lp, o.base);
+#pragma unroll
+    for (int p = 0; p < 9; p++) {
+        const int q = 2 * p + 1, qb = q + 1;
+        const float Lp = lam[q] + lam[qb], Lm = lam[q] - lam[qb];
+        const float hp = fmaf(hlp, Lp, o.base);
+        const float hm = fmaf(hlm, Lm, cdot(q, o.lx, o.ly, o.lz));
+        out[q] = lam[q] + (hp + hm);
+        out[qb] = lam[qb] + (hp - hm);
+    }
 }
 
 // per-block sums of the five parameter terms into one of kAdjSlots FP64 slots
@@ -267,6 +306,8 @@ __global__ void __launch_bounds__(128, 6) adjoint_bulk_kernel(const Dev d, const
             // source of direction q: i - c_q . (1, nx, nx ny) (a grid-uniform offset) where y
             // and z stay inside the grid (the same for a whole warp); x edges wrap or bounce
             const bool inner = y > 0 && y < d.ny - 1 && z > 0 && z < d.nz - 1;
+            // no x edge in the warp's 32-aligned run of x either: every source at the offset
+            const bool plain = inner && (x & ~31) > 0 && (x | 31) < d.nx - 1;
             const bool edge0 = x == 0, edge1 = x == d.nx - 1, perx = d.bc[0] != 0;
             const uint32_t xm = x == 0 ? nx - 1 : x - 1, xp = x == d.nx - 1 ? 0 : x + 1;
             const uint32_t ym = (y == 0 ? d.ny - 1 : y - 1) * nx, yp = (y == d.ny - 1 ? 0 : y + 1) * nx, y0 = y * nx;
@@ -274,9 +315,18 @@ __global__ void __launch_bounds__(128, 6) adjoint_bulk_kernel(const Dev d, const
             const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
             const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
             const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
+            // periodic x: the x-edge lanes' sources one period over (0 elsewhere)
+            const uint32_t adjp = edge0 ? nx : 0u, adjm = edge1 ? 0u - nx : 0u;
             // (plane, index) of the PDF direction q pulls: its own opposite PDF beyond a wall
             auto link = [&](int q, uint32_t& plane, uint32_t& idx) {
-                if (inner) {
+                if (plain) {
+                    plane = (uint32_t)q;
+                    idx = i - (uint32_t)(cx(q) + cy(q) * (int32_t)nx + cz(q) * (int32_t)nxy);   // modulo 2^32
+                } else if (inner && perx) {
+                    plane = (uint32_t)q;
+                    idx = i - (uint32_t)(cx(q) + cy(q) * (int32_t)nx + cz(q) * (int32_t)nxy) +
+                          (cx(q) == 1 ? adjp : (cx(q) == -1 ? adjm : 0u));
+                } else if (inner) {
                     const int32_t o = cx(q) + cy(q) * (int32_t)nx + cz(q) * (int32_t)nxy;
                     bool wall = false;
                     int32_t adj = 0;
@@ -305,11 +355,13 @@ __global__ void __launch_bounds__(128, 6) adjoint_bulk_kernel(const Dev d, const
                 lam[q] = __ldcs(lam_in + (size_t)q * N + i);
             }
             const AdjOut o = collide_adjoint(d, fin, lam, acc);
+            float out[kQ];
+            adj_in_all(d, lam, o, out);
 #pragma unroll
             for (int q = 0; q < kQ; q++) {
                 uint32_t pl, ix;
                 link(q, pl, ix);
-                __stcs(lam_out + (size_t)pl * N + ix, adj_in_q(d, q, lam, o));
+                __stcs(lam_out + (size_t)pl * N + ix, out[q]);
             }
         }
     }

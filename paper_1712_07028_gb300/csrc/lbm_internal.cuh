@@ -244,6 +244,7 @@ struct Dev {
         float lp45;          // 4.5 lambda_+
         float hg[3];         // g / 2
         float K[9], M[9];    // per opposite pair (q = 2k+1, 2k+2): 9 (1 + lambda_+/2) c_q.g, (1 + lambda_-/2) c_q.g
+        float cg[9];         // per opposite pair: c_q.g
     } cc;
     float sigma;
     float rho_g0;
@@ -540,6 +541,7 @@ inline void set_collision_consts(Dev& d) {
         const double cg = cx(q) * (double)d.g[0] + cy(q) * (double)d.g[1] + cz(q) * (double)d.g[2];
         k.K[p] = (float)(9.0 * cp * cg);
         k.M[p] = (float)(cm * cg);
+        k.cg[p] = (float)cg;
     }
 }
 
