@@ -161,6 +161,7 @@ struct Scalars {
     uint32_t n_liq;       // and liquid cells, at the back
     uint32_t n_rare;      // liquid cells with links into two spheres or into gas (wl_rare)
     uint32_t n_paired;    // spheres with partners this step (sph_list)
+    uint32_t n_coupled;   // spheres whose sub-steps feel lubrication this step (sph_cpl)
     uint32_t ticket;      // blocks of the end-of-step scan that have finished
     uint32_t n_fix;       // BULK cells the end of the last step changed or whose neighbours it changed
     uint32_t fix_all;     // the fix list overflowed: the fix pass takes every BULK cell
@@ -281,6 +282,7 @@ struct Dev {
     uint32_t* bin_ids;        // [nbins][bin_cap]
     uint32_t* npairs;         // [max_sph] partners within lubrication reach this step
     uint32_t* sph_list;       // [max_sph] the spheres with partners this step (n_paired of them)
+    uint32_t* sph_cpl;        // [max_sph] the spheres with a partner within lubrication reach (n_coupled)
     uint32_t* pairs;          // [max_sph][kPairCap]
     unsigned long long* merge_keys;   // [kMergeCap] pairs (lo + 1) << 32 | hi of touching roots, 0 = free
     uint32_t* merge_list;     // [kMergeCap] slots of merge_keys in use, in insertion order

@@ -55,6 +55,7 @@ __device__ inline void sph_prepare_one(const Dev& d, const int P) {
 }
 __global__ void sph_prepare_kernel(const Dev d) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P == 0) d.sc->n_coupled = 0u;   // the first sub-step launch lists them anew
     if (P < d.nsph) sph_prepare_one(d, P);
 }
 
@@ -361,9 +362,71 @@ __device__ void substep_one(const Dev& d, const Sphere* src, Sphere* dst, const 
     dst[P] = o;
 }
 
-__global__ void sph_substep_kernel(const Dev d, const Sphere* src, Sphere* dst, const double dt) {
+// Sub-steps of many spheres, one launch per sub-step. The first launch splits them: a sphere with
+// no partner that can come within lubrication reach this step (an FP32 prefilter on the
+// step-start centres of the link data, with the same margin as the one-block kernel below)
+// takes all its sub-steps at once in closed form and writes its final state to both buffers;
+// the others take their first sub-step and are listed, and only they run in the later launches
+// (partners are symmetric: a listed sphere reads only listed spheres).
+__device__ bool sph_coupled(const Dev& d, const int P) {
+    const SphLink lp = d.sphl[P];
+    const float Rp = (float)d.sph[P].R;
+    const int L[3] = {d.nx, d.ny, d.nz};
+    const uint32_t np = min(d.npairs[P], (uint32_t)kPairCap);
+    for (uint32_t k = 0; k < np; k++) {
+        const uint32_t Q = d.pairs[(size_t)P * kPairCap + k];
+        const SphLink lq = d.sphl[Q];
+        float g2 = 0.f;
+        for (int c = 0; c < 3; c++) {
+            int di = lq.xi[c] - lp.xi[c];
+            if (d.bc[c]) {
+                if (2 * di > L[c]) di -= L[c];
+                else if (2 * di < -L[c]) di += L[c];
+            }
+            const float v = (float)di + (lq.xf[c] - lp.xf[c]);
+            g2 += v * v;
+        }
+        const float reach = Rp + (float)d.sph[Q].R + 2.f / 3.f + 0.5f;
+        if (g2 <= reach * reach) return true;
+    }
+    return false;
+}
+// all n sub-steps of a sphere that feels no lubrication: constant increments, u_k = u_0 + k du,
+// x_n = x_0 + dt (n u_0 + n(n+1)/2 du), w_n = w_0 + n dw (the sub-step recurrence up to FP64
+// rounding; the same expressions as the one-block kernel)
+__device__ Sphere substeps_closed(const Dev& d, const Sphere& s, const double dt) {
+    Sphere o = s;
+    const double m = s.rho * 4.0 / 3.0 * kPi * s.R * s.R * s.R, I = 0.4 * m * s.R * s.R;
+    const int L[3] = {d.nx, d.ny, d.nz};
+    const bool hasp = s.hasp != 0.0;
+    const double nsub = (double)d.n_sub, tri = 0.5 * nsub * (nsub + 1.0);
+    for (int k = 0; k < 3; k++) {
+        const double Fh = hasp ? 0.5 * (s.F[k] + s.Fp[k]) : s.F[k];
+        const double Th = hasp ? 0.5 * (s.T[k] + s.Tp[k]) : s.T[k];
+        const double du = dt * (Fh + 0.0 + m * d.gd[k]) / m, dw = dt * Th / I;
+        o.x[k] = s.x[k] + dt * (nsub * s.u[k] + tri * du);
+        if (d.bc[k]) o.x[k] = wrap_pos(o.x[k], L[k]);
+        o.u[k] = s.u[k] + nsub * du;
+        o.w[k] = s.w[k] + nsub * dw;
+        o.Fl[k] = 0.0;
+    }
+    return o;
+}
+__global__ void sph_substep_first_kernel(const Dev d, Sphere* src, Sphere* dst, const double dt) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P < d.nsph) substep_one(d, src, dst, dt, P);
+    if (P >= d.nsph) return;
+    if (sph_coupled(d, P)) {
+        substep_one(d, src, dst, dt, P);
+        d.sph_cpl[atomicAdd(&d.sc->n_coupled, 1u)] = (uint32_t)P;
+    } else {
+        const Sphere o = substeps_closed(d, src[P], dt);
+        dst[P] = o;
+        src[P] = o;   // no listed sphere reads it
+    }
+}
+__global__ void sph_substep_list_kernel(const Dev d, const Sphere* src, Sphere* dst, const double dt) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < *(volatile const uint32_t*)&d.sc->n_coupled) substep_one(d, src, dst, dt, (int)d.sph_cpl[t]);
 }
 
 // All sub-steps in one block (up to 1024 spheres, one per thread): positions and velocities
@@ -511,9 +574,14 @@ __global__ void sph_prescribed_kernel(const Dev d) {
     if (P < d.nsph) sph_prescribed_one(d, P);
 }
 
+// after an odd number of sub-steps: the listed spheres' final states into the sphere table
+// (the others wrote theirs to both buffers)
 __global__ void sph_copy_kernel(const Dev d) {
-    const int P = blockIdx.x * blockDim.x + threadIdx.x;
-    if (P < d.nsph) d.sph[P] = d.sph_tmp[P];
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < *(volatile const uint32_t*)&d.sc->n_coupled) {
+        const uint32_t P = d.sph_cpl[t];
+        d.sph[P] = d.sph_tmp[P];
+    }
 }
 
 // ---------------------------------------------------------------- cover / uncover
@@ -851,9 +919,10 @@ void launch_spheres_move(const Dev& d, cudaStream_t st) {
     if (d.sphere_mode == LBM_SPHERES_FREE) {
         const double dt = 1.0 / d.n_sub;
         for (int k = 0; k < d.n_sub; k++) {
-            const Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
+            Sphere* src = (k & 1) ? d.sph_tmp : d.sph;
             Sphere* dst = (k & 1) ? d.sph : d.sph_tmp;
-            sph_substep_kernel<<<nb, tb, 0, st>>>(d, src, dst, dt);
+            if (k == 0) sph_substep_first_kernel<<<nb, tb, 0, st>>>(d, src, dst, dt);
+            else sph_substep_list_kernel<<<nb, tb, 0, st>>>(d, src, dst, dt);
         }
         if (d.n_sub & 1) sph_copy_kernel<<<nb, tb, 0, st>>>(d);
     } else if (d.sphere_mode == LBM_SPHERES_PRESCRIBED) {
