@@ -84,57 +84,58 @@ __device__ __forceinline__ void for_partners(const Dev& d, int P, const double* 
 // the momentum-exchange paragraph), reflected by Eq. bbrule with rho_w = 1 at P's surface.
 // One block per sphere P; its threads share the cells of each close partner's box, and only
 // cells that can be such a node (covered by Q, within R_P + 1.5 of P) are read.
-// links between obstacle nodes of sphere P and of its partners, by a group of nt threads
-// (a multiple of 32; t the thread's index in the group); the group's sums go to F_P, T_P with
-// one FP64 atomic per warp that has a link.
-// The group is the whole block (its shared memory holds each partner's box, set up by one
-// thread: FP64 issue is scarce on this GPU, and every thread doing it cost more than the scan).
-__device__ inline void sph_contact_one(const Dev& d, const int P, const int t, const int nt) {
-    __shared__ int sTotal, sLo[3], sExt[3];
-    __shared__ float sOq[3], sOp[3], sRQ2, sRP2;
+// links between obstacle nodes of sphere P and of its partners, by one warp (lane of 32); the
+// warp's sums go to F_P, T_P with one FP64 atomic per sum.  Each partner's box, the cells both
+// within R_Q of Q's centre and within R_P + 1.5 of P's, comes from the two spheres' link data
+// (integer cell and FP32 fraction of each centre: no FP64 arithmetic, which issues slowly on this
+// GPU), one cell wider on every side than the exact box so that its rounding cannot cut a cell
+// off; the FP32 distance tests (with margins) and the lattice's types and owners decide, and
+// each link's momentum is computed in FP64 from the sphere table.  Every lane forms the box: in a
+// warp that costs the same instructions as one lane forming it.
+__device__ inline void sph_contact_one(const Dev& d, const int P, const int lane) {
     const Sphere& s = d.sph[P];
     double F[3] = {0, 0, 0}, T[3] = {0, 0, 0};
     const int L[3] = {d.nx, d.ny, d.nz};
     const uint32_t np = min(d.npairs[P], (uint32_t)kPairCap);
     const bool valid = finite3(s.x) && s.R > 0.0 && s.R < 64.0;
+    const SphLink lp = d.sphl[P];
+    const float RP = (float)s.R;
     for (uint32_t pk = 0; valid && pk < np; pk++) {
         const uint32_t Q = d.pairs[(size_t)P * kPairCap + pk];
         const Sphere& o = d.sph[Q];
-        if (t == 0) {
-            int total = 0;
-            if (finite3(o.x) && o.R > 0.0 && o.R < 64.0) {
-                double cq[3];   // Q's centre, unwrapped next to P
-                for (int k = 0; k < 3; k++) cq[k] = s.x[k] + min_image(d, k, o.x[k], s.x[k]);
-                const double dd2 = (cq[0] - s.x[0]) * (cq[0] - s.x[0]) + (cq[1] - s.x[1]) * (cq[1] - s.x[1]) + (cq[2] - s.x[2]) * (cq[2] - s.x[2]);
-                const double reach = s.R + o.R + 2.0;
-                if (dd2 <= reach * reach) {
-                    // the box of the cells both within R_Q of Q's centre and within R_P + 1.5 of
-                    // P's: the overlap of the two spheres' boxes (a cell or so thick where they
-                    // nearly touch)
-                    total = 1;
-                    for (int k = 0; k < 3; k++) {
-                        sLo[k] = (int)floor(fmax(cq[k] - o.R, s.x[k] - (s.R + 1.5)));
-                        sExt[k] = max(0, (int)ceil(fmin(cq[k] + o.R, s.x[k] + (s.R + 1.5))) - sLo[k] + 1);
-                        sOq[k] = (float)((double)sLo[k] - cq[k]);
-                        sOp[k] = (float)((double)sLo[k] - s.x[k]);
-                        total *= sExt[k];
-                    }
-                    // a necessary condition only (the lattice's owners decide), with a margin
-                    // for FP32
-                    sRQ2 = (float)(o.R * o.R) + 0.01f;
-                    sRP2 = (float)((s.R + 1.5) * (s.R + 1.5)) + 0.01f;
-                }
+        if (!(finite3(o.x) && o.R > 0.0 && o.R < 64.0)) continue;
+        const SphLink lq = d.sphl[Q];
+        const float RQ = (float)o.R;
+        float cq[3];   // Q's centre relative to P's integer cell, minimum image
+        float dd2 = 0.f;
+        for (int k = 0; k < 3; k++) {
+            int di = lq.xi[k] - lp.xi[k];
+            if (d.bc[k]) {
+                if (2 * di > L[k]) di -= L[k];
+                else if (2 * di < -L[k]) di += L[k];
             }
-            sTotal = total;
+            cq[k] = lp.xf[k] + ((float)di + (lq.xf[k] - lp.xf[k]));
+            const float v = cq[k] - lp.xf[k];
+            dd2 += v * v;
         }
-        __syncthreads();
-        const int total = sTotal;
-        const int lo[3] = {sLo[0], sLo[1], sLo[2]}, ext[3] = {sExt[0], sExt[1], sExt[2]};
-        const float oq[3] = {sOq[0], sOq[1], sOq[2]}, op[3] = {sOp[0], sOp[1], sOp[2]};
-        const float RQ2 = sRQ2, RP2 = sRP2;
-        __syncthreads();   // thread 0 rewrites the box for the next partner
+        // beyond R_P + R_Q + 2 two spheres have no adjacent obstacle nodes (the margin covers FP32)
+        const float reach = RP + RQ + 2.f;
+        if (dd2 > reach * reach + 1e-3f) continue;
+        int lo[3], ext[3], total = 1;
+        float oq[3], op[3];
+        for (int k = 0; k < 3; k++) {
+            const int l = (int)floorf(fmaxf(cq[k] - RQ, lp.xf[k] - (RP + 1.5f))) - 1;
+            const int h = (int)ceilf(fminf(cq[k] + RQ, lp.xf[k] + (RP + 1.5f))) + 1;
+            ext[k] = max(0, h - l + 1);
+            lo[k] = lp.xi[k] + l;
+            oq[k] = (float)l - cq[k];
+            op[k] = (float)l - lp.xf[k];
+            total *= ext[k];
+        }
+        // a necessary condition only (the lattice's owners decide), with a margin for FP32
+        const float RQ2 = RQ * RQ + 0.01f, RP2 = (RP + 1.5f) * (RP + 1.5f) + 0.01f;
         {
-            for (int e = t; e < total; e += nt) {
+            for (int e = lane; e < total; e += 32) {
                 const int ex[3] = {e % ext[0], (e / ext[0]) % ext[1], e / (ext[0] * ext[1])};
                 int w[3] = {lo[0] + ex[0], lo[1] + ex[1], lo[2] + ex[2]};
                 float aq = 0.f, ap = 0.f;
@@ -186,10 +187,9 @@ __device__ inline void sph_contact_one(const Dev& d, const int P, const int t, c
             }
         }
     }
-    // (uniform over each warp: only warps with a link sum)
+    // (uniform over the warp: only warps with a link sum)
     const bool any = F[0] != 0.0 || F[1] != 0.0 || F[2] != 0.0 || T[0] != 0.0 || T[1] != 0.0 || T[2] != 0.0;
     if (np == 0 || !__any_sync(0xffffffffu, any)) return;
-    const int lane = t & 31;
     double v[6] = {F[0], F[1], F[2], T[0], T[1], T[2]};
     for (int c = 0; c < 6; c++) v[c] = warp_sum(v[c]);
     SphereAcc& a = d.acc[P];
@@ -198,10 +198,11 @@ __device__ inline void sph_contact_one(const Dev& d, const int P, const int t, c
             if (v[c] != 0.0) atomicAdd(c < 3 ? &a.C[c] : &a.TC[c - 3], v[c]);
 }
 
-// blocks over the spheres with partners (listed by the pair pass; block-uniform loop)
+// one warp per sphere with partners (listed by the pair pass)
 __global__ void sph_contact_kernel(const Dev d) {
     const uint32_t n = min(*(volatile const uint32_t*)&d.sc->n_paired, (uint32_t)d.nsph);
-    for (uint32_t k = blockIdx.x; k < n; k += gridDim.x) sph_contact_one(d, (int)d.sph_list[k], threadIdx.x, blockDim.x);
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t k = warp_id(); k < n; k += nw) sph_contact_one(d, (int)d.sph_list[k], threadIdx.x & 31);
 }
 
 // The gas's pressure on the sphere surface the gas touches.  The sweep's links come from
@@ -899,7 +900,7 @@ void launch_cover_touch(const Dev& d, cudaStream_t st) {
 void launch_spheres_links(const Dev& d, int g, cudaStream_t st) {
     if (d.nsph == 0) return;
     sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
-    sph_contact_kernel<<<d.nsph < 152 * 8 ? d.nsph : 152 * 8, 128, 0, st>>>(d);
+    sph_contact_kernel<<<d.nsph < 152 * 32 ? (d.nsph + 3) / 4 : 152 * 8, 128, 0, st>>>(d);
     sph_gas_kernel<<<d.nsph, 128, 0, st>>>(d, g);
 }
 
