@@ -598,6 +598,7 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
     // rounding), and FP64 decides again only the cells whose FP32 distance is near R.
     __shared__ int sGo[kTouchWarps], sLo[kTouchWarps][3], sExt[kTouchWarps][3];
     __shared__ float sA0[kTouchWarps][3], sA1[kTouchWarps][3], sR2f[kTouchWarps];
+    __shared__ double sOff[kTouchWarps][3];
     const int wb = threadIdx.x >> 5;
     const Sphere& s = d.sph[P];
     const int L[3] = {d.nx, d.ny, d.nz};
@@ -631,6 +632,7 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
                     if (hi - lo + 1 > lim) go = 0;
                     sA0[wb][k] = (float)(lo - i0) - x0f;        // cell lo minus the old centre
                     sA1[wb][k] = sA0[wb][k] - off;              // ... minus the new centre
+                    sOff[wb][k] = min_image(d, k, s.x[k], s.x0[k]);   // for the FP64 decisions
                 }
                 if (!go) atomicOr(&d.sc->status, S_UNSTABLE);
                 sR2f[wb] = (float)(s.R * s.R);
@@ -643,9 +645,10 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
     const int lo[3] = {sLo[wb][0], sLo[wb][1], sLo[wb][2]}, ext[3] = {sExt[wb][0], sExt[wb][1], sExt[wb][2]};
     const float a0[3] = {sA0[wb][0], sA0[wb][1], sA0[wb][2]}, a1[3] = {sA1[wb][0], sA1[wb][1], sA1[wb][2]};
     // cell offsets from both centres in FP32 decide wherever |d^2 - R^2| clears their rounding
-    // error by far; the few cells closer to the sphere's surface are decided in FP64
-    // FP32 squared distances below ~50 carry an error under 1e-5 here
-    const float R2f = sR2f[wb], band = 1e-4f * (1.f + R2f);
+    // error by far; the few cells closer to the sphere's surface are decided in FP64.  The FP32
+    // offsets carry an error under 1e-6 (an exact integer difference less an FP32 fraction), so
+    // squared distances near R^2 one of at most a few 1e-6 (1 + R^2): the band is 2e-5 (1 + R^2)
+    const float R2f = sR2f[wb], band = 2e-5f * (1.f + R2f);
     // each lane takes columns (x, y) of the box and walks them along z
     const int nxy = ext[0] * ext[1];
     for (int exy = lane; exy < nxy; exy += 32) {
@@ -662,8 +665,7 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
                 const double R2 = s.R * s.R;
                 double d0 = 0, d1 = 0;
                 for (int k = 0; k < 3; k++) {
-                    const double off = min_image(d, k, s.x[k], s.x0[k]);   // new centre relative to the old
-                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + off);
+                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + sOff[wb][k]);
                     d0 += a * a;
                     d1 += b * b;
                 }
