@@ -283,11 +283,14 @@ struct Dev {
     uint32_t* npairs;         // [max_sph] partners within lubrication reach this step
     uint32_t* sph_list;       // [max_sph] the spheres with partners this step (n_paired of them)
     uint32_t* sph_cpl;        // [max_sph] the spheres with a partner within lubrication reach (n_coupled)
+    uint32_t* sph_near;       // [max_sph][kNearCap] those partners of each listed sphere (sph_nnear of them)
+    uint32_t* sph_nnear;      // [max_sph]
     uint32_t* pairs;          // [max_sph][kPairCap]
     unsigned long long* merge_keys;   // [kMergeCap] pairs (lo + 1) << 32 | hi of touching roots, 0 = free
     uint32_t* merge_list;     // [kMergeCap] slots of merge_keys in use, in insertion order
 };
 constexpr int kPairCap = 32;
+constexpr int kNearCap = 12;   // partners within lubrication reach (at most 12 equal spheres touch one)
 constexpr int kBoundaryGrid = 152 * 2;   // blocks of the general boundary sweep when it runs alone
 
 __device__ __forceinline__ size_t cell_index(const Dev& d, int x, int y, int z) {

@@ -326,13 +326,14 @@ __global__ void sph_pairs_kernel(const Dev d) {
 // u += dt F_tot/m, w += dt T/I, x += dt u into dst.  The hydrodynamic force and torque are
 // the mean of this step's and the previous step's momentum exchange (Ladd 1994), which keeps
 // light spheres from a two-step oscillation.
-__device__ void substep_one(const Dev& d, const Sphere* src, Sphere* dst, const double dt, const int P) {
+// (partners: the np sphere ids of list)
+__device__ void substep_one(const Dev& d, const Sphere* src, Sphere* dst, const double dt, const int P,
+                            const uint32_t* list, const uint32_t np) {
     const Sphere& s = src[P];
     const double dc = 2.0 / 3.0, mu = ((double)d.tau - 0.5) / 3.0;
     double Fl[3] = {0, 0, 0};
-    const uint32_t np = min(d.npairs[P], (uint32_t)kPairCap);
     for (uint32_t k = 0; k < np; k++) {
-        const Sphere& o = src[d.pairs[(size_t)P * kPairCap + k]];
+        const Sphere& o = src[list[k]];
         double dd[3];
         for (int c = 0; c < 3; c++) dd[c] = min_image(d, c, o.x[c], s.x[c]);   // x_12 = x_Q - x_P
         const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
@@ -363,13 +364,15 @@ __device__ void substep_one(const Dev& d, const Sphere* src, Sphere* dst, const 
     dst[P] = o;
 }
 
-// Sub-steps of many spheres, one launch per sub-step. The first launch splits them: a sphere with
-// no partner that can come within lubrication reach this step (an FP32 prefilter on the
-// step-start centres of the link data, with the same margin as the one-block kernel below)
-// takes all its sub-steps at once in closed form and writes its final state to both buffers;
-// the others take their first sub-step and are listed, and only they run in the later launches
-// (partners are symmetric: a listed sphere reads only listed spheres).
-__device__ bool sph_coupled(const Dev& d, const int P) {
+// Sub-steps of many spheres, one launch per sub-step. The first launch splits them: the partners
+// that can come within lubrication reach this step are found by an FP32 prefilter on the
+// step-start centres of the link data, with the same margin as the one-block kernel below; a
+// sphere with none takes all its sub-steps at once in closed form and writes its final state to
+// both buffers; the others keep their near partners, take their first sub-step and are listed,
+// and only they run in the later launches, over those partners only (the others cannot come
+// within reach; partners are symmetric: a listed sphere reads only listed spheres).
+__device__ uint32_t sph_near_partners(const Dev& d, const int P, uint32_t* near) {
+    uint32_t nn = 0;
     const SphLink lp = d.sphl[P];
     const float Rp = (float)d.sph[P].R;
     const int L[3] = {d.nx, d.ny, d.nz};
@@ -388,9 +391,11 @@ __device__ bool sph_coupled(const Dev& d, const int P) {
             g2 += v * v;
         }
         const float reach = Rp + (float)d.sph[Q].R + 2.f / 3.f + 0.5f;
-        if (g2 <= reach * reach) return true;
+        if (g2 > reach * reach) continue;
+        if (nn < (uint32_t)kNearCap) near[nn++] = Q;
+        else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
     }
-    return false;
+    return nn;
 }
 // all n sub-steps of a sphere that feels no lubrication: constant increments, u_k = u_0 + k du,
 // x_n = x_0 + dt (n u_0 + n(n+1)/2 du), w_n = w_0 + n dw (the sub-step recurrence up to FP64
@@ -416,8 +421,11 @@ __device__ Sphere substeps_closed(const Dev& d, const Sphere& s, const double dt
 __global__ void sph_substep_first_kernel(const Dev d, Sphere* src, Sphere* dst, const double dt) {
     const int P = blockIdx.x * blockDim.x + threadIdx.x;
     if (P >= d.nsph) return;
-    if (sph_coupled(d, P)) {
-        substep_one(d, src, dst, dt, P);
+    uint32_t* near = d.sph_near + (size_t)P * kNearCap;
+    const uint32_t nn = sph_near_partners(d, P, near);
+    if (nn > 0) {
+        d.sph_nnear[P] = nn;
+        substep_one(d, src, dst, dt, P, near, nn);
         d.sph_cpl[atomicAdd(&d.sc->n_coupled, 1u)] = (uint32_t)P;
     } else {
         const Sphere o = substeps_closed(d, src[P], dt);
@@ -427,7 +435,10 @@ __global__ void sph_substep_first_kernel(const Dev d, Sphere* src, Sphere* dst, 
 }
 __global__ void sph_substep_list_kernel(const Dev d, const Sphere* src, Sphere* dst, const double dt) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < *(volatile const uint32_t*)&d.sc->n_coupled) substep_one(d, src, dst, dt, (int)d.sph_cpl[t]);
+    if (t < *(volatile const uint32_t*)&d.sc->n_coupled) {
+        const uint32_t P = d.sph_cpl[t];
+        substep_one(d, src, dst, dt, (int)P, d.sph_near + (size_t)P * kNearCap, d.sph_nnear[P]);
+    }
 }
 
 // All sub-steps in one block (up to 1024 spheres, one per thread): positions and velocities
