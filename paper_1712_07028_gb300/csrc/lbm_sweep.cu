@@ -76,6 +76,69 @@ __device__ __forceinline__ void sph_flush_direct(const Dev& d, const SphAcc& a) 
 }
 
 
+// A block's sphere sums of one round of the shell kernels, gathered in shared memory: a table of
+// kAccSlots slots keyed by sphere id (slot = id mod kAccSlots), FP32 and integer sums added with
+// shared-memory atomics; a cell whose slot another sphere holds adds straight to the global
+// accumulators.  In scan order the 32 cells of a warp lie around a dozen or more spheres (a row
+// crosses one after another), so a reduction over the warp would take that many rounds; the
+// block's 128 cells (four rows or so) meet about as many spheres, each several times.
+constexpr int kAccSlots = 64;
+struct AccTable {
+    uint32_t key[kAccSlots];
+    float v[kAccSlots][6];   // J, (x - x_P) x J
+    int iv[kAccSlots][6];    // K, x_img x K (integer parts)
+};
+__device__ __forceinline__ void acc_table_clear(AccTable& t) {
+    for (int s = threadIdx.x; s < kAccSlots; s += blockDim.x) {
+        t.key[s] = kNone;
+#pragma unroll
+        for (int c = 0; c < 6; c++) { t.v[s][c] = 0.f; t.iv[s][c] = 0; }
+    }
+}
+__device__ __forceinline__ void acc_table_add(const Dev& d, const SphAcc& acc, AccTable& t) {
+    if (acc.pid == kNone) return;
+    const float v[6] = {acc.J[0], acc.J[1], acc.J[2], acc.r[1] * acc.J[2] - acc.r[2] * acc.J[1],
+                        acc.r[2] * acc.J[0] - acc.r[0] * acc.J[2], acc.r[0] * acc.J[1] - acc.r[1] * acc.J[0]};
+    const int iv[6] = {acc.K[0], acc.K[1], acc.K[2], acc.xi[1] * acc.K[2] - acc.xi[2] * acc.K[1],
+                       acc.xi[2] * acc.K[0] - acc.xi[0] * acc.K[2], acc.xi[0] * acc.K[1] - acc.xi[1] * acc.K[0]};
+    const int s = (int)(acc.pid & (uint32_t)(kAccSlots - 1));
+    const uint32_t k = atomicCAS(&t.key[s], kNone, acc.pid);
+    if (k == kNone || k == acc.pid) {
+#pragma unroll
+        for (int c = 0; c < 6; c++) {
+            atomicAdd(&t.v[s][c], v[c]);
+            atomicAdd(&t.iv[s][c], iv[c]);
+        }
+    } else {
+        SphereAcc& g = d.acc[acc.pid];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            atomicAdd(&g.J[c], (double)v[c]);
+            atomicAdd(&g.TJ[c], (double)v[3 + c]);
+            atomicAdd(&g.K[c], (unsigned long long)(long long)iv[c]);
+            atomicAdd(&g.XK[c], (unsigned long long)(long long)iv[3 + c]);
+        }
+    }
+}
+// (after a block barrier) the table's sums to the global accumulators, the table cleared
+__device__ __forceinline__ void acc_table_flush(const Dev& d, AccTable& t) {
+    for (int s = threadIdx.x; s < kAccSlots; s += blockDim.x) {
+        const uint32_t P = t.key[s];
+        if (P == kNone) continue;
+        SphereAcc& g = d.acc[P];
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            if (t.v[s][c] != 0.f) atomicAdd(&g.J[c], (double)t.v[s][c]);
+            if (t.v[s][3 + c] != 0.f) atomicAdd(&g.TJ[c], (double)t.v[s][3 + c]);
+            if (t.iv[s][c] != 0) atomicAdd(&g.K[c], (unsigned long long)(long long)t.iv[s][c]);
+            if (t.iv[s][3 + c] != 0) atomicAdd(&g.XK[c], (unsigned long long)(long long)t.iv[s][3 + c]);
+            t.v[s][c] = t.v[s][3 + c] = 0.f;
+            t.iv[s][c] = t.iv[s][3 + c] = 0;
+        }
+        t.key[s] = kNone;
+    }
+}
+
 // the lanes' sphere accumulators summed over the warp, sphere by sphere, then one FP64 atomic per
 // warp and sphere (every lane of the warp takes part)
 __device__ __forceinline__ void sph_acc_warp_reduce(const Dev& d, const SphAcc& acc) {
@@ -660,7 +723,12 @@ __global__ void __launch_bounds__(128, Mode == kBndLeanFast ? 6 : (Mode != kBndG
     __shared__ uint32_t sNif[4], sVb[4];
     __shared__ double sV[4];
     __shared__ float sS[4];
+    __shared__ AccTable sAcc;   // (the shell instances' sphere sums)
     float sbb_t = 0.f;   // Lean: the thread's bounce-back mass over all its rounds
+    if (Lean) {
+        acc_table_clear(sAcc);
+        __syncthreads();
+    }
 
     // every thread of the block runs the same number of rounds (block and warp collectives)
     for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
@@ -685,7 +753,10 @@ __global__ void __launch_bounds__(128, Mode == kBndLeanFast ? 6 : (Mode != kBndG
 
         if (Lean) {
             sbb_t += sbb;
-            sph_acc_warp_reduce(d, acc);
+            acc_table_add(d, acc, sAcc);
+            __syncthreads();
+            acc_table_flush(d, sAcc);
+            __syncthreads();
             continue;
         }
         // ---- per-warp partial sums: interface part of the bubble volumes (1 - phi, FP64),
