@@ -93,7 +93,7 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, tmark, wl_link, wl_rare, sph_list, sph_cpl, sph_near, sph_nnear, mass, phi[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
+    size_t f[2], flags, mark, tmark, wl_link, wl_rare, sph_list, sph_cpl, sph_near, sph_nnear, mass, phi[2], rho[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
         adj_srho, adj_part, merge_keys, merge_list, lab, split_list, part_key, part_root, part_V, part_new, bub_cnt, total;
     size_t N, wl_cap, nbins_max;
 };
@@ -114,6 +114,8 @@ Layout layout_of(const lbm_params* p) {
     L.mass = take(4 * L.N);
     L.phi[0] = take(4 * L.N);
     L.phi[1] = take(4 * L.N);
+    L.rho[0] = p->max_spheres > 32 ? take(4 * L.N) : 0;   // (only the lean shell kernel reads them)
+    L.rho[1] = p->max_spheres > 32 ? take(4 * L.N) : 0;
     L.owner = take(4 * L.N);
     L.kappa = p->sigma > 0.0 ? take(4 * L.N) : 0;
     L.bub = take(sizeof(Bubble) * (size_t)p->max_bubbles);
@@ -343,6 +345,10 @@ int first_step(lbm_ctx* c) {
     d.mass = (float*)(a + L.mass);
     d.phi[0] = (float*)(a + L.phi[0]);
     d.phi[1] = (float*)(a + L.phi[1]);
+    // the densities are kept only where the lean shell kernel runs (it alone reads them)
+    const bool keep_rho = d.split_liq && p->max_spheres > 32;
+    d.rho[0] = keep_rho ? (float*)(a + L.rho[0]) : nullptr;
+    d.rho[1] = keep_rho ? (float*)(a + L.rho[1]) : nullptr;
     d.owner = (uint32_t*)(a + L.owner);
     d.kappa = p->sigma > 0.0 ? (float*)(a + L.kappa) : nullptr;
     d.bub = (Bubble*)(a + L.bub);
@@ -745,7 +751,10 @@ int lbm_import_state(lbm_ctx* c, const float* f) {
     int rc = adjoint_ready(c);
     if (rc) return rc;
     const size_t bytes = sizeof(float) * kQ * c->d.N;
-    return cuda_fail(cudaMemcpyAsync(c->d.f[c->cur], f, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    if ((rc = cuda_fail(cudaMemcpyAsync(c->d.f[c->cur], f, bytes, cudaMemcpyDeviceToDevice, c->stream)))) return rc;
+    if (!c->d.rho[0]) return LBM_OK;
+    launch_rho_of_grid(c->d, c->cur, c->stream);   // the densities of the imported PDFs
+    return launched(c, 1);
 }
 
 int lbm_set_params(lbm_ctx* c, double tau, const double g[3]) {

@@ -143,6 +143,7 @@ __device__ void conv_newif(const Dev& d, const int nxt, const uint32_t wid, cons
         const float rb = cnt ? rs / cnt : 1.f;
         const float ub[3] = {cnt ? ux / cnt : 0.f, cnt ? uy / cnt : 0.f, cnt ? uz / cnt : 0.f};
         if (lane < kQ) Store<S>::put(f, (size_t)lane * d.N + i, equilibrium_dev(lane, rb, ub));
+        if (lane == 0 && d.rho[nxt]) d.rho[nxt][i] = rb;
     }
 }
 

@@ -256,6 +256,9 @@ struct Dev {
     uint8_t* tmark;           // [N] cover / uncover marks (K_TOUCH, K_UNCOV), zero between steps
     float* mass;              // [N]
     float* phi[2];            // [N] fill level, double-buffered with the PDFs
+    float* rho[2];            // [N] density of the PDFs in grid g, as the collision (or the
+                              // initialisation) that wrote them formed it: the wall density of the
+                              // next step's bounce-back links without summing the cell's PDFs
     uint32_t* owner;          // [N] bubble id of gas/interface cells, sphere id of obstacle cells
     float* kappa;             // [N] curvature (sigma > 0 only)
     Bubble* bub;              // [max_bub]
@@ -561,7 +564,7 @@ inline void set_collision_consts(Dev& d) {
 // cu = c_q.u, cg = c_q.G, G = gw g, c+- = 1 + lambda_+-/2, c1 = 1 + (lambda_+ + lambda_-)/2,
 // c2 = (lambda_+ - lambda_-)/2: the same collision as f + lambda_+ (f+ - e+) + lambda_- (f- - e-)
 // + c+ G+ + c- G- written out per pair, with the grid-uniform factors computed on the host.
-__device__ __forceinline__ void trt_collide(const Dev& d, const float (&fin)[kQ], float gw, float (&out)[kQ]) {
+__device__ __forceinline__ float trt_collide(const Dev& d, const float (&fin)[kQ], float gw, float (&out)[kQ]) {
     const Dev::CollisionConsts& k = d.cc;
     float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
 #pragma unroll
@@ -593,16 +596,22 @@ __device__ __forceinline__ void trt_collide(const Dev& d, const float (&fin)[kQ]
         out[q] = fmaf(k.c1, fin[q], fmaf(k.c2, fin[qb], al + be));
         out[qb] = fmaf(k.c1, fin[qb], fmaf(k.c2, fin[q], al - be));
     }
+    return rho;
 }
 
-// the collision of one cell, its post-collision deviations stored to grid fb (CS: streaming stores)
+// the collision of one cell, its post-collision deviations stored to grid fb (CS: streaming
+// stores) and, with rhob, its density to rhob[i]
 template <int S, bool CS = false>
 __device__ __forceinline__ void collide_store(const Dev& d, typename Store<S>::T* __restrict__ fb, size_t i, const float (&fin)[kQ],
-                                              float gw = 1.f) {
+                                              float gw = 1.f, float* __restrict__ rhob = nullptr) {
     float out[kQ];
-    trt_collide(d, fin, gw, out);
+    const float rho = trt_collide(d, fin, gw, out);
 #pragma unroll
     for (int q = 0; q < kQ; q++) (CS ? Store<S>::put_cs : Store<S>::put)(fb, (size_t)q * d.N + i, out[q]);
+    if (rhob) {
+        if (CS) __stcs(rhob + i, rho);
+        else rhob[i] = rho;
+    }
 }
 
 // minimum-image difference a - b along axis k (beyond 4 periods, or not finite, the value is
@@ -817,6 +826,9 @@ void launch_bins_insert(const Dev& d, cudaStream_t s);
 int spheres_launches(const Dev& d);
 int spheres_links_launches(const Dev& d);
 void launch_init(const Dev& d, const double* bub_geom_dev, cudaStream_t s);
+// rho[g] = 1 + the sum of grid g's PDFs (deviations) of every active cell (after the PDFs of grid
+// g were written from outside the sweep)
+void launch_rho_of_grid(const Dev& d, int g, cudaStream_t s);
 void launch_bulk_all(const Dev& d, cudaStream_t s);
 void launch_fields(const Dev& d, int cur, float* rho, float* u, float* phi, uint8_t* flags, cudaStream_t s);
 void launch_export(const Dev& d, int cur, float* f, uint8_t* flags, float* m, float* phi, int32_t* owner, float* kappa, cudaStream_t s);

@@ -815,6 +815,7 @@ __device__ inline void cover_refill_dev(const Dev& d, const int nxt, const uint3
         const float rb = nfl ? rs / (float)nfl : 1.f;
         if (lane < kQ) Store<S>::put(f, (size_t)lane * d.N + i, equilibrium_dev(lane, rb, uf));
         if (lane != 0) continue;
+        if (d.rho[nxt]) d.rho[nxt][i] = rb;
         if (ngas > 0) {
             const float pb = ps / (float)nfl;
             d.flags[i] = F_IF;

@@ -391,6 +391,26 @@ __global__ void init_kernel(const Dev d, const double* geo) {
         d.phi[1][i] = ph;
         if (d.kappa) d.kappa[i] = 0.f;
         for (int q = 0; q < kQ; q++) Store<S>::put(f, (size_t)q * d.N + i, wgt(q) * (rho - 1.f));   // e(rho, 0) - w
+        if (d.rho[0]) d.rho[0][i] = rho;
+    }
+}
+
+template <int S>
+__global__ void rho_of_grid_kernel(const Dev d, const int g) {
+    using T = typename Store<S>::T;
+    const T* f = static_cast<const T*>(d.f[g]);
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
+        if (!(d.flags[i] & F_ACTIVE)) continue;
+        float dr = 0.f;
+        for (int q = 0; q < kQ; q++) dr += Store<S>::get_nc(f, (size_t)q * d.N + i);
+        d.rho[g][i] = 1.f + dr;
+    }
+}
+void launch_rho_of_grid(const Dev& d, int g, cudaStream_t s) {
+    switch (d.storage) {
+        case LBM_STORE_F32: rho_of_grid_kernel<LBM_STORE_F32><<<152 * 16, 256, 0, s>>>(d, g); break;
+        case LBM_STORE_F16DEV: rho_of_grid_kernel<LBM_STORE_F16DEV><<<152 * 16, 256, 0, s>>>(d, g); break;
+        default: rho_of_grid_kernel<LBM_STORE_BF16DEV><<<152 * 16, 256, 0, s>>>(d, g); break;
     }
 }
 

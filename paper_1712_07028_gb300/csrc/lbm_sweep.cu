@@ -340,10 +340,11 @@ __device__ __forceinline__ void bulk_load(const Dev& d, const typename Store<S>:
 // pull-stream and collide one BULK cell (x, y, z) = i
 template <int S>
 __device__ __forceinline__ void bulk_cell(const Dev& d, const typename Store<S>::T* __restrict__ fa,
-                                          typename Store<S>::T* __restrict__ fb, int x, int y, int z, uint32_t i) {
+                                          typename Store<S>::T* __restrict__ fb, int x, int y, int z, uint32_t i,
+                                          float* __restrict__ rhob) {
     float fin[kQ];
     bulk_load<S, true>(d, fa, x, y, z, i, fin);
-    collide_store<S, true>(d, fb, i, fin);
+    collide_store<S, true>(d, fb, i, fin, 1.f, rhob);
 }
 
 // every liquid cell whose neighbours all carry PDFs or lie beyond a wall; other active cells
@@ -372,8 +373,8 @@ __global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int 
     const bool bulk = (fl & F_ACTIVE) && (fl & F_BULK);
     const T* __restrict__ fa = static_cast<const T*>(d.f[cur]);
     T* __restrict__ fb = static_cast<T*>(d.f[cur ^ 1]);
-    if (!Whole) {
-        if (bulk) bulk_cell<S>(d, fa, fb, x, y, z, i);
+    if (!Whole) {   // (the densities are the forward step's: not written)
+        if (bulk) bulk_cell<S>(d, fa, fb, x, y, z, i, nullptr);
         return;
     }
     // (all 32 lanes reach the vote: blocks are whole warps and nothing returned before it)
@@ -385,7 +386,7 @@ __global__ void __launch_bounds__(128) sweep_bulk_kernel(const Dev d, const int 
 #pragma unroll
         for (int q = 0; q < kQ; q++) fin[q] = 0.f;
     }
-    collide_store<S, true>(d, fb, i, fin);
+    collide_store<S, true>(d, fb, i, fin, 1.f, d.rho[cur ^ 1]);
 }
 
 // the fix pass: the listed BULK cells again (or every BULK cell when the list overflowed),
@@ -403,7 +404,7 @@ __global__ void __launch_bounds__(128) sweep_fix_kernel(const Dev d, const int c
         if (!(fl & F_LIQ) || !(fl & F_BULK)) continue;
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        bulk_cell<S>(d, fa, fb, x, y, z, i);
+        bulk_cell<S>(d, fa, fb, x, y, z, i, d.rho[cur ^ 1]);
     }
 }
 
@@ -571,7 +572,7 @@ __device__ __forceinline__ void boundary_cell(const Dev& d, const typename Store
             wl_push(d.wl_conv, &d.sc->n_conv, (uint32_t)d.wl_cap, (uint32_t)i, &d.sc->status);
         }
     }
-    collide_store<S>(d, fb, i, fin, gw);
+    collide_store<S>(d, fb, i, fin, gw, d.rho[cur ^ 1]);
 }
 
 // ------------------------------------------------ link words of the liquid segment
@@ -633,10 +634,14 @@ void launch_link_classify(const Dev& d, cudaStream_t s) { link_classify_kernel<<
 
 // a liquid-segment cell whose obstacle links all go into its first sphere P0 (mask: bit q set
 // for a link from an obstacle cell), the others streaming or beyond a no-slip wall: the lean
-// instance of boundary_cell without any neighbour type or owner load, the same arithmetic
+// instance of boundary_cell without any neighbour type or owner load, the same arithmetic.  One
+// load per direction: the pulled PDF of a streaming link, the cell's own opposite PDF of a wall
+// or sphere link (bounce-back); the wall density (the cell's density of the last step) is the one
+// the collision that wrote the cell's PDFs stored in rhoa, not a sum of its 19 PDFs.
 template <int S>
 __device__ __forceinline__ void lean_cell(const Dev& d, const typename Store<S>::T* __restrict__ fa,
-                                          typename Store<S>::T* __restrict__ fb, const size_t i, const uint32_t mask,
+                                          typename Store<S>::T* __restrict__ fb, const float* __restrict__ rhoa,
+                                          float* __restrict__ rhob, const size_t i, const uint32_t mask,
                                           const uint32_t P0, SphAcc& acc, float& sbb) {
     const size_t N = d.N;
     int x, y, z;
@@ -648,27 +653,23 @@ __device__ __forceinline__ void lean_cell(const Dev& d, const typename Store<S>:
     const bool wxm = !d.bc[0] && x == 0, wxp = !d.bc[0] && x == d.nx - 1;
     const bool wym = !d.bc[1] && y == 0, wyp = !d.bc[1] && y == d.ny - 1;
     const bool wzm = !d.bc[2] && z == 0, wzp = !d.bc[2] && z == d.nz - 1;
-    float fo[kQ], fin[kQ];
+    float fin[kQ];
     uint32_t wl = 0u;   // bit q: the link comes from beyond a wall
+    fin[0] = Store<S>::get(fa, i);
 #pragma unroll
-    for (int q = 0; q < kQ; q++) fo[q] = Store<S>::get(fa, (size_t)q * N + i);
-    fin[0] = fo[0];
-#pragma unroll
-    for (int q = 1; q < kQ; q++) {   // the streaming links' pulled PDFs
+    for (int q = 1; q < kQ; q++) {
         const uint32_t sx = cx(q) == 1 ? xm : (cx(q) == -1 ? xp : (uint32_t)x);
         const uint32_t sy = cy(q) == 1 ? ym : (cy(q) == -1 ? yp : y0);
         const uint32_t sz = cz(q) == 1 ? zm : (cz(q) == -1 ? zp : z0);
         const bool wall = (cx(q) == 1 && wxm) || (cx(q) == -1 && wxp) || (cy(q) == 1 && wym) ||
                           (cy(q) == -1 && wyp) || (cz(q) == 1 && wzm) || (cz(q) == -1 && wzp);
         wl |= wall ? 1u << q : 0u;
-        fin[q] = (!wall && !(mask & (1u << q))) ? Store<S>::get(fa, (size_t)q * N + (sx + sy + sz)) : 0.f;
+        const bool bb = wall || (mask & (1u << q)) != 0u;   // bounce-back: the cell's own f*_qb
+        fin[q] = Store<S>::get(fa, (size_t)(bb ? opp(q) : q) * N + (bb ? (uint32_t)i : sx + sy + sz));
     }
-    float drho0 = 0.f;
-#pragma unroll
-    for (int q = 0; q < kQ; q++) drho0 += fo[q];
-    const float rho0 = 1.f + drho0;
-    float ucx = 0.f, ucy = 0.f, ucz = 0.f;
+    float ucx = 0.f, ucy = 0.f, ucz = 0.f, rho0 = 1.f;
     if (mask) {
+        rho0 = rhoa[i];
         // c_q . u_w at the link midpoint equals c_q . (u_P + w_P x r) at the cell centre
         sph_begin(d, acc, P0, x, y, z);
         ucx = acc.u[0] + acc.w[1] * acc.r[2] - acc.w[2] * acc.r[1];
@@ -677,20 +678,18 @@ __device__ __forceinline__ void lean_cell(const Dev& d, const typename Store<S>:
     }
 #pragma unroll
     for (int q = 1; q < kQ; q++) {
-        const int qb = opp(q);
-        if (wl & (1u << q)) {
-            fin[q] = fo[qb];                                        // no-slip wall
-        } else if (mask & (1u << q)) {                              // Eq. bbrule
+        if (!(wl & (1u << q)) && (mask & (1u << q))) {              // Eq. bbrule
+            const float fob = fin[q];                                // f*_qb of the cell
             const float corr = 6.f * wgt(q) * rho0 * cdot(q, ucx, ucy, ucz);
-            fin[q] = fo[qb] + corr;
+            fin[q] = fob + corr;
             // dj = -c_q (f*_qb + f_q(t+1)) = -c_q (2 w_q) - c_q (2 (f*_qb - w_q) + corr)
-            const float dev = 2.f * fo[qb] + corr;
+            const float dev = 2.f * fob + corr;
             acc.J[0] = cacc(-cx(q), acc.J[0], dev); acc.J[1] = cacc(-cy(q), acc.J[1], dev); acc.J[2] = cacc(-cz(q), acc.J[2], dev);
             acc.K[0] -= w72(q) * cx(q); acc.K[1] -= w72(q) * cy(q); acc.K[2] -= w72(q) * cz(q);
             sbb += corr;
         }
     }
-    collide_store<S>(d, fb, i, fin, 1.f);
+    collide_store<S>(d, fb, i, fin, 1.f, rhob);
 }
 
 // every other active cell: walls, sphere links, gas links, interface mass exchange.  Two
@@ -744,7 +743,8 @@ __global__ void __launch_bounds__(128, Mode == kBndLeanFast ? 6 : (Mode != kBndG
                 // a classified liquid cell with links into one sphere only: no neighbour loads
                 // (the others are the rare instance's)
                 const uint2 lk = d.wl_link[k];
-                if (!(lk.x & kLinkRare)) lean_cell<S>(d, fa, fb, list[(uint32_t)N - 1u - k], lk.x, lk.y, acc, sbb);
+                if (!(lk.x & kLinkRare))
+                    lean_cell<S>(d, fa, fb, d.rho[cur], d.rho[cur ^ 1], list[(uint32_t)N - 1u - k], lk.x, lk.y, acc, sbb);
             } else {
                 const size_t i = Mode == kBndRare ? d.wl_rare[k] : (Lean ? list[(uint32_t)N - 1u - k] : blist_cell(d, k, ngen));
                 boundary_cell<S, Lean>(d, fa, fb, phia, phib, cur, i, acc, sbb, vb, vphi, isIFc);
