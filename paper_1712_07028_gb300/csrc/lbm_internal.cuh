@@ -121,6 +121,16 @@ __host__ __device__ inline SphLink sph_link_of(const Sphere& s) {
     }
     return l;
 }
+// the cells a moved sphere may have covered or uncovered: its box (the union of the old and new
+// centres' boxes, a cell of margin), the offsets of the box's first cell from both centres in
+// FP32, R^2, and the new centre relative to the old in FP64 for the decisions near the surface
+struct TouchBox {
+    int lo[3], ext[3];
+    float a0[3], a1[3];
+    float r2f;
+    int go;   // the sphere moved (and its box is sound)
+    double off[3];
+};
 struct SphereAcc {       // per-step momentum-exchange accumulators (zeroed by the sphere update)
     double J[3];         // sum of the deviation part of dj
     double TJ[3];        // sum of (x - x_P) x (deviation part of dj)
@@ -287,6 +297,7 @@ struct Dev {
     uint32_t* sph_list;       // [max_sph] the spheres with partners this step (n_paired of them)
     uint32_t* sph_cpl;        // [max_sph] the spheres with a partner within lubrication reach (n_coupled)
     uint32_t* sph_near;       // [max_sph][kNearCap] those partners of each listed sphere (sph_nnear of them)
+    struct TouchBox* tbox;    // [max_sph] each moved sphere's box for the touch kernel
     uint32_t* sph_nnear;      // [max_sph]
     uint32_t* pairs;          // [max_sph][kPairCap]
     unsigned long long* merge_keys;   // [kMergeCap] pairs (lo + 1) << 32 | hi of touching roots, 0 = free

@@ -597,69 +597,73 @@ __global__ void sph_copy_kernel(const Dev d) {
 }
 
 // ---------------------------------------------------------------- cover / uncover
-// One warp per sphere: cells of the union of its old and new boxes whose coverage by this
-// sphere changed are touched (deduplicated into a worklist).
 constexpr int kTouchWarps = 4;   // spheres per block of the touch kernel
-__device__ inline void cover_touch_one(const Dev& d, const int P, const int lane) {
-    // the box and the cell offsets from both centres, set up by one lane (FP64 issue is scarce
-    // on this GPU: every lane doing it cost more than the box scan) and shared through the
-    // warp's slots of shared memory.  FP64 only splits each centre into an integer cell and an
-    // FP32 fraction (as the sweep's link data does); the box bounds and offsets follow in
-    // integer and FP32 arithmetic (the box has a cell of margin on every side, far beyond their
-    // rounding), and FP64 decides again only the cells whose FP32 distance is near R.
-    __shared__ int sGo[kTouchWarps], sLo[kTouchWarps][3], sExt[kTouchWarps][3];
-    __shared__ float sA0[kTouchWarps][3], sA1[kTouchWarps][3], sR2f[kTouchWarps];
-    __shared__ double sOff[kTouchWarps][3];
-    const int wb = threadIdx.x >> 5;
+// Each moved sphere's box and offsets, one thread per sphere (its FP64 work then fills every
+// lane of a warp, where the touch kernel's warp per sphere would issue it for one lane): FP64
+// only splits each centre into an integer cell and an FP32 fraction (as the sweep's link data
+// does); the box bounds and offsets follow in integer and FP32 arithmetic (the box has a cell of
+// margin on every side, far beyond their rounding).  Also the next sweep's link data.
+__device__ void touch_box_prep(const Dev& d, const int P) {
     const Sphere& s = d.sph[P];
     const int L[3] = {d.nx, d.ny, d.nz};
-    if (lane == 0) {
-        const SphLink ln = sph_link_of(s);
-        d.sphl[P] = ln;   // the next sweep's link data
-        int go = 0;
-        if (s.x[0] != s.x0[0] || s.x[1] != s.x0[1] || s.x[2] != s.x0[2]) {
-            // a sphere whose centre is not finite or moved more than a cell in one step is left
-            // alone (the fluid has gone unstable; the status word says so)
-            if (!finite3(s.x) || !finite3(s.x0) || !(s.R > 0.0 && s.R < 64.0)) {
-                atomicOr(&d.sc->status, S_UNSTABLE);
-            } else {
-                const float Rf = (float)s.R;
-                const int lim = 2 * (int)ceilf(Rf) + 8;
-                go = 1;
-                for (int k = 0; k < 3; k++) {
-                    const double f0 = floor(s.x0[k]);
-                    const int i0 = (int)f0;
-                    const float x0f = (float)(s.x0[k] - f0);   // old centre = i0 + x0f
-                    int di = ln.xi[k] - i0;                     // new centre - old: di + (xf - x0f), minimum image
-                    if (d.bc[k]) {
-                        if (2 * di > L[k]) di -= L[k];
-                        else if (2 * di < -L[k]) di += L[k];
-                    }
-                    const float off = (float)di + (ln.xf[k] - x0f);
-                    const int lo = i0 + (int)floorf(fminf(x0f, x0f + off) - Rf) - 1;
-                    const int hi = i0 + (int)ceilf(fmaxf(x0f, x0f + off) + Rf) + 1;
-                    sLo[wb][k] = lo;
-                    sExt[wb][k] = hi - lo + 1;
-                    if (hi - lo + 1 > lim) go = 0;
-                    sA0[wb][k] = (float)(lo - i0) - x0f;        // cell lo minus the old centre
-                    sA1[wb][k] = sA0[wb][k] - off;              // ... minus the new centre
-                    sOff[wb][k] = min_image(d, k, s.x[k], s.x0[k]);   // for the FP64 decisions
+    const SphLink ln = sph_link_of(s);
+    d.sphl[P] = ln;   // the next sweep's link data
+    TouchBox b;
+    b.go = 0;
+    if (s.x[0] != s.x0[0] || s.x[1] != s.x0[1] || s.x[2] != s.x0[2]) {
+        // a sphere whose centre is not finite or moved more than a cell in one step is left
+        // alone (the fluid has gone unstable; the status word says so)
+        if (!finite3(s.x) || !finite3(s.x0) || !(s.R > 0.0 && s.R < 64.0)) {
+            atomicOr(&d.sc->status, S_UNSTABLE);
+        } else {
+            const float Rf = (float)s.R;
+            const int lim = 2 * (int)ceilf(Rf) + 8;
+            b.go = 1;
+            for (int k = 0; k < 3; k++) {
+                const double f0 = floor(s.x0[k]);
+                const int i0 = (int)f0;
+                const float x0f = (float)(s.x0[k] - f0);   // old centre = i0 + x0f
+                int di = ln.xi[k] - i0;                     // new centre - old: di + (xf - x0f), minimum image
+                if (d.bc[k]) {
+                    if (2 * di > L[k]) di -= L[k];
+                    else if (2 * di < -L[k]) di += L[k];
                 }
-                if (!go) atomicOr(&d.sc->status, S_UNSTABLE);
-                sR2f[wb] = (float)(s.R * s.R);
+                const float off = (float)di + (ln.xf[k] - x0f);
+                const int lo = i0 + (int)floorf(fminf(x0f, x0f + off) - Rf) - 1;
+                const int hi = i0 + (int)ceilf(fmaxf(x0f, x0f + off) + Rf) + 1;
+                b.lo[k] = lo;
+                b.ext[k] = hi - lo + 1;
+                if (hi - lo + 1 > lim) b.go = 0;
+                b.a0[k] = (float)(lo - i0) - x0f;   // cell lo minus the old centre
+                b.a1[k] = b.a0[k] - off;            // ... minus the new centre
+                b.off[k] = min_image(d, k, s.x[k], s.x0[k]);   // for the FP64 decisions
             }
+            if (!b.go) atomicOr(&d.sc->status, S_UNSTABLE);
+            b.r2f = (float)(s.R * s.R);
         }
-        sGo[wb] = go;
     }
-    __syncwarp();
-    if (!sGo[wb]) return;   // (uniform over the warp)
-    const int lo[3] = {sLo[wb][0], sLo[wb][1], sLo[wb][2]}, ext[3] = {sExt[wb][0], sExt[wb][1], sExt[wb][2]};
-    const float a0[3] = {sA0[wb][0], sA0[wb][1], sA0[wb][2]}, a1[3] = {sA1[wb][0], sA1[wb][1], sA1[wb][2]};
+    d.tbox[P] = b;
+}
+__global__ void cover_touch_prep_kernel(const Dev d) {
+    const int P = blockIdx.x * blockDim.x + threadIdx.x;
+    if (P < d.nsph) touch_box_prep(d, P);
+}
+
+// One warp per sphere: the cells of its box whose coverage by this sphere changed are touched
+// (deduplicated into a worklist).
+__device__ inline void cover_touch_one(const Dev& d, const int P, const int lane) {
+    const TouchBox& bx = d.tbox[P];
+    const Sphere& s = d.sph[P];
+    const int L[3] = {d.nx, d.ny, d.nz};
+    if (!bx.go) return;   // (uniform over the warp)
+    const double sOffk[3] = {bx.off[0], bx.off[1], bx.off[2]};
+    const int lo[3] = {bx.lo[0], bx.lo[1], bx.lo[2]}, ext[3] = {bx.ext[0], bx.ext[1], bx.ext[2]};
+    const float a0[3] = {bx.a0[0], bx.a0[1], bx.a0[2]}, a1[3] = {bx.a1[0], bx.a1[1], bx.a1[2]};
     // cell offsets from both centres in FP32 decide wherever |d^2 - R^2| clears their rounding
     // error by far; the few cells closer to the sphere's surface are decided in FP64.  The FP32
     // offsets carry an error under 1e-6 (an exact integer difference less an FP32 fraction), so
     // squared distances near R^2 one of at most a few 1e-6 (1 + R^2): the band is 2e-5 (1 + R^2)
-    const float R2f = sR2f[wb], band = 2e-5f * (1.f + R2f);
+    const float R2f = bx.r2f, band = 2e-5f * (1.f + R2f);
     // each lane takes columns (x, y) of the box and walks them along z
     const int nxy = ext[0] * ext[1];
     for (int exy = lane; exy < nxy; exy += 32) {
@@ -676,7 +680,7 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
                 const double R2 = s.R * s.R;
                 double d0 = 0, d1 = 0;
                 for (int k = 0; k < 3; k++) {
-                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + sOff[wb][k]);
+                    const double a = (double)w[k] - s.x0[k], b = (double)w[k] - (s.x0[k] + sOffk[k]);
                     d0 += a * a;
                     d1 += b * b;
                 }
@@ -699,9 +703,17 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
     }
 }
 
+// Prepared: the boxes were set up by cover_touch_prep_kernel; else lane 0 sets its sphere's up
+// (few spheres: one launch less on the step's critical path)
+template <bool Prepared>
 __global__ void __launch_bounds__(32 * kTouchWarps) cover_touch_kernel(const Dev d) {
     const int P = blockIdx.x * kTouchWarps + (threadIdx.x >> 5);
-    if (P < d.nsph) cover_touch_one(d, P, threadIdx.x & 31);
+    if (P >= d.nsph) return;   // (uniform over the warp)
+    if (!Prepared) {
+        if ((threadIdx.x & 31) == 0) touch_box_prep(d, P);
+        __syncwarp();
+    }
+    cover_touch_one(d, P, threadIdx.x & 31);
 }
 
 // touched cells: the lowest id of the spheres covering them now decides; obstacle cells no
@@ -889,7 +901,8 @@ int spheres_launches(const Dev& d) {   // launch_spheres_move + launch_spheres_c
     int n;
     if (d.sphere_mode == LBM_SPHERES_FREE) n = d.nsph <= 1024 ? 1 : 1 + d.n_sub + (d.n_sub & 1);
     else n = 1 + (d.sphere_mode == LBM_SPHERES_PRESCRIBED ? 1 : 0);
-    if (d.sphere_mode != LBM_SPHERES_FIXED) n += 2;   // touch, cover cluster
+    // touch preparation (more than 1024 spheres), touch, cover cluster
+    if (d.sphere_mode != LBM_SPHERES_FIXED) n += d.nsph > 1024 ? 3 : 2;
     return n;
 }
 
@@ -903,9 +916,16 @@ void prepare_sphere_kernels() {
 // leave alone, so it may run concurrently with them
 // the cells whose coverage the move changes (reads only the sphere table; its marks have an
 // array of their own, so it may run while the conversions do)
+// (with more than 1024 spheres the boxes are set up by a kernel of their own)
 void launch_cover_touch(const Dev& d, cudaStream_t st) {
-    if (d.sphere_mode != LBM_SPHERES_FIXED)
-        cover_touch_kernel<<<(d.nsph + kTouchWarps - 1) / kTouchWarps, 32 * kTouchWarps, 0, st>>>(d);
+    if (d.sphere_mode == LBM_SPHERES_FIXED) return;
+    const int nb = (d.nsph + kTouchWarps - 1) / kTouchWarps;
+    if (d.nsph > 1024) {
+        cover_touch_prep_kernel<<<(d.nsph + 127) / 128, 128, 0, st>>>(d);
+        cover_touch_kernel<true><<<nb, 32 * kTouchWarps, 0, st>>>(d);
+    } else {
+        cover_touch_kernel<false><<<nb, 32 * kTouchWarps, 0, st>>>(d);
+    }
 }
 
 // partner lists and the links between obstacle nodes of two spheres: they read only the
