@@ -93,7 +93,7 @@ int check_params(const lbm_params* p) {
 size_t pdf_bytes(const lbm_params* p) { return p->storage == LBM_STORE_F32 ? 4 : 2; }
 
 struct Layout {
-    size_t f[2], flags, mark, tmark, wl_link, wl_rare, sph_list, sph_cpl, sph_near, sph_nnear, tbox, mass, phi[2], rho[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
+    size_t f[2], flags, mark, tmark, wl_link, wl_rare, sph_list, sph_cpl, sph_near, sph_nnear, tbox, sph_bin, mass, phi[2], rho[2], owner, kappa, bub, sph, sph_tmp, sphl, gasflag, acc, sc, wl[4], wl_slow, wl_fix, bin_cnt, bin_ids, npairs, pairs, geo,
         adj_srho, adj_part, merge_keys, merge_list, lab, split_list, part_key, part_root, part_V, part_new, bub_cnt, total;
     size_t N, wl_cap, nbins_max;
 };
@@ -139,6 +139,7 @@ Layout layout_of(const lbm_params* p) {
     L.sph_near = take(4 * (size_t)kNearCap * (size_t)p->max_spheres);
     L.sph_nnear = take(4 * (size_t)p->max_spheres);
     L.tbox = take(sizeof(TouchBox) * (size_t)p->max_spheres);
+    L.sph_bin = take(sizeof(int4) * (size_t)p->max_spheres);
     L.pairs = take(4 * (size_t)p->max_spheres * kPairCap);
     L.geo = take(sizeof(double) * 4 * (size_t)p->max_bubbles);
     L.adj_srho = take(4 * L.N);
@@ -383,6 +384,7 @@ int first_step(lbm_ctx* c) {
     d.sph_near = (uint32_t*)(a + L.sph_near);
     d.sph_nnear = (uint32_t*)(a + L.sph_nnear);
     d.tbox = (TouchBox*)(a + L.tbox);
+    d.sph_bin = (int4*)(a + L.sph_bin);
     d.pairs = (uint32_t*)(a + L.pairs);
     d.merge_keys = (unsigned long long*)(a + L.merge_keys);
     d.merge_list = (uint32_t*)(a + L.merge_list);

@@ -298,6 +298,7 @@ struct Dev {
     uint32_t* sph_cpl;        // [max_sph] the spheres with a partner within lubrication reach (n_coupled)
     uint32_t* sph_near;       // [max_sph][kNearCap] those partners of each listed sphere (sph_nnear of them)
     struct TouchBox* tbox;    // [max_sph] each moved sphere's box for the touch kernel
+    int4* sph_bin;            // [max_sph] bin of each sphere's centre (kept with more than 1024 spheres)
     uint32_t* sph_nnear;      // [max_sph]
     uint32_t* pairs;          // [max_sph][kPairCap]
     unsigned long long* merge_keys;   // [kMergeCap] pairs (lo + 1) << 32 | hi of touching roots, 0 = free
@@ -808,7 +809,10 @@ __device__ inline void step_close(const Dev& d, const uint32_t t, const uint32_t
     if (bin_spheres)
         for (uint32_t P = t; P < (uint32_t)d.nsph; P += nt) {
             const Sphere& sp = d.sph[P];
-            const size_t bi = bin_index(d, bin_coord(d, 0, sp.x[0]), bin_coord(d, 1, sp.x[1]), bin_coord(d, 2, sp.x[2]));
+            // (with more than 1024 spheres the touch preparation has found the bins)
+            const int4 bb = d.nsph > 1024 ? d.sph_bin[P]
+                                          : make_int4(bin_coord(d, 0, sp.x[0]), bin_coord(d, 1, sp.x[1]), bin_coord(d, 2, sp.x[2]), 0);
+            const size_t bi = bin_index(d, bb.x, bb.y, bb.z);
             const uint32_t slot = atomicAdd(&d.bin_cnt[bi], 1u);
             if (slot < (uint32_t)d.bin_cap) d.bin_ids[bi * d.bin_cap + slot] = P;
             else atomicOr(&d.sc->status, S_BIN_OVERFLOW);

@@ -15,7 +15,9 @@ __global__ void bins_insert_kernel(const Dev d) {
     if (P >= d.nsph) return;
     const Sphere& s = d.sph[P];
     d.gasflag[P] = d.gasflag[d.max_sph + P] = 1u;   // the first gas-pressure pass scans every sphere
-    const size_t bi = bin_index(d, bin_coord(d, 0, s.x0[0]), bin_coord(d, 1, s.x0[1]), bin_coord(d, 2, s.x0[2]));
+    const int4 bb = make_int4(bin_coord(d, 0, s.x0[0]), bin_coord(d, 1, s.x0[1]), bin_coord(d, 2, s.x0[2]), 0);
+    d.sph_bin[P] = bb;
+    const size_t bi = bin_index(d, bb.x, bb.y, bb.z);
     const uint32_t slot = atomicAdd(&d.bin_cnt[bi], 1u);
     if (slot < (uint32_t)d.bin_cap) d.bin_ids[bi * d.bin_cap + slot] = (uint32_t)P;
     else atomicOr(&d.sc->status, S_BIN_OVERFLOW);
@@ -288,9 +290,12 @@ __device__ inline void sph_pairs_one(const Dev& d, const uint32_t P, const int l
     if (lane == 0) d.npairs[P] = 0;
     __syncwarp();
     int sx[3], sy[3], sz[3];
-    const int nx_ = bin_span(d, 0, bin_coord(d, 0, s.x[0]), sx);
-    const int ny_ = bin_span(d, 1, bin_coord(d, 1, s.x[1]), sy);
-    const int nz_ = bin_span(d, 2, bin_coord(d, 2, s.x[2]), sz);
+    // (with more than 1024 spheres the touch preparation has found the sphere's bin)
+    const int4 bb = d.nsph > 1024 ? d.sph_bin[P]
+                                  : make_int4(bin_coord(d, 0, s.x[0]), bin_coord(d, 1, s.x[1]), bin_coord(d, 2, s.x[2]), 0);
+    const int nx_ = bin_span(d, 0, bb.x, sx);
+    const int ny_ = bin_span(d, 1, bb.y, sy);
+    const int nz_ = bin_span(d, 2, bb.z, sz);
     if (lane < nx_ * ny_ * nz_ && finite3(s.x)) {
         const size_t bi = bin_index(d, sx[lane % nx_], sy[(lane / nx_) % ny_], sz[lane / (nx_ * ny_)]);
         uint32_t cnt = d.bin_cnt[bi];
@@ -608,6 +613,7 @@ __device__ void touch_box_prep(const Dev& d, const int P) {
     const int L[3] = {d.nx, d.ny, d.nz};
     const SphLink ln = sph_link_of(s);
     d.sphl[P] = ln;   // the next sweep's link data
+    d.sph_bin[P] = make_int4(bin_coord(d, 0, s.x[0]), bin_coord(d, 1, s.x[1]), bin_coord(d, 2, s.x[2]), 0);
     TouchBox b;
     b.go = 0;
     if (s.x[0] != s.x0[0] || s.x[1] != s.x0[1] || s.x[2] != s.x0[2]) {
@@ -865,12 +871,11 @@ __device__ inline void cover_finish_dev(const Dev& d, const uint32_t wid, const 
     }
 }
 
-// the bins of the step-start centres are emptied (the end-of-step scan bins the new ones)
+// the bins are emptied (the end-of-step scan bins the new centres): every bin that holds a
+// sphere holds a step-start centre, so clearing them all is clearing those
 __device__ inline void bins_clear(const Dev& d, const uint32_t t, const uint32_t nt) {
-    for (uint32_t P = t; P < (uint32_t)d.nsph; P += nt) {
-        const Sphere& sp = d.sph[P];
-        d.bin_cnt[bin_index(d, bin_coord(d, 0, sp.x0[0]), bin_coord(d, 1, sp.x0[1]), bin_coord(d, 2, sp.x0[2]))] = 0;
-    }
+    const size_t nb = (size_t)d.nbx * (size_t)d.nby * (size_t)d.nbz;
+    for (size_t b = t; b < nb; b += nt) d.bin_cnt[b] = 0u;
 }
 
 // apply, refill and finish in one launch: one thread-block cluster, the phases separated by
