@@ -159,6 +159,14 @@ int lbm_add_bubble(lbm_ctx* ctx, const double c[3], double r, int* id);
 int lbm_add_sphere(lbm_ctx* ctx, const double c[3], double r, double rho_p, const double u[3],
                    const double w[3], int* id);
 
+/* The same for n spheres at once, from host arrays: centres c[n][3], radii r[n], densities
+ * rho_p[n], velocities u[n][3] and angular velocities w[n][3] (u, w may be NULL: at rest).
+ * They get ids first_id .. first_id + n - 1 (*first_id, host, may be NULL).  Every sphere is
+ * checked before any is added: LBM_EINVAL (nothing added) if one has r <= 0 or rho_p <= 0 or
+ * they do not fit the table (max_spheres); LBM_ESTATE after the first lbm_step. */
+int lbm_add_spheres(lbm_ctx* ctx, int n, const double* c, const double* r, const double* rho_p, const double* u,
+                    const double* w, int* first_id);
+
 /* Advance nsteps >= 0 time steps.  The first call initialises the fields on the device
  * (liquid at rest, bubbles, layer closure, spheres).  Asynchronous: problems found on the
  * device are latched in the status word and reported by lbm_status / lbm_forces.

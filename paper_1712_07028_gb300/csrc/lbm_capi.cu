@@ -569,6 +569,21 @@ int lbm_add_sphere(lbm_ctx* c, const double cen[3], double r, double rho_p, cons
     return LBM_OK;
 }
 
+int lbm_add_spheres(lbm_ctx* c, int n, const double* cen, const double* r, const double* rho_p, const double* u,
+                    const double* w, int* first_id) {
+    if (!c || n < 0 || (n > 0 && (!cen || !r || !rho_p))) return LBM_EINVAL;
+    if (c->started) return LBM_ESTATE;
+    if ((long long)c->sph_init.size() + n > (long long)c->p.max_spheres) return LBM_EINVAL;
+    for (int a = 0; a < n; a++)
+        if (!(r[a] > 0.0) || !(rho_p[a] > 0.0)) return LBM_EINVAL;
+    if (first_id) *first_id = (int)c->sph_init.size();
+    for (int a = 0; a < n; a++) {
+        const int rc = lbm_add_sphere(c, cen + 3 * a, r[a], rho_p[a], u ? u + 3 * a : nullptr, w ? w + 3 * a : nullptr, nullptr);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
 int lbm_step(lbm_ctx* c, int nsteps) {
     if (!c || nsteps < 0) return LBM_EINVAL;
     int rc;

@@ -21,7 +21,7 @@ CELL_LIQUID, CELL_INTERFACE, CELL_GAS, CELL_OBSTACLE = 1, 2, 4, 8
 S_UNSTABLE, S_OVERFLOW, S_BUBBLE_GONE, S_BIN_OVERFLOW, S_FAST_SPHERE, S_MERGE, S_SPLIT = 1, 2, 4, 8, 32, 64, 128
 
 # every entry point include/lbm.h declares
-EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_step",
+EXPORTS = ("lbm_arena_bytes", "lbm_init", "lbm_set_stream", "lbm_add_bubble", "lbm_add_sphere", "lbm_add_spheres", "lbm_step",
            "lbm_forces", "lbm_spheres", "lbm_lubrication", "lbm_bubbles", "lbm_bubble_roots", "lbm_bubble_splits", "lbm_fields", "lbm_export_state", "lbm_mass_budget",
            "lbm_status", "lbm_profile", "lbm_profile_read", "lbm_copy_bytes", "lbm_launch_count",
            "lbm_bubble_volumes_noalloc", "lbm_set_params", "lbm_import_state", "lbm_objective", "lbm_objective_read",
@@ -63,6 +63,7 @@ def load():
     L.lbm_set_stream.argtypes = [vp, vp]
     L.lbm_add_bubble.argtypes = [vp, pd, d, ctypes.POINTER(i32)]
     L.lbm_add_sphere.argtypes = [vp, pd, d, d, pd, pd, ctypes.POINTER(i32)]
+    L.lbm_add_spheres.argtypes = [vp, i32, vp, vp, vp, vp, vp, ctypes.POINTER(i32)]
     L.lbm_step.argtypes = [vp, i32]
     L.lbm_forces.argtypes = [vp, pd, pd, i32]
     L.lbm_spheres.argtypes = [vp, pd, pd, pd, i32]
@@ -146,9 +147,15 @@ class Sim:
         self.N = wl.nx * wl.ny * wl.nz
         for b in wl.bubbles:
             _check("lbm_add_bubble", L.lbm_add_bubble(self.ctx, _dp(_v3(b.c)), float(b.r), None))
-        for s in wl.spheres:
-            _check("lbm_add_sphere", L.lbm_add_sphere(self.ctx, _dp(_v3(s.x)), float(s.r), float(s.rho), _dp(_v3(s.u)),
-                                                      _dp(_v3(s.w)), None))
+        if wl.spheres:   # one call for the whole table
+            sp = wl.spheres
+            x = np.ascontiguousarray([s.x for s in sp], dtype=np.float64)
+            r = np.ascontiguousarray([s.r for s in sp], dtype=np.float64)
+            rho = np.ascontiguousarray([s.rho for s in sp], dtype=np.float64)
+            u = np.ascontiguousarray([s.u for s in sp], dtype=np.float64)
+            w = np.ascontiguousarray([s.w for s in sp], dtype=np.float64)
+            _check("lbm_add_spheres", L.lbm_add_spheres(self.ctx, len(sp), *[ctypes.c_void_p(a.ctypes.data) for a in (x, r, rho, u, w)],
+                                                        None))
         self.nsph = len(wl.spheres)
         # bubble ids: the bubbles given, or with splitting every row of the table
         self.nbub = int(self.params.max_bubbles) if wl.split_every > 0 else len(wl.bubbles)

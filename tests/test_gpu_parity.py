@@ -279,6 +279,82 @@ def test_abi_argument_errors(lbm):
     assert L.lbm_step(sim.ctx, -1) == lbm.LBM_EINVAL
 
 
+def _ctx_one_by_one(lbm, wl):
+    """a context built through the ABI with one lbm_add_sphere call per sphere (Sim uses the batch
+    call); returns (ctx, arena) on the current stream"""
+    import torch
+    L = lbm.load()
+    p = lbm.make_params(wl)
+    nbytes = ctypes.c_size_t()
+    assert L.lbm_arena_bytes(ctypes.byref(p), ctypes.byref(nbytes)) == 0
+    arena = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+    ctx = ctypes.c_void_p()
+    stream = torch.cuda.current_stream().cuda_stream
+    assert L.lbm_init(ctypes.byref(p), ctypes.c_void_p(arena.data_ptr()), nbytes.value, ctypes.c_void_p(stream), ctypes.byref(ctx)) == 0
+    dp = lambda v: np.ascontiguousarray(v, dtype=np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    for b in wl.bubbles:
+        c = np.array(b.c, dtype=np.float64)
+        assert L.lbm_add_bubble(ctx, c.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(b.r), None) == 0
+    for k, s in enumerate(wl.spheres):
+        x, u, w = (np.array(v, dtype=np.float64) for v in (s.x, s.u, s.w))
+        i = ctypes.c_int(-1)
+        assert L.lbm_add_sphere(ctx, x.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(s.r), float(s.rho),
+                                u.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(i)) == 0
+        assert i.value == k
+    return ctx, arena
+
+
+def test_add_spheres_batch_matches_one_by_one(lbm):
+    """lbm_add_spheres (the binding's path) adds the table lbm_add_sphere adds sphere by sphere:
+    the two contexts step alike (to round-off: the sphere sums are FP64 atomics, whose order
+    varies from run to run); a batch with one bad sphere adds none of them, and a batch after the
+    first step is refused"""
+    import torch
+    L = lbm.load()
+    wl = _sphere_bed(60)
+    a = lbm.Sim(wl)
+    ctx, arena = _ctx_one_by_one(lbm, wl)
+    a.step(5)
+    assert L.lbm_step(ctx, 5) == 0
+    n = len(wl.spheres)
+    xa, xb = np.zeros((n, 3)), np.zeros((n, 3))
+    pd = ctypes.POINTER(ctypes.c_double)
+    for ctx_, x in ((a.ctx, xa), (ctx, xb)):
+        assert L.lbm_spheres(ctx_, x.ctypes.data_as(pd), None, None, n) == 0
+    torch.cuda.synchronize()
+    assert np.abs(xa - xb).max() <= 1e-12
+    fa = torch.empty((19,) + a.shape, dtype=torch.float32, device="cuda")
+    fb = torch.empty_like(fa)
+    assert L.lbm_export_state(a.ctx, ctypes.c_void_p(fa.data_ptr()), None, None, None, None, None) == 0
+    assert L.lbm_export_state(ctx, ctypes.c_void_p(fb.data_ptr()), None, None, None, None, None) == 0
+    torch.cuda.synchronize()
+    assert (fa - fb).abs().max().item() <= 1e-6
+    # a refused batch adds nothing; after the first step every batch is refused
+    wl2 = _sphere_bed(0)
+    p = lbm.make_params(wl2, max_spheres=8)
+    nbytes = ctypes.c_size_t()
+    assert L.lbm_arena_bytes(ctypes.byref(p), ctypes.byref(nbytes)) == 0
+    arena2 = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+    ctx2 = ctypes.c_void_p()
+    assert L.lbm_init(ctypes.byref(p), ctypes.c_void_p(arena2.data_ptr()), nbytes.value,
+                      ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(ctx2)) == 0
+    c = np.array([[20.0, 20.0, 20.0], [40.0, 40.0, 40.0]])
+    r, rho = np.array([4.0, -1.0]), np.array([1.5, 1.5])
+    vp = lambda v: ctypes.c_void_p(v.ctypes.data)
+    first = ctypes.c_int(-1)
+    assert L.lbm_add_spheres(ctx2, 2, vp(c), vp(r), vp(rho), None, None, ctypes.byref(first)) == lbm.LBM_EINVAL
+    r[1] = 4.0
+    assert L.lbm_add_spheres(ctx2, 9, vp(np.zeros((9, 3))), vp(np.full(9, 4.0)), vp(np.full(9, 1.5)), None, None, None) == lbm.LBM_EINVAL
+    assert L.lbm_add_spheres(ctx2, 2, vp(c), vp(r), vp(rho), None, None, ctypes.byref(first)) == 0
+    assert first.value == 0
+    assert L.lbm_step(ctx2, 1) == 0
+    assert L.lbm_add_spheres(ctx2, 1, vp(c), vp(r), vp(rho), None, None, None) == lbm.LBM_ESTATE
+    for x in (ctx, ctx2):
+        L.lbm_destroy(x)
+    torch.cuda.synchronize()
+
+
 def test_launch_count(lbm):
     wl = W.column_c0()
     sim = lbm.Sim(wl)
