@@ -316,6 +316,8 @@ int first_step(lbm_ctx* c) {
     d.n_sub = p->n_substeps;
     d.sphere_mode = p->sphere_mode;
     d.ngeo = (int)(c->bub_geo.size() / 4);
+    d.geo_rmax = 0.0;
+    for (int b = 0; b < d.ngeo; b++) d.geo_rmax = std::max(d.geo_rmax, c->bub_geo[4 * b + 3]);
     d.split_every = p->split_every;
     // with splitting, new bubbles take free rows: every row of the table is a bubble id
     d.nbub = p->split_every > 0 ? std::max(p->max_bubbles, d.ngeo) : d.ngeo;

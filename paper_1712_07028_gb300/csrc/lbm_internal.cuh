@@ -223,6 +223,7 @@ struct Dev {
     uint8_t face[6];          // faces -x, +x, -y, +y, -z, +z of non-periodic axes: FACE_*
     int special;              // some face is free-slip or open
     int split_liq;            // the liquid boundary segment has its own (lean) sweep kernel
+    double geo_rmax;          // the largest radius among them
     int ngeo;                 // bubbles given at the start (their geometry); nbub is the table's
                               // size when bubbles split, else ngeo
     int split_every;          // > 0: bubbles split into their connected parts every so many steps

@@ -327,10 +327,33 @@ void launch_curvature(const Dev& d, int nxt, cudaStream_t s) {
 // phi = prod_b clamp(|x - c_b| - (r_b - 1/2), 0, 1); gas / liquid / interface; liquid cells
 // with a gas neighbour become interface cells (phi = 1) with that gas cell's bubble; f* =
 // e(1,0), m = phi; then cells covered by a sphere (lowest id) become obstacle cells.
-__device__ void bubble_fill(const Dev& d, const double* geo, int x, int y, int z, float& ph, uint32_t& own) {
+// With g32 (the bubbles' centres and r - 1/2 in FP32, where no bubble nears half a periodic
+// period), a bubble whose FP32 distance clears the blend shell c in [0, 1] by a margin of 1e-3
+// (four times the FP32 error of coordinates up to 4096) contributes its clamped factor, 1 or 0,
+// without FP64;
+// FP64 decides the cells near the shell, so the result is the FP64 formula's.  *minc (if given)
+// receives the smallest FP32 c over the bubbles.
+__device__ void bubble_fill(const Dev& d, const double* geo, const float4* g32, int x, int y, int z, float& ph,
+                            uint32_t& own, float* minc = nullptr) {
     double v = 1.0;
     own = kNone;
+    float mc = 3.0e38f;
     for (int b = 0; b < d.ngeo; b++) {
+        if (g32) {
+            const float4 gb = g32[b];
+            float dx = (float)x - gb.x, dy = (float)y - gb.y, dz = (float)z - gb.z;
+            if (d.bc[0]) dx -= (float)d.nx * rintf(dx / (float)d.nx);
+            if (d.bc[1]) dy -= (float)d.ny * rintf(dy / (float)d.ny);
+            if (d.bc[2]) dz -= (float)d.nz * rintf(dz / (float)d.nz);
+            const float c32 = sqrtf(dx * dx + dy * dy + dz * dz) - gb.w;
+            mc = fminf(mc, c32);
+            if (c32 > 1.001f) continue;   // factor 1
+            if (c32 < -0.001f) {          // factor 0
+                if (own == kNone) own = (uint32_t)b;
+                v = 0.0;
+                continue;
+            }
+        }
         const double ddx = min_image(d, 0, (double)x, geo[4 * b + 0]);
         const double ddy = min_image(d, 1, (double)y, geo[4 * b + 1]);
         const double ddz = min_image(d, 2, (double)z, geo[4 * b + 2]);
@@ -340,12 +363,20 @@ __device__ void bubble_fill(const Dev& d, const double* geo, int x, int y, int z
         v *= c;
     }
     ph = (float)v;
+    if (minc) *minc = mc;
 }
 
 template <int S>
-__global__ void init_kernel(const Dev d, const double* geo) {
+__global__ void init_kernel(const Dev d, const double* geo, const int use32) {
     using T = typename Store<S>::T;
     T* f = static_cast<T*>(d.f[0]);
+    extern __shared__ float4 sg32[];   // (with use32) the bubbles' centres and r - 1/2 in FP32
+    if (use32) {
+        for (int b = threadIdx.x; b < d.ngeo; b += blockDim.x)
+            sg32[b] = make_float4((float)geo[4 * b], (float)geo[4 * b + 1], (float)geo[4 * b + 2], (float)(geo[4 * b + 3] - 0.5));
+        __syncthreads();
+    }
+    const float4* g32 = use32 ? sg32 : nullptr;
     // every bubble its own root; its initial gas density: rho_gas0, or (hydrostatic start) the
     // liquid's pressure at its centre plus the Laplace jump 2 sigma / r, as a density (p = rho/3)
     // (rows beyond the given bubbles, room for splitting, start free: no cells, no gas)
@@ -360,11 +391,13 @@ __global__ void init_kernel(const Dev d, const double* geo) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.N; i += (size_t)gridDim.x * blockDim.x) {
         int x, y, z;
         cell_xyz(d, i, x, y, z);
-        float ph;
+        float ph, minc;
         uint32_t own;
-        bubble_fill(d, geo, x, y, z, ph, own);
+        bubble_fill(d, geo, g32, x, y, z, ph, own, &minc);
         uint8_t t = ph <= 0.f ? F_GAS : (ph >= 1.f ? F_LIQ : F_IF);
-        if (t == F_LIQ && d.nbub > 0) {   // layer closure
+        // layer closure (a neighbour, at most sqrt 2 away, can be gas only where some bubble's c
+        // is below sqrt 2: with the FP32 distances, a margin beyond that)
+        if (t == F_LIQ && d.nbub > 0 && (!g32 || minc < 1.5f)) {
             for (int q = 1; q < kQ; q++) {
                 size_t j;
                 if (!nbr(d, x, y, z, cx(q), cy(q), cz(q), j)) continue;
@@ -372,7 +405,7 @@ __global__ void init_kernel(const Dev d, const double* geo) {
                 cell_xyz(d, j, a, b, c);
                 float pj;
                 uint32_t oj;
-                bubble_fill(d, geo, a, b, c, pj, oj);
+                bubble_fill(d, geo, g32, a, b, c, pj, oj);
                 if (pj <= 0.f) { t = F_IF; ph = 1.f; own = oj; break; }
             }
         }
@@ -415,10 +448,17 @@ void launch_rho_of_grid(const Dev& d, int g, cudaStream_t s) {
 }
 
 void launch_init(const Dev& d, const double* geo, cudaStream_t s) {
+    // the FP32 prefilter of the fill levels: its table in shared memory, and no bubble within two
+    // cells of half a periodic period (where an FP32 minimum image could pick another image)
+    bool use32 = d.ngeo > 0 && d.ngeo <= 2048 && d.nx <= 4096 && d.ny <= 4096 && d.nz <= 4096;
+    if (use32 && d.geo_rmax + 2.0 >= 0.5 * (double)std::min(d.bc[0] ? d.nx : 1 << 30,
+                                                              std::min(d.bc[1] ? d.ny : 1 << 30, d.bc[2] ? d.nz : 1 << 30)))
+        use32 = false;
+    const size_t shm = use32 ? sizeof(float4) * (size_t)d.ngeo : 0;
     switch (d.storage) {
-        case LBM_STORE_F32: init_kernel<LBM_STORE_F32><<<152 * 16, 256, 0, s>>>(d, geo); break;
-        case LBM_STORE_F16DEV: init_kernel<LBM_STORE_F16DEV><<<152 * 16, 256, 0, s>>>(d, geo); break;
-        default: init_kernel<LBM_STORE_BF16DEV><<<152 * 16, 256, 0, s>>>(d, geo); break;
+        case LBM_STORE_F32: init_kernel<LBM_STORE_F32><<<152 * 16, 256, shm, s>>>(d, geo, use32 ? 1 : 0); break;
+        case LBM_STORE_F16DEV: init_kernel<LBM_STORE_F16DEV><<<152 * 16, 256, shm, s>>>(d, geo, use32 ? 1 : 0); break;
+        default: init_kernel<LBM_STORE_BF16DEV><<<152 * 16, 256, shm, s>>>(d, geo, use32 ? 1 : 0); break;
     }
 }
 
