@@ -939,7 +939,8 @@ void launch_cover_touch(const Dev& d, cudaStream_t st) {
 void launch_spheres_links(const Dev& d, int g, cudaStream_t st) {
     if (d.nsph == 0) return;
     sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
-    sph_contact_kernel<<<d.nsph < 152 * 32 ? (d.nsph + 3) / 4 : 152 * 8, 128, 0, st>>>(d);
+    // (many spheres: two blocks per SM, a share of the warp slots beside the bulk sweep)
+    sph_contact_kernel<<<d.nsph < 152 * 32 ? (d.nsph + 3) / 4 : 152 * 2, 128, 0, st>>>(d);
     sph_gas_kernel<<<d.nsph, 128, 0, st>>>(d, g);
 }
 

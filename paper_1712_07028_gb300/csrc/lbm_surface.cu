@@ -274,7 +274,7 @@ __global__ void list_rescan_kernel(const Dev d) {
 void launch_list_rescan(const Dev& d, cudaStream_t s) {   // after the step close (list length 0)
     const size_t nvec = d.N / 16 + 1;
     int blocks = (int)((nvec + 511) / 512);
-    if (blocks > 152 * 4) blocks = 152 * 4;
+    if (blocks > 152 * 2) blocks = 152 * 2;   // (beside the bulk sweep: a share of the SMs' warp slots)
     list_rescan_kernel<<<blocks, 512, 0, s>>>(d);
 }
 

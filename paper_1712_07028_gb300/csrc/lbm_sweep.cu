@@ -630,7 +630,10 @@ __global__ void __launch_bounds__(256) link_classify_kernel(const Dev d) {
     }
 }
 
-void launch_link_classify(const Dev& d, cudaStream_t s) { link_classify_kernel<<<152 * 8, 256, 0, s>>>(d); }
+// (two blocks per SM: it runs beside the bulk sweep at high priority, and a grid that filled every
+// SM's warp slots would hold them from the bulk sweep's blocks for its whole duration; a single
+// block per SM leaves it too slow for the chain of end-of-step kernels it ends)
+void launch_link_classify(const Dev& d, cudaStream_t s) { link_classify_kernel<<<152 * 2, 256, 0, s>>>(d); }
 
 // a liquid-segment cell whose obstacle links all go into its first sphere P0 (mask: bit q set
 // for a link from an obstacle cell), the others streaming or beyond a no-slip wall: the lean
