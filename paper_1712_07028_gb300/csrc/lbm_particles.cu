@@ -916,12 +916,9 @@ void prepare_sphere_kernels() {
     cudaFuncSetAttribute(sph_substeps_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (13 * 8 + 3 * 4) * 1024);
 }
 
-// forces of the step, lubrication partners, contact links and the sub-stepped motion: reads
-// only the sweep's force sums, the sphere table and obstacle cells, which the conversions
-// leave alone, so it may run concurrently with them
 // the cells whose coverage the move changes (reads only the sphere table; its marks have an
-// array of their own, so it may run while the conversions do)
-// (with more than 1024 spheres the boxes are set up by a kernel of their own)
+// array of their own, so it may run while the conversions do); with more than 1024 spheres the
+// boxes are set up by a kernel of their own
 void launch_cover_touch(const Dev& d, cudaStream_t st) {
     if (d.sphere_mode == LBM_SPHERES_FIXED) return;
     const int nb = (d.nsph + kTouchWarps - 1) / kTouchWarps;
@@ -934,8 +931,9 @@ void launch_cover_touch(const Dev& d, cudaStream_t st) {
 }
 
 // partner lists and the links between obstacle nodes of two spheres: they read only the
-// step-start centres (binned), the sphere table and obstacle cells, so they run while the
-// sweep's boundary kernel does (their sums wait in the accumulators for sph_prepare_one)
+// step-start centres (binned), the sphere table and obstacle cells, all final once the cover
+// kernel has run, so they run beside the rest of the end-of-step kernels, the next bulk sweep and
+// its boundary sweep (their sums wait in the accumulators for sph_prepare_one)
 void launch_spheres_links(const Dev& d, int g, cudaStream_t st) {
     if (d.nsph == 0) return;
     sph_pairs_kernel<<<(d.nsph * 32 + 127) / 128, 128, 0, st>>>(d);
@@ -945,7 +943,9 @@ void launch_spheres_links(const Dev& d, int g, cudaStream_t st) {
 }
 
 // the step's force and torque, then the motion: sub-stepped Newton-Euler (free spheres) or
-// the prescribed velocity
+// the prescribed velocity, lubrication among the partners; it reads only the sweep's force sums,
+// the sphere table and obstacle cells, which the conversions leave alone, so it may run
+// concurrently with them
 void launch_spheres_move(const Dev& d, cudaStream_t st) {
     if (d.nsph == 0) return;
     const int tb = 128, nb = (d.nsph + tb - 1) / tb;
