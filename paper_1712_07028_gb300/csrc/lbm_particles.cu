@@ -713,13 +713,14 @@ __device__ inline void cover_touch_one(const Dev& d, const int P, const int lane
 // (few spheres: one launch less on the step's critical path)
 template <bool Prepared>
 __global__ void __launch_bounds__(32 * kTouchWarps) cover_touch_kernel(const Dev d) {
-    const int P = blockIdx.x * kTouchWarps + (threadIdx.x >> 5);
-    if (P >= d.nsph) return;   // (uniform over the warp)
-    if (!Prepared) {
-        if ((threadIdx.x & 31) == 0) touch_box_prep(d, P);
-        __syncwarp();
+    // (a warp's spheres one after another: the loop bound is uniform over the warp)
+    for (int P = blockIdx.x * kTouchWarps + (threadIdx.x >> 5); P < d.nsph; P += gridDim.x * kTouchWarps) {
+        if (!Prepared) {
+            if ((threadIdx.x & 31) == 0) touch_box_prep(d, P);
+            __syncwarp();
+        }
+        cover_touch_one(d, P, threadIdx.x & 31);
     }
-    cover_touch_one(d, P, threadIdx.x & 31);
 }
 
 // touched cells: the lowest id of the spheres covering them now decides; obstacle cells no
@@ -924,7 +925,9 @@ void launch_cover_touch(const Dev& d, cudaStream_t st) {
     const int nb = (d.nsph + kTouchWarps - 1) / kTouchWarps;
     if (d.nsph > 1024) {
         cover_touch_prep_kernel<<<(d.nsph + 127) / 128, 128, 0, st>>>(d);
-        cover_touch_kernel<true><<<nb, 32 * kTouchWarps, 0, st>>>(d);
+        // (at most four blocks per SM: it runs beside the bulk sweep at high priority, and a grid of
+        // one warp per sphere would take every SM's warp slots while it runs)
+        cover_touch_kernel<true><<<nb < 152 * 4 ? nb : 152 * 4, 32 * kTouchWarps, 0, st>>>(d);
     } else {
         cover_touch_kernel<false><<<nb, 32 * kTouchWarps, 0, st>>>(d);
     }
